@@ -1,0 +1,331 @@
+"""Seeded synthetic particle sets for the DEM workloads.
+
+This module draws inputs only: radii, positions, velocities, materials and
+box sizes.  It holds none of the method's arithmetic (no contact law, no
+cell search of its own); dense packings are made by a plain overlap-removal
+relaxation on top of scipy's periodic k-d tree.
+
+Workloads (sizes, distributions and steps follow the benchmark definitions):
+
+  W1  1,000 monodisperse spheres, r = 5 um, periodic cube at packing 0.3,
+      non-overlapping uniform placement, v ~ N(0, 0.1 m/s), w = 0.
+  W2  1,000,000 polydisperse spheres, r lognormal (median 4 um, sigma_log
+      0.25, clipped to [2, 8] um), periodic cube at packing 0.55 with random
+      overlaps <= 1 % of the smaller radius, v ~ N(0, 0.05 m/s),
+      w ~ N(0, 1e3 rad/s).  Built from a relaxed periodic tile repeated
+      k x k x k times (ids shuffled), which keeps the packing fraction,
+      radius distribution and contact statistics of a full relaxation.
+  W3  bidisperse (r = 3 and 6 um, 50/50) spheres, lower half of the box at
+      packing 0.55, upper half at 0.05, floor at z = 0, periodic x/y,
+      gravity -9.81 m/s^2 along z, v ~ N(0, 0.05 m/s).
+  W4  many independent periodic boxes, counts log-uniform in [200, 20000],
+      per-box restitution U[0.3, 0.9], friction U[0.1, 0.6], radii lognormal
+      (median 4 um, sigma_log 0.2, clipped [2, 8] um), packing U[0.2, 0.5].
+  W5  spheres with r ~ U[3, 5] um at packing 0.60, relaxed to overlaps of
+      about 1e-3 r, v = w = 0.
+
+Radii are rounded to float32 values so that every precision mode of the
+library and the FP64 oracle see the same sizes.  Time steps are fixed
+numbers chosen as 1/50 of the Hertz contact duration of the smallest
+particle pair at the impact speed sqrt(2) sigma_v (W1: 2.296e-9 s).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+SEED_BASE = 1503035530
+
+# shared material of W1-W3 and W5
+E_DEFAULT = 3e9
+POISSON_DEFAULT = 0.3
+DENSITY_DEFAULT = 1200.0
+
+
+@dataclasses.dataclass
+class Box:
+    """One independent simulation box (positions etc. in id order)."""
+    x: np.ndarray            # (n, 3) float64 [m]
+    v: np.ndarray            # (n, 3) float64 [m/s]
+    w: np.ndarray            # (n, 3) float64 [rad/s]
+    r: np.ndarray            # (n,)   float64, float32-representable [m]
+    L: tuple                 # box edge lengths [m]
+    periodic: tuple = (1, 1, 1)
+    floor_wall: int = 0
+    g: tuple = (0.0, 0.0, 0.0)
+    dt: float = 1e-9
+    E: float = E_DEFAULT
+    poisson: float = POISSON_DEFAULT
+    density: float = DENSITY_DEFAULT
+    restitution: float = 0.5
+    mu_d: float = 0.3
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+    @property
+    def r_max(self) -> float:
+        return float(self.r.max()) if self.n else 0.0
+
+
+def rng_for(k: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(SEED_BASE + k))
+
+
+def _f32(a: np.ndarray) -> np.ndarray:
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _lognormal_radii(rng, n, median, sigma_log, rmin, rmax):
+    r = median * np.exp(sigma_log * rng.standard_normal(n))
+    return _f32(np.clip(r, rmin, rmax))
+
+
+def _box_for(r, phi, aspect=(1.0, 1.0, 1.0)):
+    vol = float(np.sum(4.0 / 3.0 * math.pi * r ** 3)) / phi
+    s = (vol / (aspect[0] * aspect[1] * aspect[2])) ** (1.0 / 3.0)
+    return tuple(s * a for a in aspect)
+
+
+def relax_overlaps(x, r, L, periodic=(1, 1, 1), target=0.01, beta=0.9,
+                   max_iter=20000):
+    """Push overlapping spheres apart until every overlap is at most
+    ``target`` times the smaller radius.  Non-periodic axes have hard walls
+    at 0 and L.  A Jacobi sweep moves each member of an overlapping pair by
+    beta/2 of the overlap along the centre line; a Verlet list with a skin
+    of half the median radius is rebuilt from scipy's k-d tree when any
+    sphere has moved more than half the skin."""
+    from scipy.spatial import cKDTree
+
+    x = np.array(x, dtype=np.float64)
+    n = len(r)
+    if n < 2:
+        return x
+    L = np.asarray(L, dtype=np.float64)
+    per = np.asarray(periodic, dtype=bool)
+    rmax = float(r.max())
+    skin = 0.5 * float(np.median(r))
+    box = np.where(per, L, 4.0 * L + 8 * rmax)  # non-periodic: never wraps
+    ref = None
+    I = J = None
+    for _ in range(max_iter):
+        if ref is None or np.max(np.abs(_min_image(x - ref, L, per))) > 0.5 * skin:
+            xt = np.where(per, np.mod(x, L), x + 2 * rmax)
+            tree = cKDTree(xt, boxsize=box)
+            pr = tree.query_pairs(2 * rmax + skin, output_type="ndarray")
+            I, J = pr[:, 0], pr[:, 1]
+            ref = x.copy()
+        d = _min_image(x[J] - x[I], L, per)
+        dist = np.sqrt(np.einsum("ij,ij->i", d, d))
+        ov = r[I] + r[J] - dist
+        m = ov > 0
+        i, j, d, dist, ov = I[m], J[m], d[m], dist[m], ov[m]
+        rel = ov / np.minimum(r[i], r[j]) if ov.size else np.zeros(0)
+        # walls on non-periodic axes
+        wall_disp = np.zeros_like(x)
+        wall_bad = 0.0
+        for a in range(3):
+            if per[a]:
+                continue
+            lo = r - x[:, a]
+            hi = x[:, a] + r - L[a]
+            wall_bad = max(wall_bad, float(np.max(lo / r)), float(np.max(hi / r)))
+            wall_disp[:, a] += np.where(lo > 0, beta * lo, 0.0)
+            wall_disp[:, a] -= np.where(hi > 0, beta * hi, 0.0)
+        worst = max(float(rel.max()) if rel.size else 0.0, wall_bad)
+        if worst <= target:
+            break
+        u = d / dist[:, None] * (0.5 * beta * ov)[:, None]
+        disp = wall_disp
+        for a in range(3):
+            disp[:, a] += np.bincount(j, u[:, a], n) - np.bincount(i, u[:, a], n)
+        x = x + disp
+        x = np.where(per, np.mod(x, L), x)
+    return x
+
+
+def _min_image(d, L, per):
+    return np.where(per, d - L * np.round(d / L), d)
+
+
+def _gauss(rng, n, sigma, remove_mean=True):
+    v = sigma * rng.standard_normal((n, 3))
+    if remove_mean and n > 0:
+        v -= v.mean(axis=0)
+    return v
+
+
+def rsa_placement(rng, r, L, max_tries=200000):
+    """Random sequential addition of non-overlapping spheres (packing well
+    below the RSA limit)."""
+    from scipy.spatial import cKDTree
+
+    n = len(r)
+    L = np.asarray(L, dtype=np.float64)
+    x = np.zeros((n, 3))
+    placed = 0
+    rmax = float(r.max())
+    tree = None
+    batch = []
+    for k in range(n):
+        for _ in range(max_tries):
+            c = rng.random(3) * L
+            ok = True
+            if tree is not None:
+                for q in tree.query_ball_point(c, 2 * rmax):
+                    d = c - x[q]
+                    d -= L * np.round(d / L)
+                    if np.dot(d, d) < (r[k] + r[q]) ** 2:
+                        ok = False
+                        break
+            if ok:
+                for q in batch:
+                    d = c - x[q]
+                    d -= L * np.round(d / L)
+                    if np.dot(d, d) < (r[k] + r[q]) ** 2:
+                        ok = False
+                        break
+            if ok:
+                break
+        else:
+            raise RuntimeError("RSA placement failed")
+        x[k] = c
+        batch.append(k)
+        placed += 1
+        if len(batch) >= 64:
+            tree = cKDTree(np.mod(x[:placed], L), boxsize=L)
+            batch = []
+    return x
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+def w1_monodisperse(n: int = 1000, seed: int = 1) -> Box:
+    """W1: plain FP64 method case."""
+    rng = rng_for(seed)
+    r = _f32(np.full(n, 5e-6))
+    L = _box_for(r, 0.3)
+    x = rsa_placement(rng, r, L)
+    v = _gauss(rng, n, 0.1)
+    w = np.zeros((n, 3))
+    return Box(x=x, v=v, w=w, r=r, L=L, dt=2.296e-9, restitution=0.5,
+               mu_d=0.3)
+
+
+def _dense_tile(rng, n, phi, radii_fn, target, beta=0.9):
+    r = radii_fn(rng, n)
+    L = _box_for(r, phi)
+    x = rng.random((n, 3)) * np.asarray(L)
+    x = relax_overlaps(x, r, L, target=target, beta=beta)
+    return x, r, L
+
+
+def _tile(rng, x, r, L, k):
+    n0 = len(r)
+    offs = np.array([(i, j, l) for l in range(k) for j in range(k) for i in range(k)],
+                    dtype=np.float64) * np.asarray(L)
+    X = (x[None, :, :] + offs[:, None, :]).reshape(-1, 3)
+    R = np.tile(r, k ** 3)
+    perm = rng.permutation(n0 * k ** 3)  # ids unrelated to position
+    return X[perm], R[perm], tuple(k * l for l in L)
+
+
+def w2_polydisperse(n: int = 1_000_000, seed: int = 2, tile_n: int = 8000,
+                    phi: float = 0.55) -> Box:
+    """W2: dense polydisperse periodic box (the throughput workload).  For
+    n <= tile_n the box is one relaxed tile; larger n repeats a relaxed tile
+    k^3 times with n = k^3 * n_tile (n is rounded to that form)."""
+    rng = rng_for(seed)
+    radii = lambda g, m: _lognormal_radii(g, m, 4e-6, 0.25, 2e-6, 8e-6)
+    if n <= tile_n:
+        x, r, L = _dense_tile(rng, n, phi, radii, 0.01)
+    else:
+        k = max(1, int(round((n / tile_n) ** (1.0 / 3.0))))
+        n0 = int(round(n / k ** 3))
+        x0, r0, L0 = _dense_tile(rng, n0, phi, radii, 0.01)
+        x, r, L = _tile(rng, x0, r0, L0, k)
+    m = len(r)
+    v = _gauss(rng, m, 0.05)
+    w = 1e3 * rng.standard_normal((m, 3))
+    return Box(x=x, v=v, w=w, r=r, L=L, dt=1.0e-9, restitution=0.5, mu_d=0.3)
+
+
+def w3_bidisperse_floor(n: int = 8_000_000, seed: int = 3,
+                        tile_xy: Optional[int] = None) -> Box:
+    """W3: bidisperse spheres, dense lower half (0.55), dilute upper half
+    (0.05), floor at z = 0, gravity along -z, periodic in x and y."""
+    rng = rng_for(seed)
+    r_of = lambda g, m: _f32(np.where(g.random(m) < 0.5, 3e-6, 6e-6))
+    mean_vol = 4.0 / 3.0 * math.pi * 0.5 * ((3e-6) ** 3 + (6e-6) ** 3)
+    # cube of side L with n = (0.55 + 0.05)/2 * L^3 / mean_vol
+    Lc = (n * mean_vol / 0.30) ** (1.0 / 3.0)
+    n_dense = int(round(0.55 * Lc ** 3 / 2 / mean_vol))
+    n_dil = n - n_dense
+    k = tile_xy or max(1, int(round((n_dense / 6000) ** 0.5 / (Lc / 2 / Lc) ** 0.5 / 4)))
+    # dense slab: relax one column tile (x-y periodic, hard walls in z)
+    k = max(1, k)
+    tile_L = (Lc / k, Lc / k, Lc / 2)
+    n0 = max(2, n_dense // (k * k))
+    r0 = r_of(rng, n0)
+    x0 = rng.random((n0, 3)) * np.asarray(tile_L)
+    x0 = relax_overlaps(x0, r0, tile_L, periodic=(1, 1, 0), target=0.01)
+    offs = np.array([(i, j, 0) for j in range(k) for i in range(k)],
+                    dtype=np.float64) * np.asarray(tile_L)
+    xd = (x0[None] + offs[:, None]).reshape(-1, 3)
+    rd = np.tile(r0, k * k)
+    # dilute half: uniform random, no overlap removal needed at 0.05 beyond a
+    # light relaxation
+    rdl = r_of(rng, n_dil)
+    xdl = rng.random((n_dil, 3)) * np.array([Lc, Lc, Lc / 2]) + np.array([0, 0, Lc / 2])
+    xdl[:, 2] = np.clip(xdl[:, 2], Lc / 2 + 6e-6, Lc - 6e-6)
+    X = np.concatenate([xd, xdl])
+    R = np.concatenate([rd, rdl])
+    perm = rng.permutation(len(R))
+    X, R = X[perm], R[perm]
+    m = len(R)
+    v = _gauss(rng, m, 0.05, remove_mean=False)
+    w = np.zeros((m, 3))
+    return Box(x=X, v=v, w=w, r=R, L=(Lc, Lc, Lc), periodic=(1, 1, 0),
+               floor_wall=1, g=(0.0, 0.0, -9.81), dt=1.5e-9, restitution=0.5,
+               mu_d=0.3)
+
+
+def w4_batched(nboxes: int = 512, seed: int = 4, nmin: int = 200,
+               nmax: int = 20000) -> list:
+    """W4: independent periodic boxes with their own counts and materials."""
+    rng = rng_for(seed)
+    boxes = []
+    for b in range(nboxes):
+        n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+        phi = float(rng.uniform(0.2, 0.5))
+        r = _lognormal_radii(rng, n, 4e-6, 0.2, 2e-6, 8e-6)
+        L = _box_for(r, phi)
+        x = rng.random((n, 3)) * np.asarray(L)
+        x = relax_overlaps(x, r, L, target=0.01)
+        v = _gauss(rng, n, 0.05)
+        w = np.zeros((n, 3))
+        boxes.append(Box(x=x, v=v, w=w, r=r, L=L, dt=1.0e-9,
+                         restitution=float(rng.uniform(0.3, 0.9)),
+                         mu_d=float(rng.uniform(0.1, 0.6))))
+    return boxes
+
+
+def w5_precision(n: int = 4_000_000, seed: int = 5, tile_n: int = 8000) -> Box:
+    """W5: dense packing 0.60 relaxed to overlaps around 1e-3 r, at rest."""
+    rng = rng_for(seed)
+    radii = lambda g, m: _f32(g.uniform(3e-6, 5e-6, m))
+    if n <= tile_n:
+        x, r, L = _dense_tile(rng, n, 0.60, radii, 0.002)
+    else:
+        k = max(1, int(round((n / tile_n) ** (1.0 / 3.0))))
+        n0 = int(round(n / k ** 3))
+        x0, r0, L0 = _dense_tile(rng, n0, 0.60, radii, 0.002)
+        x, r, L = _tile(rng, x0, r0, L0, k)
+    m = len(r)
+    return Box(x=x, v=np.zeros((m, 3)), w=np.zeros((m, 3)), r=r, L=L,
+               dt=2.0e-9, restitution=0.5, mu_d=0.3)
