@@ -1,0 +1,254 @@
+/*
+ * dem.h -- C ABI of the GB300 DEM library (libdem_gb300.so).
+ *
+ * One time step of the discrete element method of Nakahara & Washizawa,
+ * "Accelerating DEM simulations on GPUs by reducing the impact of warp
+ * divergences" (arXiv 1503.03553), run on one GPU:
+ *   - cell binning and a Morton-ordered counting sort (Sec. 4.2, kernels
+ *     CalcHash, BitonicSort, FindCellBoundsAndReorder),
+ *   - contact detection over the 27 neighbour cells (Sec. 2, last
+ *     paragraph; Algorithm 1) with warp-level compaction of true contacts
+ *     into a dense contact list (the paper's two-loop split, Sec. 3.4 and
+ *     Sec. 4.3, carried to a global list),
+ *   - carry-over of the tangential displacement history between steps
+ *     (Sec. 2 "condensed format of a sparse matrix"; Sec. 4.2
+ *     InitializeContactIDs),
+ *   - Hertz-Mindlin contact force and torque, Eq. (1), Eq. (vt), Eq. (dt),
+ *     the k_n, k_t, eta definitions and the Coulomb cap Eq. (sliding
+ *     friction) with its delta_t reset,
+ *   - floor wall (Sec. 3.3 item 5; CollideRectangle) and gravity
+ *     (ForceGravity),
+ *   - a deterministic per-particle force sum and symplectic Euler
+ *     integration (Sec. 4.2, Integrate).
+ *
+ * Conventions for every entry point
+ *   Units are SI.  Particle arrays are in id order: element k (or row k of
+ *   an n x 3 array, row-major) belongs to particle id k of that box.
+ *   A `where` argument says whether caller pointers are host (DEM_HOST) or
+ *   device (DEM_DEVICE) memory of the context's GPU.  Caller memory is only
+ *   read or written during the call; the library never keeps a caller
+ *   pointer.  The library owns all device state; it allocates it in
+ *   dem_create through the caller's allocator hook (or cudaMallocAsync when
+ *   the hook is NULL) and frees it in dem_destroy.  All work is ordered on
+ *   the configuration's CUDA stream.  Calls on one context must not run
+ *   concurrently from several host threads.
+ *   Errors are returned as dem_status codes; nothing aborts and no C++
+ *   exception crosses the ABI.  A device-side error (capacity overflow,
+ *   non-finite state, failed internal consistency check) is recorded in a
+ *   status word that dem_step returns; it stays set until dem_destroy.
+ *   dem_last_error gives a one-line description of the last failure.
+ */
+#ifndef DEM_GB300_H
+#define DEM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DEM_ABI_VERSION 1
+
+typedef enum {
+  DEM_OK = 0,
+  DEM_ERR_ARG = 1,        /* invalid argument (null, out of range, bad box) */
+  DEM_ERR_ALLOC = 2,      /* device allocation failed                      */
+  DEM_ERR_CUDA = 3,       /* a CUDA runtime call failed                     */
+  DEM_ERR_CAPACITY = 4,   /* a contact row or the contact list overflowed   */
+  DEM_ERR_NONFINITE = 5,  /* a position, velocity or force became NaN/Inf   */
+  DEM_ERR_TIMEOUT = 6,    /* a bounded device wait gave up                  */
+  DEM_ERR_STATE = 7       /* call out of order (e.g. step before particles) */
+} dem_status;
+
+/* Arithmetic of the force path.
+ *   DEM_FP64  : everything in FP64 (the plain form).
+ *   DEM_MIXED : FP32 force arithmetic; master positions in 64-bit fixed
+ *               point (quantum 2^-60 m), overlap from an exact position
+ *               difference, tangential history accumulated as a float-float
+ *               pair.
+ *   DEM_FP32  : FP32 everywhere (positions, history, forces). */
+typedef enum { DEM_FP64 = 0, DEM_MIXED = 1, DEM_FP32 = 2 } dem_precision;
+
+typedef enum { DEM_HOST = 0, DEM_DEVICE = 1 } dem_where;
+
+/* Contact-force kernel layout.
+ *   DEM_COLLIDE_COMPACT : contact search writes a dense contact list; one
+ *                         thread per contact computes the force; a
+ *                         per-particle pass sums it (no float atomics).
+ *   DEM_COLLIDE_FUSED   : Algorithm 1 of the paper: one thread per particle
+ *                         searches and computes the force of each contact as
+ *                         it is found (each pair evaluated from both sides). */
+typedef enum { DEM_COLLIDE_COMPACT = 0, DEM_COLLIDE_FUSED = 1 } dem_collide;
+
+/* One material (Sec. 2: sigma, G, E, m via density; alpha from epsilon).
+ * The transverse modulus is G = E / (2 (1 + poisson)). */
+typedef struct {
+  double E;            /* Young's modulus [Pa]                  */
+  double poisson;      /* Poisson ratio                         */
+  double density;      /* [kg/m^3]                              */
+  double restitution;  /* coefficient of restitution, (0, 1]    */
+  double mu_d;         /* sliding friction coefficient, >= 0    */
+} dem_material;
+
+/* One independent box.  Periodic axes wrap positions into [0, L).
+ * Non-periodic axes are open; floor_wall adds a flat wall at z = 0. */
+typedef struct {
+  double L[3];            /* edge lengths [m], > 0                        */
+  int32_t periodic[3];    /* 1 = periodic                                 */
+  int32_t floor_wall;     /* 1 = wall at z = 0 (z must be non-periodic)    */
+  double g[3];            /* gravity [m/s^2]                              */
+  double dt;              /* time step [s]                                */
+  int32_t material;       /* index into dem_config.materials              */
+  int32_t ncell[3];       /* cell grid; 0 = largest grid with cells at     */
+                          /* least 2 r_max (1 + 1e-5) wide                 */
+  int64_t max_particles;  /* capacity of the box                          */
+  double r_max;           /* largest radius the box will hold [m]         */
+} dem_box;
+
+typedef struct {
+  int32_t nboxes;
+  const dem_box* boxes;
+  int32_t nmaterials;
+  const dem_material* materials;
+  int32_t precision;          /* dem_precision                              */
+  int32_t collide;            /* dem_collide                                */
+  int32_t kn_literal;         /* 1 = k_n with the printed (2 - sigma^2)/E    */
+                              /* term of Sec. 2 instead of Hertz 1 - sigma^2 */
+  int32_t row_capacity;       /* max contacts of one particle; 0 = 32       */
+  int32_t graph_steps;        /* steps per captured CUDA graph; 0 = 16,     */
+                              /* -1 = launch kernels directly              */
+  int32_t block;              /* threads per block of per-particle kernels; */
+                              /* 0 = 256                                   */
+  void* stream;               /* cudaStream_t; NULL = legacy default stream */
+  void* (*alloc)(size_t bytes, void* ctx);  /* device allocator or NULL     */
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+} dem_config;
+
+typedef struct dem_ctx dem_ctx;
+
+/* Create a context on the current CUDA device and allocate all device state
+ * for cfg (copied; cfg need not outlive the call).  On success *out holds
+ * the context; on failure *out is NULL and the status says why.
+ * DEM_ERR_ARG: inconsistent configuration (a periodic axis with fewer than 3
+ * cells, cells narrower than 2 r_max, bad material index, floor on a
+ * periodic z axis, ...). */
+dem_status dem_create(const dem_config* cfg, dem_ctx** out);
+
+/* Replace the particles of one box (Sec. 4.2: the CPU only creates the
+ * initial configuration).  n <= max_particles; x, v, omega: n x 3; radius:
+ * n, each in (0, r_max].  Clears the box's contact history.  In DEM_MIXED
+ * and DEM_FP32 radii are stored as float32 and positions are rounded to the
+ * mode's representation. */
+dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
+                             const double* x, const double* v,
+                             const double* omega, const double* radius,
+                             int32_t where);
+
+/* Overwrite positions, velocities and angular velocities (n x 3 each, any
+ * may be NULL to keep it) of the particles already in a box, keeping radii
+ * and the contact history. */
+dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
+                         const double* v, const double* omega, int32_t where);
+
+/* Advance every box by nsteps >= 0 steps.  Each step: sort by cell, find
+ * contacts, carry delta_t history, compute forces and torques, integrate.
+ * Returns after the work is enqueued and the device status word is read
+ * (one stream synchronisation per call). */
+dem_status dem_step(dem_ctx* ctx, int64_t nsteps);
+
+/* Read the state of one box in id order: x, v, omega (n x 3); force and
+ * torque (n x 3): the totals used in the last step (contacts, wall and
+ * gravity).  Any pointer may be NULL. */
+dem_status dem_get_state(dem_ctx* ctx, int32_t box, double* x, double* v,
+                         double* omega, double* force, double* torque,
+                         int32_t where);
+
+/* Number of particles currently in a box. */
+dem_status dem_get_count(dem_ctx* ctx, int32_t box, int64_t* n);
+
+/* Contact list of one box after the last step (host pointers), sorted by
+ * (id_lo, id_hi), id_lo < id_hi: the pairs found in that step and their
+ * tangential displacement delta_t (cap x 3) after the step's update, as
+ * stored for the next step.  *n receives the count; DEM_ERR_CAPACITY if it
+ * exceeds cap (nothing written then). */
+dem_status dem_get_contacts(dem_ctx* ctx, int32_t box, int64_t cap,
+                            int64_t* n, int32_t* id_lo, int32_t* id_hi,
+                            double* delta_t);
+
+/* Per-contact force of the last step (host pointers), in the order of
+ * dem_get_contacts: F (cap x 3) is the force on particle id_lo from Eq. (1)
+ * after the Coulomb cap; nF (cap x 3) is n x F with n the unit normal from
+ * id_lo to id_hi, so the torques are T_lo = r_lo nF and T_hi = r_hi nF.
+ * Either output may be NULL.  DEM_ERR_CAPACITY if the count exceeds cap. */
+dem_status dem_get_contact_forces(dem_ctx* ctx, int32_t box, int64_t cap,
+                                  int64_t* n, int32_t* id_lo, int32_t* id_hi,
+                                  double* F, double* nF);
+
+/* Replace the contact history of one box (host pointers, any order,
+ * id_lo < id_hi < count) so that the next step starts from it
+ * (checkpoint restore). */
+dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
+                            const int32_t* id_lo, const int32_t* id_hi,
+                            const double* delta_t);
+
+/* Sort order used in the last step (host pointers, n entries each, may be
+ * NULL): the particle id held by each storage slot, and the linear cell
+ * (cz*ny + cy)*nx + cx of that slot.  Slots are ordered by (Morton code of
+ * the cell, id). */
+dem_status dem_get_order(dem_ctx* ctx, int32_t box, int32_t* id_by_slot,
+                         int32_t* cell_by_slot);
+
+/* Cell grid of a box. */
+dem_status dem_get_grid(dem_ctx* ctx, int32_t box, int32_t ncell[3]);
+
+#define DEM_NSTATS 10
+/* Diagnostics of one box from the current state and the last step's
+ * contacts, reduced in FP64 in a fixed order:
+ *   [0] translational kinetic energy   [1] rotational kinetic energy
+ *   [2..4] total momentum              [5] number of contacts
+ *   [6] mean coordination 2 C / n      [7] max overlap / smaller radius
+ *   [8] max |F_t| / (mu |F_n|) before the cap   [9] particles in the box */
+dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]);
+
+/* Milliseconds of device time per step phase, averaged over the steps of
+ * the last dem_step call run with timing on (dem_set_timing).  Phases:
+ * [0] sort (scan, scatter, cell order, reorder)  [1] contact search
+ * [2] list compaction  [3] force  [4] sum + integrate + bin.
+ * Returns the number of phases written (<= cap). */
+int32_t dem_get_phase_times(dem_ctx* ctx, double* ms, int32_t cap);
+dem_status dem_set_timing(dem_ctx* ctx, int32_t on);
+
+/* Kernel launches issued per step by the current configuration. */
+int32_t dem_launches_per_step(const dem_ctx* ctx);
+
+/* Block until all queued work of the context finished; returns the sticky
+ * device status. */
+dem_status dem_sync(dem_ctx* ctx);
+
+/* Description of the last failure on ctx (or of the last dem_create failure
+ * when ctx is NULL).  The string lives until the next call on ctx. */
+const char* dem_last_error(const dem_ctx* ctx);
+
+/* Release all device memory and the context.  NULL is allowed. */
+dem_status dem_destroy(dem_ctx* ctx);
+
+int32_t dem_abi_version(void);
+
+/* Restitution parameter (Sec. 2: eta_n = eta_t = alpha(eps) sqrt(m* k_n
+ * sqrt(dn)), alpha "a function of the coefficient of restitution", not
+ * given in the paper).  The library defines alpha as the exact inverse of
+ * the rebound of its own normal law: the scaled two-body equation
+ * x'' = -x^{3/2} - alpha x^{1/4} x', x(0) = 0, x'(0) = 1, rebounds with
+ * speed eps whatever the impact speed, mass or size.  Host-only functions;
+ * they need no GPU.  dem_alpha_of_restitution(eps) for eps in (0, 1]
+ * (NaN outside, or when eps is below the rebound of alpha = 4);
+ * dem_restitution_of_alpha(alpha) for alpha >= 0 (0 = no rebound). */
+double dem_alpha_of_restitution(double eps);
+double dem_restitution_of_alpha(double alpha);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEM_GB300_H */

@@ -1,0 +1,981 @@
+// dem_engine.cu -- host engine and C ABI of the GB300 DEM library.
+//
+// Owns the device state of all boxes (flat arrays; box b holds storage slots
+// [pbase_b, pbase_b + cap_b) and cells [lin_base_b, lin_base_b + ncells_b)),
+// orders one time step as a fixed sequence of kernels on one stream, and
+// replays G steps at a time from a captured CUDA graph.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dem.h"
+#include "dem_kernels.cuh"
+
+using namespace dem;
+
+namespace {
+
+constexpr int kPhases = 5;
+thread_local std::string g_create_error;
+
+struct Timing {
+  bool on = false;
+  cudaEvent_t ev[kPhases + 1] = {};
+  double acc[kPhases] = {};
+  int steps = 0;
+};
+
+}  // namespace
+
+struct dem_ctx {
+  dem_config cfg{};
+  std::vector<dem_box> boxes;
+  std::vector<dem_material> mats;
+  int mode = kMIXED;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int device = 0;
+  int nsm = 152;
+  int N = 0, K = 32, Cmax = 0, M_lin = 0, M_rank = 0;
+  int block = 256;
+  int graph_steps = 16;
+  int max_cap = 0;
+  std::vector<BoxDev> hbox;
+  std::vector<void*> allocs;
+  Dev dev{};
+  PState ps[2]{};
+  CList cl[2]{};
+  int parity = 0;
+  bool any_floor = false;
+  bool have_particles = false;
+  bool have_ft = false;
+  std::vector<char> hist_cleared;  // per box: history dropped by set_particles
+  unsigned* h_status = nullptr;  // pinned
+  int* h_count = nullptr;        // pinned
+  double* staging = nullptr;     // device, max_cap x 16 doubles
+  int* staging_i = nullptr;      // device, max_cap x 2 ints
+  std::string err;
+  unsigned sticky = 0;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  Timing tm;
+  double phase_ms[kPhases] = {};
+};
+
+namespace {
+
+dem_status fail(dem_ctx* c, dem_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+#define CK(call)                                                          \
+  do {                                                                    \
+    cudaError_t e_ = (call);                                              \
+    if (e_ != cudaSuccess)                                                \
+      return fail(ctx, DEM_ERR_CUDA,                                      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));    \
+  } while (0)
+
+void* dalloc(dem_ctx* ctx, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (ctx->cfg.alloc) {
+    p = ctx->cfg.alloc(bytes, ctx->cfg.alloc_ctx);
+  } else if (cudaMallocAsync(&p, bytes, ctx->stream) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) ctx->allocs.push_back(p);
+  return p;
+}
+
+void free_all(dem_ctx* ctx) {
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) {
+    if (ctx->cfg.free) ctx->cfg.free(p, ctx->cfg.alloc_ctx);
+    else if (!ctx->cfg.alloc) cudaFreeAsync(p, ctx->stream);
+  }
+  ctx->allocs.clear();
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+}
+
+uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  // spread 21 bits of each coordinate three apart (magic-number form)
+  auto spread = [](uint64_t v) {
+    v &= 0x1fffff;
+    v = (v | v << 32) & 0x1f00000000ffffull;
+    v = (v | v << 16) & 0x1f0000ff0000ffull;
+    v = (v | v << 8) & 0x100f00f00f00f00full;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+    v = (v | v << 2) & 0x1249249249249249ull;
+    return v;
+  };
+  return spread(x) | (spread(y) << 1) | (spread(z) << 2);
+}
+
+int launches_per_step(const dem_ctx*) { return 12; }
+
+size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
+size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
+size_t dt_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
+
+int blocks_for(long long n, int b) { return (int)((n + b - 1) / b); }
+
+// --------------------------------------------------------------------------
+// one step, enqueued on ctx->stream
+// --------------------------------------------------------------------------
+template <int M>
+void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
+  const int q = 1 - p;
+  Dev& d = ctx->dev;
+  cudaStream_t s = ctx->stream;
+  const int bs = ctx->block;
+  const bool tm = ctx->tm.on;
+  if (tm) cudaEventRecord(ctx->tm.ev[0], s);
+  // 1. cell counts -> starts (rank order) and ranges (linear cells)
+  int nbc = blocks_for(d.M_rank, kScanTile);
+  k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
+  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0,
+                                           d.status, 0u);
+  k_scan_apply<<<nbc, kScanThreads, 0, s>>>(
+      d.ccount, d.M_rank, d.scan_bsum,
+      CellEpi{d.cstart, d.crange, d.lin_of_rank});
+  // 2. counting sort by (Morton cell, id) and reorder into parity q
+  k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
+  k_cellsort<<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ctx->ps[p]);
+  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q]);
+  if (tm) cudaEventRecord(ctx->tm.ev[1], s);
+  // 3. contact search into per-particle rows
+  k_candidates<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
+  if (tm) cudaEventRecord(ctx->tm.ev[2], s);
+  // 4. owned counts -> dense contact list
+  int nbr = blocks_for(d.N, kScanTile);
+  k_scan_reduce<<<nbr, kScanThreads, 0, s>>>(d.ocnt, d.N, d.scan_bsum);
+  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbr, ctx->cl[q].count,
+                                           d.Cmax, d.status, kStListOverflow);
+  k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.ocnt, d.N, d.scan_bsum,
+                                            RowEpi{d, ctx->ps[q], ctx->cl[q]});
+  if (tm) cudaEventRecord(ctx->tm.ev[3], s);
+  // 5. one thread per contact
+  k_force<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[p], ctx->cl[q]);
+  if (tm) cudaEventRecord(ctx->tm.ev[4], s);
+  // 6. sum, wall, gravity, integrate, bin
+  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q],
+                                                          store_ft ? 1 : 0);
+  if (tm) cudaEventRecord(ctx->tm.ev[5], s);
+}
+
+void enqueue(dem_ctx* ctx, int p, bool store_ft) {
+  switch (ctx->mode) {
+    case kFP64: enqueue_step<kFP64>(ctx, p, store_ft); break;
+    case kMIXED: enqueue_step<kMIXED>(ctx, p, store_ft); break;
+    default: enqueue_step<kFP32>(ctx, p, store_ft); break;
+  }
+}
+
+dem_status check_box(dem_ctx* ctx, int32_t box) {
+  if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");
+  if (box < 0 || box >= (int)ctx->boxes.size())
+    return fail(ctx, DEM_ERR_ARG, "box index out of range");
+  return DEM_OK;
+}
+
+dem_status upload_box(dem_ctx* ctx, int b) {
+  CK(cudaMemcpyAsync((void*)(ctx->dev.boxes + b), &ctx->hbox[b], sizeof(BoxDev),
+                     cudaMemcpyHostToDevice, ctx->stream));
+  return DEM_OK;
+}
+
+dem_status read_status(dem_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_status, ctx->dev.status, sizeof(unsigned),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->sticky |= *ctx->h_status;
+  unsigned st = ctx->sticky;
+  if (st & (kStRowOverflow | kStListOverflow))
+    return fail(ctx, DEM_ERR_CAPACITY,
+                (st & kStRowOverflow) ? "a particle has more contacts than row_capacity"
+                                      : "contact list longer than its capacity");
+  if (st & (kStNonFinite | kStRange))
+    return fail(ctx, DEM_ERR_NONFINITE, "non-finite or out-of-range particle state");
+  if (st & kStInconsistent)
+    return fail(ctx, DEM_ERR_STATE, "contact seen by one member of a pair only");
+  return DEM_OK;
+}
+
+}  // namespace
+
+// ==========================================================================
+// C ABI
+// ==========================================================================
+extern "C" {
+
+int32_t dem_abi_version(void) { return DEM_ABI_VERSION; }
+
+const char* dem_last_error(const dem_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+int32_t dem_launches_per_step(const dem_ctx* ctx) {
+  return ctx ? launches_per_step(ctx) : 0;
+}
+
+dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
+  dem_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, DEM_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!cfg || cfg->nboxes <= 0 || !cfg->boxes || cfg->nmaterials <= 0 ||
+      !cfg->materials)
+    return fail(nullptr, DEM_ERR_ARG, "config needs boxes and materials");
+  if (cfg->precision < 0 || cfg->precision > 2)
+    return fail(nullptr, DEM_ERR_ARG, "bad precision");
+  if (cfg->collide != DEM_COLLIDE_COMPACT)
+    return fail(nullptr, DEM_ERR_ARG, "collide layout not available");
+  if (!!cfg->alloc != !!cfg->free)
+    return fail(nullptr, DEM_ERR_ARG, "alloc and free hooks go together");
+  ctx = new dem_ctx();
+  ctx->cfg = *cfg;
+  ctx->boxes.assign(cfg->boxes, cfg->boxes + cfg->nboxes);
+  ctx->mats.assign(cfg->materials, cfg->materials + cfg->nmaterials);
+  ctx->cfg.boxes = nullptr;
+  ctx->cfg.materials = nullptr;
+  ctx->mode = cfg->precision == DEM_FP64 ? kFP64
+              : cfg->precision == DEM_MIXED ? kMIXED : kFP32;
+  ctx->K = cfg->row_capacity > 0 ? cfg->row_capacity : 32;
+  ctx->block = cfg->block > 0 ? cfg->block : 256;
+  ctx->graph_steps = cfg->graph_steps == 0 ? 16 : cfg->graph_steps;
+  if (ctx->graph_steps > 0 && (ctx->graph_steps & 1)) ctx->graph_steps += 1;
+  auto bail = [&](dem_status s, const std::string& m) {
+    g_create_error = m;
+    if (ctx) {
+      free_all(ctx);
+      if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+      if (ctx->h_status) cudaFreeHost(ctx->h_status);
+      if (ctx->h_count) cudaFreeHost(ctx->h_count);
+      delete ctx;
+    }
+    return s;
+  };
+  if (ctx->K < 2 || ctx->K > 1024) return bail(DEM_ERR_ARG, "row_capacity out of range");
+  if (ctx->block < 32 || ctx->block > 1024 || (ctx->block & 31))
+    return bail(DEM_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
+  if (cudaGetDevice(&ctx->device) != cudaSuccess)
+    return bail(DEM_ERR_CUDA, "no CUDA device");
+  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (cfg->stream) {
+    ctx->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreate(&ctx->stream) != cudaSuccess)
+      return bail(DEM_ERR_CUDA, "stream creation failed");
+    ctx->own_stream = true;
+  }
+
+  // ---- boxes: geometry, cell grids, material constants --------------------
+  long long N = 0, Mlin = 0, Mrank = 0;
+  int max_cap = 0;
+  std::vector<std::vector<int>> rank_tab(ctx->boxes.size());
+  for (size_t b = 0; b < ctx->boxes.size(); ++b) {
+    const dem_box& bx = ctx->boxes[b];
+    BoxDev B{};
+    if (bx.material < 0 || bx.material >= cfg->nmaterials)
+      return bail(DEM_ERR_ARG, "box material index out of range");
+    const dem_material& mt = ctx->mats[bx.material];
+    if (!(mt.E > 0) || !(mt.poisson > -1 && mt.poisson < 0.5) || !(mt.density > 0) ||
+        !(mt.restitution > 0 && mt.restitution <= 1) || !(mt.mu_d >= 0))
+      return bail(DEM_ERR_ARG, "material parameters out of range");
+    if (!(bx.r_max > 0) || !(bx.dt > 0) || bx.max_particles < 0 ||
+        bx.max_particles > (1ll << 30))
+      return bail(DEM_ERR_ARG, "box needs r_max > 0, dt > 0, capacity in [0, 2^30]");
+    if (bx.floor_wall && bx.periodic[2])
+      return bail(DEM_ERR_ARG, "floor wall needs a non-periodic z axis");
+    long long ncell = 1;
+    for (int a = 0; a < 3; ++a) {
+      if (!(bx.L[a] > 0) || bx.L[a] * 0x1p60 >= 0x1p62)
+        return bail(DEM_ERR_ARG, "box length out of range (0, 4 m)");
+      int n = bx.ncell[a];
+      double hmin = 2.0 * bx.r_max * (1.0 + 1e-5);
+      if (n <= 0) n = std::max(1, (int)std::floor(bx.L[a] / hmin));
+      if (bx.L[a] / n < hmin)
+        return bail(DEM_ERR_ARG, "cells narrower than 2 r_max (1 + 1e-5)");
+      if (bx.periodic[a] && n < 3)
+        return bail(DEM_ERR_ARG, "a periodic axis needs at least 3 cells");
+      if (n > kMaxAxisCells) return bail(DEM_ERR_ARG, "more than 1024 cells on an axis");
+      B.n[a] = n;
+      B.periodic[a] = bx.periodic[a] ? 1 : 0;
+      B.Lq[a] = std::llround(std::ldexp(bx.L[a], kFixShift));
+      B.Hq[a] = B.Lq[a] / n;
+      B.L[a] = bx.L[a];
+      B.half_L[a] = 0.5 * bx.L[a];
+      B.inv_h[a] = (double)n / bx.L[a];
+      B.Lf[a] = (float)bx.L[a];
+      B.half_Lf[a] = 0.5f * B.Lf[a];
+      B.inv_hf[a] = (float)((double)n / bx.L[a]);
+      long long H = B.Hq[a], L = B.Lq[a];
+      long long S[5] = {-H, 0, H, (long long)(n - 1) * H - L, L - (long long)(n - 1) * H};
+      for (int k = 0; k < 5; ++k) B.shift[a][k] = (float)S[k] * 0x1p-60f;
+      ncell *= n;
+    }
+    if (ncell > (1ll << 30)) return bail(DEM_ERR_ARG, "too many cells");
+    B.floor_wall = bx.floor_wall ? 1 : 0;
+    ctx->any_floor |= B.floor_wall != 0;
+    B.ncells = (int)ncell;
+    B.lin_base = (int)Mlin;
+    B.rank_base = (int)Mrank;
+    B.pbase = (int)N;
+    B.cap = (int)bx.max_particles;
+    B.nlive = 0;
+    B.dt = bx.dt;
+    B.dt_f = (float)bx.dt;
+    B.dtq_f = (float)std::ldexp(bx.dt, kFixShift);
+    for (int a = 0; a < 3; ++a) {
+      B.g[a] = bx.g[a];
+      B.g_f[a] = (float)bx.g[a];
+    }
+    double s = mt.poisson;
+    double cn = cfg->kn_literal ? (2.0 - s * s) : (1.0 - s * s);
+    double G = mt.E / (2.0 * (1.0 + s));
+    B.kn_c = 4.0 / 3.0 / (cn / mt.E + cn / mt.E);
+    B.kt_c = 8.0 / ((2.0 - s) / G + (2.0 - s) / G);
+    B.alpha = dem_alpha_of_restitution(mt.restitution);
+    if (!std::isfinite(B.alpha)) return bail(DEM_ERR_ARG, "restitution too small");
+    B.mu = mt.mu_d;
+    B.kn_cf = (float)B.kn_c;
+    B.kt_cf = (float)B.kt_c;
+    B.alpha_f = (float)B.alpha;
+    B.mu_f = (float)B.mu;
+    B.density = mt.density;
+    // box-local Morton rank of every cell (dense)
+    std::vector<std::pair<uint64_t, int>> codes((size_t)ncell);
+    for (int cz = 0, l = 0; cz < B.n[2]; ++cz)
+      for (int cy = 0; cy < B.n[1]; ++cy)
+        for (int cx = 0; cx < B.n[0]; ++cx, ++l)
+          codes[l] = {morton3(cx, cy, cz), l};
+    std::sort(codes.begin(), codes.end());
+    rank_tab[b].resize((size_t)ncell);
+    for (long long r = 0; r < ncell; ++r) rank_tab[b][codes[r].second] = (int)r;
+    N += bx.max_particles;
+    Mlin += ncell;
+    Mrank += ncell + 1;
+    max_cap = std::max(max_cap, (int)bx.max_particles);
+    ctx->hbox.push_back(B);
+  }
+  const long long scan_limit = (long long)kScanTile * kScanTopThreads * kScanTopItems;
+  if (N > scan_limit || Mrank > scan_limit)
+    return bail(DEM_ERR_ARG, "more than 2^25 slots or cells in one context");
+  ctx->hist_cleared.assign(ctx->boxes.size(), 0);
+  ctx->N = (int)N;
+  ctx->M_lin = (int)Mlin;
+  ctx->M_rank = (int)Mrank;
+  ctx->max_cap = max_cap;
+  long long cmax = (long long)N * (ctx->K / 2 + 1);
+  if (cmax > (1ll << 31) - 1) cmax = (1ll << 31) - 1;
+  ctx->Cmax = (int)std::max(1ll, cmax);
+
+  // ---- device allocations ----------------------------------------------------
+  const int M = ctx->mode;
+  const size_t n = (size_t)std::max(1, ctx->N);
+  Dev& d = ctx->dev;
+  d.N = ctx->N;
+  d.K = ctx->K;
+  d.Cmax = ctx->Cmax;
+  d.M_lin = ctx->M_lin;
+  d.M_rank = ctx->M_rank;
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* p = dalloc(ctx, bytes);
+    ok = ok && p;
+    return p;
+  };
+  d.boxes = (const BoxDev*)A(sizeof(BoxDev) * ctx->hbox.size());
+  d.slot_box = (const int*)A(sizeof(int) * n);
+  d.rank_of_lin = (const int*)A(sizeof(int) * std::max(1, ctx->M_lin));
+  d.lin_of_rank = (const int*)A(sizeof(int) * std::max(1, ctx->M_rank));
+  d.ccount = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
+  d.cstart = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
+  d.crange = (int2*)A(sizeof(int2) * std::max(1, ctx->M_lin));
+  d.perm = (int*)A(sizeof(int) * n);
+  d.row = (int*)A(sizeof(int) * n * ctx->K);
+  d.ocnt = (int*)A(sizeof(int) * n);
+  d.icnt = (int*)A(sizeof(int) * n);
+  d.hstart = (int*)A(sizeof(int) * n);
+  d.Fc = A(v4_bytes(M) * ctx->Cmax);
+  d.nFc = A(v4_bytes(M) * ctx->Cmax);
+  d.Fout = A(v4_bytes(M) * n);
+  d.Tout = A(v4_bytes(M) * n);
+  d.status = (unsigned*)A(sizeof(unsigned));
+  d.diag = (unsigned*)A(sizeof(unsigned) * 2 * ctx->hbox.size());
+  d.scan_bsum = (int*)A(sizeof(int) * 8192);
+  for (int p = 0; p < 2; ++p) {
+    PState& s = ctx->ps[p];
+    s.px = A(pos_bytes(M) * n);
+    s.py = A(pos_bytes(M) * n);
+    s.pz = A(pos_bytes(M) * n);
+    s.vel = A(v4_bytes(M) * n);
+    s.omg = A(v4_bytes(M) * n);
+    s.posr = A(v4_bytes(M) * n);
+    s.id = (int*)A(sizeof(int) * n);
+    s.cellc = (int*)A(sizeof(int) * n);
+    s.cellg = (int*)A(sizeof(int) * n);
+    if (ctx->any_floor) {
+      s.wx = A(dt_bytes(M) * n);
+      s.wy = A(dt_bytes(M) * n);
+      s.wz = A(dt_bytes(M) * n);
+    }
+    CList& c = ctx->cl[p];
+    c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
+    c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
+    c.dx = A(dt_bytes(M) * ctx->Cmax);
+    c.dy = A(dt_bytes(M) * ctx->Cmax);
+    c.dz = A(dt_bytes(M) * ctx->Cmax);
+    c.rs = (int*)A(sizeof(int) * n);
+    c.rc = (int*)A(sizeof(int) * n);
+    c.count = (int*)A(sizeof(int));
+  }
+  ctx->staging = (double*)A(sizeof(double) * 16 * (size_t)std::max(1, max_cap));
+  ctx->staging_i = (int*)A(sizeof(int) * 2 * (size_t)std::max(1, max_cap));
+  if (!ok) return bail(DEM_ERR_ALLOC, "device allocation failed");
+  if (cudaMallocHost(&ctx->h_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_count, sizeof(int)) != cudaSuccess)
+    return bail(DEM_ERR_ALLOC, "pinned host allocation failed");
+
+  // ---- initial contents --------------------------------------------------------
+  std::vector<int> slot_box(n, 0), rol(std::max(1, ctx->M_lin)),
+      lor(std::max(1, ctx->M_rank)), cnt(std::max(1, ctx->M_rank), 0);
+  for (size_t b = 0; b < ctx->hbox.size(); ++b) {
+    const BoxDev& B = ctx->hbox[b];
+    for (int k = 0; k < B.cap; ++k) slot_box[B.pbase + k] = (int)b;
+    for (int l = 0; l < B.ncells; ++l) {
+      int r = rank_tab[b][l];
+      rol[B.lin_base + l] = r;
+      lor[B.rank_base + r] = B.lin_base + l;
+    }
+    lor[B.rank_base + B.ncells] = -1;
+    cnt[B.rank_base + B.ncells] = B.cap;  // all slots free
+  }
+  cudaStream_t s = ctx->stream;
+  auto H2D = [&](const void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync((void*)dst, src, bytes, cudaMemcpyHostToDevice, s);
+  };
+  cudaError_t e = cudaSuccess;
+  if (!e) e = H2D(d.boxes, ctx->hbox.data(), sizeof(BoxDev) * ctx->hbox.size());
+  if (!e) e = H2D(d.slot_box, slot_box.data(), sizeof(int) * n);
+  if (!e) e = H2D(d.rank_of_lin, rol.data(), sizeof(int) * rol.size());
+  if (!e) e = H2D(d.lin_of_rank, lor.data(), sizeof(int) * lor.size());
+  if (!e) e = H2D(d.ccount, cnt.data(), sizeof(int) * cnt.size());
+  if (!e) e = cudaMemsetAsync(d.status, 0, sizeof(unsigned), s);
+  if (!e) e = cudaMemsetAsync(d.diag, 0, sizeof(unsigned) * 2 * ctx->hbox.size(), s);
+  if (!e) e = cudaMemsetAsync(d.ocnt, 0, sizeof(int) * n, s);
+  if (!e) e = cudaMemsetAsync(d.icnt, 0, sizeof(int) * n, s);
+  for (int p = 0; p < 2 && !e; ++p) {
+    e = cudaMemsetAsync(ctx->cl[p].rc, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(ctx->cl[p].rs, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(ctx->cl[p].count, 0, sizeof(int), s);
+  }
+  if (!e) e = cudaStreamSynchronize(s);
+  if (e) return bail(DEM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  *out = ctx;
+  return DEM_OK;
+}
+
+dem_status dem_destroy(dem_ctx* ctx) {
+  if (!ctx) return DEM_OK;
+  for (auto& g : ctx->gexec)
+    if (g) cudaGraphExecDestroy(g);
+  if (ctx->tm.ev[0])
+    for (auto& ev : ctx->tm.ev) cudaEventDestroy(ev);
+  free_all(ctx);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  if (ctx->h_count) cudaFreeHost(ctx->h_count);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return DEM_OK;
+}
+
+dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
+                             const double* x, const double* v,
+                             const double* omega, const double* radius,
+                             int32_t where) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  BoxDev& B = ctx->hbox[box];
+  if (n < 0 || n > B.cap) return fail(ctx, DEM_ERR_ARG, "n exceeds the box capacity");
+  if (n > 0 && (!x || !v || !omega || !radius))
+    return fail(ctx, DEM_ERR_ARG, "x, v, omega and radius are required");
+  if (where != DEM_HOST && where != DEM_DEVICE) return fail(ctx, DEM_ERR_ARG, "bad where");
+  const double rmax = ctx->boxes[box].r_max;
+  if (where == DEM_HOST) {
+    for (int64_t k = 0; k < n; ++k) {
+      double r = radius[k];
+      if (!(r > 0.0) || r > rmax)
+        return fail(ctx, DEM_ERR_ARG, "radius outside (0, r_max]");
+      for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(x[3 * k + a]) || !std::isfinite(v[3 * k + a]) ||
+            !std::isfinite(omega[3 * k + a]))
+          return fail(ctx, DEM_ERR_ARG, "non-finite particle state");
+    }
+  }
+  cudaStream_t s = ctx->stream;
+  const int p = ctx->parity;
+  // clear the box's cell counts; all unused slots go to its free-slot cell
+  CK(cudaMemsetAsync(ctx->dev.ccount + B.rank_base, 0, sizeof(int) * B.ncells, s));
+  int freec = B.cap - (int)n;
+  CK(cudaMemcpyAsync(ctx->dev.ccount + B.rank_base + B.ncells, &freec, sizeof(int),
+                     cudaMemcpyHostToDevice, s));
+  B.nlive = (int)n;
+  st = upload_box(ctx, box);
+  if (st) return st;
+  // the box's history is empty: no particle owns a stored contact
+  for (int q = 0; q < 2; ++q)
+    CK(cudaMemsetAsync(ctx->cl[q].rc + B.pbase, 0, sizeof(int) * B.cap, s));
+  ctx->hist_cleared[box] = 1;
+  if (n > 0) {
+    const double *dx = x, *dv = v, *dw = omega, *dr = radius;
+    if (where == DEM_HOST) {
+      double* stg = ctx->staging;
+      CK(cudaMemcpyAsync(stg, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(stg + 3 * n, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(stg + 6 * n, omega, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(stg + 9 * n, radius, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      dx = stg;
+      dv = stg + 3 * n;
+      dw = stg + 6 * n;
+      dr = stg + 9 * n;
+    }
+    int nb = blocks_for(n, 256);
+    switch (ctx->mode) {
+      case kFP64: k_set_particles<kFP64><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, (int)n, dx, dv, dw, dr); break;
+      case kMIXED: k_set_particles<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, (int)n, dx, dv, dw, dr); break;
+      default: k_set_particles<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, (int)n, dx, dv, dw, dr); break;
+    }
+    CK(cudaGetLastError());
+  }
+  ctx->have_particles = true;
+  ctx->have_ft = false;
+  return read_status(ctx);
+}
+
+dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
+                         const double* v, const double* omega, int32_t where) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  const BoxDev& B = ctx->hbox[box];
+  int n = B.nlive;
+  if (where != DEM_HOST && where != DEM_DEVICE) return fail(ctx, DEM_ERR_ARG, "bad where");
+  if (n == 0) return DEM_OK;
+  cudaStream_t s = ctx->stream;
+  const double *dx = x, *dv = v, *dw = omega;
+  if (where == DEM_HOST) {
+    double* stg = ctx->staging;
+    if (x) { CK(cudaMemcpyAsync(stg, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)); dx = stg; }
+    if (v) { CK(cudaMemcpyAsync(stg + 3 * n, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)); dv = stg + 3 * n; }
+    if (omega) { CK(cudaMemcpyAsync(stg + 6 * n, omega, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)); dw = stg + 6 * n; }
+  }
+  int nb = blocks_for(n, 256);
+  const int p = ctx->parity;
+  switch (ctx->mode) {
+    case kFP64: k_set_state<kFP64><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, dx, dv, dw); break;
+    case kMIXED: k_set_state<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, dx, dv, dw); break;
+    default: k_set_state<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, dx, dv, dw); break;
+  }
+  CK(cudaGetLastError());
+  return DEM_OK;
+}
+
+static dem_status build_graph(dem_ctx* ctx, int p) {
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  int q = p;
+  for (int k = 0; k < ctx->graph_steps; ++k) {
+    enqueue(ctx, q, k == ctx->graph_steps - 1);
+    q = 1 - q;
+  }
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (e != cudaSuccess) return fail(ctx, DEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&ctx->gexec[p], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(ctx, DEM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return DEM_OK;
+}
+
+dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
+  if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");
+  if (nsteps < 0) return fail(ctx, DEM_ERR_ARG, "nsteps < 0");
+  if (!ctx->have_particles) return fail(ctx, DEM_ERR_STATE, "no particles set");
+  if (ctx->sticky) return read_status(ctx);
+  if (nsteps == 0) return DEM_OK;
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemsetAsync(ctx->dev.diag, 0, sizeof(unsigned) * 2 * ctx->hbox.size(), s));
+  int64_t left = nsteps;
+  const bool timing = ctx->tm.on;
+  if (timing) {
+    for (double& a : ctx->tm.acc) a = 0.0;
+    ctx->tm.steps = 0;
+  }
+  if (ctx->graph_steps > 0 && !timing) {
+    while (left >= ctx->graph_steps) {
+      int p = ctx->parity;
+      if (!ctx->gexec[p]) {
+        dem_status st = build_graph(ctx, p);
+        if (st) return st;
+      }
+      CK(cudaGraphLaunch(ctx->gexec[p], s));
+      left -= ctx->graph_steps;  // an even number of steps: parity unchanged
+    }
+  }
+  while (left > 0) {
+    enqueue(ctx, ctx->parity, left == 1);
+    CK(cudaGetLastError());
+    if (timing) {
+      CK(cudaEventSynchronize(ctx->tm.ev[kPhases]));
+      for (int k = 0; k < kPhases; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->tm.ev[k], ctx->tm.ev[k + 1]);
+        ctx->tm.acc[k] += ms;
+      }
+      ctx->tm.steps++;
+    }
+    ctx->parity = 1 - ctx->parity;
+    --left;
+  }
+  if (timing && ctx->tm.steps)
+    for (int k = 0; k < kPhases; ++k) ctx->phase_ms[k] = ctx->tm.acc[k] / ctx->tm.steps;
+  ctx->have_ft = true;
+  std::fill(ctx->hist_cleared.begin(), ctx->hist_cleared.end(), 0);
+  return read_status(ctx);
+}
+
+dem_status dem_set_timing(dem_ctx* ctx, int32_t on) {
+  if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");
+  if (on && !ctx->tm.ev[0])
+    for (auto& ev : ctx->tm.ev) CK(cudaEventCreate(&ev));
+  ctx->tm.on = on != 0;
+  return DEM_OK;
+}
+
+int32_t dem_get_phase_times(dem_ctx* ctx, double* ms, int32_t cap) {
+  if (!ctx || !ms) return 0;
+  int k = std::min(cap, kPhases);
+  for (int q = 0; q < k; ++q) ms[q] = ctx->phase_ms[q];
+  return k;
+}
+
+dem_status dem_sync(dem_ctx* ctx) {
+  if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");
+  return read_status(ctx);
+}
+
+dem_status dem_get_count(dem_ctx* ctx, int32_t box, int64_t* n) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  if (!n) return fail(ctx, DEM_ERR_ARG, "n is null");
+  *n = ctx->hbox[box].nlive;
+  return DEM_OK;
+}
+
+dem_status dem_get_grid(dem_ctx* ctx, int32_t box, int32_t ncell[3]) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  if (!ncell) return fail(ctx, DEM_ERR_ARG, "ncell is null");
+  for (int a = 0; a < 3; ++a) ncell[a] = ctx->hbox[box].n[a];
+  return DEM_OK;
+}
+
+dem_status dem_get_state(dem_ctx* ctx, int32_t box, double* x, double* v,
+                         double* omega, double* force, double* torque,
+                         int32_t where) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  if (where != DEM_HOST && where != DEM_DEVICE) return fail(ctx, DEM_ERR_ARG, "bad where");
+  const BoxDev& B = ctx->hbox[box];
+  int n = B.nlive;
+  if (n == 0) return DEM_OK;
+  cudaStream_t s = ctx->stream;
+  double* outs[5] = {x, v, omega, force, torque};
+  double* dptr[5];
+  for (int k = 0; k < 5; ++k)
+    dptr[k] = outs[k] ? (where == DEM_HOST ? ctx->staging + (size_t)3 * n * k : outs[k]) : nullptr;
+  int nb = blocks_for(n, 256);
+  const int p = ctx->parity;
+  int hf = ctx->have_ft ? 1 : 0;
+  switch (ctx->mode) {
+    case kFP64: k_get_state<kFP64><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4], hf); break;
+    case kMIXED: k_get_state<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4], hf); break;
+    default: k_get_state<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4], hf); break;
+  }
+  CK(cudaGetLastError());
+  if (where == DEM_HOST)
+    for (int k = 0; k < 5; ++k)
+      if (outs[k])
+        CK(cudaMemcpyAsync(outs[k], dptr[k], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return DEM_OK;
+}
+
+dem_status dem_get_order(dem_ctx* ctx, int32_t box, int32_t* id_by_slot,
+                         int32_t* cell_by_slot) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  const BoxDev& B = ctx->hbox[box];
+  int n = B.nlive;
+  if (n == 0) return DEM_OK;
+  cudaStream_t s = ctx->stream;
+  int* a = ctx->staging_i;
+  int* c = ctx->staging_i + n;
+  k_get_order<<<blocks_for(n, 256), 256, 0, s>>>(ctx->dev, ctx->ps[ctx->parity], box, a, c);
+  CK(cudaGetLastError());
+  if (id_by_slot) CK(cudaMemcpyAsync(id_by_slot, a, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  if (cell_by_slot) CK(cudaMemcpyAsync(cell_by_slot, c, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return DEM_OK;
+}
+
+// Download the current contact list (all boxes) as host vectors.
+static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
+                                std::vector<double>& dts) {
+  cudaStream_t s = ctx->stream;
+  const CList& c = ctx->cl[ctx->parity];
+  CK(cudaMemcpyAsync(ctx->h_count, c.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int nc = *ctx->h_count;
+  hid.resize(nc);
+  dts.assign((size_t)3 * nc, 0.0);
+  if (nc == 0) return DEM_OK;
+  CK(cudaMemcpyAsync(hid.data(), c.hid, sizeof(int2) * nc, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  void* comps[3] = {c.dx, c.dy, c.dz};
+  const size_t eb = dt_bytes(ctx->mode);
+  std::vector<unsigned char> raw(eb * nc);
+  for (int a = 0; a < 3; ++a) {
+    CK(cudaMemcpyAsync(raw.data(), comps[a], eb * nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < nc; ++k) {
+      double val;
+      if (ctx->mode == kMIXED) {
+        float hl[2];
+        std::memcpy(hl, raw.data() + 8 * k, 8);
+        val = (double)hl[0] + (double)hl[1];
+      } else if (ctx->mode == kFP64) {
+        std::memcpy(&val, raw.data() + 8 * k, 8);
+      } else {
+        float f;
+        std::memcpy(&f, raw.data() + 4 * k, 4);
+        val = f;
+      }
+      dts[(size_t)3 * k + a] = val;
+    }
+  }
+  // entries of boxes whose particles were replaced are no longer history
+  size_t w = 0;
+  for (size_t k = 0; k < hid.size(); ++k) {
+    int b = -1;
+    for (size_t q = 0; q < ctx->hbox.size(); ++q)
+      if (hid[k].x >= ctx->hbox[q].pbase && hid[k].x < ctx->hbox[q].pbase + ctx->hbox[q].cap) {
+        b = (int)q;
+        break;
+      }
+    if (b < 0 || ctx->hist_cleared[b]) continue;
+    hid[w] = hid[k];
+    for (int a = 0; a < 3; ++a) dts[3 * w + a] = dts[3 * k + a];
+    ++w;
+  }
+  hid.resize(w);
+  dts.resize(3 * w);
+  return DEM_OK;
+}
+
+dem_status dem_get_contacts(dem_ctx* ctx, int32_t box, int64_t cap, int64_t* n,
+                            int32_t* id_lo, int32_t* id_hi, double* delta_t) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  if (!n) return fail(ctx, DEM_ERR_ARG, "n is null");
+  std::vector<int2> hid;
+  std::vector<double> dts;
+  st = download_list(ctx, hid, dts);
+  if (st) return st;
+  const BoxDev& B = ctx->hbox[box];
+  std::vector<int> sel;
+  for (size_t k = 0; k < hid.size(); ++k)
+    if (hid[k].x >= B.pbase && hid[k].x < B.pbase + B.nlive) sel.push_back((int)k);
+  std::sort(sel.begin(), sel.end(), [&](int a, int b) {
+    return hid[a].x != hid[b].x ? hid[a].x < hid[b].x : hid[a].y < hid[b].y;
+  });
+  *n = (int64_t)sel.size();
+  if ((int64_t)sel.size() > cap) return fail(ctx, DEM_ERR_CAPACITY, "cap smaller than the contact count");
+  for (size_t q = 0; q < sel.size(); ++q) {
+    int k = sel[q];
+    if (id_lo) id_lo[q] = hid[k].x - B.pbase;
+    if (id_hi) id_hi[q] = hid[k].y - B.pbase;
+    if (delta_t)
+      for (int a = 0; a < 3; ++a) delta_t[3 * q + a] = dts[(size_t)3 * k + a];
+  }
+  return DEM_OK;
+}
+
+dem_status dem_get_contact_forces(dem_ctx* ctx, int32_t box, int64_t cap,
+                                  int64_t* n, int32_t* id_lo, int32_t* id_hi,
+                                  double* F, double* nF) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  if (!n) return fail(ctx, DEM_ERR_ARG, "n is null");
+  const BoxDev& B = ctx->hbox[box];
+  cudaStream_t s = ctx->stream;
+  const CList& c = ctx->cl[ctx->parity];
+  CK(cudaMemcpyAsync(ctx->h_count, c.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int nc = ctx->hist_cleared[box] ? 0 : *ctx->h_count;
+  std::vector<int2> hid(nc);
+  const size_t vb = v4_bytes(ctx->mode);
+  std::vector<unsigned char> f(vb * std::max(1, nc)), q(vb * std::max(1, nc));
+  if (nc > 0) {
+    CK(cudaMemcpyAsync(hid.data(), c.hid, sizeof(int2) * nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(f.data(), ctx->dev.Fc, vb * nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(q.data(), ctx->dev.nFc, vb * nc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  std::vector<int> sel;
+  for (int k = 0; k < nc; ++k)
+    if (hid[k].x >= B.pbase && hid[k].x < B.pbase + B.nlive) sel.push_back(k);
+  std::sort(sel.begin(), sel.end(), [&](int a, int b) {
+    return hid[a].x != hid[b].x ? hid[a].x < hid[b].x : hid[a].y < hid[b].y;
+  });
+  *n = (int64_t)sel.size();
+  if ((int64_t)sel.size() > cap) return fail(ctx, DEM_ERR_CAPACITY, "cap smaller than the contact count");
+  auto get = [&](const std::vector<unsigned char>& buf, int k, int a) {
+    if (ctx->mode == kFP64) {
+      double v;
+      std::memcpy(&v, buf.data() + 32 * (size_t)k + 8 * a, 8);
+      return v;
+    }
+    float v;
+    std::memcpy(&v, buf.data() + 16 * (size_t)k + 4 * a, 4);
+    return (double)v;
+  };
+  for (size_t t = 0; t < sel.size(); ++t) {
+    int k = sel[t];
+    if (id_lo) id_lo[t] = hid[k].x - B.pbase;
+    if (id_hi) id_hi[t] = hid[k].y - B.pbase;
+    for (int a = 0; a < 3; ++a) {
+      if (F) F[3 * t + a] = get(f, k, a);
+      if (nF) nF[3 * t + a] = get(q, k, a);
+    }
+  }
+  return DEM_OK;
+}
+
+dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
+                            const int32_t* id_lo, const int32_t* id_hi,
+                            const double* delta_t) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  const BoxDev& B = ctx->hbox[box];
+  if (n < 0 || (n > 0 && (!id_lo || !id_hi || !delta_t)))
+    return fail(ctx, DEM_ERR_ARG, "bad contact arrays");
+  for (int64_t k = 0; k < n; ++k)
+    if (id_lo[k] < 0 || id_hi[k] >= B.nlive || id_lo[k] >= id_hi[k])
+      return fail(ctx, DEM_ERR_ARG, "contact ids must satisfy 0 <= lo < hi < count");
+  std::vector<int2> hid;
+  std::vector<double> dts;
+  st = download_list(ctx, hid, dts);
+  if (st) return st;
+  // keep other boxes' entries, replace this box's
+  std::vector<std::pair<int2, std::array<double, 3>>> all;
+  for (size_t k = 0; k < hid.size(); ++k)
+    if (!(hid[k].x >= B.pbase && hid[k].x < B.pbase + B.cap))
+      all.push_back({hid[k], {dts[3 * k], dts[3 * k + 1], dts[3 * k + 2]}});
+  for (int64_t k = 0; k < n; ++k)
+    all.push_back({make_int2(B.pbase + id_lo[k], B.pbase + id_hi[k]),
+                   {delta_t[3 * k], delta_t[3 * k + 1], delta_t[3 * k + 2]}});
+  std::sort(all.begin(), all.end(), [](const auto& a, const auto& b) {
+    return a.first.x != b.first.x ? a.first.x < b.first.x : a.first.y < b.first.y;
+  });
+  for (size_t k = 1; k < all.size(); ++k)
+    if (all[k].first.x == all[k - 1].first.x && all[k].first.y == all[k - 1].first.y)
+      return fail(ctx, DEM_ERR_ARG, "duplicate contact");
+  if ((long long)all.size() > ctx->Cmax) return fail(ctx, DEM_ERR_CAPACITY, "contact list capacity");
+  const int nc = (int)all.size();
+  std::vector<int> rs(ctx->N, 0), rc(ctx->N, 0);
+  std::vector<int2> h2(nc);
+  const size_t eb = dt_bytes(ctx->mode);
+  std::vector<unsigned char> comp[3];
+  for (int a = 0; a < 3; ++a) comp[a].resize(eb * std::max(1, nc));
+  for (int k = 0; k < nc; ++k) {
+    h2[k] = all[k].first;
+    int lo = all[k].first.x;
+    if (rc[lo] == 0) rs[lo] = k;
+    rc[lo]++;
+    for (int a = 0; a < 3; ++a) {
+      double val = all[k].second[a];
+      if (ctx->mode == kMIXED) {
+        float hl[2];
+        hl[0] = (float)val;
+        hl[1] = (float)(val - (double)hl[0]);
+        std::memcpy(comp[a].data() + 8 * k, hl, 8);
+      } else if (ctx->mode == kFP64) {
+        std::memcpy(comp[a].data() + 8 * k, &val, 8);
+      } else {
+        float f = (float)val;
+        std::memcpy(comp[a].data() + 4 * k, &f, 4);
+      }
+    }
+  }
+  cudaStream_t s = ctx->stream;
+  const CList& c = ctx->cl[ctx->parity];
+  if (nc > 0) {
+    CK(cudaMemcpyAsync(c.hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.dx, comp[0].data(), eb * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.dy, comp[1].data(), eb * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.dz, comp[2].data(), eb * nc, cudaMemcpyHostToDevice, s));
+  }
+  CK(cudaMemcpyAsync(c.rs, rs.data(), sizeof(int) * ctx->N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c.rc, rc.data(), sizeof(int) * ctx->N, cudaMemcpyHostToDevice, s));
+  *ctx->h_count = nc;
+  CK(cudaMemcpyAsync(c.count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  std::fill(ctx->hist_cleared.begin(), ctx->hist_cleared.end(), 0);
+  return DEM_OK;
+}
+
+dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  if (!out) return fail(ctx, DEM_ERR_ARG, "out is null");
+  cudaStream_t s = ctx->stream;
+  double* dout = ctx->staging;
+  const int p = ctx->parity;
+  switch (ctx->mode) {
+    case kFP64: k_stats<kFP64><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dout); break;
+    case kMIXED: k_stats<kMIXED><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dout); break;
+    default: k_stats<kFP32><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dout); break;
+  }
+  CK(cudaGetLastError());
+  double h[6];
+  unsigned dg[2];
+  CK(cudaMemcpyAsync(h, dout, sizeof(h), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(dg, ctx->dev.diag + 2 * box, sizeof(dg), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int n = ctx->hbox[box].nlive;
+  float f0, f1;
+  std::memcpy(&f0, &dg[0], 4);
+  std::memcpy(&f1, &dg[1], 4);
+  out[0] = h[0];
+  out[1] = h[1];
+  out[2] = h[2];
+  out[3] = h[3];
+  out[4] = h[4];
+  out[5] = h[5];
+  out[6] = n > 0 ? 2.0 * h[5] / n : 0.0;
+  out[7] = f0;
+  out[8] = f1;
+  out[9] = n;
+  return DEM_OK;
+}
+
+}  // extern "C"

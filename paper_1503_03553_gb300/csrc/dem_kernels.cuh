@@ -1,0 +1,1245 @@
+// dem_kernels.cuh -- CUDA kernels of one DEM time step (sm_103a).
+//
+// Per step (Nakahara & Washizawa, arXiv 1503.03553, Sec. 4.2 kernel list,
+// re-laid out for one GB300):
+//   scan of cell counts        -> cell starts          (CalcHash/BitonicSort)
+//   k_scatter + k_cellsort     -> permutation by (Morton cell, id)
+//   k_reorder                  -> state in sorted order (FindCellBoundsAndReorder)
+//   k_candidates               -> per-particle contact rows (the loops of
+//                                 Algorithm 1; the paper's first loop, Sec. 3.4)
+//   scan of owned counts       -> dense contact list    (Sec. 3.4 split, global)
+//   k_force                    -> one thread per contact: Eq. (1), Eq. (vt),
+//                                 Eq. (dt), Coulomb cap, history carry
+//                                 (InitializeContactIDs + Collide)
+//   k_gather_integrate         -> per-particle sum in fixed order, floor wall
+//                                 (CollideRectangle), gravity (ForceGravity),
+//                                 symplectic Euler (Integrate), next binning
+#pragma once
+
+#include "dem_common.cuh"
+
+namespace dem {
+
+// ---------------------------------------------------------------------------
+// precision traits
+// ---------------------------------------------------------------------------
+template <int M> struct Tr;
+template <> struct Tr<kMIXED> {
+  using P = long long;  // fixed-point position (quanta)
+  using R = float;      // force arithmetic
+  using V4 = float4;    // (v, m) and (w, r)
+  using PR = float4;    // predicate record: offset from the cell origin + r
+  using DT = float2;    // one delta_t component as (hi, lo)
+};
+template <> struct Tr<kFP64> {
+  using P = double;
+  using R = double;
+  using V4 = d4;
+  using PR = d4;        // absolute position + radius
+  using DT = double;
+};
+template <> struct Tr<kFP32> {
+  using P = float;
+  using R = float;
+  using V4 = float4;
+  using PR = float4;
+  using DT = float;
+};
+
+// One parity of the per-slot particle state (slots sorted by cell).
+struct PState {
+  void* px;
+  void* py;
+  void* pz;
+  void* vel;    // V4 (vx, vy, vz, m)
+  void* omg;    // V4 (wx, wy, wz, r)
+  void* posr;   // PR
+  int* id;      // global id = box slot base + id within the box
+  int* cellc;   // packed cell coordinates
+  int* cellg;   // rank-space cell after integration
+  void* wx;     // floor-wall delta_t (DT); null when no box has a floor
+  void* wy;
+  void* wz;
+};
+
+// One parity of the contact list: the pairs of one step.
+struct CList {
+  int2* pair;   // storage slots (lo, hi) of that step
+  int2* hid;    // global ids (lo, hi), lo < hi
+  void* dx;     // delta_t after the step, per component (DT)
+  void* dy;
+  void* dz;
+  int* rs;      // by global id of the lower particle: first contact ...
+  int* rc;      // ... and the number of contacts it owns
+  int* count;   // number of contacts (device scalar)
+};
+
+struct Dev {
+  const BoxDev* boxes;
+  const int* slot_box;
+  int N;         // slots over all boxes
+  int K;         // row capacity per particle
+  int Cmax;      // contact list capacity
+  int M_lin;     // cells over all boxes
+  int M_rank;    // cells + one free-slot cell per box
+  const int* rank_of_lin;  // box-local Morton rank of each linear cell
+  const int* lin_of_rank;  // global linear cell of each rank cell, -1 = free
+  int* ccount;   // per rank cell: particles binned, then a scatter cursor
+  int* cstart;   // per rank cell: first slot
+  int2* crange;  // per linear cell: (first slot, count)
+  int* perm;     // new slot -> old slot
+  int* row;      // N x K: owned partners from the front, others from the back
+  int* ocnt;     // contacts a slot owns (partner has the larger id)
+  int* icnt;     // contacts owned by the partner
+  int* hstart;   // first list entry of a slot's owned contacts
+  void* Fc;      // V4 per contact: force on the lower-id particle
+  void* nFc;     // V4 per contact: n x F
+  void* Fout;    // V4 per slot: total force of the last step
+  void* Tout;    // V4 per slot: total torque of the last step
+  unsigned* status;
+  unsigned* diag;  // per box: max overlap / r_min, max |F_t| / (mu |F_n|)
+  int* scan_bsum;
+};
+
+__device__ __forceinline__ void flag(unsigned* st, unsigned bit) {
+  atomicOr(st, bit);
+}
+
+// ---------------------------------------------------------------------------
+// small 3-vectors
+// ---------------------------------------------------------------------------
+template <typename R> struct v3 {
+  R x, y, z;
+};
+template <typename R>
+__device__ __forceinline__ v3<R> operator+(v3<R> a, v3<R> b) {
+  return {a.x + b.x, a.y + b.y, a.z + b.z};
+}
+template <typename R>
+__device__ __forceinline__ v3<R> operator-(v3<R> a, v3<R> b) {
+  return {a.x - b.x, a.y - b.y, a.z - b.z};
+}
+template <typename R>
+__device__ __forceinline__ v3<R> operator*(R s, v3<R> a) {
+  return {s * a.x, s * a.y, s * a.z};
+}
+template <typename R>
+__device__ __forceinline__ v3<R> operator*(v3<R> a, R s) {
+  return {a.x * s, a.y * s, a.z * s};
+}
+template <typename R>
+__device__ __forceinline__ R dot(v3<R> a, v3<R> b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename R>
+__device__ __forceinline__ v3<R> cross(v3<R> a, v3<R> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename R>
+__device__ __forceinline__ R norm(v3<R> a) {
+  return sqrt(dot(a, a));
+}
+template <typename V>
+__device__ __forceinline__ auto xyz(V v) -> v3<decltype(v.x)> {
+  return {v.x, v.y, v.z};
+}
+
+// ---------------------------------------------------------------------------
+// cell rule: exact floor division in fixed point; floor(x n / L) otherwise
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ int cell_coord(const BoxDev& B, int a,
+                                          typename Tr<M>::P x);
+template <>
+__device__ __forceinline__ int cell_coord<kMIXED>(const BoxDev& B, int a,
+                                                  long long X) {
+  return clampi(floor_div64(X, B.Hq[a]), B.n[a]);
+}
+template <>
+__device__ __forceinline__ int cell_coord<kFP64>(const BoxDev& B, int a,
+                                                 double x) {
+  return clampi((long long)floor(__dmul_rn(x, B.inv_h[a])), B.n[a]);
+}
+template <>
+__device__ __forceinline__ int cell_coord<kFP32>(const BoxDev& B, int a,
+                                                 float x) {
+  return clampi((long long)floorf(__fmul_rn(x, B.inv_hf[a])), B.n[a]);
+}
+
+__device__ __forceinline__ int rank_cell(const Dev& d, const BoxDev& B, int cx,
+                                         int cy, int cz) {
+  int lin = (cz * B.n[1] + cy) * B.n[0] + cx;
+  return B.rank_base + d.rank_of_lin[B.lin_base + lin];
+}
+
+template <int M>
+__device__ __forceinline__ typename Tr<M>::P wrap_pos(const BoxDev& B, int a,
+                                                      typename Tr<M>::P x);
+template <>
+__device__ __forceinline__ long long wrap_pos<kMIXED>(const BoxDev& B, int a,
+                                                      long long X) {
+  if (!B.periodic[a]) return X;
+  long long L = B.Lq[a];
+  if (X >= L || X < 0) X -= floor_div64(X, L) * L;
+  return X;
+}
+template <>
+__device__ __forceinline__ double wrap_pos<kFP64>(const BoxDev& B, int a,
+                                                  double x) {
+  if (!B.periodic[a]) return x;
+  double L = B.L[a];
+  int guard = 0;
+  while (x >= L && guard++ < 64) x -= L;
+  while (x < 0.0 && guard++ < 128) x += L;
+  return x;
+}
+template <>
+__device__ __forceinline__ float wrap_pos<kFP32>(const BoxDev& B, int a,
+                                                 float x) {
+  if (!B.periodic[a]) return x;
+  float L = B.Lf[a];
+  int guard = 0;
+  while (x >= L && guard++ < 64) x -= L;
+  while (x < 0.0f && guard++ < 128) x += L;
+  return x;
+}
+
+template <int M>
+__device__ __forceinline__ typename Tr<M>::R pos_metres(typename Tr<M>::P p) {
+  return (typename Tr<M>::R)p;
+}
+
+// ---------------------------------------------------------------------------
+// set particles: id order -> slots pbase + id; initial binning
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_set_particles(Dev d, PState s, int box, int n,
+                                const double* __restrict__ x,
+                                const double* __restrict__ v,
+                                const double* __restrict__ w,
+                                const double* __restrict__ r) {
+  using T = Tr<M>;
+  using P = typename T::P;
+  using R = typename T::R;
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const BoxDev& B = d.boxes[box];
+  int slot = B.pbase + k;
+  P p[3];
+  int c[3];
+  bool bad = false;
+  for (int a = 0; a < 3; ++a) {
+    double xa = x[3 * k + a];
+    if (!isfinite(xa)) bad = true;
+    if (M == kMIXED) {
+      double sx = xa * 0x1p60;
+      if (!(fabs(sx) < 0x1p62)) { bad = true; sx = 0.0; }
+      p[a] = (P)wrap_pos<kMIXED>(B, a, __double2ll_rn(sx));
+    } else if (M == kFP64) {
+      p[a] = (P)wrap_pos<kFP64>(B, a, bad ? 0.0 : xa);
+    } else {
+      p[a] = (P)wrap_pos<kFP32>(B, a, bad ? 0.0f : (float)xa);
+    }
+    c[a] = cell_coord<M>(B, a, p[a]);
+  }
+  if (bad) flag(d.status, kStNonFinite);
+  ((P*)s.px)[slot] = p[0];
+  ((P*)s.py)[slot] = p[1];
+  ((P*)s.pz)[slot] = p[2];
+  double rr = r[k];
+  double m = B.density * (4.0 / 3.0) * 3.14159265358979323846 * rr * rr * rr;
+  using V4 = typename T::V4;
+  st4((V4*)s.vel + slot, mk4<R>((R)v[3 * k], (R)v[3 * k + 1], (R)v[3 * k + 2], (R)m));
+  st4((V4*)s.omg + slot, mk4<R>((R)w[3 * k], (R)w[3 * k + 1], (R)w[3 * k + 2], (R)rr));
+  s.id[slot] = slot;
+  s.cellc[slot] = pack_cell(c[0], c[1], c[2]);
+  int g = rank_cell(d, B, c[0], c[1], c[2]);
+  s.cellg[slot] = g;
+  atomicAdd(&d.ccount[g], 1);
+  if (s.wx) {
+    using DT = typename T::DT;
+    ((DT*)s.wx)[slot] = DT{};
+    ((DT*)s.wy)[slot] = DT{};
+    ((DT*)s.wz)[slot] = DT{};
+  }
+}
+
+// Overwrite x / v / w of live particles (id order), keep everything else.
+template <int M>
+__global__ void k_set_state(Dev d, PState s, int box, int n,
+                            const double* __restrict__ x,
+                            const double* __restrict__ v,
+                            const double* __restrict__ w) {
+  using T = Tr<M>;
+  using P = typename T::P;
+  using R = typename T::R;
+  using V4 = typename T::V4;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const BoxDev& B = d.boxes[box];
+  if (t >= B.nlive) return;
+  int slot = B.pbase + t;
+  int k = s.id[slot] - B.pbase;  // id held by this slot
+  if (x) {
+    P p[3];
+    int c[3];
+    for (int a = 0; a < 3; ++a) {
+      double xa = x[3 * k + a];
+      if (M == kMIXED) {
+        double sx = xa * 0x1p60;
+        if (!(fabs(sx) < 0x1p62)) { flag(d.status, kStNonFinite); sx = 0.0; }
+        p[a] = (P)wrap_pos<kMIXED>(B, a, __double2ll_rn(sx));
+      } else if (M == kFP64) {
+        p[a] = (P)wrap_pos<kFP64>(B, a, xa);
+      } else {
+        p[a] = (P)wrap_pos<kFP32>(B, a, (float)xa);
+      }
+      c[a] = cell_coord<M>(B, a, p[a]);
+    }
+    ((P*)s.px)[slot] = p[0];
+    ((P*)s.py)[slot] = p[1];
+    ((P*)s.pz)[slot] = p[2];
+    int old = s.cellg[slot];
+    int g = rank_cell(d, B, c[0], c[1], c[2]);
+    if (g != old) {
+      atomicSub(&d.ccount[old], 1);
+      atomicAdd(&d.ccount[g], 1);
+    }
+    s.cellg[slot] = g;
+    s.cellc[slot] = pack_cell(c[0], c[1], c[2]);
+  }
+  if (v) {
+    V4 q = ((V4*)s.vel)[slot];
+    q.x = (R)v[3 * k];
+    q.y = (R)v[3 * k + 1];
+    q.z = (R)v[3 * k + 2];
+    st4((V4*)s.vel + slot, q);
+  }
+  if (w) {
+    V4 q = ((V4*)s.omg)[slot];
+    q.x = (R)w[3 * k];
+    q.y = (R)w[3 * k + 1];
+    q.z = (R)w[3 * k + 2];
+    st4((V4*)s.omg + slot, q);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// device-wide exclusive scan (three passes, deterministic)
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 4096
+constexpr int kScanTopThreads = 1024;
+constexpr int kScanTopItems = 8;                     // <= 8192 tiles
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns the prefix and
+// the block total in *total
+template <int NT>
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+  __shared__ int wsum[NT / 32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int inc = warp_incl_scan(v);
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < NT / 32 ? wsum[lane] : 0;
+    int si = warp_incl_scan(s);
+    if (lane < NT / 32) wsum[lane] = si - s;
+    if (lane == NT / 32 - 1) *total = si;
+  }
+  __syncthreads();
+  int r = wsum[wid] + inc - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_reduce(const int* __restrict__ in, int n, int* __restrict__ bsum) {
+  int base = blockIdx.x * kScanTile;
+  int s = 0;
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    int idx = base + k;
+    if (idx < n) s += in[idx];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ int ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int q = 0; q < kScanThreads / 32; ++q) t += ws[q];
+    bsum[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the tile sums in place.  *total gets the grand total,
+// clamped to cap (a larger total sets status bit over_bit).
+__global__ void __launch_bounds__(kScanTopThreads)
+k_scan_top(int* bsum, int nb, int* total, int cap, unsigned* status,
+           unsigned over_bit) {
+  __shared__ int tot;
+  int v[kScanTopItems];
+  int s = 0;
+  int base = threadIdx.x * kScanTopItems;
+#pragma unroll
+  for (int q = 0; q < kScanTopItems; ++q) {
+    int idx = base + q;
+    v[q] = idx < nb ? bsum[idx] : 0;
+    s += v[q];
+  }
+  int pre = block_excl_scan<kScanTopThreads>(s, &tot);
+#pragma unroll
+  for (int q = 0; q < kScanTopItems; ++q) {
+    int idx = base + q;
+    if (idx < nb) bsum[idx] = pre;
+    pre += v[q];
+  }
+  if (threadIdx.x == 0 && total) {
+    int t = tot;
+    if (t > cap) {
+      atomicOr(status, over_bit);
+      t = cap;
+    }
+    *total = t;
+  }
+}
+
+// Per tile: coalesced load to shared memory, 16 consecutive items per
+// thread, block scan, then the epilogue is called once per item
+// epi(index, count, exclusive_prefix) with coalesced indices.
+template <class Epi>
+__global__ void __launch_bounds__(kScanThreads)
+k_scan_apply(const int* __restrict__ in, int n, const int* __restrict__ bsum,
+             Epi epi) {
+  __shared__ int buf[kScanTile];
+  __shared__ int tot;
+  int base = blockIdx.x * kScanTile;
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    int idx = base + k;
+    buf[k] = idx < n ? in[idx] : 0;
+  }
+  __syncthreads();
+  int v[kScanItems];
+  int s = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    v[q] = buf[threadIdx.x * kScanItems + q];
+    s += v[q];
+  }
+  int pre = block_excl_scan<kScanThreads>(s, &tot) + bsum[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    buf[threadIdx.x * kScanItems + q] = pre;
+    pre += v[q];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    int idx = base + k;
+    if (idx < n) epi(idx, in[idx], buf[k]);
+  }
+}
+
+// cell counts -> cell starts (rank order) and (start, count) by linear cell
+struct CellEpi {
+  int* cstart;
+  int2* crange;
+  const int* lin_of_rank;
+  __device__ void operator()(int g, int cnt, int pre) const {
+    cstart[g] = pre;
+    int lin = lin_of_rank[g];
+    if (lin >= 0) crange[lin] = make_int2(pre, cnt);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// counting sort: scatter then order each cell by id
+// ---------------------------------------------------------------------------
+__global__ void k_scatter(Dev d, PState a) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[s]];
+  if (s - B.pbase >= B.nlive) return;
+  int g = a.cellg[s];
+  int left = atomicSub(&d.ccount[g], 1);
+  int pos = d.cstart[g] + left - 1;
+  if (left <= 0 || pos < 0 || pos >= d.N) {  // counts out of step: report
+    flag(d.status, kStInconsistent);
+    return;
+  }
+  d.perm[pos] = s;
+}
+
+// Insertion sort of each cell's segment of perm by particle id: the slot
+// order is (Morton rank of the cell, id), independent of atomic timing.
+__global__ void k_cellsort(Dev d, PState a) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= d.M_lin) return;
+  int2 r = d.crange[l];
+  if (r.y < 2) return;
+  int* seg = d.perm + r.x;
+  constexpr int kLocal = 24;
+  if (r.y <= kLocal) {
+    int sl[kLocal], key[kLocal];
+    for (int q = 0; q < r.y; ++q) {
+      sl[q] = seg[q];
+      key[q] = a.id[sl[q]];
+    }
+    for (int q = 1; q < r.y; ++q) {
+      int ks = key[q], ss = sl[q], p = q - 1;
+      while (p >= 0 && key[p] > ks) {
+        key[p + 1] = key[p];
+        sl[p + 1] = sl[p];
+        --p;
+      }
+      key[p + 1] = ks;
+      sl[p + 1] = ss;
+    }
+    for (int q = 0; q < r.y; ++q) seg[q] = sl[q];
+  } else {
+    for (int q = 1; q < r.y; ++q) {
+      int ss = seg[q], ks = a.id[ss], p = q - 1;
+      while (p >= 0 && a.id[seg[p]] > ks) {
+        seg[p + 1] = seg[p];
+        --p;
+      }
+      seg[p + 1] = ss;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// reorder the state into sorted slots; build the predicate record
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_reorder(Dev d, PState a, PState b) {
+  using T = Tr<M>;
+  using P = typename T::P;
+  using V4 = typename T::V4;
+  using PR = typename T::PR;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[t]];
+  if (t - B.pbase >= B.nlive) return;
+  int s = d.perm[t];
+  P x = ((const P*)a.px)[s], y = ((const P*)a.py)[s], z = ((const P*)a.pz)[s];
+  ((P*)b.px)[t] = x;
+  ((P*)b.py)[t] = y;
+  ((P*)b.pz)[t] = z;
+  V4 vel = ld4((const V4*)a.vel + s);
+  V4 om = ld4((const V4*)a.omg + s);
+  st4((V4*)b.vel + t, vel);
+  st4((V4*)b.omg + t, om);
+  b.id[t] = a.id[s];
+  int cc = a.cellc[s];
+  b.cellc[t] = cc;
+  if (a.wx) {
+    using DT = typename T::DT;
+    ((DT*)b.wx)[t] = ((const DT*)a.wx)[s];
+    ((DT*)b.wy)[t] = ((const DT*)a.wy)[s];
+    ((DT*)b.wz)[t] = ((const DT*)a.wz)[s];
+  }
+  PR pr;
+  if (M == kMIXED) {
+    int cx, cy, cz;
+    unpack_cell(cc, cx, cy, cz);
+    long long X = (long long)x, Y = (long long)y, Z = (long long)z;
+    pr.x = __fmul_rn(i64_to_f32_rn(X - (long long)cx * B.Hq[0]), kQ);
+    pr.y = __fmul_rn(i64_to_f32_rn(Y - (long long)cy * B.Hq[1]), kQ);
+    pr.z = __fmul_rn(i64_to_f32_rn(Z - (long long)cz * B.Hq[2]), kQ);
+  } else {
+    pr.x = x;
+    pr.y = y;
+    pr.z = z;
+  }
+  pr.w = om.w;
+  st4((PR*)b.posr + t, pr);
+}
+
+// ---------------------------------------------------------------------------
+// contact predicates (must match the oracle's rounding bit for bit)
+// ---------------------------------------------------------------------------
+// fixed rule: dx = (o_j - o_i) + shift, |d|^2 = (dx dx + dy dy) + dz dz
+__device__ __forceinline__ bool pred_fixed(float4 pi, float4 pj, float sx,
+                                           float sy, float sz) {
+  float dx = __fadd_rn(__fsub_rn(pj.x, pi.x), sx);
+  float dy = __fadd_rn(__fsub_rn(pj.y, pi.y), sy);
+  float dz = __fadd_rn(__fsub_rn(pj.z, pi.z), sz);
+  float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
+                       __fmul_rn(dz, dz));
+  float R = __fadd_rn(pi.w, pj.w);
+  return d2 < __fmul_rn(R, R);
+}
+
+__device__ __forceinline__ double min_image(double d, const BoxDev& B, int a) {
+  if (B.periodic[a]) {
+    if (d > B.half_L[a]) d = __dsub_rn(d, B.L[a]);
+    else if (d < -B.half_L[a]) d = __dadd_rn(d, B.L[a]);
+  }
+  return d;
+}
+__device__ __forceinline__ float min_image(float d, const BoxDev& B, int a) {
+  if (B.periodic[a]) {
+    if (d > B.half_Lf[a]) d = __fsub_rn(d, B.Lf[a]);
+    else if (d < -B.half_Lf[a]) d = __fadd_rn(d, B.Lf[a]);
+  }
+  return d;
+}
+__device__ __forceinline__ bool pred_abs(const d4& pi, const d4& pj,
+                                         const BoxDev& B) {
+  double dx = min_image(__dsub_rn(pj.x, pi.x), B, 0);
+  double dy = min_image(__dsub_rn(pj.y, pi.y), B, 1);
+  double dz = min_image(__dsub_rn(pj.z, pi.z), B, 2);
+  double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
+                        __dmul_rn(dz, dz));
+  double R = __dadd_rn(pi.w, pj.w);
+  return d2 < __dmul_rn(R, R);
+}
+__device__ __forceinline__ bool pred_abs(const float4& pi, const float4& pj,
+                                         const BoxDev& B) {
+  float dx = min_image(__fsub_rn(pj.x, pi.x), B, 0);
+  float dy = min_image(__fsub_rn(pj.y, pi.y), B, 1);
+  float dz = min_image(__fsub_rn(pj.z, pi.z), B, 2);
+  float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
+                       __fmul_rn(dz, dz));
+  float R = __fadd_rn(pi.w, pj.w);
+  return d2 < __fmul_rn(R, R);
+}
+
+// neighbour cell along one axis: returns false when it lies outside a
+// non-periodic box; *shift gets the fixed-rule shift in metres
+__device__ __forceinline__ bool nb_axis(const BoxDev& B, int a, int c, int dlt,
+                                        int& cn, float& shift) {
+  int n = B.n[a];
+  cn = c + dlt;
+  if (cn < 0) {
+    if (!B.periodic[a]) return false;
+    cn = n - 1;
+    shift = B.shift[a][3];
+  } else if (cn >= n) {
+    if (!B.periodic[a]) return false;
+    cn = 0;
+    shift = B.shift[a][4];
+  } else {
+    shift = B.shift[a][dlt + 1];
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// contact search: one thread per particle over the 27 neighbour cells
+// (Algorithm 1 loops), writing partner slots into the particle's row
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_candidates(Dev d, PState b) {
+  using T = Tr<M>;
+  using PR = typename T::PR;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[i]];
+  if (i - B.pbase >= B.nlive) {
+    d.ocnt[i] = 0;
+    d.icnt[i] = 0;
+    return;
+  }
+  const PR* __restrict__ posr = (const PR*)b.posr;
+  PR pi = ld4(posr + i);
+  int idi = b.id[i];
+  int cx, cy, cz;
+  unpack_cell(b.cellc[i], cx, cy, cz);
+  int own = 0, inc = 0;
+  const int K = d.K;
+  int* rowp = d.row + (size_t)i * K;
+  bool over = false;
+  for (int dz = -1; dz <= 1; ++dz) {
+    int czn;
+    float sz;
+    if (!nb_axis(B, 2, cz, dz, czn, sz)) continue;
+    for (int dy = -1; dy <= 1; ++dy) {
+      int cyn;
+      float sy;
+      if (!nb_axis(B, 1, cy, dy, cyn, sy)) continue;
+      for (int dx = -1; dx <= 1; ++dx) {
+        int cxn;
+        float sx;
+        if (!nb_axis(B, 0, cx, dx, cxn, sx)) continue;
+        int lin = (czn * B.n[1] + cyn) * B.n[0] + cxn;
+        int2 rg = d.crange[B.lin_base + lin];
+        for (int j = rg.x; j < rg.x + rg.y; ++j) {
+          if (j == i) continue;
+          PR pj = ld4(posr + j);
+          bool hit;
+          if (M == kMIXED)
+            hit = pred_fixed(*(const float4*)&pi, *(const float4*)&pj, sx, sy, sz);
+          else
+            hit = pred_abs(pi, pj, B);
+          if (hit) {
+            if (own + inc >= K) {
+              over = true;
+              continue;
+            }
+            if (b.id[j] > idi) rowp[own++] = j;
+            else rowp[K - 1 - inc++] = j;
+          }
+        }
+      }
+    }
+  }
+  if (over) flag(d.status, kStRowOverflow);
+  d.ocnt[i] = own;
+  d.icnt[i] = inc;
+}
+
+// owned counts -> contact list: each slot writes its owned pairs at its
+// prefix and its row of the by-id history index
+struct RowEpi {
+  Dev d;
+  PState b;
+  CList cn;
+  __device__ void operator()(int i, int own, int pre) const {
+    d.hstart[i] = pre;
+    const BoxDev& B = d.boxes[d.slot_box[i]];
+    if (i - B.pbase >= B.nlive) return;
+    int idi = b.id[i];
+    int n = own;
+    if (pre + n > d.Cmax) n = max(0, d.Cmax - pre);
+    cn.rs[idi] = pre;
+    cn.rc[idi] = n;
+    const int* rowp = d.row + (size_t)i * d.K;
+    for (int k = 0; k < n; ++k) {
+      int j = rowp[k];
+      cn.pair[pre + k] = make_int2(i, j);
+      cn.hid[pre + k] = make_int2(idi, b.id[j]);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// contact geometry: unit normal n (from 1 to 2) and overlap dn
+// ---------------------------------------------------------------------------
+// Fixed point: exact integer difference, exact float-float |d|^2, then
+// dn = (R^2 - |d|^2) / (R + |d|) with the numerator from float-float terms,
+// so the overlap keeps FP32 relative accuracy however small it is.
+__device__ __forceinline__ void geom_fixed(const BoxDev& B, long long X1,
+                                           long long Y1, long long Z1,
+                                           long long X2, long long Y2,
+                                           long long Z2, float r1, float r2,
+                                           v3<float>& n, float& dn) {
+  long long D[3] = {X2 - X1, Y2 - Y1, Z2 - Z1};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (B.periodic[a]) {
+      long long L = B.Lq[a], h = L >> 1;
+      if (D[a] > h) D[a] -= L;
+      else if (D[a] < -h) D[a] += L;
+    }
+  }
+  ff dx = i64_to_ff(D[0]), dy = i64_to_ff(D[1]), dz = i64_to_ff(D[2]);
+  // to metres (exact power-of-two scaling)
+  dx.hi = __fmul_rn(dx.hi, kQ); dx.lo = __fmul_rn(dx.lo, kQ);
+  dy.hi = __fmul_rn(dy.hi, kQ); dy.lo = __fmul_rn(dy.lo, kQ);
+  dz.hi = __fmul_rn(dz.hi, kQ); dz.lo = __fmul_rn(dz.lo, kQ);
+  ff px = two_prod(dx.hi, dx.hi), py = two_prod(dy.hi, dy.hi),
+     pz = two_prod(dz.hi, dz.hi);
+  ff s1 = two_sum(px.hi, py.hi);
+  ff s2 = two_sum(s1.hi, pz.hi);
+  float t = px.lo + py.lo + pz.lo + s1.lo + s2.lo +
+            2.0f * (dx.hi * dx.lo + dy.hi * dy.lo + dz.hi * dz.lo);
+  ff S = fast_two_sum(s2.hi, t);
+  ff R = two_sum(r1, r2);
+  ff R2 = two_prod(R.hi, R.hi);
+  float R2lo = R2.lo + 2.0f * R.hi * R.lo;
+  ff df = two_sum(R2.hi, -S.hi);
+  float num = df.hi + (df.lo + (R2lo - S.lo));
+  float dist = sqrtf(S.hi);
+  dn = num / (R.hi + dist);
+  if (dist > 0.0f) {
+    float inv = 1.0f / dist;
+    n = {dx.hi * inv, dy.hi * inv, dz.hi * inv};
+  } else {
+    n = {0.0f, 0.0f, 0.0f};
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void geom_abs(const BoxDev& B, R x1, R y1, R z1,
+                                         R x2, R y2, R z2, R r1, R r2,
+                                         v3<R>& n, R& dn) {
+  v3<R> dd = {min_image(x2 - x1, B, 0), min_image(y2 - y1, B, 1),
+              min_image(z2 - z1, B, 2)};
+  R dist = norm(dd);
+  if (dist > R(0)) n = (R(1) / dist) * dd;
+  else n = {R(0), R(0), R(0)};
+  dn = (r1 + r2) - dist;
+}
+
+// ---------------------------------------------------------------------------
+// the contact law (Sec. 2): Eq. (vt), Eq. (dt), Eq. (1), coefficients,
+// Coulomb cap with the delta_t reset.  Particle 1 is the lower id; v is
+// v1 - v2; n points from 1 to 2.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct ContactOut {
+  v3<R> F;      // force on particle 1
+  v3<R> nF;     // n x F
+  v3<R> dt;     // new delta_t (plain part)
+  R ratio;      // |F_t| / (mu |F_n|) before the cap
+  bool capped;
+};
+
+template <typename R>
+__device__ __forceinline__ void contact_law(
+    R kn_c, R kt_c, R alpha, R mu, R dtstep, v3<R> n, R dn, R r1, R r2,
+    R m1, R m2, v3<R> v1, v3<R> v2, v3<R> w1, v3<R> w2, v3<R> dt_old,
+    bool wall, ContactOut<R>& o, v3<R>& dt_delta) {
+  v3<R> v = v1 - v2;
+  R vns = dot(v, n);
+  v3<R> vn = vns * n;
+  v3<R> rot = wall ? r1 * w1 : (r1 * w1 + r2 * w2);
+  v3<R> vt = v - vn + cross(rot, n);                      // Eq. (vt)
+  R dd = dot(dt_old, n);
+  dt_delta = (dtstep * vt) - (dd * n);                     // Eq. (dt) increment
+  v3<R> dtn = dt_old + dt_delta;
+  R Rs = wall ? r1 : r1 * r2 / (r1 + r2);
+  R ms = wall ? m1 : m1 * m2 / (m1 + m2);
+  R sdn = sqrt(dn);
+  R kn = kn_c * sqrt(Rs);
+  R kt = kt_c * sqrt(Rs * dn);
+  R eta = alpha * sqrt(ms * kn * sdn);                     // eta_n = eta_t
+  R fel = kn * dn * sdn;
+  v3<R> Fn = (-fel) * n - eta * vn;                        // Eq. (1), normal
+  v3<R> Ft = (-kt) * dtn - eta * vt;                       // Eq. (1), tangential
+  R aFn = norm(Fn), aFt = norm(Ft);
+  R lim = mu * aFn;
+  o.ratio = lim > R(0) ? aFt / lim : (aFt > R(0) ? R(1e30) : R(0));
+  o.capped = aFt > lim;
+  if (o.capped) {                                          // Eq. (sliding friction)
+    R s = lim / aFt;
+    Ft = s * Ft;
+    dtn = (R(-1) / kt) * Ft;                               // F_t,new = -k_t delta_t
+  }
+  o.dt = dtn;
+  o.F = Fn + Ft;
+  o.nF = cross(n, o.F);
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned* p, float v) {
+  if (v > 0.0f && isfinite(v)) atomicMax(p, __float_as_uint(v));
+}
+
+// ---------------------------------------------------------------------------
+// force: one thread per contact of the dense list
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256)
+k_force(Dev d, PState b, CList co, CList cn) {
+  using T = Tr<M>;
+  using P = typename T::P;
+  using R = typename T::R;
+  using V4 = typename T::V4;
+  using DT = typename T::DT;
+  const int nc = *cn.count;
+  const P* __restrict__ px = (const P*)b.px;
+  const P* __restrict__ py = (const P*)b.py;
+  const P* __restrict__ pz = (const P*)b.pz;
+  const V4* __restrict__ vel = (const V4*)b.vel;
+  const V4* __restrict__ omg = (const V4*)b.omg;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
+       c += gridDim.x * blockDim.x) {
+    int2 pr = cn.pair[c];
+    int2 ids = cn.hid[c];
+    int i = pr.x, j = pr.y;
+    int box = d.slot_box[i];
+    const BoxDev& B = d.boxes[box];
+    // history of this pair from the previous step's list (InitializeContactIDs)
+    int os = co.rs[ids.x], on = co.rc[ids.x], found = -1;
+    for (int k = 0; k < on; ++k)
+      if (co.hid[os + k].y == ids.y) {
+        found = os + k;
+        break;
+      }
+    V4 v1 = ld4(vel + i), v2 = ld4(vel + j);
+    V4 w1 = ld4(omg + i), w2 = ld4(omg + j);
+    R r1 = w1.w, r2 = w2.w;
+    v3<R> n;
+    R dn;
+    if (M == kMIXED) {
+      float fn_dn;
+      v3<float> fn_n;
+      geom_fixed(B, (long long)px[i], (long long)py[i], (long long)pz[i],
+                 (long long)px[j], (long long)py[j], (long long)pz[j],
+                 (float)r1, (float)r2, fn_n, fn_dn);
+      n = {(R)fn_n.x, (R)fn_n.y, (R)fn_n.z};
+      dn = (R)fn_dn;
+    } else {
+      geom_abs<R>(B, (R)px[i], (R)py[i], (R)pz[i], (R)px[j], (R)py[j],
+                  (R)pz[j], r1, r2, n, dn);
+    }
+    V4 F4 = {}, N4 = {};
+    DT ox = {}, oy = {}, oz = {};
+    if (found >= 0) {
+      ox = ((const DT*)co.dx)[found];
+      oy = ((const DT*)co.dy)[found];
+      oz = ((const DT*)co.dz)[found];
+    }
+    DT nx = {}, ny = {}, nz = {};
+    if (dn > R(0)) {
+      v3<R> dold;
+      if (M == kMIXED) {
+        const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
+                     *fz = (const float2*)&oz;
+        dold = {(R)(fx->x + fx->y), (R)(fy->x + fy->y), (R)(fz->x + fz->y)};
+      } else {
+        dold = {*(const R*)&ox, *(const R*)&oy, *(const R*)&oz};
+      }
+      ContactOut<R> o;
+      v3<R> inc;
+      R kn_c = M == kFP64 ? (R)B.kn_c : (R)B.kn_cf;
+      R kt_c = M == kFP64 ? (R)B.kt_c : (R)B.kt_cf;
+      R al = M == kFP64 ? (R)B.alpha : (R)B.alpha_f;
+      R mu = M == kFP64 ? (R)B.mu : (R)B.mu_f;
+      R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
+      contact_law<R>(kn_c, kt_c, al, mu, dts, n, dn, r1, r2, (R)v1.w, (R)v2.w,
+                     xyz(v1), xyz(v2), xyz(w1), xyz(w2), dold, false, o, inc);
+      if (M == kMIXED) {
+        // carry delta_t as a float-float sum unless the cap reset it
+        float2* qx = (float2*)&nx;
+        float2* qy = (float2*)&ny;
+        float2* qz = (float2*)&nz;
+        if (o.capped) {
+          *qx = make_float2((float)o.dt.x, 0.f);
+          *qy = make_float2((float)o.dt.y, 0.f);
+          *qz = make_float2((float)o.dt.z, 0.f);
+        } else {
+          const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
+                       *fz = (const float2*)&oz;
+          ff ax = ff_add_f({fx->x, fx->y}, (float)inc.x);
+          ff ay = ff_add_f({fy->x, fy->y}, (float)inc.y);
+          ff az = ff_add_f({fz->x, fz->y}, (float)inc.z);
+          *qx = make_float2(ax.hi, ax.lo);
+          *qy = make_float2(ay.hi, ay.lo);
+          *qz = make_float2(az.hi, az.lo);
+        }
+      } else {
+        *(R*)&nx = o.dt.x;
+        *(R*)&ny = o.dt.y;
+        *(R*)&nz = o.dt.z;
+      }
+      F4 = mk4<R>(o.F.x, o.F.y, o.F.z, R(0));
+      N4 = mk4<R>(o.nF.x, o.nF.y, o.nF.z, R(0));
+      R rmin = r1 < r2 ? r1 : r2;
+      atomic_max_pos(d.diag + 2 * box, (float)(dn / rmin));
+      atomic_max_pos(d.diag + 2 * box + 1, (float)o.ratio);
+    }
+    ((DT*)cn.dx)[c] = nx;
+    ((DT*)cn.dy)[c] = ny;
+    ((DT*)cn.dz)[c] = nz;
+    st4((V4*)d.Fc + c, F4);
+    st4((V4*)d.nFc + c, N4);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-particle sum (fixed order), floor wall, gravity, symplectic Euler,
+// then binning for the next step
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_gather_integrate(Dev d, PState b, int store_ft) {
+  using T = Tr<M>;
+  using P = typename T::P;
+  using R = typename T::R;
+  using V4 = typename T::V4;
+  using DT = typename T::DT;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[i]];
+  if (i - B.pbase >= B.nlive) return;
+  const V4* Fc = (const V4*)d.Fc;
+  const V4* nFc = (const V4*)d.nFc;
+  v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
+  int own = d.ocnt[i], hs = d.hstart[i], inc = d.icnt[i];
+  for (int k = 0; k < own; ++k) {
+    if (hs + k >= d.Cmax) break;
+    V4 f = ld4(Fc + hs + k), q = ld4(nFc + hs + k);
+    F = F + xyz(f);
+    Ns = Ns + xyz(q);
+  }
+  const int K = d.K;
+  const int* rowi = d.row + (size_t)i * K;
+  for (int k = 0; k < inc; ++k) {
+    int j = rowi[K - 1 - k];
+    int oj = d.ocnt[j], hj = d.hstart[j], c = -1;
+    const int* rowj = d.row + (size_t)j * K;
+    for (int q = 0; q < oj; ++q)
+      if (rowj[q] == i) {
+        c = hj + q;
+        break;
+      }
+    if (c < 0 || c >= d.Cmax) {
+      flag(d.status, kStInconsistent);
+      continue;
+    }
+    V4 f = ld4(Fc + c), q = ld4(nFc + c);
+    F = F - xyz(f);
+    Ns = Ns + xyz(q);
+  }
+  V4 vm = ((const V4*)b.vel)[i];
+  V4 wr = ((const V4*)b.omg)[i];
+  R m = vm.w, r = wr.w;
+  v3<R> Tq = r * Ns;  // T = r (n x F), same sign for both members of a pair
+  P x = ((P*)b.px)[i], y = ((P*)b.py)[i], z = ((P*)b.pz)[i];
+  // floor wall at z = 0: a body of infinite radius and mass at rest
+  if (B.floor_wall) {
+    R dn;
+    if (M == kMIXED) {
+      // overlap r - z from the exact fixed-point height: r (a float) is an
+      // exact count of quanta, so only the final conversion rounds
+      unsigned badr = 0;
+      long long rq = f32_to_i64_rn(__fmul_rn((float)r, kInvQ), &badr);
+      dn = (R)__fmul_rn(i64_to_f32_rn(rq - (long long)z), kQ);
+    } else {
+      dn = r - (R)z;
+    }
+    DT* wx = (DT*)b.wx;
+    DT* wy = (DT*)b.wy;
+    DT* wz = (DT*)b.wz;
+    if (dn > R(0)) {
+      v3<R> dold;
+      DT ox = wx[i], oy = wy[i], oz = wz[i];
+      if (M == kMIXED) {
+        const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
+                     *fz = (const float2*)&oz;
+        dold = {(R)(fx->x + fx->y), (R)(fy->x + fy->y), (R)(fz->x + fz->y)};
+      } else {
+        dold = {*(const R*)&ox, *(const R*)&oy, *(const R*)&oz};
+      }
+      v3<R> nw = {R(0), R(0), R(-1)};
+      v3<R> zero = {R(0), R(0), R(0)};
+      ContactOut<R> o;
+      v3<R> incd;
+      R kn_c = M == kFP64 ? (R)B.kn_c : (R)B.kn_cf;
+      R kt_c = M == kFP64 ? (R)B.kt_c : (R)B.kt_cf;
+      R al = M == kFP64 ? (R)B.alpha : (R)B.alpha_f;
+      R mu = M == kFP64 ? (R)B.mu : (R)B.mu_f;
+      R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
+      contact_law<R>(kn_c, kt_c, al, mu, dts, nw, dn, r, R(0), m, R(0),
+                     xyz(vm), zero, xyz(wr), zero, dold, true, o, incd);
+      F = F + o.F;
+      Tq = Tq + r * o.nF;
+      if (M == kMIXED) {
+        float2 qx, qy, qz;
+        if (o.capped) {
+          qx = make_float2((float)o.dt.x, 0.f);
+          qy = make_float2((float)o.dt.y, 0.f);
+          qz = make_float2((float)o.dt.z, 0.f);
+        } else {
+          const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
+                       *fz = (const float2*)&oz;
+          ff ax = ff_add_f({fx->x, fx->y}, (float)incd.x);
+          ff ay = ff_add_f({fy->x, fy->y}, (float)incd.y);
+          ff az = ff_add_f({fz->x, fz->y}, (float)incd.z);
+          qx = make_float2(ax.hi, ax.lo);
+          qy = make_float2(ay.hi, ay.lo);
+          qz = make_float2(az.hi, az.lo);
+        }
+        wx[i] = *(DT*)&qx;
+        wy[i] = *(DT*)&qy;
+        wz[i] = *(DT*)&qz;
+      } else {
+        R tx = o.dt.x, ty = o.dt.y, tz = o.dt.z;
+        wx[i] = *(DT*)&tx;
+        wy[i] = *(DT*)&ty;
+        wz[i] = *(DT*)&tz;
+      }
+    } else {
+      wx[i] = DT{};
+      wy[i] = DT{};
+      wz[i] = DT{};
+    }
+  }
+  // gravity (ForceGravity)
+  if (M == kFP64) F = F + m * v3<R>{(R)B.g[0], (R)B.g[1], (R)B.g[2]};
+  else F = F + m * v3<R>{(R)B.g_f[0], (R)B.g_f[1], (R)B.g_f[2]};
+  if (store_ft) {
+    st4((V4*)d.Fout + i, mk4<R>(F.x, F.y, F.z, R(0)));
+    st4((V4*)d.Tout + i, mk4<R>(Tq.x, Tq.y, Tq.z, R(0)));
+  }
+  // symplectic Euler: v += F/m dt, w += T/I dt, x += v dt, I = 2/5 m r^2
+  R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
+  R am = dts / m;
+  R aw = dts / (R(0.4) * m * r * r);
+  vm.x += F.x * am;
+  vm.y += F.y * am;
+  vm.z += F.z * am;
+  wr.x += Tq.x * aw;
+  wr.y += Tq.y * aw;
+  wr.z += Tq.z * aw;
+  bool finite = isfinite(vm.x) && isfinite(vm.y) && isfinite(vm.z) &&
+                isfinite(wr.x) && isfinite(wr.y) && isfinite(wr.z);
+  if (!finite) {
+    flag(d.status, kStNonFinite);
+    vm.x = vm.y = vm.z = R(0);
+    wr.x = wr.y = wr.z = R(0);
+  }
+  st4((V4*)b.vel + i, vm);
+  st4((V4*)b.omg + i, wr);
+  int c[3];
+  int cc = b.cellc[i];
+  unpack_cell(cc, c[0], c[1], c[2]);
+  P p[3] = {x, y, z};
+  R vv[3] = {vm.x, vm.y, vm.z};
+  unsigned bad = 0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (M == kMIXED) {
+      long long X = (long long)p[a];
+      long long D = f32_to_i64_rn(__fmul_rn((float)vv[a], B.dtq_f), &bad);
+      X += D;
+      int ca = c[a];
+      const long long H = B.Hq[a];
+      const int n = B.n[a];
+      if (B.periodic[a]) {
+        const long long L = B.Lq[a];
+        if (X >= L) {
+          X -= L;
+          ca = 0;
+        } else if (X < 0) {
+          X += L;
+          ca = n - 1;
+        }
+        if (X < 0 || X >= L) {  // moved more than a box length
+          X = wrap_pos<kMIXED>(B, a, X);
+          ca = cell_coord<kMIXED>(B, a, X);
+        }
+      }
+      // step to the containing cell (particles move far less than a cell)
+      int guard = 0;
+      while (ca > 0 && X < (long long)ca * H && guard++ < 4) --ca;
+      while (ca < n - 1 && X >= (long long)(ca + 1) * H && guard++ < 8) ++ca;
+      if (guard >= 4) ca = cell_coord<kMIXED>(B, a, X);
+      p[a] = (P)X;
+      c[a] = ca;
+    } else {
+      P xa = p[a] + (P)(vv[a] * dts);
+      xa = wrap_pos<M>(B, a, xa);
+      p[a] = xa;
+      c[a] = cell_coord<M>(B, a, xa);
+    }
+  }
+  if (bad) flag(d.status, kStRange);
+  ((P*)b.px)[i] = p[0];
+  ((P*)b.py)[i] = p[1];
+  ((P*)b.pz)[i] = p[2];
+  b.cellc[i] = pack_cell(c[0], c[1], c[2]);
+  int g = rank_cell(d, B, c[0], c[1], c[2]);
+  b.cellg[i] = g;
+  atomicAdd(&d.ccount[g], 1);
+}
+
+// ---------------------------------------------------------------------------
+// state out (id order, FP64)
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_get_state(Dev d, PState b, int box, double* x, double* v,
+                            double* w, double* F, double* Tq, int have_ft) {
+  using T = Tr<M>;
+  using P = typename T::P;
+  using V4 = typename T::V4;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const BoxDev& B = d.boxes[box];
+  if (t >= B.nlive) return;
+  int slot = B.pbase + t;
+  int k = b.id[slot] - B.pbase;
+  if (x) {
+    P p[3] = {((P*)b.px)[slot], ((P*)b.py)[slot], ((P*)b.pz)[slot]};
+    for (int a = 0; a < 3; ++a) {
+      if (M == kMIXED) x[3 * k + a] = (double)(long long)p[a] * 0x1p-60;
+      else x[3 * k + a] = (double)p[a];
+    }
+  }
+  if (v) {
+    V4 q = ((const V4*)b.vel)[slot];
+    v[3 * k] = q.x;
+    v[3 * k + 1] = q.y;
+    v[3 * k + 2] = q.z;
+  }
+  if (w) {
+    V4 q = ((const V4*)b.omg)[slot];
+    w[3 * k] = q.x;
+    w[3 * k + 1] = q.y;
+    w[3 * k + 2] = q.z;
+  }
+  if (F) {
+    V4 q = {};
+    if (have_ft) q = ((const V4*)d.Fout)[slot];
+    F[3 * k] = q.x;
+    F[3 * k + 1] = q.y;
+    F[3 * k + 2] = q.z;
+  }
+  if (Tq) {
+    V4 q = {};
+    if (have_ft) q = ((const V4*)d.Tout)[slot];
+    Tq[3 * k] = q.x;
+    Tq[3 * k + 1] = q.y;
+    Tq[3 * k + 2] = q.z;
+  }
+}
+
+__global__ void k_get_order(Dev d, PState b, int box, int* id_by_slot,
+                            int* cell_by_slot) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const BoxDev& B = d.boxes[box];
+  if (t >= B.nlive) return;
+  int slot = B.pbase + t;
+  if (id_by_slot) id_by_slot[t] = b.id[slot] - B.pbase;
+  if (cell_by_slot) {
+    int cx, cy, cz;
+    unpack_cell(b.cellc[slot], cx, cy, cz);
+    cell_by_slot[t] = (cz * B.n[1] + cy) * B.n[0] + cx;
+  }
+}
+
+// per-box FP64 reductions in a fixed order (one block per box)
+template <int M>
+__global__ void k_stats(Dev d, PState b, int box, double* out) {
+  using T = Tr<M>;
+  using V4 = typename T::V4;
+  const BoxDev& B = d.boxes[box];
+  double acc[6] = {0, 0, 0, 0, 0, 0};  // KEt, KEr, Px, Py, Pz, contacts
+  for (int t = threadIdx.x; t < B.nlive; t += blockDim.x) {
+    int s = B.pbase + t;
+    V4 vm = ((const V4*)b.vel)[s];
+    V4 wr = ((const V4*)b.omg)[s];
+    double m = vm.w, r = wr.w;
+    double vx = vm.x, vy = vm.y, vz = vm.z;
+    double wx = wr.x, wy = wr.y, wz = wr.z;
+    acc[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+    acc[1] += 0.5 * 0.4 * m * r * r * (wx * wx + wy * wy + wz * wz);
+    acc[2] += m * vx;
+    acc[3] += m * vy;
+    acc[4] += m * vz;
+    acc[5] += (double)d.ocnt[s];
+  }
+  __shared__ double sh[6][256];
+  for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 6; ++q) out[q] = sh[q][0];
+}
+
+}  // namespace dem

@@ -1,0 +1,189 @@
+"""Parity harness: one step of the CUDA library against the FP64 oracle.
+
+Both sides start from the same seeded state.  Positions are quantised to the
+library's 2^-60 m fixed point (DEM_MIXED) or rounded to float32 (DEM_FP32)
+before either side sees them, radii are float32 values already, and both
+sides use the same explicit cell grid, so the contact predicate and the sort
+order can be compared bit for bit.
+
+Tolerances (per contact c, oracle values):
+  |F_gpu - F_ora|   <= rtol * S_c + f_c
+  |nF_gpu - nF_ora| <= rtol * S_c + f_c + 1e-6 |F_ora|
+  S_c = k_n dn^1.5 + eta |v_n| + k_t |delta_t| + eta |v_t|  (sum of the
+        magnitudes of the terms of Eq. (1): the error of a float sum is
+        bounded by the unit roundoff times this, not by |F|)
+  f_c = 1e-9 k_n R*^1.5  (absolute floor)
+with rtol = 1e-5 for FP32 force arithmetic and 1e-9 for FP64.  Contacts whose
+Coulomb ratio lies within 1e-4 of 1 may be capped on one side only and are
+reported, not compared.  Per particle the bounds add up over its contacts.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+import oracle as O
+
+RTOL = {"mixed": 1e-5, "fp32": 1e-5, "fp64": 1e-9}
+PRED = {"mixed": O.PRED_FIXED_F32, "fp64": O.PRED_FP64, "fp32": O.PRED_ABS_F32}
+
+
+def quantize(x):
+    return np.ldexp(np.round(np.ldexp(np.asarray(x, np.float64), 60)), -60)
+
+
+def grid_for(box):
+    hmin = 2.0 * box.r_max * (1.0 + 1e-5)
+    return [max(1, int(math.floor(box.L[a] / hmin))) for a in range(3)]
+
+
+def prepared(box, precision):
+    """Copy of ``box`` with positions in the precision mode's representation
+    (so that both sides start from bit-identical positions)."""
+    b = dataclasses.replace(box)
+    x = np.array(box.x, np.float64)
+    L = np.asarray(box.L)
+    per = np.asarray(box.periodic, bool)
+    x = np.where(per, np.mod(x, L), x)
+    if precision == "mixed":
+        x = quantize(x)
+        x = np.where(per & (x >= L), x - L, x)
+    elif precision == "fp32":
+        x = x.astype(np.float32).astype(np.float64)
+        x = np.where(per & (x >= L.astype(np.float32)), 0.0, x)
+    b.x = x
+    b.v = np.array(box.v, np.float64)
+    b.w = np.array(box.w, np.float64)
+    b.r = np.array(box.r, np.float64)
+    return b
+
+
+def oracle_params(box, precision, ncell, brute_force=0):
+    return O.make_params(box.L, box.dt, E=box.E, poisson=box.poisson,
+                         density=box.density, restitution=box.restitution,
+                         mu_d=box.mu_d, periodic=box.periodic,
+                         floor_wall=box.floor_wall, g=box.g, ncell=ncell,
+                         predicate=PRED[precision], brute_force=brute_force)
+
+
+def gpu_run(boxes, precision, ncells, steps=1, **kw):
+    """Create a context for ``boxes``, set particles, run ``steps`` steps
+    and collect everything per box."""
+    import paper_1503_03553_gb300 as D
+
+    ctx = D.Context(boxes, precision=precision, ncell=ncells, **kw)
+    try:
+        for k, b in enumerate(boxes):
+            ctx.set_particles(k, b.x, b.v, b.w, b.r)
+        ctx.step(steps)
+        out = []
+        for k in range(len(boxes)):
+            st = ctx.get_state(k)
+            lo, hi, dt = ctx.contacts(k)
+            flo, fhi, F, nF = ctx.contact_forces(k)
+            order, cells = ctx.order(k)
+            out.append(dict(state=st, lo=lo, hi=hi, dt=dt, flo=flo, fhi=fhi, Fc=F,
+                            nFc=nF, order=order, cells=cells, stats=ctx.stats(k)))
+        return out
+    finally:
+        ctx.close()
+
+
+def oracle_run(box, precision, ncell):
+    p = oracle_params(box, precision, ncell)
+    cell, order = O.order(p, box.x)
+    s = O.State(box.x, box.v, box.w, box.r, floor_wall=bool(box.floor_wall))
+    x0, v0, w0 = s.x.copy(), s.v.copy(), s.w.copy()
+    out = O.step(p, s)
+    out.update(order=order, cell=cell, x=s.x, v=s.v, w=s.w, x0=x0, v0=v0, w0=w0,
+               params=p)
+    return out
+
+
+def _contact_bounds(box, o, rtol):
+    info = o["info"]
+    lo, hi = o["lo"], o["hi"]
+    r = box.r
+    Rs = r[lo] * r[hi] / (r[lo] + r[hi])
+    kn_c = O.kn(o["params"], 1.0, 1.0) / math.sqrt(0.5)
+    kn = kn_c * np.sqrt(Rs)
+    floor = 1e-9 * kn * Rs ** 1.5
+    bF = rtol * info["scale"] + floor
+    return bF, floor
+
+
+def check_one_step(box, g, o, precision, allow_dont_care=True):
+    """Compare one step; returns a metrics dict, raises AssertionError."""
+    rtol = RTOL[precision]
+    m = {}
+    # 1. sort order and contact set: bit-exact
+    assert np.array_equal(g["order"], o["order"]), "sort order differs"
+    assert np.array_equal(g["cells"], o["cell"][o["order"]]), "cells differ"
+    assert np.array_equal(g["lo"], o["lo"]) and np.array_equal(g["hi"], o["hi"]), (
+        f"contact sets differ: gpu {len(g['lo'])} oracle {len(o['lo'])}")
+    assert np.array_equal(g["flo"], o["lo"]) and np.array_equal(g["fhi"], o["hi"])
+    nc = len(o["lo"])
+    m["contacts"] = nc
+    info = o["info"]
+    bF, floor = _contact_bounds(box, o, rtol)
+    dont = np.abs(info["ratio"] - 1.0) < 1e-4 if allow_dont_care else np.zeros(nc, bool)
+    m["dont_care"] = int(dont.sum())
+    ok = ~dont
+    eF = np.linalg.norm(g["Fc"] - info["F"], axis=1)
+    enF = np.linalg.norm(g["nFc"] - info["nF"], axis=1)
+    normF = np.linalg.norm(info["F"], axis=1)
+    if nc:
+        m["max_F_err_over_scale"] = float(np.max((eF / (info["scale"] + floor))[ok], initial=0))
+        rel = eF / np.maximum(normF, 1e-300)
+        m["p99_F_rel_err"] = float(np.percentile(rel[ok & (normF > 0)], 99)) if np.any(ok & (normF > 0)) else 0.0
+        bad = ok & (eF > bF)
+        assert not np.any(bad), (
+            f"{int(bad.sum())} contact forces outside tolerance; worst "
+            f"{float(np.max((eF / bF)[ok])):.3g} x bound")
+        bad = ok & (enF > bF + 1e-6 * normF)
+        assert not np.any(bad), f"{int(bad.sum())} n x F outside tolerance"
+        # tangential history after the step
+        lo, hi = o["lo"], o["hi"]
+        v0, w0, r = o["v0"], o["w0"], box.r
+        vscale = (np.linalg.norm(v0[lo], axis=1) + np.linalg.norm(v0[hi], axis=1)
+                  + r[lo] * np.linalg.norm(w0[lo], axis=1) + r[hi] * np.linalg.norm(w0[hi], axis=1))
+        kt = np.where(info["kt"] > 0, info["kt"], np.inf)
+        bdt = rtol * (np.linalg.norm(o["dt"], axis=1) + box.dt * vscale + info["scale"] / kt) + 1e-30
+        edt = np.linalg.norm(g["dt"] - o["dt"], axis=1)
+        bad = ok & (edt > bdt)
+        assert not np.any(bad), f"{int(bad.sum())} delta_t outside tolerance"
+        m["max_dt_err_over_bound"] = float(np.max((edt / bdt)[ok], initial=0))
+    # 2. per-particle totals
+    n = box.n
+    bP = np.zeros(n)
+    np.add.at(bP, o["lo"], bF)
+    np.add.at(bP, o["hi"], bF)
+    mass = box.density * 4.0 / 3.0 * math.pi * box.r ** 3
+    gmag = float(np.linalg.norm(box.g))
+    bP += 1e-6 * mass * gmag + 1e-300
+    if box.floor_wall:
+        # wall contacts: k_n r^1.5 dn^1.5 scale, bounded via the force itself
+        bP += 1e-5 * np.linalg.norm(o["F"], axis=1) + 1e-5 * mass * gmag
+    if dont.any():
+        np.add.at(bP, o["lo"][dont], np.inf)
+        np.add.at(bP, o["hi"][dont], np.inf)
+    eP = np.linalg.norm(g["state"]["F"] - o["F"], axis=1)
+    assert np.all(eP <= bP), f"{int((eP > bP).sum())} particle forces outside tolerance"
+    eT = np.linalg.norm(g["state"]["T"] - o["T"], axis=1)
+    assert np.all(eT <= box.r * (bP + 1e-6 * np.linalg.norm(o["F"], axis=1)) * 2 + 1e-300), "torques"
+    m["max_particle_F_err_over_bound"] = float(np.max(eP / bP))
+    # 3. state after the step
+    vs = np.linalg.norm(o["v"], axis=1) + box.dt / mass * bP
+    ev = np.linalg.norm(g["state"]["v"] - o["v"], axis=1)
+    vtol = (1e-6 if precision != "fp64" else 1e-12) * vs + box.dt / mass * bP
+    assert np.all(ev <= vtol * 1.0001 + 1e-30), "velocities after the step"
+    dx = g["state"]["x"] - o["x"]
+    L = np.asarray(box.L)
+    per = np.asarray(box.periodic, bool)
+    dx = np.where(per, dx - L * np.round(dx / L), dx)
+    ex = np.linalg.norm(dx, axis=1)
+    xtol = box.dt * vtol * 2 + (1e-6 if precision == "fp32" else 0) * np.max(L) + 4 * 2.0 ** -60 + 1e-19
+    assert np.all(ex <= xtol), f"positions after the step, worst {float(np.max(ex / xtol)):.3g}"
+    return m
