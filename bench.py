@@ -1,0 +1,390 @@
+"""Throughput of the GB300 DEM step: particle-steps per second.
+
+Workload (default): 1,000,000 polydisperse spheres (lognormal radii, median
+4 um, sigma_log 0.25, clipped to [2, 8] um), periodic box at packing 0.55
+with overlaps up to 1 % of the smaller radius, v ~ N(0, 0.05 m/s),
+w ~ N(0, 1e3 rad/s), material E = 3 GPa, Poisson 0.3, 1200 kg/m^3,
+restitution 0.5, mu_D 0.3, dt = 1 ns.  One step = sort, contact search,
+contact list, force, sum + integrate (all kernels of the library).
+
+Prints one JSON line.  `value` is device-timed (CUDA events on the
+library's stream) with the state resident in HBM; `e2e` runs the same steps
+through the C ABI with host buffers (state in from pinned memory, state out
+to pinned memory every step).  `--impl reference` times the FP64 CPU oracle
+on the host cores instead (a periodic sub-box of the same workload).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       multi-GPU: python -m torch.distributed.run --nproc-per-node N bench.py --gpus N
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s"
+L2_BYTES = 126.5 * 2 ** 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the FP64-GPU, parity and CPU-baseline side legs")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index),
+                                      f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"],
+                                     capture_output=True, text=True, timeout=5).stdout
+                for line in out.strip().splitlines():
+                    self.rows.append([c.strip() for c in line.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic traffic model (bytes per particle-step, DEM_MIXED layout)
+# ---------------------------------------------------------------------------
+def phase_bytes(n, c_half, ncells):
+    """Unique bytes each phase must move per step: every array element read
+    or written once (neighbour re-reads served by caches are not counted).
+    n particles, c_half contacts per particle (half list), ncells cells."""
+    C = c_half * n
+    sort = ncells * (4 + 4 + 8 + 4) + n * (4 + 4 + 4 + 4      # scan, scatter
+                                           + 4 + 4 + 4          # cell sort
+                                           + 4 + 2 * (24 + 16 + 16 + 4) + 4 + 4 + 16)  # reorder
+    search = n * (16 + 4 + 4 + 8) + ncells * 8 + 2 * C * 4
+    compact = n * (4 + 4 + 4 + 8) + C * (4 + 8 + 8)
+    force = C * (8 + 8 + 8 + 8 + 24 + 24 + 16 + 16) + n * (24 + 16 + 16)
+    integrate = n * (4 + 4 + 4 + 2 * (24 + 16 + 16) + 4 + 4 + 4 + 4) + 2 * C * (32 + 4)
+    return {"sort": sort, "search": search, "compact": compact, "force": force,
+            "integrate": integrate}
+
+
+PHASES = ["sort", "search", "compact", "force", "integrate"]
+PHASE_KERNELS = {"sort": 6, "search": 1, "compact": 3, "force": 1, "integrate": 1}
+
+
+def _torch_setup(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return torch, rank, world, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(x, world, torch):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _workload(n, seed):
+    from paper_1503_03553_gb300 import synth
+    box = synth.w2_polydisperse(n=n, seed=seed)
+    # positions on the library's fixed-point grid so that the parity leg
+    # and the oracle see bit-identical inputs
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import prepared
+    return box, prepared(box, "mixed")
+
+
+def _time_steps(ctx, torch, steps, world):
+    s = ctx.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    _barrier(world)
+    torch.cuda.synchronize()
+    e0.record(s)
+    ctx.step(steps)
+    e1.record(s)
+    torch.cuda.synchronize()
+    _barrier(world)
+    return e0.elapsed_time(e1) / 1e3
+
+
+def _oracle_rate(box, seconds, max_steps=3):
+    """Time the FP64 oracle on this machine for about `seconds` (>= 1 step).
+    Returns (particle-steps/s, steps, seconds)."""
+    import oracle as O
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import oracle_params, grid_for
+    p = oracle_params(box, "mixed", grid_for(box))
+    O.alpha(box.restitution)  # restitution solve outside the timed region
+    s = O.State(box.x, box.v, box.w, box.r)
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        O.step(p, s)
+        k += 1
+        dt = time.perf_counter() - t0
+        if dt >= seconds or k >= max_steps:
+            break
+    return box.n * k / dt, k, dt
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as the reference arm.  Each step is one oracle
+    step of a periodic box drawn from the same workload definition, sized so
+    that warm-up plus timed steps take about two minutes on one host core."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1503_03553_gb300 import synth
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import oracle_params, grid_for, prepared
+    calib = prepared(synth.w2_polydisperse(n=8000, seed=2), "mixed")
+    p = oracle_params(calib, "mixed", grid_for(calib))
+    O.alpha(calib.restitution)
+    s = O.State(calib.x, calib.v, calib.w, calib.r)
+    t0 = time.perf_counter()
+    O.step(p, s)
+    rate = calib.n / (time.perf_counter() - t0)
+    n_s = int(0.6 * rate * 120.0 / max(1, args.steps + args.warmup))
+    n_s = max(500, min(n_s, 1_000_000))
+    if n_s >= 64000:
+        k = int((n_s / 8000) ** (1.0 / 3.0))
+        box = synth.w2_polydisperse(n=8000 * k ** 3, seed=2, tile_n=8000)
+        what = f"{k}^3 relaxed 8000-particle tiles"
+    else:
+        box = synth.w2_polydisperse(n=n_s, seed=2, tile_n=max(n_s, 8000))
+        what = "one relaxed periodic box"
+    box = prepared(box, "mixed")
+    p = oracle_params(box, "mixed", grid_for(box))
+    s = O.State(box.x, box.v, box.w, box.r)
+    for _ in range(args.warmup):
+        O.step(p, s)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(p, s)
+    dt = time.perf_counter() - t0
+    value = box.n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"W2 polydisperse periodic box, {box.n} particles ({what}; "
+                   "same radius law, packing and overlaps as the 1,000,000-particle workload)",
+                   "n": box.n},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} timed oracle steps of {box.n} particles"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    torch, rank, world, local = _torch_setup(args)
+    import paper_1503_03553_gb300 as D
+    if not os.path.exists(D.LIB_PATH):
+        from paper_1503_03553_gb300 import build
+        build.build()
+    raw, box = _workload(args.n, 2 + rank)
+    n = box.n
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import grid_for
+    ncell = grid_for(box)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ctx = D.Context([box], precision=args.precision, ncell=[ncell])
+    ctx.set_particles(0, box.x, box.v, box.w, box.r)
+    ctx.step(args.warmup)
+    # ---- timed region: K steps, CUDA graphs, device time -------------------
+    with ClockSampler(local) as clk:
+        secs = _time_steps(ctx, torch, args.steps, world)
+    secs = _max_over_ranks(secs, world, torch)
+    value = n * world * args.steps / secs
+    stats = ctx.stats(0)
+    c_half = stats[5] / n
+    # ---- per-phase device time (same workload, direct launches) -----------
+    ctx.set_timing(True)
+    phase_steps = min(100, max(10, args.steps // 4))
+    ctx.step(phase_steps)
+    ph = ctx.phase_times()
+    ctx.set_timing(False)
+    ncells = int(np.prod(ncell))
+    pb = phase_bytes(n, c_half, ncells)
+    ph_ms = dict(zip(PHASES, ph.tolist()))
+    dom = max(ph_ms, key=ph_ms.get)
+    peaks, src = _peaks()
+    achieved = pb[dom] / (ph_ms[dom] * 1e-3) / 1e9
+    total_bytes = sum(pb.values())
+    roof = {"bound": "hbm", "kernel_phase": dom, "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": src,
+            "algorithmic_bytes_per_launch": pb[dom],
+            "phase_ms": ph_ms, "phase_bytes": pb,
+            "step_algorithmic_bytes": total_bytes,
+            "step_frac_of_hbm": total_bytes / (secs / args.steps) / 1e9 / peaks["hbm_gbs"]}
+    tr_path = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            tr = json.load(open(tr_path))
+            if tr.get("phase") == dom and tr.get("n") and tr.get("precision") == args.precision:
+                roof["traffic"] = tr["bytes_per_launch"] * n / tr["n"]
+                roof["traffic_source"] = tr.get("source")
+        except Exception:
+            pass
+    # ---- end to end through the C ABI with host buffers -----------------
+    pin = lambda: torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    hx, hv, hw, hF, hT = pin(), pin(), pin(), pin(), pin()
+    D.dem_get_state(ctx.ctx, 0, hx, hv, hw, hF, hT)
+    _barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        D.dem_set_state(ctx.ctx, 0, hx, hv, hw)
+        ctx.step(1)
+        D.dem_get_state(ctx.ctx, 0, hx, hv, hw, hF, hT)
+    e2e_secs = _max_over_ranks(time.perf_counter() - t0, world, torch)
+    e2e = {"value": n * world * args.e2e_steps / e2e_secs, "unit": METRIC,
+           "h2d_bytes_per_step": 3 * n * 3 * 8, "d2h_bytes_per_step": 5 * n * 3 * 8,
+           "steps": args.e2e_steps}
+    launches = ctx.launches_per_step() * args.steps
+    ctx.close()
+    compare = {}
+    cpu = None
+    if rank == 0 and not args.no_compare:
+        compare = _side_legs(args, D, torch, box, ncell, stream)
+        rate, k, dt = _oracle_rate(box, args.cpu_seconds, max_steps=1)
+        cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"{k} oracle step(s) of the full {n}-particle workload, "
+                         f"one host thread, {dt:.1f} s"}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"mixed": "f32 (fixed-point positions, float-float history)",
+                  "fp64": "f64", "fp32": "f32"}[args.precision],
+        "data": "synthetic (seeded generator)",
+        "config": {"workload": f"W2 polydisperse periodic box, {n} particles per GPU, "
+                   "packing 0.55, dense contact network",
+                   "n_per_gpu": n, "precision": args.precision, "ncell": ncell,
+                   "contacts_per_particle": c_half,
+                   "l2": f"inputs larger than L2: a step touches {total_bytes / 1e6:.0f} MB "
+                         f"of unique data vs {L2_BYTES / 1e6:.0f} MB L2",
+                   "parallelism": f"{world} independent replica(s), one per GPU"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches, "clocks": clk.summary(),
+        "compare": compare,
+    }
+    print(json.dumps(line))
+
+
+def _side_legs(args, D, torch, box, ncell, stream):
+    """FP64 GPU throughput on the same workload, and force error of one step
+    against the FP64 oracle over every contact of the full workload."""
+    out = {}
+    with torch.cuda.stream(stream):
+        ctx = D.Context([box], precision="fp64", ncell=[ncell])
+    ctx.set_particles(0, box.x, box.v, box.w, box.r)
+    ctx.step(3)
+    k = max(8, args.steps // 20)
+    secs = _time_steps(ctx, torch, k, 1)
+    out["fp64_gpu"] = {"value": box.n * k / secs, "unit": METRIC, "steps": k,
+                       "ms_per_step": secs / k * 1e3}
+    ctx.close()
+    try:
+        from parity import gpu_run, oracle_run, check_one_step
+        g = gpu_run([box], "mixed", [ncell])[0]
+        o = oracle_run(box, "mixed", ncell)
+        m = check_one_step(box, g, o, "mixed")
+        out["force_parity_vs_fp64_oracle"] = {"pass": True, **m}
+    except AssertionError as e:
+        out["force_parity_vs_fp64_oracle"] = {"pass": False, "error": str(e)[:300]}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -276,10 +276,49 @@ static int cell_step(const orc_params* p, int a, int32_t ci, int32_t cj,
   return 2;
 }
 
-/* Is (i, j) a contact?  xi, xj are FP64 positions, ri, rj radii. */
-static int is_contact(const orc_params* p, const double* xi, const double* xj,
-                      double ri, double rj) {
+/* Per-particle data the predicates need, computed once per call: cell
+ * coordinates under the predicate's cell rule and, for the fixed-point rule,
+ * the single-precision offsets from the cell origin. */
+typedef struct {
+  int32_t* cc;   /* n x 3 cell coordinates        */
+  float* off;    /* n x 3 offsets (fixed rule)     */
+  int64_t Lq[3]; /* box length in quanta           */
+  int64_t H[3];  /* cell edge in quanta            */
+} pred_data;
+
+static int pred_init(const orc_params* p, int64_t n, const double* x,
+                     pred_data* pd) {
+  int64_t i;
   int a;
+  pd->cc = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(n > 0 ? n : 1));
+  pd->off = (float*)malloc(sizeof(float) * 3 * (size_t)(n > 0 ? n : 1));
+  if (!pd->cc || !pd->off) { free(pd->cc); free(pd->off); return 1; }
+  for (a = 0; a < 3; ++a) {
+    pd->Lq[a] = to_fixed(p->L[a]);
+    pd->H[a] = pd->Lq[a] / p->ncell[a];
+  }
+  for (i = 0; i < n; ++i)
+    for (a = 0; a < 3; ++a) {
+      int32_t c = cell_coord(p, a, x[3 * i + a]);
+      pd->cc[3 * i + a] = c;
+      pd->off[3 * i + a] = p->predicate == ORC_PRED_FIXED_F32
+                               ? fixed_offset(p, a, x[3 * i + a], c) : 0.0f;
+    }
+  return 0;
+}
+
+static void pred_free(pred_data* pd) {
+  free(pd->cc);
+  free(pd->off);
+}
+
+/* Is (i, j) a contact?  x holds FP64 positions, r radii. */
+static int is_contact(const orc_params* p, const pred_data* pd,
+                      const double* x, const double* r, int64_t i,
+                      int64_t j) {
+  int a;
+  const double* xi = &x[3 * i];
+  const double* xj = &x[3 * j];
   if (p->predicate == ORC_PRED_FP64) {
     double d[3], d2, R;
     for (a = 0; a < 3; ++a) {
@@ -291,7 +330,7 @@ static int is_contact(const orc_params* p, const double* xi, const double* xj,
       }
     }
     d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-    R = ri + rj;
+    R = r[i] + r[j];
     return d2 < R * R;
   } else if (p->predicate == ORC_PRED_FIXED_F32) {
     /* Offsets from the cell origins in FP32, plus the exact cell shift
@@ -299,22 +338,18 @@ static int is_contact(const orc_params* p, const double* xi, const double* xj,
     float d[3], d2, R;
     for (a = 0; a < 3; ++a) {
       int image;
-      int32_t ci = cell_coord(p, a, xi[a]);
-      int32_t cj = cell_coord(p, a, xj[a]);
+      int32_t ci = pd->cc[3 * i + a];
+      int32_t cj = pd->cc[3 * j + a];
       int step = cell_step(p, a, ci, cj, &image);
-      int64_t Lq, H, S;
-      float oi, oj, s;
+      int64_t S;
+      float s;
       if (step == 2) return 0;
-      Lq = to_fixed(p->L[a]);
-      H = Lq / p->ncell[a];
-      S = (int64_t)(cj - ci) * H + (int64_t)image * Lq;
-      oi = fixed_offset(p, a, xi[a], ci);
-      oj = fixed_offset(p, a, xj[a], cj);
+      S = (int64_t)(cj - ci) * pd->H[a] + (int64_t)image * pd->Lq[a];
       s = (float)S * 0x1p-60f;
-      d[a] = (oj - oi) + s;
+      d[a] = (pd->off[3 * j + a] - pd->off[3 * i + a]) + s;
     }
     d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-    R = (float)ri + (float)rj;
+    R = (float)r[i] + (float)r[j];
     return d2 < R * R;
   } else {
     float d[3], d2, R;
@@ -328,7 +363,7 @@ static int is_contact(const orc_params* p, const double* xi, const double* xj,
       }
     }
     d2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
-    R = (float)ri + (float)rj;
+    R = (float)r[i] + (float)r[j];
     return d2 < R * R;
   }
 }
@@ -395,11 +430,13 @@ static int cmp_pair(const void* a, const void* b) {
 static int64_t find_pairs(const orc_params* p, int64_t n, const double* x,
                           const double* r, int64_t cap, pair32* out) {
   int64_t cnt = 0, i, j;
+  pred_data pd;
+  if (pred_init(p, n, x, &pd)) return -2;
   if (p->brute_force) {
     for (i = 0; i < n; ++i)
       for (j = i + 1; j < n; ++j)
-        if (is_contact(p, &x[3 * i], &x[3 * j], r[i], r[j])) {
-          if (cnt >= cap) return -1;
+        if (is_contact(p, &pd, x, r, i, j)) {
+          if (cnt >= cap) { pred_free(&pd); return -1; }
           out[cnt].lo = (int32_t)i;
           out[cnt].hi = (int32_t)j;
           ++cnt;
@@ -409,15 +446,12 @@ static int64_t find_pairs(const orc_params* p, int64_t n, const double* x,
     int64_t M = (int64_t)nx * ny * nz;
     int64_t* head = (int64_t*)malloc(sizeof(int64_t) * (size_t)M);
     int64_t* next = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
-    int32_t* cc = (int32_t*)malloc(sizeof(int32_t) * 3 * (size_t)(n > 0 ? n : 1));
-    if (!head || !next || !cc) { free(head); free(next); free(cc); return -2; }
+    const int32_t* cc = pd.cc;
+    if (!head || !next) { free(head); free(next); pred_free(&pd); return -2; }
     for (i = 0; i < M; ++i) head[i] = -1;
     /* build linked cells; inserting in descending id keeps lists ascending */
     for (i = n - 1; i >= 0; --i) {
-      int a;
-      int64_t lin;
-      for (a = 0; a < 3; ++a) cc[3 * i + a] = cell_coord(p, a, x[3 * i + a]);
-      lin = ((int64_t)cc[3 * i + 2] * ny + cc[3 * i + 1]) * nx + cc[3 * i + 0];
+      int64_t lin = ((int64_t)cc[3 * i + 2] * ny + cc[3 * i + 1]) * nx + cc[3 * i + 0];
       next[i] = head[lin];
       head[lin] = i;
     }
@@ -448,8 +482,8 @@ static int64_t find_pairs(const orc_params* p, int64_t n, const double* x,
       for (q = 0; q < nnb; ++q) {
         for (j = head[nb[q]]; j >= 0; j = next[j]) {
           if (j <= i) continue;
-          if (is_contact(p, &x[3 * i], &x[3 * j], r[i], r[j])) {
-            if (cnt >= cap) { free(head); free(next); free(cc); return -1; }
+          if (is_contact(p, &pd, x, r, i, j)) {
+            if (cnt >= cap) { free(head); free(next); pred_free(&pd); return -1; }
             out[cnt].lo = (int32_t)i;
             out[cnt].hi = (int32_t)j;
             ++cnt;
@@ -459,8 +493,8 @@ static int64_t find_pairs(const orc_params* p, int64_t n, const double* x,
     }
     free(head);
     free(next);
-    free(cc);
   }
+  pred_free(&pd);
   qsort(out, (size_t)cnt, sizeof(pair32), cmp_pair);
   return cnt;
 }

@@ -25,9 +25,14 @@ namespace {
 constexpr int kPhases = 5;
 thread_local std::string g_create_error;
 
+// Per-phase timing: a ring of event sets, one set per step, read back when
+// the ring is full and at the end of dem_step (no synchronisation per step).
+constexpr int kRing = 64;
 struct Timing {
   bool on = false;
-  cudaEvent_t ev[kPhases + 1] = {};
+  bool made = false;
+  cudaEvent_t ev[kRing][kPhases + 1] = {};
+  int used = 0;  // sets recorded since the last read
   double acc[kPhases] = {};
   int steps = 0;
 };
@@ -139,7 +144,8 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   cudaStream_t s = ctx->stream;
   const int bs = ctx->block;
   const bool tm = ctx->tm.on;
-  if (tm) cudaEventRecord(ctx->tm.ev[0], s);
+  cudaEvent_t* ev = ctx->tm.ev[ctx->tm.used % kRing];
+  if (tm) cudaEventRecord(ev[0], s);
   // 1. cell counts -> starts (rank order) and ranges (linear cells)
   int nbc = blocks_for(d.M_rank, kScanTile);
   k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
@@ -152,10 +158,10 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
   k_cellsort<<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ctx->ps[p]);
   k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q]);
-  if (tm) cudaEventRecord(ctx->tm.ev[1], s);
+  if (tm) cudaEventRecord(ev[1], s);
   // 3. contact search into per-particle rows
   k_candidates<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
-  if (tm) cudaEventRecord(ctx->tm.ev[2], s);
+  if (tm) cudaEventRecord(ev[2], s);
   // 4. owned counts -> dense contact list
   int nbr = blocks_for(d.N, kScanTile);
   k_scan_reduce<<<nbr, kScanThreads, 0, s>>>(d.ocnt, d.N, d.scan_bsum);
@@ -163,14 +169,14 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
                                            d.Cmax, d.status, kStListOverflow);
   k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.ocnt, d.N, d.scan_bsum,
                                             RowEpi{d, ctx->ps[q], ctx->cl[q]});
-  if (tm) cudaEventRecord(ctx->tm.ev[3], s);
+  if (tm) cudaEventRecord(ev[3], s);
   // 5. one thread per contact
   k_force<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[p], ctx->cl[q]);
-  if (tm) cudaEventRecord(ctx->tm.ev[4], s);
+  if (tm) cudaEventRecord(ev[4], s);
   // 6. sum, wall, gravity, integrate, bin
   k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q],
                                                           store_ft ? 1 : 0);
-  if (tm) cudaEventRecord(ctx->tm.ev[5], s);
+  if (tm) cudaEventRecord(ev[5], s);
 }
 
 void enqueue(dem_ctx* ctx, int p, bool store_ft) {
@@ -423,6 +429,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     s.posr = A(v4_bytes(M) * n);
     s.id = (int*)A(sizeof(int) * n);
     s.cellc = (int*)A(sizeof(int) * n);
+    s.cellx = (int*)A(sizeof(int) * n);
     s.cellg = (int*)A(sizeof(int) * n);
     if (ctx->any_floor) {
       s.wx = A(dt_bytes(M) * n);
@@ -489,8 +496,9 @@ dem_status dem_destroy(dem_ctx* ctx) {
   if (!ctx) return DEM_OK;
   for (auto& g : ctx->gexec)
     if (g) cudaGraphExecDestroy(g);
-  if (ctx->tm.ev[0])
-    for (auto& ev : ctx->tm.ev) cudaEventDestroy(ev);
+  if (ctx->tm.made)
+    for (auto& set : ctx->tm.ev)
+      for (auto& ev : set) cudaEventDestroy(ev);
   free_all(ctx);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->h_count) cudaFreeHost(ctx->h_count);
@@ -630,20 +638,32 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
       left -= ctx->graph_steps;  // an even number of steps: parity unchanged
     }
   }
+  auto drain = [&]() -> dem_status {
+    if (!ctx->tm.used) return DEM_OK;
+    CK(cudaEventSynchronize(ctx->tm.ev[(ctx->tm.used - 1) % kRing][kPhases]));
+    for (int u = 0; u < ctx->tm.used; ++u)
+      for (int k = 0; k < kPhases; ++k) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ctx->tm.ev[u][k], ctx->tm.ev[u][k + 1]);
+        ctx->tm.acc[k] += ms;
+      }
+    ctx->tm.steps += ctx->tm.used;
+    ctx->tm.used = 0;
+    return DEM_OK;
+  };
   while (left > 0) {
     enqueue(ctx, ctx->parity, left == 1);
     CK(cudaGetLastError());
-    if (timing) {
-      CK(cudaEventSynchronize(ctx->tm.ev[kPhases]));
-      for (int k = 0; k < kPhases; ++k) {
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, ctx->tm.ev[k], ctx->tm.ev[k + 1]);
-        ctx->tm.acc[k] += ms;
-      }
-      ctx->tm.steps++;
+    if (timing && ++ctx->tm.used == kRing) {
+      dem_status st = drain();
+      if (st) return st;
     }
     ctx->parity = 1 - ctx->parity;
     --left;
+  }
+  if (timing) {
+    dem_status st = drain();
+    if (st) return st;
   }
   if (timing && ctx->tm.steps)
     for (int k = 0; k < kPhases; ++k) ctx->phase_ms[k] = ctx->tm.acc[k] / ctx->tm.steps;
@@ -654,8 +674,12 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
 
 dem_status dem_set_timing(dem_ctx* ctx, int32_t on) {
   if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");
-  if (on && !ctx->tm.ev[0])
-    for (auto& ev : ctx->tm.ev) CK(cudaEventCreate(&ev));
+  if (on && !ctx->tm.made) {
+    for (auto& set : ctx->tm.ev)
+      for (auto& ev : set) CK(cudaEventCreate(&ev));
+    ctx->tm.made = true;
+  }
+  ctx->tm.used = 0;
   ctx->tm.on = on != 0;
   return DEM_OK;
 }

@@ -55,7 +55,8 @@ struct PState {
   void* omg;    // V4 (wx, wy, wz, r)
   void* posr;   // PR
   int* id;      // global id = box slot base + id within the box
-  int* cellc;   // packed cell coordinates
+  int* cellc;   // packed cell coordinates used by this parity's sort
+  int* cellx;   // packed cell coordinates after integration (next sort)
   int* cellg;   // rank-space cell after integration
   void* wx;     // floor-wall delta_t (DT); null when no box has a floor
   void* wy;
@@ -253,6 +254,7 @@ __global__ void k_set_particles(Dev d, PState s, int box, int n,
   st4((V4*)s.omg + slot, mk4<R>((R)w[3 * k], (R)w[3 * k + 1], (R)w[3 * k + 2], (R)rr));
   s.id[slot] = slot;
   s.cellc[slot] = pack_cell(c[0], c[1], c[2]);
+  s.cellx[slot] = pack_cell(c[0], c[1], c[2]);
   int g = rank_cell(d, B, c[0], c[1], c[2]);
   s.cellg[slot] = g;
   atomicAdd(&d.ccount[g], 1);
@@ -306,6 +308,7 @@ __global__ void k_set_state(Dev d, PState s, int box, int n,
     }
     s.cellg[slot] = g;
     s.cellc[slot] = pack_cell(c[0], c[1], c[2]);
+    s.cellx[slot] = pack_cell(c[0], c[1], c[2]);
   }
   if (v) {
     V4 q = ((V4*)s.vel)[slot];
@@ -541,7 +544,7 @@ __global__ void k_reorder(Dev d, PState a, PState b) {
   st4((V4*)b.vel + t, vel);
   st4((V4*)b.omg + t, om);
   b.id[t] = a.id[s];
-  int cc = a.cellc[s];
+  int cc = a.cellx[s];
   b.cellc[t] = cc;
   if (a.wx) {
     using DT = typename T::DT;
@@ -727,9 +730,43 @@ struct RowEpi {
 // ---------------------------------------------------------------------------
 // contact geometry: unit normal n (from 1 to 2) and overlap dn
 // ---------------------------------------------------------------------------
-// Fixed point: exact integer difference, exact float-float |d|^2, then
-// dn = (R^2 - |d|^2) / (R + |d|) with the numerator from float-float terms,
-// so the overlap keeps FP32 relative accuracy however small it is.
+// Fixed point: the position difference D is an exact integer (quanta), the
+// radii are float32 values and therefore exact integers of quanta too, so
+// R^2 - |D|^2 is formed exactly in 128-bit integers.  The overlap
+// dn = (R^2 - |D|^2) / (R + |D|) then has FP32 relative accuracy however
+// small it is (Eq. (1) has eta ~ dn^{1/4}, which amplifies any absolute
+// error of a near-zero overlap without bound).
+struct u128 {
+  unsigned long long hi, lo;
+};
+__device__ __forceinline__ void u128_add_sq(u128& a, unsigned long long x) {
+  unsigned long long l = x * x, h = __umul64hi(x, x);
+  a.lo += l;
+  a.hi += h + (a.lo < l ? 1ull : 0ull);
+}
+__device__ __forceinline__ bool u128_less(u128 a, u128 b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ u128 u128_sub(u128 a, u128 b) {  // a >= b
+  u128 r;
+  r.lo = a.lo - b.lo;
+  r.hi = a.hi - b.hi - (a.lo < b.lo ? 1ull : 0ull);
+  return r;
+}
+// to float without the FP64 pipe: top 32 significant bits, truncated
+// (relative error below 2^-31), then one rounding to float and an exact
+// power-of-two scale
+__device__ __forceinline__ float u128_to_f32(u128 a) {
+  if (a.hi == 0 && (a.lo >> 32) == 0) return __uint2float_rn((unsigned)a.lo);
+  int bits = a.hi ? 128 - __clzll((long long)a.hi) : 64 - __clzll((long long)a.lo);
+  int sh = bits - 32;  // > 0
+  unsigned m;
+  if (sh >= 64) m = (unsigned)(a.hi >> (sh - 64));
+  else m = (unsigned)((a.hi << (64 - sh)) | (a.lo >> sh));
+  float f = __uint2float_rn(m);
+  return __fmul_rn(f, __int_as_float((127 + sh) << 23));  // sh <= 96
+}
+
 __device__ __forceinline__ void geom_fixed(const BoxDev& B, long long X1,
                                            long long Y1, long long Z1,
                                            long long X2, long long Y2,
@@ -744,28 +781,26 @@ __device__ __forceinline__ void geom_fixed(const BoxDev& B, long long X1,
       else if (D[a] < -h) D[a] += L;
     }
   }
-  ff dx = i64_to_ff(D[0]), dy = i64_to_ff(D[1]), dz = i64_to_ff(D[2]);
-  // to metres (exact power-of-two scaling)
-  dx.hi = __fmul_rn(dx.hi, kQ); dx.lo = __fmul_rn(dx.lo, kQ);
-  dy.hi = __fmul_rn(dy.hi, kQ); dy.lo = __fmul_rn(dy.lo, kQ);
-  dz.hi = __fmul_rn(dz.hi, kQ); dz.lo = __fmul_rn(dz.lo, kQ);
-  ff px = two_prod(dx.hi, dx.hi), py = two_prod(dy.hi, dy.hi),
-     pz = two_prod(dz.hi, dz.hi);
-  ff s1 = two_sum(px.hi, py.hi);
-  ff s2 = two_sum(s1.hi, pz.hi);
-  float t = px.lo + py.lo + pz.lo + s1.lo + s2.lo +
-            2.0f * (dx.hi * dx.lo + dy.hi * dy.lo + dz.hi * dz.lo);
-  ff S = fast_two_sum(s2.hi, t);
-  ff R = two_sum(r1, r2);
-  ff R2 = two_prod(R.hi, R.hi);
-  float R2lo = R2.lo + 2.0f * R.hi * R.lo;
-  ff df = two_sum(R2.hi, -S.hi);
-  float num = df.hi + (df.lo + (R2lo - S.lo));
-  float dist = sqrtf(S.hi);
-  dn = num / (R.hi + dist);
-  if (dist > 0.0f) {
-    float inv = 1.0f / dist;
-    n = {dx.hi * inv, dy.hi * inv, dz.hi * inv};
+  u128 S = {0ull, 0ull};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    u128_add_sq(S, (unsigned long long)(D[a] < 0 ? -D[a] : D[a]));
+  unsigned bad = 0;
+  long long Rq = f32_to_i64_rn(__fmul_rn(r1, kInvQ), &bad) +
+                 f32_to_i64_rn(__fmul_rn(r2, kInvQ), &bad);
+  u128 R2 = {0ull, 0ull};
+  u128_add_sq(R2, (unsigned long long)Rq);
+  float distq = sqrtf(u128_to_f32(S));
+  if (u128_less(S, R2)) {
+    float num = u128_to_f32(u128_sub(R2, S));
+    dn = __fmul_rn(num / (i64_to_f32_rn(Rq) + distq), kQ);
+  } else {
+    dn = 0.0f;
+  }
+  if (distq > 0.0f) {
+    float inv = 1.0f / distq;
+    n = {i64_to_f32_rn(D[0]) * inv, i64_to_f32_rn(D[1]) * inv,
+         i64_to_f32_rn(D[2]) * inv};
   } else {
     n = {0.0f, 0.0f, 0.0f};
   }
@@ -1140,7 +1175,7 @@ __global__ void k_gather_integrate(Dev d, PState b, int store_ft) {
   ((P*)b.px)[i] = p[0];
   ((P*)b.py)[i] = p[1];
   ((P*)b.pz)[i] = p[2];
-  b.cellc[i] = pack_cell(c[0], c[1], c[2]);
+  b.cellx[i] = pack_cell(c[0], c[1], c[2]);
   int g = rank_cell(d, B, c[0], c[1], c[2]);
   b.cellg[i] = g;
   atomicAdd(&d.ccount[g], 1);

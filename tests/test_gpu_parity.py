@@ -62,9 +62,10 @@ def test_one_step_monodisperse_fp64():
     check_one_step(b, g, o, "fp64")
 
 
-@pytest.mark.parametrize("n", [1, 2, 33, 257])
+@pytest.mark.parametrize("n", [1, 2, 33, 257, 4097])
 def test_ragged_small_counts(n):
-    box = synth.w2_polydisperse(n=max(n, 8), seed=24)
+    # the first n particles of a dense box: same box and grid, few contacts
+    box = synth.w2_polydisperse(n=6000, seed=24, tile_n=6000)
     sel = slice(0, n)
     box.x, box.v, box.w, box.r = box.x[sel], box.v[sel], box.w[sel], box.r[sel]
     b, g, o = _one(box, "mixed")
