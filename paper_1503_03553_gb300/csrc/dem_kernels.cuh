@@ -889,6 +889,10 @@ k_force(Dev d, PState b, CList co, CList cn) {
   const P* __restrict__ pz = (const P*)b.pz;
   const V4* __restrict__ vel = (const V4*)b.vel;
   const V4* __restrict__ omg = (const V4*)b.omg;
+  // per-box diagnostics are kept in registers and reduced once per warp:
+  // one atomic per warp instead of two per contact on a single address
+  int mbox = -1;
+  float m_ov = 0.0f, m_ratio = 0.0f;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
        c += gridDim.x * blockDim.x) {
     int2 pr = cn.pair[c];
@@ -973,14 +977,37 @@ k_force(Dev d, PState b, CList co, CList cn) {
       F4 = mk4<R>(o.F.x, o.F.y, o.F.z, R(0));
       N4 = mk4<R>(o.nF.x, o.nF.y, o.nF.z, R(0));
       R rmin = r1 < r2 ? r1 : r2;
-      atomic_max_pos(d.diag + 2 * box, (float)(dn / rmin));
-      atomic_max_pos(d.diag + 2 * box + 1, (float)o.ratio);
+      if (box != mbox) {
+        if (mbox >= 0) {
+          atomic_max_pos(d.diag + 2 * mbox, m_ov);
+          atomic_max_pos(d.diag + 2 * mbox + 1, m_ratio);
+        }
+        mbox = box;
+        m_ov = m_ratio = 0.0f;
+      }
+      float ov = (float)(dn / rmin), ra = (float)o.ratio;
+      if (isfinite(ov)) m_ov = fmaxf(m_ov, ov);
+      if (isfinite(ra)) m_ratio = fmaxf(m_ratio, ra);
     }
     ((DT*)cn.dx)[c] = nx;
     ((DT*)cn.dy)[c] = ny;
     ((DT*)cn.dz)[c] = nz;
     st4((V4*)d.Fc + c, F4);
     st4((V4*)d.nFc + c, N4);
+  }
+  // every lane of the warp reaches this point
+  const unsigned full = 0xffffffffu;
+  int b0 = __reduce_max_sync(full, mbox);
+  if (__all_sync(full, mbox == b0 || mbox < 0)) {
+    unsigned u_ov = __reduce_max_sync(full, mbox >= 0 ? __float_as_uint(m_ov) : 0u);
+    unsigned u_ra = __reduce_max_sync(full, mbox >= 0 ? __float_as_uint(m_ratio) : 0u);
+    if ((threadIdx.x & 31) == 0 && b0 >= 0) {
+      if (u_ov) atomicMax(d.diag + 2 * b0, u_ov);
+      if (u_ra) atomicMax(d.diag + 2 * b0 + 1, u_ra);
+    }
+  } else if (mbox >= 0) {
+    atomic_max_pos(d.diag + 2 * mbox, m_ov);
+    atomic_max_pos(d.diag + 2 * mbox + 1, m_ratio);
   }
 }
 
