@@ -236,6 +236,43 @@ dem_status dem_destroy(dem_ctx* ctx);
 
 int32_t dem_abi_version(void);
 
+/* Contact detection for one small box without any device allocation.
+ * (The paper has no counterpart: this is a library service.)
+ *
+ * Who needs it: callers that cannot allocate device memory when they need a
+ * contact list -- code running inside another framework's memory pool or
+ * under a fixed memory budget, code that must not grow its footprint after
+ * start-up, or latency-critical code that must not call cudaMalloc (it can
+ * synchronise the device).  dem_create allocates; this call does not: it
+ * runs the same binning, sorting and search kernels as dem_step with all
+ * scratch carved from one file-scope device array of about 4.7 MB that every
+ * GPU loading this library holds until the process exits.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Inputs (device memory of the current GPU): x (n x 3 FP64 positions [m]),
+ * radius (n, each at most half the narrowest cell edge L[a]/ncell[a]).
+ * Host arrays: box lengths L, periodic flags and the cell grid ncell
+ * (periodic axes need >= 3 cells).  The contact rule is DEM_MIXED's: the
+ * position is rounded to 2^-60 m fixed point and a pair is in contact when
+ * the single-precision test of dem_step accepts it.
+ * Output: pairs (device, cap x 2 int32, 8-byte aligned) receives
+ * (id_lo, id_hi) of every contact, id_lo < id_hi, grouped by id_lo in cell
+ * order; *count (host) the number of contacts.
+ * Limits: n <= 8192, ncell[0] * ncell[1] * ncell[2] <= 32768, at most
+ * 131072 contacts (fewer if cap is smaller) and 32 per particle; larger
+ * sizes are rejected with DEM_ERR_ARG (sizes) or DEM_ERR_CAPACITY (contacts).
+ * Runs on `stream` (cudaStream_t, NULL = legacy default) and returns after
+ * synchronising it.  The first call on a device looks up the array's device
+ * address (once per device, with that device current); make that first call
+ * before any stream capture.  All calls share the one array, which keeps
+ * the previous call's contents (each call clears what must start at zero):
+ * calls that overlap on the GPU, from several streams or threads, race.
+ * Errors are described by dem_last_error(NULL). */
+dem_status dem_contacts_static(int64_t n, const double* x, const double* radius,
+                               const double L[3], const int32_t periodic[3],
+                               const int32_t ncell[3], int64_t cap,
+                               int32_t* pairs, int64_t* count, void* stream);
+
 /* Restitution parameter (Sec. 2: eta_n = eta_t = alpha(eps) sqrt(m* k_n
  * sqrt(dn)), alpha "a function of the coefficient of restitution", not
  * given in the paper).  The library defines alpha as the exact inverse of

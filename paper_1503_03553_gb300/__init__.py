@@ -98,6 +98,8 @@ def lib() -> C.CDLL:
         "dem_last_error": (C.c_char_p, [vp]),
         "dem_alpha_of_restitution": (C.c_double, [C.c_double]),
         "dem_restitution_of_alpha": (C.c_double, [C.c_double]),
+        "dem_contacts_static": (C.c_int, [C.c_int64, vp, vp, dp, ip, ip, C.c_int64, vp,
+                                          i64p, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -148,6 +150,27 @@ def dem_alpha_of_restitution(eps: float) -> float:
 
 def dem_restitution_of_alpha(alpha: float) -> float:
     return lib().dem_restitution_of_alpha(float(alpha))
+
+
+def dem_contacts_static(x, radius, L, periodic, ncell, pairs, stream=None) -> int:
+    """Contact list of one small box with no device allocation (see the
+    C declaration).  x: CUDA float64 (n, 3); radius: CUDA float64 (n,);
+    pairs: CUDA int32 (cap, 2) receiving (id_lo, id_hi).  Returns the count."""
+    import torch
+    for t, dt in ((x, torch.float64), (radius, torch.float64), (pairs, torch.int32)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError("x, radius must be contiguous CUDA float64; pairs CUDA int32")
+    n = int(x.shape[0])
+    Ld = (C.c_double * 3)(*[float(v) for v in L])
+    per = (C.c_int32 * 3)(*[int(v) for v in periodic])
+    nc = (C.c_int32 * 3)(*[int(v) for v in ncell])
+    cnt = C.c_int64(0)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    st = lib().dem_contacts_static(n, C.c_void_p(x.data_ptr()), C.c_void_p(radius.data_ptr()),
+                                   Ld, per, nc, int(pairs.shape[0]), C.c_void_p(pairs.data_ptr()),
+                                   C.byref(cnt), C.c_void_p(s.cuda_stream))
+    _check(None, st)
+    return cnt.value
 
 
 def dem_create(cfg: dem_config) -> C.c_void_p:

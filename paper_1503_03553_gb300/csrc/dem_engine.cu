@@ -6,6 +6,7 @@
 // replays G steps at a time from a captured CUDA graph.
 #include <algorithm>
 #include <array>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1003,3 +1004,261 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
 }
 
 }  // extern "C"
+
+// ==========================================================================
+// Contact detection without device allocation (dem_contacts_static).
+//
+// Some callers cannot allocate device memory at the moment they need a
+// contact list: code running inside another framework's memory pool or
+// under a fixed memory budget, code that must not grow its footprint once
+// it is running, or code that must not call cudaMalloc (which may
+// synchronise the device) on a latency-critical path.  For them this entry
+// point runs the same search kernels as dem_step on one small box, with all
+// of its scratch carved from one file-scope device array of fixed size.
+// The array exists on every GPU that loads this library until the process
+// exits (about 4.7 MB).
+// ==========================================================================
+namespace {
+
+constexpr int kStaticMaxParticles = 8192;
+constexpr int kStaticMaxCells = 32768;
+constexpr int kStaticMaxContacts = 131072;
+constexpr int kStaticK = 32;
+
+// layout of the scratch array (every part 256-byte aligned)
+struct StaticLayout {
+  size_t box, slot_box, rol, lor, ccount, cstart, crange, perm, row, ocnt,
+      icnt, hstart, bsum, status, count, pair, rs, rc, state[2][10], total;
+};
+
+constexpr size_t al(size_t v) { return (v + 255) & ~size_t(255); }
+
+StaticLayout static_layout() {
+  StaticLayout L{};
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = al(o + bytes);
+    return at;
+  };
+  const size_t N = kStaticMaxParticles, M = kStaticMaxCells;
+  L.box = take(sizeof(BoxDev));
+  L.slot_box = take(4 * N);
+  L.rol = take(4 * M);
+  L.lor = take(4 * (M + 1));
+  L.ccount = take(4 * (M + 1));
+  L.cstart = take(4 * (M + 1));
+  L.crange = take(8 * M);
+  L.perm = take(4 * N);
+  L.row = take(4 * N * kStaticK);
+  L.ocnt = take(4 * N);
+  L.icnt = take(4 * N);
+  L.hstart = take(4 * N);
+  L.bsum = take(4 * 8192);
+  L.status = take(4);
+  L.count = take(4);
+  L.pair = take(8 * (size_t)kStaticMaxContacts);
+  L.rs = take(4 * N);
+  L.rc = take(4 * N);
+  for (int p = 0; p < 2; ++p) {
+    const size_t sz[10] = {8 * N, 8 * N, 8 * N, 16 * N, 16 * N, 16 * N, 4 * N, 4 * N, 4 * N, 4 * N};
+    for (int k = 0; k < 10; ++k) L.state[p][k] = take(sz[k]);
+  }
+  L.total = o;
+  return L;
+}
+
+// Upper bound of the layout above (checked at set-up).
+constexpr size_t kStaticScratchBytes = 4900000;
+
+}  // namespace
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// symbol; the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_dem_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_addr[kMaxDevices] = {};
+
+__global__ void k_static_iota(int* rank_of_lin, int* lin_of_rank, int M) {
+  int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l < M) {
+    rank_of_lin[l] = l;
+    lin_of_rank[l] = l;
+  } else if (l == M) {
+    lin_of_rank[M] = -1;
+  }
+}
+
+// a radius above half the narrowest cell would let contacts skip a cell
+__global__ void k_static_check_radius(const double* r, int n, double hmin,
+                                      unsigned* status) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n && !(2.0 * r[k] * (1.0 + 1e-5) <= hmin && r[k] > 0.0))
+    atomicOr(status, 0x100u);
+}
+
+}  // namespace
+
+extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
+                                          const double* radius,
+                                          const double L[3],
+                                          const int32_t periodic[3],
+                                          const int32_t ncell[3], int64_t cap,
+                                          int32_t* pairs, int64_t* count,
+                                          void* stream) {
+  dem_ctx* ctx = nullptr;  // errors go to the create-error string
+  if (!count) return fail(ctx, DEM_ERR_ARG, "count is null");
+  *count = 0;
+  if (n < 0 || n > kStaticMaxParticles)
+    return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: n must be in [0, 8192]");
+  if (!L || !periodic || !ncell || cap < 0 || (cap > 0 && !pairs) ||
+      (n > 0 && (!x || !radius)))
+    return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: null or negative argument");
+  if (((uintptr_t)pairs & 7) != 0)
+    return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: pairs must be 8-byte aligned");
+  long long M = 1;
+  double hmin = 1e300;
+  for (int a = 0; a < 3; ++a) {
+    if (!(L[a] > 0) || L[a] * 0x1p60 >= 0x1p62)
+      return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: box length out of range (0, 4 m)");
+    if (ncell[a] < 1 || ncell[a] > kMaxAxisCells || (periodic[a] && ncell[a] < 3))
+      return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: bad cell grid (periodic axes need >= 3 cells)");
+    M *= ncell[a];
+    hmin = std::min(hmin, L[a] / ncell[a]);
+  }
+  if (M > kStaticMaxCells)
+    return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: more than 32768 cells");
+  if (n == 0) return DEM_OK;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return fail(ctx, DEM_ERR_CUDA, "dem_contacts_static: no usable current device");
+  const StaticLayout lay = static_layout();
+  unsigned char* base = nullptr;
+  {
+    // set-up, once per device, with that device current
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_addr[dev]) {
+      if (lay.total > kStaticScratchBytes)
+        return fail(ctx, DEM_ERR_ALLOC, "dem_contacts_static: scratch layout exceeds the array");
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_dem_static_scratch);
+      if (e != cudaSuccess || !p)
+        return fail(ctx, DEM_ERR_CUDA, std::string("dem_contacts_static: cudaGetSymbolAddress: ") +
+                                           cudaGetErrorString(e));
+      g_static_addr[dev] = (unsigned char*)p;
+    }
+    base = g_static_addr[dev];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int N = (int)n;
+
+  BoxDev B{};
+  for (int a = 0; a < 3; ++a) {
+    int nc = ncell[a];
+    B.n[a] = nc;
+    B.periodic[a] = periodic[a] ? 1 : 0;
+    B.Lq[a] = std::llround(std::ldexp(L[a], kFixShift));
+    B.Hq[a] = B.Lq[a] / nc;
+    B.L[a] = L[a];
+    B.half_L[a] = 0.5 * L[a];
+    B.inv_h[a] = (double)nc / L[a];
+    B.Lf[a] = (float)L[a];
+    B.half_Lf[a] = 0.5f * B.Lf[a];
+    B.inv_hf[a] = (float)((double)nc / L[a]);
+    long long H = B.Hq[a], Lq = B.Lq[a];
+    long long S[5] = {-H, 0, H, (long long)(nc - 1) * H - Lq, Lq - (long long)(nc - 1) * H};
+    for (int k = 0; k < 5; ++k) B.shift[a][k] = (float)S[k] * 0x1p-60f;
+  }
+  B.ncells = (int)M;
+  B.cap = N;
+  B.nlive = N;
+  B.density = 1.0;
+
+  Dev d{};
+  d.boxes = (const BoxDev*)(base + lay.box);
+  d.slot_box = (const int*)(base + lay.slot_box);
+  d.N = N;
+  d.K = kStaticK;
+  d.Cmax = (int)std::min<int64_t>(cap, kStaticMaxContacts);
+  d.M_lin = (int)M;
+  d.M_rank = (int)M + 1;
+  d.rank_of_lin = (const int*)(base + lay.rol);
+  d.lin_of_rank = (const int*)(base + lay.lor);
+  d.ccount = (int*)(base + lay.ccount);
+  d.cstart = (int*)(base + lay.cstart);
+  d.crange = (int2*)(base + lay.crange);
+  d.perm = (int*)(base + lay.perm);
+  d.row = (int*)(base + lay.row);
+  d.ocnt = (int*)(base + lay.ocnt);
+  d.icnt = (int*)(base + lay.icnt);
+  d.hstart = (int*)(base + lay.hstart);
+  d.status = (unsigned*)(base + lay.status);
+  d.scan_bsum = (int*)(base + lay.bsum);
+  PState ps[2];
+  for (int p = 0; p < 2; ++p) {
+    const size_t* o = lay.state[p];
+    ps[p] = PState{base + o[0], base + o[1], base + o[2], base + o[3], base + o[4], base + o[5],
+                   (int*)(base + o[6]), (int*)(base + o[7]), (int*)(base + o[8]),
+                   (int*)(base + o[9]), nullptr, nullptr, nullptr};
+  }
+  CList cn{};
+  cn.pair = (int2*)(base + lay.pair);
+  cn.hid = (int2*)pairs;
+  cn.rs = (int*)(base + lay.rs);
+  cn.rc = (int*)(base + lay.rc);
+  cn.count = (int*)(base + lay.count);
+
+  // The array keeps the previous call's contents: clear what must start at
+  // zero (cell counts, box index of every slot, status, count).
+  auto ck = [&](cudaError_t e, const char* what) -> dem_status {
+    if (e == cudaSuccess) return DEM_OK;
+    return fail(ctx, DEM_ERR_CUDA, std::string("dem_contacts_static: ") + what + ": " +
+                                       cudaGetErrorString(e));
+  };
+  dem_status st;
+  if ((st = ck(cudaMemcpyAsync(base + lay.box, &B, sizeof(BoxDev), cudaMemcpyHostToDevice, s), "box")))
+    return st;
+  if ((st = ck(cudaMemsetAsync(d.ccount, 0, 4 * (size_t)(M + 1), s), "counts"))) return st;
+  if ((st = ck(cudaMemsetAsync((void*)d.slot_box, 0, 4 * (size_t)N, s), "slots"))) return st;
+  if ((st = ck(cudaMemsetAsync(d.status, 0, 4, s), "status"))) return st;
+  if ((st = ck(cudaMemsetAsync(cn.count, 0, 4, s), "count"))) return st;
+  k_static_iota<<<blocks_for(M + 1, 256), 256, 0, s>>>((int*)d.rank_of_lin, (int*)d.lin_of_rank, (int)M);
+  k_static_check_radius<<<blocks_for(N, 256), 256, 0, s>>>(radius, N, hmin, d.status);
+  // bin, sort, search, compact: the DEM_MIXED kernels of dem_step
+  k_set_particles<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], 0, N, x, x, x, radius);
+  int nbc = blocks_for(d.M_rank, kScanTile);
+  k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
+  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u);
+  k_scan_apply<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum,
+                                            CellEpi{d.cstart, d.crange, d.lin_of_rank});
+  k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
+  k_cellsort<<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ps[0]);
+  k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1]);
+  k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1]);
+  int nbr = blocks_for(N, kScanTile);
+  k_scan_reduce<<<nbr, kScanThreads, 0, s>>>(d.ocnt, N, d.scan_bsum);
+  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbr, cn.count, d.Cmax, d.status,
+                                           kStListOverflow);
+  k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.ocnt, N, d.scan_bsum, RowEpi{d, ps[1], cn});
+  if ((st = ck(cudaGetLastError(), "launch"))) return st;
+  int hcount = 0;
+  unsigned hstatus = 0;
+  if ((st = ck(cudaMemcpyAsync(&hcount, cn.count, 4, cudaMemcpyDeviceToHost, s), "count read")))
+    return st;
+  if ((st = ck(cudaMemcpyAsync(&hstatus, d.status, 4, cudaMemcpyDeviceToHost, s), "status read")))
+    return st;
+  if ((st = ck(cudaStreamSynchronize(s), "synchronise"))) return st;
+  *count = hcount;
+  if (hstatus & 0x100u)
+    return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: a radius exceeds half the cell edge");
+  if (hstatus & kStNonFinite) return fail(ctx, DEM_ERR_NONFINITE, "dem_contacts_static: non-finite position");
+  if (hstatus & (kStRowOverflow | kStListOverflow))
+    return fail(ctx, DEM_ERR_CAPACITY, "dem_contacts_static: contacts exceed cap, 131072, or 32 per particle");
+  if (hstatus) return fail(ctx, DEM_ERR_STATE, "dem_contacts_static: internal consistency check failed");
+  return DEM_OK;
+}
