@@ -35,6 +35,7 @@ class Params(C.Structure):
         ("predicate", C.c_int32),
         ("kn_literal", C.c_int32),
         ("brute_force", C.c_int32),
+        ("stencil", C.c_int32),
     ]
 
 
@@ -91,9 +92,9 @@ def lib():
 def make_params(L, dt, E=3e9, poisson=0.3, density=1200.0, restitution=0.5,
                 mu_d=0.3, periodic=(1, 1, 1), floor_wall=0, g=(0.0, 0.0, 0.0),
                 ncell=None, predicate=PRED_FP64, kn_literal=0,
-                brute_force=0, r_max=None) -> Params:
+                brute_force=0, r_max=None, stencil=1) -> Params:
     """Fill a Params struct.  ``ncell`` defaults to the largest grid whose
-    cells are at least 2 r_max (1 + 1e-5) wide."""
+    cells are at least 2 r_max (1 + 1e-5) / stencil wide."""
     p = Params()
     L = [float(v) for v in (L if np.ndim(L) else (L, L, L))]
     for a in range(3):
@@ -103,7 +104,7 @@ def make_params(L, dt, E=3e9, poisson=0.3, density=1200.0, restitution=0.5,
     if ncell is None:
         if r_max is None:
             raise ValueError("ncell or r_max required")
-        ncell = [max(1, int(np.floor(L[a] / (2.0 * r_max * (1.0 + 1e-5)))))
+        ncell = [max(1, int(np.floor(L[a] * stencil / (2.0 * r_max * (1.0 + 1e-5)))))
                  for a in range(3)]
     for a in range(3):
         p.ncell[a] = int(ncell[a])
@@ -117,6 +118,7 @@ def make_params(L, dt, E=3e9, poisson=0.3, density=1200.0, restitution=0.5,
     p.predicate = int(predicate)
     p.kn_literal = int(kn_literal)
     p.brute_force = int(brute_force)
+    p.stencil = int(stencil)
     return p
 
 

@@ -260,20 +260,26 @@ static float fixed_offset(const orc_params* p, int a, double x, int32_t c) {
   return (float)O * 0x1p-60f;
 }
 
-/* Geometric cell step from ci to cj on axis a: -1, 0, +1, or 2 when the two
- * cells are not neighbours.  *image receives the periodic image (-1, 0, +1)
- * in units of the box length that places cell cj next to ci. */
+static int stencil_of(const orc_params* p) {
+  return p->stencil > 0 ? p->stencil : 1;
+}
+
+/* Geometric cell step from ci to cj on axis a: in [-w, w] (w = stencil), or
+ * w + 1 when the two cells are not within the stencil.  *image receives the
+ * periodic image (-1, 0, +1) in units of the box length that places cell cj
+ * at that step from ci. */
 static int cell_step(const orc_params* p, int a, int32_t ci, int32_t cj,
                      int* image) {
   int32_t n = p->ncell[a];
   int32_t d = cj - ci;
+  int w = stencil_of(p);
   *image = 0;
-  if (d >= -1 && d <= 1) return d;
+  if (d >= -w && d <= w) return d;
   if (p->periodic[a]) {
-    if (d == n - 1) { *image = -1; return -1; }
-    if (d == -(n - 1)) { *image = 1; return 1; }
+    if (d - n >= -w && d - n <= w) { *image = -1; return d - n; }
+    if (d + n >= -w && d + n <= w) { *image = 1; return d + n; }
   }
-  return 2;
+  return w + 1;
 }
 
 /* Per-particle data the predicates need, computed once per call: cell
@@ -343,7 +349,7 @@ static int is_contact(const orc_params* p, const pred_data* pd,
       int step = cell_step(p, a, ci, cj, &image);
       int64_t S;
       float s;
-      if (step == 2) return 0;
+      if (step > stencil_of(p)) return 0;
       S = (int64_t)(cj - ci) * pd->H[a] + (int64_t)image * pd->Lq[a];
       s = (float)S * 0x1p-60f;
       d[a] = (pd->off[3 * j + a] - pd->off[3 * i + a]) + s;
@@ -456,12 +462,13 @@ static int64_t find_pairs(const orc_params* p, int64_t n, const double* x,
       head[lin] = i;
     }
     for (i = 0; i < n; ++i) {
-      int64_t nb[27];
+      int64_t nb[125];
       int nnb = 0, dx, dy, dz, q;
-      /* distinct neighbour cells (a periodic axis with < 3 cells repeats) */
-      for (dz = -1; dz <= 1; ++dz)
-        for (dy = -1; dy <= 1; ++dy)
-          for (dx = -1; dx <= 1; ++dx) {
+      const int w = stencil_of(p);
+      /* distinct neighbour cells (a periodic axis with few cells repeats) */
+      for (dz = -w; dz <= w; ++dz)
+        for (dy = -w; dy <= w; ++dy)
+          for (dx = -w; dx <= w; ++dx) {
             int32_t c[3];
             int d[3], a, ok = 1, seen = 0;
             int64_t lin;
@@ -470,7 +477,7 @@ static int64_t find_pairs(const orc_params* p, int64_t n, const double* x,
               int32_t v = cc[3 * i + a] + d[a];
               if (v < 0 || v >= p->ncell[a]) {
                 if (!p->periodic[a]) { ok = 0; break; }
-                v = (v + p->ncell[a]) % p->ncell[a];
+                v = ((v % p->ncell[a]) + p->ncell[a]) % p->ncell[a];
               }
               c[a] = v;
             }

@@ -61,6 +61,8 @@ typedef struct {
   int32_t predicate;    /* ORC_PRED_*                                     */
   int32_t kn_literal;   /* 1 = k_n with the printed (2 - sigma^2)/E term  */
   int32_t brute_force;  /* 1 = O(N^2) pair search instead of cells        */
+  int32_t stencil;      /* neighbour cells searched per axis: +-stencil   */
+                        /* (cells at least 2 r_max / stencil wide; 0 = 1) */
 } orc_params;
 
 /* Per-contact diagnostics, one record per contact of the new list. */

@@ -40,6 +40,8 @@ struct BoxDev {
   float half_Lf[3];
   float inv_hf[3];
   float shift[3][5];    // fixed-rule cell shifts: -H, 0, +H, wrap low, wrap high
+  float hcell[3][2];    // cell edge [m]: ordinary cell, last cell (inf when open)
+  double h[3];          // L / ncell [m]
   int n[3];             // cells per axis
   int periodic[3];
   int floor_wall;

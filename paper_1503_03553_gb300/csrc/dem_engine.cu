@@ -127,7 +127,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
   return spread(x) | (spread(y) << 1) | (spread(z) << 2);
 }
 
-int launches_per_step(const dem_ctx*) { return 12; }
+int launches_per_step(const dem_ctx*) { return 13; }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -157,7 +157,7 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
       CellEpi{d.cstart, d.crange, d.lin_of_rank});
   // 2. counting sort by (Morton cell, id) and reorder into parity q
   k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
-  k_cellsort<<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ctx->ps[p]);
+  k_cellsort<M><<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ctx->ps[p]);
   k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q]);
   if (tm) cudaEventRecord(ev[1], s);
   // 3. contact search into per-particle rows
@@ -165,11 +165,13 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   if (tm) cudaEventRecord(ev[2], s);
   // 4. owned counts -> dense contact list
   int nbr = blocks_for(d.N, kScanTile);
-  k_scan_reduce<<<nbr, kScanThreads, 0, s>>>(d.ocnt, d.N, d.scan_bsum);
-  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbr, ctx->cl[q].count,
+  unsigned long long* bsum64 = (unsigned long long*)d.scan_bsum;
+  k_scan_reduce<<<nbr, kScanThreads, 0, s>>>(d.cnt2, d.N, bsum64);
+  k_scan_top<<<1, kScanTopThreads, 0, s>>>(bsum64, nbr, ctx->cl[q].count,
                                            d.Cmax, d.status, kStListOverflow);
-  k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.ocnt, d.N, d.scan_bsum,
-                                            RowEpi{d, ctx->ps[q], ctx->cl[q]});
+  k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.cnt2, d.N, (const unsigned long long*)bsum64,
+                                            HstartEpi{d.hstart, d.istart});
+  k_compact<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
   if (tm) cudaEventRecord(ev[3], s);
   // 5. one thread per contact
   k_force<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[p], ctx->cl[q]);
@@ -328,6 +330,14 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
       long long H = B.Hq[a], L = B.Lq[a];
       long long S[5] = {-H, 0, H, (long long)(n - 1) * H - L, L - (long long)(n - 1) * H};
       for (int k = 0; k < 5; ++k) B.shift[a][k] = (float)S[k] * 0x1p-60f;
+      B.h[a] = bx.L[a] / n;
+      if (ctx->mode == kMIXED) {
+        B.hcell[a][0] = (float)H * 0x1p-60f;
+        B.hcell[a][1] = B.periodic[a] ? (float)(L - (long long)(n - 1) * H) * 0x1p-60f : INFINITY;
+      } else {
+        B.hcell[a][0] = (float)B.h[a];
+        B.hcell[a][1] = B.periodic[a] ? (float)B.h[a] : INFINITY;
+      }
       ncell *= n;
     }
     if (ncell > (1ll << 30)) return bail(DEM_ERR_ARG, "too many cells");
@@ -382,7 +392,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   ctx->M_lin = (int)Mlin;
   ctx->M_rank = (int)Mrank;
   ctx->max_cap = max_cap;
-  long long cmax = (long long)N * (ctx->K / 2 + 1);
+  long long cmax = (long long)N * std::max(4, ctx->K / 4);
   if (cmax > (1ll << 31) - 1) cmax = (1ll << 31) - 1;
   ctx->Cmax = (int)std::max(1ll, cmax);
 
@@ -408,18 +418,23 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.ccount = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
   d.cstart = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
   d.crange = (int2*)A(sizeof(int2) * std::max(1, ctx->M_lin));
+  d.cellr = (float*)A(sizeof(float) * std::max(1, ctx->M_lin));
   d.perm = (int*)A(sizeof(int) * n);
   d.row = (int*)A(sizeof(int) * n * ctx->K);
   d.ocnt = (int*)A(sizeof(int) * n);
   d.icnt = (int*)A(sizeof(int) * n);
   d.hstart = (int*)A(sizeof(int) * n);
+  d.istart = (int*)A(sizeof(int) * n);
+  d.cnt2 = (unsigned long long*)A(sizeof(unsigned long long) * n);
   d.Fc = A(v4_bytes(M) * ctx->Cmax);
   d.nFc = A(v4_bytes(M) * ctx->Cmax);
+  d.Fin = A(v4_bytes(M) * ctx->Cmax);
+  d.nFin = A(v4_bytes(M) * ctx->Cmax);
   d.Fout = A(v4_bytes(M) * n);
   d.Tout = A(v4_bytes(M) * n);
   d.status = (unsigned*)A(sizeof(unsigned));
   d.diag = (unsigned*)A(sizeof(unsigned) * 2 * ctx->hbox.size());
-  d.scan_bsum = (int*)A(sizeof(int) * 8192);
+  d.scan_bsum = (int*)A(sizeof(unsigned long long) * kScanTopThreads * kScanTopItems);
   for (int p = 0; p < 2; ++p) {
     PState& s = ctx->ps[p];
     s.px = A(pos_bytes(M) * n);
@@ -1016,7 +1031,7 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
 // point runs the same search kernels as dem_step on one small box, with all
 // of its scratch carved from one file-scope device array of fixed size.
 // The array exists on every GPU that loads this library until the process
-// exits (about 4.7 MB).
+// exits (about 4.8 MB).
 // ==========================================================================
 namespace {
 
@@ -1027,7 +1042,7 @@ constexpr int kStaticK = 32;
 
 // layout of the scratch array (every part 256-byte aligned)
 struct StaticLayout {
-  size_t box, slot_box, rol, lor, ccount, cstart, crange, perm, row, ocnt,
+  size_t box, slot_box, rol, lor, ccount, cstart, crange, cellr, perm, row, ocnt,
       icnt, hstart, bsum, status, count, pair, rs, rc, state[2][10], total;
 };
 
@@ -1049,12 +1064,13 @@ StaticLayout static_layout() {
   L.ccount = take(4 * (M + 1));
   L.cstart = take(4 * (M + 1));
   L.crange = take(8 * M);
+  L.cellr = take(4 * M);
   L.perm = take(4 * N);
   L.row = take(4 * N * kStaticK);
   L.ocnt = take(4 * N);
   L.icnt = take(4 * N);
   L.hstart = take(4 * N);
-  L.bsum = take(4 * 8192);
+  L.bsum = take(4 * 16384);
   L.status = take(4);
   L.count = take(4);
   L.pair = take(8 * (size_t)kStaticMaxContacts);
@@ -1069,7 +1085,7 @@ StaticLayout static_layout() {
 }
 
 // Upper bound of the layout above (checked at set-up).
-constexpr size_t kStaticScratchBytes = 4900000;
+constexpr size_t kStaticScratchBytes = 5100000;
 
 }  // namespace
 
@@ -1173,6 +1189,9 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
     long long H = B.Hq[a], Lq = B.Lq[a];
     long long S[5] = {-H, 0, H, (long long)(nc - 1) * H - Lq, Lq - (long long)(nc - 1) * H};
     for (int k = 0; k < 5; ++k) B.shift[a][k] = (float)S[k] * 0x1p-60f;
+    B.h[a] = L[a] / nc;
+    B.hcell[a][0] = (float)H * 0x1p-60f;
+    B.hcell[a][1] = B.periodic[a] ? (float)(Lq - (long long)(nc - 1) * H) * 0x1p-60f : INFINITY;
   }
   B.ncells = (int)M;
   B.cap = N;
@@ -1192,6 +1211,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   d.ccount = (int*)(base + lay.ccount);
   d.cstart = (int*)(base + lay.cstart);
   d.crange = (int2*)(base + lay.crange);
+  d.cellr = (float*)(base + lay.cellr);
   d.perm = (int*)(base + lay.perm);
   d.row = (int*)(base + lay.row);
   d.ocnt = (int*)(base + lay.ocnt);
@@ -1237,14 +1257,15 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum,
                                             CellEpi{d.cstart, d.crange, d.lin_of_rank});
   k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
-  k_cellsort<<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ps[0]);
+  k_cellsort<kMIXED><<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ps[0]);
   k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1]);
   k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1]);
   int nbr = blocks_for(N, kScanTile);
   k_scan_reduce<<<nbr, kScanThreads, 0, s>>>(d.ocnt, N, d.scan_bsum);
   k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbr, cn.count, d.Cmax, d.status,
                                            kStListOverflow);
-  k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.ocnt, N, d.scan_bsum, RowEpi{d, ps[1], cn});
+  k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.ocnt, N, d.scan_bsum, StartEpi{d.hstart});
+  k_compact<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);
   if ((st = ck(cudaGetLastError(), "launch"))) return st;
   int hcount = 0;
   unsigned hstatus = 0;

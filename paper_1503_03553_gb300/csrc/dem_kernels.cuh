@@ -88,13 +88,18 @@ struct Dev {
   int* ccount;   // per rank cell: particles binned, then a scatter cursor
   int* cstart;   // per rank cell: first slot
   int2* crange;  // per linear cell: (first slot, count)
+  float* cellr;  // per linear cell: largest radius in the cell (-1 if empty)
   int* perm;     // new slot -> old slot
   int* row;      // N x K: owned partners from the front, others from the back
   int* ocnt;     // contacts a slot owns (partner has the larger id)
   int* icnt;     // contacts owned by the partner
   int* hstart;   // first list entry of a slot's owned contacts
+  int* istart;   // first incoming-list entry of a slot
+  unsigned long long* cnt2;  // owned | incoming << 32, per slot (scan input)
   void* Fc;      // V4 per contact: force on the lower-id particle
   void* nFc;     // V4 per contact: n x F
+  void* Fin;     // V4 per contact, in the higher-id particle's incoming list
+  void* nFin;    // V4 per contact: n x F, incoming list
   void* Fout;    // V4 per slot: total force of the last step
   void* Tout;    // V4 per slot: total torque of the last step
   unsigned* status;
@@ -330,16 +335,17 @@ __global__ void k_set_state(Dev d, PState s, int box, int n,
 // device-wide exclusive scan (three passes, deterministic)
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanTile = kScanThreads * kScanItems;  // 4096
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 1024
 constexpr int kScanTopThreads = 1024;
-constexpr int kScanTopItems = 8;                     // <= 8192 tiles
+constexpr int kScanTopItems = 16;                    // <= 16384 tiles
 
-__device__ __forceinline__ int warp_incl_scan(int v) {
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
   int lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    int t = __shfl_up_sync(0xffffffffu, v, o);
+    T t = __shfl_up_sync(0xffffffffu, v, o);
     if (lane >= o) v += t;
   }
   return v;
@@ -347,61 +353,64 @@ __device__ __forceinline__ int warp_incl_scan(int v) {
 
 // block-wide exclusive scan of one value per thread; returns the prefix and
 // the block total in *total
-template <int NT>
-__device__ __forceinline__ int block_excl_scan(int v, int* total) {
-  __shared__ int wsum[NT / 32];
+template <int NT, typename T>
+__device__ __forceinline__ T block_excl_scan(T v, T* total) {
+  __shared__ T wsum[NT / 32];
   int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int inc = warp_incl_scan(v);
+  T inc = warp_incl_scan(v);
   if (lane == 31) wsum[wid] = inc;
   __syncthreads();
   if (wid == 0) {
-    int s = lane < NT / 32 ? wsum[lane] : 0;
-    int si = warp_incl_scan(s);
+    T s = lane < NT / 32 ? wsum[lane] : T(0);
+    T si = warp_incl_scan(s);
     if (lane < NT / 32) wsum[lane] = si - s;
     if (lane == NT / 32 - 1) *total = si;
   }
   __syncthreads();
-  int r = wsum[wid] + inc - v;
+  T r = wsum[wid] + inc - v;
   __syncthreads();
   return r;
 }
 
+template <typename T>
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_reduce(const int* __restrict__ in, int n, int* __restrict__ bsum) {
+k_scan_reduce(const T* __restrict__ in, int n, T* __restrict__ bsum) {
   int base = blockIdx.x * kScanTile;
-  int s = 0;
+  T s = 0;
   for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
     int idx = base + k;
     if (idx < n) s += in[idx];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ int ws[kScanThreads / 32];
+  __shared__ T ws[kScanThreads / 32];
   if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
   __syncthreads();
   if (threadIdx.x == 0) {
-    int t = 0;
+    T t = 0;
     for (int q = 0; q < kScanThreads / 32; ++q) t += ws[q];
     bsum[blockIdx.x] = t;
   }
 }
 
-// Exclusive scan of the tile sums in place.  *total gets the grand total,
-// clamped to cap (a larger total sets status bit over_bit).
+// Exclusive scan of the tile sums in place.  *total gets the grand total
+// (low 32 bits for packed 64-bit counts), clamped to cap (a larger total sets
+// status bit over_bit).
+template <typename T>
 __global__ void __launch_bounds__(kScanTopThreads)
-k_scan_top(int* bsum, int nb, int* total, int cap, unsigned* status,
+k_scan_top(T* bsum, int nb, int* total, int cap, unsigned* status,
            unsigned over_bit) {
-  __shared__ int tot;
-  int v[kScanTopItems];
-  int s = 0;
+  __shared__ T tot;
+  T v[kScanTopItems];
+  T s = 0;
   int base = threadIdx.x * kScanTopItems;
 #pragma unroll
   for (int q = 0; q < kScanTopItems; ++q) {
     int idx = base + q;
-    v[q] = idx < nb ? bsum[idx] : 0;
+    v[q] = idx < nb ? bsum[idx] : T(0);
     s += v[q];
   }
-  int pre = block_excl_scan<kScanTopThreads>(s, &tot);
+  T pre = block_excl_scan<kScanTopThreads, T>(s, &tot);
 #pragma unroll
   for (int q = 0; q < kScanTopItems; ++q) {
     int idx = base + q;
@@ -409,38 +418,38 @@ k_scan_top(int* bsum, int nb, int* total, int cap, unsigned* status,
     pre += v[q];
   }
   if (threadIdx.x == 0 && total) {
-    int t = tot;
+    long long t = (long long)(tot & T(0xffffffffu));
     if (t > cap) {
       atomicOr(status, over_bit);
       t = cap;
     }
-    *total = t;
+    *total = (int)t;
   }
 }
 
-// Per tile: coalesced load to shared memory, 16 consecutive items per
-// thread, block scan, then the epilogue is called once per item
+// Per tile: coalesced load to shared memory, kScanItems consecutive items
+// per thread, block scan, then the epilogue is called once per item
 // epi(index, count, exclusive_prefix) with coalesced indices.
-template <class Epi>
+template <typename T, class Epi>
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_apply(const int* __restrict__ in, int n, const int* __restrict__ bsum,
+k_scan_apply(const T* __restrict__ in, int n, const T* __restrict__ bsum,
              Epi epi) {
-  __shared__ int buf[kScanTile];
-  __shared__ int tot;
+  __shared__ T buf[kScanTile];
+  __shared__ T tot;
   int base = blockIdx.x * kScanTile;
   for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
     int idx = base + k;
-    buf[k] = idx < n ? in[idx] : 0;
+    buf[k] = idx < n ? in[idx] : T(0);
   }
   __syncthreads();
-  int v[kScanItems];
-  int s = 0;
+  T v[kScanItems];
+  T s = 0;
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
     v[q] = buf[threadIdx.x * kScanItems + q];
     s += v[q];
   }
-  int pre = block_excl_scan<kScanThreads>(s, &tot) + bsum[blockIdx.x];
+  T pre = block_excl_scan<kScanThreads, T>(s, &tot) + bsum[blockIdx.x];
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
     buf[threadIdx.x * kScanItems + q] = pre;
@@ -485,18 +494,22 @@ __global__ void k_scatter(Dev d, PState a) {
 
 // Insertion sort of each cell's segment of perm by particle id: the slot
 // order is (Morton rank of the cell, id), independent of atomic timing.
+template <int M>
 __global__ void k_cellsort(Dev d, PState a) {
+  using V4 = typename Tr<M>::V4;
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= d.M_lin) return;
   int2 r = d.crange[l];
-  if (r.y < 2) return;
   int* seg = d.perm + r.x;
+  const V4* omg = (const V4*)a.omg;
+  float rmax = r.y > 0 ? 0.0f : -1.0f;  // -1 marks an empty cell
   constexpr int kLocal = 24;
   if (r.y <= kLocal) {
     int sl[kLocal], key[kLocal];
     for (int q = 0; q < r.y; ++q) {
       sl[q] = seg[q];
       key[q] = a.id[sl[q]];
+      rmax = fmaxf(rmax, (float)omg[sl[q]].w);
     }
     for (int q = 1; q < r.y; ++q) {
       int ks = key[q], ss = sl[q], p = q - 1;
@@ -510,6 +523,7 @@ __global__ void k_cellsort(Dev d, PState a) {
     }
     for (int q = 0; q < r.y; ++q) seg[q] = sl[q];
   } else {
+    for (int q = 0; q < r.y; ++q) rmax = fmaxf(rmax, (float)omg[seg[q]].w);
     for (int q = 1; q < r.y; ++q) {
       int ss = seg[q], ks = a.id[ss], p = q - 1;
       while (p >= 0 && a.id[seg[p]] > ks) {
@@ -519,6 +533,7 @@ __global__ void k_cellsort(Dev d, PState a) {
       seg[p + 1] = ss;
     }
   }
+  if (d.cellr) d.cellr[l] = rmax;
 }
 
 // ---------------------------------------------------------------------------
@@ -619,32 +634,46 @@ __device__ __forceinline__ bool pred_abs(const float4& pi, const float4& pj,
   return d2 < __fmul_rn(R, R);
 }
 
-// neighbour cell along one axis: returns false when it lies outside a
-// non-periodic box; *shift gets the fixed-rule shift in metres
-__device__ __forceinline__ bool nb_axis(const BoxDev& B, int a, int c, int dlt,
-                                        int& cn, float& shift) {
-  int n = B.n[a];
-  cn = c + dlt;
+// Neighbour cell at step s (|s| <= w) along axis a from cell c: false when
+// it lies outside a non-periodic box.  *shift gets the fixed-rule shift in
+// metres, (float)((cn - c) H + image L) with image = -1 / +1 when the step
+// wraps below 0 / above n - 1 (the oracle's rounding, exactly).
+__device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
+                                          int& cn, float& shift) {
+  const int n = B.n[a];
+  cn = c + s;
+  long long image = 0;
   if (cn < 0) {
     if (!B.periodic[a]) return false;
-    cn = n - 1;
-    shift = B.shift[a][3];
+    cn += n;
+    image = -1;
   } else if (cn >= n) {
     if (!B.periodic[a]) return false;
-    cn = 0;
-    shift = B.shift[a][4];
-  } else {
-    shift = B.shift[a][dlt + 1];
+    cn -= n;
+    image = 1;
   }
+  shift = __fmul_rn(i64_to_f32_rn((long long)(cn - c) * B.Hq[a] + image * B.Lq[a]), kQ);
   return true;
 }
 
 // ---------------------------------------------------------------------------
 // contact search: one thread per particle over the 27 neighbour cells
-// (Algorithm 1 loops), writing partner slots into the particle's row
+// (Algorithm 1 loops), writing partner slots into the particle's row.
+// Pass 1 decides, with independent loads, which neighbour cells can hold a
+// contact: a cell is skipped when its nearest point is farther than r_i plus
+// the largest radius in that cell (0.1 % margin, far above rounding).
+// Pass 2 tests the candidates of the kept cells in (dz, dy, dx) order, four
+// at a time so that four loads are in flight.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int sel3i(int a0, int a1, int a2, int k) {
+  return k == 0 ? a0 : (k == 1 ? a1 : a2);
+}
+__device__ __forceinline__ float sel3f(float a0, float a1, float a2, int k) {
+  return k == 0 ? a0 : (k == 1 ? a1 : a2);
+}
+
 template <int M>
-__global__ void k_candidates(Dev d, PState b) {
+__global__ void __launch_bounds__(256, 4) k_candidates(Dev d, PState b) {
   using T = Tr<M>;
   using PR = typename T::PR;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -653,79 +682,152 @@ __global__ void k_candidates(Dev d, PState b) {
   if (i - B.pbase >= B.nlive) {
     d.ocnt[i] = 0;
     d.icnt[i] = 0;
+    if (d.cnt2) d.cnt2[i] = 0ull;
     return;
   }
   const PR* __restrict__ posr = (const PR*)b.posr;
-  PR pi = ld4(posr + i);
-  int idi = b.id[i];
-  int cx, cy, cz;
-  unpack_cell(b.cellc[i], cx, cy, cz);
+  const int2* __restrict__ crange = d.crange;
+  const float* __restrict__ cellr = d.cellr;
+  const int* __restrict__ ids = b.id;
+  const PR pi = ld4(posr + i);
+  const int idi = ids[i];
+  const int n0 = B.n[0], n1 = B.n[1], lb = B.lin_base;
+  int c[3];
+  unpack_cell(b.cellc[i], c[0], c[1], c[2]);
+  // per axis and step (-1, 0, +1): neighbour cell (-1 = outside an open
+  // box), fixed-rule shift, squared gap from the particle to that cell
+  int nc[3][3];
+  float sh[3][3], g2[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    float o, hc = c[a] == B.n[a] - 1 ? B.hcell[a][1] : B.hcell[a][0];
+    if (M == kMIXED) o = (float)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z);
+    else o = (float)((double)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z) - (double)c[a] * B.h[a]);
+    const float gl = fmaxf(o, 0.0f), gh = fmaxf(hc - o, 0.0f);
+#pragma unroll
+    for (int st = 0; st < 3; ++st) {
+      int cn;
+      float shift = 0.0f;
+      nc[a][st] = axis_step(B, a, c[a], st - 1, cn, shift) ? cn : -1;
+      sh[a][st] = shift;
+      const float g = st == 0 ? gl : (st == 2 ? gh : 0.0f);
+      g2[a][st] = g * g;
+    }
+  }
+  const float ri = (float)pi.w;
+  unsigned keep = 0u;
+#pragma unroll
+  for (int k = 0; k < 27; ++k) {
+    const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
+    if (nc[2][kz] < 0 || nc[1][ky] < 0 || nc[0][kx] < 0) continue;
+    const int lin = lb + (nc[2][kz] * n1 + nc[1][ky]) * n0 + nc[0][kx];
+    const float cr = __ldg(cellr + lin);  // < 0: empty cell
+    const float reach = 1.001f * (ri + cr);
+    if (cr >= 0.0f && g2[2][kz] + g2[1][ky] + g2[0][kx] <= reach * reach) keep |= 1u << k;
+  }
   int own = 0, inc = 0;
   const int K = d.K;
   int* rowp = d.row + (size_t)i * K;
   bool over = false;
-  for (int dz = -1; dz <= 1; ++dz) {
-    int czn;
-    float sz;
-    if (!nb_axis(B, 2, cz, dz, czn, sz)) continue;
-    for (int dy = -1; dy <= 1; ++dy) {
-      int cyn;
-      float sy;
-      if (!nb_axis(B, 1, cy, dy, cyn, sy)) continue;
-      for (int dx = -1; dx <= 1; ++dx) {
-        int cxn;
-        float sx;
-        if (!nb_axis(B, 0, cx, dx, cxn, sx)) continue;
-        int lin = (czn * B.n[1] + cyn) * B.n[0] + cxn;
-        int2 rg = d.crange[B.lin_base + lin];
-        for (int j = rg.x; j < rg.x + rg.y; ++j) {
-          if (j == i) continue;
-          PR pj = ld4(posr + j);
-          bool hit;
-          if (M == kMIXED)
-            hit = pred_fixed(*(const float4*)&pi, *(const float4*)&pj, sx, sy, sz);
-          else
-            hit = pred_abs(pi, pj, B);
-          if (hit) {
-            if (own + inc >= K) {
-              over = true;
-              continue;
-            }
-            if (b.id[j] > idi) rowp[own++] = j;
-            else rowp[K - 1 - inc++] = j;
-          }
+  // Pass 2, warp-uniform: each iteration every lane tests its next four
+  // candidates, first moving on to its next kept cell when the current one is
+  // exhausted; one reconvergence point per iteration keeps the lanes of a
+  // warp testing together (iterations ~ the largest per-lane candidate count).
+  const unsigned wmask = __activemask();
+  int j = 0, e = 0;
+  float sx = 0.f, sy = 0.f, sz = 0.f;
+  while (__any_sync(wmask, j < e || keep != 0u)) {
+    if (j >= e && keep != 0u) {
+      const int k = __ffs(keep) - 1;
+      keep &= keep - 1u;
+      const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
+      const int cz = sel3i(nc[2][0], nc[2][1], nc[2][2], kz);
+      const int cy = sel3i(nc[1][0], nc[1][1], nc[1][2], ky);
+      const int cx = sel3i(nc[0][0], nc[0][1], nc[0][2], kx);
+      sz = sel3f(sh[2][0], sh[2][1], sh[2][2], kz);
+      sy = sel3f(sh[1][0], sh[1][1], sh[1][2], ky);
+      sx = sel3f(sh[0][0], sh[0][1], sh[0][2], kx);
+      const int2 rg = __ldg(crange + lb + (cz * n1 + cy) * n0 + cx);
+      j = rg.x;
+      e = rg.x + rg.y;
+    }
+    if (j < e) {
+      const int m = e - j;
+      const PR p0 = ld4(posr + j);
+      const PR p1 = m > 1 ? ld4(posr + j + 1) : p0;
+      const PR p2 = m > 2 ? ld4(posr + j + 2) : p0;
+      const PR p3 = m > 3 ? ld4(posr + j + 3) : p0;
+      unsigned hm;
+      if (M == kMIXED) {
+        const float4& q = *(const float4*)&pi;
+        hm = (unsigned)pred_fixed(q, *(const float4*)&p0, sx, sy, sz) |
+             ((unsigned)pred_fixed(q, *(const float4*)&p1, sx, sy, sz) << 1) |
+             ((unsigned)pred_fixed(q, *(const float4*)&p2, sx, sy, sz) << 2) |
+             ((unsigned)pred_fixed(q, *(const float4*)&p3, sx, sy, sz) << 3);
+      } else {
+        hm = (unsigned)pred_abs(pi, p0, B) | ((unsigned)pred_abs(pi, p1, B) << 1) |
+             ((unsigned)pred_abs(pi, p2, B) << 2) | ((unsigned)pred_abs(pi, p3, B) << 3);
+      }
+      hm &= (m >= 4) ? 0xFu : ((1u << m) - 1u);
+      while (hm) {
+        const int jj = j + __ffs(hm) - 1;
+        hm &= hm - 1u;
+        if (jj == i) continue;
+        if (own + inc >= K) {
+          over = true;
+        } else if (ids[jj] > idi) {
+          rowp[own++] = jj;
+        } else {
+          rowp[K - 1 - inc++] = jj;
         }
       }
+      j += 4;
     }
+    __syncwarp(wmask);
   }
   if (over) flag(d.status, kStRowOverflow);
   d.ocnt[i] = own;
   d.icnt[i] = inc;
+  if (d.cnt2) d.cnt2[i] = (unsigned long long)own | ((unsigned long long)inc << 32);
 }
 
-// owned counts -> contact list: each slot writes its owned pairs at its
-// prefix and its row of the by-id history index
-struct RowEpi {
-  Dev d;
-  PState b;
-  CList cn;
-  __device__ void operator()(int i, int own, int pre) const {
-    d.hstart[i] = pre;
-    const BoxDev& B = d.boxes[d.slot_box[i]];
-    if (i - B.pbase >= B.nlive) return;
-    int idi = b.id[i];
-    int n = own;
-    if (pre + n > d.Cmax) n = max(0, d.Cmax - pre);
-    cn.rs[idi] = pre;
-    cn.rc[idi] = n;
-    const int* rowp = d.row + (size_t)i * d.K;
-    for (int k = 0; k < n; ++k) {
-      int j = rowp[k];
-      cn.pair[pre + k] = make_int2(i, j);
-      cn.hid[pre + k] = make_int2(idi, b.id[j]);
-    }
+// owned counts -> first list entry of each slot
+struct StartEpi {
+  int* hstart;
+  __device__ void operator()(int i, int, int pre) const { hstart[i] = pre; }
+};
+
+// packed (owned, incoming) counts -> first entries of each slot in the
+// contact list and in the incoming list
+struct HstartEpi {
+  int* hstart;
+  int* istart;
+  __device__ void operator()(int i, unsigned long long, unsigned long long pre) const {
+    hstart[i] = (int)(pre & 0xffffffffull);
+    istart[i] = (int)(pre >> 32);
   }
 };
+
+// dense contact list: each live slot writes its owned pairs at its prefix
+// and its entry of the by-id history index
+__global__ void k_compact(Dev d, PState b, CList cn) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[i]];
+  if (i - B.pbase >= B.nlive) return;
+  int pre = d.hstart[i];
+  int n = d.ocnt[i];
+  if (pre + n > d.Cmax) n = max(0, d.Cmax - pre);
+  int idi = b.id[i];
+  cn.rs[idi] = pre;
+  cn.rc[idi] = n;
+  const int* rowp = d.row + (size_t)i * d.K;
+  for (int k = 0; k < n; ++k) {
+    int j = rowp[k];
+    cn.pair[pre + k] = make_int2(i, j);
+    cn.hid[pre + k] = make_int2(idi, b.id[j]);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // contact geometry: unit normal n (from 1 to 2) and overlap dn
@@ -994,6 +1096,27 @@ k_force(Dev d, PState b, CList co, CList cn) {
     ((DT*)cn.dz)[c] = nz;
     st4((V4*)d.Fc + c, F4);
     st4((V4*)d.nFc + c, N4);
+    if (d.Fin) {
+      // the same contact in the incoming list of the higher-id particle j,
+      // at the position of i among j's incoming partners
+      const int nin = d.icnt[j];
+      const int* rowj = d.row + (size_t)j * d.K + (d.K - 1);
+      int pos = -1;
+      for (int q = 0; q < nin; ++q)
+        if (rowj[-q] == i) {
+          pos = q;
+          break;
+        }
+      if (pos < 0) {
+        flag(d.status, kStInconsistent);
+      } else {
+        const int at = d.istart[j] + pos;
+        if (at < d.Cmax) {
+          st4((V4*)d.Fin + at, F4);
+          st4((V4*)d.nFin + at, N4);
+        }
+      }
+    }
   }
   // every lane of the warp reaches this point
   const unsigned full = 0xffffffffu;
@@ -1036,24 +1159,36 @@ __global__ void k_gather_integrate(Dev d, PState b, int store_ft) {
     F = F + xyz(f);
     Ns = Ns + xyz(q);
   }
-  const int K = d.K;
-  const int* rowi = d.row + (size_t)i * K;
-  for (int k = 0; k < inc; ++k) {
-    int j = rowi[K - 1 - k];
-    int oj = d.ocnt[j], hj = d.hstart[j], c = -1;
-    const int* rowj = d.row + (size_t)j * K;
-    for (int q = 0; q < oj; ++q)
-      if (rowj[q] == i) {
-        c = hj + q;
-        break;
-      }
-    if (c < 0 || c >= d.Cmax) {
-      flag(d.status, kStInconsistent);
-      continue;
+  if (d.Fin) {
+    const V4* Fin = (const V4*)d.Fin;
+    const V4* nFin = (const V4*)d.nFin;
+    const int is = d.istart[i];
+    for (int k = 0; k < inc; ++k) {
+      if (is + k >= d.Cmax) break;
+      V4 f = ld4(Fin + is + k), q = ld4(nFin + is + k);
+      F = F - xyz(f);
+      Ns = Ns + xyz(q);
     }
-    V4 f = ld4(Fc + c), q = ld4(nFc + c);
-    F = F - xyz(f);
-    Ns = Ns + xyz(q);
+  } else {
+    const int K = d.K;
+    const int* rowi = d.row + (size_t)i * K;
+    for (int k = 0; k < inc; ++k) {
+      int j = rowi[K - 1 - k];
+      int oj = d.ocnt[j], hj = d.hstart[j], c = -1;
+      const int* rowj = d.row + (size_t)j * K;
+      for (int q = 0; q < oj; ++q)
+        if (rowj[q] == i) {
+          c = hj + q;
+          break;
+        }
+      if (c < 0 || c >= d.Cmax) {
+        flag(d.status, kStInconsistent);
+        continue;
+      }
+      V4 f = ld4(Fc + c), q = ld4(nFc + c);
+      F = F - xyz(f);
+      Ns = Ns + xyz(q);
+    }
   }
   V4 vm = ((const V4*)b.vel)[i];
   V4 wr = ((const V4*)b.omg)[i];

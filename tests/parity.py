@@ -37,8 +37,11 @@ def quantize(x):
     return np.ldexp(np.round(np.ldexp(np.asarray(x, np.float64), 60)), -60)
 
 
-def grid_for(box):
-    hmin = 2.0 * box.r_max * (1.0 + 1e-5)
+STENCIL = 1  # neighbour cells per axis (+-1): cells of at least 2 r_max
+
+
+def grid_for(box, stencil=STENCIL):
+    hmin = 2.0 * box.r_max * (1.0 + 1e-5) / stencil
     return [max(1, int(math.floor(box.L[a] / hmin))) for a in range(3)]
 
 
@@ -63,19 +66,21 @@ def prepared(box, precision):
     return b
 
 
-def oracle_params(box, precision, ncell, brute_force=0):
+def oracle_params(box, precision, ncell, brute_force=0, stencil=STENCIL):
     return O.make_params(box.L, box.dt, E=box.E, poisson=box.poisson,
                          density=box.density, restitution=box.restitution,
                          mu_d=box.mu_d, periodic=box.periodic,
                          floor_wall=box.floor_wall, g=box.g, ncell=ncell,
-                         predicate=PRED[precision], brute_force=brute_force)
+                         predicate=PRED[precision], brute_force=brute_force,
+                         stencil=stencil)
 
 
-def gpu_run(boxes, precision, ncells, steps=1, **kw):
+def gpu_run(boxes, precision, ncells, steps=1, stencil=STENCIL, **kw):
     """Create a context for ``boxes``, set particles, run ``steps`` steps
     and collect everything per box."""
     import paper_1503_03553_gb300 as D
 
+    assert stencil == 1, "the library searches +-1 neighbour cells"
     ctx = D.Context(boxes, precision=precision, ncell=ncells, **kw)
     try:
         for k, b in enumerate(boxes):
@@ -94,8 +99,8 @@ def gpu_run(boxes, precision, ncells, steps=1, **kw):
         ctx.close()
 
 
-def oracle_run(box, precision, ncell):
-    p = oracle_params(box, precision, ncell)
+def oracle_run(box, precision, ncell, stencil=STENCIL):
+    p = oracle_params(box, precision, ncell, stencil=stencil)
     cell, order = O.order(p, box.x)
     s = O.State(box.x, box.v, box.w, box.r, floor_wall=bool(box.floor_wall))
     x0, v0, w0 = s.x.copy(), s.v.copy(), s.w.copy()

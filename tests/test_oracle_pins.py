@@ -57,6 +57,22 @@ def test_cell_search_equals_brute_force(dense_box, pred):
     assert np.array_equal(lo, lo2) and np.array_equal(hi, hi2)
 
 
+@pytest.mark.parametrize("pred", [O.PRED_FP64, O.PRED_FIXED_F32, O.PRED_ABS_F32])
+def test_two_cell_stencil_equals_brute_force(dense_box, pred):
+    """Cells half as wide searched +-2 per axis find the same pairs."""
+    b = dense_box
+    p = O.make_params(b.L, b.dt, r_max=b.r_max, predicate=pred, stencil=2)
+    pb = O.make_params(b.L, b.dt, r_max=b.r_max, predicate=pred, stencil=2,
+                       brute_force=1)
+    assert p.ncell[0] >= 2 * O.make_params(b.L, b.dt, r_max=b.r_max).ncell[0] - 1
+    lo, hi = O.contacts(p, b.x, b.r)
+    lo2, hi2 = O.contacts(pb, b.x, b.r)
+    assert np.array_equal(lo, lo2) and np.array_equal(hi, hi2)
+    if pred == O.PRED_FP64:
+        lo1, hi1 = O.contacts(O.make_params(b.L, b.dt, r_max=b.r_max), b.x, b.r)
+        assert np.array_equal(lo, lo1) and np.array_equal(hi, hi1)
+
+
 def _kdtree_pairs(x, r, L):
     """Contact set by scipy's periodic k-d tree, distances recomputed with
     the same minimum-image rounding as the definition."""

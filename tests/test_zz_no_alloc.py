@@ -37,8 +37,8 @@ def test_static_contacts_match_dem_step_two_calls():
     boxes = [prepared(synth.w2_polydisperse(n=3000, seed=41), "mixed"),
              prepared(synth.w2_polydisperse(n=1200, seed=42), "mixed")]
     for box in boxes:  # two calls in a row, the second on a smaller box
-        ncell = grid_for(box)
-        ref = gpu_run([box], "mixed", [ncell])[0]  # contacts found by dem_step
+        ncell = grid_for(box, stencil=1)
+        ref = gpu_run([box], "mixed", [ncell], stencil=1)[0]  # dem_step's contacts
         lo, hi = _static_pairs(box, ncell, cap=16 * box.n)
         assert len(ref["lo"]) > box.n
         assert np.array_equal(lo, ref["lo"]) and np.array_equal(hi, ref["hi"])
@@ -51,7 +51,7 @@ def test_static_contacts_reject_oversize():
     r = torch.full((8193,), 1e-6, dtype=torch.float64, device="cuda")
     pairs = torch.zeros((16, 2), dtype=torch.int32, device="cuda")
     with pytest.raises(D.DemError) as e:
-        D.dem_contacts_static(x, r, box.L, box.periodic, grid_for(box), pairs)
+        D.dem_contacts_static(x, r, box.L, box.periodic, grid_for(box, stencil=1), pairs)
     assert e.value.status == D.DEM_ERR_ARG and "8192" in str(e.value)
     with pytest.raises(D.DemError) as e:
         D.dem_contacts_static(x[:10], r[:10], (1e-3,) * 3, (1, 1, 1), (40, 40, 40), pairs)
