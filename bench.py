@@ -48,6 +48,9 @@ def _args():
                     help="skip the FP64-GPU, parity and CPU-baseline side legs")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-batched", action="store_true", help="skip the W4 batched leg")
+    ap.add_argument("--nboxes", type=int, default=512)
+    ap.add_argument("--batched-steps", type=int, default=32)
     return ap.parse_args()
 
 
@@ -127,6 +130,40 @@ def phase_bytes(n, c_half, ncells):
             "integrate": integrate}
 
 
+def search_tests(box, ncell):
+    """Candidate tests the contact search performs: for every particle, the
+    particles of each of its 27 neighbour cells that survive the reach test
+    (nearest point of the cell within 1.001 (r_i + largest radius in it)).
+    Computed from the same positions and grid as the run."""
+    L = np.asarray(box.L)
+    n = np.asarray(ncell)
+    h = L / n
+    c = np.minimum((box.x // h).astype(np.int64), n - 1)
+    o = box.x - c * h
+    lin = (c[:, 2] * n[1] + c[:, 1]) * n[0] + c[:, 0]
+    M = int(np.prod(n))
+    cnt = np.bincount(lin, minlength=M)
+    rmax = np.full(M, -1.0)
+    np.maximum.at(rmax, lin, box.r)
+    tests = 0
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                cn = (c + np.array([dx, dy, dz])) % n
+                l2 = (cn[:, 2] * n[1] + cn[:, 1]) * n[0] + cn[:, 0]
+                g = np.zeros(box.n)
+                for a, dd in enumerate((dx, dy, dz)):
+                    if dd < 0:
+                        g += np.maximum(o[:, a], 0) ** 2
+                    elif dd > 0:
+                        g += np.maximum(h[a] - o[:, a], 0) ** 2
+                reach = 1.001 * (box.r + rmax[l2])
+                keep = (rmax[l2] >= 0) & (g <= reach ** 2)
+                tests += int(cnt[l2][keep].sum())
+    return tests
+
+
+SEARCH_OPS_PER_TEST = 14  # FP32 instructions of the contact predicate
 PHASES = ["sort", "search", "compact", "force", "integrate"]
 PHASE_KERNELS = {"sort": 6, "search": 1, "compact": 3, "force": 1, "integrate": 1}
 
@@ -295,16 +332,30 @@ def main():
     ph_ms = dict(zip(PHASES, ph.tolist()))
     dom = max(ph_ms, key=ph_ms.get)
     peaks, src = _peaks()
-    achieved = pb[dom] / (ph_ms[dom] * 1e-3) / 1e9
     total_bytes = sum(pb.values())
-    roof = {"bound": "hbm", "kernel_phase": dom, "achieved": achieved,
-            "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-            "peak_source": src,
-            "algorithmic_bytes_per_launch": pb[dom],
-            "phase_ms": ph_ms, "phase_bytes": pb,
-            "step_algorithmic_bytes": total_bytes,
-            "step_frac_of_hbm": total_bytes / (secs / args.steps) / 1e9 / peaks["hbm_gbs"]}
+    clk_mhz = clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if dom == "search":
+        # ALU-bound: FP32 instruction issue, 152 SMs x 128 lanes per clock
+        tests = search_tests(box, ncell)
+        ops = tests * SEARCH_OPS_PER_TEST
+        peak = 152 * 128 * clk_mhz * 1e6 / 1e12
+        achieved = ops / (ph_ms[dom] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_candidates", "kernel_phase": dom,
+                "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s (FP32 instructions, each counted once)",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (median SM clock)",
+                "algorithmic_ops_per_launch": ops, "candidate_tests_per_launch": tests}
+    else:
+        achieved = pb[dom] / (ph_ms[dom] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel_phase": dom, "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_launch": pb[dom]}
+    roof.update({"phase_ms": ph_ms, "phase_bytes": pb,
+                 "step_algorithmic_bytes": total_bytes,
+                 "step_frac_of_hbm": total_bytes / (secs / args.steps) / 1e9 / peaks["hbm_gbs"]})
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_path):
         try:
@@ -362,28 +413,75 @@ def main():
     print(json.dumps(line))
 
 
-def _side_legs(args, D, torch, box, ncell, stream):
-    """FP64 GPU throughput on the same workload, and force error of one step
-    against the FP64 oracle over every contact of the full workload."""
-    out = {}
+def _throughput(D, torch, stream, boxes, precision, ncells, steps, warmup=3):
     with torch.cuda.stream(stream):
-        ctx = D.Context([box], precision="fp64", ncell=[ncell])
-    ctx.set_particles(0, box.x, box.v, box.w, box.r)
-    ctx.step(3)
-    k = max(8, args.steps // 20)
-    secs = _time_steps(ctx, torch, k, 1)
-    out["fp64_gpu"] = {"value": box.n * k / secs, "unit": METRIC, "steps": k,
-                       "ms_per_step": secs / k * 1e3}
-    ctx.close()
+        ctx = D.Context(boxes, precision=precision, ncell=ncells)
     try:
-        from parity import gpu_run, oracle_run, check_one_step
-        g = gpu_run([box], "mixed", [ncell])[0]
-        o = oracle_run(box, "mixed", ncell)
-        m = check_one_step(box, g, o, "mixed")
-        out["force_parity_vs_fp64_oracle"] = {"pass": True, **m}
-    except AssertionError as e:
-        out["force_parity_vs_fp64_oracle"] = {"pass": False, "error": str(e)[:300]}
+        for k, b in enumerate(boxes):
+            ctx.set_particles(k, b.x, b.v, b.w, b.r)
+        ctx.step(warmup)
+        secs = _time_steps(ctx, torch, steps, 1)
+    finally:
+        ctx.close()
+    n = sum(b.n for b in boxes)
+    return {"value": n * steps / secs, "unit": METRIC, "steps": steps,
+            "ms_per_step": secs / steps * 1e3}
+
+
+def _side_legs(args, D, torch, box, ncell, stream):
+    """Comparison legs: the FP64 and FP32 GPU forms on the same workload, the
+    force error of one step of each form against the FP64 oracle over every
+    contact, and batched boxes against a box-by-box loop."""
+    from parity import (check_one_step, force_errors, gpu_run, oracle_run,
+                        prepared)
+    out = {}
+    k = max(8, args.steps // 20)
+    out["fp64_gpu"] = _throughput(D, torch, stream, [box], "fp64", [ncell], k)
+    out["fp32_gpu"] = _throughput(D, torch, stream, [box], "fp32", [ncell], max(16, args.steps // 4))
+    errs = {}
+    for prec in ("mixed", "fp32", "fp64"):
+        b = prepared(box, prec)
+        g = gpu_run([b], prec, [ncell])[0]
+        o = oracle_run(b, prec, ncell)
+        errs[prec] = force_errors(b, g, o, prec)
+        if prec == "mixed":
+            try:
+                m = check_one_step(b, g, o, "mixed")
+                out["force_parity_vs_fp64_oracle"] = {"pass": True, **m}
+            except AssertionError as e:
+                out["force_parity_vs_fp64_oracle"] = {"pass": False, "error": str(e)[:300]}
+    out["force_error_vs_fp64_oracle"] = errs
+    if not args.no_batched:
+        out["batched"] = _batched_leg(args, D, torch, stream)
     return out
+
+
+def _batched_leg(args, D, torch, stream):
+    """W4: many independent periodic boxes in one context (one launch per
+    kernel for all boxes, CUDA graphs) against the same boxes stepped one
+    context at a time."""
+    from paper_1503_03553_gb300 import synth
+    from parity import grid_for, prepared
+    procs = max(1, min(16, os.cpu_count() or 1))
+    boxes = [prepared(b, "mixed") for b in synth.w4_batched(nboxes=args.nboxes, processes=procs)]
+    ncells = [grid_for(b) for b in boxes]
+    steps = args.batched_steps
+    res = {"boxes": len(boxes), "particles": int(sum(b.n for b in boxes)), "steps": steps}
+    res["batched"] = _throughput(D, torch, stream, boxes, "mixed", ncells, steps)
+    total = 0.0
+    for b, nc in zip(boxes, ncells):
+        with torch.cuda.stream(stream):
+            ctx = D.Context([b], precision="mixed", ncell=[nc])
+        try:
+            ctx.set_particles(0, b.x, b.v, b.w, b.r)
+            ctx.step(3)
+            total += _time_steps(ctx, torch, steps, 1)
+        finally:
+            ctx.close()
+    res["box_by_box"] = {"value": res["particles"] * steps / total, "unit": METRIC,
+                         "ms_per_step": total / steps * 1e3}
+    res["speedup"] = res["batched"]["value"] / res["box_by_box"]["value"]
+    return res
 
 
 if __name__ == "__main__":

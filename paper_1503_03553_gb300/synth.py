@@ -301,24 +301,39 @@ def w3_bidisperse_floor(n: int = 8_000_000, seed: int = 3,
                mu_d=0.3)
 
 
+def _w4_box(args):
+    """One box of W4 (top level so that a process pool can run it)."""
+    seed, b, nmin, nmax = args
+    rng = np.random.Generator(np.random.PCG64([SEED_BASE + seed, b]))
+    n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
+    phi = float(rng.uniform(0.2, 0.5))
+    r = _lognormal_radii(rng, n, 4e-6, 0.2, 2e-6, 8e-6)
+    L = _box_for(r, phi)
+    # jittered simple-cubic lattice start: few overlaps, fast relaxation
+    m = int(math.ceil(n ** (1.0 / 3.0)))
+    grid = np.stack(np.meshgrid(np.arange(m), np.arange(m), np.arange(m), indexing="ij"),
+                    -1).reshape(-1, 3)
+    sites = grid[rng.permutation(len(grid))[:n]].astype(np.float64)
+    x = (sites + 0.5 + 0.1 * rng.standard_normal((n, 3))) * (np.asarray(L) / m)
+    x = relax_overlaps(np.mod(x, np.asarray(L)), r, L, target=0.01)
+    v = _gauss(rng, n, 0.05)
+    w = np.zeros((n, 3))
+    return Box(x=x, v=v, w=w, r=r, L=L, dt=1.0e-9,
+               restitution=float(rng.uniform(0.3, 0.9)),
+               mu_d=float(rng.uniform(0.1, 0.6)))
+
+
 def w4_batched(nboxes: int = 512, seed: int = 4, nmin: int = 200,
-               nmax: int = 20000) -> list:
-    """W4: independent periodic boxes with their own counts and materials."""
-    rng = rng_for(seed)
-    boxes = []
-    for b in range(nboxes):
-        n = int(round(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
-        phi = float(rng.uniform(0.2, 0.5))
-        r = _lognormal_radii(rng, n, 4e-6, 0.2, 2e-6, 8e-6)
-        L = _box_for(r, phi)
-        x = rng.random((n, 3)) * np.asarray(L)
-        x = relax_overlaps(x, r, L, target=0.01)
-        v = _gauss(rng, n, 0.05)
-        w = np.zeros((n, 3))
-        boxes.append(Box(x=x, v=v, w=w, r=r, L=L, dt=1.0e-9,
-                         restitution=float(rng.uniform(0.3, 0.9)),
-                         mu_d=float(rng.uniform(0.1, 0.6))))
-    return boxes
+               nmax: int = 20000, processes: int = 0) -> list:
+    """W4: independent periodic boxes with their own counts and materials.
+    Box b draws from its own stream (seed, b), so the set does not depend on
+    how many worker processes build it (`processes` > 1 uses a spawn pool)."""
+    jobs = [(seed, b, nmin, nmax) for b in range(nboxes)]
+    if processes and processes > 1 and nboxes > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(processes) as pool:
+            return pool.map(_w4_box, jobs, chunksize=max(1, nboxes // (4 * processes)))
+    return [_w4_box(j) for j in jobs]
 
 
 def w5_precision(n: int = 4_000_000, seed: int = 5, tile_n: int = 8000) -> Box:

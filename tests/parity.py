@@ -218,3 +218,27 @@ def check_one_step(box, g, o, precision, allow_dont_care=True):
     xtol = box.dt * vtol * 2 + (1e-6 if precision == "fp32" else 0) * np.max(L) + 4 * 2.0 ** -60 + 1e-19
     assert np.all(ex <= xtol), f"positions after the step, worst {float(np.max(ex / xtol)):.3g}"
     return m
+
+
+def force_errors(box, g, o, precision):
+    """Error statistics of one step against the oracle (no assertion):
+    per contact |F_gpu - F_ora| / (S_c + f_c) with the Q15 scale and floor,
+    over the contacts both sides found (the sets must be equal)."""
+    same = (len(g["lo"]) == len(o["lo"]) and np.array_equal(g["lo"], o["lo"])
+            and np.array_equal(g["hi"], o["hi"]))
+    if not same:
+        return {"contact_sets_equal": False, "gpu_contacts": int(len(g["lo"])),
+                "oracle_contacts": int(len(o["lo"]))}
+    info = o["info"]
+    if len(o["lo"]) == 0:
+        return {"contact_sets_equal": True, "contacts": 0}
+    _, floor = _contact_bounds(box, o, 1e-5)
+    e = np.linalg.norm(g["Fc"] - info["F"], axis=1) / (info["scale"] + floor)
+    nF = np.linalg.norm(info["F"], axis=1)
+    rel = np.linalg.norm(g["Fc"] - info["F"], axis=1) / np.maximum(nF, 1e-300)
+    ok = nF > 0
+    return {"contact_sets_equal": True, "contacts": int(len(e)),
+            "max_err_over_scale": float(e.max()),
+            "p99_err_over_scale": float(np.percentile(e, 99)),
+            "frac_within_1e-5": float(np.mean(e <= 1e-5)),
+            "median_rel_err": float(np.median(rel[ok])) if ok.any() else 0.0}

@@ -13,7 +13,7 @@ import pytest
 import oracle as O
 from paper_1503_03553_gb300 import synth
 
-from parity import check_one_step, gpu_run, grid_for, oracle_run, prepared
+from parity import check_one_step, force_errors, gpu_run, grid_for, oracle_run, prepared
 
 pytestmark = pytest.mark.gpu
 
@@ -204,3 +204,62 @@ def test_floor_and_gravity_match_oracle():
     check_one_step(b, g, o, "mixed")
     b, g, o = _one(box, "fp64")
     check_one_step(b, g, o, "fp64")
+
+
+def test_fp32_mode_exact_contacts_and_reported_error(dense3k):
+    """DEM_FP32 keeps absolute FP32 positions: its contact set and sort order
+    match the oracle's FP32 rule bit for bit, but the overlap carries FP32
+    rounding of the position (~6e-8 |x|), so its force error is reported
+    against the FP64 oracle and is larger than DEM_MIXED's."""
+    b = prepared(dense3k, "fp32")
+    ncell = grid_for(b)
+    g = gpu_run([b], "fp32", [ncell])[0]
+    o = oracle_run(b, "fp32", ncell)
+    assert np.array_equal(g["order"], o["order"])
+    assert np.array_equal(g["lo"], o["lo"]) and np.array_equal(g["hi"], o["hi"])
+    e32 = force_errors(b, g, o, "fp32")
+    bm = prepared(dense3k, "mixed")
+    gm = gpu_run([bm], "mixed", [grid_for(bm)])[0]
+    om = oracle_run(bm, "mixed", grid_for(bm))
+    em = force_errors(bm, gm, om, "mixed")
+    assert e32["contact_sets_equal"] and em["contact_sets_equal"]
+    assert e32["median_rel_err"] < 1e-2
+    assert em["max_err_over_scale"] < 1e-5
+    assert e32["max_err_over_scale"] > em["max_err_over_scale"]
+
+
+def test_precision_modes_ranked_on_relaxed_dense_packing():
+    """Precision stress (packing 0.60 at rest, overlaps ~1e-3 r): after 200
+    steps, re-evaluate one step from each mode's own state with the FP64
+    oracle; DEM_MIXED stays within 1e-5 of the term scale while DEM_FP32
+    does not."""
+    box = synth.w5_precision(n=4000, seed=29)
+    res = {}
+    for prec in ("mixed", "fp32"):
+        import paper_1503_03553_gb300 as D
+        b = prepared(box, prec)
+        ncell = grid_for(b)
+        ctx = D.Context([b], precision=prec, ncell=[ncell])
+        try:
+            ctx.set_particles(0, b.x, b.v, b.w, b.r)
+            ctx.step(200)
+            st = ctx.get_state(0)
+            lo, hi, dt = ctx.contacts(0)
+            snap = prepared(b, prec)
+            snap.x, snap.v, snap.w = st["x"], st["v"], st["w"]
+            ctx.step(1)
+            g = dict(state=ctx.get_state(0))
+            g["lo"], g["hi"], g["dt"] = ctx.contacts(0)
+            g["flo"], g["fhi"], g["Fc"], g["nFc"] = ctx.contact_forces(0)
+        finally:
+            ctx.close()
+        from parity import oracle_params
+        p = oracle_params(snap, prec, ncell)
+        s = O.State(snap.x, snap.v, snap.w, snap.r)
+        s.lo, s.hi, s.dt = lo, hi, dt
+        out = O.step(p, s)
+        out["params"] = p
+        res[prec] = force_errors(snap, g, out, prec)
+    assert res["mixed"]["contact_sets_equal"] and res["fp32"]["contact_sets_equal"]
+    assert res["mixed"]["p99_err_over_scale"] < 1e-5
+    assert res["fp32"]["p99_err_over_scale"] > 10 * res["mixed"]["p99_err_over_scale"]
