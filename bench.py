@@ -413,9 +413,9 @@ def main():
     print(json.dumps(line))
 
 
-def _throughput(D, torch, stream, boxes, precision, ncells, steps, warmup=3):
+def _throughput(D, torch, stream, boxes, precision, ncells, steps, warmup=3, **kw):
     with torch.cuda.stream(stream):
-        ctx = D.Context(boxes, precision=precision, ncell=ncells)
+        ctx = D.Context(boxes, precision=precision, ncell=ncells, **kw)
     try:
         for k, b in enumerate(boxes):
             ctx.set_particles(k, b.x, b.v, b.w, b.r)
@@ -451,9 +451,40 @@ def _side_legs(args, D, torch, box, ncell, stream):
             except AssertionError as e:
                 out["force_parity_vs_fp64_oracle"] = {"pass": False, "error": str(e)[:300]}
     out["force_error_vs_fp64_oracle"] = errs
+    out["collide_fused_vs_compact"] = _fused_leg(args, D, torch, stream, box, ncell)
     if not args.no_batched:
         out["batched"] = _batched_leg(args, D, torch, stream)
     return out
+
+
+def _phase_ms(D, torch, stream, boxes, precision, ncells, steps, **kw):
+    with torch.cuda.stream(stream):
+        ctx = D.Context(boxes, precision=precision, ncell=ncells, **kw)
+    try:
+        for k, b in enumerate(boxes):
+            ctx.set_particles(k, b.x, b.v, b.w, b.r)
+        ctx.step(3)
+        ctx.set_timing(True)
+        ctx.step(steps)
+        return dict(zip(PHASES, ctx.phase_times().tolist()))
+    finally:
+        ctx.close()
+
+
+def _fused_leg(args, D, torch, stream, box, ncell):
+    """The paper's comparison on this workload: Algorithm 1 (search and force
+    fused per particle, no contact list) against the split pipeline (search,
+    dense contact list, one thread per contact).  'collide' is the time of
+    the contact part of the step: fused kernel vs search + list + force."""
+    steps = max(16, args.steps // 8)
+    fused = _throughput(D, torch, stream, [box], "mixed", [ncell], steps,
+                        collide=D.DEM_COLLIDE_FUSED)
+    pf = _phase_ms(D, torch, stream, [box], "mixed", [ncell], 20, collide=D.DEM_COLLIDE_FUSED)
+    pc = _phase_ms(D, torch, stream, [box], "mixed", [ncell], 20)
+    cf = pf["search"] + pf["compact"] + pf["force"]
+    cc = pc["search"] + pc["compact"] + pc["force"]
+    return {"fused_step": fused, "collide_ms_fused": cf, "collide_ms_compact": cc,
+            "collide_speedup_of_compaction": cf / cc}
 
 
 def _batched_leg(args, D, torch, stream):

@@ -53,6 +53,8 @@ struct dem_ctx {
   int block = 256;
   int graph_steps = 16;
   int max_cap = 0;
+  bool fused = false;  // DEM_COLLIDE_FUSED: Algorithm 1, no contact list
+  int ko = 8;          // fused: stored contacts per particle
   std::vector<BoxDev> hbox;
   std::vector<void*> allocs;
   Dev dev{};
@@ -127,7 +129,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
   return spread(x) | (spread(y) << 1) | (spread(z) << 2);
 }
 
-int launches_per_step(const dem_ctx*) { return 13; }
+int launches_per_step(const dem_ctx* ctx) { return ctx->fused ? 8 : 13; }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -160,6 +162,20 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   k_cellsort<M><<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ctx->ps[p]);
   k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q]);
   if (tm) cudaEventRecord(ev[1], s);
+  if (ctx->fused) {
+    // Algorithm 1: search and force in one pass, no contact list
+    k_collide_fused<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[p],
+                                                          ctx->cl[q], ctx->ko);
+    if (tm) {
+      cudaEventRecord(ev[2], s);
+      cudaEventRecord(ev[3], s);
+      cudaEventRecord(ev[4], s);
+    }
+    k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q],
+                                                            store_ft ? 1 : 0);
+    if (tm) cudaEventRecord(ev[5], s);
+    return;
+  }
   // 3. contact search into per-particle rows
   k_candidates<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
   if (tm) cudaEventRecord(ev[2], s);
@@ -246,8 +262,8 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     return fail(nullptr, DEM_ERR_ARG, "config needs boxes and materials");
   if (cfg->precision < 0 || cfg->precision > 2)
     return fail(nullptr, DEM_ERR_ARG, "bad precision");
-  if (cfg->collide != DEM_COLLIDE_COMPACT)
-    return fail(nullptr, DEM_ERR_ARG, "collide layout not available");
+  if (cfg->collide != DEM_COLLIDE_COMPACT && cfg->collide != DEM_COLLIDE_FUSED)
+    return fail(nullptr, DEM_ERR_ARG, "collide must be DEM_COLLIDE_COMPACT or DEM_COLLIDE_FUSED");
   if (!!cfg->alloc != !!cfg->free)
     return fail(nullptr, DEM_ERR_ARG, "alloc and free hooks go together");
   ctx = new dem_ctx();
@@ -259,6 +275,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   ctx->mode = cfg->precision == DEM_FP64 ? kFP64
               : cfg->precision == DEM_MIXED ? kMIXED : kFP32;
   ctx->K = cfg->row_capacity > 0 ? cfg->row_capacity : 32;
+  ctx->fused = cfg->collide == DEM_COLLIDE_FUSED;
   ctx->block = cfg->block > 0 ? cfg->block : 256;
   ctx->graph_steps = cfg->graph_steps == 0 ? 16 : cfg->graph_steps;
   if (ctx->graph_steps > 0 && (ctx->graph_steps & 1)) ctx->graph_steps += 1;
@@ -392,9 +409,13 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   ctx->M_lin = (int)Mlin;
   ctx->M_rank = (int)Mrank;
   ctx->max_cap = max_cap;
-  long long cmax = (long long)N * std::max(4, ctx->K / 4);
+  // dense list: 8 contacts per particle on average is ample (dense
+  // packings hold 1-3); the fused layout needs a block per particle of the
+  // most contacts one particle may own
+  long long cmax = (long long)N * (ctx->fused ? std::max(4, ctx->K / 2) : std::max(4, ctx->K / 4));
   if (cmax > (1ll << 31) - 1) cmax = (1ll << 31) - 1;
   ctx->Cmax = (int)std::max(1ll, cmax);
+  ctx->ko = (int)std::max(1ll, cmax / std::max(1ll, N));
 
   // ---- device allocations ----------------------------------------------------
   const int M = ctx->mode;
@@ -428,8 +449,13 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.cnt2 = (unsigned long long*)A(sizeof(unsigned long long) * n);
   d.Fc = A(v4_bytes(M) * ctx->Cmax);
   d.nFc = A(v4_bytes(M) * ctx->Cmax);
-  d.Fin = A(v4_bytes(M) * ctx->Cmax);
-  d.nFin = A(v4_bytes(M) * ctx->Cmax);
+  if (ctx->fused) {
+    d.Ffused = A(v4_bytes(M) * n);
+    d.Tfused = A(v4_bytes(M) * n);
+  } else {
+    d.Fin = A(v4_bytes(M) * ctx->Cmax);
+    d.nFin = A(v4_bytes(M) * ctx->Cmax);
+  }
   d.Fout = A(v4_bytes(M) * n);
   d.Tout = A(v4_bytes(M) * n);
   d.status = (unsigned*)A(sizeof(unsigned));
@@ -777,57 +803,84 @@ dem_status dem_get_order(dem_ctx* ctx, int32_t box, int32_t* id_by_slot,
   return DEM_OK;
 }
 
-// Download the current contact list (all boxes) as host vectors.
+// Download the current contact list of all boxes as host vectors, walking
+// each particle's (start, count) index: works for the dense list, the fused
+// layout's per-slot blocks and a list restored by dem_set_contacts.
+// Optional per-contact force and n x F.
 static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
-                                std::vector<double>& dts) {
+                                std::vector<double>& dts,
+                                std::vector<double>* F = nullptr,
+                                std::vector<double>* nF = nullptr) {
   cudaStream_t s = ctx->stream;
   const CList& c = ctx->cl[ctx->parity];
-  CK(cudaMemcpyAsync(ctx->h_count, c.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  const int N = ctx->N;
+  std::vector<int> rs(N), rc(N);
+  hid.clear();
+  dts.clear();
+  if (N == 0) return DEM_OK;
+  CK(cudaMemcpyAsync(rs.data(), c.rs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rc.data(), c.rc, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  int nc = *ctx->h_count;
-  hid.resize(nc);
-  dts.assign((size_t)3 * nc, 0.0);
-  if (nc == 0) return DEM_OK;
-  CK(cudaMemcpyAsync(hid.data(), c.hid, sizeof(int2) * nc, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  void* comps[3] = {c.dx, c.dy, c.dz};
-  const size_t eb = dt_bytes(ctx->mode);
-  std::vector<unsigned char> raw(eb * nc);
-  for (int a = 0; a < 3; ++a) {
-    CK(cudaMemcpyAsync(raw.data(), comps[a], eb * nc, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    for (int k = 0; k < nc; ++k) {
-      double val;
-      if (ctx->mode == kMIXED) {
-        float hl[2];
-        std::memcpy(hl, raw.data() + 8 * k, 8);
-        val = (double)hl[0] + (double)hl[1];
-      } else if (ctx->mode == kFP64) {
-        std::memcpy(&val, raw.data() + 8 * k, 8);
-      } else {
-        float f;
-        std::memcpy(&f, raw.data() + 4 * k, 4);
-        val = f;
-      }
-      dts[(size_t)3 * k + a] = val;
+  long long top = 0;
+  for (const BoxDev& B : ctx->hbox)
+    for (int g = B.pbase; g < B.pbase + B.nlive; ++g)
+      if (rc[g] > 0) top = std::max(top, (long long)rs[g] + rc[g]);
+  top = std::min<long long>(top, ctx->Cmax);
+  std::vector<int2> h(top);
+  const size_t eb = dt_bytes(ctx->mode), vb = v4_bytes(ctx->mode);
+  std::vector<unsigned char> raw[3], fr, nr;
+  for (int a = 0; a < 3; ++a) raw[a].resize(eb * std::max(1ll, top));
+  if (top > 0) {
+    CK(cudaMemcpyAsync(h.data(), c.hid, sizeof(int2) * top, cudaMemcpyDeviceToHost, s));
+    void* comps[3] = {c.dx, c.dy, c.dz};
+    for (int a = 0; a < 3; ++a)
+      CK(cudaMemcpyAsync(raw[a].data(), comps[a], eb * top, cudaMemcpyDeviceToHost, s));
+    if (F) {
+      fr.resize(vb * top);
+      nr.resize(vb * top);
+      CK(cudaMemcpyAsync(fr.data(), ctx->dev.Fc, vb * top, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(nr.data(), ctx->dev.nFc, vb * top, cudaMemcpyDeviceToHost, s));
     }
+    CK(cudaStreamSynchronize(s));
   }
-  // entries of boxes whose particles were replaced are no longer history
-  size_t w = 0;
-  for (size_t k = 0; k < hid.size(); ++k) {
-    int b = -1;
-    for (size_t q = 0; q < ctx->hbox.size(); ++q)
-      if (hid[k].x >= ctx->hbox[q].pbase && hid[k].x < ctx->hbox[q].pbase + ctx->hbox[q].cap) {
-        b = (int)q;
-        break;
+  auto dtval = [&](int a, long long k) {
+    double val;
+    if (ctx->mode == kMIXED) {
+      float hl[2];
+      std::memcpy(hl, raw[a].data() + 8 * k, 8);
+      val = (double)hl[0] + (double)hl[1];
+    } else if (ctx->mode == kFP64) {
+      std::memcpy(&val, raw[a].data() + 8 * k, 8);
+    } else {
+      float f;
+      std::memcpy(&f, raw[a].data() + 4 * k, 4);
+      val = f;
+    }
+    return val;
+  };
+  auto v4val = [&](const std::vector<unsigned char>& buf, long long k, int a) {
+    if (ctx->mode == kFP64) {
+      double v;
+      std::memcpy(&v, buf.data() + 32 * k + 8 * a, 8);
+      return v;
+    }
+    float v;
+    std::memcpy(&v, buf.data() + 16 * k + 4 * a, 4);
+    return (double)v;
+  };
+  for (const BoxDev& B : ctx->hbox)
+    for (int g = B.pbase; g < B.pbase + B.nlive; ++g)
+      for (int k = 0; k < rc[g]; ++k) {
+        long long e = (long long)rs[g] + k;
+        if (e >= top) break;
+        hid.push_back(h[e]);
+        for (int a = 0; a < 3; ++a) dts.push_back(dtval(a, e));
+        if (F)
+          for (int a = 0; a < 3; ++a) {
+            F->push_back(v4val(fr, e, a));
+            nF->push_back(v4val(nr, e, a));
+          }
       }
-    if (b < 0 || ctx->hist_cleared[b]) continue;
-    hid[w] = hid[k];
-    for (int a = 0; a < 3; ++a) dts[3 * w + a] = dts[3 * k + a];
-    ++w;
-  }
-  hid.resize(w);
-  dts.resize(3 * w);
   return DEM_OK;
 }
 
@@ -865,46 +918,26 @@ dem_status dem_get_contact_forces(dem_ctx* ctx, int32_t box, int64_t cap,
   dem_status st = check_box(ctx, box);
   if (st) return st;
   if (!n) return fail(ctx, DEM_ERR_ARG, "n is null");
+  std::vector<int2> hid;
+  std::vector<double> dts, f, q;
+  st = download_list(ctx, hid, dts, &f, &q);
+  if (st) return st;
   const BoxDev& B = ctx->hbox[box];
-  cudaStream_t s = ctx->stream;
-  const CList& c = ctx->cl[ctx->parity];
-  CK(cudaMemcpyAsync(ctx->h_count, c.count, sizeof(int), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  int nc = ctx->hist_cleared[box] ? 0 : *ctx->h_count;
-  std::vector<int2> hid(nc);
-  const size_t vb = v4_bytes(ctx->mode);
-  std::vector<unsigned char> f(vb * std::max(1, nc)), q(vb * std::max(1, nc));
-  if (nc > 0) {
-    CK(cudaMemcpyAsync(hid.data(), c.hid, sizeof(int2) * nc, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(f.data(), ctx->dev.Fc, vb * nc, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(q.data(), ctx->dev.nFc, vb * nc, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-  }
   std::vector<int> sel;
-  for (int k = 0; k < nc; ++k)
-    if (hid[k].x >= B.pbase && hid[k].x < B.pbase + B.nlive) sel.push_back(k);
+  for (size_t k = 0; k < hid.size(); ++k)
+    if (hid[k].x >= B.pbase && hid[k].x < B.pbase + B.nlive) sel.push_back((int)k);
   std::sort(sel.begin(), sel.end(), [&](int a, int b) {
     return hid[a].x != hid[b].x ? hid[a].x < hid[b].x : hid[a].y < hid[b].y;
   });
   *n = (int64_t)sel.size();
   if ((int64_t)sel.size() > cap) return fail(ctx, DEM_ERR_CAPACITY, "cap smaller than the contact count");
-  auto get = [&](const std::vector<unsigned char>& buf, int k, int a) {
-    if (ctx->mode == kFP64) {
-      double v;
-      std::memcpy(&v, buf.data() + 32 * (size_t)k + 8 * a, 8);
-      return v;
-    }
-    float v;
-    std::memcpy(&v, buf.data() + 16 * (size_t)k + 4 * a, 4);
-    return (double)v;
-  };
   for (size_t t = 0; t < sel.size(); ++t) {
     int k = sel[t];
     if (id_lo) id_lo[t] = hid[k].x - B.pbase;
     if (id_hi) id_hi[t] = hid[k].y - B.pbase;
     for (int a = 0; a < 3; ++a) {
-      if (F) F[3 * t + a] = get(f, k, a);
-      if (nF) nF[3 * t + a] = get(q, k, a);
+      if (F) F[3 * t + a] = f[3 * (size_t)k + a];
+      if (nF) nF[3 * t + a] = q[3 * (size_t)k + a];
     }
   }
   return DEM_OK;

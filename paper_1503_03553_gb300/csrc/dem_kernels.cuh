@@ -98,6 +98,8 @@ struct Dev {
   unsigned long long* cnt2;  // owned | incoming << 32, per slot (scan input)
   void* Fc;      // V4 per contact: force on the lower-id particle
   void* nFc;     // V4 per contact: n x F
+  void* Ffused;  // V4 per slot: contact force sum of the fused layout
+  void* Tfused;  // V4 per slot: contact torque sum of the fused layout
   void* Fin;     // V4 per contact, in the higher-id particle's incoming list
   void* nFin;    // V4 per contact: n x F, incoming list
   void* Fout;    // V4 per slot: total force of the last step
@@ -975,127 +977,174 @@ __device__ __forceinline__ void atomic_max_pos(unsigned* p, float v) {
 }
 
 // ---------------------------------------------------------------------------
+// one pair: history lookup (InitializeContactIDs) and the contact law.  i is
+// the slot of the lower-id particle, j of the higher; idlo / idhi their ids.
+// ---------------------------------------------------------------------------
+template <int M>
+struct PairOut {
+  typename Tr<M>::V4 F4, N4;      // force on the lower particle, n x F
+  typename Tr<M>::DT nx, ny, nz;  // delta_t after the step
+  float ov, ratio;                // overlap / r_min, Coulomb ratio (0 if none)
+};
+
+template <int M>
+__device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
+                                           const CList& co, const BoxDev& B,
+                                           int i, int j, int idlo, int idhi,
+                                           PairOut<M>& out) {
+  using T = Tr<M>;
+  using P = typename T::P;
+  using R = typename T::R;
+  using V4 = typename T::V4;
+  using DT = typename T::DT;
+  const P* __restrict__ px = (const P*)b.px;
+  const P* __restrict__ py = (const P*)b.py;
+  const P* __restrict__ pz = (const P*)b.pz;
+  const V4* __restrict__ vel = (const V4*)b.vel;
+  const V4* __restrict__ omg = (const V4*)b.omg;
+  // history of this pair from the previous step's list
+  int os = co.rs[idlo], on = co.rc[idlo], found = -1;
+  for (int k = 0; k < on; ++k)
+    if (co.hid[os + k].y == idhi) {
+      found = os + k;
+      break;
+    }
+  V4 v1 = ld4(vel + i), v2 = ld4(vel + j);
+  V4 w1 = ld4(omg + i), w2 = ld4(omg + j);
+  R r1 = w1.w, r2 = w2.w;
+  v3<R> n;
+  R dn;
+  if (M == kMIXED) {
+    float fn_dn;
+    v3<float> fn_n;
+    geom_fixed(B, (long long)px[i], (long long)py[i], (long long)pz[i],
+               (long long)px[j], (long long)py[j], (long long)pz[j],
+               (float)r1, (float)r2, fn_n, fn_dn);
+    n = {(R)fn_n.x, (R)fn_n.y, (R)fn_n.z};
+    dn = (R)fn_dn;
+  } else {
+    geom_abs<R>(B, (R)px[i], (R)py[i], (R)pz[i], (R)px[j], (R)py[j],
+                (R)pz[j], r1, r2, n, dn);
+  }
+  out.F4 = V4{};
+  out.N4 = V4{};
+  out.nx = out.ny = out.nz = DT{};
+  out.ov = out.ratio = 0.0f;
+  DT ox = {}, oy = {}, oz = {};
+  if (found >= 0) {
+    ox = ((const DT*)co.dx)[found];
+    oy = ((const DT*)co.dy)[found];
+    oz = ((const DT*)co.dz)[found];
+  }
+  if (!(dn > R(0))) return;
+  v3<R> dold;
+  if (M == kMIXED) {
+    const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
+                 *fz = (const float2*)&oz;
+    dold = {(R)(fx->x + fx->y), (R)(fy->x + fy->y), (R)(fz->x + fz->y)};
+  } else {
+    dold = {*(const R*)&ox, *(const R*)&oy, *(const R*)&oz};
+  }
+  ContactOut<R> o;
+  v3<R> inc;
+  R kn_c = M == kFP64 ? (R)B.kn_c : (R)B.kn_cf;
+  R kt_c = M == kFP64 ? (R)B.kt_c : (R)B.kt_cf;
+  R al = M == kFP64 ? (R)B.alpha : (R)B.alpha_f;
+  R mu = M == kFP64 ? (R)B.mu : (R)B.mu_f;
+  R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
+  contact_law<R>(kn_c, kt_c, al, mu, dts, n, dn, r1, r2, (R)v1.w, (R)v2.w,
+                 xyz(v1), xyz(v2), xyz(w1), xyz(w2), dold, false, o, inc);
+  if (M == kMIXED) {
+    // carry delta_t as a float-float sum unless the cap reset it
+    float2* qx = (float2*)&out.nx;
+    float2* qy = (float2*)&out.ny;
+    float2* qz = (float2*)&out.nz;
+    if (o.capped) {
+      *qx = make_float2((float)o.dt.x, 0.f);
+      *qy = make_float2((float)o.dt.y, 0.f);
+      *qz = make_float2((float)o.dt.z, 0.f);
+    } else {
+      const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
+                   *fz = (const float2*)&oz;
+      ff ax = ff_add_f({fx->x, fx->y}, (float)inc.x);
+      ff ay = ff_add_f({fy->x, fy->y}, (float)inc.y);
+      ff az = ff_add_f({fz->x, fz->y}, (float)inc.z);
+      *qx = make_float2(ax.hi, ax.lo);
+      *qy = make_float2(ay.hi, ay.lo);
+      *qz = make_float2(az.hi, az.lo);
+    }
+  } else {
+    *(R*)&out.nx = o.dt.x;
+    *(R*)&out.ny = o.dt.y;
+    *(R*)&out.nz = o.dt.z;
+  }
+  out.F4 = mk4<R>(o.F.x, o.F.y, o.F.z, R(0));
+  out.N4 = mk4<R>(o.nF.x, o.nF.y, o.nF.z, R(0));
+  R rmin = r1 < r2 ? r1 : r2;
+  out.ov = (float)(dn / rmin);
+  out.ratio = (float)o.ratio;
+}
+
+// warp-level max of the per-box diagnostics held in registers; every lane
+// of the warp must call this
+__device__ __forceinline__ void flush_diag(const Dev& d, int mbox, float m_ov,
+                                           float m_ratio) {
+  const unsigned full = 0xffffffffu;
+  int b0 = __reduce_max_sync(full, mbox);
+  if (__all_sync(full, mbox == b0 || mbox < 0)) {
+    unsigned u_ov = __reduce_max_sync(full, mbox >= 0 ? __float_as_uint(m_ov) : 0u);
+    unsigned u_ra = __reduce_max_sync(full, mbox >= 0 ? __float_as_uint(m_ratio) : 0u);
+    if ((threadIdx.x & 31) == 0 && b0 >= 0) {
+      if (u_ov) atomicMax(d.diag + 2 * b0, u_ov);
+      if (u_ra) atomicMax(d.diag + 2 * b0 + 1, u_ra);
+    }
+  } else if (mbox >= 0) {
+    atomic_max_pos(d.diag + 2 * mbox, m_ov);
+    atomic_max_pos(d.diag + 2 * mbox + 1, m_ratio);
+  }
+}
+
+__device__ __forceinline__ void track_diag(const Dev& d, int box, float ov,
+                                           float ratio, int& mbox, float& m_ov,
+                                           float& m_ratio) {
+  if (box != mbox) {
+    if (mbox >= 0) {
+      atomic_max_pos(d.diag + 2 * mbox, m_ov);
+      atomic_max_pos(d.diag + 2 * mbox + 1, m_ratio);
+    }
+    mbox = box;
+    m_ov = m_ratio = 0.0f;
+  }
+  if (isfinite(ov)) m_ov = fmaxf(m_ov, ov);
+  if (isfinite(ratio)) m_ratio = fmaxf(m_ratio, ratio);
+}
+
+// ---------------------------------------------------------------------------
 // force: one thread per contact of the dense list
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(256)
 k_force(Dev d, PState b, CList co, CList cn) {
   using T = Tr<M>;
-  using P = typename T::P;
-  using R = typename T::R;
   using V4 = typename T::V4;
   using DT = typename T::DT;
   const int nc = *cn.count;
-  const P* __restrict__ px = (const P*)b.px;
-  const P* __restrict__ py = (const P*)b.py;
-  const P* __restrict__ pz = (const P*)b.pz;
-  const V4* __restrict__ vel = (const V4*)b.vel;
-  const V4* __restrict__ omg = (const V4*)b.omg;
-  // per-box diagnostics are kept in registers and reduced once per warp:
-  // one atomic per warp instead of two per contact on a single address
   int mbox = -1;
   float m_ov = 0.0f, m_ratio = 0.0f;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
        c += gridDim.x * blockDim.x) {
-    int2 pr = cn.pair[c];
-    int2 ids = cn.hid[c];
-    int i = pr.x, j = pr.y;
-    int box = d.slot_box[i];
+    const int2 pr = cn.pair[c];
+    const int2 ids = cn.hid[c];
+    const int i = pr.x, j = pr.y;
+    const int box = d.slot_box[i];
     const BoxDev& B = d.boxes[box];
-    // history of this pair from the previous step's list (InitializeContactIDs)
-    int os = co.rs[ids.x], on = co.rc[ids.x], found = -1;
-    for (int k = 0; k < on; ++k)
-      if (co.hid[os + k].y == ids.y) {
-        found = os + k;
-        break;
-      }
-    V4 v1 = ld4(vel + i), v2 = ld4(vel + j);
-    V4 w1 = ld4(omg + i), w2 = ld4(omg + j);
-    R r1 = w1.w, r2 = w2.w;
-    v3<R> n;
-    R dn;
-    if (M == kMIXED) {
-      float fn_dn;
-      v3<float> fn_n;
-      geom_fixed(B, (long long)px[i], (long long)py[i], (long long)pz[i],
-                 (long long)px[j], (long long)py[j], (long long)pz[j],
-                 (float)r1, (float)r2, fn_n, fn_dn);
-      n = {(R)fn_n.x, (R)fn_n.y, (R)fn_n.z};
-      dn = (R)fn_dn;
-    } else {
-      geom_abs<R>(B, (R)px[i], (R)py[i], (R)pz[i], (R)px[j], (R)py[j],
-                  (R)pz[j], r1, r2, n, dn);
-    }
-    V4 F4 = {}, N4 = {};
-    DT ox = {}, oy = {}, oz = {};
-    if (found >= 0) {
-      ox = ((const DT*)co.dx)[found];
-      oy = ((const DT*)co.dy)[found];
-      oz = ((const DT*)co.dz)[found];
-    }
-    DT nx = {}, ny = {}, nz = {};
-    if (dn > R(0)) {
-      v3<R> dold;
-      if (M == kMIXED) {
-        const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
-                     *fz = (const float2*)&oz;
-        dold = {(R)(fx->x + fx->y), (R)(fy->x + fy->y), (R)(fz->x + fz->y)};
-      } else {
-        dold = {*(const R*)&ox, *(const R*)&oy, *(const R*)&oz};
-      }
-      ContactOut<R> o;
-      v3<R> inc;
-      R kn_c = M == kFP64 ? (R)B.kn_c : (R)B.kn_cf;
-      R kt_c = M == kFP64 ? (R)B.kt_c : (R)B.kt_cf;
-      R al = M == kFP64 ? (R)B.alpha : (R)B.alpha_f;
-      R mu = M == kFP64 ? (R)B.mu : (R)B.mu_f;
-      R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
-      contact_law<R>(kn_c, kt_c, al, mu, dts, n, dn, r1, r2, (R)v1.w, (R)v2.w,
-                     xyz(v1), xyz(v2), xyz(w1), xyz(w2), dold, false, o, inc);
-      if (M == kMIXED) {
-        // carry delta_t as a float-float sum unless the cap reset it
-        float2* qx = (float2*)&nx;
-        float2* qy = (float2*)&ny;
-        float2* qz = (float2*)&nz;
-        if (o.capped) {
-          *qx = make_float2((float)o.dt.x, 0.f);
-          *qy = make_float2((float)o.dt.y, 0.f);
-          *qz = make_float2((float)o.dt.z, 0.f);
-        } else {
-          const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
-                       *fz = (const float2*)&oz;
-          ff ax = ff_add_f({fx->x, fx->y}, (float)inc.x);
-          ff ay = ff_add_f({fy->x, fy->y}, (float)inc.y);
-          ff az = ff_add_f({fz->x, fz->y}, (float)inc.z);
-          *qx = make_float2(ax.hi, ax.lo);
-          *qy = make_float2(ay.hi, ay.lo);
-          *qz = make_float2(az.hi, az.lo);
-        }
-      } else {
-        *(R*)&nx = o.dt.x;
-        *(R*)&ny = o.dt.y;
-        *(R*)&nz = o.dt.z;
-      }
-      F4 = mk4<R>(o.F.x, o.F.y, o.F.z, R(0));
-      N4 = mk4<R>(o.nF.x, o.nF.y, o.nF.z, R(0));
-      R rmin = r1 < r2 ? r1 : r2;
-      if (box != mbox) {
-        if (mbox >= 0) {
-          atomic_max_pos(d.diag + 2 * mbox, m_ov);
-          atomic_max_pos(d.diag + 2 * mbox + 1, m_ratio);
-        }
-        mbox = box;
-        m_ov = m_ratio = 0.0f;
-      }
-      float ov = (float)(dn / rmin), ra = (float)o.ratio;
-      if (isfinite(ov)) m_ov = fmaxf(m_ov, ov);
-      if (isfinite(ra)) m_ratio = fmaxf(m_ratio, ra);
-    }
-    ((DT*)cn.dx)[c] = nx;
-    ((DT*)cn.dy)[c] = ny;
-    ((DT*)cn.dz)[c] = nz;
-    st4((V4*)d.Fc + c, F4);
-    st4((V4*)d.nFc + c, N4);
+    PairOut<M> o;
+    pair_force<M>(d, b, co, B, i, j, ids.x, ids.y, o);
+    ((DT*)cn.dx)[c] = o.nx;
+    ((DT*)cn.dy)[c] = o.ny;
+    ((DT*)cn.dz)[c] = o.nz;
+    st4((V4*)d.Fc + c, o.F4);
+    st4((V4*)d.nFc + c, o.N4);
     if (d.Fin) {
       // the same contact in the incoming list of the higher-id particle j,
       // at the position of i among j's incoming partners
@@ -1112,26 +1161,112 @@ k_force(Dev d, PState b, CList co, CList cn) {
       } else {
         const int at = d.istart[j] + pos;
         if (at < d.Cmax) {
-          st4((V4*)d.Fin + at, F4);
-          st4((V4*)d.nFin + at, N4);
+          st4((V4*)d.Fin + at, o.F4);
+          st4((V4*)d.nFin + at, o.N4);
         }
       }
     }
+    if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
   }
-  // every lane of the warp reaches this point
-  const unsigned full = 0xffffffffu;
-  int b0 = __reduce_max_sync(full, mbox);
-  if (__all_sync(full, mbox == b0 || mbox < 0)) {
-    unsigned u_ov = __reduce_max_sync(full, mbox >= 0 ? __float_as_uint(m_ov) : 0u);
-    unsigned u_ra = __reduce_max_sync(full, mbox >= 0 ? __float_as_uint(m_ratio) : 0u);
-    if ((threadIdx.x & 31) == 0 && b0 >= 0) {
-      if (u_ov) atomicMax(d.diag + 2 * b0, u_ov);
-      if (u_ra) atomicMax(d.diag + 2 * b0 + 1, u_ra);
+  flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
+}
+
+// ---------------------------------------------------------------------------
+// Algorithm 1 of the paper, fused (DEM_COLLIDE_FUSED): one thread per
+// particle scans its neighbour cells and computes the force of each contact
+// as soon as it finds it (no contact list, no action-reaction: each pair is
+// evaluated by both of its particles, in the same orientation, so the two
+// results are exact negatives).  The lower-id particle stores the pair's
+// delta_t in its slot's block of ko entries of the next list.
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256)
+k_collide_fused(Dev d, PState b, CList co, CList cn, int ko) {
+  using T = Tr<M>;
+  using PR = typename T::PR;
+  using V4 = typename T::V4;
+  using DT = typename T::DT;
+  using R = typename T::R;
+  int mbox = -1;
+  float m_ov = 0.0f, m_ratio = 0.0f;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool live = false;
+  if (i < d.N) {
+    const BoxDev& B0 = d.boxes[d.slot_box[i]];
+    live = i - B0.pbase < B0.nlive;
+    if (!live) d.ocnt[i] = 0;
+  }
+  if (live) {
+    const int box = d.slot_box[i];
+    const BoxDev& B = d.boxes[box];
+    const PR* __restrict__ posr = (const PR*)b.posr;
+    const int* __restrict__ ids = b.id;
+    const PR pi = ld4(posr + i);
+    const int idi = ids[i];
+    int c[3];
+    unpack_cell(b.cellc[i], c[0], c[1], c[2]);
+    v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
+    int own = 0;
+    bool over = false;
+    for (int dz = -1; dz <= 1; ++dz) {
+      int czn;
+      float sz;
+      if (!axis_step(B, 2, c[2], dz, czn, sz)) continue;
+      for (int dy = -1; dy <= 1; ++dy) {
+        int cyn;
+        float sy;
+        if (!axis_step(B, 1, c[1], dy, cyn, sy)) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          int cxn;
+          float sx;
+          if (!axis_step(B, 0, c[0], dx, cxn, sx)) continue;
+          const int2 rg = d.crange[B.lin_base + (czn * B.n[1] + cyn) * B.n[0] + cxn];
+          for (int j = rg.x; j < rg.x + rg.y; ++j) {
+            if (j == i) continue;
+            const PR pj = ld4(posr + j);
+            bool hit;
+            if (M == kMIXED)
+              hit = pred_fixed(*(const float4*)&pi, *(const float4*)&pj, sx, sy, sz);
+            else
+              hit = pred_abs(pi, pj, B);
+            if (!hit) continue;
+            const int idj = ids[j];
+            const bool lo = idi < idj;
+            PairOut<M> o;
+            if (lo) pair_force<M>(d, b, co, B, i, j, idi, idj, o);
+            else pair_force<M>(d, b, co, B, j, i, idj, idi, o);
+            if (lo) {
+              F = F + xyz(o.F4);
+              if (own < ko) {
+                const int cc = i * ko + own;
+                cn.hid[cc] = make_int2(idi, idj);
+                ((DT*)cn.dx)[cc] = o.nx;
+                ((DT*)cn.dy)[cc] = o.ny;
+                ((DT*)cn.dz)[cc] = o.nz;
+                st4((V4*)d.Fc + cc, o.F4);
+                st4((V4*)d.nFc + cc, o.N4);
+                ++own;
+              } else {
+                over = true;
+              }
+              if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
+            } else {
+              F = F - xyz(o.F4);
+            }
+            Ns = Ns + xyz(o.N4);
+          }
+        }
+      }
     }
-  } else if (mbox >= 0) {
-    atomic_max_pos(d.diag + 2 * mbox, m_ov);
-    atomic_max_pos(d.diag + 2 * mbox + 1, m_ratio);
+    if (over) flag(d.status, kStListOverflow);
+    const R r = (R)pi.w;
+    st4((V4*)d.Ffused + i, mk4<R>(F.x, F.y, F.z, R(0)));
+    st4((V4*)d.Tfused + i, mk4<R>(r * Ns.x, r * Ns.y, r * Ns.z, R(0)));
+    cn.rs[idi] = i * ko;
+    cn.rc[idi] = own;
+    d.ocnt[i] = own;
   }
+  flush_diag(d, mbox, m_ov, m_ratio);
 }
 
 // ---------------------------------------------------------------------------
@@ -1152,7 +1287,8 @@ __global__ void k_gather_integrate(Dev d, PState b, int store_ft) {
   const V4* Fc = (const V4*)d.Fc;
   const V4* nFc = (const V4*)d.nFc;
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
-  int own = d.ocnt[i], hs = d.hstart[i], inc = d.icnt[i];
+  const bool fused = d.Ffused != nullptr;
+  int own = fused ? 0 : d.ocnt[i], hs = fused ? 0 : d.hstart[i], inc = fused ? 0 : d.icnt[i];
   for (int k = 0; k < own; ++k) {
     if (hs + k >= d.Cmax) break;
     V4 f = ld4(Fc + hs + k), q = ld4(nFc + hs + k);
@@ -1194,6 +1330,10 @@ __global__ void k_gather_integrate(Dev d, PState b, int store_ft) {
   V4 wr = ((const V4*)b.omg)[i];
   R m = vm.w, r = wr.w;
   v3<R> Tq = r * Ns;  // T = r (n x F), same sign for both members of a pair
+  if (d.Ffused) {
+    F = xyz(ld4((const V4*)d.Ffused + i));
+    Tq = xyz(ld4((const V4*)d.Tfused + i));
+  }
   P x = ((P*)b.px)[i], y = ((P*)b.py)[i], z = ((P*)b.pz)[i];
   // floor wall at z = 0: a body of infinite radius and mass at rest
   if (B.floor_wall) {
