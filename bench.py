@@ -188,13 +188,26 @@ def _barrier(world):
         dist.barrier()
 
 
-def _max_over_ranks(x, world, torch):
+def combine_ranks(x, world):
+    """Largest value over ranks (the timed region ends when the slowest rank
+    ends).  Works on NCCL (GPU tensor) and gloo (CPU tensor) groups."""
     if world == 1:
         return x
+    import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(n_per_rank, world, steps, secs):
+    """Whole-job particle-steps/s: every rank advances its own replica."""
+    return n_per_rank * world * steps / secs
+
+
+def _max_over_ranks(x, world, torch):
+    return combine_ranks(x, world)
 
 
 def _workload(n, seed):
@@ -318,7 +331,7 @@ def main():
     with ClockSampler(local) as clk:
         secs = _time_steps(ctx, torch, args.steps, world)
     secs = _max_over_ranks(secs, world, torch)
-    value = n * world * args.steps / secs
+    value = job_throughput(n, world, args.steps, secs)
     stats = ctx.stats(0)
     c_half = stats[5] / n
     # ---- per-phase device time (same workload, direct launches) -----------
@@ -358,9 +371,16 @@ def main():
                  "step_frac_of_hbm": total_bytes / (secs / args.steps) / 1e9 / peaks["hbm_gbs"]})
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tr_path):
+        # only while the kernels are the ones the counters were taken on
         try:
+            import hashlib
             tr = json.load(open(tr_path))
-            if tr.get("phase") == dom and tr.get("n") and tr.get("precision") == args.precision:
+            h = hashlib.sha256()
+            for f in ("dem_kernels.cuh", "dem_common.cuh"):
+                with open(os.path.join(ROOT, "paper_1503_03553_gb300", "csrc", f), "rb") as fh:
+                    h.update(fh.read())
+            if (tr.get("phase") == dom and tr.get("precision") == args.precision
+                    and tr.get("kernel_sha256") == h.hexdigest()):
                 roof["traffic"] = tr["bytes_per_launch"] * n / tr["n"]
                 roof["traffic_source"] = tr.get("source")
         except Exception:

@@ -220,6 +220,15 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]);
 int32_t dem_get_phase_times(dem_ctx* ctx, double* ms, int32_t cap);
 dem_status dem_set_timing(dem_ctx* ctx, int32_t on);
 
+/* Autotuner (orchestration): times every combination of the per-particle
+ * kernels' block size {128, 256, 512} and the CUDA-graph length {8, 16, 32}
+ * on the live state, `steps` steps each (at least 4), and keeps the fastest
+ * for this context.  The timed steps advance the simulation like dem_step.
+ * best_ms (may be NULL) receives the best time per step in milliseconds;
+ * block and graph_steps (may be NULL) the chosen values. */
+dem_status dem_autotune(dem_ctx* ctx, int64_t steps, double* best_ms,
+                        int32_t* block, int32_t* graph_steps);
+
 /* Kernel launches issued per step by the current configuration. */
 int32_t dem_launches_per_step(const dem_ctx* ctx);
 

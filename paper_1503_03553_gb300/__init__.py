@@ -94,6 +94,7 @@ def lib() -> C.CDLL:
         "dem_get_phase_times": (C.c_int32, [vp, dp, C.c_int32]),
         "dem_set_timing": (C.c_int, [vp, C.c_int32]),
         "dem_launches_per_step": (C.c_int32, [vp]),
+        "dem_autotune": (C.c_int, [vp, C.c_int64, dp, ip, ip]),
         "dem_sync": (C.c_int, [vp]),
         "dem_last_error": (C.c_char_p, [vp]),
         "dem_alpha_of_restitution": (C.c_double, [C.c_double]),
@@ -301,6 +302,16 @@ def dem_get_phase_times(ctx) -> np.ndarray:
     return out[:k].copy()
 
 
+def dem_autotune(ctx, steps: int = 32):
+    """Pick the fastest block size and graph length on the live state;
+    returns (best ms per step, block, graph_steps)."""
+    ms = C.c_double()
+    blk = C.c_int32()
+    gs = C.c_int32()
+    _check(ctx, lib().dem_autotune(ctx, int(steps), C.byref(ms), C.byref(blk), C.byref(gs)))
+    return ms.value, blk.value, gs.value
+
+
 def dem_launches_per_step(ctx) -> int:
     return lib().dem_launches_per_step(ctx)
 
@@ -447,6 +458,9 @@ class Context:
 
     def launches_per_step(self):
         return dem_launches_per_step(self.ctx)
+
+    def autotune(self, steps=32):
+        return dem_autotune(self.ctx, steps)
 
     def set_timing(self, on=True):
         dem_set_timing(self.ctx, on)

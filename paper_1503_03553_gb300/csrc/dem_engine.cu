@@ -177,7 +177,9 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
     return;
   }
   // 3. contact search into per-particle rows
-  k_candidates<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
+  // the search kernel is compiled for at most 256 threads per block
+  const int bs_search = bs < 256 ? bs : 256;
+  k_candidates<M><<<blocks_for(d.N, bs_search), bs_search, 0, s>>>(d, ctx->ps[q]);
   if (tm) cudaEventRecord(ev[2], s);
   // 4. owned counts -> dense contact list
   int nbr = blocks_for(d.N, kScanTile);
@@ -711,6 +713,67 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
     for (int k = 0; k < kPhases; ++k) ctx->phase_ms[k] = ctx->tm.acc[k] / ctx->tm.steps;
   ctx->have_ft = true;
   std::fill(ctx->hist_cleared.begin(), ctx->hist_cleared.end(), 0);
+  return read_status(ctx);
+}
+
+dem_status dem_autotune(dem_ctx* ctx, int64_t steps, double* best_ms,
+                        int32_t* block, int32_t* graph_steps) {
+  if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");
+  if (!ctx->have_particles) return fail(ctx, DEM_ERR_STATE, "no particles set");
+  if (steps < 4) steps = 4;
+  const int blocks[3] = {128, 256, 512};
+  const int graphs[3] = {8, 16, 32};
+  const bool was_timing = ctx->tm.on;
+  ctx->tm.on = false;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int bb = ctx->block, bg = ctx->graph_steps;
+  for (int gb : blocks)
+    for (int gg : graphs) {
+      ctx->block = gb;
+      ctx->graph_steps = gg;
+      for (auto& g : ctx->gexec)
+        if (g) {
+          cudaGraphExecDestroy(g);
+          g = nullptr;
+        }
+      // one untimed graph-length of warm-up, then the timed steps
+      dem_status st = dem_step(ctx, gg);
+      if (st) break;
+      const int64_t k = std::max<int64_t>(steps / gg, 1) * gg;
+      CK(cudaEventRecord(e0, ctx->stream));
+      st = dem_step(ctx, k);
+      CK(cudaEventRecord(e1, ctx->stream));
+      CK(cudaEventSynchronize(e1));
+      if (st) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return st;
+      }
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      const double per = ms / (double)k;
+      if (per < best) {
+        best = per;
+        bb = gb;
+        bg = gg;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->block = bb;
+  ctx->graph_steps = bg;
+  for (auto& g : ctx->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  ctx->tm.on = was_timing;
+  if (best_ms) *best_ms = best;
+  if (block) *block = bb;
+  if (graph_steps) *graph_steps = bg;
   return read_status(ctx);
 }
 

@@ -289,3 +289,24 @@ def test_fused_and_compact_agree_over_steps(dense3k):
     scale = np.abs(c["state"]["v"]).max()
     assert np.allclose(f["state"]["v"], c["state"]["v"], rtol=0, atol=1e-5 * scale)
     assert np.allclose(f["dt"], c["dt"], rtol=1e-4, atol=1e-4 * np.abs(c["dt"]).max())
+
+
+def test_autotune_picks_a_valid_config_and_keeps_results_exact(dense3k):
+    """The autotuner only changes launch shapes: a tuned context and an
+    untuned one give bit-identical states for the same number of steps."""
+    import paper_1503_03553_gb300 as D
+    b = prepared(dense3k, "mixed")
+    ncell = grid_for(b)
+    ctx = D.Context([b], precision="mixed", ncell=[ncell])
+    try:
+        ctx.set_particles(0, b.x, b.v, b.w, b.r)
+        ms, blk, gs = ctx.autotune(steps=8)
+        assert ms > 0 and blk in (128, 256, 512) and gs in (8, 16, 32)
+        # per block size and graph length g: g warm-up steps + the timed steps
+        ran = 3 * sum(g + max(8 // g, 1) * g for g in (8, 16, 32))
+        tuned = ctx.get_state(0)
+    finally:
+        ctx.close()
+    ref = gpu_run([b], "mixed", [ncell], steps=ran)[0]["state"]
+    for k in ("x", "v", "w"):
+        assert np.array_equal(tuned[k], ref[k]), k
