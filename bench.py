@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--no-batched", action="store_true", help="skip the W4 batched leg")
     ap.add_argument("--nboxes", type=int, default=512)
     ap.add_argument("--batched-steps", type=int, default=32)
+    ap.add_argument("--w3", action="store_true",
+                    help="add the 8M-particle floor/gravity leg (dense + dilute halves)")
     return ap.parse_args()
 
 
@@ -474,7 +476,27 @@ def _side_legs(args, D, torch, box, ncell, stream):
     out["collide_fused_vs_compact"] = _fused_leg(args, D, torch, stream, box, ncell)
     if not args.no_batched:
         out["batched"] = _batched_leg(args, D, torch, stream)
+    if args.w3:
+        out["w3_floor_8M"] = _w3_leg(args, D, torch, stream)
     return out
+
+
+def _w3_leg(args, D, torch, stream):
+    """W3: 8,000,000 bidisperse spheres, dense lower half and dilute upper
+    half (divergence stress), floor and gravity: contact-list compaction vs
+    the fused Algorithm 1, and the FP32 / FP64 forms."""
+    from paper_1503_03553_gb300 import synth
+    from parity import grid_for, prepared
+    box = prepared(synth.w3_bidisperse_floor(n=8_000_000, seed=3), "mixed")
+    nc = grid_for(box)
+    res = {"particles": box.n, "ncell": nc}
+    res["mixed_compact"] = _throughput(D, torch, stream, [box], "mixed", [nc], 40)
+    res["mixed_compact"]["phase_ms"] = _phase_ms(D, torch, stream, [box], "mixed", [nc], 10)
+    res["mixed_fused"] = _throughput(D, torch, stream, [box], "mixed", [nc], 8,
+                                     collide=D.DEM_COLLIDE_FUSED)
+    res["fp32_compact"] = _throughput(D, torch, stream, [box], "fp32", [nc], 40)
+    res["fp64_compact"] = _throughput(D, torch, stream, [box], "fp64", [nc], 8)
+    return res
 
 
 def _phase_ms(D, torch, stream, boxes, precision, ncells, steps, **kw):

@@ -262,35 +262,29 @@ def w2_polydisperse(n: int = 1_000_000, seed: int = 2, tile_n: int = 8000,
 
 
 def w3_bidisperse_floor(n: int = 8_000_000, seed: int = 3,
-                        tile_xy: Optional[int] = None) -> Box:
-    """W3: bidisperse spheres, dense lower half (0.55), dilute upper half
-    (0.05), floor at z = 0, gravity along -z, periodic in x and y."""
+                        column_n: int = 20000) -> Box:
+    """W3: bidisperse spheres (r = 3 and 6 um, 50/50 by number) in a cube,
+    lower half at packing 0.55, upper half at 0.05, floor at z = 0, gravity
+    along -z, periodic in x and y.  Built from one relaxed column (periodic
+    in x and y, hard floor and lid during the relaxation) of about column_n
+    spheres, repeated k x k times in x and y with shuffled ids."""
     rng = rng_for(seed)
-    r_of = lambda g, m: _f32(np.where(g.random(m) < 0.5, 3e-6, 6e-6))
     mean_vol = 4.0 / 3.0 * math.pi * 0.5 * ((3e-6) ** 3 + (6e-6) ** 3)
-    # cube of side L with n = (0.55 + 0.05)/2 * L^3 / mean_vol
-    Lc = (n * mean_vol / 0.30) ** (1.0 / 3.0)
-    n_dense = int(round(0.55 * Lc ** 3 / 2 / mean_vol))
-    n_dil = n - n_dense
-    k = tile_xy or max(1, int(round((n_dense / 6000) ** 0.5 / (Lc / 2 / Lc) ** 0.5 / 4)))
-    # dense slab: relax one column tile (x-y periodic, hard walls in z)
-    k = max(1, k)
-    tile_L = (Lc / k, Lc / k, Lc / 2)
-    n0 = max(2, n_dense // (k * k))
-    r0 = r_of(rng, n0)
-    x0 = rng.random((n0, 3)) * np.asarray(tile_L)
-    x0 = relax_overlaps(x0, r0, tile_L, periodic=(1, 1, 0), target=0.01)
+    Lc = (n * mean_vol / 0.30) ** (1.0 / 3.0)  # average packing (0.55+0.05)/2
+    k = max(1, int(round(math.sqrt(n / column_n))))
+    cl = (Lc / k, Lc / k, Lc)
+    n_col = int(round(n / (k * k)))
+    n_dense = int(round(n_col * 0.55 / 0.60))
+    n_dil = n_col - n_dense
+    r = _f32(np.where(rng.random(n_col) < 0.5, 3e-6, 6e-6))
+    x = rng.random((n_col, 3)) * np.asarray(cl)
+    x[:n_dense, 2] *= 0.5
+    x[n_dense:, 2] = Lc / 2 + x[n_dense:, 2] * 0.5
+    x = relax_overlaps(x, r, cl, periodic=(1, 1, 0), target=0.01)
     offs = np.array([(i, j, 0) for j in range(k) for i in range(k)],
-                    dtype=np.float64) * np.asarray(tile_L)
-    xd = (x0[None] + offs[:, None]).reshape(-1, 3)
-    rd = np.tile(r0, k * k)
-    # dilute half: uniform random, no overlap removal needed at 0.05 beyond a
-    # light relaxation
-    rdl = r_of(rng, n_dil)
-    xdl = rng.random((n_dil, 3)) * np.array([Lc, Lc, Lc / 2]) + np.array([0, 0, Lc / 2])
-    xdl[:, 2] = np.clip(xdl[:, 2], Lc / 2 + 6e-6, Lc - 6e-6)
-    X = np.concatenate([xd, xdl])
-    R = np.concatenate([rd, rdl])
+                    dtype=np.float64) * np.asarray(cl)
+    X = (x[None] + offs[:, None]).reshape(-1, 3)
+    R = np.tile(r, k * k)
     perm = rng.permutation(len(R))
     X, R = X[perm], R[perm]
     m = len(R)

@@ -199,7 +199,7 @@ def test_multi_step_statistics_track_oracle(dense3k):
 
 
 def test_floor_and_gravity_match_oracle():
-    box = synth.w3_bidisperse_floor(n=6000, seed=28, tile_xy=1)
+    box = synth.w3_bidisperse_floor(n=6000, seed=28, column_n=6000)
     b, g, o = _one(box, "mixed")
     check_one_step(b, g, o, "mixed")
     b, g, o = _one(box, "fp64")
