@@ -133,10 +133,12 @@ def phase_bytes(n, c_half, ncells):
 
 
 def search_tests(box, ncell):
-    """Candidate tests the contact search performs: for every particle, the
-    particles of each of its 27 neighbour cells that survive the reach test
-    (nearest point of the cell within 1.001 (r_i + largest radius in it)).
-    Computed from the same positions and grid as the run."""
+    """Candidate tests the contact search performs: every pair is tested once,
+    by the particle whose half of the neighbourhood holds the other (its own
+    cell's later slots and the 13 cells after it in (dz, dy, dx) order); of
+    those 13 cells only the ones that survive the reach test count (nearest
+    point of the cell within 1.001 (r_i + largest radius in it)).  Computed
+    from the same positions and grid as the run."""
     L = np.asarray(box.L)
     n = np.asarray(ncell)
     h = L / n
@@ -147,10 +149,12 @@ def search_tests(box, ncell):
     cnt = np.bincount(lin, minlength=M)
     rmax = np.full(M, -1.0)
     np.maximum.at(rmax, lin, box.r)
-    tests = 0
+    tests = int((cnt * (cnt - 1) // 2).sum())  # own cell, later slots
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
             for dx in (-1, 0, 1):
+                if (dz, dy, dx) <= (0, 0, 0):
+                    continue
                 cn = (c + np.array([dx, dy, dz])) % n
                 l2 = (cn[:, 2] * n[1] + cn[:, 1]) * n[0] + cn[:, 0]
                 g = np.zeros(box.n)

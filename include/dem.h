@@ -116,7 +116,8 @@ typedef struct {
   int32_t collide;            /* dem_collide                                */
   int32_t kn_literal;         /* 1 = k_n with the printed (2 - sigma^2)/E    */
                               /* term of Sec. 2 instead of Hertz 1 - sigma^2 */
-  int32_t row_capacity;       /* max contacts of one particle; 0 = 32       */
+  int32_t row_capacity;       /* max contacts of one particle, 2..126;      */
+                              /* 0 = 32                                     */
   int32_t graph_steps;        /* steps per captured CUDA graph; 0 = 16,     */
                               /* -1 = launch kernels directly              */
   int32_t block;              /* threads per block of per-particle kernels; */
@@ -266,11 +267,14 @@ int32_t dem_abi_version(void);
  * position is rounded to 2^-60 m fixed point and a pair is in contact when
  * the single-precision test of dem_step accepts it.
  * Output: pairs (device, cap x 2 int32, 8-byte aligned) receives
- * (id_lo, id_hi) of every contact, id_lo < id_hi, grouped by id_lo in cell
- * order; *count (host) the number of contacts.
+ * (id_lo, id_hi) of every contact, id_lo < id_hi, each pair once, in an
+ * order fixed by the cell grid (sort them for a canonical order); *count
+ * (host) the number of contacts.
  * Limits: n <= 8192, ncell[0] * ncell[1] * ncell[2] <= 32768, at most
- * 131072 contacts (fewer if cap is smaller) and 32 per particle; larger
- * sizes are rejected with DEM_ERR_ARG (sizes) or DEM_ERR_CAPACITY (contacts).
+ * 131072 contacts (fewer if cap is smaller), and at most 32 partners found
+ * by one particle in its half of the neighbour cells (its own cell's later
+ * slots and the 13 cells after it); larger sizes are rejected with
+ * DEM_ERR_ARG (sizes) or DEM_ERR_CAPACITY (contacts).
  * Runs on `stream` (cudaStream_t, NULL = legacy default) and returns after
  * synchronising it.  The first call on a device looks up the array's device
  * address (once per device, with that device current); make that first call

@@ -42,6 +42,7 @@ struct BoxDev {
   float shift[3][5];    // fixed-rule cell shifts: -H, 0, +H, wrap low, wrap high
   float hcell[3][2];    // cell edge [m]: ordinary cell, last cell (inf when open)
   double h[3];          // L / ncell [m]
+  float rmax_f;         // largest radius the box may hold [m]
   int n[3];             // cells per axis
   int periodic[3];
   int floor_wall;

@@ -171,7 +171,7 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
       cudaEventRecord(ev[3], s);
       cudaEventRecord(ev[4], s);
     }
-    k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q],
+    k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q],
                                                             store_ft ? 1 : 0);
     if (tm) cudaEventRecord(ev[5], s);
     return;
@@ -188,14 +188,14 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   k_scan_top<<<1, kScanTopThreads, 0, s>>>(bsum64, nbr, ctx->cl[q].count,
                                            d.Cmax, d.status, kStListOverflow);
   k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.cnt2, d.N, (const unsigned long long*)bsum64,
-                                            HstartEpi{d.hstart, d.istart});
+                                            HstartEpi{d.hstart, d.istart, d.icnt, d.status, d.K});
   k_compact<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
   if (tm) cudaEventRecord(ev[3], s);
   // 5. one thread per contact
   k_force<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[p], ctx->cl[q]);
   if (tm) cudaEventRecord(ev[4], s);
   // 6. sum, wall, gravity, integrate, bin
-  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q],
+  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q],
                                                           store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
@@ -292,7 +292,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     }
     return s;
   };
-  if (ctx->K < 2 || ctx->K > 1024) return bail(DEM_ERR_ARG, "row_capacity out of range");
+  if (ctx->K < 2 || ctx->K > 126) return bail(DEM_ERR_ARG, "row_capacity out of range [2, 126]");
   if (ctx->block < 32 || ctx->block > 1024 || (ctx->block & 31))
     return bail(DEM_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
   if (cudaGetDevice(&ctx->device) != cudaSuccess)
@@ -361,6 +361,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     }
     if (ncell > (1ll << 30)) return bail(DEM_ERR_ARG, "too many cells");
     B.floor_wall = bx.floor_wall ? 1 : 0;
+    B.rmax_f = (float)bx.r_max;
     ctx->any_floor |= B.floor_wall != 0;
     B.ncells = (int)ncell;
     B.lin_base = (int)Mlin;
@@ -405,7 +406,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   }
   const long long scan_limit = (long long)kScanTile * kScanTopThreads * kScanTopItems;
   if (N > scan_limit || Mrank > scan_limit)
-    return bail(DEM_ERR_ARG, "more than 2^25 slots or cells in one context");
+    return bail(DEM_ERR_ARG, "more than 2^24 slots or cells in one context");
   ctx->hist_cleared.assign(ctx->boxes.size(), 0);
   ctx->N = (int)N;
   ctx->M_lin = (int)Mlin;
@@ -455,8 +456,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     d.Ffused = A(v4_bytes(M) * n);
     d.Tfused = A(v4_bytes(M) * n);
   } else {
-    d.Fin = A(v4_bytes(M) * ctx->Cmax);
-    d.nFin = A(v4_bytes(M) * ctx->Cmax);
+    d.inlist = (int*)A(sizeof(int) * ctx->Cmax);
   }
   d.Fout = A(v4_bytes(M) * n);
   d.Tout = A(v4_bytes(M) * n);
@@ -1293,6 +1293,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   B.cap = N;
   B.nlive = N;
   B.density = 1.0;
+  B.rmax_f = (float)(0.5 * hmin);
 
   Dev d{};
   d.boxes = (const BoxDev*)(base + lay.box);

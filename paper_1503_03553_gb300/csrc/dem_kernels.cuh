@@ -90,18 +90,17 @@ struct Dev {
   int2* crange;  // per linear cell: (first slot, count)
   float* cellr;  // per linear cell: largest radius in the cell (-1 if empty)
   int* perm;     // new slot -> old slot
-  int* row;      // N x K: owned partners from the front, others from the back
-  int* ocnt;     // contacts a slot owns (partner has the larger id)
-  int* icnt;     // contacts owned by the partner
-  int* hstart;   // first list entry of a slot's owned contacts
+  int* row;      // N x K: partners a slot found (slot | incoming position << 24)
+  int* ocnt;     // contacts a slot found (half stencil)
+  int* icnt;     // contacts in which a slot was found by its partner
+  int* hstart;   // first list entry of a slot's found contacts
   int* istart;   // first incoming-list entry of a slot
-  unsigned long long* cnt2;  // owned | incoming << 32, per slot (scan input)
+  unsigned long long* cnt2;  // found | incoming << 32, per slot (scan input)
+  int* inlist;   // incoming list: contact indices, grouped by partner slot
   void* Fc;      // V4 per contact: force on the lower-id particle
   void* nFc;     // V4 per contact: n x F
   void* Ffused;  // V4 per slot: contact force sum of the fused layout
   void* Tfused;  // V4 per slot: contact torque sum of the fused layout
-  void* Fin;     // V4 per contact, in the higher-id particle's incoming list
-  void* nFin;    // V4 per contact: n x F, incoming list
   void* Fout;    // V4 per slot: total force of the last step
   void* Tout;    // V4 per slot: total torque of the last step
   unsigned* status;
@@ -501,7 +500,7 @@ __global__ void k_cellsort(Dev d, PState a) {
   using V4 = typename Tr<M>::V4;
   int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= d.M_lin) return;
-  int2 r = d.crange[l];
+  const int2 r = d.crange[l];
   int* seg = d.perm + r.x;
   const V4* omg = (const V4*)a.omg;
   float rmax = r.y > 0 ? 0.0f : -1.0f;  // -1 marks an empty cell
@@ -561,6 +560,7 @@ __global__ void k_reorder(Dev d, PState a, PState b) {
   st4((V4*)b.vel + t, vel);
   st4((V4*)b.omg + t, om);
   b.id[t] = a.id[s];
+  if (d.cnt2) d.cnt2[t] = 0ull;  // the search accumulates into it
   int cc = a.cellx[s];
   b.cellc[t] = cc;
   if (a.wx) {
@@ -640,6 +640,12 @@ __device__ __forceinline__ bool pred_abs(const float4& pi, const float4& pj,
 // it lies outside a non-periodic box.  *shift gets the fixed-rule shift in
 // metres, (float)((cn - c) H + image L) with image = -1 / +1 when the step
 // wraps below 0 / above n - 1 (the oracle's rounding, exactly).
+// neighbour cell index along one axis, wrapped (callers check that a step
+// out of an open box is never taken)
+__device__ __forceinline__ int wrap_cell(int cn, int n) {
+  return cn < 0 ? cn + n : (cn >= n ? cn - n : cn);
+}
+
 __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
                                           int& cn, float& shift) {
   const int n = B.n[a];
@@ -659,23 +665,25 @@ __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
 }
 
 // ---------------------------------------------------------------------------
-// contact search: one thread per particle over the 27 neighbour cells
-// (Algorithm 1 loops), writing partner slots into the particle's row.
+// contact search: one thread per particle over half of the 27 neighbour
+// cells (Algorithm 1 loops, each pair tested once): its own cell from the
+// next slot on and the 13 cells after it in (dz, dy, dx) order.  With at
+// least 3 cells on every periodic axis each pair of distinct cells is then
+// one step apart in exactly one direction, and the predicate is exactly
+// antisymmetric, so the pairs found are the pairs of the full stencil.
+// Found partners go into the particle's row; each found pair also takes the
+// next position in the partner's incoming count (a 64-bit atomic add on the
+// packed counts; the order of those positions is fixed later, when the
+// incoming list is summed in contact-index order).
 // Pass 1 decides, with independent loads, which neighbour cells can hold a
 // contact: a cell is skipped when its nearest point is farther than r_i plus
 // the largest radius in that cell (0.1 % margin, far above rounding).
 // Pass 2 tests the candidates of the kept cells in (dz, dy, dx) order, four
 // at a time so that four loads are in flight.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int sel3i(int a0, int a1, int a2, int k) {
-  return k == 0 ? a0 : (k == 1 ? a1 : a2);
-}
-__device__ __forceinline__ float sel3f(float a0, float a1, float a2, int k) {
-  return k == 0 ? a0 : (k == 1 ? a1 : a2);
-}
 
 template <int M>
-__global__ void __launch_bounds__(256, 4) k_candidates(Dev d, PState b) {
+__global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, PState b) {
   using T = Tr<M>;
   using PR = typename T::PR;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -683,53 +691,59 @@ __global__ void __launch_bounds__(256, 4) k_candidates(Dev d, PState b) {
   const BoxDev& B = d.boxes[d.slot_box[i]];
   if (i - B.pbase >= B.nlive) {
     d.ocnt[i] = 0;
-    d.icnt[i] = 0;
     if (d.cnt2) d.cnt2[i] = 0ull;
     return;
   }
   const PR* __restrict__ posr = (const PR*)b.posr;
   const int2* __restrict__ crange = d.crange;
   const float* __restrict__ cellr = d.cellr;
-  const int* __restrict__ ids = b.id;
   const PR pi = ld4(posr + i);
-  const int idi = ids[i];
-  const int n0 = B.n[0], n1 = B.n[1], lb = B.lin_base;
   int c[3];
   unpack_cell(b.cellc[i], c[0], c[1], c[2]);
-  // per axis and step (-1, 0, +1): neighbour cell (-1 = outside an open
-  // box), fixed-rule shift, squared gap from the particle to that cell
-  int nc[3][3];
-  float sh[3][3], g2[3][3];
+  // gaps from the particle to the lower and upper neighbour cell per axis
+  float glo[3], ghi[3];
+  unsigned valid = 0u;  // bit 3a+st: step st-1 along axis a exists
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float o, hc = c[a] == B.n[a] - 1 ? B.hcell[a][1] : B.hcell[a][0];
     if (M == kMIXED) o = (float)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z);
     else o = (float)((double)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z) - (double)c[a] * B.h[a]);
-    const float gl = fmaxf(o, 0.0f), gh = fmaxf(hc - o, 0.0f);
-#pragma unroll
-    for (int st = 0; st < 3; ++st) {
-      int cn;
-      float shift = 0.0f;
-      nc[a][st] = axis_step(B, a, c[a], st - 1, cn, shift) ? cn : -1;
-      sh[a][st] = shift;
-      const float g = st == 0 ? gl : (st == 2 ? gh : 0.0f);
-      g2[a][st] = g * g;
-    }
+    glo[a] = fmaxf(o, 0.0f);
+    ghi[a] = fmaxf(hc - o, 0.0f);
+    const bool per = B.periodic[a] != 0;
+    valid |= (per || c[a] > 0 ? 1u : 0u) << (3 * a);
+    valid |= 1u << (3 * a + 1);
+    valid |= (per || c[a] < B.n[a] - 1 ? 1u : 0u) << (3 * a + 2);
   }
+  auto gap2 = [&](int a, int st) -> float {
+    const float g = st == 0 ? glo[a] : (st == 2 ? ghi[a] : 0.0f);
+    return g * g;
+  };
   const float ri = (float)pi.w;
+  // Pass 1: a neighbour cell is kept when it holds particles and its nearest
+  // point lies within r_i plus the largest radius in it (0.1 % margin); the
+  // box's largest radius screens cells by arithmetic before any load, and the
+  // loads left are independent of one another.
+  const float rb = 1.001f * (ri + B.rmax_f);
+  const float rb2 = rb * rb;
   unsigned keep = 0u;
 #pragma unroll
-  for (int k = 0; k < 27; ++k) {
+  for (int k = 13; k < 27; ++k) {
     const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
-    if (nc[2][kz] < 0 || nc[1][ky] < 0 || nc[0][kx] < 0) continue;
-    const int lin = lb + (nc[2][kz] * n1 + nc[1][ky]) * n0 + nc[0][kx];
-    const float cr = __ldg(cellr + lin);  // < 0: empty cell
-    const float reach = 1.001f * (ri + cr);
-    if (cr >= 0.0f && g2[2][kz] + g2[1][ky] + g2[0][kx] <= reach * reach) keep |= 1u << k;
+    const float g2 = gap2(2, kz) + gap2(1, ky) + gap2(0, kx);
+    if (((valid >> (6 + kz)) & (valid >> (3 + ky)) & (valid >> kx) & 1u) && g2 <= rb2) {
+      const int cz = wrap_cell(c[2] + kz - 1, B.n[2]);
+      const int cy = wrap_cell(c[1] + ky - 1, B.n[1]);
+      const int cx = wrap_cell(c[0] + kx - 1, B.n[0]);
+      const float cr = __ldg(cellr + B.lin_base + (cz * B.n[1] + cy) * B.n[0] + cx);
+      const float reach = 1.001f * (ri + cr);  // cr < 0: empty cell
+      if (cr >= 0.0f && g2 <= reach * reach) keep |= 1u << k;
+    }
   }
-  int own = 0, inc = 0;
+  int own = 0;
   const int K = d.K;
   int* rowp = d.row + (size_t)i * K;
+  unsigned long long* cnt2 = d.cnt2;
   bool over = false;
   // Pass 2, warp-uniform: each iteration every lane tests its next four
   // candidates, first moving on to its next kept cell when the current one is
@@ -743,15 +757,13 @@ __global__ void __launch_bounds__(256, 4) k_candidates(Dev d, PState b) {
       const int k = __ffs(keep) - 1;
       keep &= keep - 1u;
       const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
-      const int cz = sel3i(nc[2][0], nc[2][1], nc[2][2], kz);
-      const int cy = sel3i(nc[1][0], nc[1][1], nc[1][2], ky);
-      const int cx = sel3i(nc[0][0], nc[0][1], nc[0][2], kx);
-      sz = sel3f(sh[2][0], sh[2][1], sh[2][2], kz);
-      sy = sel3f(sh[1][0], sh[1][1], sh[1][2], ky);
-      sx = sel3f(sh[0][0], sh[0][1], sh[0][2], kx);
-      const int2 rg = __ldg(crange + lb + (cz * n1 + cy) * n0 + cx);
-      j = rg.x;
-      e = rg.x + rg.y;
+      int cz, cy, cx;
+      axis_step(B, 2, c[2], kz - 1, cz, sz);
+      axis_step(B, 1, c[1], ky - 1, cy, sy);
+      axis_step(B, 0, c[0], kx - 1, cx, sx);
+      const int2 cr = __ldg(crange + B.lin_base + (cz * B.n[1] + cy) * B.n[0] + cx);
+      j = k == 13 ? i + 1 : cr.x;  // own cell: later slots only
+      e = cr.x + cr.y;
     }
     if (j < e) {
       const int m = e - j;
@@ -774,13 +786,12 @@ __global__ void __launch_bounds__(256, 4) k_candidates(Dev d, PState b) {
       while (hm) {
         const int jj = j + __ffs(hm) - 1;
         hm &= hm - 1u;
-        if (jj == i) continue;
-        if (own + inc >= K) {
+        if (own >= K) {
           over = true;
-        } else if (ids[jj] > idi) {
-          rowp[own++] = jj;
         } else {
-          rowp[K - 1 - inc++] = jj;
+          unsigned pos = 0u;
+          if (cnt2) pos = (unsigned)(atomicAdd(cnt2 + jj, 1ull << 32) >> 32);
+          rowp[own++] = jj | (int)(min(pos, 127u) << 24);
         }
       }
       j += 4;
@@ -789,29 +800,36 @@ __global__ void __launch_bounds__(256, 4) k_candidates(Dev d, PState b) {
   }
   if (over) flag(d.status, kStRowOverflow);
   d.ocnt[i] = own;
-  d.icnt[i] = inc;
-  if (d.cnt2) d.cnt2[i] = (unsigned long long)own | ((unsigned long long)inc << 32);
+  if (cnt2) atomicAdd(cnt2 + i, (unsigned long long)own);
 }
 
-// owned counts -> first list entry of each slot
+// found counts -> first list entry of each slot
 struct StartEpi {
   int* hstart;
   __device__ void operator()(int i, int, int pre) const { hstart[i] = pre; }
 };
 
-// packed (owned, incoming) counts -> first entries of each slot in the
-// contact list and in the incoming list
+// packed (found, incoming) counts -> first entries of each slot in the
+// contact list and in the incoming list, the incoming count, and the check
+// that a particle's contacts fit its row capacity
 struct HstartEpi {
   int* hstart;
   int* istart;
-  __device__ void operator()(int i, unsigned long long, unsigned long long pre) const {
+  int* icnt;
+  unsigned* status;
+  int K;
+  __device__ void operator()(int i, unsigned long long v, unsigned long long pre) const {
     hstart[i] = (int)(pre & 0xffffffffull);
     istart[i] = (int)(pre >> 32);
+    const int own = (int)(v & 0xffffffffull), inc = (int)(v >> 32);
+    icnt[i] = inc;
+    if (own + inc > K) flag(status, kStRowOverflow);
   }
 };
 
-// dense contact list: each live slot writes its owned pairs at its prefix
-// and its entry of the by-id history index
+// dense contact list: each live slot writes the pairs it found at its
+// prefix, oriented (lower id, higher id), its entry of the by-id history
+// index, and each contact's index into the partner's incoming list
 __global__ void k_compact(Dev d, PState b, CList cn) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
@@ -825,9 +843,18 @@ __global__ void k_compact(Dev d, PState b, CList cn) {
   cn.rc[idi] = n;
   const int* rowp = d.row + (size_t)i * d.K;
   for (int k = 0; k < n; ++k) {
-    int j = rowp[k];
-    cn.pair[pre + k] = make_int2(i, j);
-    cn.hid[pre + k] = make_int2(idi, b.id[j]);
+    const int w = rowp[k];
+    const int j = w & 0xffffff, pos = (w >> 24) & 127;
+    const int idj = b.id[j];
+    const int c = pre + k;
+    cn.pair[c] = idi < idj ? make_int2(i, j) : make_int2(j, i);
+    cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
+    if (d.inlist) {
+      // positions past 126 only occur with more than 127 contacts on one
+      // particle, which the row capacity check has already reported
+      const int at = d.istart[j] + pos;
+      if (pos < 127 && at < d.Cmax) d.inlist[at] = c;
+    }
   }
 }
 
@@ -1002,13 +1029,30 @@ __device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
   const P* __restrict__ pz = (const P*)b.pz;
   const V4* __restrict__ vel = (const V4*)b.vel;
   const V4* __restrict__ omg = (const V4*)b.omg;
-  // history of this pair from the previous step's list
-  int os = co.rs[idlo], on = co.rc[idlo], found = -1;
-  for (int k = 0; k < on; ++k)
-    if (co.hid[os + k].y == idhi) {
-      found = os + k;
-      break;
+  // history of this pair from the previous step's list: a pair is listed in
+  // the block of the particle that found it, which may be either of the two
+  int found = -1;
+  {
+    int os = co.rs[idlo], on = co.rc[idlo];
+    for (int k = 0; k < on; ++k) {
+      const int2 h = co.hid[os + k];
+      if (h.x == idlo && h.y == idhi) {
+        found = os + k;
+        break;
+      }
     }
+    if (found < 0) {
+      os = co.rs[idhi];
+      on = co.rc[idhi];
+      for (int k = 0; k < on; ++k) {
+        const int2 h = co.hid[os + k];
+        if (h.x == idlo && h.y == idhi) {
+          found = os + k;
+          break;
+        }
+      }
+    }
+  }
   V4 v1 = ld4(vel + i), v2 = ld4(vel + j);
   V4 w1 = ld4(omg + i), w2 = ld4(omg + j);
   R r1 = w1.w, r2 = w2.w;
@@ -1145,27 +1189,6 @@ k_force(Dev d, PState b, CList co, CList cn) {
     ((DT*)cn.dz)[c] = o.nz;
     st4((V4*)d.Fc + c, o.F4);
     st4((V4*)d.nFc + c, o.N4);
-    if (d.Fin) {
-      // the same contact in the incoming list of the higher-id particle j,
-      // at the position of i among j's incoming partners
-      const int nin = d.icnt[j];
-      const int* rowj = d.row + (size_t)j * d.K + (d.K - 1);
-      int pos = -1;
-      for (int q = 0; q < nin; ++q)
-        if (rowj[-q] == i) {
-          pos = q;
-          break;
-        }
-      if (pos < 0) {
-        flag(d.status, kStInconsistent);
-      } else {
-        const int at = d.istart[j] + pos;
-        if (at < d.Cmax) {
-          st4((V4*)d.Fin + at, o.F4);
-          st4((V4*)d.nFin + at, o.N4);
-        }
-      }
-    }
     if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
   }
   flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
@@ -1274,7 +1297,7 @@ k_collide_fused(Dev d, PState b, CList co, CList cn, int ko) {
 // then binning for the next step
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void k_gather_integrate(Dev d, PState b, int store_ft) {
+__global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
   using T = Tr<M>;
   using P = typename T::P;
   using R = typename T::R;
@@ -1289,40 +1312,38 @@ __global__ void k_gather_integrate(Dev d, PState b, int store_ft) {
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
   const bool fused = d.Ffused != nullptr;
   int own = fused ? 0 : d.ocnt[i], hs = fused ? 0 : d.hstart[i], inc = fused ? 0 : d.icnt[i];
+  // Fc is the force on the pair's lower-id member: added when this slot is
+  // that member, subtracted otherwise; n x F enters with the same sign for
+  // both.  Found contacts are summed in list order, incoming ones in
+  // increasing contact index (the order their positions were taken in is
+  // not reproducible; this one is).
   for (int k = 0; k < own; ++k) {
-    if (hs + k >= d.Cmax) break;
-    V4 f = ld4(Fc + hs + k), q = ld4(nFc + hs + k);
-    F = F + xyz(f);
+    const int c = hs + k;
+    if (c >= d.Cmax) break;
+    const V4 f = ld4(Fc + c), q = ld4(nFc + c);
+    if (cn.pair[c].x == i) F = F + xyz(f);
+    else F = F - xyz(f);
     Ns = Ns + xyz(q);
   }
-  if (d.Fin) {
-    const V4* Fin = (const V4*)d.Fin;
-    const V4* nFin = (const V4*)d.nFin;
+  if (inc > 0) {
     const int is = d.istart[i];
-    for (int k = 0; k < inc; ++k) {
-      if (is + k >= d.Cmax) break;
-      V4 f = ld4(Fin + is + k), q = ld4(nFin + is + k);
-      F = F - xyz(f);
-      Ns = Ns + xyz(q);
-    }
-  } else {
-    const int K = d.K;
-    const int* rowi = d.row + (size_t)i * K;
-    for (int k = 0; k < inc; ++k) {
-      int j = rowi[K - 1 - k];
-      int oj = d.ocnt[j], hj = d.hstart[j], c = -1;
-      const int* rowj = d.row + (size_t)j * K;
-      for (int q = 0; q < oj; ++q)
-        if (rowj[q] == i) {
-          c = hj + q;
-          break;
-        }
-      if (c < 0 || c >= d.Cmax) {
-        flag(d.status, kStInconsistent);
-        continue;
+    const int n = min(inc, d.Cmax - is);
+    const int* il = d.inlist + is;
+    int prev = -1;
+    for (int t = 0; t < n; ++t) {
+      int c = 0x7fffffff;
+      for (int q = 0; q < n; ++q) {
+        const int v = il[q];
+        if (v > prev && v < c) c = v;
       }
-      V4 f = ld4(Fc + c), q = ld4(nFc + c);
-      F = F - xyz(f);
+      if (c >= d.Cmax) {
+        flag(d.status, kStInconsistent);
+        break;
+      }
+      prev = c;
+      const V4 f = ld4(Fc + c), q = ld4(nFc + c);
+      if (cn.pair[c].x == i) F = F + xyz(f);
+      else F = F - xyz(f);
       Ns = Ns + xyz(q);
     }
   }
