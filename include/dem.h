@@ -116,8 +116,7 @@ typedef struct {
   int32_t collide;            /* dem_collide                                */
   int32_t kn_literal;         /* 1 = k_n with the printed (2 - sigma^2)/E    */
                               /* term of Sec. 2 instead of Hertz 1 - sigma^2 */
-  int32_t row_capacity;       /* max contacts of one particle, 2..126;      */
-                              /* 0 = 32                                     */
+  int32_t row_capacity;       /* max contacts of one particle; 0 = 32       */
   int32_t graph_steps;        /* steps per captured CUDA graph; 0 = 16,     */
                               /* -1 = launch kernels directly              */
   int32_t block;              /* threads per block of per-particle kernels; */

@@ -292,7 +292,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     }
     return s;
   };
-  if (ctx->K < 2 || ctx->K > 126) return bail(DEM_ERR_ARG, "row_capacity out of range [2, 126]");
+  if (ctx->K < 2 || ctx->K > 1024) return bail(DEM_ERR_ARG, "row_capacity out of range");
   if (ctx->block < 32 || ctx->block > 1024 || (ctx->block & 31))
     return bail(DEM_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
   if (cudaGetDevice(&ctx->device) != cudaSuccess)

@@ -90,7 +90,7 @@ struct Dev {
   int2* crange;  // per linear cell: (first slot, count)
   float* cellr;  // per linear cell: largest radius in the cell (-1 if empty)
   int* perm;     // new slot -> old slot
-  int* row;      // N x K: partners a slot found (slot | incoming position << 24)
+  int* row;      // N x K: partner slots a slot found
   int* ocnt;     // contacts a slot found (half stencil)
   int* icnt;     // contacts in which a slot was found by its partner
   int* hstart;   // first list entry of a slot's found contacts
@@ -650,17 +650,17 @@ __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
                                           int& cn, float& shift) {
   const int n = B.n[a];
   cn = c + s;
-  long long image = 0;
+  int k = s + 1;  // fixed-rule shift (cn - c) H + image L, tabulated per box
   if (cn < 0) {
     if (!B.periodic[a]) return false;
     cn += n;
-    image = -1;
+    k = 3;
   } else if (cn >= n) {
     if (!B.periodic[a]) return false;
     cn -= n;
-    image = 1;
+    k = 4;
   }
-  shift = __fmul_rn(i64_to_f32_rn((long long)(cn - c) * B.Hq[a] + image * B.Lq[a]), kQ);
+  shift = B.shift[a][k];
   return true;
 }
 
@@ -671,10 +671,9 @@ __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
 // least 3 cells on every periodic axis each pair of distinct cells is then
 // one step apart in exactly one direction, and the predicate is exactly
 // antisymmetric, so the pairs found are the pairs of the full stencil.
-// Found partners go into the particle's row; each found pair also takes the
-// next position in the partner's incoming count (a 64-bit atomic add on the
-// packed counts; the order of those positions is fixed later, when the
-// incoming list is summed in contact-index order).
+// Found partners go into the particle's row; each found pair also adds one
+// to the partner's incoming count (a 64-bit atomic add on the packed counts
+// whose result is not used, so the search never waits for it).
 // Pass 1 decides, with independent loads, which neighbour cells can hold a
 // contact: a cell is skipped when its nearest point is farther than r_i plus
 // the largest radius in that cell (0.1 % margin, far above rounding).
@@ -700,25 +699,34 @@ __global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, P
   const PR pi = ld4(posr + i);
   int c[3];
   unpack_cell(b.cellc[i], c[0], c[1], c[2]);
-  // gaps from the particle to the lower and upper neighbour cell per axis
-  float glo[3], ghi[3];
-  unsigned valid = 0u;  // bit 3a+st: step st-1 along axis a exists
+  // Per axis: squared gaps from the particle to the lower and upper
+  // neighbour cell, the neighbour cells' offsets in the linear cell index
+  // and their fixed-rule shifts (only the steps the half stencil takes:
+  // z 0/+1, y and x -1/0/+1); invalid steps (out of an open box) clear bits
+  // of 'valid' (bit 3a + st for step st - 1 along axis a).
+  float g2lo[3], g2hi[3];
+  unsigned valid = 0u;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float o, hc = c[a] == B.n[a] - 1 ? B.hcell[a][1] : B.hcell[a][0];
     if (M == kMIXED) o = (float)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z);
     else o = (float)((double)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z) - (double)c[a] * B.h[a]);
-    glo[a] = fmaxf(o, 0.0f);
-    ghi[a] = fmaxf(hc - o, 0.0f);
+    const float gl = fmaxf(o, 0.0f), gh = fmaxf(hc - o, 0.0f);
+    g2lo[a] = gl * gl;
+    g2hi[a] = gh * gh;
     const bool per = B.periodic[a] != 0;
     valid |= (per || c[a] > 0 ? 1u : 0u) << (3 * a);
     valid |= 1u << (3 * a + 1);
     valid |= (per || c[a] < B.n[a] - 1 ? 1u : 0u) << (3 * a + 2);
   }
-  auto gap2 = [&](int a, int st) -> float {
-    const float g = st == 0 ? glo[a] : (st == 2 ? ghi[a] : 0.0f);
-    return g * g;
-  };
+  const int n0 = B.n[0], n01 = B.n[0] * B.n[1];
+  const bool xw0 = c[0] == 0, xw2 = c[0] == B.n[0] - 1;
+  const bool yw0 = c[1] == 0, yw2 = c[1] == B.n[1] - 1;
+  const bool zw2 = c[2] == B.n[2] - 1;
+  const int X0 = xw0 ? B.n[0] - 1 : c[0] - 1, X1 = c[0], X2 = xw2 ? 0 : c[0] + 1;
+  const int Y0 = (yw0 ? B.n[1] - 1 : c[1] - 1) * n0, Y1 = c[1] * n0,
+            Y2 = (yw2 ? 0 : c[1] + 1) * n0;
+  const int Z1 = B.lin_base + c[2] * n01, Z2 = B.lin_base + (zw2 ? 0 : c[2] + 1) * n01;
   const float ri = (float)pi.w;
   // Pass 1: a neighbour cell is kept when it holds particles and its nearest
   // point lies within r_i plus the largest radius in it (0.1 % margin); the
@@ -730,12 +738,12 @@ __global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, P
 #pragma unroll
   for (int k = 13; k < 27; ++k) {
     const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
-    const float g2 = gap2(2, kz) + gap2(1, ky) + gap2(0, kx);
+    const float g2 = (kz == 2 ? g2hi[2] : 0.0f) + (ky == 0 ? g2lo[1] : ky == 2 ? g2hi[1] : 0.0f) +
+                     (kx == 0 ? g2lo[0] : kx == 2 ? g2hi[0] : 0.0f);
     if (((valid >> (6 + kz)) & (valid >> (3 + ky)) & (valid >> kx) & 1u) && g2 <= rb2) {
-      const int cz = wrap_cell(c[2] + kz - 1, B.n[2]);
-      const int cy = wrap_cell(c[1] + ky - 1, B.n[1]);
-      const int cx = wrap_cell(c[0] + kx - 1, B.n[0]);
-      const float cr = __ldg(cellr + B.lin_base + (cz * B.n[1] + cy) * B.n[0] + cx);
+      const int lin = (kz == 2 ? Z2 : Z1) + (ky == 0 ? Y0 : ky == 1 ? Y1 : Y2) +
+                      (kx == 0 ? X0 : kx == 1 ? X1 : X2);
+      const float cr = __ldg(cellr + lin);
       const float reach = 1.001f * (ri + cr);  // cr < 0: empty cell
       if (cr >= 0.0f && g2 <= reach * reach) keep |= 1u << k;
     }
@@ -756,14 +764,18 @@ __global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, P
     if (j >= e && keep != 0u) {
       const int k = __ffs(keep) - 1;
       keep &= keep - 1u;
-      const int kz = k / 9, ky = (k / 3) % 3, kx = k % 3;
-      int cz, cy, cx;
-      axis_step(B, 2, c[2], kz - 1, cz, sz);
-      axis_step(B, 1, c[1], ky - 1, cy, sy);
-      axis_step(B, 0, c[0], kx - 1, cx, sx);
-      const int2 cr = __ldg(crange + B.lin_base + (cz * B.n[1] + cy) * B.n[0] + cx);
+      const int kz = k >= 18 ? 2 : 1, r9 = k - 9 * kz;
+      const int ky = r9 >= 6 ? 2 : (r9 >= 3 ? 1 : 0), kx = r9 - 3 * ky;
+      const int lin = (kz == 2 ? Z2 : Z1) + (ky == 0 ? Y0 : ky == 1 ? Y1 : Y2) +
+                      (kx == 0 ? X0 : kx == 1 ? X1 : X2);
+      const int2 cr = __ldg(crange + lin);
       j = k == 13 ? i + 1 : cr.x;  // own cell: later slots only
       e = cr.x + cr.y;
+      if (M == kMIXED) {
+        sz = kz == 2 ? B.shift[2][zw2 ? 4 : 2] : 0.0f;
+        sy = ky == 1 ? 0.0f : (ky == 0 ? B.shift[1][yw0 ? 3 : 0] : B.shift[1][yw2 ? 4 : 2]);
+        sx = kx == 1 ? 0.0f : (kx == 0 ? B.shift[0][xw0 ? 3 : 0] : B.shift[0][xw2 ? 4 : 2]);
+      }
     }
     if (j < e) {
       const int m = e - j;
@@ -789,9 +801,8 @@ __global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, P
         if (own >= K) {
           over = true;
         } else {
-          unsigned pos = 0u;
-          if (cnt2) pos = (unsigned)(atomicAdd(cnt2 + jj, 1ull << 32) >> 32);
-          rowp[own++] = jj | (int)(min(pos, 127u) << 24);
+          if (cnt2) atomicAdd(cnt2 + jj, 1ull << 32);
+          rowp[own++] = jj;
         }
       }
       j += 4;
@@ -829,7 +840,10 @@ struct HstartEpi {
 
 // dense contact list: each live slot writes the pairs it found at its
 // prefix, oriented (lower id, higher id), its entry of the by-id history
-// index, and each contact's index into the partner's incoming list
+// index, and each contact's index into the partner's incoming list.  The
+// position in that list is taken by counting the partner's incoming count
+// (already scanned) back down to zero, so positions 0 .. inc-1 are each
+// taken once, in an order that the gather does not depend on.
 __global__ void k_compact(Dev d, PState b, CList cn) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
@@ -843,17 +857,17 @@ __global__ void k_compact(Dev d, PState b, CList cn) {
   cn.rc[idi] = n;
   const int* rowp = d.row + (size_t)i * d.K;
   for (int k = 0; k < n; ++k) {
-    const int w = rowp[k];
-    const int j = w & 0xffffff, pos = (w >> 24) & 127;
+    const int j = rowp[k];
     const int idj = b.id[j];
     const int c = pre + k;
     cn.pair[c] = idi < idj ? make_int2(i, j) : make_int2(j, i);
     cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
     if (d.inlist) {
-      // positions past 126 only occur with more than 127 contacts on one
-      // particle, which the row capacity check has already reported
+      const unsigned long long old =
+          atomicAdd(d.cnt2 + j, 0ull - (1ull << 32));  // incoming count - 1
+      const int pos = (int)(old >> 32) - 1;
       const int at = d.istart[j] + pos;
-      if (pos < 127 && at < d.Cmax) d.inlist[at] = c;
+      if (pos >= 0 && at < d.Cmax) d.inlist[at] = c;
     }
   }
 }
