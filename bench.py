@@ -171,7 +171,7 @@ def search_tests(box, ncell):
 
 SEARCH_OPS_PER_TEST = 14  # FP32 instructions of the contact predicate
 PHASES = ["sort", "search", "compact", "force", "integrate"]
-PHASE_KERNELS = {"sort": 6, "search": 1, "compact": 3, "force": 1, "integrate": 1}
+PHASE_KERNELS = {"sort": 5, "search": 1, "compact": 3, "force": 1, "integrate": 1}
 
 
 def _torch_setup(args):

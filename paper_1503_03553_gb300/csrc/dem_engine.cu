@@ -129,7 +129,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
   return spread(x) | (spread(y) << 1) | (spread(z) << 2);
 }
 
-int launches_per_step(const dem_ctx* ctx) { return ctx->fused ? 8 : 13; }
+int launches_per_step(const dem_ctx* ctx) { return ctx->fused ? 7 : 12; }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -156,10 +156,9 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
                                            d.status, 0u);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(
       d.ccount, d.M_rank, d.scan_bsum,
-      CellEpi{d.cstart, d.crange, d.lin_of_rank});
+      CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank});
   // 2. counting sort by (Morton cell, id) and reorder into parity q
   k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
-  k_cellsort<M><<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ctx->ps[p]);
   k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q]);
   if (tm) cudaEventRecord(ev[1], s);
   if (ctx->fused) {
@@ -444,6 +443,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.crange = (int2*)A(sizeof(int2) * std::max(1, ctx->M_lin));
   d.cellr = (float*)A(sizeof(float) * std::max(1, ctx->M_lin));
   d.perm = (int*)A(sizeof(int) * n);
+  d.pcell = (int*)A(sizeof(int) * n);
   d.row = (int*)A(sizeof(int) * n * ctx->K);
   d.ocnt = (int*)A(sizeof(int) * n);
   d.icnt = (int*)A(sizeof(int) * n);
@@ -1138,7 +1138,7 @@ constexpr int kStaticK = 32;
 
 // layout of the scratch array (every part 256-byte aligned)
 struct StaticLayout {
-  size_t box, slot_box, rol, lor, ccount, cstart, crange, cellr, perm, row, ocnt,
+  size_t box, slot_box, rol, lor, ccount, cstart, crange, cellr, perm, pcell, row, ocnt,
       icnt, hstart, bsum, status, count, pair, rs, rc, state[2][10], total;
 };
 
@@ -1162,6 +1162,7 @@ StaticLayout static_layout() {
   L.crange = take(8 * M);
   L.cellr = take(4 * M);
   L.perm = take(4 * N);
+  L.pcell = take(4 * N);
   L.row = take(4 * N * kStaticK);
   L.ocnt = take(4 * N);
   L.icnt = take(4 * N);
@@ -1310,6 +1311,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   d.crange = (int2*)(base + lay.crange);
   d.cellr = (float*)(base + lay.cellr);
   d.perm = (int*)(base + lay.perm);
+  d.pcell = (int*)(base + lay.pcell);
   d.row = (int*)(base + lay.row);
   d.ocnt = (int*)(base + lay.ocnt);
   d.icnt = (int*)(base + lay.icnt);
@@ -1352,9 +1354,8 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
   k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum,
-                                            CellEpi{d.cstart, d.crange, d.lin_of_rank});
+                                            CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank});
   k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
-  k_cellsort<kMIXED><<<blocks_for(d.M_lin, 128), 128, 0, s>>>(d, ps[0]);
   k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1]);
   k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1]);
   int nbr = blocks_for(N, kScanTile);

@@ -89,7 +89,8 @@ struct Dev {
   int* cstart;   // per rank cell: first slot
   int2* crange;  // per linear cell: (first slot, count)
   float* cellr;  // per linear cell: largest radius in the cell (-1 if empty)
-  int* perm;     // new slot -> old slot
+  int* perm;     // scatter position -> old slot (cell order, not yet by id)
+  int* pcell;    // scatter position -> linear cell
   int* row;      // N x K: partner slots a slot found
   int* ocnt;     // contacts a slot found (half stencil)
   int* icnt;     // contacts in which a slot was found by its partner
@@ -467,16 +468,21 @@ k_scan_apply(const T* __restrict__ in, int n, const T* __restrict__ bsum,
 struct CellEpi {
   int* cstart;
   int2* crange;
+  float* cellr;  // reset to -1 (empty); the reorder raises it to the largest radius
   const int* lin_of_rank;
   __device__ void operator()(int g, int cnt, int pre) const {
     cstart[g] = pre;
     int lin = lin_of_rank[g];
-    if (lin >= 0) crange[lin] = make_int2(pre, cnt);
+    if (lin >= 0) {
+      crange[lin] = make_int2(pre, cnt);
+      if (cellr) cellr[lin] = -1.0f;
+    }
   }
 };
 
 // ---------------------------------------------------------------------------
-// counting sort: scatter then order each cell by id
+// counting sort, pass 1: each particle takes a position in its cell's range
+// (in atomic order) and records its old slot and its cell there
 // ---------------------------------------------------------------------------
 __global__ void k_scatter(Dev d, PState a) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -491,54 +497,15 @@ __global__ void k_scatter(Dev d, PState a) {
     return;
   }
   d.perm[pos] = s;
-}
-
-// Insertion sort of each cell's segment of perm by particle id: the slot
-// order is (Morton rank of the cell, id), independent of atomic timing.
-template <int M>
-__global__ void k_cellsort(Dev d, PState a) {
-  using V4 = typename Tr<M>::V4;
-  int l = blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= d.M_lin) return;
-  const int2 r = d.crange[l];
-  int* seg = d.perm + r.x;
-  const V4* omg = (const V4*)a.omg;
-  float rmax = r.y > 0 ? 0.0f : -1.0f;  // -1 marks an empty cell
-  constexpr int kLocal = 24;
-  if (r.y <= kLocal) {
-    int sl[kLocal], key[kLocal];
-    for (int q = 0; q < r.y; ++q) {
-      sl[q] = seg[q];
-      key[q] = a.id[sl[q]];
-      rmax = fmaxf(rmax, (float)omg[sl[q]].w);
-    }
-    for (int q = 1; q < r.y; ++q) {
-      int ks = key[q], ss = sl[q], p = q - 1;
-      while (p >= 0 && key[p] > ks) {
-        key[p + 1] = key[p];
-        sl[p + 1] = sl[p];
-        --p;
-      }
-      key[p + 1] = ks;
-      sl[p + 1] = ss;
-    }
-    for (int q = 0; q < r.y; ++q) seg[q] = sl[q];
-  } else {
-    for (int q = 0; q < r.y; ++q) rmax = fmaxf(rmax, (float)omg[seg[q]].w);
-    for (int q = 1; q < r.y; ++q) {
-      int ss = seg[q], ks = a.id[ss], p = q - 1;
-      while (p >= 0 && a.id[seg[p]] > ks) {
-        seg[p + 1] = seg[p];
-        --p;
-      }
-      seg[p + 1] = ss;
-    }
-  }
-  if (d.cellr) d.cellr[l] = rmax;
+  d.pcell[pos] = d.lin_of_rank[g];
 }
 
 // ---------------------------------------------------------------------------
-// reorder the state into sorted slots; build the predicate record
+// counting sort, pass 2: each particle's final slot is its cell's start plus
+// the number of cell-mates with a smaller id, so the slot order is (Morton
+// rank of the cell, id) whatever the atomic order of pass 1; the state moves
+// there, the predicate record is built, and the cell's largest radius is
+// raised to the particle's (positive floats order like their bit patterns)
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void k_reorder(Dev d, PState a, PState b) {
@@ -546,11 +513,18 @@ __global__ void k_reorder(Dev d, PState a, PState b) {
   using P = typename T::P;
   using V4 = typename T::V4;
   using PR = typename T::PR;
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= d.N) return;
-  const BoxDev& B = d.boxes[d.slot_box[t]];
-  if (t - B.pbase >= B.nlive) return;
-  int s = d.perm[t];
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;  // scatter position
+  if (q >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[q]];
+  if (q - B.pbase >= B.nlive) return;
+  if (d.cnt2) d.cnt2[q] = 0ull;  // the search accumulates into it
+  const int s = d.perm[q];
+  const int lin = d.pcell[q];
+  const int2 rg = d.crange[lin];
+  const int key = a.id[s];
+  int rank = 0;
+  for (int u = rg.x; u < rg.x + rg.y; ++u) rank += a.id[d.perm[u]] < key ? 1 : 0;
+  const int t = rg.x + rank;  // final slot
   P x = ((const P*)a.px)[s], y = ((const P*)a.py)[s], z = ((const P*)a.pz)[s];
   ((P*)b.px)[t] = x;
   ((P*)b.py)[t] = y;
@@ -559,8 +533,7 @@ __global__ void k_reorder(Dev d, PState a, PState b) {
   V4 om = ld4((const V4*)a.omg + s);
   st4((V4*)b.vel + t, vel);
   st4((V4*)b.omg + t, om);
-  b.id[t] = a.id[s];
-  if (d.cnt2) d.cnt2[t] = 0ull;  // the search accumulates into it
+  b.id[t] = key;
   int cc = a.cellx[s];
   b.cellc[t] = cc;
   if (a.wx) {
@@ -584,6 +557,7 @@ __global__ void k_reorder(Dev d, PState a, PState b) {
   }
   pr.w = om.w;
   st4((PR*)b.posr + t, pr);
+  if (d.cellr) atomicMax((int*)d.cellr + lin, __float_as_int((float)om.w));
 }
 
 // ---------------------------------------------------------------------------
