@@ -129,7 +129,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
   return spread(x) | (spread(y) << 1) | (spread(z) << 2);
 }
 
-int launches_per_step(const dem_ctx* ctx) { return ctx->fused ? 7 : 12; }
+int launches_per_step(const dem_ctx* ctx) { return ctx->fused ? 7 : 8; }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -159,7 +159,8 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
       CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank});
   // 2. counting sort by (Morton cell, id) and reorder into parity q
   k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
-  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q]);
+  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q],
+                                                  ctx->fused ? nullptr : ctx->cl[q].count);
   if (tm) cudaEventRecord(ev[1], s);
   if (ctx->fused) {
     // Algorithm 1: search and force in one pass, no contact list
@@ -175,21 +176,14 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
     if (tm) cudaEventRecord(ev[5], s);
     return;
   }
-  // 3. contact search into per-particle rows
+  // 3. contact search and dense contact list
   // the search kernel is compiled for at most 256 threads per block
   const int bs_search = bs < 256 ? bs : 256;
-  k_candidates<M><<<blocks_for(d.N, bs_search), bs_search, 0, s>>>(d, ctx->ps[q]);
-  if (tm) cudaEventRecord(ev[2], s);
-  // 4. owned counts -> dense contact list
-  int nbr = blocks_for(d.N, kScanTile);
-  unsigned long long* bsum64 = (unsigned long long*)d.scan_bsum;
-  k_scan_reduce<<<nbr, kScanThreads, 0, s>>>(d.cnt2, d.N, bsum64);
-  k_scan_top<<<1, kScanTopThreads, 0, s>>>(bsum64, nbr, ctx->cl[q].count,
-                                           d.Cmax, d.status, kStListOverflow);
-  k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.cnt2, d.N, (const unsigned long long*)bsum64,
-                                            HstartEpi{d.hstart, d.istart, d.icnt, d.status, d.K});
-  k_compact<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
-  if (tm) cudaEventRecord(ev[3], s);
+  k_candidates<M><<<blocks_for(d.N, bs_search), bs_search, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
+  if (tm) {
+    cudaEventRecord(ev[2], s);
+    cudaEventRecord(ev[3], s);
+  }
   // 5. one thread per contact
   k_force<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[p], ctx->cl[q]);
   if (tm) cudaEventRecord(ev[4], s);
@@ -448,15 +442,13 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.ocnt = (int*)A(sizeof(int) * n);
   d.icnt = (int*)A(sizeof(int) * n);
   d.hstart = (int*)A(sizeof(int) * n);
-  d.istart = (int*)A(sizeof(int) * n);
-  d.cnt2 = (unsigned long long*)A(sizeof(unsigned long long) * n);
   d.Fc = A(v4_bytes(M) * ctx->Cmax);
   d.nFc = A(v4_bytes(M) * ctx->Cmax);
   if (ctx->fused) {
     d.Ffused = A(v4_bytes(M) * n);
     d.Tfused = A(v4_bytes(M) * n);
   } else {
-    d.inlist = (int*)A(sizeof(int) * ctx->Cmax);
+    d.inrow = (int*)A(sizeof(int) * n * ctx->K);
   }
   d.Fout = A(v4_bytes(M) * n);
   d.Tout = A(v4_bytes(M) * n);
@@ -1356,14 +1348,8 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum,
                                             CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank});
   k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
-  k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1]);
-  k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1]);
-  int nbr = blocks_for(N, kScanTile);
-  k_scan_reduce<<<nbr, kScanThreads, 0, s>>>(d.ocnt, N, d.scan_bsum);
-  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbr, cn.count, d.Cmax, d.status,
-                                           kStListOverflow);
-  k_scan_apply<<<nbr, kScanThreads, 0, s>>>(d.ocnt, N, d.scan_bsum, StartEpi{d.hstart});
-  k_compact<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);
+  k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1], cn.count);
+  k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);
   if ((st = ck(cudaGetLastError(), "launch"))) return st;
   int hcount = 0;
   unsigned hstatus = 0;
@@ -1372,7 +1358,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   if ((st = ck(cudaMemcpyAsync(&hstatus, d.status, 4, cudaMemcpyDeviceToHost, s), "status read")))
     return st;
   if ((st = ck(cudaStreamSynchronize(s), "synchronise"))) return st;
-  *count = hcount;
+  *count = std::min(hcount, d.Cmax);
   if (hstatus & 0x100u)
     return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: a radius exceeds half the cell edge");
   if (hstatus & kStNonFinite) return fail(ctx, DEM_ERR_NONFINITE, "dem_contacts_static: non-finite position");

@@ -5,9 +5,10 @@
 //   scan of cell counts        -> cell starts          (CalcHash/BitonicSort)
 //   k_scatter + k_cellsort     -> permutation by (Morton cell, id)
 //   k_reorder                  -> state in sorted order (FindCellBoundsAndReorder)
-//   k_candidates               -> per-particle contact rows (the loops of
-//                                 Algorithm 1; the paper's first loop, Sec. 3.4)
-//   scan of owned counts       -> dense contact list    (Sec. 3.4 split, global)
+//   k_candidates               -> contact search over half the neighbour cells
+//                                 (the loops of Algorithm 1; the paper's first
+//                                 loop, Sec. 3.4) and the dense contact list
+//                                 (Sec. 3.4 split, global)
 //   k_force                    -> one thread per contact: Eq. (1), Eq. (vt),
 //                                 Eq. (dt), Coulomb cap, history carry
 //                                 (InitializeContactIDs + Collide)
@@ -95,9 +96,8 @@ struct Dev {
   int* ocnt;     // contacts a slot found (half stencil)
   int* icnt;     // contacts in which a slot was found by its partner
   int* hstart;   // first list entry of a slot's found contacts
-  int* istart;   // first incoming-list entry of a slot
-  unsigned long long* cnt2;  // found | incoming << 32, per slot (scan input)
-  int* inlist;   // incoming list: contact indices, grouped by partner slot
+  int* inrow;    // N x K: list entries of the contacts in which a slot was
+                 // found by its partner (any order)
   void* Fc;      // V4 per contact: force on the lower-id particle
   void* nFc;     // V4 per contact: n x F
   void* Ffused;  // V4 per slot: contact force sum of the fused layout
@@ -508,16 +508,17 @@ __global__ void k_scatter(Dev d, PState a) {
 // raised to the particle's (positive floats order like their bit patterns)
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void k_reorder(Dev d, PState a, PState b) {
+__global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   using T = Tr<M>;
   using P = typename T::P;
   using V4 = typename T::V4;
   using PR = typename T::PR;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // scatter position
+  if (q == 0 && cursor) *cursor = 0;  // the search allocates list entries
   if (q >= d.N) return;
+  if (d.icnt) d.icnt[q] = 0;  // the search counts into it
   const BoxDev& B = d.boxes[d.slot_box[q]];
   if (q - B.pbase >= B.nlive) return;
-  if (d.cnt2) d.cnt2[q] = 0ull;  // the search accumulates into it
   const int s = d.perm[q];
   const int lin = d.pcell[q];
   const int2 rg = d.crange[lin];
@@ -645,9 +646,13 @@ __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
 // least 3 cells on every periodic axis each pair of distinct cells is then
 // one step apart in exactly one direction, and the predicate is exactly
 // antisymmetric, so the pairs found are the pairs of the full stencil.
-// Found partners go into the particle's row; each found pair also adds one
-// to the partner's incoming count (a 64-bit atomic add on the packed counts
-// whose result is not used, so the search never waits for it).
+// Found partners go into the particle's row.  The same kernel then writes
+// the dense contact list: each warp takes a block of list entries for all
+// its particles' contacts with one atomic add on the list length (the
+// warp's position in the list depends on timing, the content of every
+// entry does not) and a warp scan places each particle's contacts there.
+// Each contact's entry index also goes into the partner's incoming row, at
+// a position taken from the partner's incoming count.
 // Pass 1 decides, with independent loads, which neighbour cells can hold a
 // contact: a cell is skipped when its nearest point is farther than r_i plus
 // the largest radius in that cell (0.1 % margin, far above rounding).
@@ -655,18 +660,12 @@ __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
 // at a time so that four loads are in flight.
 // ---------------------------------------------------------------------------
 
+// the search of one live slot: partners into its row, returns how many
 template <int M>
-__global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, PState b) {
+__device__ __forceinline__ int search_row(const Dev& d, const PState& b, const BoxDev& B,
+                                          int i) {
   using T = Tr<M>;
   using PR = typename T::PR;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.N) return;
-  const BoxDev& B = d.boxes[d.slot_box[i]];
-  if (i - B.pbase >= B.nlive) {
-    d.ocnt[i] = 0;
-    if (d.cnt2) d.cnt2[i] = 0ull;
-    return;
-  }
   const PR* __restrict__ posr = (const PR*)b.posr;
   const int2* __restrict__ crange = d.crange;
   const float* __restrict__ cellr = d.cellr;
@@ -725,7 +724,6 @@ __global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, P
   int own = 0;
   const int K = d.K;
   int* rowp = d.row + (size_t)i * K;
-  unsigned long long* cnt2 = d.cnt2;
   bool over = false;
   // Pass 2, warp-uniform: each iteration every lane tests its next four
   // candidates, first moving on to its next kept cell when the current one is
@@ -775,7 +773,6 @@ __global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, P
         if (own >= K) {
           over = true;
         } else {
-          if (cnt2) atomicAdd(cnt2 + jj, 1ull << 32);
           rowp[own++] = jj;
         }
       }
@@ -784,64 +781,60 @@ __global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5) k_candidates(Dev d, P
     __syncwarp(wmask);
   }
   if (over) flag(d.status, kStRowOverflow);
-  d.ocnt[i] = own;
-  if (cnt2) atomicAdd(cnt2 + i, (unsigned long long)own);
+  return own;
 }
 
-// found counts -> first list entry of each slot
-struct StartEpi {
-  int* hstart;
-  __device__ void operator()(int i, int, int pre) const { hstart[i] = pre; }
-};
-
-// packed (found, incoming) counts -> first entries of each slot in the
-// contact list and in the incoming list, the incoming count, and the check
-// that a particle's contacts fit its row capacity
-struct HstartEpi {
-  int* hstart;
-  int* istart;
-  int* icnt;
-  unsigned* status;
-  int K;
-  __device__ void operator()(int i, unsigned long long v, unsigned long long pre) const {
-    hstart[i] = (int)(pre & 0xffffffffull);
-    istart[i] = (int)(pre >> 32);
-    const int own = (int)(v & 0xffffffffull), inc = (int)(v >> 32);
-    icnt[i] = inc;
-    if (own + inc > K) flag(status, kStRowOverflow);
+template <int M>
+__global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5)
+k_candidates(Dev d, PState b, CList cn) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // whole warps run
+  int own = 0;
+  bool live = false;
+  if (i < d.N) {
+    const BoxDev& B = d.boxes[d.slot_box[i]];
+    live = i - B.pbase < B.nlive;
+    if (live) own = search_row<M>(d, b, B, i);
   }
-};
-
-// dense contact list: each live slot writes the pairs it found at its
-// prefix, oriented (lower id, higher id), its entry of the by-id history
-// index, and each contact's index into the partner's incoming list.  The
-// position in that list is taken by counting the partner's incoming count
-// (already scanned) back down to zero, so positions 0 .. inc-1 are each
-// taken once, in an order that the gather does not depend on.
-__global__ void k_compact(Dev d, PState b, CList cn) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.N) return;
-  const BoxDev& B = d.boxes[d.slot_box[i]];
-  if (i - B.pbase >= B.nlive) return;
-  int pre = d.hstart[i];
-  int n = d.ocnt[i];
-  if (pre + n > d.Cmax) n = max(0, d.Cmax - pre);
-  int idi = b.id[i];
-  cn.rs[idi] = pre;
+  __syncwarp();
+  // the warp's block of list entries
+  const int lane = threadIdx.x & 31;
+  const int incl = warp_incl_scan(own);
+  int base = 0;
+  if (lane == 31 && incl > 0) base = atomicAdd(cn.count, incl);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  if (!live) {
+    if (i < d.N) d.ocnt[i] = 0;
+    return;
+  }
+  const long long pre = (long long)base + incl - own;
+  int n = own;
+  if (pre + n > d.Cmax) {
+    flag(d.status, kStListOverflow);
+    n = (int)max(0ll, (long long)d.Cmax - pre);
+  }
+  const int hs = (int)min(pre, (long long)d.Cmax);
+  d.hstart[i] = hs;
+  d.ocnt[i] = n;
+  const int idi = b.id[i];
+  cn.rs[idi] = hs;
   cn.rc[idi] = n;
-  const int* rowp = d.row + (size_t)i * d.K;
-  for (int k = 0; k < n; ++k) {
-    const int j = rowp[k];
-    const int idj = b.id[j];
-    const int c = pre + k;
-    cn.pair[c] = idi < idj ? make_int2(i, j) : make_int2(j, i);
-    cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
-    if (d.inlist) {
-      const unsigned long long old =
-          atomicAdd(d.cnt2 + j, 0ull - (1ull << 32));  // incoming count - 1
-      const int pos = (int)(old >> 32) - 1;
-      const int at = d.istart[j] + pos;
-      if (pos >= 0 && at < d.Cmax) d.inlist[at] = c;
+  const int K = d.K;
+  const int* rowp = d.row + (size_t)i * K;
+  for (int k = 0; k < n; k += 4) {
+    int jj[4], pos[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) jj[u] = k + u < n ? rowp[k + u] : -1;
+    // incoming positions of four partners, issued before any result is used
+#pragma unroll
+    for (int u = 0; u < 4; ++u) pos[u] = (d.inrow && jj[u] >= 0) ? atomicAdd(d.icnt + jj[u], 1) : K;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (jj[u] < 0) continue;
+      const int j = jj[u], c = hs + k + u;
+      const int idj = b.id[j];
+      cn.pair[c] = idi < idj ? make_int2(i, j) : make_int2(j, i);
+      cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
+      if (pos[u] < K) d.inrow[(size_t)j * K + pos[u]] = c;
     }
   }
 }
@@ -1160,7 +1153,7 @@ k_force(Dev d, PState b, CList co, CList cn) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   using DT = typename T::DT;
-  const int nc = *cn.count;
+  const int nc = min(*cn.count, d.Cmax);
   int mbox = -1;
   float m_ov = 0.0f, m_ratio = 0.0f;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
@@ -1313,26 +1306,64 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
     else F = F - xyz(f);
     Ns = Ns + xyz(q);
   }
+  if (own + inc > d.K) flag(d.status, kStRowOverflow);
   if (inc > 0) {
-    const int is = d.istart[i];
-    const int n = min(inc, d.Cmax - is);
-    const int* il = d.inlist + is;
-    int prev = -1;
-    for (int t = 0; t < n; ++t) {
-      int c = 0x7fffffff;
-      for (int q = 0; q < n; ++q) {
-        const int v = il[q];
-        if (v > prev && v < c) c = v;
+    // contacts found by the partners, in increasing partner slot (one
+    // contact per partner, and unlike the list entries slots do not depend
+    // on timing)
+    const int n = min(inc, d.K);
+    const int* il = d.inrow + (size_t)i * d.K;
+    if (n <= 4) {
+      // up to four: in registers, sorted by a compare-exchange network
+      int c[4], pk[4];
+      bool lo[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        c[u] = u < n ? il[u] : -1;
+        const int2 pr = c[u] >= 0 ? cn.pair[c[u]] : make_int2(i, 0x7fffffff);
+        lo[u] = pr.x == i;
+        pk[u] = lo[u] ? pr.y : pr.x;
       }
-      if (c >= d.Cmax) {
-        flag(d.status, kStInconsistent);
-        break;
+      auto cx = [&](int a2, int b2) {
+        if (pk[b2] < pk[a2]) {
+          const int tp = pk[a2], tc = c[a2];
+          const bool tl = lo[a2];
+          pk[a2] = pk[b2]; c[a2] = c[b2]; lo[a2] = lo[b2];
+          pk[b2] = tp; c[b2] = tc; lo[b2] = tl;
+        }
+      };
+      cx(0, 1); cx(2, 3); cx(0, 2); cx(1, 3); cx(1, 2);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (c[u] < 0) continue;
+        const V4 f = ld4(Fc + c[u]), q = ld4(nFc + c[u]);
+        if (lo[u]) F = F + xyz(f);
+        else F = F - xyz(f);
+        Ns = Ns + xyz(q);
       }
-      prev = c;
-      const V4 f = ld4(Fc + c), q = ld4(nFc + c);
-      if (cn.pair[c].x == i) F = F + xyz(f);
-      else F = F - xyz(f);
-      Ns = Ns + xyz(q);
+    } else {
+      int prev = -1;
+      for (int t = 0; t < n; ++t) {
+        int pbest = 0x7fffffff, cb = -1;
+        for (int u = 0; u < n; ++u) {
+          const int cu = il[u];
+          const int2 pr = cn.pair[cu];
+          const int pu = pr.x == i ? pr.y : pr.x;
+          if (pu > prev && pu < pbest) {
+            pbest = pu;
+            cb = cu;
+          }
+        }
+        if (cb < 0) {
+          flag(d.status, kStInconsistent);
+          break;
+        }
+        prev = pbest;
+        const V4 f = ld4(Fc + cb), q = ld4(nFc + cb);
+        if (cn.pair[cb].x == i) F = F + xyz(f);
+        else F = F - xyz(f);
+        Ns = Ns + xyz(q);
+      }
     }
   }
   V4 vm = ((const V4*)b.vel)[i];
