@@ -119,15 +119,19 @@ class ClockSampler:
 def phase_bytes(n, c_half, ncells):
     """Unique bytes each phase must move per step: every array element read
     or written once (neighbour re-reads served by caches are not counted).
-    n particles, c_half contacts per particle (half list), ncells cells."""
+    n particles, c_half contacts per particle (half list), ncells cells.
+    The contact list is written by the search kernel, so the compaction
+    phase moves nothing of its own."""
     C = c_half * n
-    sort = ncells * (4 + 4 + 8 + 4) + n * (4 + 4 + 4 + 4      # scan, scatter
-                                           + 4 + 4 + 4          # cell sort
-                                           + 4 + 2 * (24 + 16 + 16 + 4) + 4 + 4 + 16)  # reorder
-    search = n * (16 + 4 + 4 + 8) + ncells * 8 + 2 * C * 4
-    compact = n * (4 + 4 + 4 + 8) + C * (4 + 8 + 8)
+    state = 24 + 16 + 16 + 4 + 4        # position, velocity, spin, id, cell
+    sort = (ncells * (4 + 4 + 8 + 4)                 # cell scan, radius reset
+            + n * (4 + 4 + 4 + 4)                    # scatter
+            + n * (4 + 4 + 8 + 2 * state + 16 + 4 + 4))  # reorder, record, radius
+    search = (n * (16 + 4 + 4 + 4 + 4 + 8) + ncells * (8 + 4)
+              + C * (4 + 4 + 8 + 8 + 4 + 4))         # rows, list, incoming rows
+    compact = 0
     force = C * (8 + 8 + 8 + 8 + 24 + 24 + 16 + 16) + n * (24 + 16 + 16)
-    integrate = n * (4 + 4 + 4 + 2 * (24 + 16 + 16) + 4 + 4 + 4 + 4) + 2 * C * (32 + 4)
+    integrate = n * (4 + 4 + 4 + 2 * (24 + 16 + 16) + 4 + 4 + 4) + C * (2 * 32 + 2 * 8 + 4)
     return {"sort": sort, "search": search, "compact": compact, "force": force,
             "integrate": integrate}
 
@@ -171,7 +175,7 @@ def search_tests(box, ncell):
 
 SEARCH_OPS_PER_TEST = 14  # FP32 instructions of the contact predicate
 PHASES = ["sort", "search", "compact", "force", "integrate"]
-PHASE_KERNELS = {"sort": 5, "search": 1, "compact": 3, "force": 1, "integrate": 1}
+PHASE_KERNELS = {"sort": 5, "search": 1, "compact": 0, "force": 1, "integrate": 1}
 
 
 def _torch_setup(args):

@@ -1014,21 +1014,21 @@ __device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
   // the block of the particle that found it, which may be either of the two
   int found = -1;
   {
-    int os = co.rs[idlo], on = co.rc[idlo];
-    for (int k = 0; k < on; ++k) {
-      const int2 h = co.hid[os + k];
+    // both blocks' bounds are loaded up front (independent loads)
+    const int os1 = co.rs[idlo], on1 = co.rc[idlo];
+    const int os2 = co.rs[idhi], on2 = co.rc[idhi];
+    for (int k = 0; k < on1; ++k) {
+      const int2 h = co.hid[os1 + k];
       if (h.x == idlo && h.y == idhi) {
-        found = os + k;
+        found = os1 + k;
         break;
       }
     }
     if (found < 0) {
-      os = co.rs[idhi];
-      on = co.rc[idhi];
-      for (int k = 0; k < on; ++k) {
-        const int2 h = co.hid[os + k];
+      for (int k = 0; k < on2; ++k) {
+        const int2 h = co.hid[os2 + k];
         if (h.x == idlo && h.y == idhi) {
-          found = os + k;
+          found = os2 + k;
           break;
         }
       }
@@ -1295,9 +1295,9 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
   int own = fused ? 0 : d.ocnt[i], hs = fused ? 0 : d.hstart[i], inc = fused ? 0 : d.icnt[i];
   // Fc is the force on the pair's lower-id member: added when this slot is
   // that member, subtracted otherwise; n x F enters with the same sign for
-  // both.  Found contacts are summed in list order, incoming ones in
-  // increasing contact index (the order their positions were taken in is
-  // not reproducible; this one is).
+  // both.  Found contacts are summed in row order, incoming ones in
+  // increasing partner slot (the list entries and the incoming positions
+  // depend on timing; these orders do not).
   for (int k = 0; k < own; ++k) {
     const int c = hs + k;
     if (c >= d.Cmax) break;
