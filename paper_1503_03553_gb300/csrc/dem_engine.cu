@@ -439,9 +439,8 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.perm = (int*)A(sizeof(int) * n);
   d.pcell = (int*)A(sizeof(int) * n);
   d.row = (int*)A(sizeof(int) * n * ctx->K);
-  d.ocnt = (int*)A(sizeof(int) * n);
   d.icnt = (int*)A(sizeof(int) * n);
-  d.hstart = (int*)A(sizeof(int) * n);
+  d.prev = (int*)A(sizeof(int) * n);
   d.Fc = A(v4_bytes(M) * ctx->Cmax);
   d.nFc = A(v4_bytes(M) * ctx->Cmax);
   if (ctx->fused) {
@@ -478,8 +477,8 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     c.dx = A(dt_bytes(M) * ctx->Cmax);
     c.dy = A(dt_bytes(M) * ctx->Cmax);
     c.dz = A(dt_bytes(M) * ctx->Cmax);
-    c.rs = (int*)A(sizeof(int) * n);
-    c.rc = (int*)A(sizeof(int) * n);
+    c.hs = (int*)A(sizeof(int) * n);
+    c.oc = (int*)A(sizeof(int) * n);
     c.count = (int*)A(sizeof(int));
   }
   ctx->staging = (double*)A(sizeof(double) * 16 * (size_t)std::max(1, max_cap));
@@ -515,11 +514,10 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   if (!e) e = H2D(d.ccount, cnt.data(), sizeof(int) * cnt.size());
   if (!e) e = cudaMemsetAsync(d.status, 0, sizeof(unsigned), s);
   if (!e) e = cudaMemsetAsync(d.diag, 0, sizeof(unsigned) * 2 * ctx->hbox.size(), s);
-  if (!e) e = cudaMemsetAsync(d.ocnt, 0, sizeof(int) * n, s);
   if (!e) e = cudaMemsetAsync(d.icnt, 0, sizeof(int) * n, s);
   for (int p = 0; p < 2 && !e; ++p) {
-    e = cudaMemsetAsync(ctx->cl[p].rc, 0, sizeof(int) * n, s);
-    if (!e) e = cudaMemsetAsync(ctx->cl[p].rs, 0, sizeof(int) * n, s);
+    e = cudaMemsetAsync(ctx->cl[p].oc, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(ctx->cl[p].hs, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(ctx->cl[p].count, 0, sizeof(int), s);
   }
   if (!e) e = cudaStreamSynchronize(s);
@@ -576,9 +574,9 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
   B.nlive = (int)n;
   st = upload_box(ctx, box);
   if (st) return st;
-  // the box's history is empty: no particle owns a stored contact
+  // the box's history is empty: no slot of the box holds a stored contact
   for (int q = 0; q < 2; ++q)
-    CK(cudaMemsetAsync(ctx->cl[q].rc + B.pbase, 0, sizeof(int) * B.cap, s));
+    CK(cudaMemsetAsync(ctx->cl[q].oc + B.pbase, 0, sizeof(int) * B.cap, s));
   ctx->hist_cleared[box] = 1;
   if (n > 0) {
     const double *dx = x, *dv = v, *dw = omega, *dr = radius;
@@ -873,8 +871,8 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
   hid.clear();
   dts.clear();
   if (N == 0) return DEM_OK;
-  CK(cudaMemcpyAsync(rs.data(), c.rs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(rc.data(), c.rc, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rs.data(), c.hs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rc.data(), c.oc, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   long long top = 0;
   for (const BoxDev& B : ctx->hbox)
@@ -1029,18 +1027,41 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
       return fail(ctx, DEM_ERR_ARG, "duplicate contact");
   if ((long long)all.size() > ctx->Cmax) return fail(ctx, DEM_ERR_CAPACITY, "contact list capacity");
   const int nc = (int)all.size();
-  std::vector<int> rs(ctx->N, 0), rc(ctx->N, 0);
-  std::vector<int2> h2(nc);
+  // the list is indexed by the slots the particles hold now: each contact
+  // goes into the block of its lower-id member's slot
+  cudaStream_t s = ctx->stream;
+  const int N = ctx->N;
+  std::vector<int> id_of(N), slot_of(N, -1);
+  CK(cudaMemcpyAsync(id_of.data(), ctx->ps[ctx->parity].id, sizeof(int) * N,
+                     cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (const BoxDev& Bx : ctx->hbox)
+    for (int g = Bx.pbase; g < Bx.pbase + Bx.nlive; ++g)
+      if (id_of[g] >= 0 && id_of[g] < N) slot_of[id_of[g]] = g;
+  std::vector<int2> slots(nc);
+  for (int k = 0; k < nc; ++k) {
+    slots[k] = make_int2(slot_of[all[k].first.x], slot_of[all[k].first.y]);
+    if (slots[k].x < 0 || slots[k].y < 0)
+      return fail(ctx, DEM_ERR_STATE, "contact of a particle that holds no slot");
+  }
+  std::vector<int> order(nc);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return slots[a].x < slots[b].x; });
+  std::vector<int> rs(N, 0), rc(N, 0);
+  std::vector<int2> h2(nc), p2(nc);
   const size_t eb = dt_bytes(ctx->mode);
   std::vector<unsigned char> comp[3];
   for (int a = 0; a < 3; ++a) comp[a].resize(eb * std::max(1, nc));
   for (int k = 0; k < nc; ++k) {
-    h2[k] = all[k].first;
-    int lo = all[k].first.x;
+    const int src = order[k];
+    h2[k] = all[src].first;
+    p2[k] = slots[src];
+    const int lo = p2[k].x;
     if (rc[lo] == 0) rs[lo] = k;
     rc[lo]++;
     for (int a = 0; a < 3; ++a) {
-      double val = all[k].second[a];
+      double val = all[src].second[a];
       if (ctx->mode == kMIXED) {
         float hl[2];
         hl[0] = (float)val;
@@ -1054,16 +1075,16 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
       }
     }
   }
-  cudaStream_t s = ctx->stream;
   const CList& c = ctx->cl[ctx->parity];
   if (nc > 0) {
     CK(cudaMemcpyAsync(c.hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.pair, p2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.dx, comp[0].data(), eb * nc, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.dy, comp[1].data(), eb * nc, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c.dz, comp[2].data(), eb * nc, cudaMemcpyHostToDevice, s));
   }
-  CK(cudaMemcpyAsync(c.rs, rs.data(), sizeof(int) * ctx->N, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(c.rc, rc.data(), sizeof(int) * ctx->N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c.hs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c.oc, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
   *ctx->h_count = nc;
   CK(cudaMemcpyAsync(c.count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
@@ -1079,9 +1100,9 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
   double* dout = ctx->staging;
   const int p = ctx->parity;
   switch (ctx->mode) {
-    case kFP64: k_stats<kFP64><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dout); break;
-    case kMIXED: k_stats<kMIXED><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dout); break;
-    default: k_stats<kFP32><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dout); break;
+    case kFP64: k_stats<kFP64><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, dout); break;
+    case kMIXED: k_stats<kMIXED><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, dout); break;
+    default: k_stats<kFP32><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, dout); break;
   }
   CK(cudaGetLastError());
   double h[6];
@@ -1130,8 +1151,8 @@ constexpr int kStaticK = 32;
 
 // layout of the scratch array (every part 256-byte aligned)
 struct StaticLayout {
-  size_t box, slot_box, rol, lor, ccount, cstart, crange, cellr, perm, pcell, row, ocnt,
-      icnt, hstart, bsum, status, count, pair, rs, rc, state[2][10], total;
+  size_t box, slot_box, rol, lor, ccount, cstart, crange, cellr, perm, pcell, row,
+      icnt, bsum, status, count, pair, rs, rc, state[2][10], total;
 };
 
 constexpr size_t al(size_t v) { return (v + 255) & ~size_t(255); }
@@ -1156,9 +1177,7 @@ StaticLayout static_layout() {
   L.perm = take(4 * N);
   L.pcell = take(4 * N);
   L.row = take(4 * N * kStaticK);
-  L.ocnt = take(4 * N);
   L.icnt = take(4 * N);
-  L.hstart = take(4 * N);
   L.bsum = take(4 * 16384);
   L.status = take(4);
   L.count = take(4);
@@ -1305,9 +1324,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   d.perm = (int*)(base + lay.perm);
   d.pcell = (int*)(base + lay.pcell);
   d.row = (int*)(base + lay.row);
-  d.ocnt = (int*)(base + lay.ocnt);
   d.icnt = (int*)(base + lay.icnt);
-  d.hstart = (int*)(base + lay.hstart);
   d.status = (unsigned*)(base + lay.status);
   d.scan_bsum = (int*)(base + lay.bsum);
   PState ps[2];
@@ -1320,8 +1337,8 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   CList cn{};
   cn.pair = (int2*)(base + lay.pair);
   cn.hid = (int2*)pairs;
-  cn.rs = (int*)(base + lay.rs);
-  cn.rc = (int*)(base + lay.rc);
+  cn.hs = (int*)(base + lay.rs);
+  cn.oc = (int*)(base + lay.rc);
   cn.count = (int*)(base + lay.count);
 
   // The array keeps the previous call's contents: clear what must start at

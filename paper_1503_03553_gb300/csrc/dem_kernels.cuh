@@ -71,8 +71,8 @@ struct CList {
   void* dx;     // delta_t after the step, per component (DT)
   void* dy;
   void* dz;
-  int* rs;      // by global id of the lower particle: first contact ...
-  int* rc;      // ... and the number of contacts it owns
+  int* hs;      // by slot: first entry of the contacts the slot found ...
+  int* oc;      // ... and how many (the slot's block of the list)
   int* count;   // number of contacts (device scalar)
 };
 
@@ -93,9 +93,8 @@ struct Dev {
   int* perm;     // scatter position -> old slot (cell order, not yet by id)
   int* pcell;    // scatter position -> linear cell
   int* row;      // N x K: partner slots a slot found
-  int* ocnt;     // contacts a slot found (half stencil)
   int* icnt;     // contacts in which a slot was found by its partner
-  int* hstart;   // first list entry of a slot's found contacts
+  int* prev;     // slot of each particle before this step's reorder
   int* inrow;    // N x K: list entries of the contacts in which a slot was
                  // found by its partner (any order)
   void* Fc;      // V4 per contact: force on the lower-id particle
@@ -526,6 +525,7 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   int rank = 0;
   for (int u = rg.x; u < rg.x + rg.y; ++u) rank += a.id[d.perm[u]] < key ? 1 : 0;
   const int t = rg.x + rank;  // final slot
+  if (d.prev) d.prev[t] = s;
   P x = ((const P*)a.px)[s], y = ((const P*)a.py)[s], z = ((const P*)a.pz)[s];
   ((P*)b.px)[t] = x;
   ((P*)b.py)[t] = y;
@@ -803,7 +803,10 @@ k_candidates(Dev d, PState b, CList cn) {
   if (lane == 31 && incl > 0) base = atomicAdd(cn.count, incl);
   base = __shfl_sync(0xffffffffu, base, 31);
   if (!live) {
-    if (i < d.N) d.ocnt[i] = 0;
+    if (i < d.N) {
+      cn.hs[i] = 0;
+      cn.oc[i] = 0;
+    }
     return;
   }
   const long long pre = (long long)base + incl - own;
@@ -813,11 +816,9 @@ k_candidates(Dev d, PState b, CList cn) {
     n = (int)max(0ll, (long long)d.Cmax - pre);
   }
   const int hs = (int)min(pre, (long long)d.Cmax);
-  d.hstart[i] = hs;
-  d.ocnt[i] = n;
+  cn.hs[i] = hs;
+  cn.oc[i] = n;
   const int idi = b.id[i];
-  cn.rs[idi] = hs;
-  cn.rc[idi] = n;
   const int K = d.K;
   const int* rowp = d.row + (size_t)i * K;
   for (int k = 0; k < n; k += 4) {
@@ -1010,24 +1011,26 @@ __device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
   const P* __restrict__ pz = (const P*)b.pz;
   const V4* __restrict__ vel = (const V4*)b.vel;
   const V4* __restrict__ omg = (const V4*)b.omg;
-  // history of this pair from the previous step's list: a pair is listed in
-  // the block of the particle that found it, which may be either of the two
+  // history of this pair from the previous step's list (the delta_t remap):
+  // the pair is listed, by the slots the two particles had then, in the
+  // block of the one that found it, which may be either; slots move little
+  // from step to step, so these reads stay near this contact's own
   int found = -1;
   {
-    // both blocks' bounds are loaded up front (independent loads)
-    const int os1 = co.rs[idlo], on1 = co.rc[idlo];
-    const int os2 = co.rs[idhi], on2 = co.rc[idhi];
+    const int si = d.prev[i], sj = d.prev[j];
+    const int os1 = co.hs[si], on1 = co.oc[si];
+    const int os2 = co.hs[sj], on2 = co.oc[sj];
     for (int k = 0; k < on1; ++k) {
-      const int2 h = co.hid[os1 + k];
-      if (h.x == idlo && h.y == idhi) {
+      const int2 h = co.pair[os1 + k];
+      if (h.x == si && h.y == sj) {
         found = os1 + k;
         break;
       }
     }
     if (found < 0) {
       for (int k = 0; k < on2; ++k) {
-        const int2 h = co.hid[os2 + k];
-        if (h.x == idlo && h.y == idhi) {
+        const int2 h = co.pair[os2 + k];
+        if (h.x == si && h.y == sj) {
           found = os2 + k;
           break;
         }
@@ -1198,7 +1201,10 @@ k_collide_fused(Dev d, PState b, CList co, CList cn, int ko) {
   if (i < d.N) {
     const BoxDev& B0 = d.boxes[d.slot_box[i]];
     live = i - B0.pbase < B0.nlive;
-    if (!live) d.ocnt[i] = 0;
+    if (!live) {
+      cn.hs[i] = 0;
+      cn.oc[i] = 0;
+    }
   }
   if (live) {
     const int box = d.slot_box[i];
@@ -1243,6 +1249,7 @@ k_collide_fused(Dev d, PState b, CList co, CList cn, int ko) {
               F = F + xyz(o.F4);
               if (own < ko) {
                 const int cc = i * ko + own;
+                cn.pair[cc] = make_int2(i, j);
                 cn.hid[cc] = make_int2(idi, idj);
                 ((DT*)cn.dx)[cc] = o.nx;
                 ((DT*)cn.dy)[cc] = o.ny;
@@ -1266,9 +1273,8 @@ k_collide_fused(Dev d, PState b, CList co, CList cn, int ko) {
     const R r = (R)pi.w;
     st4((V4*)d.Ffused + i, mk4<R>(F.x, F.y, F.z, R(0)));
     st4((V4*)d.Tfused + i, mk4<R>(r * Ns.x, r * Ns.y, r * Ns.z, R(0)));
-    cn.rs[idi] = i * ko;
-    cn.rc[idi] = own;
-    d.ocnt[i] = own;
+    cn.hs[i] = i * ko;
+    cn.oc[i] = own;
   }
   flush_diag(d, mbox, m_ov, m_ratio);
 }
@@ -1292,7 +1298,7 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
   const V4* nFc = (const V4*)d.nFc;
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
   const bool fused = d.Ffused != nullptr;
-  int own = fused ? 0 : d.ocnt[i], hs = fused ? 0 : d.hstart[i], inc = fused ? 0 : d.icnt[i];
+  int own = fused ? 0 : cn.oc[i], hs = fused ? 0 : cn.hs[i], inc = fused ? 0 : d.icnt[i];
   // Fc is the force on the pair's lower-id member: added when this slot is
   // that member, subtracted otherwise; n x F enters with the same sign for
   // both.  Found contacts are summed in row order, incoming ones in
@@ -1588,7 +1594,7 @@ __global__ void k_get_order(Dev d, PState b, int box, int* id_by_slot,
 
 // per-box FP64 reductions in a fixed order (one block per box)
 template <int M>
-__global__ void k_stats(Dev d, PState b, int box, double* out) {
+__global__ void k_stats(Dev d, PState b, const int* oc, int box, double* out) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   const BoxDev& B = d.boxes[box];
@@ -1605,7 +1611,7 @@ __global__ void k_stats(Dev d, PState b, int box, double* out) {
     acc[2] += m * vx;
     acc[3] += m * vy;
     acc[4] += m * vz;
-    acc[5] += (double)d.ocnt[s];
+    acc[5] += (double)oc[s];
   }
   __shared__ double sh[6][256];
   for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = acc[q];
