@@ -60,6 +60,8 @@ struct dem_ctx {
   Dev dev{};
   PState ps[2]{};
   CList cl[2]{};
+  int* cs[2]{};                // cell starts of the order held by state 0 / 1
+  unsigned char* dirty[2]{};   // changed-cell flags read by a step of parity 0 / 1
   int parity = 0;
   bool any_floor = false;
   bool have_particles = false;
@@ -143,7 +145,13 @@ int blocks_for(long long n, int b) { return (int)((n + b - 1) / b); }
 template <int M>
 void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   const int q = 1 - p;
-  Dev& d = ctx->dev;
+  // this step sorts the order of state p into state q: cell starts of both
+  // orders, and the changed-cell flags read now and collected for next time
+  Dev d = ctx->dev;
+  d.cstart = ctx->cs[q];
+  d.cstart_old = ctx->cs[p];
+  d.dirty = ctx->dirty[p];
+  d.dirty_next = ctx->dirty[q];
   cudaStream_t s = ctx->stream;
   const int bs = ctx->block;
   const bool tm = ctx->tm.on;
@@ -156,7 +164,7 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
                                            d.status, 0u);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(
       d.ccount, d.M_rank, d.scan_bsum,
-      CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank});
+      CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank, d.dirty, d.dirty_next, d.ccur});
   // 2. counting sort by (Morton cell, id) and reorder into parity q
   k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
   k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q],
@@ -433,7 +441,11 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.rank_of_lin = (const int*)A(sizeof(int) * std::max(1, ctx->M_lin));
   d.lin_of_rank = (const int*)A(sizeof(int) * std::max(1, ctx->M_rank));
   d.ccount = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
-  d.cstart = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
+  d.ccur = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
+  for (int p = 0; p < 2; ++p) {
+    ctx->cs[p] = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
+    ctx->dirty[p] = (unsigned char*)A(std::max(1, ctx->M_rank));
+  }
   d.crange = (int2*)A(sizeof(int2) * std::max(1, ctx->M_lin));
   d.cellr = (float*)A(sizeof(float) * std::max(1, ctx->M_lin));
   d.perm = (int*)A(sizeof(int) * n);
@@ -516,6 +528,10 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   if (!e) e = cudaMemsetAsync(d.diag, 0, sizeof(unsigned) * 2 * ctx->hbox.size(), s);
   if (!e) e = cudaMemsetAsync(d.icnt, 0, sizeof(int) * n, s);
   for (int p = 0; p < 2 && !e; ++p) {
+    e = cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s);
+    if (!e) e = cudaMemsetAsync(ctx->cs[p], 0, sizeof(int) * std::max(1, ctx->M_rank), s);
+  }
+  for (int p = 0; p < 2 && !e; ++p) {
     e = cudaMemsetAsync(ctx->cl[p].oc, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(ctx->cl[p].hs, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(ctx->cl[p].count, 0, sizeof(int), s);
@@ -577,6 +593,8 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
   // the box's history is empty: no slot of the box holds a stored contact
   for (int q = 0; q < 2; ++q)
     CK(cudaMemsetAsync(ctx->cl[q].oc + B.pbase, 0, sizeof(int) * B.cap, s));
+  // the next sort starts from the order the particles were given in
+  CK(cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s));
   ctx->hist_cleared[box] = 1;
   if (n > 0) {
     const double *dx = x, *dv = v, *dw = omega, *dr = radius;
@@ -627,6 +645,8 @@ dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
     case kMIXED: k_set_state<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, dx, dv, dw); break;
     default: k_set_state<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, dx, dv, dw); break;
   }
+  // new positions may have changed cells: the next sort starts from scratch
+  if (dx) CK(cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s));
   CK(cudaGetLastError());
   return DEM_OK;
 }
@@ -1151,7 +1171,7 @@ constexpr int kStaticK = 32;
 
 // layout of the scratch array (every part 256-byte aligned)
 struct StaticLayout {
-  size_t box, slot_box, rol, lor, ccount, cstart, crange, cellr, perm, pcell, row,
+  size_t box, slot_box, rol, lor, ccount, cstart, ccur, dirty, crange, cellr, perm, pcell, row,
       icnt, bsum, status, count, pair, rs, rc, state[2][10], total;
 };
 
@@ -1172,6 +1192,8 @@ StaticLayout static_layout() {
   L.lor = take(4 * (M + 1));
   L.ccount = take(4 * (M + 1));
   L.cstart = take(4 * (M + 1));
+  L.ccur = take(4 * (M + 1));
+  L.dirty = take(M + 1);
   L.crange = take(8 * M);
   L.cellr = take(4 * M);
   L.perm = take(4 * N);
@@ -1319,6 +1341,9 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   d.lin_of_rank = (const int*)(base + lay.lor);
   d.ccount = (int*)(base + lay.ccount);
   d.cstart = (int*)(base + lay.cstart);
+  d.cstart_old = d.cstart;
+  d.ccur = (int*)(base + lay.ccur);
+  d.dirty = (const unsigned char*)(base + lay.dirty);
   d.crange = (int2*)(base + lay.crange);
   d.cellr = (float*)(base + lay.cellr);
   d.perm = (int*)(base + lay.perm);
@@ -1342,7 +1367,8 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   cn.count = (int*)(base + lay.count);
 
   // The array keeps the previous call's contents: clear what must start at
-  // zero (cell counts, box index of every slot, status, count).
+  // zero (cell counts, box index of every slot, status, count) and mark
+  // every cell changed (no order to keep from a previous call).
   auto ck = [&](cudaError_t e, const char* what) -> dem_status {
     if (e == cudaSuccess) return DEM_OK;
     return fail(ctx, DEM_ERR_CUDA, std::string("dem_contacts_static: ") + what + ": " +
@@ -1352,6 +1378,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   if ((st = ck(cudaMemcpyAsync(base + lay.box, &B, sizeof(BoxDev), cudaMemcpyHostToDevice, s), "box")))
     return st;
   if ((st = ck(cudaMemsetAsync(d.ccount, 0, 4 * (size_t)(M + 1), s), "counts"))) return st;
+  if ((st = ck(cudaMemsetAsync(base + lay.dirty, 1, (size_t)(M + 1), s), "cell flags"))) return st;
   if ((st = ck(cudaMemsetAsync((void*)d.slot_box, 0, 4 * (size_t)N, s), "slots"))) return st;
   if ((st = ck(cudaMemsetAsync(d.status, 0, 4, s), "status"))) return st;
   if ((st = ck(cudaMemsetAsync(cn.count, 0, 4, s), "count"))) return st;
@@ -1363,7 +1390,8 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
   k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum,
-                                            CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank});
+                                            CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank,
+                                                    d.dirty, nullptr, d.ccur});
   k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
   k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1], cn.count);
   k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);

@@ -86,8 +86,12 @@ struct Dev {
   int M_rank;    // cells + one free-slot cell per box
   const int* rank_of_lin;  // box-local Morton rank of each linear cell
   const int* lin_of_rank;  // global linear cell of each rank cell, -1 = free
-  int* ccount;   // per rank cell: particles binned, then a scatter cursor
-  int* cstart;   // per rank cell: first slot
+  int* ccount;   // per rank cell: particles in it (kept up to date by movers)
+  int* cstart;   // per rank cell: first slot in the order being built
+  const int* cstart_old;  // per rank cell: first slot in the current order
+  int* ccur;     // per rank cell: scatter cursor of a cell that changed
+  const unsigned char* dirty;  // per rank cell: members changed since the last sort
+  unsigned char* dirty_next;   // the same, collected for the next sort
   int2* crange;  // per linear cell: (first slot, count)
   float* cellr;  // per linear cell: largest radius in the cell (-1 if empty)
   int* perm;     // scatter position -> old slot (cell order, not yet by id)
@@ -464,47 +468,69 @@ k_scan_apply(const T* __restrict__ in, int n, const T* __restrict__ bsum,
 }
 
 // cell counts -> cell starts (rank order) and (start, count) by linear cell
+// For a cell whose members changed it also zeroes the scatter cursor and
+// resets the largest radius to -1 (empty; the reorder raises it), and it
+// clears the cell's flag for the next sort.
 struct CellEpi {
   int* cstart;
   int2* crange;
-  float* cellr;  // reset to -1 (empty); the reorder raises it to the largest radius
+  float* cellr;
   const int* lin_of_rank;
+  const unsigned char* dirty;
+  unsigned char* dirty_next;
+  int* ccur;
   __device__ void operator()(int g, int cnt, int pre) const {
     cstart[g] = pre;
+    const bool changed = dirty[g] != 0;
+    if (changed) ccur[g] = 0;
+    if (dirty_next) dirty_next[g] = 0;
     int lin = lin_of_rank[g];
     if (lin >= 0) {
       crange[lin] = make_int2(pre, cnt);
-      if (cellr) cellr[lin] = -1.0f;
+      if (cellr && changed) cellr[lin] = -1.0f;
     }
   }
 };
 
 // ---------------------------------------------------------------------------
 // counting sort, pass 1: each particle takes a position in its cell's range
-// (in atomic order) and records its old slot and its cell there
+// and records its old slot and its cell there.  A cell whose members did not
+// change since the last sort keeps their order (sorted by id): position =
+// new start + old position in the cell, no atomics.  Particles of a changed
+// cell take positions in atomic order; pass 2 sorts those.
 // ---------------------------------------------------------------------------
 __global__ void k_scatter(Dev d, PState a) {
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= d.N) return;
   const BoxDev& B = d.boxes[d.slot_box[s]];
   if (s - B.pbase >= B.nlive) return;
-  int g = a.cellg[s];
-  int left = atomicSub(&d.ccount[g], 1);
-  int pos = d.cstart[g] + left - 1;
-  if (left <= 0 || pos < 0 || pos >= d.N) {  // counts out of step: report
+  const int g = a.cellg[s];
+  int pos;
+  if (!d.dirty[g]) {
+    pos = d.cstart[g] + (s - d.cstart_old[g]);
+  } else {
+    const int k = atomicAdd(&d.ccur[g], 1);
+    if (k >= d.ccount[g]) {  // counts out of step: report
+      flag(d.status, kStInconsistent);
+      return;
+    }
+    pos = d.cstart[g] + k;
+  }
+  if (pos < 0 || pos >= d.N) {
     flag(d.status, kStInconsistent);
     return;
   }
   d.perm[pos] = s;
-  d.pcell[pos] = d.lin_of_rank[g];
+  d.pcell[pos] = g;
 }
 
 // ---------------------------------------------------------------------------
-// counting sort, pass 2: each particle's final slot is its cell's start plus
-// the number of cell-mates with a smaller id, so the slot order is (Morton
-// rank of the cell, id) whatever the atomic order of pass 1; the state moves
-// there, the predicate record is built, and the cell's largest radius is
-// raised to the particle's (positive floats order like their bit patterns)
+// counting sort, pass 2: in a changed cell each particle's final slot is the
+// cell's start plus the number of cell-mates with a smaller id, so the slot
+// order is (Morton rank of the cell, id) whatever the atomic order of pass 1,
+// and the cell's largest radius is raised to the particle's (positive floats
+// order like their bit patterns); in an unchanged cell pass 1 already placed
+// it.  The state moves there and the predicate record is built.
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
@@ -519,12 +545,17 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   const BoxDev& B = d.boxes[d.slot_box[q]];
   if (q - B.pbase >= B.nlive) return;
   const int s = d.perm[q];
-  const int lin = d.pcell[q];
-  const int2 rg = d.crange[lin];
+  const int g = d.pcell[q];
+  const int lin = d.lin_of_rank[g];
+  const bool changed = d.dirty[g] != 0;
   const int key = a.id[s];
-  int rank = 0;
-  for (int u = rg.x; u < rg.x + rg.y; ++u) rank += a.id[d.perm[u]] < key ? 1 : 0;
-  const int t = rg.x + rank;  // final slot
+  int t = q;  // final slot
+  if (changed) {
+    const int2 rg = d.crange[lin];
+    int rank = 0;
+    for (int u = rg.x; u < rg.x + rg.y; ++u) rank += a.id[d.perm[u]] < key ? 1 : 0;
+    t = rg.x + rank;
+  }
   if (d.prev) d.prev[t] = s;
   P x = ((const P*)a.px)[s], y = ((const P*)a.py)[s], z = ((const P*)a.pz)[s];
   ((P*)b.px)[t] = x;
@@ -537,6 +568,7 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   b.id[t] = key;
   int cc = a.cellx[s];
   b.cellc[t] = cc;
+  b.cellg[t] = g;
   if (a.wx) {
     using DT = typename T::DT;
     ((DT*)b.wx)[t] = ((const DT*)a.wx)[s];
@@ -558,7 +590,7 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   }
   pr.w = om.w;
   st4((PR*)b.posr + t, pr);
-  if (d.cellr) atomicMax((int*)d.cellr + lin, __float_as_int((float)om.w));
+  if (d.cellr && changed) atomicMax((int*)d.cellr + lin, __float_as_int((float)om.w));
 }
 
 // ---------------------------------------------------------------------------
@@ -1523,10 +1555,18 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
   ((P*)b.px)[i] = p[0];
   ((P*)b.py)[i] = p[1];
   ((P*)b.pz)[i] = p[2];
-  b.cellx[i] = pack_cell(c[0], c[1], c[2]);
-  int g = rank_cell(d, B, c[0], c[1], c[2]);
-  b.cellg[i] = g;
-  atomicAdd(&d.ccount[g], 1);
+  const int cnew = pack_cell(c[0], c[1], c[2]);
+  b.cellx[i] = cnew;
+  if (cnew != cc) {
+    // moved to another cell: counts and the changed-cell flags of both
+    const int g0 = b.cellg[i];
+    const int g = rank_cell(d, B, c[0], c[1], c[2]);
+    b.cellg[i] = g;
+    atomicSub(&d.ccount[g0], 1);
+    atomicAdd(&d.ccount[g], 1);
+    d.dirty_next[g0] = 1;
+    d.dirty_next[g] = 1;
+  }
 }
 
 // ---------------------------------------------------------------------------
