@@ -522,19 +522,28 @@ def _phase_ms(D, torch, stream, boxes, precision, ncells, steps, **kw):
 
 
 def _fused_leg(args, D, torch, stream, box, ncell):
-    """The paper's comparison on this workload: Algorithm 1 (search and force
-    fused per particle, no contact list) against the split pipeline (search,
-    dense contact list, one thread per contact).  'collide' is the time of
-    the contact part of the step: fused kernel vs search + list + force."""
+    """The paper's comparison on this workload.  Its two per-particle Collide
+    forms: Algorithm 1 as printed (search and force fused, each force as soon
+    as its contact is found) and its improvement (Sec. 3.4: a first loop keeps
+    the contact partners, a second computes their forces); against the split
+    pipeline here (search, dense contact list, one thread per contact).
+    'collide' is the contact part of the step: the per-particle kernel vs
+    search + list + force."""
     steps = max(16, args.steps // 8)
-    fused = _throughput(D, torch, stream, [box], "mixed", [ncell], steps,
-                        collide=D.DEM_COLLIDE_FUSED)
-    pf = _phase_ms(D, torch, stream, [box], "mixed", [ncell], 20, collide=D.DEM_COLLIDE_FUSED)
+    out = {}
+    coll = {}
+    for name, form in (("fused", D.DEM_COLLIDE_FUSED), ("twoloop", D.DEM_COLLIDE_TWOLOOP)):
+        out[f"{name}_step"] = _throughput(D, torch, stream, [box], "mixed", [ncell], steps,
+                                          collide=form)
+        pf = _phase_ms(D, torch, stream, [box], "mixed", [ncell], 20, collide=form)
+        coll[name] = pf["search"] + pf["compact"] + pf["force"]
     pc = _phase_ms(D, torch, stream, [box], "mixed", [ncell], 20)
-    cf = pf["search"] + pf["compact"] + pf["force"]
-    cc = pc["search"] + pc["compact"] + pc["force"]
-    return {"fused_step": fused, "collide_ms_fused": cf, "collide_ms_compact": cc,
-            "collide_speedup_of_compaction": cf / cc}
+    coll["compact"] = pc["search"] + pc["compact"] + pc["force"]
+    out.update({"collide_ms_fused": coll["fused"], "collide_ms_twoloop": coll["twoloop"],
+                "collide_ms_compact": coll["compact"],
+                "twoloop_speedup_over_fused": coll["fused"] / coll["twoloop"],
+                "collide_speedup_of_compaction": coll["fused"] / coll["compact"]})
+    return out
 
 
 def _batched_leg(args, D, torch, stream):

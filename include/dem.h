@@ -79,8 +79,17 @@ typedef enum { DEM_HOST = 0, DEM_DEVICE = 1 } dem_where;
  *                         per-particle pass sums it (no float atomics).
  *   DEM_COLLIDE_FUSED   : Algorithm 1 of the paper: one thread per particle
  *                         searches and computes the force of each contact as
- *                         it is found (each pair evaluated from both sides). */
-typedef enum { DEM_COLLIDE_COMPACT = 0, DEM_COLLIDE_FUSED = 1 } dem_collide;
+ *                         it is found (each pair evaluated from both sides).
+ *   DEM_COLLIDE_TWOLOOP : the paper's improved Collide (Sec. 3.4): one thread
+ *                         per particle first finds and keeps all its contact
+ *                         partners, then computes their forces in a second
+ *                         loop.  Same results as DEM_COLLIDE_FUSED, bit for
+ *                         bit (same summation order). */
+typedef enum {
+  DEM_COLLIDE_COMPACT = 0,
+  DEM_COLLIDE_FUSED = 1,
+  DEM_COLLIDE_TWOLOOP = 2
+} dem_collide;
 
 /* One material (Sec. 2: sigma, G, E, m via density; alpha from epsilon).
  * The transverse modulus is G = E / (2 (1 + poisson)). */

@@ -23,7 +23,7 @@ DEM_OK, DEM_ERR_ARG, DEM_ERR_ALLOC, DEM_ERR_CUDA, DEM_ERR_CAPACITY = 0, 1, 2, 3,
 DEM_ERR_NONFINITE, DEM_ERR_TIMEOUT, DEM_ERR_STATE = 5, 6, 7
 DEM_FP64, DEM_MIXED, DEM_FP32 = 0, 1, 2
 DEM_HOST, DEM_DEVICE = 0, 1
-DEM_COLLIDE_COMPACT, DEM_COLLIDE_FUSED = 0, 1
+DEM_COLLIDE_COMPACT, DEM_COLLIDE_FUSED, DEM_COLLIDE_TWOLOOP = 0, 1, 2
 DEM_NSTATS = 10
 PRECISIONS = {"fp64": DEM_FP64, "mixed": DEM_MIXED, "fp32": DEM_FP32}
 STATUS_NAMES = {0: "DEM_OK", 1: "DEM_ERR_ARG", 2: "DEM_ERR_ALLOC", 3: "DEM_ERR_CUDA",

@@ -53,7 +53,8 @@ struct dem_ctx {
   int block = 256;
   int graph_steps = 16;
   int max_cap = 0;
-  bool fused = false;  // DEM_COLLIDE_FUSED: Algorithm 1, no contact list
+  bool fused = false;  // a per-particle Collide form: no contact list
+  bool twoloop = false;  // DEM_COLLIDE_TWOLOOP: the paper's two-loop form
   int ko = 8;          // fused: stored contacts per particle
   std::vector<BoxDev> hbox;
   std::vector<void*> allocs;
@@ -172,8 +173,12 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   if (tm) cudaEventRecord(ev[1], s);
   if (ctx->fused) {
     // Algorithm 1: search and force in one pass, no contact list
-    k_collide_fused<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[p],
-                                                          ctx->cl[q], ctx->ko);
+    if (ctx->twoloop)
+      k_collide_per_particle<M, true><<<blocks_for(d.N, bs), bs, 0, s>>>(
+          d, ctx->ps[q], ctx->cl[p], ctx->cl[q], ctx->ko);
+    else
+      k_collide_per_particle<M, false><<<blocks_for(d.N, bs), bs, 0, s>>>(
+          d, ctx->ps[q], ctx->cl[p], ctx->cl[q], ctx->ko);
     if (tm) {
       cudaEventRecord(ev[2], s);
       cudaEventRecord(ev[3], s);
@@ -265,8 +270,10 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     return fail(nullptr, DEM_ERR_ARG, "config needs boxes and materials");
   if (cfg->precision < 0 || cfg->precision > 2)
     return fail(nullptr, DEM_ERR_ARG, "bad precision");
-  if (cfg->collide != DEM_COLLIDE_COMPACT && cfg->collide != DEM_COLLIDE_FUSED)
-    return fail(nullptr, DEM_ERR_ARG, "collide must be DEM_COLLIDE_COMPACT or DEM_COLLIDE_FUSED");
+  if (cfg->collide != DEM_COLLIDE_COMPACT && cfg->collide != DEM_COLLIDE_FUSED &&
+      cfg->collide != DEM_COLLIDE_TWOLOOP)
+    return fail(nullptr, DEM_ERR_ARG,
+                "collide must be DEM_COLLIDE_COMPACT, DEM_COLLIDE_FUSED or DEM_COLLIDE_TWOLOOP");
   if (!!cfg->alloc != !!cfg->free)
     return fail(nullptr, DEM_ERR_ARG, "alloc and free hooks go together");
   ctx = new dem_ctx();
@@ -278,7 +285,8 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   ctx->mode = cfg->precision == DEM_FP64 ? kFP64
               : cfg->precision == DEM_MIXED ? kMIXED : kFP32;
   ctx->K = cfg->row_capacity > 0 ? cfg->row_capacity : 32;
-  ctx->fused = cfg->collide == DEM_COLLIDE_FUSED;
+  ctx->fused = cfg->collide == DEM_COLLIDE_FUSED || cfg->collide == DEM_COLLIDE_TWOLOOP;
+  ctx->twoloop = cfg->collide == DEM_COLLIDE_TWOLOOP;
   ctx->block = cfg->block > 0 ? cfg->block : 256;
   ctx->graph_steps = cfg->graph_steps == 0 ? 16 : cfg->graph_steps;
   if (ctx->graph_steps > 0 && (ctx->graph_steps & 1)) ctx->graph_steps += 1;

@@ -1211,16 +1211,21 @@ k_force(Dev d, PState b, CList co, CList cn) {
 }
 
 // ---------------------------------------------------------------------------
-// Algorithm 1 of the paper, fused (DEM_COLLIDE_FUSED): one thread per
-// particle scans its neighbour cells and computes the force of each contact
-// as soon as it finds it (no contact list, no action-reaction: each pair is
+// The paper's per-particle Collide forms: one thread per particle scans its
+// 27 neighbour cells; no contact list, no action-reaction (each pair is
 // evaluated by both of its particles, in the same orientation, so the two
 // results are exact negatives).  The lower-id particle stores the pair's
 // delta_t in its slot's block of ko entries of the next list.
+//   kTwoLoop = false (DEM_COLLIDE_FUSED): Algorithm 1 as printed, the force
+//     of each contact computed as soon as the contact is found.
+//   kTwoLoop = true (DEM_COLLIDE_TWOLOOP): the paper's improvement (Sec. 3.4):
+//     a first loop only tests candidates and keeps the partners in contact
+//     (here in the particle's row), a second loop computes their forces.
+// Both sum the contacts in the same order, so their results are identical.
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, bool kTwoLoop>
 __global__ void __launch_bounds__(256)
-k_collide_fused(Dev d, PState b, CList co, CList cn, int ko) {
+k_collide_per_particle(Dev d, PState b, CList co, CList cn, int ko) {
   using T = Tr<M>;
   using PR = typename T::PR;
   using V4 = typename T::V4;
@@ -1250,6 +1255,36 @@ k_collide_fused(Dev d, PState b, CList co, CList cn, int ko) {
     v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
     int own = 0;
     bool over = false;
+    auto force_with = [&](int j) {
+      const int idj = ids[j];
+      const bool lo = idi < idj;
+      PairOut<M> o;
+      if (lo) pair_force<M>(d, b, co, B, i, j, idi, idj, o);
+      else pair_force<M>(d, b, co, B, j, i, idj, idi, o);
+      if (lo) {
+        F = F + xyz(o.F4);
+        if (own < ko) {
+          const int cc = i * ko + own;
+          cn.pair[cc] = make_int2(i, j);
+          cn.hid[cc] = make_int2(idi, idj);
+          ((DT*)cn.dx)[cc] = o.nx;
+          ((DT*)cn.dy)[cc] = o.ny;
+          ((DT*)cn.dz)[cc] = o.nz;
+          st4((V4*)d.Fc + cc, o.F4);
+          st4((V4*)d.nFc + cc, o.N4);
+          ++own;
+        } else {
+          over = true;
+        }
+        if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
+      } else {
+        F = F - xyz(o.F4);
+      }
+      Ns = Ns + xyz(o.N4);
+    };
+    int* rowp = d.row + (size_t)i * d.K;
+    int nfound = 0;
+    bool row_over = false;
     for (int dz = -1; dz <= 1; ++dz) {
       int czn;
       float sz;
@@ -1272,35 +1307,19 @@ k_collide_fused(Dev d, PState b, CList co, CList cn, int ko) {
             else
               hit = pred_abs(pi, pj, B);
             if (!hit) continue;
-            const int idj = ids[j];
-            const bool lo = idi < idj;
-            PairOut<M> o;
-            if (lo) pair_force<M>(d, b, co, B, i, j, idi, idj, o);
-            else pair_force<M>(d, b, co, B, j, i, idj, idi, o);
-            if (lo) {
-              F = F + xyz(o.F4);
-              if (own < ko) {
-                const int cc = i * ko + own;
-                cn.pair[cc] = make_int2(i, j);
-                cn.hid[cc] = make_int2(idi, idj);
-                ((DT*)cn.dx)[cc] = o.nx;
-                ((DT*)cn.dy)[cc] = o.ny;
-                ((DT*)cn.dz)[cc] = o.nz;
-                st4((V4*)d.Fc + cc, o.F4);
-                st4((V4*)d.nFc + cc, o.N4);
-                ++own;
-              } else {
-                over = true;
-              }
-              if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
+            if (kTwoLoop) {
+              if (nfound < d.K) rowp[nfound++] = j;
+              else row_over = true;
             } else {
-              F = F - xyz(o.F4);
+              force_with(j);
             }
-            Ns = Ns + xyz(o.N4);
           }
         }
       }
     }
+    if (kTwoLoop)
+      for (int k = 0; k < nfound; ++k) force_with(rowp[k]);
+    if (row_over) flag(d.status, kStRowOverflow);
     if (over) flag(d.status, kStListOverflow);
     const R r = (R)pi.w;
     st4((V4*)d.Ffused + i, mk4<R>(F.x, F.y, F.z, R(0)));

@@ -277,6 +277,32 @@ def test_fused_algorithm1_matches_oracle(dense3k, precision):
     check_one_step(b, g, o, precision)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_twoloop_collide_matches_oracle(dense3k, precision):
+    """DEM_COLLIDE_TWOLOOP (the paper's improvement, Sec. 3.4: a first loop
+    keeps the contact partners, a second loop computes their forces)."""
+    import paper_1503_03553_gb300 as D
+    b = prepared(dense3k, precision)
+    ncell = grid_for(b)
+    g = gpu_run([b], precision, [ncell], collide=D.DEM_COLLIDE_TWOLOOP)[0]
+    o = oracle_run(b, precision, ncell)
+    check_one_step(b, g, o, precision)
+
+
+def test_twoloop_and_fused_bit_identical_over_steps(dense3k):
+    """The two per-particle forms find the same contacts and sum them in the
+    same order: identical states, contacts and histories after 5 steps."""
+    import paper_1503_03553_gb300 as D
+    b = prepared(dense3k, "mixed")
+    ncell = grid_for(b)
+    t = gpu_run([b], "mixed", [ncell], steps=5, collide=D.DEM_COLLIDE_TWOLOOP)[0]
+    f = gpu_run([b], "mixed", [ncell], steps=5, collide=D.DEM_COLLIDE_FUSED)[0]
+    assert np.array_equal(t["lo"], f["lo"]) and np.array_equal(t["hi"], f["hi"])
+    for k in ("x", "v", "w"):
+        assert np.array_equal(t["state"][k], f["state"][k])
+    assert np.array_equal(t["dt"], f["dt"])
+
+
 def test_fused_and_compact_agree_over_steps(dense3k):
     import paper_1503_03553_gb300 as D
     b = prepared(dense3k, "mixed")
