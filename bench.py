@@ -53,6 +53,12 @@ def _args():
     ap.add_argument("--batched-steps", type=int, default=32)
     ap.add_argument("--w3", action="store_true",
                     help="add the 8M-particle floor/gravity leg (dense + dilute halves)")
+    ap.add_argument("--w5", action="store_true",
+                    help="add the W5 precision-stress leg (4 M spheres at packing 0.60, "
+                         "10,000 steps of each form, oracle snapshots every 1,000 steps)")
+    ap.add_argument("--w5-n", type=int, default=4_000_000)
+    ap.add_argument("--w5-steps", type=int, default=10_000)
+    ap.add_argument("--w5-every", type=int, default=1_000)
     return ap.parse_args()
 
 
@@ -486,6 +492,8 @@ def _side_legs(args, D, torch, box, ncell, stream):
         out["batched"] = _batched_leg(args, D, torch, stream)
     if args.w3:
         out["w3_floor_8M"] = _w3_leg(args, D, torch, stream)
+    if args.w5:
+        out["w5_precision"] = _w5_leg(args, D, torch, stream)
     return out
 
 
@@ -502,8 +510,91 @@ def _w3_leg(args, D, torch, stream):
     res["mixed_compact"]["phase_ms"] = _phase_ms(D, torch, stream, [box], "mixed", [nc], 10)
     res["mixed_fused"] = _throughput(D, torch, stream, [box], "mixed", [nc], 8,
                                      collide=D.DEM_COLLIDE_FUSED)
+    res["mixed_twoloop"] = _throughput(D, torch, stream, [box], "mixed", [nc], 8,
+                                       collide=D.DEM_COLLIDE_TWOLOOP)
     res["fp32_compact"] = _throughput(D, torch, stream, [box], "fp32", [nc], 40)
     res["fp64_compact"] = _throughput(D, torch, stream, [box], "fp64", [nc], 8)
+    return res
+
+
+def _w5_oracle(path):
+    """Worker (spawned, no GPU): one FP64 oracle step from a saved GPU
+    snapshot (state and contact history) and the error statistics of the
+    GPU's forces of the same step."""
+    import pickle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle as O
+    from parity import force_errors, oracle_params
+    with open(path, "rb") as fh:
+        b2, g, hist, prec, ncell = pickle.load(fh)
+    os.remove(path)
+    s = O.State(b2.x, b2.v, b2.w, b2.r)
+    s.lo, s.hi, s.dt = hist
+    p = oracle_params(b2, prec, ncell)
+    out = O.step(p, s)
+    out["params"] = p
+    return force_errors(b2, g, out, prec)
+
+
+def _w5_leg(args, D, torch, stream):
+    """W5 precision stress: spheres of radius U[3, 5] um at packing 0.60
+    relaxed to overlaps of about 1e-3 r, at rest; each form runs the full
+    step count, and every 'every' steps the force of one step from the
+    form's own state and history is compared with the FP64 oracle
+    re-evaluating that step (a full oracle run of this size is out of
+    reach).  The oracle steps run in spawned host processes while the GPU
+    continues."""
+    import multiprocessing as mp
+    import pickle
+    import tempfile
+    from paper_1503_03553_gb300 import synth
+    from parity import grid_for, prepared
+    raw = synth.w5_precision(n=args.w5_n, seed=5)
+    res = {"particles": raw.n, "steps": args.w5_steps, "every": args.w5_every}
+    tmp = tempfile.mkdtemp(prefix="w5_")
+    workers = max(1, min(8, (os.cpu_count() or 2) - 2))
+    pending = []
+    with mp.get_context("spawn").Pool(workers) as pool:
+        for prec in ("mixed", "fp32", "fp64"):
+            b = prepared(raw, prec)
+            nc = grid_for(b)
+            with torch.cuda.stream(stream):
+                ctx = D.Context([b], precision=prec, ncell=[nc])
+            try:
+                ctx.set_particles(0, b.x, b.v, b.w, b.r)
+                gpu_s = 0.0
+                for k in range(args.w5_steps // args.w5_every):
+                    gpu_s += _time_steps(ctx, torch, args.w5_every, 1)
+                    st = ctx.get_state(0)
+                    hist = ctx.contacts(0)
+                    ctx.step(1)
+                    g = {}
+                    g["lo"], g["hi"], _ = ctx.contacts(0)
+                    _, _, g["Fc"], _ = ctx.contact_forces(0)
+                    b2 = prepared(b, prec)
+                    b2.x, b2.v, b2.w = st["x"], st["v"], st["w"]
+                    path = os.path.join(tmp, f"{prec}_{k}.pkl")
+                    with open(path, "wb") as fh:
+                        pickle.dump((b2, g, hist, prec, nc), fh, protocol=4)
+                    del g, hist, st, b2
+                    while sum(not r.ready() for _, _, r in pending) >= workers:
+                        time.sleep(0.5)
+                    pending.append((prec, (k + 1) * args.w5_every,
+                                    pool.apply_async(_w5_oracle, (path,))))
+                res[prec] = {"ms_per_step": 1e3 * gpu_s / args.w5_steps,
+                             "contacts_at_end": int(ctx.stats(0)[5])}
+            finally:
+                ctx.close()
+        for prec, step, r in pending:
+            res[prec].setdefault("snapshots", []).append({"step": step, **r.get()})
+    for prec in ("mixed", "fp32", "fp64"):
+        sn = res[prec]["snapshots"]
+        res[prec]["worst_max_err_over_scale"] = max(x.get("max_err_over_scale", float("inf")) for x in sn)
+        res[prec]["min_frac_within_1e-5"] = min(x.get("frac_within_1e-5", 0.0) for x in sn)
+        res[prec]["worst_max_err_over_scale_cared"] = max(
+            x.get("max_err_over_scale_cared", float("inf")) for x in sn)
+        res[prec]["min_frac_within_1e-5_cared"] = min(x.get("frac_within_1e-5_cared", 0.0) for x in sn)
+        res[prec]["contact_sets_equal"] = all(x["contact_sets_equal"] for x in sn)
     return res
 
 
