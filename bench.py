@@ -56,6 +56,8 @@ def _args():
     ap.add_argument("--w5", action="store_true",
                     help="add the W5 precision-stress leg (4 M spheres at packing 0.60, "
                          "10,000 steps of each form, oracle snapshots every 1,000 steps)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="add a particle-count sweep of the W2 workload (0.1 to 8 M)")
     ap.add_argument("--w5-n", type=int, default=4_000_000)
     ap.add_argument("--w5-steps", type=int, default=10_000)
     ap.add_argument("--w5-every", type=int, default=1_000)
@@ -343,6 +345,7 @@ def main():
         ctx = D.Context([box], precision=args.precision, ncell=[ncell])
     ctx.set_particles(0, box.x, box.v, box.w, box.r)
     ctx.step(args.warmup)
+    contacts_before = ctx.stats(0)[5]
     # ---- timed region: K steps, CUDA graphs, device time -------------------
     with ClockSampler(local) as clk:
         secs = _time_steps(ctx, torch, args.steps, world)
@@ -350,6 +353,8 @@ def main():
     value = job_throughput(n, world, args.steps, secs)
     stats = ctx.stats(0)
     c_half = stats[5] / n
+    # half contacts evaluated per second (mean of the counts before and after)
+    contact_evals = 0.5 * (contacts_before + stats[5]) * world * args.steps / secs
     # ---- per-phase device time (same workload, direct launches) -----------
     ctx.set_timing(True)
     phase_steps = min(100, max(10, args.steps // 4))
@@ -432,6 +437,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
+        "contact_evals_per_s": contact_evals,
         "dtype": {"mixed": "f32 (fixed-point positions, float-float history)",
                   "fp64": "f64", "fp32": "f32"}[args.precision],
         "data": "synthetic (seeded generator)",
@@ -494,7 +500,25 @@ def _side_legs(args, D, torch, box, ncell, stream):
         out["w3_floor_8M"] = _w3_leg(args, D, torch, stream)
     if args.w5:
         out["w5_precision"] = _w5_leg(args, D, torch, stream)
+    if args.sweep:
+        out["n_sweep"] = _sweep_leg(args, D, torch, stream)
     return out
+
+
+def _sweep_leg(args, D, torch, stream):
+    """Particle-steps/s of the MIXED form against the particle count, W2
+    radius law and packing (tiles of 8,000 relaxed spheres)."""
+    from paper_1503_03553_gb300 import synth
+    from parity import grid_for, prepared
+    rows = []
+    for n in (100_000, 300_000, 1_000_000, 3_000_000, 8_000_000):
+        box = prepared(synth.w2_polydisperse(n=n, seed=2), "mixed")
+        nc = grid_for(box)
+        steps = max(20, int(2e8 / box.n))
+        r = _throughput(D, torch, stream, [box], "mixed", [nc], steps, warmup=5)
+        r.update({"particles": box.n, "ncell": nc})
+        rows.append(r)
+    return rows
 
 
 def _w3_leg(args, D, torch, stream):

@@ -1126,12 +1126,15 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
   if (!out) return fail(ctx, DEM_ERR_ARG, "out is null");
   cudaStream_t s = ctx->stream;
   double* dout = ctx->staging;
+  double* part = ctx->staging + 8;
+  const int nparts = std::max(1, std::min(512, blocks_for(ctx->hbox[box].nlive, 256)));
   const int p = ctx->parity;
   switch (ctx->mode) {
-    case kFP64: k_stats<kFP64><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, dout); break;
-    case kMIXED: k_stats<kMIXED><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, dout); break;
-    default: k_stats<kFP32><<<1, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, dout); break;
+    case kFP64: k_stats<kFP64><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, part); break;
+    case kMIXED: k_stats<kMIXED><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, part); break;
+    default: k_stats<kFP32><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, part); break;
   }
+  k_stats_final<<<1, 32, 0, s>>>(part, nparts, dout);
   CK(cudaGetLastError());
   double h[6];
   unsigned dg[2];

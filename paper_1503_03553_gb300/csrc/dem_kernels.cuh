@@ -1652,13 +1652,17 @@ __global__ void k_get_order(Dev d, PState b, int box, int* id_by_slot,
 }
 
 // per-box FP64 reductions in a fixed order (one block per box)
+// Box statistics in FP64: each block sums a strided share of the box's
+// slots into part[block][6]; k_stats_final adds the parts in block order
+// (a fixed order: the result does not depend on timing).
 template <int M>
-__global__ void k_stats(Dev d, PState b, const int* oc, int box, double* out) {
+__global__ void k_stats(Dev d, PState b, const int* oc, int box, double* part) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   const BoxDev& B = d.boxes[box];
   double acc[6] = {0, 0, 0, 0, 0, 0};  // KEt, KEr, Px, Py, Pz, contacts
-  for (int t = threadIdx.x; t < B.nlive; t += blockDim.x) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < B.nlive;
+       t += gridDim.x * blockDim.x) {
     int s = B.pbase + t;
     V4 vm = ((const V4*)b.vel)[s];
     V4 wr = ((const V4*)b.omg)[s];
@@ -1681,7 +1685,15 @@ __global__ void k_stats(Dev d, PState b, const int* oc, int box, double* out) {
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int q = 0; q < 6; ++q) out[q] = sh[q][0];
+    for (int q = 0; q < 6; ++q) part[6 * blockIdx.x + q] = sh[q][0];
+}
+
+__global__ void k_stats_final(const double* part, int nparts, double* out) {
+  const int q = threadIdx.x;
+  if (q >= 6) return;
+  double s = 0.0;
+  for (int k = 0; k < nparts; ++k) s += part[6 * k + q];
+  out[q] = s;
 }
 
 }  // namespace dem
