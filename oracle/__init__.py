@@ -19,6 +19,21 @@ PRED_FIXED_F32 = 1
 PRED_ABS_F32 = 2
 
 
+WALL_RECT, WALL_LINE = 0, 1
+
+
+class Wall(C.Structure):
+    """Rectangle p + s u + t v (u perpendicular to v) or segment p + s u,
+    s, t in [0, 1]."""
+    _fields_ = [
+        ("kind", C.c_int32),
+        ("pad", C.c_int32),
+        ("p", C.c_double * 3),
+        ("u", C.c_double * 3),
+        ("v", C.c_double * 3),
+    ]
+
+
 class Params(C.Structure):
     _fields_ = [
         ("L", C.c_double * 3),
@@ -36,6 +51,8 @@ class Params(C.Structure):
         ("kn_literal", C.c_int32),
         ("brute_force", C.c_int32),
         ("stencil", C.c_int32),
+        ("nwalls", C.c_int32),
+        ("walls", C.POINTER(Wall)),
     ]
 
 
@@ -92,9 +109,11 @@ def lib():
 def make_params(L, dt, E=3e9, poisson=0.3, density=1200.0, restitution=0.5,
                 mu_d=0.3, periodic=(1, 1, 1), floor_wall=0, g=(0.0, 0.0, 0.0),
                 ncell=None, predicate=PRED_FP64, kn_literal=0,
-                brute_force=0, r_max=None, stencil=1) -> Params:
+                brute_force=0, r_max=None, stencil=1, walls=()) -> Params:
     """Fill a Params struct.  ``ncell`` defaults to the largest grid whose
-    cells are at least 2 r_max (1 + 1e-5) / stencil wide."""
+    cells are at least 2 r_max (1 + 1e-5) / stencil wide.  ``walls``: a
+    sequence of (kind, p, u, v) with kind WALL_RECT or WALL_LINE (v unused
+    for a line)."""
     p = Params()
     L = [float(v) for v in (L if np.ndim(L) else (L, L, L))]
     for a in range(3):
@@ -119,6 +138,18 @@ def make_params(L, dt, E=3e9, poisson=0.3, density=1200.0, restitution=0.5,
     p.kn_literal = int(kn_literal)
     p.brute_force = int(brute_force)
     p.stencil = int(stencil)
+    walls = list(walls)
+    p.nwalls = len(walls)
+    if walls:
+        arr = (Wall * len(walls))()
+        for k, (kind, pw, uw, vw) in enumerate(walls):
+            arr[k].kind = int(kind)
+            for a in range(3):
+                arr[k].p[a] = float(pw[a])
+                arr[k].u[a] = float(uw[a])
+                arr[k].v[a] = float(vw[a]) if vw is not None else 0.0
+        p.walls = C.cast(arr, C.POINTER(Wall))
+        p._walls_keepalive = arr  # the struct only holds a pointer
     return p
 
 
@@ -171,7 +202,7 @@ def contacts(p: Params, x: np.ndarray, r: np.ndarray, cap: int | None = None):
 class State:
     """Particle state in id order plus the contact history."""
 
-    def __init__(self, x, v, w, r, floor_wall=False):
+    def __init__(self, x, v, w, r, floor_wall=False, nwalls=0):
         self.x = np.array(x, dtype=np.float64, order="C")
         self.v = np.array(v, dtype=np.float64, order="C")
         self.w = np.array(w, dtype=np.float64, order="C")
@@ -180,7 +211,9 @@ class State:
         self.lo = np.zeros(0, np.int32)
         self.hi = np.zeros(0, np.int32)
         self.dt = np.zeros((0, 3), np.float64)
-        self.wall_dt = np.zeros((n, 3), np.float64) if floor_wall else None
+        nw = (1 if floor_wall else 0) + int(nwalls)
+        # per particle and wall (the floor first): delta_t history
+        self.wall_dt = np.zeros((n, nw, 3), np.float64) if nw else None
 
     @property
     def n(self):

@@ -529,6 +529,34 @@ static int64_t find_history(int64_t nc, const int32_t* lo, const int32_t* hi,
   return -1;
 }
 
+/* Overlap of a particle (centre c, radius r) with a rectangle or line wall:
+ * q = the wall's point closest to c (coordinates along the edges clamped to
+ * [0, 1]), n = (q - c) / |q - c| (from the particle to the wall), returns
+ * r - |q - c|.  A centre lying on the wall has no normal: no contact. */
+static double wall_overlap(const orc_wall* wl, const double c[3], double r,
+                           double n[3]) {
+  double d[3], q[3], e[3], s, t = 0.0, dist;
+  int a;
+  for (a = 0; a < 3; ++a) d[a] = c[a] - wl->p[a];
+  s = dot3(d, wl->u) / dot3(wl->u, wl->u);
+  s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+  if (wl->kind == ORC_WALL_RECT) {
+    t = dot3(d, wl->v) / dot3(wl->v, wl->v);
+    t = t < 0.0 ? 0.0 : (t > 1.0 ? 1.0 : t);
+  }
+  for (a = 0; a < 3; ++a) {
+    q[a] = wl->p[a] + s * wl->u[a] + (wl->kind == ORC_WALL_RECT ? t * wl->v[a] : 0.0);
+    e[a] = q[a] - c[a];
+  }
+  dist = norm3(e);
+  if (!(dist > 0.0)) {
+    n[0] = n[1] = n[2] = 0.0;
+    return 0.0;
+  }
+  for (a = 0; a < 3; ++a) n[a] = e[a] / dist;
+  return r - dist;
+}
+
 /* Periodic wrap into [0, L). */
 static double wrap(double x, double L) {
   while (x >= L) x -= L;
@@ -600,25 +628,41 @@ int orc_step(const orc_params* p, int64_t n, double* x, double* v, double* w,
   }
   *nc_out = nc;
 
-  /* floor wall at z = 0: a particle of infinite radius and mass at rest */
-  if (p->floor_wall) {
+  /* walls: the floor z = 0, then rectangles and lines, each a particle of
+   * infinite radius and mass at rest touching the particle at the wall's
+   * point closest to its centre (Sec. 3.3 item 5) */
+  {
     static const double zero3[3] = {0.0, 0.0, 0.0};
-    static const double nwall[3] = {0.0, 0.0, -1.0};
-    for (i = 0; i < n; ++i) {
-      double dn = r[i] - x[3 * i + 2];
-      if (dn > 0.0) {
-        double dto[3], dtn[3];
-        orc_contact_info ci;
-        for (a = 0; a < 3; ++a) dto[a] = wall_dt ? wall_dt[3 * i + a] : 0.0;
-        contact_force(p, alpha, nwall, dn, r[i], 0.0, mass_of(p, r[i]), 0.0,
-                      &v[3 * i], zero3, &w[3 * i], zero3, dto, dtn, &ci);
-        for (a = 0; a < 3; ++a) {
-          Fp[3 * i + a] += ci.F[a];
-          Tp[3 * i + a] += r[i] * ci.nF[a];
-          if (wall_dt) wall_dt[3 * i + a] = dtn[a];
+    const int nw = (p->floor_wall ? 1 : 0) + p->nwalls;
+    int wi;
+    for (wi = 0; wi < nw; ++wi) {
+      const int floor = p->floor_wall && wi == 0;
+      const orc_wall* wl = floor ? NULL : &p->walls[wi - (p->floor_wall ? 1 : 0)];
+      for (i = 0; i < n; ++i) {
+        double nwall[3], dn;
+        double* hist = wall_dt ? &wall_dt[3 * (i * nw + wi)] : NULL;
+        if (floor) {
+          nwall[0] = 0.0;
+          nwall[1] = 0.0;
+          nwall[2] = -1.0;
+          dn = r[i] - x[3 * i + 2];
+        } else {
+          dn = wall_overlap(wl, &x[3 * i], r[i], nwall);
         }
-      } else if (wall_dt) {
-        for (a = 0; a < 3; ++a) wall_dt[3 * i + a] = 0.0;
+        if (dn > 0.0) {
+          double dto[3], dtn[3];
+          orc_contact_info ci;
+          for (a = 0; a < 3; ++a) dto[a] = hist ? hist[a] : 0.0;
+          contact_force(p, alpha, nwall, dn, r[i], 0.0, mass_of(p, r[i]), 0.0,
+                        &v[3 * i], zero3, &w[3 * i], zero3, dto, dtn, &ci);
+          for (a = 0; a < 3; ++a) {
+            Fp[3 * i + a] += ci.F[a];
+            Tp[3 * i + a] += r[i] * ci.nF[a];
+            if (hist) hist[a] = dtn[a];
+          }
+        } else if (hist) {
+          for (a = 0; a < 3; ++a) hist[a] = 0.0;
+        }
       }
     }
   }

@@ -17,8 +17,10 @@
  *                  delta_t reset, torque T = r (n x F)
  *   history        delta_t kept per pair and erased when a pair separates
  *                  (Sec. 4.2, kernel "InitializeContactIDs")
- *   walls          flat floor z = 0 treated like a particle of infinite
- *                  radius and mass (Sec. 3.3 item 5, "CollideRectangle")
+ *   walls          flat floor z = 0, rectangles and straight line segments,
+ *                  each treated like a particle of infinite radius and mass
+ *                  at rest (Sec. 3.3 item 5; kernels "CollideRectangle" and
+ *                  "CollideLine" of Sec. 4.2)
  *   gravity        m g (Sec. 4.2, "ForceGravity")
  *   integration    symplectic Euler (Sec. 4.2 "Integrate"; scheme unstated)
  *   alpha(eps)     exact inversion of the restitution of the paper's own
@@ -46,6 +48,19 @@ enum {
   ORC_PRED_ABS_F32 = 2     /* FP32 absolute position, FP32 minimum image  */
 };
 
+/* A wall (Sec. 3.3 item 5: rectangles and straight lines).
+ *   ORC_WALL_RECT  the rectangle p + s u + t v, s, t in [0, 1], u and v
+ *                  perpendicular; a particle touches its closest point
+ *                  (face, edge or corner)
+ *   ORC_WALL_LINE  the segment p + s u, s in [0, 1]
+ * Walls are not repeated across periodic boundaries. */
+enum { ORC_WALL_RECT = 0, ORC_WALL_LINE = 1 };
+typedef struct {
+  int32_t kind;
+  int32_t pad;
+  double p[3], u[3], v[3];
+} orc_wall;
+
 typedef struct {
   double L[3];          /* box edge lengths [m]; box is [0, L)            */
   double g[3];          /* gravitational acceleration [m/s^2]            */
@@ -63,6 +78,8 @@ typedef struct {
   int32_t brute_force;  /* 1 = O(N^2) pair search instead of cells        */
   int32_t stencil;      /* neighbour cells searched per axis: +-stencil   */
                         /* (cells at least 2 r_max / stencil wide; 0 = 1) */
+  int32_t nwalls;       /* rectangle and line walls                       */
+  const orc_wall* walls;
 } orc_params;
 
 /* Per-contact diagnostics, one record per contact of the new list. */
@@ -98,7 +115,8 @@ int64_t orc_contacts(const orc_params* p, int64_t n, const double* x,
 
 /* One time step in place on x, v, w (n x 3 each, id order).
  *   in:  contact history (nc_in pairs sorted by (lo, hi)) with delta_t
- *        (nc_in x 3); wall_dt (n x 3, may be NULL when there is no floor)
+ *        (nc_in x 3); wall_dt (n x nw x 3 with nw = floor_wall + nwalls,
+ *        the floor first, then the walls in order; may be NULL when nw = 0)
  *   out: new contact list and delta_t (sorted by (lo, hi)), per-contact
  *        info (may be NULL), per-particle force F and torque T used in the
  *        step (n x 3 each, may be NULL).
