@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define DEM_ABI_VERSION 1
+#define DEM_ABI_VERSION 2
 
 typedef enum {
   DEM_OK = 0,
@@ -101,8 +101,28 @@ typedef struct {
   double mu_d;         /* sliding friction coefficient, >= 0    */
 } dem_material;
 
+/* A wall (Sec. 3.3 item 5: rectangles and straight lines; Sec. 4.2 kernels
+ * CollideRectangle and CollideLine).  A wall is a body of infinite radius
+ * and mass at rest of the box's material; a particle touches it at the
+ * wall's point closest to its centre, and the force is that of a
+ * particle-particle contact with R* = r and m* = m.  Each particle keeps a
+ * tangential history per wall.  Walls are not repeated across periodic
+ * boundaries.
+ *   DEM_WALL_RECT : the rectangle p + s u + t v, s and t in [0, 1]; u and v
+ *                   must be perpendicular (|u.v| <= 1e-9 |u||v|)
+ *   DEM_WALL_LINE : the segment p + s u, s in [0, 1] (v unused) */
+typedef enum { DEM_WALL_RECT = 0, DEM_WALL_LINE = 1 } dem_wall_kind;
+typedef struct {
+  int32_t kind;        /* dem_wall_kind                                */
+  int32_t pad;
+  double p[3];         /* corner / first end [m]                       */
+  double u[3];         /* first edge / segment [m], non-zero           */
+  double v[3];         /* second edge [m] (rectangles)                 */
+} dem_wall;
+
 /* One independent box.  Periodic axes wrap positions into [0, L).
- * Non-periodic axes are open; floor_wall adds a flat wall at z = 0. */
+ * Non-periodic axes are open; floor_wall adds a flat wall at z = 0, walls
+ * adds rectangles and lines (at most 15 per box, floor included). */
 typedef struct {
   double L[3];            /* edge lengths [m], > 0                        */
   int32_t periodic[3];    /* 1 = periodic                                 */
@@ -114,6 +134,8 @@ typedef struct {
                           /* least 2 r_max (1 + 1e-5) wide                 */
   int64_t max_particles;  /* capacity of the box                          */
   double r_max;           /* largest radius the box will hold [m]         */
+  int32_t nwalls;         /* rectangle and line walls (0 = none)           */
+  const dem_wall* walls;  /* nwalls entries, read during dem_create        */
 } dem_box;
 
 typedef struct {

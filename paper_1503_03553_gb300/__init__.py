@@ -42,11 +42,20 @@ class dem_material(C.Structure):
                 ("restitution", C.c_double), ("mu_d", C.c_double)]
 
 
+class dem_wall(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("p", C.c_double * 3),
+                ("u", C.c_double * 3), ("v", C.c_double * 3)]
+
+
+DEM_WALL_RECT, DEM_WALL_LINE = 0, 1
+
+
 class dem_box(C.Structure):
     _fields_ = [("L", C.c_double * 3), ("periodic", C.c_int32 * 3),
                 ("floor_wall", C.c_int32), ("g", C.c_double * 3), ("dt", C.c_double),
                 ("material", C.c_int32), ("ncell", C.c_int32 * 3),
-                ("max_particles", C.c_int64), ("r_max", C.c_double)]
+                ("max_particles", C.c_int64), ("r_max", C.c_double),
+                ("nwalls", C.c_int32), ("walls", C.POINTER(dem_wall))]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -363,6 +372,18 @@ class Context:
             bx.material = k
             bx.max_particles = int(capacities[k]) if capacities is not None else int(g("n"))
             bx.r_max = float(r_max[k]) if r_max is not None else float(g("r_max"))
+            walls = list(g("walls", ()) or ())
+            bx.nwalls = len(walls)
+            if walls:
+                arr = (dem_wall * len(walls))()
+                for q, (kind, pw, uw, vw) in enumerate(walls):
+                    arr[q].kind = int(kind)
+                    for a in range(3):
+                        arr[q].p[a] = float(pw[a])
+                        arr[q].u[a] = float(uw[a])
+                        arr[q].v[a] = float(vw[a]) if vw is not None else 0.0
+                bx.walls = C.cast(arr, C.POINTER(dem_wall))
+                self._wall_arrays = getattr(self, "_wall_arrays", []) + [arr]
         cfg = dem_config()
         cfg.nboxes = nb
         cfg.boxes = self._boxes

@@ -29,6 +29,17 @@ enum : unsigned {
   kStRange = 16u,          // fixed-point position out of range
 };
 
+// A rectangle (p + s u + t v) or line (p + s u) wall, s, t in [0, 1]: the
+// geometry in FP64 for the contact and in FP32 for a conservative cull.
+struct WallDev {
+  int kind;             // 0 rectangle, 1 line
+  double p[3], u[3], v[3];
+  double inv_uu, inv_vv;  // 1 / u.u, 1 / v.v (0 for a line)
+  float pf[3], uf[3], vf[3];
+  float inv_uuf, inv_vvf;
+  float slack;          // cull margin [m]: far above the FP32 geometry error
+};
+
 // Per-box constants, filled on the host at creation.
 struct BoxDev {
   long long Lq[3];      // box length in quanta
@@ -46,6 +57,8 @@ struct BoxDev {
   int n[3];             // cells per axis
   int periodic[3];
   int floor_wall;
+  int nwalls;           // rectangle and line walls
+  int wall_base;        // first of them in the context's wall array
   int lin_base;         // first cell of this box in linear-cell space
   int rank_base;        // first cell in rank space (ncells + 1: last is the
                         // box's "free slot" cell holding unused capacity)

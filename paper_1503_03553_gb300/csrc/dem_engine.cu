@@ -65,6 +65,8 @@ struct dem_ctx {
   unsigned char* dirty[2]{};   // changed-cell flags read by a step of parity 0 / 1
   int parity = 0;
   bool any_floor = false;
+  int nwh = 0;                   // wall histories per slot (largest box)
+  std::vector<WallDev> hwalls;   // all boxes' rectangle and line walls
   bool have_particles = false;
   bool have_ft = false;
   std::vector<char> hist_cleared;  // per box: history dropped by set_particles
@@ -372,6 +374,41 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     B.floor_wall = bx.floor_wall ? 1 : 0;
     B.rmax_f = (float)bx.r_max;
     ctx->any_floor |= B.floor_wall != 0;
+    // rectangle and line walls
+    if (bx.nwalls < 0 || (bx.nwalls > 0 && !bx.walls) || B.floor_wall + bx.nwalls > 15)
+      return bail(DEM_ERR_ARG, "a box holds 0 to 15 walls (floor included), listed in walls");
+    B.nwalls = bx.nwalls;
+    B.wall_base = (int)ctx->hwalls.size();
+    for (int k = 0; k < bx.nwalls; ++k) {
+      const dem_wall& w = bx.walls[k];
+      auto dot = [](const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; };
+      const double uu = dot(w.u, w.u), vv = dot(w.v, w.v);
+      const bool ok_kind = w.kind == DEM_WALL_RECT || w.kind == DEM_WALL_LINE;
+      const bool finite = std::isfinite(uu) && std::isfinite(vv) && std::isfinite(dot(w.p, w.p));
+      if (!ok_kind || !finite || !(uu > 0) ||
+          (w.kind == DEM_WALL_RECT && (!(vv > 0) || std::fabs(dot(w.u, w.v)) > 1e-9 * std::sqrt(uu * vv))))
+        return bail(DEM_ERR_ARG, "wall: kind RECT or LINE, non-zero edges, rectangle edges perpendicular");
+      WallDev W{};
+      W.kind = w.kind == DEM_WALL_RECT ? 0 : 1;
+      for (int a = 0; a < 3; ++a) {
+        W.p[a] = w.p[a];
+        W.u[a] = w.u[a];
+        W.v[a] = W.kind == 0 ? w.v[a] : 0.0;
+        W.pf[a] = (float)W.p[a];
+        W.uf[a] = (float)W.u[a];
+        W.vf[a] = (float)W.v[a];
+      }
+      W.inv_uu = 1.0 / uu;
+      W.inv_vv = W.kind == 0 ? 1.0 / vv : 0.0;
+      W.inv_uuf = (float)W.inv_uu;
+      W.inv_vvf = (float)W.inv_vv;
+      // FP32 geometry errs by a few ulps of the coordinates involved
+      const double span = std::sqrt(dot(w.p, w.p)) + std::sqrt(uu) + (W.kind == 0 ? std::sqrt(vv) : 0.0) +
+                          std::max(bx.L[0], std::max(bx.L[1], bx.L[2]));
+      W.slack = (float)(1e-5 * span + 1e-3 * bx.r_max);
+      ctx->hwalls.push_back(W);
+    }
+    ctx->nwh = std::max(ctx->nwh, B.floor_wall + B.nwalls);
     B.ncells = (int)ncell;
     B.lin_base = (int)Mlin;
     B.rank_base = (int)Mrank;
@@ -445,6 +482,8 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     return p;
   };
   d.boxes = (const BoxDev*)A(sizeof(BoxDev) * ctx->hbox.size());
+  d.walls = ctx->hwalls.empty() ? nullptr : (const WallDev*)A(sizeof(WallDev) * ctx->hwalls.size());
+  d.nwh = ctx->nwh;
   d.slot_box = (const int*)A(sizeof(int) * n);
   d.rank_of_lin = (const int*)A(sizeof(int) * std::max(1, ctx->M_lin));
   d.lin_of_rank = (const int*)A(sizeof(int) * std::max(1, ctx->M_rank));
@@ -486,10 +525,10 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     s.cellc = (int*)A(sizeof(int) * n);
     s.cellx = (int*)A(sizeof(int) * n);
     s.cellg = (int*)A(sizeof(int) * n);
-    if (ctx->any_floor) {
-      s.wx = A(dt_bytes(M) * n);
-      s.wy = A(dt_bytes(M) * n);
-      s.wz = A(dt_bytes(M) * n);
+    if (ctx->nwh > 0) {
+      s.wx = A(dt_bytes(M) * n * ctx->nwh);
+      s.wy = A(dt_bytes(M) * n * ctx->nwh);
+      s.wz = A(dt_bytes(M) * n * ctx->nwh);
     }
     CList& c = ctx->cl[p];
     c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
@@ -528,6 +567,8 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   };
   cudaError_t e = cudaSuccess;
   if (!e) e = H2D(d.boxes, ctx->hbox.data(), sizeof(BoxDev) * ctx->hbox.size());
+  if (!e && !ctx->hwalls.empty())
+    e = H2D(d.walls, ctx->hwalls.data(), sizeof(WallDev) * ctx->hwalls.size());
   if (!e) e = H2D(d.slot_box, slot_box.data(), sizeof(int) * n);
   if (!e) e = H2D(d.rank_of_lin, rol.data(), sizeof(int) * rol.size());
   if (!e) e = H2D(d.lin_of_rank, lor.data(), sizeof(int) * lor.size());

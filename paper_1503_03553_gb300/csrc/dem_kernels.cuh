@@ -17,6 +17,8 @@
 //                                 symplectic Euler (Integrate), next binning
 #pragma once
 
+#include <type_traits>
+
 #include "dem_common.cuh"
 
 namespace dem {
@@ -78,6 +80,8 @@ struct CList {
 
 struct Dev {
   const BoxDev* boxes;
+  const WallDev* walls;  // all boxes' rectangle and line walls
+  int nwh;               // wall histories per slot (floor + walls, largest box)
   const int* slot_box;
   int N;         // slots over all boxes
   int K;         // row capacity per particle
@@ -270,9 +274,12 @@ __global__ void k_set_particles(Dev d, PState s, int box, int n,
   atomicAdd(&d.ccount[g], 1);
   if (s.wx) {
     using DT = typename T::DT;
-    ((DT*)s.wx)[slot] = DT{};
-    ((DT*)s.wy)[slot] = DT{};
-    ((DT*)s.wz)[slot] = DT{};
+    for (int q = 0; q < d.nwh; ++q) {
+      const size_t h = (size_t)slot * d.nwh + q;
+      ((DT*)s.wx)[h] = DT{};
+      ((DT*)s.wy)[h] = DT{};
+      ((DT*)s.wz)[h] = DT{};
+    }
   }
 }
 
@@ -571,9 +578,12 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   b.cellg[t] = g;
   if (a.wx) {
     using DT = typename T::DT;
-    ((DT*)b.wx)[t] = ((const DT*)a.wx)[s];
-    ((DT*)b.wy)[t] = ((const DT*)a.wy)[s];
-    ((DT*)b.wz)[t] = ((const DT*)a.wz)[s];
+    for (int w = 0; w < d.nwh; ++w) {
+      const size_t hs = (size_t)s * d.nwh + w, ht = (size_t)t * d.nwh + w;
+      ((DT*)b.wx)[ht] = ((const DT*)a.wx)[hs];
+      ((DT*)b.wy)[ht] = ((const DT*)a.wy)[hs];
+      ((DT*)b.wz)[ht] = ((const DT*)a.wz)[hs];
+    }
   }
   PR pr;
   if (M == kMIXED) {
@@ -1432,7 +1442,67 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
     Tq = xyz(ld4((const V4*)d.Tfused + i));
   }
   P x = ((P*)b.px)[i], y = ((P*)b.py)[i], z = ((P*)b.pz)[i];
-  // floor wall at z = 0: a body of infinite radius and mass at rest
+  // Walls (Sec. 3.3 item 5): the floor z = 0, rectangles and lines, each a
+  // body of infinite radius and mass at rest (R* = r, m* = m), touching the
+  // particle at its point closest to the particle's centre; the particle
+  // keeps one delta_t per wall (the floor first).
+  DT* wx = (DT*)b.wx;
+  DT* wy = (DT*)b.wy;
+  DT* wz = (DT*)b.wz;
+  auto wall_contact = [&](v3<R> nw, R dn, size_t h) {
+    v3<R> dold;
+    DT ox = wx[h], oy = wy[h], oz = wz[h];
+    if (M == kMIXED) {
+      const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
+                   *fz = (const float2*)&oz;
+      dold = {(R)(fx->x + fx->y), (R)(fy->x + fy->y), (R)(fz->x + fz->y)};
+    } else {
+      dold = {*(const R*)&ox, *(const R*)&oy, *(const R*)&oz};
+    }
+    v3<R> zero = {R(0), R(0), R(0)};
+    ContactOut<R> o;
+    v3<R> incd;
+    R kn_c = M == kFP64 ? (R)B.kn_c : (R)B.kn_cf;
+    R kt_c = M == kFP64 ? (R)B.kt_c : (R)B.kt_cf;
+    R al = M == kFP64 ? (R)B.alpha : (R)B.alpha_f;
+    R mu = M == kFP64 ? (R)B.mu : (R)B.mu_f;
+    R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
+    contact_law<R>(kn_c, kt_c, al, mu, dts, nw, dn, r, R(0), m, R(0),
+                   xyz(vm), zero, xyz(wr), zero, dold, true, o, incd);
+    F = F + o.F;
+    Tq = Tq + r * o.nF;
+    if (M == kMIXED) {
+      float2 qx, qy, qz;
+      if (o.capped) {
+        qx = make_float2((float)o.dt.x, 0.f);
+        qy = make_float2((float)o.dt.y, 0.f);
+        qz = make_float2((float)o.dt.z, 0.f);
+      } else {
+        const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
+                     *fz = (const float2*)&oz;
+        ff ax = ff_add_f({fx->x, fx->y}, (float)incd.x);
+        ff ay = ff_add_f({fy->x, fy->y}, (float)incd.y);
+        ff az = ff_add_f({fz->x, fz->y}, (float)incd.z);
+        qx = make_float2(ax.hi, ax.lo);
+        qy = make_float2(ay.hi, ay.lo);
+        qz = make_float2(az.hi, az.lo);
+      }
+      wx[h] = *(DT*)&qx;
+      wy[h] = *(DT*)&qy;
+      wz[h] = *(DT*)&qz;
+    } else {
+      R tx = o.dt.x, ty = o.dt.y, tz = o.dt.z;
+      wx[h] = *(DT*)&tx;
+      wy[h] = *(DT*)&ty;
+      wz[h] = *(DT*)&tz;
+    }
+  };
+  auto wall_clear = [&](size_t h) {
+    wx[h] = DT{};
+    wy[h] = DT{};
+    wz[h] = DT{};
+  };
+  const size_t hbase = (size_t)i * d.nwh;
   if (B.floor_wall) {
     R dn;
     if (M == kMIXED) {
@@ -1444,61 +1514,74 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
     } else {
       dn = r - (R)z;
     }
-    DT* wx = (DT*)b.wx;
-    DT* wy = (DT*)b.wy;
-    DT* wz = (DT*)b.wz;
-    if (dn > R(0)) {
-      v3<R> dold;
-      DT ox = wx[i], oy = wy[i], oz = wz[i];
-      if (M == kMIXED) {
-        const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
-                     *fz = (const float2*)&oz;
-        dold = {(R)(fx->x + fx->y), (R)(fy->x + fy->y), (R)(fz->x + fz->y)};
-      } else {
-        dold = {*(const R*)&ox, *(const R*)&oy, *(const R*)&oz};
-      }
-      v3<R> nw = {R(0), R(0), R(-1)};
-      v3<R> zero = {R(0), R(0), R(0)};
-      ContactOut<R> o;
-      v3<R> incd;
-      R kn_c = M == kFP64 ? (R)B.kn_c : (R)B.kn_cf;
-      R kt_c = M == kFP64 ? (R)B.kt_c : (R)B.kt_cf;
-      R al = M == kFP64 ? (R)B.alpha : (R)B.alpha_f;
-      R mu = M == kFP64 ? (R)B.mu : (R)B.mu_f;
-      R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
-      contact_law<R>(kn_c, kt_c, al, mu, dts, nw, dn, r, R(0), m, R(0),
-                     xyz(vm), zero, xyz(wr), zero, dold, true, o, incd);
-      F = F + o.F;
-      Tq = Tq + r * o.nF;
-      if (M == kMIXED) {
-        float2 qx, qy, qz;
-        if (o.capped) {
-          qx = make_float2((float)o.dt.x, 0.f);
-          qy = make_float2((float)o.dt.y, 0.f);
-          qz = make_float2((float)o.dt.z, 0.f);
-        } else {
-          const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
-                       *fz = (const float2*)&oz;
-          ff ax = ff_add_f({fx->x, fx->y}, (float)incd.x);
-          ff ay = ff_add_f({fy->x, fy->y}, (float)incd.y);
-          ff az = ff_add_f({fz->x, fz->y}, (float)incd.z);
-          qx = make_float2(ax.hi, ax.lo);
-          qy = make_float2(ay.hi, ay.lo);
-          qz = make_float2(az.hi, az.lo);
-        }
-        wx[i] = *(DT*)&qx;
-        wy[i] = *(DT*)&qy;
-        wz[i] = *(DT*)&qz;
-      } else {
-        R tx = o.dt.x, ty = o.dt.y, tz = o.dt.z;
-        wx[i] = *(DT*)&tx;
-        wy[i] = *(DT*)&ty;
-        wz[i] = *(DT*)&tz;
-      }
+    if (dn > R(0)) wall_contact({R(0), R(0), R(-1)}, dn, hbase);
+    else wall_clear(hbase);
+  }
+  if (B.nwalls > 0) {
+    // centre in FP32 (cull) and in the geometry precision (FP64 unless FP32)
+    float cf[3];
+    if (M == kMIXED) {
+      cf[0] = __fmul_rn(i64_to_f32_rn((long long)x), kQ);
+      cf[1] = __fmul_rn(i64_to_f32_rn((long long)y), kQ);
+      cf[2] = __fmul_rn(i64_to_f32_rn((long long)z), kQ);
     } else {
-      wx[i] = DT{};
-      wy[i] = DT{};
-      wz[i] = DT{};
+      cf[0] = (float)x;
+      cf[1] = (float)y;
+      cf[2] = (float)z;
+    }
+    for (int k = 0; k < B.nwalls; ++k) {
+      const WallDev& Wl = d.walls[B.wall_base + k];
+      const size_t h = hbase + (B.floor_wall ? 1 : 0) + k;
+      // conservative FP32 cull: farther than r + slack cannot touch
+      float e2f;
+      {
+        float df[3], qf[3];
+        for (int a = 0; a < 3; ++a) df[a] = cf[a] - Wl.pf[a];
+        float sf = (df[0] * Wl.uf[0] + df[1] * Wl.uf[1] + df[2] * Wl.uf[2]) * Wl.inv_uuf;
+        sf = fminf(fmaxf(sf, 0.0f), 1.0f);
+        float tf = 0.0f;
+        if (Wl.kind == 0) {
+          tf = (df[0] * Wl.vf[0] + df[1] * Wl.vf[1] + df[2] * Wl.vf[2]) * Wl.inv_vvf;
+          tf = fminf(fmaxf(tf, 0.0f), 1.0f);
+        }
+        for (int a = 0; a < 3; ++a) qf[a] = Wl.pf[a] + sf * Wl.uf[a] + tf * Wl.vf[a] - cf[a];
+        e2f = qf[0] * qf[0] + qf[1] * qf[1] + qf[2] * qf[2];
+      }
+      const float reachf = (float)r + Wl.slack;
+      if (!(e2f <= reachf * reachf)) {
+        wall_clear(h);
+        continue;
+      }
+      // the contact geometry (FP64 unless FP32), as the oracle writes it
+      using G = typename std::conditional<M == kFP32, float, double>::type;
+      G c[3];
+      if (M == kMIXED) {
+        c[0] = (G)__ll2double_rn((long long)x) * 0x1p-60;
+        c[1] = (G)__ll2double_rn((long long)y) * 0x1p-60;
+        c[2] = (G)__ll2double_rn((long long)z) * 0x1p-60;
+      } else {
+        c[0] = (G)x;
+        c[1] = (G)y;
+        c[2] = (G)z;
+      }
+      G dd[3], e[3];
+      for (int a = 0; a < 3; ++a) dd[a] = c[a] - (G)Wl.p[a];
+      G sw = (dd[0] * (G)Wl.u[0] + dd[1] * (G)Wl.u[1] + dd[2] * (G)Wl.u[2]) * (G)Wl.inv_uu;
+      sw = sw < G(0) ? G(0) : (sw > G(1) ? G(1) : sw);
+      G tw = G(0);
+      if (Wl.kind == 0) {
+        tw = (dd[0] * (G)Wl.v[0] + dd[1] * (G)Wl.v[1] + dd[2] * (G)Wl.v[2]) * (G)Wl.inv_vv;
+        tw = tw < G(0) ? G(0) : (tw > G(1) ? G(1) : tw);
+      }
+      for (int a = 0; a < 3; ++a) e[a] = (G)Wl.p[a] + sw * (G)Wl.u[a] + tw * (G)Wl.v[a] - c[a];
+      const G dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+      const G dnw = (G)r - dist;
+      if (dist > G(0) && dnw > G(0)) {
+        const G inv = G(1) / dist;
+        wall_contact({(R)(e[0] * inv), (R)(e[1] * inv), (R)(e[2] * inv)}, (R)dnw, h);
+      } else {
+        wall_clear(h);
+      }
     }
   }
   // gravity (ForceGravity)

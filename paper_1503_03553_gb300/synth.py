@@ -62,6 +62,7 @@ class Box:
     density: float = DENSITY_DEFAULT
     restitution: float = 0.5
     mu_d: float = 0.3
+    walls: tuple = ()        # (kind, p, u, v): 0 = rectangle, 1 = line
 
     @property
     def n(self) -> int:

@@ -72,7 +72,7 @@ def oracle_params(box, precision, ncell, brute_force=0, stencil=STENCIL):
                          mu_d=box.mu_d, periodic=box.periodic,
                          floor_wall=box.floor_wall, g=box.g, ncell=ncell,
                          predicate=PRED[precision], brute_force=brute_force,
-                         stencil=stencil)
+                         stencil=stencil, walls=getattr(box, "walls", ()))
 
 
 def gpu_run(boxes, precision, ncells, steps=1, stencil=STENCIL, **kw):
@@ -102,7 +102,8 @@ def gpu_run(boxes, precision, ncells, steps=1, stencil=STENCIL, **kw):
 def oracle_run(box, precision, ncell, stencil=STENCIL):
     p = oracle_params(box, precision, ncell, stencil=stencil)
     cell, order = O.order(p, box.x)
-    s = O.State(box.x, box.v, box.w, box.r, floor_wall=bool(box.floor_wall))
+    s = O.State(box.x, box.v, box.w, box.r, floor_wall=bool(box.floor_wall),
+                nwalls=len(getattr(box, "walls", ())))
     x0, v0, w0 = s.x.copy(), s.v.copy(), s.w.copy()
     out = O.step(p, s)
     out.update(order=order, cell=cell, x=s.x, v=s.v, w=s.w, x0=x0, v0=v0, w0=w0,
@@ -194,7 +195,7 @@ def check_one_step(box, g, o, precision, allow_dont_care=True):
     mass = box.density * 4.0 / 3.0 * math.pi * box.r ** 3
     gmag = float(np.linalg.norm(box.g))
     bP += 1e-6 * mass * gmag + 1e-300
-    if box.floor_wall:
+    if box.floor_wall or len(getattr(box, "walls", ())):
         # wall contacts: k_n r^1.5 dn^1.5 scale, bounded via the force itself
         bP += 1e-5 * np.linalg.norm(o["F"], axis=1) + 1e-5 * mass * gmag
     if dont.any():
