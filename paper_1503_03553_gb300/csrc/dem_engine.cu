@@ -134,7 +134,9 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
   return spread(x) | (spread(y) << 1) | (spread(z) << 2);
 }
 
-int launches_per_step(const dem_ctx* ctx) { return ctx->fused ? 7 : 8; }
+int launches_per_step(const dem_ctx* ctx) {
+  return (ctx->fused ? 7 : 8) + (ctx->hwalls.empty() ? 0 : 1);
+}
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -186,6 +188,7 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
       cudaEventRecord(ev[3], s);
       cudaEventRecord(ev[4], s);
     }
+    if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
     k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q],
                                                             store_ft ? 1 : 0);
     if (tm) cudaEventRecord(ev[5], s);
@@ -203,6 +206,7 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   k_force<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[p], ctx->cl[q]);
   if (tm) cudaEventRecord(ev[4], s);
   // 6. sum, wall, gravity, integrate, bin
+  if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
   k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q],
                                                           store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
@@ -507,6 +511,10 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     d.Tfused = A(v4_bytes(M) * n);
   } else {
     d.inrow = (int*)A(sizeof(int) * n * ctx->K);
+  }
+  if (!ctx->hwalls.empty()) {
+    d.Fwall = A(v4_bytes(M) * n);
+    d.Twall = A(v4_bytes(M) * n);
   }
   d.Fout = A(v4_bytes(M) * n);
   d.Tout = A(v4_bytes(M) * n);

@@ -109,6 +109,8 @@ struct Dev {
   void* nFc;     // V4 per contact: n x F
   void* Ffused;  // V4 per slot: contact force sum of the fused layout
   void* Tfused;  // V4 per slot: contact torque sum of the fused layout
+  void* Fwall;   // V4 per slot: rectangle and line walls' force (k_walls)
+  void* Twall;   // V4 per slot: their torque
   void* Fout;    // V4 per slot: total force of the last step
   void* Tout;    // V4 per slot: total torque of the last step
   unsigned* status;
@@ -1341,6 +1343,166 @@ k_collide_per_particle(Dev d, PState b, CList co, CList cn, int ko) {
 }
 
 // ---------------------------------------------------------------------------
+// walls: one particle-wall contact of Eq. (1) with the wall as a body of
+// infinite radius and mass at rest, its delta_t kept in the particle's slot
+// h of the wall histories (float-float in DEM_MIXED)
+// ---------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ void wall_force(const Dev& d, const PState& b, const BoxDev& B,
+                                           size_t h, v3<typename Tr<M>::R> nw,
+                                           typename Tr<M>::R dn, const typename Tr<M>::V4& vm,
+                                           const typename Tr<M>::V4& wr,
+                                           v3<typename Tr<M>::R>& F, v3<typename Tr<M>::R>& Tq) {
+  using T = Tr<M>;
+  using R = typename T::R;
+  using DT = typename T::DT;
+  DT* wx = (DT*)b.wx;
+  DT* wy = (DT*)b.wy;
+  DT* wz = (DT*)b.wz;
+  const R m = vm.w, r = wr.w;
+  v3<R> dold;
+  DT ox = wx[h], oy = wy[h], oz = wz[h];
+  if (M == kMIXED) {
+    const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy, *fz = (const float2*)&oz;
+    dold = {(R)(fx->x + fx->y), (R)(fy->x + fy->y), (R)(fz->x + fz->y)};
+  } else {
+    dold = {*(const R*)&ox, *(const R*)&oy, *(const R*)&oz};
+  }
+  v3<R> zero = {R(0), R(0), R(0)};
+  ContactOut<R> o;
+  v3<R> incd;
+  R kn_c = M == kFP64 ? (R)B.kn_c : (R)B.kn_cf;
+  R kt_c = M == kFP64 ? (R)B.kt_c : (R)B.kt_cf;
+  R al = M == kFP64 ? (R)B.alpha : (R)B.alpha_f;
+  R mu = M == kFP64 ? (R)B.mu : (R)B.mu_f;
+  R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
+  contact_law<R>(kn_c, kt_c, al, mu, dts, nw, dn, r, R(0), m, R(0), xyz(vm), zero, xyz(wr),
+                 zero, dold, true, o, incd);
+  F = F + o.F;
+  Tq = Tq + r * o.nF;
+  if (M == kMIXED) {
+    float2 qx, qy, qz;
+    if (o.capped) {
+      qx = make_float2((float)o.dt.x, 0.f);
+      qy = make_float2((float)o.dt.y, 0.f);
+      qz = make_float2((float)o.dt.z, 0.f);
+    } else {
+      const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy, *fz = (const float2*)&oz;
+      ff ax = ff_add_f({fx->x, fx->y}, (float)incd.x);
+      ff ay = ff_add_f({fy->x, fy->y}, (float)incd.y);
+      ff az = ff_add_f({fz->x, fz->y}, (float)incd.z);
+      qx = make_float2(ax.hi, ax.lo);
+      qy = make_float2(ay.hi, ay.lo);
+      qz = make_float2(az.hi, az.lo);
+    }
+    wx[h] = *(DT*)&qx;
+    wy[h] = *(DT*)&qy;
+    wz[h] = *(DT*)&qz;
+  } else {
+    R tx = o.dt.x, ty = o.dt.y, tz = o.dt.z;
+    wx[h] = *(DT*)&tx;
+    wy[h] = *(DT*)&ty;
+    wz[h] = *(DT*)&tz;
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void wall_clear(const PState& b, size_t h) {
+  using DT = typename Tr<M>::DT;
+  ((DT*)b.wx)[h] = DT{};
+  ((DT*)b.wy)[h] = DT{};
+  ((DT*)b.wz)[h] = DT{};
+}
+
+// Rectangle and line walls (CollideRectangle, CollideLine), one thread per
+// particle of a box that has them: the contact point is the wall's point
+// closest to the particle's centre, found first in FP32 (a conservative
+// cull: a particle farther than r + slack cannot touch) and then, for the
+// particles that pass, in the oracle's FP64 arithmetic (FP32 in DEM_FP32).
+// The sum of the walls' forces and torques goes to Fwall / Twall.
+template <int M>
+__global__ void k_walls(Dev d, PState b) {
+  using T = Tr<M>;
+  using P = typename T::P;
+  using R = typename T::R;
+  using V4 = typename T::V4;
+  using G = typename std::conditional<M == kFP32, float, double>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[i]];
+  if (i - B.pbase >= B.nlive || B.nwalls == 0) return;
+  const P x = ((const P*)b.px)[i], y = ((const P*)b.py)[i], z = ((const P*)b.pz)[i];
+  const V4 vm = ld4((const V4*)b.vel + i), wr = ld4((const V4*)b.omg + i);
+  const R r = wr.w;
+  float cf[3];
+  if (M == kMIXED) {
+    cf[0] = __fmul_rn(i64_to_f32_rn((long long)x), kQ);
+    cf[1] = __fmul_rn(i64_to_f32_rn((long long)y), kQ);
+    cf[2] = __fmul_rn(i64_to_f32_rn((long long)z), kQ);
+  } else {
+    cf[0] = (float)x;
+    cf[1] = (float)y;
+    cf[2] = (float)z;
+  }
+  v3<R> F = {R(0), R(0), R(0)}, Tq = {R(0), R(0), R(0)};
+  const size_t hbase = (size_t)i * d.nwh + (B.floor_wall ? 1 : 0);
+  for (int k = 0; k < B.nwalls; ++k) {
+    const WallDev& Wl = d.walls[B.wall_base + k];
+    const size_t h = hbase + k;
+    float e2f;
+    {
+      float df[3], qf[3];
+      for (int a = 0; a < 3; ++a) df[a] = cf[a] - Wl.pf[a];
+      float sf = (df[0] * Wl.uf[0] + df[1] * Wl.uf[1] + df[2] * Wl.uf[2]) * Wl.inv_uuf;
+      sf = fminf(fmaxf(sf, 0.0f), 1.0f);
+      float tf = 0.0f;
+      if (Wl.kind == 0) {
+        tf = (df[0] * Wl.vf[0] + df[1] * Wl.vf[1] + df[2] * Wl.vf[2]) * Wl.inv_vvf;
+        tf = fminf(fmaxf(tf, 0.0f), 1.0f);
+      }
+      for (int a = 0; a < 3; ++a) qf[a] = Wl.pf[a] + sf * Wl.uf[a] + tf * Wl.vf[a] - cf[a];
+      e2f = qf[0] * qf[0] + qf[1] * qf[1] + qf[2] * qf[2];
+    }
+    const float reachf = (float)r + Wl.slack;
+    if (!(e2f <= reachf * reachf)) {
+      wall_clear<M>(b, h);
+      continue;
+    }
+    G c[3];
+    if (M == kMIXED) {
+      c[0] = (G)__ll2double_rn((long long)x) * 0x1p-60;
+      c[1] = (G)__ll2double_rn((long long)y) * 0x1p-60;
+      c[2] = (G)__ll2double_rn((long long)z) * 0x1p-60;
+    } else {
+      c[0] = (G)x;
+      c[1] = (G)y;
+      c[2] = (G)z;
+    }
+    G dd[3], e[3];
+    for (int a = 0; a < 3; ++a) dd[a] = c[a] - (G)Wl.p[a];
+    G sw = (dd[0] * (G)Wl.u[0] + dd[1] * (G)Wl.u[1] + dd[2] * (G)Wl.u[2]) * (G)Wl.inv_uu;
+    sw = sw < G(0) ? G(0) : (sw > G(1) ? G(1) : sw);
+    G tw = G(0);
+    if (Wl.kind == 0) {
+      tw = (dd[0] * (G)Wl.v[0] + dd[1] * (G)Wl.v[1] + dd[2] * (G)Wl.v[2]) * (G)Wl.inv_vv;
+      tw = tw < G(0) ? G(0) : (tw > G(1) ? G(1) : tw);
+    }
+    for (int a = 0; a < 3; ++a) e[a] = (G)Wl.p[a] + sw * (G)Wl.u[a] + tw * (G)Wl.v[a] - c[a];
+    const G dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+    const G dnw = (G)r - dist;
+    if (dist > G(0) && dnw > G(0)) {
+      const G inv = G(1) / dist;
+      wall_force<M>(d, b, B, h, {(R)(e[0] * inv), (R)(e[1] * inv), (R)(e[2] * inv)}, (R)dnw,
+                    vm, wr, F, Tq);
+    } else {
+      wall_clear<M>(b, h);
+    }
+  }
+  st4((V4*)d.Fwall + i, mk4<R>(F.x, F.y, F.z, R(0)));
+  st4((V4*)d.Twall + i, mk4<R>(Tq.x, Tq.y, Tq.z, R(0)));
+}
+
+// ---------------------------------------------------------------------------
 // per-particle sum (fixed order), floor wall, gravity, symplectic Euler,
 // then binning for the next step
 // ---------------------------------------------------------------------------
@@ -1442,66 +1604,10 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
     Tq = xyz(ld4((const V4*)d.Tfused + i));
   }
   P x = ((P*)b.px)[i], y = ((P*)b.py)[i], z = ((P*)b.pz)[i];
-  // Walls (Sec. 3.3 item 5): the floor z = 0, rectangles and lines, each a
-  // body of infinite radius and mass at rest (R* = r, m* = m), touching the
-  // particle at its point closest to the particle's centre; the particle
-  // keeps one delta_t per wall (the floor first).
-  DT* wx = (DT*)b.wx;
-  DT* wy = (DT*)b.wy;
-  DT* wz = (DT*)b.wz;
-  auto wall_contact = [&](v3<R> nw, R dn, size_t h) {
-    v3<R> dold;
-    DT ox = wx[h], oy = wy[h], oz = wz[h];
-    if (M == kMIXED) {
-      const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
-                   *fz = (const float2*)&oz;
-      dold = {(R)(fx->x + fx->y), (R)(fy->x + fy->y), (R)(fz->x + fz->y)};
-    } else {
-      dold = {*(const R*)&ox, *(const R*)&oy, *(const R*)&oz};
-    }
-    v3<R> zero = {R(0), R(0), R(0)};
-    ContactOut<R> o;
-    v3<R> incd;
-    R kn_c = M == kFP64 ? (R)B.kn_c : (R)B.kn_cf;
-    R kt_c = M == kFP64 ? (R)B.kt_c : (R)B.kt_cf;
-    R al = M == kFP64 ? (R)B.alpha : (R)B.alpha_f;
-    R mu = M == kFP64 ? (R)B.mu : (R)B.mu_f;
-    R dts = M == kFP64 ? (R)B.dt : (R)B.dt_f;
-    contact_law<R>(kn_c, kt_c, al, mu, dts, nw, dn, r, R(0), m, R(0),
-                   xyz(vm), zero, xyz(wr), zero, dold, true, o, incd);
-    F = F + o.F;
-    Tq = Tq + r * o.nF;
-    if (M == kMIXED) {
-      float2 qx, qy, qz;
-      if (o.capped) {
-        qx = make_float2((float)o.dt.x, 0.f);
-        qy = make_float2((float)o.dt.y, 0.f);
-        qz = make_float2((float)o.dt.z, 0.f);
-      } else {
-        const float2 *fx = (const float2*)&ox, *fy = (const float2*)&oy,
-                     *fz = (const float2*)&oz;
-        ff ax = ff_add_f({fx->x, fx->y}, (float)incd.x);
-        ff ay = ff_add_f({fy->x, fy->y}, (float)incd.y);
-        ff az = ff_add_f({fz->x, fz->y}, (float)incd.z);
-        qx = make_float2(ax.hi, ax.lo);
-        qy = make_float2(ay.hi, ay.lo);
-        qz = make_float2(az.hi, az.lo);
-      }
-      wx[h] = *(DT*)&qx;
-      wy[h] = *(DT*)&qy;
-      wz[h] = *(DT*)&qz;
-    } else {
-      R tx = o.dt.x, ty = o.dt.y, tz = o.dt.z;
-      wx[h] = *(DT*)&tx;
-      wy[h] = *(DT*)&ty;
-      wz[h] = *(DT*)&tz;
-    }
-  };
-  auto wall_clear = [&](size_t h) {
-    wx[h] = DT{};
-    wy[h] = DT{};
-    wz[h] = DT{};
-  };
+  // Walls (Sec. 3.3 item 5): the floor z = 0 here; rectangles and lines
+  // were summed by k_walls into Fwall / Twall.  Each is a body of infinite
+  // radius and mass at rest (R* = r, m* = m); the particle keeps one delta_t
+  // per wall (the floor first).
   const size_t hbase = (size_t)i * d.nwh;
   if (B.floor_wall) {
     R dn;
@@ -1514,75 +1620,12 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
     } else {
       dn = r - (R)z;
     }
-    if (dn > R(0)) wall_contact({R(0), R(0), R(-1)}, dn, hbase);
-    else wall_clear(hbase);
+    if (dn > R(0)) wall_force<M>(d, b, B, hbase, {R(0), R(0), R(-1)}, dn, vm, wr, F, Tq);
+    else wall_clear<M>(b, hbase);
   }
-  if (B.nwalls > 0) {
-    // centre in FP32 (cull) and in the geometry precision (FP64 unless FP32)
-    float cf[3];
-    if (M == kMIXED) {
-      cf[0] = __fmul_rn(i64_to_f32_rn((long long)x), kQ);
-      cf[1] = __fmul_rn(i64_to_f32_rn((long long)y), kQ);
-      cf[2] = __fmul_rn(i64_to_f32_rn((long long)z), kQ);
-    } else {
-      cf[0] = (float)x;
-      cf[1] = (float)y;
-      cf[2] = (float)z;
-    }
-    for (int k = 0; k < B.nwalls; ++k) {
-      const WallDev& Wl = d.walls[B.wall_base + k];
-      const size_t h = hbase + (B.floor_wall ? 1 : 0) + k;
-      // conservative FP32 cull: farther than r + slack cannot touch
-      float e2f;
-      {
-        float df[3], qf[3];
-        for (int a = 0; a < 3; ++a) df[a] = cf[a] - Wl.pf[a];
-        float sf = (df[0] * Wl.uf[0] + df[1] * Wl.uf[1] + df[2] * Wl.uf[2]) * Wl.inv_uuf;
-        sf = fminf(fmaxf(sf, 0.0f), 1.0f);
-        float tf = 0.0f;
-        if (Wl.kind == 0) {
-          tf = (df[0] * Wl.vf[0] + df[1] * Wl.vf[1] + df[2] * Wl.vf[2]) * Wl.inv_vvf;
-          tf = fminf(fmaxf(tf, 0.0f), 1.0f);
-        }
-        for (int a = 0; a < 3; ++a) qf[a] = Wl.pf[a] + sf * Wl.uf[a] + tf * Wl.vf[a] - cf[a];
-        e2f = qf[0] * qf[0] + qf[1] * qf[1] + qf[2] * qf[2];
-      }
-      const float reachf = (float)r + Wl.slack;
-      if (!(e2f <= reachf * reachf)) {
-        wall_clear(h);
-        continue;
-      }
-      // the contact geometry (FP64 unless FP32), as the oracle writes it
-      using G = typename std::conditional<M == kFP32, float, double>::type;
-      G c[3];
-      if (M == kMIXED) {
-        c[0] = (G)__ll2double_rn((long long)x) * 0x1p-60;
-        c[1] = (G)__ll2double_rn((long long)y) * 0x1p-60;
-        c[2] = (G)__ll2double_rn((long long)z) * 0x1p-60;
-      } else {
-        c[0] = (G)x;
-        c[1] = (G)y;
-        c[2] = (G)z;
-      }
-      G dd[3], e[3];
-      for (int a = 0; a < 3; ++a) dd[a] = c[a] - (G)Wl.p[a];
-      G sw = (dd[0] * (G)Wl.u[0] + dd[1] * (G)Wl.u[1] + dd[2] * (G)Wl.u[2]) * (G)Wl.inv_uu;
-      sw = sw < G(0) ? G(0) : (sw > G(1) ? G(1) : sw);
-      G tw = G(0);
-      if (Wl.kind == 0) {
-        tw = (dd[0] * (G)Wl.v[0] + dd[1] * (G)Wl.v[1] + dd[2] * (G)Wl.v[2]) * (G)Wl.inv_vv;
-        tw = tw < G(0) ? G(0) : (tw > G(1) ? G(1) : tw);
-      }
-      for (int a = 0; a < 3; ++a) e[a] = (G)Wl.p[a] + sw * (G)Wl.u[a] + tw * (G)Wl.v[a] - c[a];
-      const G dist = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-      const G dnw = (G)r - dist;
-      if (dist > G(0) && dnw > G(0)) {
-        const G inv = G(1) / dist;
-        wall_contact({(R)(e[0] * inv), (R)(e[1] * inv), (R)(e[2] * inv)}, (R)dnw, h);
-      } else {
-        wall_clear(h);
-      }
-    }
+  if (d.Fwall && B.nwalls > 0) {
+    F = F + xyz(ld4((const V4*)d.Fwall + i));
+    Tq = Tq + xyz(ld4((const V4*)d.Twall + i));
   }
   // gravity (ForceGravity)
   if (M == kFP64) F = F + m * v3<R>{(R)B.g[0], (R)B.g[1], (R)B.g[2]};
