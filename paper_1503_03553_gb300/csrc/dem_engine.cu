@@ -47,6 +47,10 @@ struct dem_ctx {
   int mode = kMIXED;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // host transfers of dem_set_state / dem_get_state: copies on their own
+  // stream, overlapped with the per-array kernels on the context's stream
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t xfer_ev[6] = {};
   int device = 0;
   int nsm = 152;
   int N = 0, K = 32, Cmax = 0, M_lin = 0, M_rank = 0;
@@ -301,6 +305,9 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     if (ctx) {
       free_all(ctx);
       if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+      if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+      for (cudaEvent_t& e : ctx->xfer_ev)
+        if (e) cudaEventDestroy(e);
       if (ctx->h_status) cudaFreeHost(ctx->h_status);
       if (ctx->h_count) cudaFreeHost(ctx->h_count);
       delete ctx;
@@ -320,6 +327,11 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
       return bail(DEM_ERR_CUDA, "stream creation failed");
     ctx->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(DEM_ERR_CUDA, "stream creation failed");
+  for (cudaEvent_t& e : ctx->xfer_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return bail(DEM_ERR_CUDA, "event creation failed");
 
   // ---- boxes: geometry, cell grids, material constants --------------------
   long long N = 0, Mlin = 0, Mrank = 0;
@@ -610,6 +622,9 @@ dem_status dem_destroy(dem_ctx* ctx) {
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   if (ctx->h_count) cudaFreeHost(ctx->h_count);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  for (cudaEvent_t& e : ctx->xfer_ev)
+    if (e) cudaEventDestroy(e);
   delete ctx;
   return DEM_OK;
 }
@@ -687,24 +702,41 @@ dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
   int n = B.nlive;
   if (where != DEM_HOST && where != DEM_DEVICE) return fail(ctx, DEM_ERR_ARG, "bad where");
   if (n == 0) return DEM_OK;
-  cudaStream_t s = ctx->stream;
-  const double *dx = x, *dv = v, *dw = omega;
-  if (where == DEM_HOST) {
-    double* stg = ctx->staging;
-    if (x) { CK(cudaMemcpyAsync(stg, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)); dx = stg; }
-    if (v) { CK(cudaMemcpyAsync(stg + 3 * n, v, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)); dv = stg + 3 * n; }
-    if (omega) { CK(cudaMemcpyAsync(stg + 6 * n, omega, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s)); dw = stg + 6 * n; }
-  }
-  int nb = blocks_for(n, 256);
+  cudaStream_t s = ctx->stream, cs = ctx->copy_stream;
+  const int nb = blocks_for(n, 256);
   const int p = ctx->parity;
-  switch (ctx->mode) {
-    case kFP64: k_set_state<kFP64><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, dx, dv, dw); break;
-    case kMIXED: k_set_state<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, dx, dv, dw); break;
-    default: k_set_state<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, dx, dv, dw); break;
+  // one array at a time: its copy (host data) on the copy stream, then its
+  // kernel on the context's stream, so that copies and kernels overlap
+  const double* in[3] = {x, v, omega};
+  if (where == DEM_HOST) {
+    // the staging buffer is free once the context's earlier work is done
+    CK(cudaEventRecord(ctx->xfer_ev[5], s));
+    CK(cudaStreamWaitEvent(cs, ctx->xfer_ev[5], 0));
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (!in[k]) continue;
+    const double* dk = in[k];
+    if (where == DEM_HOST) {
+      double* stg = ctx->staging + (size_t)3 * n * k;
+      CK(cudaMemcpyAsync(stg, in[k], sizeof(double) * 3 * n, cudaMemcpyHostToDevice, cs));
+      CK(cudaEventRecord(ctx->xfer_ev[k], cs));
+      CK(cudaStreamWaitEvent(s, ctx->xfer_ev[k], 0));
+      dk = stg;
+    }
+    const double* a0 = k == 0 ? dk : nullptr;
+    const double* a1 = k == 1 ? dk : nullptr;
+    const double* a2 = k == 2 ? dk : nullptr;
+    switch (ctx->mode) {
+      case kFP64: k_set_state<kFP64><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, a0, a1, a2); break;
+      case kMIXED: k_set_state<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, a0, a1, a2); break;
+      default: k_set_state<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, a0, a1, a2); break;
+    }
+    CK(cudaGetLastError());
   }
   // new positions may have changed cells: the next sort starts from scratch
-  if (dx) CK(cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s));
-  CK(cudaGetLastError());
+  if (x) CK(cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s));
+  // the caller's host arrays are read by the time the call returns
+  if (where == DEM_HOST) CK(cudaStreamSynchronize(cs));
   return DEM_OK;
 }
 
@@ -893,25 +925,32 @@ dem_status dem_get_state(dem_ctx* ctx, int32_t box, double* x, double* v,
   const BoxDev& B = ctx->hbox[box];
   int n = B.nlive;
   if (n == 0) return DEM_OK;
-  cudaStream_t s = ctx->stream;
+  cudaStream_t s = ctx->stream, cs = ctx->copy_stream;
   double* outs[5] = {x, v, omega, force, torque};
-  double* dptr[5];
-  for (int k = 0; k < 5; ++k)
-    dptr[k] = outs[k] ? (where == DEM_HOST ? ctx->staging + (size_t)3 * n * k : outs[k]) : nullptr;
-  int nb = blocks_for(n, 256);
+  const int nb = blocks_for(n, 256);
   const int p = ctx->parity;
-  int hf = ctx->have_ft ? 1 : 0;
-  switch (ctx->mode) {
-    case kFP64: k_get_state<kFP64><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4], hf); break;
-    case kMIXED: k_get_state<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4], hf); break;
-    default: k_get_state<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, dptr[0], dptr[1], dptr[2], dptr[3], dptr[4], hf); break;
+  const int hf = ctx->have_ft ? 1 : 0;
+  // one array at a time: its kernel (id order, into staging) on the
+  // context's stream, then its copy to the host on the copy stream
+  for (int k = 0; k < 5; ++k) {
+    if (!outs[k]) continue;
+    double* dk = where == DEM_HOST ? ctx->staging + (size_t)3 * n * k : outs[k];
+    double* o[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    o[k] = dk;
+    switch (ctx->mode) {
+      case kFP64: k_get_state<kFP64><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, o[0], o[1], o[2], o[3], o[4], hf); break;
+      case kMIXED: k_get_state<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, o[0], o[1], o[2], o[3], o[4], hf); break;
+      default: k_get_state<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, o[0], o[1], o[2], o[3], o[4], hf); break;
+    }
+    CK(cudaGetLastError());
+    if (where == DEM_HOST) {
+      CK(cudaEventRecord(ctx->xfer_ev[k], s));
+      CK(cudaStreamWaitEvent(cs, ctx->xfer_ev[k], 0));
+      CK(cudaMemcpyAsync(outs[k], dk, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, cs));
+    }
   }
-  CK(cudaGetLastError());
-  if (where == DEM_HOST)
-    for (int k = 0; k < 5; ++k)
-      if (outs[k])
-        CK(cudaMemcpyAsync(outs[k], dptr[k], sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (where == DEM_HOST) CK(cudaStreamSynchronize(cs));
   return DEM_OK;
 }
 
