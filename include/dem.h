@@ -286,7 +286,7 @@ int32_t dem_abi_version(void);
  * start-up, or latency-critical code that must not call cudaMalloc (it can
  * synchronise the device).  dem_create allocates; this call does not: it
  * runs the same binning, sorting and search kernels as dem_step with all
- * scratch carved from one file-scope device array of about 4.8 MB that every
+ * scratch carved from one file-scope device array of about 5.8 MB that every
  * GPU loading this library holds until the process exits.  It calls no
  * cudaMalloc, cudaFree or allocating library routine.
  *

@@ -139,7 +139,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 }
 
 int launches_per_step(const dem_ctx* ctx) {
-  return (ctx->fused ? 7 : 8) + (ctx->hwalls.empty() ? 0 : 1);
+  return (ctx->fused ? 7 : 9) + (ctx->hwalls.empty() ? 0 : 1);
 }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
@@ -173,11 +173,14 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
                                            d.status, 0u);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(
       d.ccount, d.M_rank, d.scan_bsum,
-      CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank, d.dirty, d.dirty_next, d.ccur});
+      CellEpi{d.cstart, d.crange, d.lin_of_rank, d.dirty, d.dirty_next, d.ccur});
   // 2. counting sort by (Morton cell, id) and reorder into parity q
   k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
   k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q],
                                                   ctx->fused ? nullptr : ctx->cl[q].count);
+  // the search's per-cell pruning boxes (the per-particle forms do not prune)
+  if (!ctx->fused)
+    k_cellbox<M><<<blocks_for(d.M_rank, 256), 256, 0, s>>>(d, ctx->ps[q]);
   if (tm) cudaEventRecord(ev[1], s);
   if (ctx->fused) {
     // Algorithm 1: search and force in one pass, no contact list
@@ -510,7 +513,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     ctx->dirty[p] = (unsigned char*)A(std::max(1, ctx->M_rank));
   }
   d.crange = (int2*)A(sizeof(int2) * std::max(1, ctx->M_lin));
-  d.cellr = (float*)A(sizeof(float) * std::max(1, ctx->M_lin));
+  d.cellbox = (float4*)A(2 * sizeof(float4) * std::max(1, ctx->M_lin));
   d.perm = (int*)A(sizeof(int) * n);
   d.pcell = (int*)A(sizeof(int) * n);
   d.row = (int*)A(sizeof(int) * n * ctx->K);
@@ -1270,7 +1273,7 @@ constexpr int kStaticK = 32;
 
 // layout of the scratch array (every part 256-byte aligned)
 struct StaticLayout {
-  size_t box, slot_box, rol, lor, ccount, cstart, ccur, dirty, crange, cellr, perm, pcell, row,
+  size_t box, slot_box, rol, lor, ccount, cstart, ccur, dirty, crange, cellbox, perm, pcell, row,
       icnt, bsum, status, count, pair, rs, rc, state[2][10], total;
 };
 
@@ -1294,7 +1297,7 @@ StaticLayout static_layout() {
   L.ccur = take(4 * (M + 1));
   L.dirty = take(M + 1);
   L.crange = take(8 * M);
-  L.cellr = take(4 * M);
+  L.cellbox = take(32 * M);
   L.perm = take(4 * N);
   L.pcell = take(4 * N);
   L.row = take(4 * N * kStaticK);
@@ -1314,7 +1317,7 @@ StaticLayout static_layout() {
 }
 
 // Upper bound of the layout above (checked at set-up).
-constexpr size_t kStaticScratchBytes = 5100000;
+constexpr size_t kStaticScratchBytes = 6000000;
 
 }  // namespace
 
@@ -1444,7 +1447,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   d.ccur = (int*)(base + lay.ccur);
   d.dirty = (const unsigned char*)(base + lay.dirty);
   d.crange = (int2*)(base + lay.crange);
-  d.cellr = (float*)(base + lay.cellr);
+  d.cellbox = (float4*)(base + lay.cellbox);
   d.perm = (int*)(base + lay.perm);
   d.pcell = (int*)(base + lay.pcell);
   d.row = (int*)(base + lay.row);
@@ -1489,10 +1492,11 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
   k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum,
-                                            CellEpi{d.cstart, d.crange, d.cellr, d.lin_of_rank,
+                                            CellEpi{d.cstart, d.crange, d.lin_of_rank,
                                                     d.dirty, nullptr, d.ccur});
   k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
   k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1], cn.count);
+  k_cellbox<kMIXED><<<blocks_for(d.M_rank, 256), 256, 0, s>>>(d, ps[1]);
   k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);
   if ((st = ck(cudaGetLastError(), "launch"))) return st;
   int hcount = 0;

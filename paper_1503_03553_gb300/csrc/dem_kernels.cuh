@@ -97,7 +97,9 @@ struct Dev {
   const unsigned char* dirty;  // per rank cell: members changed since the last sort
   unsigned char* dirty_next;   // the same, collected for the next sort
   int2* crange;  // per linear cell: (first slot, count)
-  float* cellr;  // per linear cell: largest radius in the cell (-1 if empty)
+  float4* cellbox;  // per linear cell, 2 entries: (lo.xyz, largest radius),
+                    // (hi.xyz, 0): the bounding box of the members' centres
+                    // as offsets from the cell origin; radius -1 if empty
   int* perm;     // scatter position -> old slot (cell order, not yet by id)
   int* pcell;    // scatter position -> linear cell
   int* row;      // N x K: partner slots a slot found
@@ -477,13 +479,11 @@ k_scan_apply(const T* __restrict__ in, int n, const T* __restrict__ bsum,
 }
 
 // cell counts -> cell starts (rank order) and (start, count) by linear cell
-// For a cell whose members changed it also zeroes the scatter cursor and
-// resets the largest radius to -1 (empty; the reorder raises it), and it
-// clears the cell's flag for the next sort.
+// For a cell whose members changed it also zeroes the scatter cursor, and
+// it clears the cell's flag for the next sort.
 struct CellEpi {
   int* cstart;
   int2* crange;
-  float* cellr;
   const int* lin_of_rank;
   const unsigned char* dirty;
   unsigned char* dirty_next;
@@ -494,10 +494,7 @@ struct CellEpi {
     if (changed) ccur[g] = 0;
     if (dirty_next) dirty_next[g] = 0;
     int lin = lin_of_rank[g];
-    if (lin >= 0) {
-      crange[lin] = make_int2(pre, cnt);
-      if (cellr && changed) cellr[lin] = -1.0f;
-    }
+    if (lin >= 0) crange[lin] = make_int2(pre, cnt);
   }
 };
 
@@ -536,10 +533,9 @@ __global__ void k_scatter(Dev d, PState a) {
 // ---------------------------------------------------------------------------
 // counting sort, pass 2: in a changed cell each particle's final slot is the
 // cell's start plus the number of cell-mates with a smaller id, so the slot
-// order is (Morton rank of the cell, id) whatever the atomic order of pass 1,
-// and the cell's largest radius is raised to the particle's (positive floats
-// order like their bit patterns); in an unchanged cell pass 1 already placed
-// it.  The state moves there and the predicate record is built.
+// order is (Morton rank of the cell, id) whatever the atomic order of pass 1;
+// in an unchanged cell pass 1 already placed it.  The state moves there and
+// the predicate record is built.
 // ---------------------------------------------------------------------------
 template <int M>
 __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
@@ -602,7 +598,58 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   }
   pr.w = om.w;
   st4((PR*)b.posr + t, pr);
-  if (d.cellr && changed) atomicMax((int*)d.cellr + lin, __float_as_int((float)om.w));
+}
+
+// ---------------------------------------------------------------------------
+// per cell: the bounding box of the members' centres (offsets from the cell
+// origin, in the search's FP32 frame) and the largest radius, which the
+// search uses to skip neighbour cells that cannot hold a contact
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void k_cellbox(Dev d, PState b) {
+  using T = Tr<M>;
+  using PR = typename T::PR;
+  // one thread per cell in Morton rank order, so that neighbouring threads
+  // read neighbouring slots; four members loaded per iteration
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= d.M_rank) return;
+  const int l = d.lin_of_rank[g];
+  if (l < 0) return;  // a box's free-slot cell
+  const int2 rg = d.crange[l];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  float rmax = -1.0f;
+  const PR* posr = (const PR*)b.posr;
+  for (int s0 = rg.x; s0 < rg.x + rg.y; s0 += 4) {
+    const int m = rg.x + rg.y - s0;
+    PR q[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) q[u] = ld4(posr + s0 + (u < m ? u : 0));
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      if (u >= m) break;
+      float o[3];
+      if (M == kMIXED) {
+        o[0] = (float)q[u].x;
+        o[1] = (float)q[u].y;
+        o[2] = (float)q[u].z;
+      } else {
+        const BoxDev& B = d.boxes[d.slot_box[s0 + u]];
+        int c[3];
+        unpack_cell(b.cellc[s0 + u], c[0], c[1], c[2]);
+        o[0] = (float)((double)q[u].x - (double)c[0] * B.h[0]);
+        o[1] = (float)((double)q[u].y - (double)c[1] * B.h[1]);
+        o[2] = (float)((double)q[u].z - (double)c[2] * B.h[2]);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = fminf(lo[a], o[a]);
+        hi[a] = fmaxf(hi[a], o[a]);
+      }
+      rmax = fmaxf(rmax, (float)q[u].w);
+    }
+  }
+  d.cellbox[2 * l] = make_float4(lo[0], lo[1], lo[2], rmax);
+  d.cellbox[2 * l + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -712,7 +759,7 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
   using PR = typename T::PR;
   const PR* __restrict__ posr = (const PR*)b.posr;
   const int2* __restrict__ crange = d.crange;
-  const float* __restrict__ cellr = d.cellr;
+  const float4* __restrict__ cellbox = d.cellbox;
   const PR pi = ld4(posr + i);
   int c[3];
   unpack_cell(b.cellc[i], c[0], c[1], c[2]);
@@ -721,13 +768,14 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
   // and their fixed-rule shifts (only the steps the half stencil takes:
   // z 0/+1, y and x -1/0/+1); invalid steps (out of an open box) clear bits
   // of 'valid' (bit 3a + st for step st - 1 along axis a).
-  float g2lo[3], g2hi[3];
+  float g2lo[3], g2hi[3], oi[3];
   unsigned valid = 0u;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     float o, hc = c[a] == B.n[a] - 1 ? B.hcell[a][1] : B.hcell[a][0];
     if (M == kMIXED) o = (float)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z);
     else o = (float)((double)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z) - (double)c[a] * B.h[a]);
+    oi[a] = o;
     const float gl = fmaxf(o, 0.0f), gh = fmaxf(hc - o, 0.0f);
     g2lo[a] = gl * gl;
     g2hi[a] = gh * gh;
@@ -745,10 +793,11 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
             Y2 = (yw2 ? 0 : c[1] + 1) * n0;
   const int Z1 = B.lin_base + c[2] * n01, Z2 = B.lin_base + (zw2 ? 0 : c[2] + 1) * n01;
   const float ri = (float)pi.w;
-  // Pass 1: a neighbour cell is kept when it holds particles and its nearest
-  // point lies within r_i plus the largest radius in it (0.1 % margin); the
-  // box's largest radius screens cells by arithmetic before any load, and the
-  // loads left are independent of one another.
+  // Pass 1: a neighbour cell is kept when it holds particles and the bounding
+  // box of their centres lies within r_i plus the largest radius in it
+  // (0.1 % margin, far above the rounding of these FP32 gaps); the box's
+  // largest radius screens cells by the cell faces first, before any load,
+  // and the loads left are independent of one another.
   const float rb = 1.001f * (ri + B.rmax_f);
   const float rb2 = rb * rb;
   unsigned keep = 0u;
@@ -760,9 +809,27 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
     if (((valid >> (6 + kz)) & (valid >> (3 + ky)) & (valid >> kx) & 1u) && g2 <= rb2) {
       const int lin = (kz == 2 ? Z2 : Z1) + (ky == 0 ? Y0 : ky == 1 ? Y1 : Y2) +
                       (kx == 0 ? X0 : kx == 1 ? X1 : X2);
-      const float cr = __ldg(cellr + lin);
-      const float reach = 1.001f * (ri + cr);  // cr < 0: empty cell
-      if (cr >= 0.0f && g2 <= reach * reach) keep |= 1u << k;
+      const float4 blo = __ldg(cellbox + 2 * lin), bhi = __ldg(cellbox + 2 * lin + 1);
+      // the neighbour cell's origin relative to this particle's cell origin
+      float sh[3];
+      if (M == kMIXED) {
+        sh[2] = kz == 2 ? B.shift[2][zw2 ? 4 : 2] : 0.0f;
+        sh[1] = ky == 1 ? 0.0f : (ky == 0 ? B.shift[1][yw0 ? 3 : 0] : B.shift[1][yw2 ? 4 : 2]);
+        sh[0] = kx == 1 ? 0.0f : (kx == 0 ? B.shift[0][xw0 ? 3 : 0] : B.shift[0][xw2 ? 4 : 2]);
+      } else {
+        sh[2] = (float)(kz - 1) * (float)B.h[2];
+        sh[1] = (float)(ky - 1) * (float)B.h[1];
+        sh[0] = (float)(kx - 1) * (float)B.h[0];
+      }
+      const float b_lo[3] = {blo.x, blo.y, blo.z}, b_hi[3] = {bhi.x, bhi.y, bhi.z};
+      float gb2 = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const float gap = fmaxf(fmaxf(b_lo[a] + sh[a] - oi[a], oi[a] - (b_hi[a] + sh[a])), 0.0f);
+        gb2 += gap * gap;
+      }
+      const float reach = 1.001f * (ri + blo.w);  // blo.w < 0: empty cell
+      if (blo.w >= 0.0f && gb2 <= reach * reach) keep |= 1u << k;
     }
   }
   int own = 0;
