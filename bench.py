@@ -148,9 +148,9 @@ def search_tests(box, ncell):
     """Candidate tests the contact search performs: every pair is tested once,
     by the particle whose half of the neighbourhood holds the other (its own
     cell's later slots and the 13 cells after it in (dz, dy, dx) order); of
-    those 13 cells only the ones that survive the reach test count (nearest
-    point of the cell within 1.001 (r_i + largest radius in it)).  Computed
-    from the same positions and grid as the run."""
+    those 13 cells only the ones that survive the reach test count (the
+    bounding box of the cell's member centres within 1.001 (r_i + largest
+    radius in it)).  Computed from the same positions and grid as the run."""
     L = np.asarray(box.L)
     n = np.asarray(ncell)
     h = L / n
@@ -161,6 +161,11 @@ def search_tests(box, ncell):
     cnt = np.bincount(lin, minlength=M)
     rmax = np.full(M, -1.0)
     np.maximum.at(rmax, lin, box.r)
+    lo = np.full((M, 3), np.inf)
+    hi = np.full((M, 3), -np.inf)
+    for a in range(3):
+        np.minimum.at(lo[:, a], lin, o[:, a])
+        np.maximum.at(hi[:, a], lin, o[:, a])
     tests = int((cnt * (cnt - 1) // 2).sum())  # own cell, later slots
     for dz in (-1, 0, 1):
         for dy in (-1, 0, 1):
@@ -171,10 +176,9 @@ def search_tests(box, ncell):
                 l2 = (cn[:, 2] * n[1] + cn[:, 1]) * n[0] + cn[:, 0]
                 g = np.zeros(box.n)
                 for a, dd in enumerate((dx, dy, dz)):
-                    if dd < 0:
-                        g += np.maximum(o[:, a], 0) ** 2
-                    elif dd > 0:
-                        g += np.maximum(h[a] - o[:, a], 0) ** 2
+                    blo = lo[l2, a] + dd * h[a]
+                    bhi = hi[l2, a] + dd * h[a]
+                    g += np.maximum(np.maximum(blo - o[:, a], o[:, a] - bhi), 0) ** 2
                 reach = 1.001 * (box.r + rmax[l2])
                 keep = (rmax[l2] >= 0) & (g <= reach ** 2)
                 tests += int(cnt[l2][keep].sum())
@@ -183,7 +187,7 @@ def search_tests(box, ncell):
 
 SEARCH_OPS_PER_TEST = 14  # FP32 instructions of the contact predicate
 PHASES = ["sort", "search", "compact", "force", "integrate"]
-PHASE_KERNELS = {"sort": 5, "search": 1, "compact": 0, "force": 1, "integrate": 1}
+PHASE_KERNELS = {"sort": 6, "search": 1, "compact": 0, "force": 1, "integrate": 1}
 
 
 def _torch_setup(args):
