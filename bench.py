@@ -132,9 +132,10 @@ def phase_bytes(n, c_half, ncells):
     phase moves nothing of its own."""
     C = c_half * n
     state = 24 + 16 + 16 + 4 + 4        # position, velocity, spin, id, cell
-    sort = (ncells * (4 + 4 + 8 + 4)                 # cell scan, radius reset
+    sort = (ncells * (4 + 4 + 8)                     # cell scan
             + n * (4 + 4 + 4 + 4)                    # scatter
-            + n * (4 + 4 + 8 + 2 * state + 16 + 4 + 4))  # reorder, record, radius
+            + n * (4 + 4 + 8 + 2 * state + 16 + 4)   # reorder, predicate record
+            + n * 16 + ncells * 32)                  # cell bounding boxes
     search = (n * (16 + 4 + 4 + 4 + 4 + 8) + ncells * (8 + 4)
               + C * (4 + 4 + 8 + 8 + 4 + 4))         # rows, list, incoming rows
     compact = 0
