@@ -667,6 +667,20 @@ __device__ __forceinline__ bool pred_fixed(float4 pi, float4 pj, float sx,
   return d2 < __fmul_rn(R, R);
 }
 
+// The same rule on the packed FP32x2 path (two lanes of one instruction,
+// each rounded as its scalar counterpart): (dx, dy) = ((x_j, y_j) +
+// (-x_i, -y_i)) + (sx, sy) and (dz, R) = ((z_j, r_j) + (-z_i, r_i)) + (sz, 0),
+// then the squares, (dx^2 + dy^2) + dz^2 < R^2.  a - b is a + (-b) exactly,
+// r_j + r_i = r_i + r_j, and R + 0 = R for R >= 0: bit for bit pred_fixed.
+__device__ __forceinline__ bool pred_fixed_packed(float4 pj, float2 nxy, float2 nzw,
+                                                  float2 sxy, float2 sz0) {
+  const float2 u = __fadd2_rn(__fadd2_rn(make_float2(pj.x, pj.y), nxy), sxy);
+  const float2 t = __fadd2_rn(__fadd2_rn(make_float2(pj.z, pj.w), nzw), sz0);
+  const float2 uu = __fmul2_rn(u, u);
+  const float2 tt = __fmul2_rn(t, t);
+  return __fadd_rn(__fadd_rn(uu.x, uu.y), tt.x) < tt.y;
+}
+
 __device__ __forceinline__ double min_image(double d, const BoxDev& B, int a) {
   if (B.periodic[a]) {
     if (d > B.half_L[a]) d = __dsub_rn(d, B.L[a]);
@@ -869,10 +883,12 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
       unsigned hm;
       if (M == kMIXED) {
         const float4& q = *(const float4*)&pi;
-        hm = (unsigned)pred_fixed(q, *(const float4*)&p0, sx, sy, sz) |
-             ((unsigned)pred_fixed(q, *(const float4*)&p1, sx, sy, sz) << 1) |
-             ((unsigned)pred_fixed(q, *(const float4*)&p2, sx, sy, sz) << 2) |
-             ((unsigned)pred_fixed(q, *(const float4*)&p3, sx, sy, sz) << 3);
+        const float2 nxy = make_float2(-q.x, -q.y), nzw = make_float2(-q.z, q.w);
+        const float2 sxy = make_float2(sx, sy), sz0 = make_float2(sz, 0.0f);
+        hm = (unsigned)pred_fixed_packed(*(const float4*)&p0, nxy, nzw, sxy, sz0) |
+             ((unsigned)pred_fixed_packed(*(const float4*)&p1, nxy, nzw, sxy, sz0) << 1) |
+             ((unsigned)pred_fixed_packed(*(const float4*)&p2, nxy, nzw, sxy, sz0) << 2) |
+             ((unsigned)pred_fixed_packed(*(const float4*)&p3, nxy, nzw, sxy, sz0) << 3);
       } else {
         hm = (unsigned)pred_abs(pi, p0, B) | ((unsigned)pred_abs(pi, p1, B) << 1) |
              ((unsigned)pred_abs(pi, p2, B) << 2) | ((unsigned)pred_abs(pi, p3, B) << 3);
