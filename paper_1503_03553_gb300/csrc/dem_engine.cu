@@ -525,7 +525,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     d.Ffused = A(v4_bytes(M) * n);
     d.Tfused = A(v4_bytes(M) * n);
   } else {
-    d.inrow = (int*)A(sizeof(int) * n * ctx->K);
+    d.inrow = (int2*)A(sizeof(int2) * n * ctx->K);
   }
   if (!ctx->hwalls.empty()) {
     d.Fwall = A(v4_bytes(M) * n);

@@ -105,8 +105,9 @@ struct Dev {
   int* row;      // N x K: partner slots a slot found
   int* icnt;     // contacts in which a slot was found by its partner
   int* prev;     // slot of each particle before this step's reorder
-  int* inrow;    // N x K: list entries of the contacts in which a slot was
-                 // found by its partner (any order)
+  int2* inrow;   // N x K: the contacts in which a slot was found by its
+                 // partner (any order): (list entry, partner slot << 1 |
+                 // 1 if this slot is the lower-id member)
   void* Fc;      // V4 per contact: force on the lower-id particle
   void* nFc;     // V4 per contact: n x F
   void* Ffused;  // V4 per slot: contact force sum of the fused layout
@@ -962,7 +963,7 @@ k_candidates(Dev d, PState b, CList cn) {
       const int idj = b.id[j];
       cn.pair[c] = idi < idj ? make_int2(i, j) : make_int2(j, i);
       cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
-      if (pos[u] < K) d.inrow[(size_t)j * K + pos[u]] = c;
+      if (pos[u] < K) d.inrow[(size_t)j * K + pos[u]] = make_int2(c, (i << 1) | (idj < idi ? 1 : 0));
     }
   }
 }
@@ -1624,24 +1625,22 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
     // contact per partner, and unlike the list entries slots do not depend
     // on timing)
     const int n = min(inc, d.K);
-    const int* il = d.inrow + (size_t)i * d.K;
+    const int2* il = d.inrow + (size_t)i * d.K;
     if (n <= 4) {
-      // up to four: in registers, sorted by a compare-exchange network
+      // up to four: in registers, sorted by a compare-exchange network on
+      // the partner slot carried in the row
       int c[4], pk[4];
-      bool lo[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        c[u] = u < n ? il[u] : -1;
-        const int2 pr = c[u] >= 0 ? cn.pair[c[u]] : make_int2(i, 0x7fffffff);
-        lo[u] = pr.x == i;
-        pk[u] = lo[u] ? pr.y : pr.x;
+        const int2 e = u < n ? il[u] : make_int2(-1, 0x7fffffff);
+        c[u] = e.x;
+        pk[u] = e.y;  // partner slot << 1 | lower-id flag: same order as the slot
       }
       auto cx = [&](int a2, int b2) {
         if (pk[b2] < pk[a2]) {
           const int tp = pk[a2], tc = c[a2];
-          const bool tl = lo[a2];
-          pk[a2] = pk[b2]; c[a2] = c[b2]; lo[a2] = lo[b2];
-          pk[b2] = tp; c[b2] = tc; lo[b2] = tl;
+          pk[a2] = pk[b2]; c[a2] = c[b2];
+          pk[b2] = tp; c[b2] = tc;
         }
       };
       cx(0, 1); cx(2, 3); cx(0, 2); cx(1, 3); cx(1, 2);
@@ -1649,7 +1648,7 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
       for (int u = 0; u < 4; ++u) {
         if (c[u] < 0) continue;
         const V4 f = ld4(Fc + c[u]), q = ld4(nFc + c[u]);
-        if (lo[u]) F = F + xyz(f);
+        if (pk[u] & 1) F = F + xyz(f);
         else F = F - xyz(f);
         Ns = Ns + xyz(q);
       }
@@ -1658,21 +1657,19 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
       for (int t = 0; t < n; ++t) {
         int pbest = 0x7fffffff, cb = -1;
         for (int u = 0; u < n; ++u) {
-          const int cu = il[u];
-          const int2 pr = cn.pair[cu];
-          const int pu = pr.x == i ? pr.y : pr.x;
-          if (pu > prev && pu < pbest) {
-            pbest = pu;
-            cb = cu;
+          const int2 e = il[u];
+          if (e.y > prev && e.y < pbest) {
+            pbest = e.y;
+            cb = e.x;
           }
         }
-        if (cb < 0) {
+        if (cb < 0 || cb >= d.Cmax) {
           flag(d.status, kStInconsistent);
           break;
         }
         prev = pbest;
         const V4 f = ld4(Fc + cb), q = ld4(nFc + cb);
-        if (cn.pair[cb].x == i) F = F + xyz(f);
+        if (pbest & 1) F = F + xyz(f);
         else F = F - xyz(f);
         Ns = Ns + xyz(q);
       }
