@@ -139,7 +139,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 }
 
 int launches_per_step(const dem_ctx* ctx) {
-  return (ctx->fused ? 7 : 9) + (ctx->hwalls.empty() ? 0 : 1);
+  return (ctx->fused ? 7 : 8) + (ctx->hwalls.empty() ? 0 : 1);
 }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
@@ -161,6 +161,7 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   d.cstart_old = ctx->cs[p];
   d.dirty = ctx->dirty[p];
   d.dirty_next = ctx->dirty[q];
+  if (ctx->fused) d.cellbox = nullptr;  // the per-particle forms do not prune
   cudaStream_t s = ctx->stream;
   const int bs = ctx->block;
   const bool tm = ctx->tm.on;
@@ -173,14 +174,11 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
                                            d.status, 0u);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(
       d.ccount, d.M_rank, d.scan_bsum,
-      CellEpi{d.cstart, d.crange, d.lin_of_rank, d.dirty, d.dirty_next, d.ccur});
+      CellEpi{d.cstart, d.crange, d.cellbox, d.lin_of_rank, d.dirty, d.dirty_next, d.ccur});
   // 2. counting sort by (Morton cell, id) and reorder into parity q
   k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
   k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q],
                                                   ctx->fused ? nullptr : ctx->cl[q].count);
-  // the search's per-cell pruning boxes (the per-particle forms do not prune)
-  if (!ctx->fused)
-    k_cellbox<M><<<blocks_for(d.M_rank, 256), 256, 0, s>>>(d, ctx->ps[q]);
   if (tm) cudaEventRecord(ev[1], s);
   if (ctx->fused) {
     // Algorithm 1: search and force in one pass, no contact list
@@ -1492,11 +1490,10 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
   k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum,
-                                            CellEpi{d.cstart, d.crange, d.lin_of_rank,
+                                            CellEpi{d.cstart, d.crange, d.cellbox, d.lin_of_rank,
                                                     d.dirty, nullptr, d.ccur});
   k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
   k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1], cn.count);
-  k_cellbox<kMIXED><<<blocks_for(d.M_rank, 256), 256, 0, s>>>(d, ps[1]);
   k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);
   if ((st = ck(cudaGetLastError(), "launch"))) return st;
   int hcount = 0;

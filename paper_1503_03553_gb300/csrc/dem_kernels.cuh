@@ -480,11 +480,12 @@ k_scan_apply(const T* __restrict__ in, int n, const T* __restrict__ bsum,
 }
 
 // cell counts -> cell starts (rank order) and (start, count) by linear cell
-// For a cell whose members changed it also zeroes the scatter cursor, and
-// it clears the cell's flag for the next sort.
+// For a cell whose members changed it also zeroes the scatter cursor; it
+// clears the cell's flag for the next sort and resets the cell's box.
 struct CellEpi {
   int* cstart;
   int2* crange;
+  float4* cellbox;  // reset for the reorder's atomics (may be null)
   const int* lin_of_rank;
   const unsigned char* dirty;
   unsigned char* dirty_next;
@@ -495,7 +496,13 @@ struct CellEpi {
     if (changed) ccur[g] = 0;
     if (dirty_next) dirty_next[g] = 0;
     int lin = lin_of_rank[g];
-    if (lin >= 0) crange[lin] = make_int2(pre, cnt);
+    if (lin >= 0) {
+      crange[lin] = make_int2(pre, cnt);
+      if (cellbox) {
+        cellbox[2 * lin] = make_float4(INFINITY, INFINITY, INFINITY, -1.0f);
+        cellbox[2 * lin + 1] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+    }
   }
 };
 
@@ -546,111 +553,122 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   using PR = typename T::PR;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // scatter position
   if (q == 0 && cursor) *cursor = 0;  // the search allocates list entries
-  if (q >= d.N) return;
-  if (d.icnt) d.icnt[q] = 0;  // the search counts into it
-  const BoxDev& B = d.boxes[d.slot_box[q]];
-  if (q - B.pbase >= B.nlive) return;
-  const int s = d.perm[q];
-  const int g = d.pcell[q];
-  const int lin = d.lin_of_rank[g];
-  const bool changed = d.dirty[g] != 0;
-  const int key = a.id[s];
-  int t = q;  // final slot
-  if (changed) {
-    const int2 rg = d.crange[lin];
-    int rank = 0;
-    for (int u = rg.x; u < rg.x + rg.y; ++u) rank += a.id[d.perm[u]] < key ? 1 : 0;
-    t = rg.x + rank;
-  }
-  if (d.prev) d.prev[t] = s;
-  P x = ((const P*)a.px)[s], y = ((const P*)a.py)[s], z = ((const P*)a.pz)[s];
-  ((P*)b.px)[t] = x;
-  ((P*)b.py)[t] = y;
-  ((P*)b.pz)[t] = z;
-  V4 vel = ld4((const V4*)a.vel + s);
-  V4 om = ld4((const V4*)a.omg + s);
-  st4((V4*)b.vel + t, vel);
-  st4((V4*)b.omg + t, om);
-  b.id[t] = key;
-  int cc = a.cellx[s];
-  b.cellc[t] = cc;
-  b.cellg[t] = g;
-  if (a.wx) {
-    using DT = typename T::DT;
-    for (int w = 0; w < d.nwh; ++w) {
-      const size_t hs = (size_t)s * d.nwh + w, ht = (size_t)t * d.nwh + w;
-      ((DT*)b.wx)[ht] = ((const DT*)a.wx)[hs];
-      ((DT*)b.wy)[ht] = ((const DT*)a.wy)[hs];
-      ((DT*)b.wz)[ht] = ((const DT*)a.wz)[hs];
-    }
-  }
-  PR pr;
-  if (M == kMIXED) {
-    int cx, cy, cz;
-    unpack_cell(cc, cx, cy, cz);
-    long long X = (long long)x, Y = (long long)y, Z = (long long)z;
-    pr.x = __fmul_rn(i64_to_f32_rn(X - (long long)cx * B.Hq[0]), kQ);
-    pr.y = __fmul_rn(i64_to_f32_rn(Y - (long long)cy * B.Hq[1]), kQ);
-    pr.z = __fmul_rn(i64_to_f32_rn(Z - (long long)cz * B.Hq[2]), kQ);
-  } else {
-    pr.x = x;
-    pr.y = y;
-    pr.z = z;
-  }
-  pr.w = om.w;
-  st4((PR*)b.posr + t, pr);
-}
-
-// ---------------------------------------------------------------------------
-// per cell: the bounding box of the members' centres (offsets from the cell
-// origin, in the search's FP32 frame) and the largest radius, which the
-// search uses to skip neighbour cells that cannot hold a contact
-// ---------------------------------------------------------------------------
-template <int M>
-__global__ void k_cellbox(Dev d, PState b) {
-  using T = Tr<M>;
-  using PR = typename T::PR;
-  // one thread per cell in Morton rank order, so that neighbouring threads
-  // read neighbouring slots; four members loaded per iteration
-  const int g = blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= d.M_rank) return;
-  const int l = d.lin_of_rank[g];
-  if (l < 0) return;  // a box's free-slot cell
-  const int2 rg = d.crange[l];
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  float rmax = -1.0f;
-  const PR* posr = (const PR*)b.posr;
-  for (int s0 = rg.x; s0 < rg.x + rg.y; s0 += 4) {
-    const int m = rg.x + rg.y - s0;
-    PR q[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) q[u] = ld4(posr + s0 + (u < m ? u : 0));
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (u >= m) break;
+  if (q < d.N && d.icnt) d.icnt[q] = 0;  // the search counts into it
+  // this particle's contribution to its cell's box: offset from the cell
+  // origin (lo) and (hi), radius; identities for lanes without a particle
+  int lin = -1;
+  float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {0.0f, 0.0f, 0.0f};
+  float brad = -1.0f;
+  if (q < d.N) {
+    const BoxDev& B = d.boxes[d.slot_box[q]];
+    if (q - B.pbase < B.nlive) {
+      const int s = d.perm[q];
+      const int g = d.pcell[q];
+      lin = d.lin_of_rank[g];
+      const bool changed = d.dirty[g] != 0;
+      const int key = a.id[s];
+      int t = q;  // final slot
+      if (changed) {
+        const int2 rg = d.crange[lin];
+        int rank = 0;
+        for (int u = rg.x; u < rg.x + rg.y; ++u) rank += a.id[d.perm[u]] < key ? 1 : 0;
+        t = rg.x + rank;
+      }
+      if (d.prev) d.prev[t] = s;
+      P x = ((const P*)a.px)[s], y = ((const P*)a.py)[s], z = ((const P*)a.pz)[s];
+      ((P*)b.px)[t] = x;
+      ((P*)b.py)[t] = y;
+      ((P*)b.pz)[t] = z;
+      V4 vel = ld4((const V4*)a.vel + s);
+      V4 om = ld4((const V4*)a.omg + s);
+      st4((V4*)b.vel + t, vel);
+      st4((V4*)b.omg + t, om);
+      b.id[t] = key;
+      int cc = a.cellx[s];
+      b.cellc[t] = cc;
+      b.cellg[t] = g;
+      if (a.wx) {
+        using DT = typename T::DT;
+        for (int w = 0; w < d.nwh; ++w) {
+          const size_t hs = (size_t)s * d.nwh + w, ht = (size_t)t * d.nwh + w;
+          ((DT*)b.wx)[ht] = ((const DT*)a.wx)[hs];
+          ((DT*)b.wy)[ht] = ((const DT*)a.wy)[hs];
+          ((DT*)b.wz)[ht] = ((const DT*)a.wz)[hs];
+        }
+      }
+      int cx, cy, cz;
+      unpack_cell(cc, cx, cy, cz);
+      PR pr;
       float o[3];
       if (M == kMIXED) {
-        o[0] = (float)q[u].x;
-        o[1] = (float)q[u].y;
-        o[2] = (float)q[u].z;
+        long long X = (long long)x, Y = (long long)y, Z = (long long)z;
+        pr.x = __fmul_rn(i64_to_f32_rn(X - (long long)cx * B.Hq[0]), kQ);
+        pr.y = __fmul_rn(i64_to_f32_rn(Y - (long long)cy * B.Hq[1]), kQ);
+        pr.z = __fmul_rn(i64_to_f32_rn(Z - (long long)cz * B.Hq[2]), kQ);
+        o[0] = pr.x;
+        o[1] = pr.y;
+        o[2] = pr.z;
       } else {
-        const BoxDev& B = d.boxes[d.slot_box[s0 + u]];
-        int c[3];
-        unpack_cell(b.cellc[s0 + u], c[0], c[1], c[2]);
-        o[0] = (float)((double)q[u].x - (double)c[0] * B.h[0]);
-        o[1] = (float)((double)q[u].y - (double)c[1] * B.h[1]);
-        o[2] = (float)((double)q[u].z - (double)c[2] * B.h[2]);
+        pr.x = x;
+        pr.y = y;
+        pr.z = z;
+        o[0] = (float)((double)x - (double)cx * B.h[0]);
+        o[1] = (float)((double)y - (double)cy * B.h[1]);
+        o[2] = (float)((double)z - (double)cz * B.h[2]);
       }
+      pr.w = om.w;
+      st4((PR*)b.posr + t, pr);
+      // a negative offset (a centre outside its clamped cell on an open
+      // axis) leaves that side of the box open: -inf below, 0 above
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        lo[a] = fminf(lo[a], o[a]);
-        hi[a] = fmaxf(hi[a], o[a]);
+      for (int c = 0; c < 3; ++c) {
+        blo[c] = o[c] >= 0.0f ? o[c] : -INFINITY;
+        bhi[c] = o[c] >= 0.0f ? o[c] : 0.0f;
       }
-      rmax = fmaxf(rmax, (float)q[u].w);
+      brad = (float)om.w;
     }
   }
-  d.cellbox[2 * l] = make_float4(lo[0], lo[1], lo[2], rmax);
-  d.cellbox[2 * l + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+  if (!d.cellbox) return;
+  // The cell boxes for the search's pruning: a reduction over each run of
+  // lanes in the same cell (scatter positions of a cell are consecutive),
+  // then one set of atomics per run.  All stored values are non-negative
+  // floats or -inf, which order like their bit patterns as signed ints.
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  unsigned same = 0u;  // bit k: the lane 2^k ahead is in the same cell
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int o = 1 << k;
+    const int other = __shfl_down_sync(full, lin, o);
+    if (lane + o < 32 && other == lin) same |= 1u << k;
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) {
+    const int o = 1 << k;
+    const bool take = (same >> k) & 1u;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float l2 = __shfl_down_sync(full, blo[c], o);
+      const float h2 = __shfl_down_sync(full, bhi[c], o);
+      if (take) {
+        blo[c] = fminf(blo[c], l2);
+        bhi[c] = fmaxf(bhi[c], h2);
+      }
+    }
+    const float r2 = __shfl_down_sync(full, brad, o);
+    if (take) brad = fmaxf(brad, r2);
+  }
+  const int prev_lin = __shfl_up_sync(full, lin, 1);
+  if (lin >= 0 && (lane == 0 || prev_lin != lin)) {
+    int* box = (int*)(d.cellbox + 2 * lin);
+    atomicMin(box + 0, __float_as_int(blo[0]));
+    atomicMin(box + 1, __float_as_int(blo[1]));
+    atomicMin(box + 2, __float_as_int(blo[2]));
+    atomicMax(box + 3, __float_as_int(brad));
+    atomicMax(box + 4, __float_as_int(bhi[0]));
+    atomicMax(box + 5, __float_as_int(bhi[1]));
+    atomicMax(box + 6, __float_as_int(bhi[2]));
+  }
 }
 
 // ---------------------------------------------------------------------------

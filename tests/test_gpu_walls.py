@@ -80,3 +80,15 @@ def test_walls_history_over_steps_tracks_oracle(walled):
     ke_o = 0.5 * np.sum(m[:, None] * s.v ** 2)
     assert ke_g == pytest.approx(ke_o, rel=1e-6)
     assert np.allclose(g["state"]["x"][:, 2], s.x[:, 2], rtol=0, atol=1e-12)
+
+
+def test_walled_and_plain_boxes_in_one_context(walled):
+    """A context holding a box with walls and one without: each box matches
+    the oracle run on it alone (the wall kernel and the wall histories skip
+    the plain box)."""
+    plain = synth.w2_polydisperse(n=2000, seed=32)
+    boxes = [prepared(walled, "mixed"), prepared(plain, "mixed")]
+    ncells = [grid_for(b) for b in boxes]
+    gs = gpu_run(boxes, "mixed", ncells)
+    for b, g, nc in zip(boxes, gs, ncells):
+        check_one_step(b, g, oracle_run(b, "mixed", nc), "mixed")
