@@ -68,12 +68,10 @@ struct dem_ctx {
   int* cs[2]{};                // cell starts of the order held by state 0 / 1
   unsigned char* dirty[2]{};   // changed-cell flags read by a step of parity 0 / 1
   int parity = 0;
-  bool any_floor = false;
   int nwh = 0;                   // wall histories per slot (largest box)
   std::vector<WallDev> hwalls;   // all boxes' rectangle and line walls
   bool have_particles = false;
   bool have_ft = false;
-  std::vector<char> hist_cleared;  // per box: history dropped by set_particles
   unsigned* h_status = nullptr;  // pinned
   int* h_count = nullptr;        // pinned
   double* staging = nullptr;     // device, max_cap x 16 doubles
@@ -390,7 +388,6 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     if (ncell > (1ll << 30)) return bail(DEM_ERR_ARG, "too many cells");
     B.floor_wall = bx.floor_wall ? 1 : 0;
     B.rmax_f = (float)bx.r_max;
-    ctx->any_floor |= B.floor_wall != 0;
     // rectangle and line walls
     if (bx.nwalls < 0 || (bx.nwalls > 0 && !bx.walls) || B.floor_wall + bx.nwalls > 15)
       return bail(DEM_ERR_ARG, "a box holds 0 to 15 walls (floor included), listed in walls");
@@ -470,7 +467,6 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   const long long scan_limit = (long long)kScanTile * kScanTopThreads * kScanTopItems;
   if (N > scan_limit || Mrank > scan_limit)
     return bail(DEM_ERR_ARG, "more than 2^24 slots or cells in one context");
-  ctx->hist_cleared.assign(ctx->boxes.size(), 0);
   ctx->N = (int)N;
   ctx->M_lin = (int)Mlin;
   ctx->M_rank = (int)Mrank;
@@ -668,7 +664,6 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
     CK(cudaMemsetAsync(ctx->cl[q].oc + B.pbase, 0, sizeof(int) * B.cap, s));
   // the next sort starts from the order the particles were given in
   CK(cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s));
-  ctx->hist_cleared[box] = 1;
   if (n > 0) {
     const double *dx = x, *dv = v, *dw = omega, *dr = radius;
     if (where == DEM_HOST) {
@@ -812,7 +807,6 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
   if (timing && ctx->tm.steps)
     for (int k = 0; k < kPhases; ++k) ctx->phase_ms[k] = ctx->tm.acc[k] / ctx->tm.steps;
   ctx->have_ft = true;
-  std::fill(ctx->hist_cleared.begin(), ctx->hist_cleared.end(), 0);
   return read_status(ctx);
 }
 
@@ -1205,7 +1199,6 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
   *ctx->h_count = nc;
   CK(cudaMemcpyAsync(c.count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
-  std::fill(ctx->hist_cleared.begin(), ctx->hist_cleared.end(), 0);
   return DEM_OK;
 }
 

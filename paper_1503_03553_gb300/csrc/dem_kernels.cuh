@@ -739,12 +739,6 @@ __device__ __forceinline__ bool pred_abs(const float4& pi, const float4& pj,
 // it lies outside a non-periodic box.  *shift gets the fixed-rule shift in
 // metres, (float)((cn - c) H + image L) with image = -1 / +1 when the step
 // wraps below 0 / above n - 1 (the oracle's rounding, exactly).
-// neighbour cell index along one axis, wrapped (callers check that a step
-// out of an open box is never taken)
-__device__ __forceinline__ int wrap_cell(int cn, int n) {
-  return cn < 0 ? cn + n : (cn >= n ? cn - n : cn);
-}
-
 __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
                                           int& cn, float& shift) {
   const int n = B.n[a];
