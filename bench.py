@@ -501,6 +501,7 @@ def _side_legs(args, D, torch, box, ncell, stream):
                 out["force_parity_vs_fp64_oracle"] = {"pass": False, "error": str(e)[:300]}
     out["force_error_vs_fp64_oracle"] = errs
     out["collide_fused_vs_compact"] = _fused_leg(args, D, torch, stream, box, ncell)
+    out["size_binned_search"] = _size_binned_leg(args, D, torch, stream, box, ncell)
     if not args.no_batched:
         out["batched"] = _batched_leg(args, D, torch, stream)
     if args.w3:
@@ -665,6 +666,29 @@ def _fused_leg(args, D, torch, stream, box, ncell):
                 "collide_ms_compact": coll["compact"],
                 "twoloop_speedup_over_fused": coll["fused"] / coll["twoloop"],
                 "collide_speedup_of_compaction": coll["fused"] / coll["compact"]})
+    return out
+
+
+def _size_binned_leg(args, D, torch, stream, box, ncell):
+    """Size-binned contact search (dem_box.r_split, Sec. 3.3's cell-size
+    trade-off) against the one-class search: step time and the search phase
+    (both search kernels) on this W2 box and on a box with radii spanning a
+    factor 8 (1-8 um), each at the library's automatic grid."""
+    import dataclasses
+    from paper_1503_03553_gb300 import synth
+    from parity import prepared
+    steps = max(16, args.steps // 8)
+    wide = prepared(synth.wide_polydisperse(n=box.n, seed=6), "mixed")
+    out = {}
+    for name, b0, splits in (("w2", box, (0.0, 5.5e-6, 6e-6)), ("radii_1_8um", wide, (0.0, 4e-6, 5e-6))):
+        rows = []
+        for rs in splits:
+            b = dataclasses.replace(b0, r_split=rs)
+            r = _throughput(D, torch, stream, [b], "mixed", None, steps)
+            ph = _phase_ms(D, torch, stream, [b], "mixed", None, 20)
+            r.update({"r_split_um": rs * 1e6, "search_ms": ph["search"], "sort_ms": ph["sort"]})
+            rows.append(r)
+        out[name] = {"particles": b0.n, "rows": rows}
     return out
 
 

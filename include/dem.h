@@ -48,7 +48,7 @@
 extern "C" {
 #endif
 
-#define DEM_ABI_VERSION 2
+#define DEM_ABI_VERSION 3
 
 typedef enum {
   DEM_OK = 0,
@@ -131,11 +131,21 @@ typedef struct {
   double dt;              /* time step [s]                                */
   int32_t material;       /* index into dem_config.materials              */
   int32_t ncell[3];       /* cell grid; 0 = largest grid with cells at     */
-                          /* least 2 r_max (1 + 1e-5) wide                 */
+                          /* least 2 r_max (1 + 1e-5) wide (see r_split)   */
   int64_t max_particles;  /* capacity of the box                          */
   double r_max;           /* largest radius the box will hold [m]         */
   int32_t nwalls;         /* rectangle and line walls (0 = none)           */
   const dem_wall* walls;  /* nwalls entries, read during dem_create        */
+  double r_split;         /* size-binned contact search (0 = off), for     */
+                          /* polydisperse boxes: a particle of radius      */
+                          /* above r_split searches the +-2 neighbour      */
+                          /* cells for all its partners, the others search */
+                          /* +-1 cells for partners of radius up to        */
+                          /* r_split.  Cells then need only be             */
+                          /* max(2 r_split, r_max) (1 + 1e-5) wide (ncell  */
+                          /* 0 picks the largest such grid) and periodic   */
+                          /* axes at least 5 cells.  Same contacts as the  */
+                          /* single-class search.  DEM_COLLIDE_COMPACT only */
 } dem_box;
 
 typedef struct {

@@ -55,7 +55,8 @@ class dem_box(C.Structure):
                 ("floor_wall", C.c_int32), ("g", C.c_double * 3), ("dt", C.c_double),
                 ("material", C.c_int32), ("ncell", C.c_int32 * 3),
                 ("max_particles", C.c_int64), ("r_max", C.c_double),
-                ("nwalls", C.c_int32), ("walls", C.POINTER(dem_wall))]
+                ("nwalls", C.c_int32), ("walls", C.POINTER(dem_wall)),
+                ("r_split", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -340,7 +341,8 @@ def dem_last_error(ctx) -> str:
 class Context:
     """Owns one dem_ctx.  ``boxes`` are objects with the fields of
     ``synth.Box`` (L, periodic, floor_wall, g, dt, E, poisson, density,
-    restitution, mu_d, r_max, n) or dicts with the same keys."""
+    restitution, mu_d, r_max, n; optional walls, r_split) or dicts with the
+    same keys."""
 
     def __init__(self, boxes: Sequence, precision="mixed", collide=DEM_COLLIDE_COMPACT,
                  kn_literal=0, row_capacity=0, graph_steps=0, block=0,
@@ -372,6 +374,7 @@ class Context:
             bx.material = k
             bx.max_particles = int(capacities[k]) if capacities is not None else int(g("n"))
             bx.r_max = float(r_max[k]) if r_max is not None else float(g("r_max"))
+            bx.r_split = float(g("r_split", 0.0) or 0.0)
             walls = list(g("walls", ()) or ())
             bx.nwalls = len(walls)
             if walls:

@@ -54,6 +54,8 @@ struct BoxDev {
   float hcell[3][2];    // cell edge [m]: ordinary cell, last cell (inf when open)
   double h[3];          // L / ncell [m]
   float rmax_f;         // largest radius the box may hold [m]
+  float rsplit_f;       // size-binned search: a particle is large when its
+                        // FP32 radius exceeds this (+inf: one class)
   int n[3];             // cells per axis
   int periodic[3];
   int floor_wall;

@@ -59,6 +59,7 @@ struct dem_ctx {
   int max_cap = 0;
   bool fused = false;  // a per-particle Collide form: no contact list
   bool twoloop = false;  // DEM_COLLIDE_TWOLOOP: the paper's two-loop form
+  bool split = false;    // some box is size-binned (r_split > 0)
   int ko = 8;          // fused: stored contacts per particle
   std::vector<BoxDev> hbox;
   std::vector<void*> allocs;
@@ -137,7 +138,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 }
 
 int launches_per_step(const dem_ctx* ctx) {
-  return (ctx->fused ? 7 : 8) + (ctx->hwalls.empty() ? 0 : 1);
+  return (ctx->fused ? 7 : 8) + (ctx->hwalls.empty() ? 0 : 1) + (ctx->split ? 1 : 0);
 }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
@@ -200,7 +201,13 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   // 3. contact search and dense contact list
   // the search kernel is compiled for at most 256 threads per block
   const int bs_search = bs < 256 ? bs : 256;
-  k_candidates<M><<<blocks_for(d.N, bs_search), bs_search, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
+  if (ctx->split) {
+    k_candidates<M, true><<<blocks_for(d.N, bs_search), bs_search, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
+    // large particles of size-binned boxes: one warp each, persistent grid
+    k_candidates_large<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
+  } else {
+    k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
+  }
   if (tm) {
     cudaEventRecord(ev[2], s);
     cudaEventRecord(ev[3], s);
@@ -350,17 +357,26 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
       return bail(DEM_ERR_ARG, "box needs r_max > 0, dt > 0, capacity in [0, 2^30]");
     if (bx.floor_wall && bx.periodic[2])
       return bail(DEM_ERR_ARG, "floor wall needs a non-periodic z axis");
+    if (!(bx.r_split >= 0) || bx.r_split > bx.r_max)
+      return bail(DEM_ERR_ARG, "r_split outside [0, r_max]");
+    const bool split = bx.r_split > 0;
+    if (split && ctx->fused)
+      return bail(DEM_ERR_ARG, "a size-binned box (r_split > 0) needs DEM_COLLIDE_COMPACT");
+    ctx->split = ctx->split || split;
     long long ncell = 1;
     for (int a = 0; a < 3; ++a) {
       if (!(bx.L[a] > 0) || bx.L[a] * 0x1p60 >= 0x1p62)
         return bail(DEM_ERR_ARG, "box length out of range (0, 4 m)");
       int n = bx.ncell[a];
-      double hmin = 2.0 * bx.r_max * (1.0 + 1e-5);
+      // small pairs within +-1 cell; with r_split, large ones within +-2
+      const double hmin = (split ? std::max(2.0 * bx.r_split, bx.r_max) : 2.0 * bx.r_max) * (1.0 + 1e-5);
       if (n <= 0) n = std::max(1, (int)std::floor(bx.L[a] / hmin));
       if (bx.L[a] / n < hmin)
-        return bail(DEM_ERR_ARG, "cells narrower than 2 r_max (1 + 1e-5)");
-      if (bx.periodic[a] && n < 3)
-        return bail(DEM_ERR_ARG, "a periodic axis needs at least 3 cells");
+        return bail(DEM_ERR_ARG, split ? "cells narrower than max(2 r_split, r_max) (1 + 1e-5)"
+                                       : "cells narrower than 2 r_max (1 + 1e-5)");
+      if (bx.periodic[a] && n < (split ? 5 : 3))
+        return bail(DEM_ERR_ARG, split ? "a periodic axis of a size-binned box needs at least 5 cells"
+                                       : "a periodic axis needs at least 3 cells");
       if (n > kMaxAxisCells) return bail(DEM_ERR_ARG, "more than 1024 cells on an axis");
       B.n[a] = n;
       B.periodic[a] = bx.periodic[a] ? 1 : 0;
@@ -388,6 +404,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     if (ncell > (1ll << 30)) return bail(DEM_ERR_ARG, "too many cells");
     B.floor_wall = bx.floor_wall ? 1 : 0;
     B.rmax_f = (float)bx.r_max;
+    B.rsplit_f = split ? (float)bx.r_split : INFINITY;
     // rectangle and line walls
     if (bx.nwalls < 0 || (bx.nwalls > 0 && !bx.walls) || B.floor_wall + bx.nwalls > 15)
       return bail(DEM_ERR_ARG, "a box holds 0 to 15 walls (floor included), listed in walls");
@@ -511,6 +528,10 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.perm = (int*)A(sizeof(int) * n);
   d.pcell = (int*)A(sizeof(int) * n);
   d.row = (int*)A(sizeof(int) * n * ctx->K);
+  if (ctx->split) {
+    d.large = (int*)A(sizeof(int) * n);
+    d.nlarge = (int*)A(sizeof(int));
+  }
   d.icnt = (int*)A(sizeof(int) * n);
   d.prev = (int*)A(sizeof(int) * n);
   d.Fc = A(v4_bytes(M) * ctx->Cmax);
@@ -1421,6 +1442,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   B.nlive = N;
   B.density = 1.0;
   B.rmax_f = (float)(0.5 * hmin);
+  B.rsplit_f = INFINITY;  // one size class
 
   Dev d{};
   d.boxes = (const BoxDev*)(base + lay.box);
@@ -1487,7 +1509,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
                                                     d.dirty, nullptr, d.ccur});
   k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
   k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1], cn.count);
-  k_candidates<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);
+  k_candidates<kMIXED, false><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);
   if ((st = ck(cudaGetLastError(), "launch"))) return st;
   int hcount = 0;
   unsigned hstatus = 0;

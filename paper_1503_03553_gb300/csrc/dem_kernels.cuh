@@ -103,6 +103,9 @@ struct Dev {
   int* perm;     // scatter position -> old slot (cell order, not yet by id)
   int* pcell;    // scatter position -> linear cell
   int* row;      // N x K: partner slots a slot found
+  int* large;    // slots of the large particles of size-binned boxes (the
+                 // search appends them; null when no box is size-binned)
+  int* nlarge;   // their number (device scalar, reset by the reorder)
   int* icnt;     // contacts in which a slot was found by its partner
   int* prev;     // slot of each particle before this step's reorder
   int2* inrow;   // N x K: the contacts in which a slot was found by its
@@ -553,6 +556,7 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   using PR = typename T::PR;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // scatter position
   if (q == 0 && cursor) *cursor = 0;  // the search allocates list entries
+  if (q == 0 && d.nlarge) *d.nlarge = 0;  // ... and appends large particles
   if (q < d.N && d.icnt) d.icnt[q] = 0;  // the search counts into it
   // this particle's contribution to its cell's box: offset from the cell
   // origin (lo) and (hi), radius; identities for lanes without a particle
@@ -778,8 +782,17 @@ __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
 // at a time so that four loads are in flight.
 // ---------------------------------------------------------------------------
 
-// the search of one live slot: partners into its row, returns how many
-template <int M>
+// Size classes of a size-binned box: a particle is large when its radius,
+// rounded to FP32, exceeds the box's r_split (every kernel decides it with
+// this one expression).
+__device__ __forceinline__ bool is_large(float r, float rs) { return r > rs; }
+__device__ __forceinline__ bool is_large(double r, float rs) { return (float)r > rs; }
+
+// the search of one live slot: partners into its row, returns how many.
+// kSplit: the slot is small in a size-binned box; large candidates are
+// skipped (the large particles find those pairs) and the pruning bounds the
+// partners' radii by r_split.
+template <int M, bool kSplit>
 __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const BoxDev& B,
                                           int i) {
   using T = Tr<M>;
@@ -825,7 +838,9 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
   // (0.1 % margin, far above the rounding of these FP32 gaps); the box's
   // largest radius screens cells by the cell faces first, before any load,
   // and the loads left are independent of one another.
-  const float rb = 1.001f * (ri + B.rmax_f);
+  // the largest radius a partner can have
+  const float rp = kSplit ? fminf(B.rmax_f, B.rsplit_f) : B.rmax_f;
+  const float rb = 1.001f * (ri + rp);
   const float rb2 = rb * rb;
   unsigned keep = 0u;
 #pragma unroll
@@ -855,7 +870,7 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
         const float gap = fmaxf(fmaxf(b_lo[a] + sh[a] - oi[a], oi[a] - (b_hi[a] + sh[a])), 0.0f);
         gb2 += gap * gap;
       }
-      const float reach = 1.001f * (ri + blo.w);  // blo.w < 0: empty cell
+      const float reach = 1.001f * (ri + (kSplit ? fminf(blo.w, rp) : blo.w));  // blo.w < 0: empty
       if (blo.w >= 0.0f && gb2 <= reach * reach) keep |= 1u << k;
     }
   }
@@ -907,6 +922,11 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
              ((unsigned)pred_abs(pi, p2, B) << 2) | ((unsigned)pred_abs(pi, p3, B) << 3);
       }
       hm &= (m >= 4) ? 0xFu : ((1u << m) - 1u);
+      if (kSplit) {
+        const float rs = B.rsplit_f;
+        hm &= ~((unsigned)is_large(p0.w, rs) | ((unsigned)is_large(p1.w, rs) << 1) |
+                ((unsigned)is_large(p2.w, rs) << 2) | ((unsigned)is_large(p3.w, rs) << 3));
+      }
       while (hm) {
         const int jj = j + __ffs(hm) - 1;
         hm &= hm - 1u;
@@ -924,31 +944,20 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
   return own;
 }
 
-template <int M>
-__global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5)
-k_candidates(Dev d, PState b, CList cn) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // whole warps run
-  int own = 0;
-  bool live = false;
-  if (i < d.N) {
-    const BoxDev& B = d.boxes[d.slot_box[i]];
-    live = i - B.pbase < B.nlive;
-    if (live) own = search_row<M>(d, b, B, i);
-  }
-  __syncwarp();
-  // the warp's block of list entries
+// The dense list entries of a warp's particles: slot i (-1: none) found
+// `own` partners, in its row.  One atomic add per warp on the list length
+// takes the warp's block (its position depends on timing, the content of
+// every entry does not), a warp scan places each particle's pairs there,
+// oriented (lower id, higher id), and each entry index also goes into the
+// partner's incoming row at a position taken from its incoming count.
+__device__ __forceinline__ void write_list(const Dev& d, const PState& b, const CList& cn, int i,
+                                           int own) {
   const int lane = threadIdx.x & 31;
   const int incl = warp_incl_scan(own);
   int base = 0;
   if (lane == 31 && incl > 0) base = atomicAdd(cn.count, incl);
   base = __shfl_sync(0xffffffffu, base, 31);
-  if (!live) {
-    if (i < d.N) {
-      cn.hs[i] = 0;
-      cn.oc[i] = 0;
-    }
-    return;
-  }
+  if (i < 0) return;
   const long long pre = (long long)base + incl - own;
   int n = own;
   if (pre + n > d.Cmax) {
@@ -976,6 +985,266 @@ k_candidates(Dev d, PState b, CList cn) {
       cn.pair[c] = idi < idj ? make_int2(i, j) : make_int2(j, i);
       cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
       if (pos[u] < K) d.inrow[(size_t)j * K + pos[u]] = make_int2(c, (i << 1) | (idj < idi ? 1 : 0));
+    }
+  }
+}
+
+// kSplit: some box is size-binned; its large particles are not searched
+// here but appended to d.large for k_candidates_large.
+template <int M, bool kSplit>
+__global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5)
+k_candidates(Dev d, PState b, CList cn) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;  // whole warps run
+  int own = 0;
+  bool live = false, large = false;
+  if (i < d.N) {
+    const BoxDev& B = d.boxes[d.slot_box[i]];
+    live = i - B.pbase < B.nlive;
+    if (kSplit && live) large = is_large(ld4((const typename Tr<M>::PR*)b.posr + i).w, B.rsplit_f);
+    if (live && !large) own = kSplit ? search_row<M, true>(d, b, B, i) : search_row<M, false>(d, b, B, i);
+  }
+  __syncwarp();
+  const int lane = threadIdx.x & 31;
+  if (kSplit) {
+    // append the warp's large particles (one atomic per warp)
+    const unsigned lb = __ballot_sync(0xffffffffu, large);
+    if (lb) {
+      const int leader = __ffs(lb) - 1;
+      int lbase = 0;
+      if (lane == leader) lbase = atomicAdd(d.nlarge, __popc(lb));
+      lbase = __shfl_sync(0xffffffffu, lbase, leader);
+      if (large) d.large[lbase + __popc(lb & ((1u << lane) - 1u))] = i;
+    }
+  }
+  if (!live && i < d.N) {
+    cn.hs[i] = 0;
+    cn.oc[i] = 0;
+  }
+  write_list(d, b, cn, live ? i : -1, own);
+}
+
+// ---------------------------------------------------------------------------
+// size-binned search, large particles.  One cell size trades the cost of
+// each particle's candidate loop against the number of cells it visits
+// (Sec. 3.3); in a polydisperse box cells sized for the largest particle
+// give every small particle a long loop.  A size-binned box (r_split > 0)
+// sizes its cells for the small particles instead (at least 2 r_split and
+// r_max wide): a small particle's partners of radius <= r_split lie within
+// +-1 cell and any partner of a large particle within +-2 cells.  The small
+// search above keeps its half stencil and skips large candidates; here the
+// 125 cells of a large particle's +-2 neighbourhood go through the same two
+// passes (face gaps with the box's largest radius, then the cell's bounding
+// box and largest radius; then the kept cells' members four at a time,
+// warp-uniform).  A large particle takes every small partner and the large
+// partners in later slots, so each pair is found once.
+// Periodic axes need at least 5 cells (the 5 cells of a step are distinct).
+// ---------------------------------------------------------------------------
+
+// Step st (-2..2) along axis a from cell c of a particle at offset o (cell
+// width hc): false outside an open box; else the neighbour cell cc, the
+// fixed-rule shift of its origin, (float)((cc - c) H + image L) exactly as
+// the contact rule rounds it (DEM_MIXED) or st * h, and the squared gap
+// from the particle to the cell's near face (whole cells in between count
+// the ordinary width, which no cell undercuts).
+template <int M>
+__device__ __forceinline__ bool axis_step2(const BoxDev& B, int a, int c, int st, float o,
+                                           float hc, int& cc, float& sh, float& g2) {
+  const int n = B.n[a];
+  cc = c + st;
+  int image = 0;
+  if (cc < 0) {
+    if (!B.periodic[a]) return false;
+    cc += n;
+    image = -1;
+  } else if (cc >= n) {
+    if (!B.periodic[a]) return false;
+    cc -= n;
+    image = 1;
+  }
+  const float H = B.hcell[a][0];
+  const float gap = st > 0 ? (hc - o) + (float)(st - 1) * H
+                           : (st < 0 ? o + (float)(-st - 1) * H : 0.0f);
+  const float gp = fmaxf(gap, 0.0f);
+  g2 = gp * gp;
+  if (M == kMIXED) {
+    const long long S = (long long)(cc - c) * B.Hq[a] + (long long)image * B.Lq[a];
+    sh = __fmul_rn(i64_to_f32_rn(S), kQ);
+  } else {
+    sh = (float)st * (float)B.h[a];
+  }
+  return true;
+}
+
+// Five lanes per large particle, six particles per warp (lanes 30 and 31
+// idle): lane s of a group takes the 25 cells of z step s - 2.  Hits of a
+// group go into the particle's row in (iteration, candidate, lane) order by
+// ballots; the group then writes the particle's block of the list (one
+// atomic per warp) and the partners' incoming rows, five entries at a time.
+template <int M>
+__global__ void __launch_bounds__(256)
+k_candidates_large(Dev d, PState b, CList cn) {
+  using T = Tr<M>;
+  using PR = typename T::PR;
+  const PR* __restrict__ posr = (const PR*)b.posr;
+  const float4* __restrict__ cellbox = d.cellbox;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int grp = lane / 5, s = lane - 5 * grp;  // grp 6: lanes 30, 31
+  const unsigned gmask = grp < 6 ? 0x1Fu << (5 * grp) : 0u;
+  const unsigned lt = (1u << lane) - 1u;
+  const int K = d.K;
+  const int nl = *d.nlarge;
+  const int nwarps = gridDim.x * (blockDim.x >> 5);
+  for (int w0 = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); 6 * w0 < nl; w0 += nwarps) {
+    const int t = 6 * w0 + grp;
+    const bool has = grp < 6 && t < nl;
+    const int i = has ? d.large[t] : 0;
+    const BoxDev& B = d.boxes[d.slot_box[i]];
+    const PR pi = ld4(posr + i);
+    int c[3];
+    unpack_cell(b.cellc[i], c[0], c[1], c[2]);
+    float oi[3], hc[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      hc[a] = c[a] == B.n[a] - 1 ? B.hcell[a][1] : B.hcell[a][0];
+      if (M == kMIXED) oi[a] = (float)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z);
+      else oi[a] = (float)((double)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z) - (double)c[a] * B.h[a]);
+    }
+    const float ri = (float)pi.w;
+    const float rb = 1.001f * (ri + B.rmax_f);
+    const float rb2 = rb * rb;
+    // Pass 1: keep bit ky 5 + kx of the lane's 25 cells
+    unsigned keep = 0u;
+    int cz = 0;
+    float shz = 0.0f, gz2 = 0.0f;
+    if (has && axis_step2<M>(B, 2, c[2], s - 2, oi[2], hc[2], cz, shz, gz2) && gz2 <= rb2) {
+      unsigned xok = 0u;
+      int xc[5];
+      float xsh[5], xg2[5];
+#pragma unroll
+      for (int kx = 0; kx < 5; ++kx)
+        if (axis_step2<M>(B, 0, c[0], kx - 2, oi[0], hc[0], xc[kx], xsh[kx], xg2[kx])) xok |= 1u << kx;
+#pragma unroll
+      for (int ky = 0; ky < 5; ++ky) {
+        int cy;
+        float shy, gy2;
+        if (!axis_step2<M>(B, 1, c[1], ky - 2, oi[1], hc[1], cy, shy, gy2)) continue;
+        const float gzy = gz2 + gy2;
+        if (gzy > rb2) continue;
+        const int row = B.lin_base + (cz * B.n[1] + cy) * B.n[0];
+#pragma unroll
+        for (int kx = 0; kx < 5; ++kx) {
+          if (!((xok >> kx) & 1u) || gzy + xg2[kx] > rb2) continue;
+          const int lin = row + xc[kx];
+          const float4 blo = __ldg(cellbox + 2 * lin), bhi = __ldg(cellbox + 2 * lin + 1);
+          const float gx = fmaxf(fmaxf(blo.x + xsh[kx] - oi[0], oi[0] - (bhi.x + xsh[kx])), 0.0f);
+          const float gy = fmaxf(fmaxf(blo.y + shy - oi[1], oi[1] - (bhi.y + shy)), 0.0f);
+          const float gz = fmaxf(fmaxf(blo.z + shz - oi[2], oi[2] - (bhi.z + shz)), 0.0f);
+          const float reach = 1.001f * (ri + blo.w);
+          if (blo.w >= 0.0f && gx * gx + gy * gy + gz * gz <= reach * reach) keep |= 1u << (ky * 5 + kx);
+        }
+      }
+    }
+    // Pass 2, warp-uniform: every lane its next four candidates per
+    // iteration; the group's hits are counted by ballot
+    int* rowp = d.row + (size_t)i * K;
+    const float rs = B.rsplit_f;
+    int own = 0;
+    int j = 0, e = 0;
+    float sx = 0.f, sy = 0.f;
+    // the next kept cell's range is loaded one cell ahead of its use
+    bool nxt = false;
+    int2 crn = make_int2(0, 0);
+    float nsx = 0.f, nsy = 0.f;
+    auto take = [&]() {
+      nxt = keep != 0u;
+      if (!nxt) return;
+      const int idx = __ffs(keep) - 1;
+      keep &= keep - 1u;
+      int cx, cy;
+      float g2;
+      axis_step2<M>(B, 0, c[0], idx % 5 - 2, oi[0], hc[0], cx, nsx, g2);
+      axis_step2<M>(B, 1, c[1], idx / 5 - 2, oi[1], hc[1], cy, nsy, g2);
+      crn = __ldg(d.crange + B.lin_base + (cz * B.n[1] + cy) * B.n[0] + cx);
+    };
+    take();
+    while (__any_sync(full, j < e || nxt)) {
+      if (j >= e && nxt) {
+        j = crn.x;
+        e = crn.x + crn.y;
+        sx = nsx;
+        sy = nsy;
+        take();
+      }
+      unsigned hm = 0u;
+      if (j < e) {
+        const int m = e - j;
+        const PR p0 = ld4(posr + j);
+        const PR p1 = m > 1 ? ld4(posr + j + 1) : p0;
+        const PR p2 = m > 2 ? ld4(posr + j + 2) : p0;
+        const PR p3 = m > 3 ? ld4(posr + j + 3) : p0;
+        if (M == kMIXED) {
+          const float4& q = *(const float4*)&pi;
+          const float2 nxy = make_float2(-q.x, -q.y), nzw = make_float2(-q.z, q.w);
+          const float2 sxy = make_float2(sx, sy), sz0 = make_float2(shz, 0.0f);
+          hm = (unsigned)pred_fixed_packed(*(const float4*)&p0, nxy, nzw, sxy, sz0) |
+               ((unsigned)pred_fixed_packed(*(const float4*)&p1, nxy, nzw, sxy, sz0) << 1) |
+               ((unsigned)pred_fixed_packed(*(const float4*)&p2, nxy, nzw, sxy, sz0) << 2) |
+               ((unsigned)pred_fixed_packed(*(const float4*)&p3, nxy, nzw, sxy, sz0) << 3);
+        } else {
+          hm = (unsigned)pred_abs(pi, p0, B) | ((unsigned)pred_abs(pi, p1, B) << 1) |
+               ((unsigned)pred_abs(pi, p2, B) << 2) | ((unsigned)pred_abs(pi, p3, B) << 3);
+        }
+        hm &= (m >= 4) ? 0xFu : ((1u << m) - 1u);
+        // not the particle itself, nor a large partner in an earlier slot
+        // (that partner's own search finds the pair)
+        hm &= ~((unsigned)(j == i || (j < i && is_large(p0.w, rs))) |
+                ((unsigned)(j + 1 == i || (j + 1 < i && is_large(p1.w, rs))) << 1) |
+                ((unsigned)(j + 2 == i || (j + 2 < i && is_large(p2.w, rs))) << 2) |
+                ((unsigned)(j + 3 == i || (j + 3 < i && is_large(p3.w, rs))) << 3));
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const bool hit = (hm >> v) & 1u;
+        const unsigned bal = __ballot_sync(full, hit) & gmask;
+        const int pos = own + __popc(bal & lt);
+        if (hit && pos < K) rowp[pos] = j + v;
+        own += __popc(bal);
+      }
+      j += 4;
+    }
+    __syncwarp();
+    // the group's particle: its block of the list, one atomic per warp
+    int n = own;
+    if (n > K) {
+      if (has && s == 0) flag(d.status, kStRowOverflow);
+      n = K;
+    }
+    const int incl = warp_incl_scan((has && s == 0) ? n : 0);
+    int base = 0;
+    if (lane == 31 && incl > 0) base = atomicAdd(cn.count, incl);
+    base = __shfl_sync(full, base, 31);
+    const int gincl = __shfl_sync(full, incl, 5 * min(grp, 5));
+    if (has) {
+      const long long pre = (long long)base + gincl - n;
+      if (pre + n > d.Cmax) {
+        if (s == 0) flag(d.status, kStListOverflow);
+        n = (int)max(0ll, (long long)d.Cmax - pre);
+      }
+      const int hs = (int)min(pre, (long long)d.Cmax);
+      if (s == 0) {
+        cn.hs[i] = hs;
+        cn.oc[i] = n;
+      }
+      const int idi = b.id[i];
+      for (int k = s; k < n; k += 5) {
+        const int j2 = rowp[k], c2 = hs + k;
+        const int pos = d.inrow ? atomicAdd(d.icnt + j2, 1) : K;
+        const int idj = b.id[j2];
+        cn.pair[c2] = idi < idj ? make_int2(i, j2) : make_int2(j2, i);
+        cn.hid[c2] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
+        if (pos < K) d.inrow[(size_t)j2 * K + pos] = make_int2(c2, (i << 1) | (idj < idi ? 1 : 0));
+      }
     }
   }
 }

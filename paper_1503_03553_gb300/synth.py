@@ -63,6 +63,8 @@ class Box:
     restitution: float = 0.5
     mu_d: float = 0.3
     walls: tuple = ()        # (kind, p, u, v): 0 = rectangle, 1 = line
+    r_split: float = 0.0     # size-binned search: radius above which a
+                             # particle searches +-2 cells (0 = off)
 
     @property
     def n(self) -> int:
@@ -249,6 +251,27 @@ def w2_polydisperse(n: int = 1_000_000, seed: int = 2, tile_n: int = 8000,
     k^3 times with n = k^3 * n_tile (n is rounded to that form)."""
     rng = rng_for(seed)
     radii = lambda g, m: _lognormal_radii(g, m, 4e-6, 0.25, 2e-6, 8e-6)
+    if n <= tile_n:
+        x, r, L = _dense_tile(rng, n, phi, radii, 0.01)
+    else:
+        k = max(1, int(round((n / tile_n) ** (1.0 / 3.0))))
+        n0 = int(round(n / k ** 3))
+        x0, r0, L0 = _dense_tile(rng, n0, phi, radii, 0.01)
+        x, r, L = _tile(rng, x0, r0, L0, k)
+    m = len(r)
+    v = _gauss(rng, m, 0.05)
+    w = 1e3 * rng.standard_normal((m, 3))
+    return Box(x=x, v=v, w=w, r=r, L=L, dt=1.0e-9, restitution=0.5, mu_d=0.3)
+
+
+def wide_polydisperse(n: int = 1_000_000, seed: int = 6, tile_n: int = 8000,
+                      phi: float = 0.5) -> Box:
+    """Dense periodic box with radii spanning a factor 8 (log-normal,
+    median 3 um, log-sd 0.5, clipped to [1, 8] um): the regime where one
+    cell size, set by the largest particle, gives the small particles long
+    candidate loops.  Built like W2 (relaxed tile, repeated k^3 times)."""
+    rng = rng_for(seed)
+    radii = lambda g, m: _lognormal_radii(g, m, 3e-6, 0.5, 1e-6, 8e-6)
     if n <= tile_n:
         x, r, L = _dense_tile(rng, n, phi, radii, 0.01)
     else:

@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 def test_abi_version(lib):
     import paper_1503_03553_gb300 as D
-    assert D.dem_abi_version() == 2
+    assert D.dem_abi_version() == 3
 
 
 @pytest.mark.parametrize("eps", [0.3, 0.5, 0.9, 0.99])
