@@ -39,7 +39,7 @@ L2_BYTES = 126.5 * 2 ** 20
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
@@ -502,6 +502,7 @@ def _side_legs(args, D, torch, box, ncell, stream):
     out["force_error_vs_fp64_oracle"] = errs
     out["collide_fused_vs_compact"] = _fused_leg(args, D, torch, stream, box, ncell)
     out["size_binned_search"] = _size_binned_leg(args, D, torch, stream, box, ncell)
+    out["fig4_kernel_times_131k"] = _fig4_leg(args, D, torch, stream)
     if not args.no_batched:
         out["batched"] = _batched_leg(args, D, torch, stream)
     if args.w3:
@@ -689,6 +690,33 @@ def _size_binned_leg(args, D, torch, stream, box, ncell):
             r.update({"r_split_um": rs * 1e6, "search_ms": ph["search"], "sort_ms": ph["sort"]})
             rows.append(r)
         out[name] = {"particles": b0.n, "rows": rows}
+    return out
+
+
+def _fig4_leg(args, D, torch, stream):
+    """The paper's kernel-time comparison (Sec. 5.2, Fig. 4) at its size,
+    131,072 particles: dense (W2 law and packing, left graph) and the
+    initialisation stage, where no particles touch (lattice gas, right
+    graph); per-phase ms of the previous Collide (Algorithm 1 as printed,
+    fused), the paper's two-loop Collide and the contact-list pipeline."""
+    from paper_1503_03553_gb300 import synth
+    from parity import grid_for, prepared
+    n = 131072
+    out = {}
+    for name, b0 in (("dense", synth.w2_polydisperse(n=n, seed=2)),
+                     ("initialisation_no_contacts", synth.lattice_gas(n=n, seed=7))):
+        b = prepared(b0, "mixed")
+        nc = grid_for(b)
+        rows = {"particles": b.n}
+        for form_name, form in (("fused_previous", D.DEM_COLLIDE_FUSED),
+                                ("twoloop_paper", D.DEM_COLLIDE_TWOLOOP),
+                                ("contact_list", D.DEM_COLLIDE_COMPACT)):
+            ph = _phase_ms(D, torch, stream, [b], "mixed", [nc], 50, collide=form)
+            ph["collide"] = ph["search"] + ph["compact"] + ph["force"]
+            rows[form_name] = {k: round(v, 5) for k, v in ph.items()}
+        rows["twoloop_speedup_over_fused_collide"] = (rows["fused_previous"]["collide"] /
+                                                      rows["twoloop_paper"]["collide"])
+        out[name] = rows
     return out
 
 

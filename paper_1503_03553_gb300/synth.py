@@ -285,6 +285,25 @@ def wide_polydisperse(n: int = 1_000_000, seed: int = 6, tile_n: int = 8000,
     return Box(x=x, v=v, w=w, r=r, L=L, dt=1.0e-9, restitution=0.5, mu_d=0.3)
 
 
+def lattice_gas(n: int = 131072, seed: int = 7, jitter: float = 0.05) -> Box:
+    """The initialisation stage of the paper's runs (Sec. 5.2): particles
+    created on a uniform cubic lattice with small random offsets, none in
+    contact.  W2's radius law; lattice spacing 2.2 r_max, so that offsets of
+    up to +-jitter r_max per component leave every pair apart; the first n
+    sites of a k^3 lattice, periodic box of k spacings."""
+    rng = rng_for(seed)
+    r = _lognormal_radii(rng, n, 4e-6, 0.25, 2e-6, 8e-6)
+    a = 2.2 * 8e-6
+    k = int(math.ceil(n ** (1.0 / 3.0) - 1e-9))
+    idx = np.arange(n)
+    site = np.stack([idx % k, (idx // k) % k, idx // (k * k)], axis=1).astype(np.float64)
+    x = (site + 0.5) * a + jitter * 8e-6 * rng.uniform(-1.0, 1.0, (n, 3))
+    L = (k * a,) * 3
+    v = _gauss(rng, n, 0.05)
+    w = 1e3 * rng.standard_normal((n, 3))
+    return Box(x=x, v=v, w=w, r=r, L=L, dt=1.0e-9, restitution=0.5, mu_d=0.3)
+
+
 def w3_bidisperse_floor(n: int = 8_000_000, seed: int = 3,
                         column_n: int = 20000) -> Box:
     """W3: bidisperse spheres (r = 3 and 6 um, 50/50 by number) in a cube,

@@ -55,3 +55,21 @@ def test_w4_boxes_vary():
     for b in boxes:
         assert 0.2 <= _phi(b) <= 0.5 + 1e-9
         assert 0.1 <= b.mu_d <= 0.6
+
+
+def test_wide_polydisperse_radii_span_a_factor_8():
+    b = synth.wide_polydisperse(n=3000, seed=6)
+    assert abs(_phi(b) - 0.5) < 1e-9
+    assert b.r.min() >= np.float32(1e-6) and b.r.max() <= np.float32(8e-6)
+    assert np.sum(b.r < 1.5e-6) > 0 and np.sum(b.r > 6e-6) > 0
+    assert abs(np.median(b.r) - 3e-6) < 0.2e-6
+
+
+def test_lattice_gas_has_no_contacts():
+    b = synth.lattice_gas(n=3000, seed=7)
+    assert b.n == 3000
+    from scipy.spatial import cKDTree
+    L = np.asarray(b.L)
+    t = cKDTree(np.mod(b.x, L), boxsize=L)
+    d, _ = t.query(np.mod(b.x, L), k=2)
+    assert np.all(d[:, 1] > 2 * b.r.max())
