@@ -778,8 +778,8 @@ __device__ __forceinline__ bool axis_step(const BoxDev& B, int a, int c, int s,
 // Pass 1 decides, with independent loads, which neighbour cells can hold a
 // contact: a cell is skipped when its nearest point is farther than r_i plus
 // the largest radius in that cell (0.1 % margin, far above rounding).
-// Pass 2 tests the candidates of the kept cells in (dz, dy, dx) order, four
-// at a time so that four loads are in flight.
+// Pass 2 tests the candidates of the kept cells in (dz, dy, dx) order, eight
+// at a time so that eight loads are in flight.
 // ---------------------------------------------------------------------------
 
 // Size classes of a size-binned box: a particle is large when its radius,
@@ -878,7 +878,7 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
   const int K = d.K;
   int* rowp = d.row + (size_t)i * K;
   bool over = false;
-  // Pass 2, warp-uniform: each iteration every lane tests its next four
+  // Pass 2, warp-uniform: each iteration every lane tests its next eight
   // candidates, first moving on to its next kept cell when the current one is
   // exhausted; one reconvergence point per iteration keeps the lanes of a
   // warp testing together (iterations ~ the largest per-lane candidate count).
@@ -904,29 +904,23 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
     }
     if (j < e) {
       const int m = e - j;
-      const PR p0 = ld4(posr + j);
-      const PR p1 = m > 1 ? ld4(posr + j + 1) : p0;
-      const PR p2 = m > 2 ? ld4(posr + j + 2) : p0;
-      const PR p3 = m > 3 ? ld4(posr + j + 3) : p0;
-      unsigned hm;
-      if (M == kMIXED) {
-        const float4& q = *(const float4*)&pi;
-        const float2 nxy = make_float2(-q.x, -q.y), nzw = make_float2(-q.z, q.w);
-        const float2 sxy = make_float2(sx, sy), sz0 = make_float2(sz, 0.0f);
-        hm = (unsigned)pred_fixed_packed(*(const float4*)&p0, nxy, nzw, sxy, sz0) |
-             ((unsigned)pred_fixed_packed(*(const float4*)&p1, nxy, nzw, sxy, sz0) << 1) |
-             ((unsigned)pred_fixed_packed(*(const float4*)&p2, nxy, nzw, sxy, sz0) << 2) |
-             ((unsigned)pred_fixed_packed(*(const float4*)&p3, nxy, nzw, sxy, sz0) << 3);
-      } else {
-        hm = (unsigned)pred_abs(pi, p0, B) | ((unsigned)pred_abs(pi, p1, B) << 1) |
-             ((unsigned)pred_abs(pi, p2, B) << 2) | ((unsigned)pred_abs(pi, p3, B) << 3);
+      unsigned hm = 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const PR pu = ld4(posr + j + (u < m ? u : 0));
+        bool h;
+        if (M == kMIXED) {
+          const float4& q = *(const float4*)&pi;
+          const float2 nxy = make_float2(-q.x, -q.y), nzw = make_float2(-q.z, q.w);
+          const float2 sxy = make_float2(sx, sy), sz0 = make_float2(sz, 0.0f);
+          h = pred_fixed_packed(*(const float4*)&pu, nxy, nzw, sxy, sz0);
+        } else {
+          h = pred_abs(pi, pu, B);
+        }
+        hm |= (unsigned)h << u;
+        if (kSplit && is_large(pu.w, B.rsplit_f)) hm &= ~(1u << u);
       }
-      hm &= (m >= 4) ? 0xFu : ((1u << m) - 1u);
-      if (kSplit) {
-        const float rs = B.rsplit_f;
-        hm &= ~((unsigned)is_large(p0.w, rs) | ((unsigned)is_large(p1.w, rs) << 1) |
-                ((unsigned)is_large(p2.w, rs) << 2) | ((unsigned)is_large(p3.w, rs) << 3));
-      }
+      hm &= (m >= 8) ? 0xFFu : ((1u << m) - 1u);
       while (hm) {
         const int jj = j + __ffs(hm) - 1;
         hm &= hm - 1u;
@@ -936,7 +930,7 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
           rowp[own++] = jj;
         }
       }
-      j += 4;
+      j += 8;
     }
     __syncwarp(wmask);
   }
@@ -992,7 +986,7 @@ __device__ __forceinline__ void write_list(const Dev& d, const PState& b, const 
 // kSplit: some box is size-binned; its large particles are not searched
 // here but appended to d.large for k_candidates_large.
 template <int M, bool kSplit>
-__global__ void __launch_bounds__(256, M == kFP64 ? 4 : 5)
+__global__ void __launch_bounds__(256, 4)
 k_candidates(Dev d, PState b, CList cn) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // whole warps run
   int own = 0;
