@@ -39,7 +39,7 @@ L2_BYTES = 126.5 * 2 ** 20
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
@@ -348,22 +348,33 @@ def main():
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         ctx = D.Context([box], precision=args.precision, ncell=[ncell])
-    ctx.set_particles(0, box.x, box.v, box.w, box.r)
+    # the workload is steps 1..K from the initial state: warm up from it,
+    # then start again from it
+    _reset(ctx, [box])
     ctx.step(args.warmup)
-    contacts_before = ctx.stats(0)[5]
+    _reset(ctx, [box])
     # ---- timed region: K steps, CUDA graphs, device time -------------------
     with ClockSampler(local) as clk:
         secs = _time_steps(ctx, torch, args.steps, world)
     secs = _max_over_ranks(secs, world, torch)
     value = job_throughput(n, world, args.steps, secs)
-    stats = ctx.stats(0)
-    c_half = stats[5] / n
-    # half contacts evaluated per second (mean of the counts before and after)
-    contact_evals = 0.5 * (contacts_before + stats[5]) * world * args.steps / secs
-    # ---- per-phase device time (same workload, direct launches) -----------
+    # ---- the same K steps again, untimed: contacts along the trajectory ---
+    # (the packing relaxes: the contact count falls during the run)
+    _reset(ctx, [box])
+    counts, chunk, done = [], max(1, args.steps // 20), 0
+    while done < args.steps:
+        k = min(chunk, args.steps - done)
+        ctx.step(k)
+        done += k
+        counts.append((k, ctx.stats(0)[5]))
+    contacts_total = sum(k * c for k, c in counts)  # each chunk at its end count
+    c_half = contacts_total / args.steps / n
+    # half contacts evaluated per second over the timed steps
+    contact_evals = contacts_total * world / secs
+    # ---- per-phase device time: the same K steps, direct launches ---------
+    _reset(ctx, [box])
     ctx.set_timing(True)
-    phase_steps = min(100, max(10, args.steps // 4))
-    ctx.step(phase_steps)
+    ctx.step(args.steps)
     ph = ctx.phase_times()
     ctx.set_timing(False)
     ncells = int(np.prod(ncell))
@@ -416,7 +427,8 @@ def main():
     # the new state back to pinned host memory
     pin = lambda: torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
     hx, hv, hw = pin(), pin(), pin()
-    D.dem_get_state(ctx.ctx, 0, hx, hv, hw, None, None)
+    _reset(ctx, [box])
+    hx[:], hv[:], hw[:] = box.x, box.v, box.w
     _barrier(world)
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
@@ -449,7 +461,9 @@ def main():
                   "fp64": "f64", "fp32": "f32"}[args.precision],
         "data": "synthetic (seeded generator)",
         "config": {"workload": f"W2 polydisperse periodic box, {n} particles per GPU, "
-                   "packing 0.55, dense contact network",
+                   "packing 0.55, dense contact network; steps 1..K from the initial "
+                   "state (the packing relaxes: contacts fall during the run)",
+                   "steps_from_initial_state": args.steps,
                    "n_per_gpu": n, "precision": args.precision, "ncell": ncell,
                    "contacts_per_particle": c_half,
                    "l2": f"inputs larger than L2: a step touches {total_bytes / 1e6:.0f} MB "
@@ -462,13 +476,21 @@ def main():
     print(json.dumps(line))
 
 
+def _reset(ctx, boxes):
+    """Every box back to its initial particles (empty contact history)."""
+    for k, b in enumerate(boxes):
+        ctx.set_particles(k, b.x, b.v, b.w, b.r)
+
+
 def _throughput(D, torch, stream, boxes, precision, ncells, steps, warmup=3, **kw):
+    """Steps 1..steps of the workload from its initial state (after an
+    untimed warm-up from the same state), device time."""
     with torch.cuda.stream(stream):
         ctx = D.Context(boxes, precision=precision, ncell=ncells, **kw)
     try:
-        for k, b in enumerate(boxes):
-            ctx.set_particles(k, b.x, b.v, b.w, b.r)
+        _reset(ctx, boxes)
         ctx.step(warmup)
+        _reset(ctx, boxes)
         secs = _time_steps(ctx, torch, steps, 1)
     finally:
         ctx.close()
@@ -484,9 +506,8 @@ def _side_legs(args, D, torch, box, ncell, stream):
     from parity import (check_one_step, force_errors, gpu_run, oracle_run,
                         prepared)
     out = {}
-    k = max(8, args.steps // 20)
-    out["fp64_gpu"] = _throughput(D, torch, stream, [box], "fp64", [ncell], k)
-    out["fp32_gpu"] = _throughput(D, torch, stream, [box], "fp32", [ncell], max(16, args.steps // 4))
+    out["fp64_gpu"] = _throughput(D, torch, stream, [box], "fp64", [ncell], args.steps)
+    out["fp32_gpu"] = _throughput(D, torch, stream, [box], "fp32", [ncell], args.steps)
     errs = {}
     for prec in ("mixed", "fp32", "fp64"):
         b = prepared(box, prec)
@@ -523,7 +544,7 @@ def _sweep_leg(args, D, torch, stream):
     for n in (100_000, 300_000, 1_000_000, 3_000_000, 8_000_000):
         box = prepared(synth.w2_polydisperse(n=n, seed=2), "mixed")
         nc = grid_for(box)
-        steps = max(20, int(2e8 / box.n))
+        steps = 200  # the same steps 1..200 from the initial state at every size
         r = _throughput(D, torch, stream, [box], "mixed", [nc], steps, warmup=5)
         r.update({"particles": box.n, "ncell": nc})
         rows.append(r)
@@ -539,14 +560,16 @@ def _w3_leg(args, D, torch, stream):
     box = prepared(synth.w3_bidisperse_floor(n=8_000_000, seed=3), "mixed")
     nc = grid_for(box)
     res = {"particles": box.n, "ncell": nc}
-    res["mixed_compact"] = _throughput(D, torch, stream, [box], "mixed", [nc], 40)
-    res["mixed_compact"]["phase_ms"] = _phase_ms(D, torch, stream, [box], "mixed", [nc], 10)
-    res["mixed_fused"] = _throughput(D, torch, stream, [box], "mixed", [nc], 8,
+    k = 500  # the workload's steps, 1..500 from the initial state, every form
+    res["steps"] = k
+    res["mixed_compact"] = _throughput(D, torch, stream, [box], "mixed", [nc], k)
+    res["mixed_compact"]["phase_ms"] = _phase_ms(D, torch, stream, [box], "mixed", [nc], k)
+    res["mixed_fused"] = _throughput(D, torch, stream, [box], "mixed", [nc], k,
                                      collide=D.DEM_COLLIDE_FUSED)
-    res["mixed_twoloop"] = _throughput(D, torch, stream, [box], "mixed", [nc], 8,
+    res["mixed_twoloop"] = _throughput(D, torch, stream, [box], "mixed", [nc], k,
                                        collide=D.DEM_COLLIDE_TWOLOOP)
-    res["fp32_compact"] = _throughput(D, torch, stream, [box], "fp32", [nc], 40)
-    res["fp64_compact"] = _throughput(D, torch, stream, [box], "fp64", [nc], 8)
+    res["fp32_compact"] = _throughput(D, torch, stream, [box], "fp32", [nc], k)
+    res["fp64_compact"] = _throughput(D, torch, stream, [box], "fp64", [nc], k)
     return res
 
 
@@ -632,12 +655,14 @@ def _w5_leg(args, D, torch, stream):
 
 
 def _phase_ms(D, torch, stream, boxes, precision, ncells, steps, **kw):
+    """Per-phase device time averaged over steps 1..steps from the initial
+    state (kernels launched one by one, events between phases)."""
     with torch.cuda.stream(stream):
         ctx = D.Context(boxes, precision=precision, ncell=ncells, **kw)
     try:
-        for k, b in enumerate(boxes):
-            ctx.set_particles(k, b.x, b.v, b.w, b.r)
+        _reset(ctx, boxes)
         ctx.step(3)
+        _reset(ctx, boxes)
         ctx.set_timing(True)
         ctx.step(steps)
         return dict(zip(PHASES, ctx.phase_times().tolist()))
@@ -653,15 +678,15 @@ def _fused_leg(args, D, torch, stream, box, ncell):
     pipeline here (search, dense contact list, one thread per contact).
     'collide' is the contact part of the step: the per-particle kernel vs
     search + list + force."""
-    steps = max(16, args.steps // 8)
+    steps = args.steps
     out = {}
     coll = {}
     for name, form in (("fused", D.DEM_COLLIDE_FUSED), ("twoloop", D.DEM_COLLIDE_TWOLOOP)):
         out[f"{name}_step"] = _throughput(D, torch, stream, [box], "mixed", [ncell], steps,
                                           collide=form)
-        pf = _phase_ms(D, torch, stream, [box], "mixed", [ncell], 20, collide=form)
+        pf = _phase_ms(D, torch, stream, [box], "mixed", [ncell], steps, collide=form)
         coll[name] = pf["search"] + pf["compact"] + pf["force"]
-    pc = _phase_ms(D, torch, stream, [box], "mixed", [ncell], 20)
+    pc = _phase_ms(D, torch, stream, [box], "mixed", [ncell], steps)
     coll["compact"] = pc["search"] + pc["compact"] + pc["force"]
     out.update({"collide_ms_fused": coll["fused"], "collide_ms_twoloop": coll["twoloop"],
                 "collide_ms_compact": coll["compact"],
@@ -678,7 +703,7 @@ def _size_binned_leg(args, D, torch, stream, box, ncell):
     import dataclasses
     from paper_1503_03553_gb300 import synth
     from parity import prepared
-    steps = max(16, args.steps // 8)
+    steps = args.steps
     wide = prepared(synth.wide_polydisperse(n=box.n, seed=6), "mixed")
     out = {}
     for name, b0, splits in (("w2", box, (0.0, 5.5e-6, 6e-6)), ("radii_1_8um", wide, (0.0, 4e-6, 5e-6))):
@@ -686,7 +711,7 @@ def _size_binned_leg(args, D, torch, stream, box, ncell):
         for rs in splits:
             b = dataclasses.replace(b0, r_split=rs)
             r = _throughput(D, torch, stream, [b], "mixed", None, steps)
-            ph = _phase_ms(D, torch, stream, [b], "mixed", None, 20)
+            ph = _phase_ms(D, torch, stream, [b], "mixed", None, steps)
             r.update({"r_split_um": rs * 1e6, "search_ms": ph["search"], "sort_ms": ph["sort"]})
             rows.append(r)
         out[name] = {"particles": b0.n, "rows": rows}
@@ -711,7 +736,7 @@ def _fig4_leg(args, D, torch, stream):
         for form_name, form in (("fused_previous", D.DEM_COLLIDE_FUSED),
                                 ("twoloop_paper", D.DEM_COLLIDE_TWOLOOP),
                                 ("contact_list", D.DEM_COLLIDE_COMPACT)):
-            ph = _phase_ms(D, torch, stream, [b], "mixed", [nc], 50, collide=form)
+            ph = _phase_ms(D, torch, stream, [b], "mixed", [nc], 200, collide=form)
             ph["collide"] = ph["search"] + ph["compact"] + ph["force"]
             rows[form_name] = {k: round(v, 5) for k, v in ph.items()}
         rows["twoloop_speedup_over_fused_collide"] = (rows["fused_previous"]["collide"] /
@@ -737,8 +762,9 @@ def _batched_leg(args, D, torch, stream):
         with torch.cuda.stream(stream):
             ctx = D.Context([b], precision="mixed", ncell=[nc])
         try:
-            ctx.set_particles(0, b.x, b.v, b.w, b.r)
+            _reset(ctx, [b])
             ctx.step(3)
+            _reset(ctx, [b])
             total += _time_steps(ctx, torch, steps, 1)
         finally:
             ctx.close()
