@@ -136,8 +136,9 @@ typedef struct {
   double r_max;           /* largest radius the box will hold [m]         */
   int32_t nwalls;         /* rectangle and line walls (0 = none)           */
   const dem_wall* walls;  /* nwalls entries, read during dem_create        */
-  double r_split;         /* size-binned contact search (0 = off), for     */
-                          /* polydisperse boxes: a particle of radius      */
+  double r_split;         /* size-binned contact search (0 = off; Sec. 3.3 */
+                          /* cell-size trade-off), for polydisperse boxes: */
+                          /* a particle of radius                          */
                           /* above r_split searches the +-2 neighbour      */
                           /* cells for all its partners, the others search */
                           /* +-1 cells for partners of radius up to        */
