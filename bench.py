@@ -50,7 +50,7 @@ def _args():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--no-batched", action="store_true", help="skip the W4 batched leg")
     ap.add_argument("--nboxes", type=int, default=512)
-    ap.add_argument("--batched-steps", type=int, default=32)
+    ap.add_argument("--batched-steps", type=int, default=100)
     ap.add_argument("--w3", action="store_true",
                     help="add the 8M-particle floor/gravity leg (dense + dilute halves)")
     ap.add_argument("--w5", action="store_true",
