@@ -61,6 +61,8 @@ def _args():
     ap.add_argument("--w5-n", type=int, default=4_000_000)
     ap.add_argument("--w5-steps", type=int, default=10_000)
     ap.add_argument("--w5-every", type=int, default=1_000)
+    ap.add_argument("--w5-forms", default="mixed,fp32,fp64",
+                    help="precision forms of the W5 leg, comma-separated")
     return ap.parse_args()
 
 
@@ -589,7 +591,7 @@ def _w5_oracle(path):
     p = oracle_params(b2, prec, ncell)
     out = O.step(p, s)
     out["params"] = p
-    return force_errors(b2, g, out, prec)
+    return force_errors(b2, g, out, prec, detail=5)
 
 
 def _w5_leg(args, D, torch, stream):
@@ -611,7 +613,7 @@ def _w5_leg(args, D, torch, stream):
     workers = max(1, min(8, (os.cpu_count() or 2) - 2))
     pending = []
     with mp.get_context("spawn").Pool(workers) as pool:
-        for prec in ("mixed", "fp32", "fp64"):
+        for prec in args.w5_forms.split(","):
             b = prepared(raw, prec)
             nc = grid_for(b)
             with torch.cuda.stream(stream):
@@ -625,7 +627,7 @@ def _w5_leg(args, D, torch, stream):
                     hist = ctx.contacts(0)
                     ctx.step(1)
                     g = {}
-                    g["lo"], g["hi"], _ = ctx.contacts(0)
+                    g["lo"], g["hi"], g["dt"] = ctx.contacts(0)
                     _, _, g["Fc"], _ = ctx.contact_forces(0)
                     b2 = prepared(b, prec)
                     b2.x, b2.v, b2.w = st["x"], st["v"], st["w"]
@@ -643,7 +645,7 @@ def _w5_leg(args, D, torch, stream):
                 ctx.close()
         for prec, step, r in pending:
             res[prec].setdefault("snapshots", []).append({"step": step, **r.get()})
-    for prec in ("mixed", "fp32", "fp64"):
+    for prec in args.w5_forms.split(","):
         sn = res[prec]["snapshots"]
         res[prec]["worst_max_err_over_scale"] = max(x.get("max_err_over_scale", float("inf")) for x in sn)
         res[prec]["min_frac_within_1e-5"] = min(x.get("frac_within_1e-5", 0.0) for x in sn)

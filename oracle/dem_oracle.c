@@ -192,7 +192,13 @@ static void contact_force(const orc_params* p, double alpha,
   fn_el = kn * pow(dn, 1.5);
   for (a = 0; a < 3; ++a) Fn[a] = -fn_el * n[a] - eta * vn[a];
   for (a = 0; a < 3; ++a) Ft[a] = -kt * dt_new[a] - eta * vt[a];
-  out->scale = fn_el + eta * fabs(vn_s) + kt * norm3(dt_new) + eta * norm3(vt);
+  /* the size of the terms whose float sum forms F (the error scale of the
+   * parity tests): Eq. (1)'s terms, with eta v_t counted by the terms of
+   * Eq. (vt), |v| + r1 |w1| + r2 |w2|: in a rolling contact the
+   * translational and rotational parts of v_t nearly cancel, and a float
+   * evaluation of v_t errs by the unit roundoff times those parts */
+  out->scale = fn_el + eta * fabs(vn_s) + kt * norm3(dt_new) +
+               eta * (norm3(v) + r1 * norm3(w1) + (r2 > 0.0 ? r2 * norm3(w2) : 0.0));
   absFn = norm3(Fn);
   absFt = norm3(Ft);
   out->ratio = (p->mu_d * absFn > 0.0) ? absFt / (p->mu_d * absFn)

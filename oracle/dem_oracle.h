@@ -88,7 +88,9 @@ typedef struct {
   double nF[3];     /* n x F                                              */
   double n[3];      /* unit normal from the lower-id particle to the other */
   double kt;        /* tangential stiffness k_t                            */
-  double scale;     /* k_n dn^1.5 + eta|v_n| + k_t|delta_t| + eta|v_t|      */
+  double scale;     /* k_n dn^1.5 + eta|v_n| + k_t|delta_t|                 */
+                    /* + eta (|v| + r1|w1| + r2|w2|): Eq. (1)'s terms, v_t  */
+                    /* counted by the terms of Eq. (vt)                      */
   double delta_n;   /* normal overlap                                     */
   double ratio;     /* |F_t| / (mu |F_n|) before the cap                  */
   int32_t capped;   /* 1 if the Coulomb cap fired                          */

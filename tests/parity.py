@@ -9,9 +9,12 @@ order can be compared bit for bit.
 Tolerances (per contact c, oracle values):
   |F_gpu - F_ora|   <= rtol * S_c + f_c
   |nF_gpu - nF_ora| <= rtol * S_c + f_c + 1e-6 |F_ora|
-  S_c = k_n dn^1.5 + eta |v_n| + k_t |delta_t| + eta |v_t|  (sum of the
-        magnitudes of the terms of Eq. (1): the error of a float sum is
-        bounded by the unit roundoff times this, not by |F|)
+  S_c = k_n dn^1.5 + eta |v_n| + k_t |delta_t| + eta (|v| + r1 |w1| + r2 |w2|)
+        (sum of the magnitudes of the terms of Eq. (1), with v_t counted by
+        the terms of Eq. (vt): the error of a float sum is bounded by the
+        unit roundoff times its terms, not by the result; in a rolling
+        contact the translational and rotational parts of v_t nearly
+        cancel)
   f_c = 1e-9 k_n R*^1.5  (absolute floor)
 with rtol = 1e-5 for FP32 force arithmetic and 1e-9 for FP64.  Contacts whose
 Coulomb ratio lies within 1e-4 of 1 may be capped on one side only, and
@@ -221,10 +224,14 @@ def check_one_step(box, g, o, precision, allow_dont_care=True):
     return m
 
 
-def force_errors(box, g, o, precision):
+def force_errors(box, g, o, precision, detail=0):
     """Error statistics of one step against the oracle (no assertion):
     per contact |F_gpu - F_ora| / (S_c + f_c) with the Q15 scale and floor,
-    over the contacts both sides found (the sets must be equal)."""
+    over the contacts both sides found (the sets must be equal).  detail > 0
+    adds the `detail` worst contacts outside the "don't care" classes, each
+    with its error split along and across the normal, overlap over R*,
+    Coulomb ratio, cap flag, |F| and k_t |delta_t| over the scale, and the
+    error of the delta_t after the step (when g has "dt")."""
     same = (len(g["lo"]) == len(o["lo"]) and np.array_equal(g["lo"], o["lo"])
             and np.array_equal(g["hi"], o["hi"]))
     if not same:
@@ -244,7 +251,27 @@ def force_errors(box, g, o, precision):
     Rs = r[o["lo"]] * r[o["hi"]] / (r[o["lo"]] + r[o["hi"]])
     dont = (np.abs(info["ratio"] - 1.0) < 1e-4) | (info["delta_n"] < 1e-10 * Rs)
     keep = ~dont
-    return {"contact_sets_equal": True, "contacts": int(len(e)),
+    worst = []
+    if detail and keep.any():
+        dF = g["Fc"] - info["F"]
+        nrm = info["n"]
+        en = np.abs(np.sum(dF * nrm, axis=1))
+        et = np.linalg.norm(dF - np.sum(dF * nrm, axis=1)[:, None] * nrm, axis=1)
+        den = info["scale"] + floor
+        idx = np.flatnonzero(keep)
+        idx = idx[np.argsort(-e[idx])][:detail]
+        for k in idx:
+            w = {"err": float(e[k]), "err_normal": float(en[k] / den[k]),
+                 "err_tangential": float(et[k] / den[k]),
+                 "dn_over_Rstar": float(info["delta_n"][k] / Rs[k]),
+                 "ratio": float(info["ratio"][k]), "capped": int(info["capped"][k]),
+                 "F_over_scale": float(nF[k] / info["scale"][k]),
+                 "kt_dt_over_scale": float(info["kt"][k] * np.linalg.norm(o["dt"][k]) / info["scale"][k])}
+            if "dt" in g:
+                w["dt_err_rel"] = float(np.linalg.norm(g["dt"][k] - o["dt"][k]) /
+                                        max(np.linalg.norm(o["dt"][k]), 1e-300))
+            worst.append(w)
+    out = {"contact_sets_equal": True, "contacts": int(len(e)),
             "max_err_over_scale": float(e.max()),
             "p99_err_over_scale": float(np.percentile(e, 99)),
             "frac_within_1e-5": float(np.mean(e <= 1e-5)),
@@ -252,3 +279,6 @@ def force_errors(box, g, o, precision):
             "dont_care": int(dont.sum()),
             "max_err_over_scale_cared": float(e[keep].max()) if keep.any() else 0.0,
             "frac_within_1e-5_cared": float(np.mean(e[keep] <= 1e-5)) if keep.any() else 1.0}
+    if detail:
+        out["worst_cared"] = worst
+    return out
