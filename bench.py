@@ -32,7 +32,12 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "particle-steps/s"
+METRIC = "particle-steps/s"  # the unit
+# the headline metric: MIXED (FP32 force arithmetic) and FP64 forms at 1M
+# particles within the 1e-5 force tolerance, batched boxes against one box
+# at a time (the comparison legs under "compare")
+METRIC_NAME = ("particle-steps/s @1M: FP32 vs FP64 GPU at force rel err\u22641e-5; "
+               "batched vs 1-by-1")
 L2_BYTES = 126.5 * 2 ** 20
 
 
@@ -318,7 +323,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     value = box.n * args.steps / dt
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC,
+        "impl": "reference", "metric": METRIC_NAME, "value": value, "unit": METRIC,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -456,19 +461,23 @@ def main():
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "metric": METRIC_NAME, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "contact_evals_per_s": contact_evals,
-        "dtype": {"mixed": "f32 (fixed-point positions, float-float history)",
-                  "fp64": "f64", "fp32": "f32"}[args.precision],
+        "dtype": {"mixed": "f32", "fp64": "f64", "fp32": "f32"}[args.precision],
         "data": "synthetic (seeded generator)",
         "config": {"workload": f"W2 polydisperse periodic box, {n} particles per GPU, "
                    "packing 0.55, dense contact network; steps 1..K from the initial "
                    "state (the packing relaxes: contacts fall during the run)",
                    "steps_from_initial_state": args.steps,
-                   "n_per_gpu": n, "precision": args.precision, "ncell": ncell,
+                   "n_per_gpu": n, "precision": args.precision,
+                   "precision_detail": {"mixed": "FP32 force arithmetic; positions in 64-bit "
+                                        "fixed point (2^-60 m); delta_t as float-float pairs",
+                                        "fp64": "FP64 throughout",
+                                        "fp32": "FP32 throughout"}[args.precision],
+                   "ncell": ncell,
                    "contacts_per_particle": c_half,
                    "l2": f"inputs larger than L2: a step touches {total_bytes / 1e6:.0f} MB "
                          f"of unique data vs {L2_BYTES / 1e6:.0f} MB L2",
