@@ -311,6 +311,32 @@ def test_spin_drives_tangential_force_and_opposing_torque():
     assert out["dt"][0] == pytest.approx([0, vt * dt, 0], rel=1e-12)
 
 
+def test_error_scale_counts_the_terms_of_the_velocity():
+    """The parity tolerance's scale S_c: the magnitudes of the terms of
+    Eq. (1), with eta v_t counted by the terms of Eq. (vt) (|v| + r1 |w1| +
+    r2 |w2|).  A rolling contact: particle 1 translates along +y at u while
+    spinning so that its contact point is at rest (v_t = 0): S_c keeps
+    eta (u + r |w|), the size of the two cancelling parts."""
+    r, dn = 5e-6, 2e-8
+    L, dt = 1e-3, 1e-9
+    u = 1e-3
+    w = u / r
+    x = np.array([[L / 2, L / 2, L / 2], [L / 2 + 2 * r - dn, L / 2, L / 2]])
+    v = np.array([[0, u, 0], [0, 0, 0]], dtype=float)
+    # contact point of 1 (at +x r) moves with v + w x (r, 0, 0); w along +z
+    # gives +y r w, so spin -z cancels the translation
+    om = np.array([[0, 0, -w], [0, 0, 0]], dtype=float)
+    s = O.State(x, v, om, np.array([r, r]))
+    p = O.make_params((L, L, L), dt, periodic=(0, 0, 0), r_max=r, mu_d=10.0)
+    out = O.step(p, s)
+    info = out["info"][0]
+    kn = hertz_kn(r / 2)
+    eta = O.alpha(0.5) * math.sqrt(mass(r) / 2 * kn * math.sqrt(dn))
+    assert np.allclose(out["dt"][0], 0.0, atol=1e-25)  # the contact point does not slip
+    expect = kn * dn ** 1.5 + eta * (u + r * w)       # v_n = 0, delta_t = 0
+    assert info["scale"] == pytest.approx(expect, rel=1e-12)
+
+
 def test_coulomb_cap_resets_history():
     """With a tiny mu the cap fires: |F_t| = mu |F_n| and k_t delta_t = -F_t."""
     r, dn, w = 5e-6, 2e-8, 1e3
