@@ -59,3 +59,34 @@ def test_create_rejects_bad_config_without_gpu(lib):
     with pytest.raises(D.DemError) as e:
         D.dem_create(cfg)
     assert e.value.status == D.DEM_ERR_ARG
+
+
+def test_header_compiles_as_c_and_matches_the_binding(tmp_path):
+    """include/dem.h compiles as C99, and the sizes and member offsets of its
+    structs are those of the ctypes structures of the binding."""
+    import ctypes as C
+    import subprocess
+    import paper_1503_03553_gb300 as D
+    structs = {"dem_material": D.dem_material, "dem_wall": D.dem_wall,
+               "dem_box": D.dem_box, "dem_config": D.dem_config}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dem.h"',
+             'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    seen = {}
+    for line in out.splitlines():
+        name, field, value = line.split()
+        seen[(name, field)] = int(value)
+    for name, cls in structs.items():
+        assert seen[(name, "size")] == C.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert seen[(name, fname)] == getattr(cls, fname).offset, (name, fname)
