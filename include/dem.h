@@ -172,18 +172,24 @@ typedef struct {
 typedef struct dem_ctx dem_ctx;
 
 /* Create a context on the current CUDA device and allocate all device state
- * for cfg (copied; cfg need not outlive the call).  On success *out holds
- * the context; on failure *out is NULL and the status says why.
+ * for cfg (copied; cfg need not outlive the call; the walls are read during
+ * the call).  On success *out holds the context; on failure *out is NULL and
+ * the status says why (dem_last_error(NULL) describes it).
  * DEM_ERR_ARG: inconsistent configuration (a periodic axis with fewer than 3
  * cells, cells narrower than 2 r_max, bad material index, floor on a
- * periodic z axis, ...). */
+ * periodic z axis, a bad wall or more than 15 per box, r_split outside
+ * [0, r_max], a size-binned box with a per-particle Collide form or a
+ * periodic axis of fewer than 5 cells, ...).  DEM_ERR_ALLOC: the allocator
+ * returned NULL.  DEM_ERR_CUDA: no device, or a CUDA call failed. */
 dem_status dem_create(const dem_config* cfg, dem_ctx** out);
 
 /* Replace the particles of one box (Sec. 4.2: the CPU only creates the
  * initial configuration).  n <= max_particles; x, v, omega: n x 3; radius:
  * n, each in (0, r_max].  Clears the box's contact history.  In DEM_MIXED
  * and DEM_FP32 radii are stored as float32 and positions are rounded to the
- * mode's representation. */
+ * mode's representation.  DEM_ERR_ARG: bad box, n above the capacity, a
+ * NULL array, a radius outside (0, r_max] or a non-finite value (host
+ * arrays are checked before any copy). */
 dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
                              const double* x, const double* v,
                              const double* omega, const double* radius,
@@ -191,19 +197,29 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
 
 /* Overwrite positions, velocities and angular velocities (n x 3 each, any
  * may be NULL to keep it) of the particles already in a box, keeping radii
- * and the contact history. */
+ * and the contact history.  Host arrays are read by the time the call
+ * returns.  A non-finite value is reported by the next dem_step
+ * (DEM_ERR_NONFINITE). */
 dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
                          const double* v, const double* omega, int32_t where);
 
-/* Advance every box by nsteps >= 0 steps.  Each step: sort by cell, find
- * contacts, carry delta_t history, compute forces and torques, integrate.
- * Returns after the work is enqueued and the device status word is read
- * (one stream synchronisation per call). */
+/* Advance every box by nsteps >= 0 steps (Sec. 4.2's kernel sequence;
+ * Algorithm 1; Eq. (1), Eq. (vt), Eq. (dt), the coefficients of Sec. 2 and
+ * the sliding-friction cap).  Each step: sort by cell, find contacts, carry
+ * delta_t history, compute forces and torques, walls and gravity,
+ * integrate.  Returns after the work is enqueued and the device status
+ * word is read (one stream synchronisation per call).  DEM_ERR_CAPACITY:
+ * a particle's contacts exceeded row_capacity or the list its capacity;
+ * DEM_ERR_NONFINITE: a non-finite or out-of-range state; DEM_ERR_STATE:
+ * no particles set, or an internal consistency check failed.  Device
+ * errors are sticky: later calls return them until dem_destroy. */
 dem_status dem_step(dem_ctx* ctx, int64_t nsteps);
 
 /* Read the state of one box in id order: x, v, omega (n x 3); force and
- * torque (n x 3): the totals used in the last step (contacts, wall and
- * gravity).  Any pointer may be NULL. */
+ * torque (n x 3): the totals used in the last step (Eq. (1) and
+ * T = r (n x F) summed over contacts, walls and gravity).  Any pointer may
+ * be NULL.  The caller owns the arrays; they are written by the time the
+ * call returns. */
 dem_status dem_get_state(dem_ctx* ctx, int32_t box, double* x, double* v,
                          double* omega, double* force, double* torque,
                          int32_t where);
@@ -214,8 +230,9 @@ dem_status dem_get_count(dem_ctx* ctx, int32_t box, int64_t* n);
 /* Contact list of one box after the last step (host pointers), sorted by
  * (id_lo, id_hi), id_lo < id_hi: the pairs found in that step and their
  * tangential displacement delta_t (cap x 3) after the step's update, as
- * stored for the next step.  *n receives the count; DEM_ERR_CAPACITY if it
- * exceeds cap (nothing written then). */
+ * stored for the next step (Sec. 2: delta_t kept per contact, in a
+ * condensed sparse format; Sec. 4.2 InitializeContactIDs).  *n receives
+ * the count; DEM_ERR_CAPACITY if it exceeds cap (nothing written then). */
 dem_status dem_get_contacts(dem_ctx* ctx, int32_t box, int64_t cap,
                             int64_t* n, int32_t* id_lo, int32_t* id_hi,
                             double* delta_t);
@@ -231,19 +248,23 @@ dem_status dem_get_contact_forces(dem_ctx* ctx, int32_t box, int64_t cap,
 
 /* Replace the contact history of one box (host pointers, any order,
  * id_lo < id_hi < count) so that the next step starts from it
- * (checkpoint restore). */
+ * (checkpoint restore of Sec. 2's per-contact delta_t).  DEM_ERR_ARG: an
+ * id out of range, not ordered or a pair given twice; DEM_ERR_CAPACITY:
+ * more pairs than the list holds. */
 dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
                             const int32_t* id_lo, const int32_t* id_hi,
                             const double* delta_t);
 
 /* Sort order used in the last step (host pointers, n entries each, may be
- * NULL): the particle id held by each storage slot, and the linear cell
- * (cz*ny + cy)*nx + cx of that slot.  Slots are ordered by (Morton code of
- * the cell, id). */
+ * NULL; Sec. 4.2 BitonicSort / FindCellBoundsAndReorder: particle data
+ * kept in cell order): the particle id held by each storage slot, and the
+ * linear cell (cz*ny + cy)*nx + cx of that slot.  Slots are ordered by
+ * (Morton code of the cell, id). */
 dem_status dem_get_order(dem_ctx* ctx, int32_t box, int32_t* id_by_slot,
                          int32_t* cell_by_slot);
 
-/* Cell grid of a box. */
+/* Cell grid of a box (Sec. 2, last paragraph: the cells of the contact
+ * search): cells per axis. */
 dem_status dem_get_grid(dem_ctx* ctx, int32_t box, int32_t ncell[3]);
 
 #define DEM_NSTATS 10
