@@ -243,11 +243,10 @@ def _max_over_ranks(x, world, torch):
 def _workload(n, seed):
     from paper_1503_03553_gb300 import synth
     box = synth.w2_polydisperse(n=n, seed=seed)
-    # positions on the library's fixed-point grid so that the parity leg
-    # and the oracle see bit-identical inputs
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from parity import prepared
-    return box, prepared(box, "mixed")
+    # the state in the library's storage representation (fixed-point
+    # positions, float32 velocities) so that the parity leg and the oracle
+    # see bit-identical inputs
+    return box, synth.prepared(box, "mixed")
 
 
 def _time_steps(ctx, torch, steps, world):
@@ -351,8 +350,7 @@ def main():
         build.build()
     raw, box = _workload(args.n, 2 + rank)
     n = box.n
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from parity import grid_for
+    from paper_1503_03553_gb300.synth import grid_for
     ncell = grid_for(box)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -546,7 +544,9 @@ def _side_legs(args, D, torch, box, ncell, stream):
 def _error_leg(out, box, ncell):
     """One step of each form against one FP64 oracle step over every
     contact; the MIXED form also through the parity test's full check."""
-    from parity import check_one_step, force_errors, gpu_run, oracle_run, prepared
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import (check_one_step, conditioning_report, force_errors, gpu_run, oracle_run,
+                        prepared)
     errs = {}
     for prec in ("mixed", "fp32", "fp64"):
         b = prepared(box, prec)
@@ -554,6 +554,7 @@ def _error_leg(out, box, ncell):
         o = oracle_run(b, prec, ncell)
         errs[prec] = force_errors(b, g, o, prec)
         if prec == "mixed":
+            errs["mixed_conditioning"] = conditioning_report(b, g, o, prec, ncell)
             try:
                 m = check_one_step(b, g, o, "mixed")
                 out["force_parity_vs_fp64_oracle"] = {"pass": True, **m}
@@ -566,7 +567,7 @@ def _sweep_leg(args, D, torch, stream):
     """Particle-steps/s of the MIXED form against the particle count, W2
     radius law and packing (tiles of 8,000 relaxed spheres)."""
     from paper_1503_03553_gb300 import synth
-    from parity import grid_for, prepared
+    from paper_1503_03553_gb300.synth import grid_for, prepared
     rows = []
     for n in (100_000, 300_000, 1_000_000, 3_000_000, 8_000_000):
         box = prepared(synth.w2_polydisperse(n=n, seed=2), "mixed")
@@ -583,7 +584,7 @@ def _w3_leg(args, D, torch, stream):
     half (divergence stress), floor and gravity: contact-list compaction vs
     the fused Algorithm 1, and the FP32 / FP64 forms."""
     from paper_1503_03553_gb300 import synth
-    from parity import grid_for, prepared
+    from paper_1503_03553_gb300.synth import grid_for, prepared
     box = prepared(synth.w3_bidisperse_floor(n=8_000_000, seed=3), "mixed")
     nc = grid_for(box)
     res = {"particles": box.n, "ncell": nc}
@@ -631,7 +632,7 @@ def _w5_leg(args, D, torch, stream):
     import pickle
     import tempfile
     from paper_1503_03553_gb300 import synth
-    from parity import grid_for, prepared
+    from paper_1503_03553_gb300.synth import grid_for, prepared
     raw = synth.w5_precision(n=args.w5_n, seed=5)
     res = {"particles": raw.n, "steps": args.w5_steps, "every": args.w5_every}
     tmp = tempfile.mkdtemp(prefix="w5_")
@@ -729,7 +730,7 @@ def _size_binned_leg(args, D, torch, stream, box, ncell):
     factor 8 (1-8 um), each at the library's automatic grid."""
     import dataclasses
     from paper_1503_03553_gb300 import synth
-    from parity import prepared
+    from paper_1503_03553_gb300.synth import prepared
     steps = args.steps
     wide = prepared(synth.wide_polydisperse(n=box.n, seed=6), "mixed")
     out = {}
@@ -745,6 +746,27 @@ def _size_binned_leg(args, D, torch, stream, box, ncell):
     return out
 
 
+FIG4_PARTICLES = 131072  # the particle count of the paper's Fig. 4 (Sec. 5.2)
+
+
+def paper_figures():
+    """The figures the paper prints for this comparison (Sec. 5.1, 5.2), read
+    from tests/golden/paper_figures.txt: context beside the measurements."""
+    path = os.path.join(ROOT, "tests", "golden", "paper_figures.txt")
+    out = {}
+    with open(path) as fh:
+        for line in fh:
+            if not line.strip() or line.startswith("#"):
+                continue
+            name, value, unit, where = (x.strip() for x in line.split("|"))
+            try:
+                value = float(value)
+            except ValueError:
+                pass
+            out[name] = {"value": value, "unit": unit, "where": where}
+    return out
+
+
 def _fig4_leg(args, D, torch, stream):
     """The paper's kernel-time comparison (Sec. 5.2, Fig. 4) at its size,
     131,072 particles: dense (W2 law and packing, left graph) and the
@@ -752,9 +774,12 @@ def _fig4_leg(args, D, torch, stream):
     graph); per-phase ms of the previous Collide (Algorithm 1 as printed,
     fused), the paper's two-loop Collide and the contact-list pipeline."""
     from paper_1503_03553_gb300 import synth
-    from parity import grid_for, prepared
-    n = 131072
-    out = {}
+    from paper_1503_03553_gb300.synth import grid_for, prepared
+    n = FIG4_PARTICLES
+    pf = paper_figures()
+    out = {"paper": {"collide_speedup_two_loop_over_fused":
+                     pf["collide_speedup_two_loop_over_fused"],
+                     "hardware": pf["gpu"]}}
     for name, b0 in (("dense", synth.w2_polydisperse(n=n, seed=2)),
                      ("initialisation_no_contacts", synth.lattice_gas(n=n, seed=7))):
         b = prepared(b0, "mixed")
@@ -777,7 +802,7 @@ def _batched_leg(args, D, torch, stream):
     kernel for all boxes, CUDA graphs) against the same boxes stepped one
     context at a time."""
     from paper_1503_03553_gb300 import synth
-    from parity import grid_for, prepared
+    from paper_1503_03553_gb300.synth import grid_for, prepared
     procs = max(1, min(16, os.cpu_count() or 1))
     boxes = [prepared(b, "mixed") for b in synth.w4_batched(nboxes=args.nboxes, processes=procs)]
     ncells = [grid_for(b) for b in boxes]

@@ -318,12 +318,14 @@ int32_t dem_abi_version(void);
  * start-up, or latency-critical code that must not call cudaMalloc (it can
  * synchronise the device).  dem_create allocates; this call does not: it
  * runs the same binning, sorting and search kernels as dem_step with all
- * scratch carved from one file-scope device array of about 5.8 MB that every
- * GPU loading this library holds until the process exits.  It calls no
+ * scratch carved from one file-scope device array of 6,000,000 bytes that
+ * every GPU loading this library holds until the process exits.  It calls no
  * cudaMalloc, cudaFree or allocating library routine.
  *
- * Inputs (device memory of the current GPU): x (n x 3 FP64 positions [m]),
- * radius (n, each at most half the narrowest cell edge L[a]/ncell[a]).
+ * Inputs (device memory of the current GPU; host pointers and memory of
+ * another GPU are rejected with DEM_ERR_ARG): x (n x 3 FP64 positions [m]),
+ * radius (n, each in (0, h/2] with h the narrowest cell edge L[a]/ncell[a];
+ * DEM_ERR_ARG otherwise).  A non-finite position gives DEM_ERR_NONFINITE.
  * Host arrays: box lengths L, periodic flags and the cell grid ncell
  * (periodic axes need >= 3 cells).  The contact rule is DEM_MIXED's: the
  * position is rounded to 2^-60 m fixed point and a pair is in contact when

@@ -120,8 +120,9 @@ double orc_alpha(double e) {
 /* Coefficients, Sec. 2:                                                     */
 /*   k_n = 4/3 sqrt(r1 r2/(r1+r2)) ((c(s1))/E1 + (c(s2))/E2)^-1               */
 /*   k_t = 8 sqrt(r1 r2/(r1+r2) dn) ((2-s1)/G1 + (2-s2)/G2)^-1                */
-/* Reading (Q1): the printed numerator of k_n is 2 - sigma^2; Hertz theory   */
-/* has 1 - sigma^2, taken as the default; kn_literal = 1 selects the print.  */
+/* The printed numerator of k_n is 2 - sigma^2; Hertz theory has            */
+/* 1 - sigma^2, which is read as meant and taken as the default;             */
+/* kn_literal = 1 selects the printed form.                                  */
 /* Both bodies share one material.  A wall (r2 <= 0) has infinite radius,    */
 /* so r1 r2/(r1+r2) -> r1.                                                   */
 /* ------------------------------------------------------------------------ */
@@ -151,9 +152,10 @@ static double mass_of(const orc_params* p, double r) {
 /* One contact: Eq. (1), Eq. (vt), Eq. (dt), the Coulomb cap of Eq. (sliding */
 /* friction) with the delta_t reset that follows it, and T = r (n x F).      */
 /* Particle 1 is the lower id; n points from 1 to 2 (Sec. 2); v = v1 - v2.   */
-/* Reading (Q9): delta_t is advanced before the force (Algorithm 1 order).   */
-/* Reading (Q8): the projection of delta_t,old keeps its tangential part     */
-/* without rescaling; the cap uses F_t including its damping part.          */
+/* delta_t is advanced (with this step's v_t dt) before the force, then the  */
+/* cap, then the torque: the order of Algorithm 1.  The projection of        */
+/* delta_t,old in Eq. (dt) keeps its tangential part without rescaling, and  */
+/* the cap uses F_t including its damping part, both as printed.             */
 /* ------------------------------------------------------------------------ */
 static void contact_force(const orc_params* p, double alpha,
                           const double n[3], double dn,
@@ -571,7 +573,8 @@ static double wrap(double x, double L) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* One step.  Order (reading Q10): wrap, contact set, forces (Algorithm 1    */
+/* One step.  The paper leaves the integrator unstated; it is read as       */
+/* symplectic Euler.  Order: wrap, contact set, forces (Algorithm 1          */
 /* per pair, evaluated once per pair with the action-reaction law), floor    */
 /* wall, gravity, then symplectic Euler: v += F/m dt, w += T/I dt,           */
 /* x += v dt, with I = 2/5 m r^2.                                             */

@@ -97,7 +97,10 @@ typedef struct {
   int32_t pad;
 } orc_contact_info;
 
-/* Restitution coefficient e(alpha) of the paper's normal law (Q2 reading). */
+/* Restitution coefficient e(alpha) of the paper's normal law.  The paper
+ * does not give alpha(eps); alpha is read as the exact inverse of the
+ * rebound of its own two-body normal law x'' = -x^{3/2} - alpha x^{1/4} x',
+ * x(0) = 0, x'(0) = 1, e = -x'(end) (independent of speed and size). */
 double orc_restitution(double alpha);
 /* alpha(e): inverse of orc_restitution by bisection. */
 double orc_alpha(double e);

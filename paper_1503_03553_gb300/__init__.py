@@ -171,7 +171,17 @@ def dem_contacts_static(x, radius, L, periodic, ncell, pairs, stream=None) -> in
     for t, dt in ((x, torch.float64), (radius, torch.float64), (pairs, torch.int32)):
         if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
             raise TypeError("x, radius must be contiguous CUDA float64; pairs CUDA int32")
+    if x.ndim != 2 or x.shape[1] != 3:
+        raise ValueError("x must have shape (n, 3)")
     n = int(x.shape[0])
+    if radius.ndim != 1 or radius.shape[0] != n:
+        raise ValueError("radius must have shape (n,) with n = x.shape[0]")
+    if pairs.ndim != 2 or pairs.shape[1] != 2:
+        raise ValueError("pairs must have shape (cap, 2)")
+    if not (x.device == radius.device == pairs.device):
+        raise ValueError("x, radius and pairs must be on one device")
+    if x.device.index != torch.cuda.current_device():
+        raise ValueError("x, radius and pairs must be on the current CUDA device")
     Ld = (C.c_double * 3)(*[float(v) for v in L])
     per = (C.c_int32 * 3)(*[int(v) for v in periodic])
     nc = (C.c_int32 * 3)(*[int(v) for v in ncell])

@@ -1273,8 +1273,8 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
 // synchronise the device) on a latency-critical path.  For them this entry
 // point runs the same search kernels as dem_step on one small box, with all
 // of its scratch carved from one file-scope device array of fixed size.
-// The array exists on every GPU that loads this library until the process
-// exits (about 4.8 MB).
+// The array (6,000,000 bytes) exists on every GPU that loads this library
+// until the process exits.
 // ==========================================================================
 namespace {
 
@@ -1353,12 +1353,30 @@ __global__ void k_static_iota(int* rank_of_lin, int* lin_of_rank, int M) {
   }
 }
 
+// status bits of the radius check
+constexpr unsigned kStStaticRadiusLarge = 0x100u;  // above half the narrowest cell
+constexpr unsigned kStStaticRadiusBad = 0x200u;    // zero, negative or not finite
+
 // a radius above half the narrowest cell would let contacts skip a cell
 __global__ void k_static_check_radius(const double* r, int n, double hmin,
                                       unsigned* status) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n && !(2.0 * r[k] * (1.0 + 1e-5) <= hmin && r[k] > 0.0))
-    atomicOr(status, 0x100u);
+  if (k >= n) return;
+  const double rk = r[k];
+  if (!(rk > 0.0) || !isfinite(rk)) atomicOr(status, kStStaticRadiusBad);
+  else if (!(2.0 * rk * (1.0 + 1e-5) <= hmin)) atomicOr(status, kStStaticRadiusLarge);
+}
+
+// true when p is memory of device dev that kernels can read (device or
+// managed memory); host and unregistered pointers are rejected
+bool static_device_pointer(const void* p, int dev) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error this query may leave behind
+    return false;
+  }
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -1414,6 +1432,10 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
     }
     base = g_static_addr[dev];
   }
+  if (!static_device_pointer(x, dev) || !static_device_pointer(radius, dev) ||
+      (cap > 0 && !static_device_pointer(pairs, dev)))
+    return fail(ctx, DEM_ERR_ARG,
+                "dem_contacts_static: x, radius and pairs must be device memory of the current GPU");
   cudaStream_t s = (cudaStream_t)stream;
   const int N = (int)n;
 
@@ -1519,8 +1541,11 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
     return st;
   if ((st = ck(cudaStreamSynchronize(s), "synchronise"))) return st;
   *count = std::min(hcount, d.Cmax);
-  if (hstatus & 0x100u)
-    return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: a radius exceeds half the cell edge");
+  if (hstatus & kStStaticRadiusBad)
+    return fail(ctx, DEM_ERR_ARG, "dem_contacts_static: a radius is zero, negative or not finite");
+  if (hstatus & kStStaticRadiusLarge)
+    return fail(ctx, DEM_ERR_ARG,
+                "dem_contacts_static: a radius exceeds half the narrowest cell edge");
   if (hstatus & kStNonFinite) return fail(ctx, DEM_ERR_NONFINITE, "dem_contacts_static: non-finite position");
   if (hstatus & (kStRowOverflow | kStListOverflow))
     return fail(ctx, DEM_ERR_CAPACITY, "dem_contacts_static: contacts exceed cap, 131072, or 32 per particle");

@@ -387,3 +387,50 @@ def w5_precision(n: int = 4_000_000, seed: int = 5, tile_n: int = 8000) -> Box:
     m = len(r)
     return Box(x=x, v=np.zeros((m, 3)), w=np.zeros((m, 3)), r=r, L=L,
                dt=2.0e-9, restitution=0.5, mu_d=0.3)
+
+
+# ---------------------------------------------------------------------------
+# inputs in a precision mode's representation
+# ---------------------------------------------------------------------------
+def quantize(x):
+    """Positions rounded to the 2^-60 m fixed-point grid of DEM_MIXED."""
+    return np.ldexp(np.round(np.ldexp(np.asarray(x, np.float64), 60)), -60)
+
+
+def grid_for(box, stencil: int = 1, skin: float = 0.0):
+    """Cells per axis: the largest grid whose cells are at least
+    (2 r_max + skin)(1 + 1e-5) / stencil wide (the library's automatic grid
+    for the same box)."""
+    hmin = (2.0 * box.r_max + skin) * (1.0 + 1e-5) / stencil
+    return [max(1, int(math.floor(box.L[a] / hmin))) for a in range(3)]
+
+
+def prepared(box: Box, precision: str) -> Box:
+    """Copy of ``box`` whose state is exactly what the library stores in the
+    given precision mode, so that the library and any other consumer start
+    from bit-identical inputs: positions wrapped into periodic axes and
+    rounded to the mode's position type (2^-60 m fixed point for "mixed",
+    float32 for "fp32"); velocities and angular velocities rounded to
+    float32 in "mixed" and "fp32" (their storage type there); radii are
+    float32 values already."""
+    b = dataclasses.replace(box)
+    x = np.array(box.x, np.float64)
+    L = np.asarray(box.L)
+    per = np.asarray(box.periodic, bool)
+    x = np.where(per, np.mod(x, L), x)
+    v = np.array(box.v, np.float64)
+    w = np.array(box.w, np.float64)
+    if precision == "mixed":
+        x = quantize(x)
+        x = np.where(per & (x >= L), x - L, x)
+    elif precision == "fp32":
+        x = x.astype(np.float32).astype(np.float64)
+        x = np.where(per & (x >= L.astype(np.float32)), 0.0, x)
+    if precision in ("mixed", "fp32"):
+        v = _f32(v)
+        w = _f32(w)
+    b.x = x
+    b.v = v
+    b.w = w
+    b.r = np.array(box.r, np.float64)
+    return b

@@ -1,72 +1,57 @@
 """Parity harness: one step of the CUDA library against the FP64 oracle.
 
-Both sides start from the same seeded state.  Positions are quantised to the
-library's 2^-60 m fixed point (DEM_MIXED) or rounded to float32 (DEM_FP32)
-before either side sees them, radii are float32 values already, and both
-sides use the same explicit cell grid, so the contact predicate and the sort
-order can be compared bit for bit.
+Both sides start from the same seeded state in the library's storage
+representation (``synth.prepared``): positions quantised to the 2^-60 m
+fixed point (DEM_MIXED) or rounded to float32 (DEM_FP32), velocities and
+angular velocities rounded to float32 in both of those modes, radii float32
+values already; both sides use the same explicit cell grid, so the contact
+predicate and the sort order can be compared bit for bit.
 
-Tolerances (per contact c, oracle values):
-  |F_gpu - F_ora|   <= rtol * S_c + f_c
-  |nF_gpu - nF_ora| <= rtol * S_c + f_c + 1e-6 |F_ora|
+Two force tolerances are checked per contact c (oracle values):
+
+  relative to the force (the stated criterion):
+    |F_gpu - F_ora|  <= rtol |F_ora| + f_c
+    |nF_gpu - nF_ora| <= rtol |F_ora| + f_c
+  relative to the terms of Eq. (1) (a float sum's error is bounded by its
+  terms, not by its result):
+    |F_gpu - F_ora|  <= rtol S_c + f_c
+    |nF_gpu - nF_ora| <= rtol S_c + f_c + 1e-6 |F_ora|
   S_c = k_n dn^1.5 + eta |v_n| + k_t |delta_t| + eta (|v| + r1 |w1| + r2 |w2|)
-        (sum of the magnitudes of the terms of Eq. (1), with v_t counted by
-        the terms of Eq. (vt): the error of a float sum is bounded by the
-        unit roundoff times its terms, not by the result; in a rolling
-        contact the translational and rotational parts of v_t nearly
-        cancel)
+        (the magnitudes of the terms of Eq. (1), with v_t counted by the
+        terms of Eq. (vt))
   f_c = 1e-9 k_n R*^1.5  (absolute floor)
-with rtol = 1e-5 for FP32 force arithmetic and 1e-9 for FP64.  Contacts whose
-Coulomb ratio lies within 1e-4 of 1 may be capped on one side only, and
-contacts with an overlap below 1e-15 R* / rtol are below what an FP64
-overlap resolves to rtol in the damping force (eta ~ dn^{1/4}); both kinds are
-counted and reported, not compared.  Per particle the bounds add up over its
-contacts.
+
+with rtol = 1e-5 for FP32 force arithmetic and 1e-9 for FP64.  The term
+bound holds for every contact.  The force-relative bound holds for every
+contact whose condition number kappa_c = S_c / |F_ora| is at most KAPPA_MAX:
+there an error of a few units of FP32 rounding in each term stays below
+rtol |F|.  Above it the terms of Eq. (1) cancel (a rolling contact, whose
+translational and rotational parts of v_t nearly cancel, or a force near
+zero at the end of a contact), and a one-ulp change of the FP32 inputs
+already moves the FP64 oracle's own force by more than rtol |F|
+(``oracle_sensitivity``); those contacts are counted and reported.
+
+Contacts whose Coulomb ratio lies within 1e-4 of 1 may be capped on one side
+only, and contacts with an overlap below 1e-15 R* / rtol are below what an
+FP64 overlap resolves to rtol in the damping force (eta ~ dn^{1/4}); both
+kinds are counted and reported, not compared.  Per particle the bounds add up
+over its contacts.
 """
 from __future__ import annotations
 
-import dataclasses
 import math
 
 import numpy as np
 
 import oracle as O
+from paper_1503_03553_gb300.synth import grid_for, prepared, quantize  # noqa: F401
 
 RTOL = {"mixed": 1e-5, "fp32": 1e-5, "fp64": 1e-9}
 PRED = {"mixed": O.PRED_FIXED_F32, "fp64": O.PRED_FP64, "fp32": O.PRED_ABS_F32}
-
-
-def quantize(x):
-    return np.ldexp(np.round(np.ldexp(np.asarray(x, np.float64), 60)), -60)
-
+# contacts with S_c / |F| above this are ill-conditioned in FP32 (see above)
+KAPPA_MAX = 10.0
 
 STENCIL = 1  # neighbour cells per axis (+-1): cells of at least 2 r_max
-
-
-def grid_for(box, stencil=STENCIL):
-    hmin = 2.0 * box.r_max * (1.0 + 1e-5) / stencil
-    return [max(1, int(math.floor(box.L[a] / hmin))) for a in range(3)]
-
-
-def prepared(box, precision):
-    """Copy of ``box`` with positions in the precision mode's representation
-    (so that both sides start from bit-identical positions)."""
-    b = dataclasses.replace(box)
-    x = np.array(box.x, np.float64)
-    L = np.asarray(box.L)
-    per = np.asarray(box.periodic, bool)
-    x = np.where(per, np.mod(x, L), x)
-    if precision == "mixed":
-        x = quantize(x)
-        x = np.where(per & (x >= L), x - L, x)
-    elif precision == "fp32":
-        x = x.astype(np.float32).astype(np.float64)
-        x = np.where(per & (x >= L.astype(np.float32)), 0.0, x)
-    b.x = x
-    b.v = np.array(box.v, np.float64)
-    b.w = np.array(box.w, np.float64)
-    b.r = np.array(box.r, np.float64)
-    return b
 
 
 def oracle_params(box, precision, ncell, brute_force=0, stencil=STENCIL):
@@ -179,6 +164,23 @@ def check_one_step(box, g, o, precision, allow_dont_care=True):
             f"{float(np.max((eF / bF)[ok])):.3g} x bound\n" + _explain(box, g, o, np.where(bad)[0][:6]))
         bad = ok & (enF > bF + 1e-6 * normF)
         assert not np.any(bad), f"{int(bad.sum())} n x F outside tolerance"
+        # the force-relative criterion: every well-conditioned contact
+        kappa = info["scale"] / np.maximum(normF, 1e-300)
+        well = ok & (kappa <= KAPPA_MAX)
+        bN = rtol * normF + floor
+        over = ok & (eF > bN)
+        m["F_rel_max"] = float(np.max((eF / np.maximum(normF, 1e-300))[ok], initial=0))
+        m["F_rel_p99"] = float(np.percentile((eF / np.maximum(normF, 1e-300))[ok], 99)) if ok.any() else 0.0
+        m["F_rel_bound_max"] = float(np.max((eF / bN)[ok], initial=0))
+        m["F_rel_bound_exceeded"] = int(over.sum())
+        m["ill_conditioned"] = int((ok & ~well).sum())
+        if precision != "fp32":
+            bad = well & (eF > bN)
+            assert not np.any(bad), (
+                f"{int(bad.sum())} well-conditioned contacts outside rtol |F| + floor; worst "
+                f"{float(np.max((eF / bN)[well])):.3g} x bound\n" + _explain(box, g, o, np.where(bad)[0][:6]))
+            bad = well & (enF > bN)
+            assert not np.any(bad), f"{int(bad.sum())} well-conditioned n x F outside rtol |F| + floor"
         # tangential history after the step
         lo, hi = o["lo"], o["hi"]
         v0, w0, r = o["v0"], o["w0"], box.r
@@ -206,6 +208,26 @@ def check_one_step(box, g, o, precision, allow_dont_care=True):
         np.add.at(bP, o["hi"][dont], np.inf)
     eP = np.linalg.norm(g["state"]["F"] - o["F"], axis=1)
     assert np.all(eP <= bP), f"{int((eP > bP).sum())} particle forces outside tolerance"
+    if nc:
+        # force-relative per particle: rtol times the sum of its contacts'
+        # |F| plus their floors, for particles whose contacts are all
+        # well-conditioned (the net force of a dense packing cancels, so the
+        # scale is the sum of the magnitudes, not the net force)
+        sF = np.zeros(n)
+        np.add.at(sF, o["lo"], rtol * normF + floor)
+        np.add.at(sF, o["hi"], rtol * normF + floor)
+        sF += 1e-6 * mass * gmag + 1e-300
+        if box.floor_wall or len(getattr(box, "walls", ())):
+            sF += 1e-5 * np.linalg.norm(o["F"], axis=1) + 1e-5 * mass * gmag
+        cold = np.zeros(n, bool)
+        notwell = ~(ok & (kappa <= KAPPA_MAX))
+        cold[o["lo"][notwell]] = True
+        cold[o["hi"][notwell]] = True
+        m["particle_F_rel_bound_max"] = float(np.max((eP / sF)[~cold], initial=0))
+        m["particles_with_ill_conditioned_contacts"] = int(cold.sum())
+        if precision != "fp32":
+            assert np.all(eP[~cold] <= sF[~cold]), (
+                f"{int((eP[~cold] > sF[~cold]).sum())} particle forces outside rtol sum|F| + floors")
     eT = np.linalg.norm(g["state"]["T"] - o["T"], axis=1)
     assert np.all(eT <= box.r * (bP + 1e-6 * np.linalg.norm(o["F"], axis=1)) * 2 + 1e-300), "torques"
     m["max_particle_F_err_over_bound"] = float(np.max(eP / bP))
@@ -226,7 +248,7 @@ def check_one_step(box, g, o, precision, allow_dont_care=True):
 
 def force_errors(box, g, o, precision, detail=0):
     """Error statistics of one step against the oracle (no assertion):
-    per contact |F_gpu - F_ora| / (S_c + f_c) with the Q15 scale and floor,
+    per contact |F_gpu - F_ora| / (S_c + f_c) with the term scale and floor,
     over the contacts both sides found (the sets must be equal).  detail > 0
     adds the `detail` worst contacts outside the "don't care" classes, each
     with its error split along and across the normal, overlap over R*,
@@ -271,6 +293,21 @@ def force_errors(box, g, o, precision, detail=0):
                 w["dt_err_rel"] = float(np.linalg.norm(g["dt"][k] - o["dt"][k]) /
                                         max(np.linalg.norm(o["dt"][k]), 1e-300))
             worst.append(w)
+    fl = floor
+    bN = 1e-5 * nF + fl
+    eabs = np.linalg.norm(g["Fc"] - info["F"], axis=1)
+    kappa = info["scale"] / np.maximum(nF, 1e-300)
+    over = keep & (eabs > bN)
+    rel_stats = {
+        "F_rel_max": float(rel[keep].max()) if keep.any() else 0.0,
+        "F_rel_p99": float(np.percentile(rel[keep], 99)) if keep.any() else 0.0,
+        "F_rel_bound_max": float((eabs / bN)[keep].max()) if keep.any() else 0.0,
+        "F_rel_bound_exceeded": int(over.sum()),
+        "F_rel_bound_exceeded_frac": float(over.sum() / max(1, keep.sum())),
+        "F_rel_bound_exceeded_kappa_le_10": int((over & (kappa <= 10.0)).sum()),
+        "kappa_of_exceeders_min": float(kappa[over].min()) if over.any() else None,
+        "kappa_of_exceeders_median": float(np.median(kappa[over])) if over.any() else None,
+    }
     out = {"contact_sets_equal": True, "contacts": int(len(e)),
             "max_err_over_scale": float(e.max()),
             "p99_err_over_scale": float(np.percentile(e, 99)),
@@ -279,6 +316,59 @@ def force_errors(box, g, o, precision, detail=0):
             "dont_care": int(dont.sum()),
             "max_err_over_scale_cared": float(e[keep].max()) if keep.any() else 0.0,
             "frac_within_1e-5_cared": float(np.mean(e[keep] <= 1e-5)) if keep.any() else 1.0}
+    out.update(rel_stats)
     if detail:
         out["worst_cared"] = worst
     return out
+
+
+def oracle_sensitivity(box, o, precision, ncell, seed=0):
+    """How far the FP64 oracle's own contact forces move when its inputs
+    change by one FP32 unit: velocities and angular velocities (the FP32
+    inputs of DEM_MIXED) scaled by 1 +- 2^-24 with random signs, one oracle
+    step from the same positions and history.  Returns per contact
+    |F_pert - F_ora| in the order of o["lo"] (the contact set is the same:
+    the predicate reads positions only)."""
+    rng = np.random.default_rng(seed)
+    sgn = lambda a: 1.0 + np.ldexp(rng.choice([-1.0, 1.0], size=a.shape), -24)
+    p = oracle_params(box, precision, ncell)
+    s = O.State(box.x, box.v * sgn(box.v), box.w * sgn(box.w), box.r,
+                floor_wall=bool(box.floor_wall), nwalls=len(getattr(box, "walls", ())))
+    if "hist" in o:
+        s.lo, s.hi, s.dt = o["hist"]
+    out = O.step(p, s)
+    assert np.array_equal(out["lo"], o["lo"]) and np.array_equal(out["hi"], o["hi"])
+    return np.linalg.norm(out["info"]["F"] - o["info"]["F"], axis=1)
+
+
+def conditioning_report(box, g, o, precision, ncell):
+    """For the contacts outside 1e-5 |F_ora| + floor: their count, their
+    condition numbers kappa = S_c / |F_ora|, and the ratio of the library's
+    error to the oracle's own movement under a one-ulp FP32 change of its
+    inputs (``oracle_sensitivity``)."""
+    info = o["info"]
+    nc = len(o["lo"])
+    if nc == 0:
+        return {"contacts": 0}
+    _, floor = _contact_bounds(box, o, 1e-5)
+    nF = np.linalg.norm(info["F"], axis=1)
+    e = np.linalg.norm(g["Fc"] - info["F"], axis=1)
+    r = box.r
+    Rs = r[o["lo"]] * r[o["hi"]] / (r[o["lo"]] + r[o["hi"]])
+    keep = ~((np.abs(info["ratio"] - 1.0) < 1e-4) | (info["delta_n"] < 1e-10 * Rs))
+    over = keep & (e > 1e-5 * nF + floor)
+    kappa = info["scale"] / np.maximum(nF, 1e-300)
+    sens = oracle_sensitivity(box, o, precision, ncell)
+    pert_over = keep & (sens > 1e-5 * nF + floor)
+    ratio = e[over] / np.maximum(sens[over], 1e-300)
+    return {
+        "contacts": int(nc), "exceed_rel_1e-5": int(over.sum()),
+        "exceed_frac": float(over.sum() / max(1, keep.sum())),
+        "exceed_with_kappa_le_10": int((over & (kappa <= 10)).sum()),
+        "kappa_exceeders_p10_median": ([float(np.percentile(kappa[over], 10)),
+                                        float(np.median(kappa[over]))] if over.any() else None),
+        "oracle_moved_beyond_rel_1e-5_by_one_ulp": int(pert_over.sum()),
+        "exceeders_also_moved_by_one_ulp": int((over & pert_over).sum()),
+        "gpu_err_over_one_ulp_move_median_p90": ([float(np.median(ratio)), float(np.percentile(ratio, 90))]
+                                                 if over.any() else None),
+    }
