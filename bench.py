@@ -49,6 +49,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
+    ap.add_argument("--skin-um", type=float, default=0.2,
+                    help="candidate-list skin in micrometres (0: search every step)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP64-GPU, parity and CPU-baseline side legs")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -351,18 +353,22 @@ def main():
     raw, box = _workload(args.n, 2 + rank)
     n = box.n
     from paper_1503_03553_gb300.synth import grid_for
-    ncell = grid_for(box)
+    skin = args.skin_um * 1e-6
+    ncell = grid_for(box, skin=skin)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        ctx = D.Context([box], precision=args.precision, ncell=[ncell])
+        ctx = D.Context([box], precision=args.precision, ncell=[ncell], skins=[skin])
     # the workload is steps 1..K from the initial state: warm up from it,
     # then start again from it
     _reset(ctx, [box])
     ctx.step(args.warmup)
     _reset(ctx, [box])
     # ---- timed region: K steps, CUDA graphs, device time -------------------
+    rs0 = ctx.resort_stats()
     with ClockSampler(local) as clk:
         secs = _time_steps(ctx, torch, args.steps, world)
+    rs1 = ctx.resort_stats()
+    resorts_timed = rs1["resorts"] - rs0["resorts"]
     secs = _max_over_ranks(secs, world, torch)
     value = job_throughput(n, world, args.steps, secs)
     # ---- the same K steps again, untimed: contacts along the trajectory ---
@@ -446,12 +452,12 @@ def main():
     e2e = {"value": n * world * args.e2e_steps / e2e_secs, "unit": METRIC,
            "h2d_bytes_per_step": 3 * n * 3 * 8, "d2h_bytes_per_step": 3 * n * 3 * 8,
            "steps": args.e2e_steps}
-    launches = ctx.launches_per_step() * args.steps
+    launches = ctx.launches_per_step() * args.steps + resorts_timed * rs1["launches_per_resort"]
     ctx.close()
     compare = {}
     cpu = None
     if rank == 0 and not args.no_compare:
-        compare = _side_legs(args, D, torch, box, ncell, stream)
+        compare = _side_legs(args, D, torch, box, ncell, stream, skin)
         rate, k, dt = _oracle_rate(box, args.cpu_seconds, max_steps=1)
         cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
                "sample": f"{k} oracle step(s) of the full {n}-particle workload, "
@@ -476,6 +482,8 @@ def main():
                                         "fp64": "FP64 throughout",
                                         "fp32": "FP32 throughout"}[args.precision],
                    "ncell": ncell,
+                   "skin_m": skin,
+                   "resorts_in_timed_steps": resorts_timed,
                    "contacts_per_particle": c_half,
                    "l2": f"inputs larger than L2: a step touches {total_bytes / 1e6:.0f} MB "
                          f"of unique data vs {L2_BYTES / 1e6:.0f} MB L2",
@@ -510,7 +518,7 @@ def _throughput(D, torch, stream, boxes, precision, ncells, steps, warmup=3, **k
             "ms_per_step": secs / steps * 1e3}
 
 
-def _side_legs(args, D, torch, box, ncell, stream):
+def _side_legs(args, D, torch, box, ncell, stream, skin):
     """Comparison legs: the FP64 and FP32 GPU forms on the same workload, the
     force error of one step of each form against the FP64 oracle over every
     contact, the paper's Collide forms, the size-binned search, the paper's
@@ -524,10 +532,15 @@ def _side_legs(args, D, torch, box, ncell, stream):
         except Exception as e:  # recorded, not hidden: the line says which leg failed
             out[name] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
 
-    leg("fp64_gpu", lambda: _throughput(D, torch, stream, [box], "fp64", [ncell], args.steps))
-    leg("fp32_gpu", lambda: _throughput(D, torch, stream, [box], "fp32", [ncell], args.steps))
+    leg("fp64_gpu", lambda: _throughput(D, torch, stream, [box], "fp64", [ncell], args.steps,
+                                        skins=[skin]))
+    leg("fp32_gpu", lambda: _throughput(D, torch, stream, [box], "fp32", [ncell], args.steps,
+                                        skins=[skin]))
+    leg("mixed_gpu_search_every_step", lambda: _throughput(D, torch, stream, [box], "mixed",
+                                                           [ncell], args.steps, skins=[0.0]))
     leg("force_error_vs_fp64_oracle", lambda: _error_leg(out, box, ncell))
-    leg("collide_fused_vs_compact", lambda: _fused_leg(args, D, torch, stream, box, ncell))
+    leg("collide_fused_vs_compact", lambda: _fused_leg(args, D, torch, stream, box,
+                                                       _grid_no_skin(box)))
     leg("size_binned_search", lambda: _size_binned_leg(args, D, torch, stream, box, ncell))
     leg("fig4_kernel_times_131k", lambda: _fig4_leg(args, D, torch, stream))
     if not args.no_batched:
@@ -539,6 +552,11 @@ def _side_legs(args, D, torch, box, ncell, stream):
     if args.sweep:
         leg("n_sweep", lambda: _sweep_leg(args, D, torch, stream))
     return out
+
+
+def _grid_no_skin(box):
+    from paper_1503_03553_gb300.synth import grid_for
+    return grid_for(box)
 
 
 def _error_leg(out, box, ncell):

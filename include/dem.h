@@ -7,9 +7,11 @@
  *   - cell binning and a Morton-ordered counting sort (Sec. 4.2, kernels
  *     CalcHash, BitonicSort, FindCellBoundsAndReorder),
  *   - contact detection over the 27 neighbour cells (Sec. 2, last
- *     paragraph; Algorithm 1) with warp-level compaction of true contacts
- *     into a dense contact list (the paper's two-loop split, Sec. 3.4 and
- *     Sec. 4.3, carried to a global list),
+ *     paragraph; Algorithm 1) into a candidate list kept between re-sorts
+ *     (pairs within a skin of contact), the contact rule applied to every
+ *     candidate each step, and warp-level compaction of the true contacts
+ *     for the force (the paper's two-loop split, Sec. 3.4 and Sec. 4.3,
+ *     carried to a global list),
  *   - carry-over of the tangential displacement history between steps
  *     (Sec. 2 "condensed format of a sparse matrix"; Sec. 4.2
  *     InitializeContactIDs),
@@ -48,7 +50,7 @@
 extern "C" {
 #endif
 
-#define DEM_ABI_VERSION 3
+#define DEM_ABI_VERSION 4
 
 typedef enum {
   DEM_OK = 0,
@@ -74,9 +76,13 @@ typedef enum { DEM_FP64 = 0, DEM_MIXED = 1, DEM_FP32 = 2 } dem_precision;
 typedef enum { DEM_HOST = 0, DEM_DEVICE = 1 } dem_where;
 
 /* Contact-force kernel layout.
- *   DEM_COLLIDE_COMPACT : contact search writes a dense contact list; one
- *                         thread per contact computes the force; a
- *                         per-particle pass sums it (no float atomics).
+ *   DEM_COLLIDE_COMPACT : the contact search writes a candidate list (the
+ *                         contacts plus, with a skin, the pairs within the
+ *                         skin of contact); every step the contact rule is
+ *                         applied to each candidate, the contacts are
+ *                         compacted by warp ballots and one thread per
+ *                         contact computes the force; a per-particle pass
+ *                         sums it in partner-id order (no float atomics).
  *   DEM_COLLIDE_FUSED   : Algorithm 1 of the paper: one thread per particle
  *                         searches and computes the force of each contact as
  *                         it is found (each pair evaluated from both sides).
@@ -147,6 +153,19 @@ typedef struct {
                           /* 0 picks the largest such grid) and periodic   */
                           /* axes at least 5 cells.  Same contacts as the  */
                           /* single-class search.  DEM_COLLIDE_COMPACT only */
+  double skin;            /* candidate-list skin [m] (0 = search every     */
+                          /* step).  The cell search at a re-sort keeps    */
+                          /* every pair within r_i + r_j + skin; each step */
+                          /* then applies the contact rule to those pairs  */
+                          /* only, and the next re-sort comes as soon as a */
+                          /* particle has moved about skin / 2 since the   */
+                          /* last one (Sec. 2 cell method; the paper       */
+                          /* searches every step).  Same contacts and      */
+                          /* results, bit for bit, whatever the skin.      */
+                          /* Cells must then be (2 r_max + skin) (1 +      */
+                          /* 1e-5) wide (max(2 r_split + skin, r_max +     */
+                          /* skin / 2) (1 + 1e-5) size-binned).            */
+                          /* DEM_COLLIDE_COMPACT only.                     */
 } dem_box;
 
 typedef struct {
@@ -205,9 +224,12 @@ dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
 
 /* Advance every box by nsteps >= 0 steps (Sec. 4.2's kernel sequence;
  * Algorithm 1; Eq. (1), Eq. (vt), Eq. (dt), the coefficients of Sec. 2 and
- * the sliding-friction cap).  Each step: sort by cell, find contacts, carry
- * delta_t history, compute forces and torques, walls and gravity,
- * integrate.  Returns after the work is enqueued and the device status
+ * the sliding-friction cap).  Each step: find contacts (with
+ * DEM_COLLIDE_COMPACT, a re-sort first when one is due: sort by cell,
+ * candidate search, delta_t history carried to the new list), compute
+ * forces and torques, walls and gravity, integrate.  The decision to
+ * re-sort is taken on the device; with CUDA graphs the re-sort kernels sit
+ * in a conditional node and do not launch in other steps.  Returns after the work is enqueued and the device status
  * word is read (one stream synchronisation per call).  DEM_ERR_CAPACITY:
  * a particle's contacts exceeded row_capacity or the list its capacity;
  * DEM_ERR_NONFINITE: a non-finite or out-of-range state; DEM_ERR_STATE:
@@ -277,9 +299,12 @@ dem_status dem_get_grid(dem_ctx* ctx, int32_t box, int32_t ncell[3]);
 dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]);
 
 /* Milliseconds of device time per step phase, averaged over the steps of
- * the last dem_step call run with timing on (dem_set_timing).  Phases:
+ * the last dem_step call run with timing on (dem_set_timing; kernels are
+ * then launched one by one and a step that does not re-sort still launches
+ * the re-sort kernels, which return at once).  Phases:
  * [0] sort (scan, scatter, cell order, reorder)  [1] contact search
- * [2] list compaction  [3] force  [4] sum + integrate + bin.
+ * [2] candidate rows and history carry-over  [3] contact rule and force
+ * [4] sum + integrate + bin (+ rectangle and line walls).
  * Returns the number of phases written (<= cap). */
 int32_t dem_get_phase_times(dem_ctx* ctx, double* ms, int32_t cap);
 dem_status dem_set_timing(dem_ctx* ctx, int32_t on);
@@ -293,8 +318,16 @@ dem_status dem_set_timing(dem_ctx* ctx, int32_t on);
 dem_status dem_autotune(dem_ctx* ctx, int64_t steps, double* best_ms,
                         int32_t* block, int32_t* graph_steps);
 
-/* Kernel launches issued per step by the current configuration. */
+/* Kernel launches issued by a step that does not re-sort in a CUDA graph
+ * (DEM_COLLIDE_COMPACT) or by any step (the per-particle forms re-sort
+ * every step). */
 int32_t dem_launches_per_step(const dem_ctx* ctx);
+
+/* Re-sort statistics of the contact-list pipeline (DEM_COLLIDE_COMPACT):
+ * out[0] re-sorts since dem_create, out[1] kernel launches a re-sort adds to
+ * its step, out[2] candidate pairs in the current list, out[3] steps since
+ * dem_create.  Zeros for the per-particle forms. */
+dem_status dem_get_resort_stats(dem_ctx* ctx, int64_t out[4]);
 
 /* Block until all queued work of the context finished; returns the sticky
  * device status. */

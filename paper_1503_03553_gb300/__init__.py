@@ -19,6 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdem_gb300.so")
 
+ABI_VERSION = 4  # the include/dem.h this binding marshals for
 DEM_OK, DEM_ERR_ARG, DEM_ERR_ALLOC, DEM_ERR_CUDA, DEM_ERR_CAPACITY = 0, 1, 2, 3, 4
 DEM_ERR_NONFINITE, DEM_ERR_TIMEOUT, DEM_ERR_STATE = 5, 6, 7
 DEM_FP64, DEM_MIXED, DEM_FP32 = 0, 1, 2
@@ -56,7 +57,7 @@ class dem_box(C.Structure):
                 ("material", C.c_int32), ("ncell", C.c_int32 * 3),
                 ("max_particles", C.c_int64), ("r_max", C.c_double),
                 ("nwalls", C.c_int32), ("walls", C.POINTER(dem_wall)),
-                ("r_split", C.c_double)]
+                ("r_split", C.c_double), ("skin", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -104,6 +105,7 @@ def lib() -> C.CDLL:
         "dem_get_phase_times": (C.c_int32, [vp, dp, C.c_int32]),
         "dem_set_timing": (C.c_int, [vp, C.c_int32]),
         "dem_launches_per_step": (C.c_int32, [vp]),
+        "dem_get_resort_stats": (C.c_int, [vp, i64p]),
         "dem_autotune": (C.c_int, [vp, C.c_int64, dp, ip, ip]),
         "dem_sync": (C.c_int, [vp]),
         "dem_last_error": (C.c_char_p, [vp]),
@@ -116,6 +118,9 @@ def lib() -> C.CDLL:
         f = getattr(L, name)
         f.restype = res
         f.argtypes = args
+    if L.dem_abi_version() != ABI_VERSION:
+        raise ImportError(f"{LIB_PATH} has ABI version {L.dem_abi_version()}, the binding "
+                          f"expects {ABI_VERSION}: rebuild it")
     _lib = L
     return L
 
@@ -336,6 +341,15 @@ def dem_launches_per_step(ctx) -> int:
     return lib().dem_launches_per_step(ctx)
 
 
+def dem_get_resort_stats(ctx) -> dict:
+    """Re-sorts so far, kernels a re-sort adds, candidate pairs in the
+    current list, steps so far (contact-list pipeline)."""
+    out = (C.c_int64 * 4)()
+    _check(ctx, lib().dem_get_resort_stats(ctx, out))
+    return {"resorts": out[0], "launches_per_resort": out[1], "candidates": out[2],
+            "steps": out[3]}
+
+
 def dem_sync(ctx) -> None:
     _check(ctx, lib().dem_sync(ctx))
 
@@ -351,14 +365,16 @@ def dem_last_error(ctx) -> str:
 class Context:
     """Owns one dem_ctx.  ``boxes`` are objects with the fields of
     ``synth.Box`` (L, periodic, floor_wall, g, dt, E, poisson, density,
-    restitution, mu_d, r_max, n; optional walls, r_split) or dicts with the
-    same keys."""
+    restitution, mu_d, r_max, n; optional walls, r_split, skin) or dicts
+    with the same keys.  ``skins`` overrides the boxes' candidate-list skins
+    [m] (0 = search every step)."""
 
     def __init__(self, boxes: Sequence, precision="mixed", collide=DEM_COLLIDE_COMPACT,
                  kn_literal=0, row_capacity=0, graph_steps=0, block=0,
                  capacities: Optional[Sequence[int]] = None,
                  r_max: Optional[Sequence[float]] = None,
-                 ncell: Optional[Sequence] = None, torch_alloc: bool = True):
+                 ncell: Optional[Sequence] = None, torch_alloc: bool = True,
+                 skins: Optional[Sequence[float]] = None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("a CUDA device is required")
@@ -385,6 +401,7 @@ class Context:
             bx.max_particles = int(capacities[k]) if capacities is not None else int(g("n"))
             bx.r_max = float(r_max[k]) if r_max is not None else float(g("r_max"))
             bx.r_split = float(g("r_split", 0.0) or 0.0)
+            bx.skin = float(skins[k]) if skins is not None else float(g("skin", 0.0) or 0.0)
             walls = list(g("walls", ()) or ())
             bx.nwalls = len(walls)
             if walls:
@@ -492,6 +509,9 @@ class Context:
 
     def launches_per_step(self):
         return dem_launches_per_step(self.ctx)
+
+    def resort_stats(self):
+        return dem_get_resort_stats(self.ctx)
 
     def autotune(self, steps=32):
         return dem_autotune(self.ctx, steps)

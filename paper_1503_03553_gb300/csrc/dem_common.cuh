@@ -29,6 +29,14 @@ enum : unsigned {
   kStRange = 16u,          // fixed-point position out of range
 };
 
+// control words of the candidate-list pipeline (device, per context)
+enum : int {
+  kCtlResort = 0,     // this step re-sorts and rebuilds the candidate list
+  kCtlRequest = 1,    // a re-sort is asked for (displacement or host call)
+  kCtlResorts = 2,    // re-sorts so far (statistics)
+  kCtlWords = 4
+};
+
 // A rectangle (p + s u + t v) or line (p + s u) wall, s, t in [0, 1]: the
 // geometry in FP64 for the contact and in FP32 for a conservative cull.
 struct WallDev {
@@ -56,6 +64,12 @@ struct BoxDev {
   float rmax_f;         // largest radius the box may hold [m]
   float rsplit_f;       // size-binned search: a particle is large when its
                         // FP32 radius exceeds this (+inf: one class)
+  float skin_f;         // candidate-list skin [m]: pairs within r_i + r_j +
+                        // skin are kept between re-sorts (0: re-sort and
+                        // search every step)
+  float disp2_lim;      // a particle displaced more than sqrt(disp2_lim)
+                        // since the last re-sort asks for the next one
+                        // (-1: every step)
   int n[3];             // cells per axis
   int periodic[3];
   int floor_wall;

@@ -64,10 +64,18 @@ struct dem_ctx {
   std::vector<BoxDev> hbox;
   std::vector<void*> allocs;
   Dev dev{};
+  // Particle state.  DEM_COLLIDE_COMPACT keeps it in ps[0] between re-sorts
+  // (a re-sort orders it into ps[1] and commits it back; parity stays 0);
+  // the per-particle Collide forms sort every step from one to the other.
   PState ps[2]{};
-  CList cl[2]{};
-  int* cs[2]{};                // cell starts of the order held by state 0 / 1
-  unsigned char* dirty[2]{};   // changed-cell flags read by a step of parity 0 / 1
+  CList cl[2]{};               // contact lists of the per-particle forms
+  VList vl[2]{};               // candidate lists: [0] current, [1] a re-sort's
+  int* cs_cur = nullptr;       // cell starts of the current order
+  int* cs_new = nullptr;       // cell starts of the order being built
+  unsigned char* collect = nullptr;  // cells changed since the last sort
+  unsigned char* chg = nullptr;      // ... as seen by the sort running now
+  bool always_resort = false;  // some box keeps no skin: re-sort every step
+  cudaStream_t body_stream = nullptr;  // captures the re-sort kernels of a graph
   int parity = 0;
   int nwh = 0;                   // wall histories per slot (largest box)
   std::vector<WallDev> hwalls;   // all boxes' rectangle and line walls
@@ -82,6 +90,7 @@ struct dem_ctx {
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
   Timing tm;
   double phase_ms[kPhases] = {};
+  int64_t steps_done = 0;
 };
 
 namespace {
@@ -137,9 +146,14 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
   return spread(x) | (spread(y) << 1) | (spread(z) << 2);
 }
 
+// kernels of a step that does not re-sort (DEM_COLLIDE_COMPACT: decide,
+// pairs, sum + integrate; the per-particle forms sort every step)
 int launches_per_step(const dem_ctx* ctx) {
-  return (ctx->fused ? 7 : 8) + (ctx->hwalls.empty() ? 0 : 1) + (ctx->split ? 1 : 0);
+  if (ctx->fused) return 7 + (ctx->hwalls.empty() ? 0 : 1);
+  return 3 + (ctx->hwalls.empty() ? 0 : 1);
 }
+// kernels a re-sort adds (cell scan x3, scatter, reorder, search, rows, commit)
+int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 8 + (ctx->split ? 1 : 0); }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -150,17 +164,18 @@ int blocks_for(long long n, int b) { return (int)((n + b - 1) / b); }
 // --------------------------------------------------------------------------
 // one step, enqueued on ctx->stream
 // --------------------------------------------------------------------------
+// The per-particle Collide forms (Algorithm 1 and its two-loop form): sort
+// every step from state p into state q, then the per-particle kernel.
 template <int M>
-void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
+void enqueue_fused(dem_ctx* ctx, int p, bool store_ft) {
   const int q = 1 - p;
-  // this step sorts the order of state p into state q: cell starts of both
-  // orders, and the changed-cell flags read now and collected for next time
   Dev d = ctx->dev;
-  d.cstart = ctx->cs[q];
-  d.cstart_old = ctx->cs[p];
-  d.dirty = ctx->dirty[p];
-  d.dirty_next = ctx->dirty[q];
-  if (ctx->fused) d.cellbox = nullptr;  // the per-particle forms do not prune
+  d.cstart = ctx->cs_new;
+  d.cstart_old = ctx->cs_cur;
+  d.chg = ctx->chg;
+  d.collect = ctx->collect;
+  d.cellbox = nullptr;  // the per-particle forms do not prune
+  d.gate = nullptr;
   cudaStream_t s = ctx->stream;
   const int bs = ctx->block;
   const bool tm = ctx->tm.on;
@@ -168,65 +183,133 @@ void enqueue_step(dem_ctx* ctx, int p, bool store_ft) {
   if (tm) cudaEventRecord(ev[0], s);
   // 1. cell counts -> starts (rank order) and ranges (linear cells)
   int nbc = blocks_for(d.M_rank, kScanTile);
-  k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
-  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0,
-                                           d.status, 0u);
+  k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum, d.gate);
+  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u, d.gate);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(
       d.ccount, d.M_rank, d.scan_bsum,
-      CellEpi{d.cstart, d.crange, d.cellbox, d.lin_of_rank, d.dirty, d.dirty_next, d.ccur});
+      CellEpi{d.cstart, d.crange, d.cellbox, d.lin_of_rank, d.collect, ctx->chg, d.ccur}, d.gate);
   // 2. counting sort by (Morton cell, id) and reorder into parity q
   k_scatter<<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p]);
-  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q],
-                                                  ctx->fused ? nullptr : ctx->cl[q].count);
+  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[p], ctx->ps[q], nullptr);
+  cudaMemcpyAsync(ctx->cs_cur, ctx->cs_new, sizeof(int) * std::max(1, d.M_rank),
+                  cudaMemcpyDeviceToDevice, s);
   if (tm) cudaEventRecord(ev[1], s);
-  if (ctx->fused) {
-    // Algorithm 1: search and force in one pass, no contact list
-    if (ctx->twoloop)
-      k_collide_per_particle<M, true><<<blocks_for(d.N, bs), bs, 0, s>>>(
-          d, ctx->ps[q], ctx->cl[p], ctx->cl[q], ctx->ko);
-    else
-      k_collide_per_particle<M, false><<<blocks_for(d.N, bs), bs, 0, s>>>(
-          d, ctx->ps[q], ctx->cl[p], ctx->cl[q], ctx->ko);
-    if (tm) {
-      cudaEventRecord(ev[2], s);
-      cudaEventRecord(ev[3], s);
-      cudaEventRecord(ev[4], s);
-    }
-    if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
-    k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q],
-                                                            store_ft ? 1 : 0);
-    if (tm) cudaEventRecord(ev[5], s);
-    return;
-  }
-  // 3. contact search and dense contact list
-  // the search kernel is compiled for at most 256 threads per block
-  const int bs_search = bs < 256 ? bs : 256;
-  if (ctx->split) {
-    k_candidates<M, true><<<blocks_for(d.N, bs_search), bs_search, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
-    // large particles of size-binned boxes: one warp each, persistent grid
-    k_candidates_large<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
-  } else {
-    k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, s>>>(d, ctx->ps[q], ctx->cl[q]);
-  }
+  // Algorithm 1: search and force in one pass, no contact list
+  if (ctx->twoloop)
+    k_collide_per_particle<M, true><<<blocks_for(d.N, bs), bs, 0, s>>>(
+        d, ctx->ps[q], ctx->cl[p], ctx->cl[q], ctx->ko);
+  else
+    k_collide_per_particle<M, false><<<blocks_for(d.N, bs), bs, 0, s>>>(
+        d, ctx->ps[q], ctx->cl[p], ctx->cl[q], ctx->ko);
   if (tm) {
     cudaEventRecord(ev[2], s);
     cudaEventRecord(ev[3], s);
+    cudaEventRecord(ev[4], s);
   }
-  // 5. one thread per contact
-  k_force<M><<<ctx->nsm * 8, 256, 0, s>>>(d, ctx->ps[q], ctx->cl[p], ctx->cl[q]);
-  if (tm) cudaEventRecord(ev[4], s);
-  // 6. sum, wall, gravity, integrate, bin
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
-  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], ctx->cl[q],
+  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], nullptr,
                                                           store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
-void enqueue(dem_ctx* ctx, int p, bool store_ft) {
+// The contact-list pipeline (DEM_COLLIDE_COMPACT).  The re-sort kernels
+// (cell scan, counting sort, reorder, candidate search, rows with the
+// history carried over, commit) go on stream rs: the step's own stream when
+// launched directly, where they read the decision from the device and return
+// at once when it is "no"; a capture stream into the body of a conditional
+// graph node otherwise, which runs them only when the decision is "yes".
+template <int M>
+void enqueue_resort(dem_ctx* ctx, cudaStream_t rs, bool tm, cudaEvent_t* ev) {
+  Dev d = ctx->dev;
+  d.cstart = ctx->cs_new;
+  d.cstart_old = ctx->cs_cur;
+  d.chg = ctx->chg;
+  d.collect = ctx->collect;
+  d.gate = d.vctl + kCtlResort;
+  const int bs = ctx->block;
+  int nbc = blocks_for(d.M_rank, kScanTile);
+  k_scan_reduce<<<nbc, kScanThreads, 0, rs>>>(d.ccount, d.M_rank, d.scan_bsum, d.gate);
+  k_scan_top<<<1, kScanTopThreads, 0, rs>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u, d.gate);
+  k_scan_apply<<<nbc, kScanThreads, 0, rs>>>(
+      d.ccount, d.M_rank, d.scan_bsum,
+      CellEpi{d.cstart, d.crange, d.cellbox, d.lin_of_rank, d.collect, ctx->chg, d.ccur}, d.gate);
+  k_scatter<<<blocks_for(d.N, bs), bs, 0, rs>>>(d, ctx->ps[0]);
+  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vl[1].count);
+  if (tm) cudaEventRecord(ev[1], rs);
+  // the search kernel is compiled for at most 256 threads per block
+  const int bs_search = bs < 256 ? bs : 256;
+  if (ctx->split) {
+    k_candidates<M, true><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
+    // large particles of size-binned boxes: one warp each, persistent grid
+    k_candidates_large<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
+  } else {
+    k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
+  }
+  if (tm) cudaEventRecord(ev[2], rs);
+  k_rows<M><<<blocks_for(d.N, 256), 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[0], ctx->vl[1]);
+  k_commit<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vl[0], ctx->vl[1],
+                                            ctx->cs_new, ctx->cs_cur);
+}
+
+template <int M>
+void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
+  Dev d = ctx->dev;
+  d.gate = nullptr;
+  d.collect = ctx->collect;
+  cudaStream_t s = ctx->stream;
+  const int bs = ctx->block;
+  if (tm) cudaEventRecord(ev[3], s);
+  k_pairs<M><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0]);
+  if (tm) cudaEventRecord(ev[4], s);
+  if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
+  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0], ctx->vl[0].flag,
+                                                          store_ft ? 1 : 0);
+  if (tm) cudaEventRecord(ev[5], s);
+}
+
+// one step launched directly (no graph)
+template <int M>
+void enqueue_compact(dem_ctx* ctx, bool store_ft) {
+  cudaStream_t s = ctx->stream;
+  const bool tm = ctx->tm.on;
+  cudaEvent_t* ev = ctx->tm.ev[ctx->tm.used % kRing];
+  if (tm) cudaEventRecord(ev[0], s);
+  k_decide<<<1, 32, 0, s>>>(ctx->dev.vctl, ctx->always_resort ? 1 : 0, 0, 0);
+  enqueue_resort<M>(ctx, s, tm, ev);
+  enqueue_tail<M>(ctx, store_ft, tm, ev);
+}
+
+// one step launched directly; returns the parity after it
+int enqueue(dem_ctx* ctx, int p, bool store_ft) {
+  if (ctx->fused) {
+    switch (ctx->mode) {
+      case kFP64: enqueue_fused<kFP64>(ctx, p, store_ft); break;
+      case kMIXED: enqueue_fused<kMIXED>(ctx, p, store_ft); break;
+      default: enqueue_fused<kFP32>(ctx, p, store_ft); break;
+    }
+    return 1 - p;
+  }
   switch (ctx->mode) {
-    case kFP64: enqueue_step<kFP64>(ctx, p, store_ft); break;
-    case kMIXED: enqueue_step<kMIXED>(ctx, p, store_ft); break;
-    default: enqueue_step<kFP32>(ctx, p, store_ft); break;
+    case kFP64: enqueue_compact<kFP64>(ctx, store_ft); break;
+    case kMIXED: enqueue_compact<kMIXED>(ctx, store_ft); break;
+    default: enqueue_compact<kFP32>(ctx, store_ft); break;
+  }
+  return p;
+}
+
+void enqueue_resort_any(dem_ctx* ctx, cudaStream_t rs) {
+  switch (ctx->mode) {
+    case kFP64: enqueue_resort<kFP64>(ctx, rs, false, nullptr); break;
+    case kMIXED: enqueue_resort<kMIXED>(ctx, rs, false, nullptr); break;
+    default: enqueue_resort<kFP32>(ctx, rs, false, nullptr); break;
+  }
+}
+
+void enqueue_tail_any(dem_ctx* ctx, bool store_ft) {
+  switch (ctx->mode) {
+    case kFP64: enqueue_tail<kFP64>(ctx, store_ft, false, nullptr); break;
+    case kMIXED: enqueue_tail<kMIXED>(ctx, store_ft, false, nullptr); break;
+    default: enqueue_tail<kFP32>(ctx, store_ft, false, nullptr); break;
   }
 }
 
@@ -312,6 +395,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
       free_all(ctx);
       if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
       if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+      if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
       for (cudaEvent_t& e : ctx->xfer_ev)
         if (e) cudaEventDestroy(e);
       if (ctx->h_status) cudaFreeHost(ctx->h_status);
@@ -321,6 +405,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     return s;
   };
   if (ctx->K < 2 || ctx->K > 1024) return bail(DEM_ERR_ARG, "row_capacity out of range");
+  ctx->K = (ctx->K + 3) & ~3;  // rows are read four entries at a time
   if (ctx->block < 32 || ctx->block > 1024 || (ctx->block & 31))
     return bail(DEM_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
   if (cudaGetDevice(&ctx->device) != cudaSuccess)
@@ -333,7 +418,8 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
       return bail(DEM_ERR_CUDA, "stream creation failed");
     ctx->own_stream = true;
   }
-  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(DEM_ERR_CUDA, "stream creation failed");
   for (cudaEvent_t& e : ctx->xfer_ev)
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
@@ -362,18 +448,25 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     const bool split = bx.r_split > 0;
     if (split && ctx->fused)
       return bail(DEM_ERR_ARG, "a size-binned box (r_split > 0) needs DEM_COLLIDE_COMPACT");
+    if (!(bx.skin >= 0) || !std::isfinite(bx.skin))
+      return bail(DEM_ERR_ARG, "skin must be finite and >= 0");
+    if (bx.skin > 0 && ctx->fused)
+      return bail(DEM_ERR_ARG, "a skin needs DEM_COLLIDE_COMPACT (the per-particle forms search every step)");
+    const double skin = bx.skin;
     ctx->split = ctx->split || split;
     long long ncell = 1;
     for (int a = 0; a < 3; ++a) {
       if (!(bx.L[a] > 0) || bx.L[a] * 0x1p60 >= 0x1p62)
         return bail(DEM_ERR_ARG, "box length out of range (0, 4 m)");
       int n = bx.ncell[a];
-      // small pairs within +-1 cell; with r_split, large ones within +-2
-      const double hmin = (split ? std::max(2.0 * bx.r_split, bx.r_max) : 2.0 * bx.r_max) * (1.0 + 1e-5);
+      // candidate pairs (reach r_i + r_j + skin) of small particles within
+      // +-1 cell; with r_split, those of large ones within +-2
+      const double hmin = (split ? std::max(2.0 * bx.r_split + skin, bx.r_max + 0.5 * skin)
+                                 : 2.0 * bx.r_max + skin) * (1.0 + 1e-5);
       if (n <= 0) n = std::max(1, (int)std::floor(bx.L[a] / hmin));
       if (bx.L[a] / n < hmin)
-        return bail(DEM_ERR_ARG, split ? "cells narrower than max(2 r_split, r_max) (1 + 1e-5)"
-                                       : "cells narrower than 2 r_max (1 + 1e-5)");
+        return bail(DEM_ERR_ARG, split ? "cells narrower than max(2 r_split + skin, r_max + skin / 2) (1 + 1e-5)"
+                                       : "cells narrower than (2 r_max + skin) (1 + 1e-5)");
       if (bx.periodic[a] && n < (split ? 5 : 3))
         return bail(DEM_ERR_ARG, split ? "a periodic axis of a size-binned box needs at least 5 cells"
                                        : "a periodic axis needs at least 3 cells");
@@ -405,6 +498,26 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     B.floor_wall = bx.floor_wall ? 1 : 0;
     B.rmax_f = (float)bx.r_max;
     B.rsplit_f = split ? (float)bx.r_split : INFINITY;
+    // The skin test.  A pair left out of the candidate list at a re-sort was
+    // at least r_i + r_j + skin apart, less the FP32 rounding of that test
+    // (far below 1e-5 of the reach); the contact rule accepts nothing
+    // farther than r_i + r_j plus its own rounding (the same bound).  So no
+    // pair outside the list can touch while every particle has moved less
+    // than half of skin - 1e-5 (4 r_max + skin), less in DEM_FP32 the
+    // rounding of its float positions (a few units of the last place of
+    // the box length) in the tests and in the displacement itself.
+    {
+      double lim = skin - 1e-5 * (4.0 * bx.r_max + skin);
+      if (ctx->mode == kFP32) {
+        const double Lmax = std::max(bx.L[0], std::max(bx.L[1], bx.L[2]));
+        const double ulp = std::ldexp(1.0, std::ilogb(Lmax) - 23);
+        lim -= 20.0 * ulp;
+      }
+      lim *= 0.5;
+      B.skin_f = (float)skin;
+      B.disp2_lim = lim > 0 ? std::nextafter((float)(lim * lim * (1.0 - 1e-6)), 0.0f) : -1.0f;
+      if (B.disp2_lim < 0.0f) ctx->always_resort = true;
+    }
     // rectangle and line walls
     if (bx.nwalls < 0 || (bx.nwalls > 0 && !bx.walls) || B.floor_wall + bx.nwalls > 15)
       return bail(DEM_ERR_ARG, "a box holds 0 to 15 walls (floor included), listed in walls");
@@ -519,10 +632,10 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.lin_of_rank = (const int*)A(sizeof(int) * std::max(1, ctx->M_rank));
   d.ccount = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
   d.ccur = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
-  for (int p = 0; p < 2; ++p) {
-    ctx->cs[p] = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
-    ctx->dirty[p] = (unsigned char*)A(std::max(1, ctx->M_rank));
-  }
+  ctx->cs_cur = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
+  ctx->cs_new = (int*)A(sizeof(int) * std::max(1, ctx->M_rank));
+  ctx->collect = (unsigned char*)A(std::max(1, ctx->M_rank));
+  ctx->chg = (unsigned char*)A(std::max(1, ctx->M_rank));
   d.crange = (int2*)A(sizeof(int2) * std::max(1, ctx->M_lin));
   d.cellbox = (float4*)A(2 * sizeof(float4) * std::max(1, ctx->M_lin));
   d.perm = (int*)A(sizeof(int) * n);
@@ -541,7 +654,13 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     d.Tfused = A(v4_bytes(M) * n);
   } else {
     d.inrow = (int2*)A(sizeof(int2) * n * ctx->K);
+    d.frow = (int*)A(sizeof(int) * n * ctx->K);
+    d.fcnt = (int*)A(sizeof(int) * n);
+    d.xb = A(pos_bytes(M) * n);
+    d.yb = A(pos_bytes(M) * n);
+    d.zb = A(pos_bytes(M) * n);
   }
+  d.vctl = (unsigned*)A(sizeof(unsigned) * kCtlWords);
   if (!ctx->hwalls.empty()) {
     d.Fwall = A(v4_bytes(M) * n);
     d.Twall = A(v4_bytes(M) * n);
@@ -568,15 +687,28 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
       s.wy = A(dt_bytes(M) * n * ctx->nwh);
       s.wz = A(dt_bytes(M) * n * ctx->nwh);
     }
-    CList& c = ctx->cl[p];
-    c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
-    c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
-    c.dx = A(dt_bytes(M) * ctx->Cmax);
-    c.dy = A(dt_bytes(M) * ctx->Cmax);
-    c.dz = A(dt_bytes(M) * ctx->Cmax);
-    c.hs = (int*)A(sizeof(int) * n);
-    c.oc = (int*)A(sizeof(int) * n);
-    c.count = (int*)A(sizeof(int));
+    if (ctx->fused) {
+      CList& c = ctx->cl[p];
+      c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
+      c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
+      c.dx = A(dt_bytes(M) * ctx->Cmax);
+      c.dy = A(dt_bytes(M) * ctx->Cmax);
+      c.dz = A(dt_bytes(M) * ctx->Cmax);
+      c.hs = (int*)A(sizeof(int) * n);
+      c.oc = (int*)A(sizeof(int) * n);
+      c.count = (int*)A(sizeof(int));
+    } else {
+      VList& c = ctx->vl[p];
+      c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
+      c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
+      c.dx = A(dt_bytes(M) * ctx->Cmax);
+      c.dy = A(dt_bytes(M) * ctx->Cmax);
+      c.dz = A(dt_bytes(M) * ctx->Cmax);
+      c.flag = (unsigned char*)A(ctx->Cmax);
+      c.hs = (int*)A(sizeof(int) * n);
+      c.oc = (int*)A(sizeof(int) * n);
+      c.count = (int*)A(sizeof(int));
+    }
   }
   ctx->staging = (double*)A(sizeof(double) * 16 * (size_t)std::max(1, max_cap));
   ctx->staging_i = (int*)A(sizeof(int) * 2 * (size_t)std::max(1, max_cap));
@@ -614,15 +746,20 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   if (!e) e = cudaMemsetAsync(d.status, 0, sizeof(unsigned), s);
   if (!e) e = cudaMemsetAsync(d.diag, 0, sizeof(unsigned) * 2 * ctx->hbox.size(), s);
   if (!e) e = cudaMemsetAsync(d.icnt, 0, sizeof(int) * n, s);
+  if (!e) e = cudaMemsetAsync(ctx->collect, 1, std::max(1, ctx->M_rank), s);
+  if (!e) e = cudaMemsetAsync(ctx->chg, 1, std::max(1, ctx->M_rank), s);
+  if (!e) e = cudaMemsetAsync(ctx->cs_cur, 0, sizeof(int) * std::max(1, ctx->M_rank), s);
+  if (!e) e = cudaMemsetAsync(ctx->cs_new, 0, sizeof(int) * std::max(1, ctx->M_rank), s);
+  if (!e) e = cudaMemsetAsync(d.vctl, 0, sizeof(unsigned) * kCtlWords, s);
   for (int p = 0; p < 2 && !e; ++p) {
-    e = cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s);
-    if (!e) e = cudaMemsetAsync(ctx->cs[p], 0, sizeof(int) * std::max(1, ctx->M_rank), s);
+    int* oc = ctx->fused ? ctx->cl[p].oc : ctx->vl[p].oc;
+    int* hs = ctx->fused ? ctx->cl[p].hs : ctx->vl[p].hs;
+    int* cnt = ctx->fused ? ctx->cl[p].count : ctx->vl[p].count;
+    e = cudaMemsetAsync(oc, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(hs, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(cnt, 0, sizeof(int), s);
   }
-  for (int p = 0; p < 2 && !e; ++p) {
-    e = cudaMemsetAsync(ctx->cl[p].oc, 0, sizeof(int) * n, s);
-    if (!e) e = cudaMemsetAsync(ctx->cl[p].hs, 0, sizeof(int) * n, s);
-    if (!e) e = cudaMemsetAsync(ctx->cl[p].count, 0, sizeof(int), s);
-  }
+  if (!e && !ctx->fused) e = cudaMemsetAsync(d.fcnt, 0, sizeof(int) * n, s);
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return bail(DEM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
   *out = ctx;
@@ -641,6 +778,7 @@ dem_status dem_destroy(dem_ctx* ctx) {
   if (ctx->h_count) cudaFreeHost(ctx->h_count);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
   for (cudaEvent_t& e : ctx->xfer_ev)
     if (e) cudaEventDestroy(e);
   delete ctx;
@@ -682,9 +820,12 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
   if (st) return st;
   // the box's history is empty: no slot of the box holds a stored contact
   for (int q = 0; q < 2; ++q)
-    CK(cudaMemsetAsync(ctx->cl[q].oc + B.pbase, 0, sizeof(int) * B.cap, s));
-  // the next sort starts from the order the particles were given in
-  CK(cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s));
+    CK(cudaMemsetAsync((ctx->fused ? ctx->cl[q].oc : ctx->vl[q].oc) + B.pbase, 0,
+                       sizeof(int) * B.cap, s));
+  // the next sort starts from the order the particles were given in, and
+  // the next step re-sorts
+  CK(cudaMemsetAsync(ctx->collect, 1, std::max(1, ctx->M_rank), s));
+  CK(cudaMemsetAsync(ctx->dev.vctl + kCtlRequest, 1, sizeof(unsigned), s));
   if (n > 0) {
     const double *dx = x, *dv = v, *dw = omega, *dr = radius;
     if (where == DEM_HOST) {
@@ -750,23 +891,71 @@ dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
     }
     CK(cudaGetLastError());
   }
-  // new positions may have changed cells: the next sort starts from scratch
-  if (x) CK(cudaMemsetAsync(ctx->dirty[p], 1, std::max(1, ctx->M_rank), s));
+  // new positions may have changed cells: the next step re-sorts from scratch
+  if (x) {
+    CK(cudaMemsetAsync(ctx->collect, 1, std::max(1, ctx->M_rank), s));
+    CK(cudaMemsetAsync(ctx->dev.vctl + kCtlRequest, 1, sizeof(unsigned), s));
+  }
   // the caller's host arrays are read by the time the call returns
   if (where == DEM_HOST) CK(cudaStreamSynchronize(cs));
   return DEM_OK;
 }
 
+// G steps in one CUDA graph.  The per-particle forms alternate the state
+// parity and need one graph per starting parity.  The contact-list pipeline
+// keeps its state in place: each step is a decision kernel, a conditional
+// node whose body holds the re-sort kernels (run only when the decision says
+// so), and the pair and integration kernels.
 static dem_status build_graph(dem_ctx* ctx, int p) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   int q = p;
-  for (int k = 0; k < ctx->graph_steps; ++k) {
-    enqueue(ctx, q, k == ctx->graph_steps - 1);
-    q = 1 - q;
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < ctx->graph_steps && e == cudaSuccess; ++k) {
+    const bool last = k == ctx->graph_steps - 1;
+    if (ctx->fused) {
+      q = enqueue(ctx, q, last);
+      continue;
+    }
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(ctx->stream, &cst, nullptr, &cg, &deps, &edges, &ndeps);
+    cudaGraphConditionalHandle h{};
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 0, 0);
+    if (e != cudaSuccess) break;
+    k_decide<<<1, 32, 0, ctx->stream>>>(ctx->dev.vctl, ctx->always_resort ? 1 : 0, h, 1);
+    e = cudaStreamGetCaptureInfo(ctx->stream, &cst, nullptr, &cg, &deps, &edges, &ndeps);
+    if (e != cudaSuccess) break;
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeIf;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, cg, deps, edges, ndeps, &cp);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) break;
+    e = cudaStreamBeginCaptureToGraph(ctx->body_stream, cp.conditional.phGraph_out[0], nullptr,
+                                      nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) break;
+    enqueue_resort_any(ctx, ctx->body_stream);
+    cudaGraph_t body = nullptr;
+    e = cudaStreamEndCapture(ctx->body_stream, &body);
+    if (e != cudaSuccess) break;
+    enqueue_tail_any(ctx, last);
   }
-  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
-  if (e != cudaSuccess) return fail(ctx, DEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return fail(ctx, DEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  }
   e = cudaGraphInstantiate(&ctx->gexec[p], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(ctx, DEM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
@@ -812,13 +1001,12 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
     return DEM_OK;
   };
   while (left > 0) {
-    enqueue(ctx, ctx->parity, left == 1);
+    ctx->parity = enqueue(ctx, ctx->parity, left == 1);
     CK(cudaGetLastError());
     if (timing && ++ctx->tm.used == kRing) {
       dem_status st = drain();
       if (st) return st;
     }
-    ctx->parity = 1 - ctx->parity;
     --left;
   }
   if (timing) {
@@ -828,6 +1016,7 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
   if (timing && ctx->tm.steps)
     for (int k = 0; k < kPhases; ++k) ctx->phase_ms[k] = ctx->tm.acc[k] / ctx->tm.steps;
   ctx->have_ft = true;
+  ctx->steps_done += nsteps;
   return read_status(ctx);
 }
 
@@ -909,6 +1098,22 @@ int32_t dem_get_phase_times(dem_ctx* ctx, double* ms, int32_t cap) {
   int k = std::min(cap, kPhases);
   for (int q = 0; q < k; ++q) ms[q] = ctx->phase_ms[q];
   return k;
+}
+
+dem_status dem_get_resort_stats(dem_ctx* ctx, int64_t out[4]) {
+  if (!ctx || !out) return fail(ctx, DEM_ERR_ARG, "null argument");
+  for (int k = 0; k < 4; ++k) out[k] = 0;
+  if (ctx->fused) return DEM_OK;
+  unsigned ctl[kCtlWords] = {};
+  int cnt = 0;
+  CK(cudaMemcpyAsync(ctl, ctx->dev.vctl, sizeof(ctl), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&cnt, ctx->vl[0].count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  out[0] = ctl[kCtlResorts];
+  out[1] = launches_per_resort(ctx);
+  out[2] = std::min(cnt, ctx->Cmax);
+  out[3] = ctx->steps_done;
+  return DEM_OK;
 }
 
 dem_status dem_sync(dem_ctx* ctx) {
@@ -997,14 +1202,22 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
                                 std::vector<double>* F = nullptr,
                                 std::vector<double>* nF = nullptr) {
   cudaStream_t s = ctx->stream;
-  const CList& c = ctx->cl[ctx->parity];
+  // the per-particle forms' list of the last step, or the candidate list
+  // (its pairs in contact in the last step carry flag 1)
+  const int* c_hs = ctx->fused ? ctx->cl[ctx->parity].hs : ctx->vl[0].hs;
+  const int* c_oc = ctx->fused ? ctx->cl[ctx->parity].oc : ctx->vl[0].oc;
+  const int2* c_hid = ctx->fused ? ctx->cl[ctx->parity].hid : ctx->vl[0].hid;
+  void* const comps[3] = {ctx->fused ? ctx->cl[ctx->parity].dx : ctx->vl[0].dx,
+                          ctx->fused ? ctx->cl[ctx->parity].dy : ctx->vl[0].dy,
+                          ctx->fused ? ctx->cl[ctx->parity].dz : ctx->vl[0].dz};
+  const unsigned char* c_flag = ctx->fused ? nullptr : ctx->vl[0].flag;
   const int N = ctx->N;
   std::vector<int> rs(N), rc(N);
   hid.clear();
   dts.clear();
   if (N == 0) return DEM_OK;
-  CK(cudaMemcpyAsync(rs.data(), c.hs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(rc.data(), c.oc, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rs.data(), c_hs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rc.data(), c_oc, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   long long top = 0;
   for (const BoxDev& B : ctx->hbox)
@@ -1013,13 +1226,13 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
   top = std::min<long long>(top, ctx->Cmax);
   std::vector<int2> h(top);
   const size_t eb = dt_bytes(ctx->mode), vb = v4_bytes(ctx->mode);
-  std::vector<unsigned char> raw[3], fr, nr;
+  std::vector<unsigned char> raw[3], fr, nr, fl(std::max(1ll, top), 1);
   for (int a = 0; a < 3; ++a) raw[a].resize(eb * std::max(1ll, top));
   if (top > 0) {
-    CK(cudaMemcpyAsync(h.data(), c.hid, sizeof(int2) * top, cudaMemcpyDeviceToHost, s));
-    void* comps[3] = {c.dx, c.dy, c.dz};
+    CK(cudaMemcpyAsync(h.data(), c_hid, sizeof(int2) * top, cudaMemcpyDeviceToHost, s));
     for (int a = 0; a < 3; ++a)
       CK(cudaMemcpyAsync(raw[a].data(), comps[a], eb * top, cudaMemcpyDeviceToHost, s));
+    if (c_flag) CK(cudaMemcpyAsync(fl.data(), c_flag, top, cudaMemcpyDeviceToHost, s));
     if (F) {
       fr.resize(vb * top);
       nr.resize(vb * top);
@@ -1058,6 +1271,7 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
       for (int k = 0; k < rc[g]; ++k) {
         long long e = (long long)rs[g] + k;
         if (e >= top) break;
+        if (!fl[e]) continue;  // a candidate pair not in contact
         hid.push_back(h[e]);
         for (int a = 0; a < 3; ++a) dts.push_back(dtval(a, e));
         if (F)
@@ -1207,18 +1421,29 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
       }
     }
   }
-  const CList& c = ctx->cl[ctx->parity];
+  // the per-particle forms read it as the previous step's list; the
+  // contact-list pipeline as its current candidate list (every pair in
+  // contact), carried into the list of the re-sort the next step makes
+  int2* c_hid = ctx->fused ? ctx->cl[ctx->parity].hid : ctx->vl[0].hid;
+  int2* c_pair = ctx->fused ? ctx->cl[ctx->parity].pair : ctx->vl[0].pair;
+  void* const c_d[3] = {ctx->fused ? ctx->cl[ctx->parity].dx : ctx->vl[0].dx,
+                        ctx->fused ? ctx->cl[ctx->parity].dy : ctx->vl[0].dy,
+                        ctx->fused ? ctx->cl[ctx->parity].dz : ctx->vl[0].dz};
+  int* c_hs = ctx->fused ? ctx->cl[ctx->parity].hs : ctx->vl[0].hs;
+  int* c_oc = ctx->fused ? ctx->cl[ctx->parity].oc : ctx->vl[0].oc;
+  int* c_count = ctx->fused ? ctx->cl[ctx->parity].count : ctx->vl[0].count;
   if (nc > 0) {
-    CK(cudaMemcpyAsync(c.hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c.pair, p2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c.dx, comp[0].data(), eb * nc, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c.dy, comp[1].data(), eb * nc, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c.dz, comp[2].data(), eb * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c_hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c_pair, p2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    for (int a = 0; a < 3; ++a)
+      CK(cudaMemcpyAsync(c_d[a], comp[a].data(), eb * nc, cudaMemcpyHostToDevice, s));
+    if (!ctx->fused) CK(cudaMemsetAsync(ctx->vl[0].flag, 1, nc, s));
   }
-  CK(cudaMemcpyAsync(c.hs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(c.oc, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c_hs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c_oc, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
   *ctx->h_count = nc;
-  CK(cudaMemcpyAsync(c.count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c_count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!ctx->fused) CK(cudaMemsetAsync(ctx->dev.vctl + kCtlRequest, 1, sizeof(unsigned), s));
   CK(cudaStreamSynchronize(s));
   return DEM_OK;
 }
@@ -1232,10 +1457,13 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
   double* part = ctx->staging + 8;
   const int nparts = std::max(1, std::min(512, blocks_for(ctx->hbox[box].nlive, 256)));
   const int p = ctx->parity;
+  const int* hs = ctx->fused ? ctx->cl[p].hs : ctx->vl[0].hs;
+  const int* oc = ctx->fused ? ctx->cl[p].oc : ctx->vl[0].oc;
+  const unsigned char* fl = ctx->fused ? nullptr : ctx->vl[0].flag;
   switch (ctx->mode) {
-    case kFP64: k_stats<kFP64><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, part); break;
-    case kMIXED: k_stats<kMIXED><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, part); break;
-    default: k_stats<kFP32><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], ctx->cl[p].oc, box, part); break;
+    case kFP64: k_stats<kFP64><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
+    case kMIXED: k_stats<kMIXED><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
+    default: k_stats<kFP32><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
   }
   k_stats_final<<<1, 32, 0, s>>>(part, nparts, dout);
   CK(cudaGetLastError());
@@ -1285,7 +1513,7 @@ constexpr int kStaticK = 32;
 
 // layout of the scratch array (every part 256-byte aligned)
 struct StaticLayout {
-  size_t box, slot_box, rol, lor, ccount, cstart, ccur, dirty, crange, cellbox, perm, pcell, row,
+  size_t box, slot_box, rol, lor, ccount, cstart, ccur, dirty, chg, crange, cellbox, perm, pcell, row,
       icnt, bsum, status, count, pair, rs, rc, state[2][10], total;
 };
 
@@ -1308,6 +1536,7 @@ StaticLayout static_layout() {
   L.cstart = take(4 * (M + 1));
   L.ccur = take(4 * (M + 1));
   L.dirty = take(M + 1);
+  L.chg = take(M + 1);
   L.crange = take(8 * M);
   L.cellbox = take(32 * M);
   L.perm = take(4 * N);
@@ -1480,7 +1709,8 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   d.cstart = (int*)(base + lay.cstart);
   d.cstart_old = d.cstart;
   d.ccur = (int*)(base + lay.ccur);
-  d.dirty = (const unsigned char*)(base + lay.dirty);
+  d.collect = (unsigned char*)(base + lay.dirty);
+  d.chg = (const unsigned char*)(base + lay.chg);
   d.crange = (int2*)(base + lay.crange);
   d.cellbox = (float4*)(base + lay.cellbox);
   d.perm = (int*)(base + lay.perm);
@@ -1496,7 +1726,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
                    (int*)(base + o[6]), (int*)(base + o[7]), (int*)(base + o[8]),
                    (int*)(base + o[9]), nullptr, nullptr, nullptr};
   }
-  CList cn{};
+  VList cn{};
   cn.pair = (int2*)(base + lay.pair);
   cn.hid = (int2*)pairs;
   cn.hs = (int*)(base + lay.rs);
@@ -1524,11 +1754,12 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   // bin, sort, search, compact: the DEM_MIXED kernels of dem_step
   k_set_particles<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], 0, N, x, x, x, radius);
   int nbc = blocks_for(d.M_rank, kScanTile);
-  k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum);
-  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u);
+  k_scan_reduce<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum, nullptr);
+  k_scan_top<<<1, kScanTopThreads, 0, s>>>(d.scan_bsum, nbc, nullptr, 0, d.status, 0u, nullptr);
   k_scan_apply<<<nbc, kScanThreads, 0, s>>>(d.ccount, d.M_rank, d.scan_bsum,
                                             CellEpi{d.cstart, d.crange, d.cellbox, d.lin_of_rank,
-                                                    d.dirty, nullptr, d.ccur});
+                                                    d.collect, (unsigned char*)d.chg, d.ccur},
+                                            nullptr);
   k_scatter<<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0]);
   k_reorder<kMIXED><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[0], ps[1], cn.count);
   k_candidates<kMIXED, false><<<blocks_for(N, 256), 256, 0, s>>>(d, ps[1], cn);

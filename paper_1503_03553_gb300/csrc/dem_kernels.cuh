@@ -5,16 +5,26 @@
 //   scan of cell counts        -> cell starts          (CalcHash/BitonicSort)
 //   k_scatter + k_cellsort     -> permutation by (Morton cell, id)
 //   k_reorder                  -> state in sorted order (FindCellBoundsAndReorder)
-//   k_candidates               -> contact search over half the neighbour cells
-//                                 (the loops of Algorithm 1; the paper's first
-//                                 loop, Sec. 3.4) and the dense contact list
-//                                 (Sec. 3.4 split, global)
-//   k_force                    -> one thread per contact: Eq. (1), Eq. (vt),
-//                                 Eq. (dt), Coulomb cap, history carry
-//                                 (InitializeContactIDs + Collide)
-//   k_gather_integrate         -> per-particle sum in fixed order, floor wall
-//                                 (CollideRectangle), gravity (ForceGravity),
-//                                 symplectic Euler (Integrate), next binning
+//   k_candidates               -> search over half the neighbour cells (the
+//                                 loops of Algorithm 1; the paper's first loop,
+//                                 Sec. 3.4) for every pair within r_i + r_j +
+//                                 skin: the candidate list (Sec. 3.4 split,
+//                                 global)
+//   k_rows                     -> each particle's candidates in partner-id
+//                                 order; delta_t history carried to the new
+//                                 list (InitializeContactIDs)
+//   k_commit                   -> the sorted state and list become current
+//   (the five kernels above run only in a step that re-sorts: the first one,
+//    and then whenever a particle has moved far enough for a pair outside the
+//    list to reach contact; k_decide makes that call on the device)
+//   k_pairs                    -> the contact rule on every candidate, ballot
+//                                 compaction of the contacts, one lane per
+//                                 contact: Eq. (1), Eq. (vt), Eq. (dt),
+//                                 Coulomb cap (Collide)
+//   k_gather_integrate         -> per-particle sum in partner-id order, floor
+//                                 wall (CollideRectangle), gravity
+//                                 (ForceGravity), symplectic Euler
+//                                 (Integrate), next binning, skin test
 #pragma once
 
 #include <type_traits>
@@ -58,15 +68,36 @@ struct PState {
   void* omg;    // V4 (wx, wy, wz, r)
   void* posr;   // PR
   int* id;      // global id = box slot base + id within the box
-  int* cellc;   // packed cell coordinates used by this parity's sort
-  int* cellx;   // packed cell coordinates after integration (next sort)
-  int* cellg;   // rank-space cell after integration
+  int* cellc;   // packed cell coordinates of the current position (set by
+                // the sort and kept up to date by the integrator)
+  int* cellx;   // packed cell coordinates at the last sort
+  int* cellg;   // rank-space cell of the current position
   void* wx;     // floor-wall delta_t (DT); null when no box has a floor
   void* wy;
   void* wz;
 };
 
-// One parity of the contact list: the pairs of one step.
+// The candidate list of the contact-list pipeline: every pair within
+// r_i + r_j + skin at the last re-sort (each pair once, in the block of the
+// slot that found it), with the pair's tangential history.  A pair is in
+// contact in a step when the contact rule accepts it then; between re-sorts
+// the list is a superset of the contacts (the re-sort comes before any
+// particle can have moved half the skin).  Two of them: the current one and
+// the one a re-sort builds.
+struct VList {
+  int2* pair;   // storage slots (lower-id member, higher-id member)
+  int2* hid;    // ids (lo, hi), lo < hi
+  void* dx;     // delta_t after the last step, per component (DT); zero
+  void* dy;     // unless the pair was in contact in that step
+  void* dz;
+  unsigned char* flag;  // 1: in contact in the last step
+  int* hs;      // by slot: first entry of the pairs the slot found ...
+  int* oc;      // ... and how many (the slot's block of the list)
+  int* count;   // entries (device scalar)
+};
+
+// One parity of the contact list of the per-particle Collide forms: the
+// pairs of one step.
 struct CList {
   int2* pair;   // storage slots (lo, hi) of that step
   int2* hid;    // global ids (lo, hi), lo < hi
@@ -94,8 +125,10 @@ struct Dev {
   int* cstart;   // per rank cell: first slot in the order being built
   const int* cstart_old;  // per rank cell: first slot in the current order
   int* ccur;     // per rank cell: scatter cursor of a cell that changed
-  const unsigned char* dirty;  // per rank cell: members changed since the last sort
-  unsigned char* dirty_next;   // the same, collected for the next sort
+  const unsigned char* chg;    // per rank cell: members changed since the
+                               // last sort (set by the cell scan of a sort)
+  unsigned char* collect;      // the same, collected by the integrator for
+                               // the next sort
   int2* crange;  // per linear cell: (first slot, count)
   float4* cellbox;  // per linear cell, 2 entries: (lo.xyz, largest radius),
                     // (hi.xyz, 0): the bounding box of the members' centres
@@ -119,6 +152,16 @@ struct Dev {
   void* Twall;   // V4 per slot: their torque
   void* Fout;    // V4 per slot: total force of the last step
   void* Tout;    // V4 per slot: total torque of the last step
+  // contact-list pipeline
+  int* frow;     // N x K: every candidate pair of a slot (entry << 1 | 1 if
+                 // the slot is the lower-id member), in increasing partner id
+  int* fcnt;     // their number per slot
+  void* xb;      // P per slot: position at the last re-sort (skin test);
+  void* yb;      // null for the per-particle Collide forms
+  void* zb;
+  unsigned* vctl;        // control words (kCtl*)
+  const unsigned* gate;  // re-sort kernels run only when *gate != 0 (null:
+                         // always)
   unsigned* status;
   unsigned* diag;  // per box: max overlap / r_min, max |F_t| / (mu |F_n|)
   int* scan_bsum;
@@ -126,6 +169,11 @@ struct Dev {
 
 __device__ __forceinline__ void flag(unsigned* st, unsigned bit) {
   atomicOr(st, bit);
+}
+
+// a re-sort kernel whose gate is closed does nothing this step
+__device__ __forceinline__ bool gated_off(const unsigned* gate) {
+  return gate != nullptr && *(const volatile unsigned*)gate == 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -394,7 +442,8 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total) {
 
 template <typename T>
 __global__ void __launch_bounds__(kScanThreads)
-k_scan_reduce(const T* __restrict__ in, int n, T* __restrict__ bsum) {
+k_scan_reduce(const T* __restrict__ in, int n, T* __restrict__ bsum, const unsigned* gate) {
+  if (gated_off(gate)) return;
   int base = blockIdx.x * kScanTile;
   T s = 0;
   for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
@@ -419,7 +468,8 @@ k_scan_reduce(const T* __restrict__ in, int n, T* __restrict__ bsum) {
 template <typename T>
 __global__ void __launch_bounds__(kScanTopThreads)
 k_scan_top(T* bsum, int nb, int* total, int cap, unsigned* status,
-           unsigned over_bit) {
+           unsigned over_bit, const unsigned* gate) {
+  if (gated_off(gate)) return;
   __shared__ T tot;
   T v[kScanTopItems];
   T s = 0;
@@ -453,7 +503,8 @@ k_scan_top(T* bsum, int nb, int* total, int cap, unsigned* status,
 template <typename T, class Epi>
 __global__ void __launch_bounds__(kScanThreads)
 k_scan_apply(const T* __restrict__ in, int n, const T* __restrict__ bsum,
-             Epi epi) {
+             Epi epi, const unsigned* gate) {
+  if (gated_off(gate)) return;
   __shared__ T buf[kScanTile];
   __shared__ T tot;
   int base = blockIdx.x * kScanTile;
@@ -483,21 +534,25 @@ k_scan_apply(const T* __restrict__ in, int n, const T* __restrict__ bsum,
 }
 
 // cell counts -> cell starts (rank order) and (start, count) by linear cell
-// For a cell whose members changed it also zeroes the scatter cursor; it
-// clears the cell's flag for the next sort and resets the cell's box.
+// For a cell whose members changed since the last sort (flag collected by
+// the integrator) it marks the cell changed for this sort and zeroes the
+// scatter cursor; it clears the collected flag and resets the cell's box.
 struct CellEpi {
   int* cstart;
   int2* crange;
   float4* cellbox;  // reset for the reorder's atomics (may be null)
   const int* lin_of_rank;
-  const unsigned char* dirty;
-  unsigned char* dirty_next;
+  unsigned char* collect;  // changed since the last sort (read and cleared)
+  unsigned char* chg;      // changed, for this sort's scatter and reorder
   int* ccur;
   __device__ void operator()(int g, int cnt, int pre) const {
     cstart[g] = pre;
-    const bool changed = dirty[g] != 0;
-    if (changed) ccur[g] = 0;
-    if (dirty_next) dirty_next[g] = 0;
+    const bool changed = collect[g] != 0;
+    chg[g] = changed ? 1 : 0;
+    if (changed) {
+      ccur[g] = 0;
+      collect[g] = 0;
+    }
     int lin = lin_of_rank[g];
     if (lin >= 0) {
       crange[lin] = make_int2(pre, cnt);
@@ -517,13 +572,14 @@ struct CellEpi {
 // cell take positions in atomic order; pass 2 sorts those.
 // ---------------------------------------------------------------------------
 __global__ void k_scatter(Dev d, PState a) {
+  if (gated_off(d.gate)) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= d.N) return;
   const BoxDev& B = d.boxes[d.slot_box[s]];
   if (s - B.pbase >= B.nlive) return;
   const int g = a.cellg[s];
   int pos;
-  if (!d.dirty[g]) {
+  if (!d.chg[g]) {
     pos = d.cstart[g] + (s - d.cstart_old[g]);
   } else {
     const int k = atomicAdd(&d.ccur[g], 1);
@@ -554,6 +610,7 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
   using P = typename T::P;
   using V4 = typename T::V4;
   using PR = typename T::PR;
+  if (gated_off(d.gate)) return;
   const int q = blockIdx.x * blockDim.x + threadIdx.x;  // scatter position
   if (q == 0 && cursor) *cursor = 0;  // the search allocates list entries
   if (q == 0 && d.nlarge) *d.nlarge = 0;  // ... and appends large particles
@@ -569,7 +626,7 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
       const int s = d.perm[q];
       const int g = d.pcell[q];
       lin = d.lin_of_rank[g];
-      const bool changed = d.dirty[g] != 0;
+      const bool changed = d.chg[g] != 0;
       const int key = a.id[s];
       int t = q;  // final slot
       if (changed) {
@@ -588,8 +645,9 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
       st4((V4*)b.vel + t, vel);
       st4((V4*)b.omg + t, om);
       b.id[t] = key;
-      int cc = a.cellx[s];
+      const int cc = a.cellc[s];  // the current cell, kept by the integrator
       b.cellc[t] = cc;
+      b.cellx[t] = cc;            // the cell this sort used
       b.cellg[t] = g;
       if (a.wx) {
         using DT = typename T::DT;
@@ -692,9 +750,12 @@ __device__ __forceinline__ bool pred_fixed(float4 pi, float4 pj, float sx,
 
 // The same rule on the packed FP32x2 path (two lanes of one instruction,
 // each rounded as its scalar counterpart): (dx, dy) = ((x_j, y_j) +
-// (-x_i, -y_i)) + (sx, sy) and (dz, R) = ((z_j, r_j) + (-z_i, r_i)) + (sz, 0),
-// then the squares, (dx^2 + dy^2) + dz^2 < R^2.  a - b is a + (-b) exactly,
-// r_j + r_i = r_i + r_j, and R + 0 = R for R >= 0: bit for bit pred_fixed.
+// (-x_i, -y_i)) + (sx, sy) and (dz, R) = ((z_j, r_j) + (-z_i, r_i)) +
+// (sz, skin), then the squares, (dx^2 + dy^2) + dz^2 < R^2.  a - b is
+// a + (-b) exactly, r_j + r_i = r_i + r_j, and R + 0 = R for R >= 0: with
+// skin = 0 bit for bit pred_fixed; with skin > 0 the reach r_i + r_j + skin
+// of a re-sort's candidate test, which accepts every pair pred_fixed accepts
+// (the same d^2 against a square that is at least as large).
 __device__ __forceinline__ bool pred_fixed_packed(float4 pj, float2 nxy, float2 nzw,
                                                   float2 sxy, float2 sz0) {
   const float2 u = __fadd2_rn(__fadd2_rn(make_float2(pj.x, pj.y), nxy), sxy);
@@ -718,24 +779,27 @@ __device__ __forceinline__ float min_image(float d, const BoxDev& B, int a) {
   }
   return d;
 }
+// absolute-position rule (DEM_FP64, DEM_FP32); skin > 0 widens the reach to
+// r_i + r_j + skin (the candidate test of a re-sort; skin = 0 is the
+// contact rule itself)
 __device__ __forceinline__ bool pred_abs(const d4& pi, const d4& pj,
-                                         const BoxDev& B) {
+                                         const BoxDev& B, float skin = 0.0f) {
   double dx = min_image(__dsub_rn(pj.x, pi.x), B, 0);
   double dy = min_image(__dsub_rn(pj.y, pi.y), B, 1);
   double dz = min_image(__dsub_rn(pj.z, pi.z), B, 2);
   double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)),
                         __dmul_rn(dz, dz));
-  double R = __dadd_rn(pi.w, pj.w);
+  double R = __dadd_rn(__dadd_rn(pi.w, pj.w), (double)skin);
   return d2 < __dmul_rn(R, R);
 }
 __device__ __forceinline__ bool pred_abs(const float4& pi, const float4& pj,
-                                         const BoxDev& B) {
+                                         const BoxDev& B, float skin = 0.0f) {
   float dx = min_image(__fsub_rn(pj.x, pi.x), B, 0);
   float dy = min_image(__fsub_rn(pj.y, pi.y), B, 1);
   float dz = min_image(__fsub_rn(pj.z, pi.z), B, 2);
   float d2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)),
                        __fmul_rn(dz, dz));
-  float R = __fadd_rn(pi.w, pj.w);
+  float R = __fadd_rn(__fadd_rn(pi.w, pj.w), skin);
   return d2 < __fmul_rn(R, R);
 }
 
@@ -840,7 +904,8 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
   // and the loads left are independent of one another.
   // the largest radius a partner can have
   const float rp = kSplit ? fminf(B.rmax_f, B.rsplit_f) : B.rmax_f;
-  const float rb = 1.001f * (ri + rp);
+  const float skin = B.skin_f;
+  const float rb = 1.001f * (ri + rp + skin);
   const float rb2 = rb * rb;
   unsigned keep = 0u;
 #pragma unroll
@@ -870,7 +935,7 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
         const float gap = fmaxf(fmaxf(b_lo[a] + sh[a] - oi[a], oi[a] - (b_hi[a] + sh[a])), 0.0f);
         gb2 += gap * gap;
       }
-      const float reach = 1.001f * (ri + (kSplit ? fminf(blo.w, rp) : blo.w));  // blo.w < 0: empty
+      const float reach = 1.001f * (ri + (kSplit ? fminf(blo.w, rp) : blo.w) + skin);  // blo.w < 0: empty
       if (blo.w >= 0.0f && gb2 <= reach * reach) keep |= 1u << k;
     }
   }
@@ -912,10 +977,10 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
         if (M == kMIXED) {
           const float4& q = *(const float4*)&pi;
           const float2 nxy = make_float2(-q.x, -q.y), nzw = make_float2(-q.z, q.w);
-          const float2 sxy = make_float2(sx, sy), sz0 = make_float2(sz, 0.0f);
+          const float2 sxy = make_float2(sx, sy), sz0 = make_float2(sz, skin);
           h = pred_fixed_packed(*(const float4*)&pu, nxy, nzw, sxy, sz0);
         } else {
-          h = pred_abs(pi, pu, B);
+          h = pred_abs(pi, pu, B, skin);
         }
         hm |= (unsigned)h << u;
         if (kSplit && is_large(pu.w, B.rsplit_f)) hm &= ~(1u << u);
@@ -944,7 +1009,7 @@ __device__ __forceinline__ int search_row(const Dev& d, const PState& b, const B
 // every entry does not), a warp scan places each particle's pairs there,
 // oriented (lower id, higher id), and each entry index also goes into the
 // partner's incoming row at a position taken from its incoming count.
-__device__ __forceinline__ void write_list(const Dev& d, const PState& b, const CList& cn, int i,
+__device__ __forceinline__ void write_list(const Dev& d, const PState& b, const VList& cn, int i,
                                            int own) {
   const int lane = threadIdx.x & 31;
   const int incl = warp_incl_scan(own);
@@ -977,7 +1042,7 @@ __device__ __forceinline__ void write_list(const Dev& d, const PState& b, const 
       const int j = jj[u], c = hs + k + u;
       const int idj = b.id[j];
       cn.pair[c] = idi < idj ? make_int2(i, j) : make_int2(j, i);
-      cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
+      if (cn.hid) cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
       if (pos[u] < K) d.inrow[(size_t)j * K + pos[u]] = make_int2(c, (i << 1) | (idj < idi ? 1 : 0));
     }
   }
@@ -987,7 +1052,8 @@ __device__ __forceinline__ void write_list(const Dev& d, const PState& b, const 
 // here but appended to d.large for k_candidates_large.
 template <int M, bool kSplit>
 __global__ void __launch_bounds__(256, 4)
-k_candidates(Dev d, PState b, CList cn) {
+k_candidates(Dev d, PState b, VList cn) {
+  if (gated_off(d.gate)) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;  // whole warps run
   int own = 0;
   bool live = false, large = false;
@@ -1076,7 +1142,8 @@ __device__ __forceinline__ bool axis_step2(const BoxDev& B, int a, int c, int st
 // atomic per warp) and the partners' incoming rows, five entries at a time.
 template <int M>
 __global__ void __launch_bounds__(256)
-k_candidates_large(Dev d, PState b, CList cn) {
+k_candidates_large(Dev d, PState b, VList cn) {
+  if (gated_off(d.gate)) return;
   using T = Tr<M>;
   using PR = typename T::PR;
   const PR* __restrict__ posr = (const PR*)b.posr;
@@ -1105,7 +1172,8 @@ k_candidates_large(Dev d, PState b, CList cn) {
       else oi[a] = (float)((double)(a == 0 ? pi.x : a == 1 ? pi.y : pi.z) - (double)c[a] * B.h[a]);
     }
     const float ri = (float)pi.w;
-    const float rb = 1.001f * (ri + B.rmax_f);
+    const float skin = B.skin_f;
+    const float rb = 1.001f * (ri + B.rmax_f + skin);
     const float rb2 = rb * rb;
     // Pass 1: keep bit ky 5 + kx of the lane's 25 cells
     unsigned keep = 0u;
@@ -1134,7 +1202,7 @@ k_candidates_large(Dev d, PState b, CList cn) {
           const float gx = fmaxf(fmaxf(blo.x + xsh[kx] - oi[0], oi[0] - (bhi.x + xsh[kx])), 0.0f);
           const float gy = fmaxf(fmaxf(blo.y + shy - oi[1], oi[1] - (bhi.y + shy)), 0.0f);
           const float gz = fmaxf(fmaxf(blo.z + shz - oi[2], oi[2] - (bhi.z + shz)), 0.0f);
-          const float reach = 1.001f * (ri + blo.w);
+          const float reach = 1.001f * (ri + blo.w + skin);
           if (blo.w >= 0.0f && gx * gx + gy * gy + gz * gz <= reach * reach) keep |= 1u << (ky * 5 + kx);
         }
       }
@@ -1180,14 +1248,14 @@ k_candidates_large(Dev d, PState b, CList cn) {
         if (M == kMIXED) {
           const float4& q = *(const float4*)&pi;
           const float2 nxy = make_float2(-q.x, -q.y), nzw = make_float2(-q.z, q.w);
-          const float2 sxy = make_float2(sx, sy), sz0 = make_float2(shz, 0.0f);
+          const float2 sxy = make_float2(sx, sy), sz0 = make_float2(shz, skin);
           hm = (unsigned)pred_fixed_packed(*(const float4*)&p0, nxy, nzw, sxy, sz0) |
                ((unsigned)pred_fixed_packed(*(const float4*)&p1, nxy, nzw, sxy, sz0) << 1) |
                ((unsigned)pred_fixed_packed(*(const float4*)&p2, nxy, nzw, sxy, sz0) << 2) |
                ((unsigned)pred_fixed_packed(*(const float4*)&p3, nxy, nzw, sxy, sz0) << 3);
         } else {
-          hm = (unsigned)pred_abs(pi, p0, B) | ((unsigned)pred_abs(pi, p1, B) << 1) |
-               ((unsigned)pred_abs(pi, p2, B) << 2) | ((unsigned)pred_abs(pi, p3, B) << 3);
+          hm = (unsigned)pred_abs(pi, p0, B, skin) | ((unsigned)pred_abs(pi, p1, B, skin) << 1) |
+               ((unsigned)pred_abs(pi, p2, B, skin) << 2) | ((unsigned)pred_abs(pi, p3, B, skin) << 3);
         }
         hm &= (m >= 4) ? 0xFu : ((1u << m) - 1u);
         // not the particle itself, nor a large partner in an earlier slot
@@ -1236,7 +1304,7 @@ k_candidates_large(Dev d, PState b, CList cn) {
         const int pos = d.inrow ? atomicAdd(d.icnt + j2, 1) : K;
         const int idj = b.id[j2];
         cn.pair[c2] = idi < idj ? make_int2(i, j2) : make_int2(j2, i);
-        cn.hid[c2] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
+        if (cn.hid) cn.hid[c2] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
         if (pos < K) d.inrow[(size_t)j2 * K + pos] = make_int2(c2, (i << 1) | (idj < idi ? 1 : 0));
       }
     }
@@ -1399,11 +1467,17 @@ struct PairOut {
   float ov, ratio;                // overlap / r_min, Coulomb ratio (0 if none)
 };
 
+// The contact law of one listed pair from its tangential history (ox, oy,
+// oz: delta_t after the previous step, zero for a new contact): geometry from
+// the exact positions, Eq. (vt), Eq. (dt), Eq. (1), the Coulomb cap, the new
+// delta_t (a float-float sum in DEM_MIXED unless the cap reset it).  i is the
+// slot of the lower-id particle, j of the higher.  A listed pair whose
+// overlap in the force arithmetic is not positive gets no force and loses
+// its history.
 template <int M>
-__device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
-                                           const CList& co, const BoxDev& B,
-                                           int i, int j, int idlo, int idhi,
-                                           PairOut<M>& out) {
+__device__ __forceinline__ void pair_law(const PState& b, const BoxDev& B, int i, int j,
+                                         typename Tr<M>::DT ox, typename Tr<M>::DT oy,
+                                         typename Tr<M>::DT oz, PairOut<M>& out) {
   using T = Tr<M>;
   using P = typename T::P;
   using R = typename T::R;
@@ -1414,32 +1488,6 @@ __device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
   const P* __restrict__ pz = (const P*)b.pz;
   const V4* __restrict__ vel = (const V4*)b.vel;
   const V4* __restrict__ omg = (const V4*)b.omg;
-  // history of this pair from the previous step's list (the delta_t remap):
-  // the pair is listed, by the slots the two particles had then, in the
-  // block of the one that found it, which may be either; slots move little
-  // from step to step, so these reads stay near this contact's own
-  int found = -1;
-  {
-    const int si = d.prev[i], sj = d.prev[j];
-    const int os1 = co.hs[si], on1 = co.oc[si];
-    const int os2 = co.hs[sj], on2 = co.oc[sj];
-    for (int k = 0; k < on1; ++k) {
-      const int2 h = co.pair[os1 + k];
-      if (h.x == si && h.y == sj) {
-        found = os1 + k;
-        break;
-      }
-    }
-    if (found < 0) {
-      for (int k = 0; k < on2; ++k) {
-        const int2 h = co.pair[os2 + k];
-        if (h.x == si && h.y == sj) {
-          found = os2 + k;
-          break;
-        }
-      }
-    }
-  }
   V4 v1 = ld4(vel + i), v2 = ld4(vel + j);
   V4 w1 = ld4(omg + i), w2 = ld4(omg + j);
   R r1 = w1.w, r2 = w2.w;
@@ -1461,12 +1509,6 @@ __device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
   out.N4 = V4{};
   out.nx = out.ny = out.nz = DT{};
   out.ov = out.ratio = 0.0f;
-  DT ox = {}, oy = {}, oz = {};
-  if (found >= 0) {
-    ox = ((const DT*)co.dx)[found];
-    oy = ((const DT*)co.dy)[found];
-    oz = ((const DT*)co.dz)[found];
-  }
   if (!(dn > R(0))) return;
   v3<R> dold;
   if (M == kMIXED) {
@@ -1516,6 +1558,48 @@ __device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
   out.ratio = (float)o.ratio;
 }
 
+
+// one pair of the per-particle Collide forms: history lookup
+// (InitializeContactIDs) in the previous step's list, then the contact law.
+// i is the slot of the lower-id particle, j of the higher.
+template <int M>
+__device__ __forceinline__ void pair_force(const Dev& d, const PState& b,
+                                           const CList& co, const BoxDev& B,
+                                           int i, int j, PairOut<M>& out) {
+  using DT = typename Tr<M>::DT;
+  // the pair is listed, by the slots the two particles had then, in the
+  // block of the one that found it, which may be either
+  int found = -1;
+  {
+    const int si = d.prev[i], sj = d.prev[j];
+    const int os1 = co.hs[si], on1 = co.oc[si];
+    const int os2 = co.hs[sj], on2 = co.oc[sj];
+    for (int k = 0; k < on1; ++k) {
+      const int2 h = co.pair[os1 + k];
+      if (h.x == si && h.y == sj) {
+        found = os1 + k;
+        break;
+      }
+    }
+    if (found < 0) {
+      for (int k = 0; k < on2; ++k) {
+        const int2 h = co.pair[os2 + k];
+        if (h.x == si && h.y == sj) {
+          found = os2 + k;
+          break;
+        }
+      }
+    }
+  }
+  DT ox = {}, oy = {}, oz = {};
+  if (found >= 0) {
+    ox = ((const DT*)co.dx)[found];
+    oy = ((const DT*)co.dy)[found];
+    oz = ((const DT*)co.dz)[found];
+  }
+  pair_law<M>(b, B, i, j, ox, oy, oz, out);
+}
+
 // warp-level max of the per-box diagnostics held in registers; every lane
 // of the warp must call this
 __device__ __forceinline__ void flush_diag(const Dev& d, int mbox, float m_ov,
@@ -1551,34 +1635,284 @@ __device__ __forceinline__ void track_diag(const Dev& d, int box, float ov,
 }
 
 // ---------------------------------------------------------------------------
-// force: one thread per contact of the dense list
+// contact-list pipeline, every step: the contact rule on each candidate pair
+// from the particles' current cells, then the force of the pairs in contact
 // ---------------------------------------------------------------------------
+
+// Fixed-rule shift of cell cj relative to cell ci along axis a for a pair the
+// cell search tests: the step st, |st| <= w, with wrap(ci + st) = cj (unique:
+// periodic axes have at least 2 w + 1 cells); the shift is that of the
+// search, (float)((cj - ci) H + image L) with image -1 / +1 when the step
+// wraps below 0 / above n - 1.  false when the cells are farther apart: the
+// cell search never tests such a pair.
 template <int M>
-__global__ void __launch_bounds__(256)
-k_force(Dev d, PState b, CList co, CList cn) {
+__device__ __forceinline__ bool pair_shift(const BoxDev& B, int a, int ci, int cj, int w,
+                                           float& sh) {
+  const int n = B.n[a];
+  const int dc = cj - ci;
+  int image = 0;
+  if (dc < -w || dc > w) {
+    if (!B.periodic[a]) return false;
+    if (dc - n >= -w && dc - n <= w) image = -1;
+    else if (dc + n >= -w && dc + n <= w) image = 1;
+    else return false;
+  }
+  if (M == kMIXED) {
+    const long long S = (long long)dc * B.Hq[a] + (long long)image * B.Lq[a];
+    sh = __fmul_rn(i64_to_f32_rn(S), kQ);
+  } else {
+    sh = 0.0f;  // the absolute-position rule needs no shift
+  }
+  return true;
+}
+
+// The contact rule of the cell search (pred_fixed in DEM_MIXED, the
+// absolute-position rule otherwise) on a listed pair, from both particles'
+// current cells and predicate records: the same decision the search takes
+// when it meets the pair (the rule is exactly antisymmetric, so the order of
+// i and j does not matter).
+template <int M>
+__device__ __forceinline__ bool pair_in_contact(const BoxDev& B, const PState& b, int i, int j) {
+  using PR = typename Tr<M>::PR;
+  const int w = B.rsplit_f < INFINITY ? 2 : 1;  // size-binned boxes: +-2 cells
+  int ci[3], cj[3];
+  unpack_cell(b.cellc[i], ci[0], ci[1], ci[2]);
+  unpack_cell(b.cellc[j], cj[0], cj[1], cj[2]);
+  float sh[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (!pair_shift<M>(B, a, ci[a], cj[a], w, sh[a])) return false;
+  const PR pi = ld4((const PR*)b.posr + i), pj = ld4((const PR*)b.posr + j);
+  if (M == kMIXED) return pred_fixed(*(const float4*)&pi, *(const float4*)&pj, sh[0], sh[1], sh[2]);
+  return pred_abs(pi, pj, B);
+}
+
+// One warp takes kPairTile candidates: each lane tests kPairU of them (their
+// loads in flight together), the pairs in contact are compacted by ballot into
+// a warp-local queue in shared memory, and the warp then computes their
+// forces 32 at a time with every lane busy.  A pair that left contact loses
+// its history.  Every output is written at the pair's own list entry.
+constexpr int kPairU = 4;
+constexpr int kPairTile = 32 * kPairU;
+constexpr int kPairWarps = 8;
+
+template <int M>
+__global__ void __launch_bounds__(32 * kPairWarps)
+k_pairs(Dev d, PState b, VList vl) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   using DT = typename T::DT;
-  const int nc = min(*cn.count, d.Cmax);
+  __shared__ int qbuf[kPairWarps][kPairTile];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int* q = qbuf[wi];
+  const int nc = min(*vl.count, d.Cmax);
+  const int nw = gridDim.x * kPairWarps;
   int mbox = -1;
   float m_ov = 0.0f, m_ratio = 0.0f;
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nc;
-       c += gridDim.x * blockDim.x) {
-    const int2 pr = cn.pair[c];
-    const int2 ids = cn.hid[c];
-    const int i = pr.x, j = pr.y;
-    const int box = d.slot_box[i];
-    const BoxDev& B = d.boxes[box];
-    PairOut<M> o;
-    pair_force<M>(d, b, co, B, i, j, ids.x, ids.y, o);
-    ((DT*)cn.dx)[c] = o.nx;
-    ((DT*)cn.dy)[c] = o.ny;
-    ((DT*)cn.dz)[c] = o.nz;
-    st4((V4*)d.Fc + c, o.F4);
-    st4((V4*)d.nFc + c, o.N4);
-    if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
+  for (int t0 = (blockIdx.x * kPairWarps + wi) * kPairTile; t0 < nc; t0 += nw * kPairTile) {
+    int2 pr[kPairU];
+#pragma unroll
+    for (int u = 0; u < kPairU; ++u) {
+      const int c = t0 + u * 32 + lane;
+      pr[u] = c < nc ? vl.pair[c] : make_int2(-1, -1);
+    }
+    int qn = 0;
+#pragma unroll
+    for (int u = 0; u < kPairU; ++u) {
+      const int c = t0 + u * 32 + lane;
+      bool hit = false;
+      if (pr[u].x >= 0) {
+        const BoxDev& B = d.boxes[d.slot_box[pr[u].x]];
+        hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
+        if (!hit && vl.flag[c]) {
+          ((DT*)vl.dx)[c] = DT{};
+          ((DT*)vl.dy)[c] = DT{};
+          ((DT*)vl.dz)[c] = DT{};
+          vl.flag[c] = 0;
+        }
+      }
+      const unsigned bal = __ballot_sync(full, hit);
+      if (hit) q[qn + __popc(bal & lt)] = c;
+      qn += __popc(bal);
+    }
+    __syncwarp();
+    for (int k = 0; k < qn; k += 32) {
+      if (k + lane < qn) {
+        const int c = q[k + lane];
+        const int2 p = vl.pair[c];
+        const int box = d.slot_box[p.x];
+        const BoxDev& B = d.boxes[box];
+        PairOut<M> o;
+        pair_law<M>(b, B, p.x, p.y, ((const DT*)vl.dx)[c], ((const DT*)vl.dy)[c],
+                    ((const DT*)vl.dz)[c], o);
+        ((DT*)vl.dx)[c] = o.nx;
+        ((DT*)vl.dy)[c] = o.ny;
+        ((DT*)vl.dz)[c] = o.nz;
+        vl.flag[c] = 1;
+        st4((V4*)d.Fc + c, o.F4);
+        st4((V4*)d.nFc + c, o.N4);
+        if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
+      }
+    }
+    __syncwarp();
   }
   flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
+}
+
+// ---------------------------------------------------------------------------
+// contact-list pipeline, at a re-sort (after the search wrote the new
+// candidate list vn in the new slot order of b): each slot's row of all its
+// candidate pairs, ordered by partner id (the order of the force sum, which
+// then does not depend on slots, re-sorts or timing), and the history of the
+// pairs it found carried over from the current list vo (old slots, reached
+// through the reorder's previous-slot map).  d.row, free after the search,
+// holds the partner ids while a row is ordered.
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256)
+k_rows(Dev d, PState b, VList vo, VList vn) {
+  if (gated_off(d.gate)) return;
+  using DT = typename Tr<M>::DT;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[i]];
+  if (i - B.pbase >= B.nlive) {
+    d.fcnt[i] = 0;
+    return;
+  }
+  const int K = d.K;
+  const int own = vn.oc[i], hs = vn.hs[i];
+  const int inc = d.icnt[i];
+  if (own + inc > K) flag(d.status, kStRowOverflow);
+  int* kr = d.row + (size_t)i * K;
+  int* vr = d.frow + (size_t)i * K;
+  int n = 0;
+  auto insert = [&](int key, int val) {
+    if (n >= K) return;
+    int pos = n;
+    while (pos > 0 && kr[pos - 1] > key) {
+      kr[pos] = kr[pos - 1];
+      vr[pos] = vr[pos - 1];
+      --pos;
+    }
+    kr[pos] = key;
+    vr[pos] = val;
+    ++n;
+  };
+  for (int k = 0; k < own; ++k) {
+    const int c = hs + k;
+    const int2 pr = vn.pair[c];
+    const bool low = pr.x == i;
+    insert(b.id[low ? pr.y : pr.x], (c << 1) | (low ? 1 : 0));
+    // history: the pair in the current list, in the block of whichever of
+    // its particles found it then
+    const int si = d.prev[pr.x], sj = d.prev[pr.y];
+    int found = -1;
+    for (int u = 0; u < 2 && found < 0; ++u) {
+      const int s0 = u == 0 ? si : sj;
+      const int os = vo.hs[s0], on = vo.oc[s0];
+      for (int e = 0; e < on; ++e) {
+        const int2 h = vo.pair[os + e];
+        if (h.x == si && h.y == sj) {
+          found = os + e;
+          break;
+        }
+      }
+    }
+    if (found >= 0) {
+      ((DT*)vn.dx)[c] = ((const DT*)vo.dx)[found];
+      ((DT*)vn.dy)[c] = ((const DT*)vo.dy)[found];
+      ((DT*)vn.dz)[c] = ((const DT*)vo.dz)[found];
+      vn.flag[c] = vo.flag[found];
+    } else {
+      ((DT*)vn.dx)[c] = DT{};
+      ((DT*)vn.dy)[c] = DT{};
+      ((DT*)vn.dz)[c] = DT{};
+      vn.flag[c] = 0;
+    }
+  }
+  const int ni = min(inc, K);
+  for (int k = 0; k < ni; ++k) {
+    const int2 e = d.inrow[(size_t)i * K + k];
+    insert(b.id[e.y >> 1], (e.x << 1) | (e.y & 1));
+  }
+  d.fcnt[i] = n;
+}
+
+// The re-sorted state b and list vn become the current a and vo (the state
+// stays in one place between re-sorts, where the integrator updates it); the
+// positions of this sort are kept for the skin test, and the new cell starts
+// become the current order's.
+template <int M>
+__global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const int* cs_new,
+                         int* cs_cur) {
+  if (gated_off(d.gate)) return;
+  using T = Tr<M>;
+  using P = typename T::P;
+  using V4 = typename T::V4;
+  using PR = typename T::PR;
+  using DT = typename T::DT;
+  const int nc = min(*vn.count, d.Cmax);
+  const int top = max(max(d.N, nc), d.M_rank);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < top; k += gridDim.x * blockDim.x) {
+    if (k < d.N) {
+      const BoxDev& B = d.boxes[d.slot_box[k]];
+      if (k - B.pbase < B.nlive) {
+        const P x = ((const P*)b.px)[k], y = ((const P*)b.py)[k], z = ((const P*)b.pz)[k];
+        ((P*)a.px)[k] = x;
+        ((P*)a.py)[k] = y;
+        ((P*)a.pz)[k] = z;
+        ((P*)d.xb)[k] = x;
+        ((P*)d.yb)[k] = y;
+        ((P*)d.zb)[k] = z;
+        st4((V4*)a.vel + k, ld4((const V4*)b.vel + k));
+        st4((V4*)a.omg + k, ld4((const V4*)b.omg + k));
+        st4((PR*)a.posr + k, ld4((const PR*)b.posr + k));
+        a.id[k] = b.id[k];
+        a.cellc[k] = b.cellc[k];
+        a.cellx[k] = b.cellx[k];
+        a.cellg[k] = b.cellg[k];
+        if (a.wx) {
+          for (int w = 0; w < d.nwh; ++w) {
+            const size_t h = (size_t)k * d.nwh + w;
+            ((DT*)a.wx)[h] = ((const DT*)b.wx)[h];
+            ((DT*)a.wy)[h] = ((const DT*)b.wy)[h];
+            ((DT*)a.wz)[h] = ((const DT*)b.wz)[h];
+          }
+        }
+      }
+      vo.hs[k] = vn.hs[k];
+      vo.oc[k] = vn.oc[k];
+    }
+    if (k < nc) {
+      vo.pair[k] = vn.pair[k];
+      vo.hid[k] = vn.hid[k];
+      ((DT*)vo.dx)[k] = ((const DT*)vn.dx)[k];
+      ((DT*)vo.dy)[k] = ((const DT*)vn.dy)[k];
+      ((DT*)vo.dz)[k] = ((const DT*)vn.dz)[k];
+      vo.flag[k] = vn.flag[k];
+    }
+    if (k < d.M_rank) cs_cur[k] = cs_new[k];
+    if (k == 0) *vo.count = nc;
+  }
+}
+
+// Whether this step re-sorts: when a particle moved far enough since the
+// last re-sort for a pair outside the candidate list to reach contact (the
+// integrator's skin test), when the host asked for it (new particles,
+// positions or history), or every step when some box keeps no skin.  In a
+// CUDA graph the decision also opens or closes the conditional node that
+// holds the re-sort kernels; launched directly, those kernels read it.
+__global__ void k_decide(unsigned* vctl, int always, cudaGraphConditionalHandle h,
+                         int set_handle) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned r = (always || vctl[kCtlRequest] != 0u) ? 1u : 0u;
+  vctl[kCtlResort] = r;
+  vctl[kCtlRequest] = 0u;
+  vctl[kCtlResorts] += r;
+  if (set_handle) cudaGraphSetConditional(h, r);
 }
 
 // ---------------------------------------------------------------------------
@@ -1630,8 +1964,8 @@ k_collide_per_particle(Dev d, PState b, CList co, CList cn, int ko) {
       const int idj = ids[j];
       const bool lo = idi < idj;
       PairOut<M> o;
-      if (lo) pair_force<M>(d, b, co, B, i, j, idi, idj, o);
-      else pair_force<M>(d, b, co, B, j, i, idj, idi, o);
+      if (lo) pair_force<M>(d, b, co, B, i, j, o);
+      else pair_force<M>(d, b, co, B, j, i, o);
       if (lo) {
         F = F + xyz(o.F4);
         if (own < ko) {
@@ -1866,7 +2200,8 @@ __global__ void k_walls(Dev d, PState b) {
 // then binning for the next step
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
+__global__ void k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag,
+                                   int store_ft) {
   using T = Tr<M>;
   using P = typename T::P;
   using R = typename T::R;
@@ -1879,74 +2214,34 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
   const V4* Fc = (const V4*)d.Fc;
   const V4* nFc = (const V4*)d.nFc;
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
-  const bool fused = d.Ffused != nullptr;
-  int own = fused ? 0 : cn.oc[i], hs = fused ? 0 : cn.hs[i], inc = fused ? 0 : d.icnt[i];
-  // Fc is the force on the pair's lower-id member: added when this slot is
-  // that member, subtracted otherwise; n x F enters with the same sign for
-  // both.  Found contacts are summed in row order, incoming ones in
-  // increasing partner slot (the list entries and the incoming positions
-  // depend on timing; these orders do not).
-  for (int k = 0; k < own; ++k) {
-    const int c = hs + k;
-    if (c >= d.Cmax) break;
-    const V4 f = ld4(Fc + c), q = ld4(nFc + c);
-    if (cn.pair[c].x == i) F = F + xyz(f);
-    else F = F - xyz(f);
-    Ns = Ns + xyz(q);
-  }
-  if (own + inc > d.K) flag(d.status, kStRowOverflow);
-  if (inc > 0) {
-    // contacts found by the partners, in increasing partner slot (one
-    // contact per partner, and unlike the list entries slots do not depend
-    // on timing)
-    const int n = min(inc, d.K);
-    const int2* il = d.inrow + (size_t)i * d.K;
-    if (n <= 4) {
-      // up to four: in registers, sorted by a compare-exchange network on
-      // the partner slot carried in the row
-      int c[4], pk[4];
+  if (!d.Ffused) {
+    // the slot's candidate pairs in increasing partner id, four at a time
+    // (their flags and forces loaded together); Fc is the force on the
+    // pair's lower-id member: added when this slot is that member,
+    // subtracted otherwise; n x F enters with the same sign for both
+    const int nrow = min(d.fcnt[i], d.K);
+    const int* row = d.frow + (size_t)i * d.K;
+    for (int k = 0; k < nrow; k += 4) {
+      const int4 e4 = *(const int4*)(row + k);
+      const int e[4] = {e4.x, e4.y, e4.z, e4.w};
+      unsigned char f[4];
+      V4 fv[4], qv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int2 e = u < n ? il[u] : make_int2(-1, 0x7fffffff);
-        c[u] = e.x;
-        pk[u] = e.y;  // partner slot << 1 | lower-id flag: same order as the slot
-      }
-      auto cx = [&](int a2, int b2) {
-        if (pk[b2] < pk[a2]) {
-          const int tp = pk[a2], tc = c[a2];
-          pk[a2] = pk[b2]; c[a2] = c[b2];
-          pk[b2] = tp; c[b2] = tc;
+        f[u] = 0;
+        if (k + u < nrow) {
+          const int c = e[u] >> 1;
+          f[u] = vl_flag[c];
+          fv[u] = ld4(Fc + c);
+          qv[u] = ld4(nFc + c);
         }
-      };
-      cx(0, 1); cx(2, 3); cx(0, 2); cx(1, 3); cx(1, 2);
+      }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (c[u] < 0) continue;
-        const V4 f = ld4(Fc + c[u]), q = ld4(nFc + c[u]);
-        if (pk[u] & 1) F = F + xyz(f);
-        else F = F - xyz(f);
-        Ns = Ns + xyz(q);
-      }
-    } else {
-      int prev = -1;
-      for (int t = 0; t < n; ++t) {
-        int pbest = 0x7fffffff, cb = -1;
-        for (int u = 0; u < n; ++u) {
-          const int2 e = il[u];
-          if (e.y > prev && e.y < pbest) {
-            pbest = e.y;
-            cb = e.x;
-          }
-        }
-        if (cb < 0 || cb >= d.Cmax) {
-          flag(d.status, kStInconsistent);
-          break;
-        }
-        prev = pbest;
-        const V4 f = ld4(Fc + cb), q = ld4(nFc + cb);
-        if (pbest & 1) F = F + xyz(f);
-        else F = F - xyz(f);
-        Ns = Ns + xyz(q);
+        if (!f[u]) continue;
+        if (e[u] & 1) F = F + xyz(fv[u]);
+        else F = F - xyz(fv[u]);
+        Ns = Ns + xyz(qv[u]);
       }
     }
   }
@@ -2056,7 +2351,60 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
   ((P*)b.py)[i] = p[1];
   ((P*)b.pz)[i] = p[2];
   const int cnew = pack_cell(c[0], c[1], c[2]);
-  b.cellx[i] = cnew;
+  b.cellc[i] = cnew;
+  // the contact rule's record for the next step: offset from the new cell's
+  // origin (DEM_MIXED, rounded as the sort rounds it) or the position, and r
+  {
+    using PR = typename T::PR;
+    PR pr;
+    if (M == kMIXED) {
+      pr.x = __fmul_rn(i64_to_f32_rn((long long)p[0] - (long long)c[0] * B.Hq[0]), kQ);
+      pr.y = __fmul_rn(i64_to_f32_rn((long long)p[1] - (long long)c[1] * B.Hq[1]), kQ);
+      pr.z = __fmul_rn(i64_to_f32_rn((long long)p[2] - (long long)c[2] * B.Hq[2]), kQ);
+    } else {
+      pr.x = p[0];
+      pr.y = p[1];
+      pr.z = p[2];
+    }
+    pr.w = wr.w;
+    st4((PR*)b.posr + i, pr);
+  }
+  // skin test: a particle displaced more than the box's limit since the last
+  // re-sort asks for the next one (the squared displacement rounded up)
+  if (d.xb && B.disp2_lim >= 0.0f) {
+    float d2;
+    if (M == kMIXED) {
+      const long long* xb3[3] = {(const long long*)d.xb, (const long long*)d.yb,
+                                 (const long long*)d.zb};
+      float acc = 0.0f;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        long long D = (long long)p[a] - xb3[a][i];
+        if (B.periodic[a]) {
+          const long long L = B.Lq[a], h = L >> 1;
+          if (D > h) D -= L;
+          else if (D < -h) D += L;
+        }
+        const float f = __fmul_rn(i64_to_f32_rn(D), kQ);
+        acc = __fmaf_ru(f, f, acc);
+      }
+      d2 = __fmul_ru(acc, 1.000001f);
+    } else {
+      const P* xb3[3] = {(const P*)d.xb, (const P*)d.yb, (const P*)d.zb};
+      double acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        double D = (double)p[a] - (double)xb3[a][i];
+        if (B.periodic[a]) {
+          if (D > B.half_L[a]) D -= B.L[a];
+          else if (D < -B.half_L[a]) D += B.L[a];
+        }
+        acc += D * D;
+      }
+      d2 = __fmul_ru(__double2float_ru(acc), 1.000001f);
+    }
+    if (d2 > B.disp2_lim) d.vctl[kCtlRequest] = 1u;
+  }
   if (cnew != cc) {
     // moved to another cell: counts and the changed-cell flags of both
     const int g0 = b.cellg[i];
@@ -2064,8 +2412,8 @@ __global__ void k_gather_integrate(Dev d, PState b, CList cn, int store_ft) {
     b.cellg[i] = g;
     atomicSub(&d.ccount[g0], 1);
     atomicAdd(&d.ccount[g], 1);
-    d.dirty_next[g0] = 1;
-    d.dirty_next[g] = 1;
+    d.collect[g0] = 1;
+    d.collect[g] = 1;
   }
 }
 
@@ -2127,7 +2475,7 @@ __global__ void k_get_order(Dev d, PState b, int box, int* id_by_slot,
   if (id_by_slot) id_by_slot[t] = b.id[slot] - B.pbase;
   if (cell_by_slot) {
     int cx, cy, cz;
-    unpack_cell(b.cellc[slot], cx, cy, cz);
+    unpack_cell(b.cellx[slot], cx, cy, cz);
     cell_by_slot[t] = (cz * B.n[1] + cy) * B.n[0] + cx;
   }
 }
@@ -2137,7 +2485,8 @@ __global__ void k_get_order(Dev d, PState b, int box, int* id_by_slot,
 // slots into part[block][6]; k_stats_final adds the parts in block order
 // (a fixed order: the result does not depend on timing).
 template <int M>
-__global__ void k_stats(Dev d, PState b, const int* oc, int box, double* part) {
+__global__ void k_stats(Dev d, PState b, const int* hs, const int* oc,
+                        const unsigned char* flag, int box, double* part) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   const BoxDev& B = d.boxes[box];
@@ -2155,7 +2504,13 @@ __global__ void k_stats(Dev d, PState b, const int* oc, int box, double* part) {
     acc[2] += m * vx;
     acc[3] += m * vy;
     acc[4] += m * vz;
-    acc[5] += (double)oc[s];
+    if (flag) {  // candidate list: the pairs in contact in the last step
+      int nin = 0;
+      for (int k = 0; k < oc[s]; ++k) nin += flag[hs[s] + k] ? 1 : 0;
+      acc[5] += (double)nin;
+    } else {
+      acc[5] += (double)oc[s];
+    }
   }
   __shared__ double sh[6][256];
   for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = acc[q];

@@ -65,6 +65,7 @@ class Box:
     walls: tuple = ()        # (kind, p, u, v): 0 = rectangle, 1 = line
     r_split: float = 0.0     # size-binned search: radius above which a
                              # particle searches +-2 cells (0 = off)
+    skin: float = 0.0        # candidate-list skin [m] (0 = search every step)
 
     @property
     def n(self) -> int:

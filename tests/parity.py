@@ -21,15 +21,15 @@ Two force tolerances are checked per contact c (oracle values):
         terms of Eq. (vt))
   f_c = 1e-9 k_n R*^1.5  (absolute floor)
 
-with rtol = 1e-5 for FP32 force arithmetic and 1e-9 for FP64.  The term
-bound holds for every contact.  The force-relative bound holds for every
-contact whose condition number kappa_c = S_c / |F_ora| is at most KAPPA_MAX:
-there an error of a few units of FP32 rounding in each term stays below
-rtol |F|.  Above it the terms of Eq. (1) cancel (a rolling contact, whose
-translational and rotational parts of v_t nearly cancel, or a force near
-zero at the end of a contact), and a one-ulp change of the FP32 inputs
-already moves the FP64 oracle's own force by more than rtol |F|
-(``oracle_sensitivity``); those contacts are counted and reported.
+with rtol = 1e-5 for FP32 force arithmetic and 1e-9 for FP64.  Both bounds
+are asserted on every contact.  The contacts whose condition number
+kappa_c = S_c / |F_ora| exceeds KAPPA_MAX are counted and reported: there the
+terms of Eq. (1) cancel (a rolling contact, whose translational and
+rotational parts of v_t nearly cancel, or a force near zero at the end of a
+contact), an error of a few units of FP32 rounding in each term can exceed
+rtol |F|, and a one-ulp change of the FP32 inputs can move the FP64
+oracle's own force by as much (``oracle_sensitivity``,
+``conditioning_report``).
 
 Contacts whose Coulomb ratio lies within 1e-4 of 1 may be capped on one side
 only, and contacts with an overlap below 1e-15 R* / rtol are below what an
@@ -65,7 +65,8 @@ def oracle_params(box, precision, ncell, brute_force=0, stencil=STENCIL):
 
 def gpu_run(boxes, precision, ncells, steps=1, stencil=STENCIL, **kw):
     """Create a context for ``boxes``, set particles, run ``steps`` steps
-    and collect everything per box."""
+    and collect everything per box (and the re-sort statistics under
+    "resorts")."""
     import paper_1503_03553_gb300 as D
 
     assert stencil == 1, "the library searches +-1 neighbour cells"
@@ -81,21 +82,28 @@ def gpu_run(boxes, precision, ncells, steps=1, stencil=STENCIL, **kw):
             flo, fhi, F, nF = ctx.contact_forces(k)
             order, cells = ctx.order(k)
             out.append(dict(state=st, lo=lo, hi=hi, dt=dt, flo=flo, fhi=fhi, Fc=F,
-                            nFc=nF, order=order, cells=cells, stats=ctx.stats(k)))
+                            nFc=nF, order=order, cells=cells, stats=ctx.stats(k),
+                            resorts=ctx.resort_stats()))
         return out
     finally:
         ctx.close()
 
 
-def oracle_run(box, precision, ncell, stencil=STENCIL):
+def oracle_run(box, precision, ncell, stencil=STENCIL, hist=None):
+    """One oracle step from box's state; hist = (id_lo, id_hi, delta_t) is
+    the contact history to start from (none: a fresh start)."""
     p = oracle_params(box, precision, ncell, stencil=stencil)
     cell, order = O.order(p, box.x)
     s = O.State(box.x, box.v, box.w, box.r, floor_wall=bool(box.floor_wall),
                 nwalls=len(getattr(box, "walls", ())))
+    if hist is not None:
+        s.lo, s.hi, s.dt = hist
     x0, v0, w0 = s.x.copy(), s.v.copy(), s.w.copy()
     out = O.step(p, s)
     out.update(order=order, cell=cell, x=s.x, v=s.v, w=s.w, x0=x0, v0=v0, w0=w0,
                params=p)
+    if hist is not None:
+        out["hist"] = hist
     return out
 
 
@@ -126,13 +134,17 @@ def _explain(box, g, o, idx):
     return "\n".join(lines)
 
 
-def check_one_step(box, g, o, precision, allow_dont_care=True):
-    """Compare one step; returns a metrics dict, raises AssertionError."""
+def check_one_step(box, g, o, precision, allow_dont_care=True, check_order=True):
+    """Compare one step; returns a metrics dict, raises AssertionError.
+    check_order=False skips the sort order and cells (a step of the
+    candidate-list pipeline that did not re-sort keeps the order of the
+    last re-sort)."""
     rtol = RTOL[precision]
     m = {}
     # 1. sort order and contact set: bit-exact
-    assert np.array_equal(g["order"], o["order"]), "sort order differs"
-    assert np.array_equal(g["cells"], o["cell"][o["order"]]), "cells differ"
+    if check_order:
+        assert np.array_equal(g["order"], o["order"]), "sort order differs"
+        assert np.array_equal(g["cells"], o["cell"][o["order"]]), "cells differ"
     assert np.array_equal(g["lo"], o["lo"]) and np.array_equal(g["hi"], o["hi"]), (
         f"contact sets differ: gpu {len(g['lo'])} oracle {len(o['lo'])}")
     assert np.array_equal(g["flo"], o["lo"]) and np.array_equal(g["fhi"], o["hi"])
@@ -175,12 +187,13 @@ def check_one_step(box, g, o, precision, allow_dont_care=True):
         m["F_rel_bound_exceeded"] = int(over.sum())
         m["ill_conditioned"] = int((ok & ~well).sum())
         if precision != "fp32":
-            bad = well & (eF > bN)
+            bad = ok & (eF > bN)
             assert not np.any(bad), (
-                f"{int(bad.sum())} well-conditioned contacts outside rtol |F| + floor; worst "
-                f"{float(np.max((eF / bN)[well])):.3g} x bound\n" + _explain(box, g, o, np.where(bad)[0][:6]))
-            bad = well & (enF > bN)
-            assert not np.any(bad), f"{int(bad.sum())} well-conditioned n x F outside rtol |F| + floor"
+                f"{int(bad.sum())} contacts outside rtol |F| + floor ({int((bad & well).sum())} of "
+                f"them well-conditioned); worst {float(np.max((eF / bN)[ok])):.3g} x bound\n"
+                + _explain(box, g, o, np.where(bad)[0][:6]))
+            bad = ok & (enF > bN)
+            assert not np.any(bad), f"{int(bad.sum())} n x F outside rtol |F| + floor"
         # tangential history after the step
         lo, hi = o["lo"], o["hi"]
         v0, w0, r = o["v0"], o["w0"], box.r
@@ -220,14 +233,17 @@ def check_one_step(box, g, o, precision, allow_dont_care=True):
         if box.floor_wall or len(getattr(box, "walls", ())):
             sF += 1e-5 * np.linalg.norm(o["F"], axis=1) + 1e-5 * mass * gmag
         cold = np.zeros(n, bool)
-        notwell = ~(ok & (kappa <= KAPPA_MAX))
+        notwell = ok & (kappa > KAPPA_MAX)
         cold[o["lo"][notwell]] = True
         cold[o["hi"][notwell]] = True
-        m["particle_F_rel_bound_max"] = float(np.max((eP / sF)[~cold], initial=0))
+        dpart = np.zeros(n, bool)  # particles with a "don't care" contact
+        dpart[o["lo"][dont]] = True
+        dpart[o["hi"][dont]] = True
+        m["particle_F_rel_bound_max"] = float(np.max((eP / sF)[~dpart], initial=0))
         m["particles_with_ill_conditioned_contacts"] = int(cold.sum())
         if precision != "fp32":
-            assert np.all(eP[~cold] <= sF[~cold]), (
-                f"{int((eP[~cold] > sF[~cold]).sum())} particle forces outside rtol sum|F| + floors")
+            assert np.all(eP[~dpart] <= sF[~dpart]), (
+                f"{int((eP[~dpart] > sF[~dpart]).sum())} particle forces outside rtol sum|F| + floors")
     eT = np.linalg.norm(g["state"]["T"] - o["T"], axis=1)
     assert np.all(eT <= box.r * (bP + 1e-6 * np.linalg.norm(o["F"], axis=1)) * 2 + 1e-300), "torques"
     m["max_particle_F_err_over_bound"] = float(np.max(eP / bP))

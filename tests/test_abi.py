@@ -31,8 +31,12 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_abi_version(lib):
+    """The library reports the version the header defines."""
+    import re
     import paper_1503_03553_gb300 as D
-    assert D.dem_abi_version() == 3
+    hdr = open(os.path.join(ROOT, "include", "dem.h")).read()
+    want = int(re.search(r"#define DEM_ABI_VERSION (\d+)", hdr).group(1))
+    assert D.dem_abi_version() == want == D.ABI_VERSION
 
 
 @pytest.mark.parametrize("eps", [0.3, 0.5, 0.9, 0.99])
