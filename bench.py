@@ -264,63 +264,88 @@ def _time_steps(ctx, torch, steps, world):
     return e0.elapsed_time(e1) / 1e3
 
 
-def _oracle_rate(box, seconds, max_steps=3):
-    """Time the FP64 oracle on this machine for about `seconds` (>= 1 step).
+def _cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo), for the record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return None
+
+
+def _oracle_threads():
+    return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
+
+
+def _oracle_rate(box, seconds, max_steps=3, parallel=False, min_steps=1):
+    """Time the FP64 oracle on this machine: steps 1..k from the box's state,
+    k between min_steps and max_steps, stopping once `seconds` have passed.
+    parallel=True runs its OpenMP build on all host cores.
     Returns (particle-steps/s, steps, seconds)."""
     import oracle as O
     sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from parity import oracle_params, grid_for
+    from parity import oracle_params
+    from paper_1503_03553_gb300.synth import grid_for
     p = oracle_params(box, "mixed", grid_for(box))
     O.alpha(box.restitution)  # restitution solve outside the timed region
+    O.lib(parallel)           # library load outside the timed region
     s = O.State(box.x, box.v, box.w, box.r)
     t0 = time.perf_counter()
     k = 0
     while True:
-        O.step(p, s)
+        O.step(p, s, parallel=parallel)
         k += 1
         dt = time.perf_counter() - t0
-        if dt >= seconds or k >= max_steps:
+        if k >= max_steps or (k >= min_steps and dt >= seconds):
             break
     return box.n * k / dt, k, dt
 
 
 def run_reference(args):
-    """The FP64 CPU oracle as the reference arm.  Each step is one oracle
-    step of a periodic box drawn from the same workload definition, sized so
-    that warm-up plus timed steps take about two minutes on one host core."""
+    """The FP64 CPU oracle as the reference arm, on all host cores (its
+    OpenMP build: the serial oracle's results bit for bit), on the GPU arm's
+    workload: the same W2 box of args.n particles, steps 1..K from its initial
+    state after W warm-up steps.  When W + K steps of the full box would not
+    end within about three minutes, each step is a sample: a periodic box of
+    the same law (8,000-particle relaxed tiles) sized to fit."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import oracle as O
     from paper_1503_03553_gb300 import synth
     sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from parity import oracle_params, grid_for, prepared
-    calib = prepared(synth.w2_polydisperse(n=8000, seed=2), "mixed")
-    p = oracle_params(calib, "mixed", grid_for(calib))
-    O.alpha(calib.restitution)
-    s = O.State(calib.x, calib.v, calib.w, calib.r)
-    t0 = time.perf_counter()
-    O.step(p, s)
-    rate = calib.n / (time.perf_counter() - t0)
-    n_s = int(0.6 * rate * 120.0 / max(1, args.steps + args.warmup))
-    n_s = max(500, min(n_s, 1_000_000))
-    if n_s >= 64000:
-        k = int((n_s / 8000) ** (1.0 / 3.0))
-        box = synth.w2_polydisperse(n=8000 * k ** 3, seed=2, tile_n=8000)
-        what = f"{k}^3 relaxed 8000-particle tiles"
+    from parity import oracle_params
+    from paper_1503_03553_gb300.synth import grid_for, prepared
+    threads = _oracle_threads()
+    full = prepared(synth.w2_polydisperse(n=args.n, seed=2), "mixed")
+    rate1, _, _ = _oracle_rate(full, 0.0, max_steps=1, parallel=True)
+    budget = 180.0
+    n_s = int(min(full.n, 0.8 * rate1 * budget / max(1, args.steps + args.warmup)))
+    if n_s >= full.n:
+        box, what, same = full, "the full workload", True
     else:
-        box = synth.w2_polydisperse(n=n_s, seed=2, tile_n=max(n_s, 8000))
-        what = "one relaxed periodic box"
-    box = prepared(box, "mixed")
+        k = max(1, int((n_s / 8000) ** (1.0 / 3.0)))
+        box = prepared(synth.w2_polydisperse(n=8000 * k ** 3, seed=2, tile_n=8000), "mixed")
+        what, same = f"a sample: {k}^3 relaxed 8000-particle tiles of the same law", False
     p = oracle_params(box, "mixed", grid_for(box))
     s = O.State(box.x, box.v, box.w, box.r)
     for _ in range(args.warmup):
-        O.step(p, s)
+        O.step(p, s, parallel=True)
     # steps 1..K from the initial state, as the GPU arm times them
     s = O.State(box.x, box.v, box.w, box.r)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        O.step(p, s)
+        O.step(p, s, parallel=True)
     dt = time.perf_counter() - t0
     value = box.n * args.steps / dt
     line = {
@@ -329,11 +354,13 @@ def run_reference(args):
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generator)",
-        "config": {"workload": f"W2 polydisperse periodic box, {box.n} particles ({what}; "
-                   "same radius law, packing and overlaps as the 1,000,000-particle workload)",
-                   "n": box.n},
-        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} timed oracle steps of {box.n} particles"},
+        "config": {"workload": f"W2 polydisperse periodic box, {box.n} particles ({what}); "
+                   "steps 1..K from the initial state",
+                   "n": box.n, "same_workload_as_gpu_arm": same},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": threads, "kind": "oracle",
+                         "cpu_model": _cpu_model(),
+                         "sample": f"{args.steps} timed oracle steps of {box.n} particles "
+                                   f"({what}), OpenMP build on {threads} threads"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -458,10 +485,17 @@ def main():
     cpu = None
     if rank == 0 and not args.no_compare:
         compare = _side_legs(args, D, torch, box, ncell, stream, skin)
-        rate, k, dt = _oracle_rate(box, args.cpu_seconds, max_steps=1)
-        cpu = {"value": rate, "unit": METRIC, "cores": 1, "kind": "oracle",
-               "sample": f"{k} oracle step(s) of the full {n}-particle workload, "
-                         f"one host thread, {dt:.1f} s"}
+        threads = _oracle_threads()
+        rate, k, dt = _oracle_rate(box, args.cpu_seconds, max_steps=10, min_steps=10,
+                                   parallel=True)
+        rate1, k1, dt1 = _oracle_rate(box, 0.0, max_steps=1)
+        cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
+               "cpu_model": _cpu_model(),
+               "sample": f"steps 1..{k} of the full {n}-particle workload, the oracle's "
+                         f"OpenMP build on {threads} host threads, {dt:.1f} s",
+               "single_thread": {"value": rate1, "unit": METRIC, "cores": 1,
+                                 "sample": f"step 1 of the same workload, one host thread, "
+                                           f"{dt1:.1f} s"}}
     if rank != 0:
         return
     line = {
@@ -539,8 +573,7 @@ def _side_legs(args, D, torch, box, ncell, stream, skin):
     leg("mixed_gpu_search_every_step", lambda: _throughput(D, torch, stream, [box], "mixed",
                                                            [ncell], args.steps, skins=[0.0]))
     leg("force_error_vs_fp64_oracle", lambda: _error_leg(out, box, ncell))
-    leg("collide_fused_vs_compact", lambda: _fused_leg(args, D, torch, stream, box,
-                                                       _grid_no_skin(box)))
+    leg("collide_fused_vs_compact", lambda: _fused_leg(args, D, torch, stream, box))
     leg("size_binned_search", lambda: _size_binned_leg(args, D, torch, stream, box, ncell))
     leg("fig4_kernel_times_131k", lambda: _fig4_leg(args, D, torch, stream))
     if not args.no_batched:
@@ -552,11 +585,6 @@ def _side_legs(args, D, torch, box, ncell, stream, skin):
     if args.sweep:
         leg("n_sweep", lambda: _sweep_leg(args, D, torch, stream))
     return out
-
-
-def _grid_no_skin(box):
-    from paper_1503_03553_gb300.synth import grid_for
-    return grid_for(box)
 
 
 def _error_leg(out, box, ncell):
@@ -716,7 +744,7 @@ def _phase_ms(D, torch, stream, boxes, precision, ncells, steps, **kw):
         ctx.close()
 
 
-def _fused_leg(args, D, torch, stream, box, ncell):
+def _fused_leg(args, D, torch, stream, box):
     """The paper's comparison on this workload.  Its two per-particle Collide
     forms: Algorithm 1 as printed (search and force fused, each force as soon
     as its contact is found) and its improvement (Sec. 3.4: a first loop keeps
@@ -724,6 +752,8 @@ def _fused_leg(args, D, torch, stream, box, ncell):
     pipeline here (search, dense contact list, one thread per contact).
     'collide' is the contact part of the step: the per-particle kernel vs
     search + list + force."""
+    from paper_1503_03553_gb300.synth import grid_for
+    ncell = grid_for(box)  # the per-particle forms search every step: finest grid
     steps = args.steps
     out = {}
     coll = {}

@@ -76,13 +76,14 @@ INFO_DTYPE = np.dtype([("F", "<f8", 3), ("nF", "<f8", 3), ("n", "<f8", 3),
                        ("pad", "<i4")])
 assert INFO_DTYPE.itemsize == C.sizeof(ContactInfo)
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+def lib(parallel: bool = False):
+    """The serial oracle library, or its OpenMP build (same results, all
+    host cores) with parallel=True."""
+    if parallel not in _libs:
+        path = _build.build(parallel=parallel)
         L = C.CDLL(path)
         dp = C.POINTER(C.c_double)
         ip = C.POINTER(C.c_int32)
@@ -102,8 +103,8 @@ def lib():
                                C.c_int64, ip, ip, dp, dp,
                                C.c_int64, C.POINTER(C.c_int64), ip, ip, dp,
                                C.c_void_p, dp, dp]
-        _lib = L
-    return _lib
+        _libs[parallel] = L
+    return _libs[parallel]
 
 
 def make_params(L, dt, E=3e9, poisson=0.3, density=1200.0, restitution=0.5,
@@ -186,14 +187,15 @@ def order(p: Params, x: np.ndarray):
     return cell, order
 
 
-def contacts(p: Params, x: np.ndarray, r: np.ndarray, cap: int | None = None):
+def contacts(p: Params, x: np.ndarray, r: np.ndarray, cap: int | None = None,
+             parallel: bool = False):
     x = np.ascontiguousarray(x, dtype=np.float64)
     r = np.ascontiguousarray(r, dtype=np.float64)
     n = x.shape[0]
     cap = cap or max(64, 32 * n)
     lo = np.zeros(cap, np.int32)
     hi = np.zeros(cap, np.int32)
-    cnt = lib().orc_contacts(C.byref(p), n, _d(x), _d(r), cap, _i(lo), _i(hi))
+    cnt = lib(parallel).orc_contacts(C.byref(p), n, _d(x), _d(r), cap, _i(lo), _i(hi))
     if cnt < 0:
         raise RuntimeError(f"orc_contacts failed ({cnt})")
     return lo[:cnt].copy(), hi[:cnt].copy()
@@ -220,9 +222,10 @@ class State:
         return self.x.shape[0]
 
 
-def step(p: Params, s: State, cap: int | None = None):
+def step(p: Params, s: State, cap: int | None = None, parallel: bool = False):
     """Advance ``s`` by one step in place.  Returns a dict with the forces
-    and torques used in the step and per-contact info of the new list."""
+    and torques used in the step and per-contact info of the new list.
+    parallel=True runs the OpenMP build (same results, bit for bit)."""
     n = s.n
     cap = cap or max(64, 32 * n)
     lo = np.zeros(cap, np.int32)
@@ -243,7 +246,7 @@ def step(p: Params, s: State, cap: int | None = None):
     else:
         n_in = s.lo.size
     wall = s.wall_dt
-    rc = lib().orc_step(C.byref(p), n, _d(s.x), _d(s.v), _d(s.w), _d(s.r),
+    rc = lib(parallel).orc_step(C.byref(p), n, _d(s.x), _d(s.v), _d(s.w), _d(s.r),
                         n_in, _i(lo_in), _i(hi_in), _d(dt_in),
                         _d(wall) if wall is not None else None,
                         cap, C.byref(nc), _i(lo), _i(hi), _d(dto),

@@ -8,14 +8,23 @@
  * every product and sum separately, exactly as written.
  *
  * Each function names the passage of Nakahara & Washizawa (arXiv 1503.03553)
- * it follows.  Readings of passages that the paper leaves open are marked
- * "Reading:"; every one of them is listed in the design notes.
+ * it follows.  Where the paper leaves a passage open, the comment states the
+ * reading taken.
+ *
+ * Built with -fopenmp -DORC_OPENMP (liboracle_omp.so) the particle and pair
+ * loops run on all host cores: each particle's contacts are found in the
+ * serial order, each pair's force is computed on its own, and each
+ * particle's contributions are added in the serial order (ascending pair
+ * index), so the results are bit for bit those of the serial build.
  */
 #include "dem_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef ORC_OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -441,6 +450,54 @@ static int cmp_pair(const void* a, const void* b) {
   return (x->hi > y->hi) - (x->hi < y->hi);
 }
 
+/* The contacts (i, j), j > i, of particle i found through the linked cells
+ * (Sec. 2, last paragraph: the neighbour cells of i's cell), in the order of
+ * the neighbour cells (dz, dy, dx) and of each cell's list; up to lim of
+ * them are written to out (out may be NULL).  Returns how many there are. */
+static int64_t scan_particle(const orc_params* p, const pred_data* pd, const double* x,
+                             const double* r, const int64_t* head, const int64_t* next,
+                             int64_t i, pair32* out, int64_t lim) {
+  int32_t nx = p->ncell[0], ny = p->ncell[1];
+  const int32_t* cc = pd->cc;
+  int64_t nb[125], j, got = 0;
+  int nnb = 0, dx, dy, dz, q;
+  const int w = stencil_of(p);
+  /* distinct neighbour cells (a periodic axis with few cells repeats) */
+  for (dz = -w; dz <= w; ++dz)
+    for (dy = -w; dy <= w; ++dy)
+      for (dx = -w; dx <= w; ++dx) {
+        int32_t c[3];
+        int d[3], a, ok = 1, seen = 0;
+        int64_t lin;
+        d[0] = dx; d[1] = dy; d[2] = dz;
+        for (a = 0; a < 3; ++a) {
+          int32_t v = cc[3 * i + a] + d[a];
+          if (v < 0 || v >= p->ncell[a]) {
+            if (!p->periodic[a]) { ok = 0; break; }
+            v = ((v % p->ncell[a]) + p->ncell[a]) % p->ncell[a];
+          }
+          c[a] = v;
+        }
+        if (!ok) continue;
+        lin = ((int64_t)c[2] * ny + c[1]) * nx + c[0];
+        for (q = 0; q < nnb; ++q) if (nb[q] == lin) seen = 1;
+        if (!seen) nb[nnb++] = lin;
+      }
+  for (q = 0; q < nnb; ++q) {
+    for (j = head[nb[q]]; j >= 0; j = next[j]) {
+      if (j <= i) continue;
+      if (is_contact(p, pd, x, r, i, j)) {
+        if (out && got < lim) {
+          out[got].lo = (int32_t)i;
+          out[got].hi = (int32_t)j;
+        }
+        ++got;
+      }
+    }
+  }
+  return got;
+}
+
 static int64_t find_pairs(const orc_params* p, int64_t n, const double* x,
                           const double* r, int64_t cap, pair32* out) {
   int64_t cnt = 0, i, j;
@@ -469,43 +526,30 @@ static int64_t find_pairs(const orc_params* p, int64_t n, const double* x,
       next[i] = head[lin];
       head[lin] = i;
     }
-    for (i = 0; i < n; ++i) {
-      int64_t nb[125];
-      int nnb = 0, dx, dy, dz, q;
-      const int w = stencil_of(p);
-      /* distinct neighbour cells (a periodic axis with few cells repeats) */
-      for (dz = -w; dz <= w; ++dz)
-        for (dy = -w; dy <= w; ++dy)
-          for (dx = -w; dx <= w; ++dx) {
-            int32_t c[3];
-            int d[3], a, ok = 1, seen = 0;
-            int64_t lin;
-            d[0] = dx; d[1] = dy; d[2] = dz;
-            for (a = 0; a < 3; ++a) {
-              int32_t v = cc[3 * i + a] + d[a];
-              if (v < 0 || v >= p->ncell[a]) {
-                if (!p->periodic[a]) { ok = 0; break; }
-                v = ((v % p->ncell[a]) + p->ncell[a]) % p->ncell[a];
-              }
-              c[a] = v;
-            }
-            if (!ok) continue;
-            lin = ((int64_t)c[2] * ny + c[1]) * nx + c[0];
-            for (q = 0; q < nnb; ++q) if (nb[q] == lin) seen = 1;
-            if (!seen) nb[nnb++] = lin;
-          }
-      for (q = 0; q < nnb; ++q) {
-        for (j = head[nb[q]]; j >= 0; j = next[j]) {
-          if (j <= i) continue;
-          if (is_contact(p, &pd, x, r, i, j)) {
-            if (cnt >= cap) { free(head); free(next); pred_free(&pd); return -1; }
-            out[cnt].lo = (int32_t)i;
-            out[cnt].hi = (int32_t)j;
-            ++cnt;
-          }
-        }
-      }
+#ifdef ORC_OPENMP
+    {
+      /* count each particle's contacts, then write them at the serial
+       * positions (the same order as the loop below) */
+      int64_t* off = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+      if (!off) { free(head); free(next); pred_free(&pd); return -2; }
+#pragma omp parallel for schedule(dynamic, 256)
+      for (i = 0; i < n; ++i)
+        off[i + 1] = scan_particle(p, &pd, x, r, head, next, i, NULL, 0);
+      for (i = 0; i < n; ++i) off[i + 1] += off[i];
+      cnt = off[n];
+      if (cnt > cap) { free(off); free(head); free(next); pred_free(&pd); return -1; }
+#pragma omp parallel for schedule(dynamic, 256)
+      for (i = 0; i < n; ++i)
+        scan_particle(p, &pd, x, r, head, next, i, out + off[i], off[i + 1] - off[i]);
+      free(off);
     }
+#else
+    for (i = 0; i < n; ++i) {
+      int64_t got = scan_particle(p, &pd, x, r, head, next, i, out + cnt, cap - cnt);
+      if (got > cap - cnt) { free(head); free(next); pred_free(&pd); return -1; }
+      cnt += got;
+    }
+#endif
     free(head);
     free(next);
   }
@@ -572,6 +616,36 @@ static double wrap(double x, double L) {
   return x;
 }
 
+/* One pair (1 = lower id): geometry with the minimum image on periodic axes,
+ * n from 1 to 2 and the overlap dn = r1 + r2 - |d| (Sec. 2), the history of
+ * the pair (zero for a new contact, Sec. 4.2 InitializeContactIDs) and the
+ * contact law; dtn receives the new delta_t. */
+static void pair_force(const orc_params* p, double alpha, const double* x, const double* v,
+                       const double* w, const double* r, int64_t nc_in, const int32_t* lo_in,
+                       const int32_t* hi_in, const double* dt_in, int32_t i1, int32_t i2,
+                       double dtn[3], orc_contact_info* ci) {
+  double d[3], nrm[3], dist, dn, m1, m2, dto[3] = {0.0, 0.0, 0.0};
+  int64_t h;
+  int a;
+  for (a = 0; a < 3; ++a) {
+    d[a] = x[3 * i2 + a] - x[3 * i1 + a];
+    if (p->periodic[a]) {
+      double hl = 0.5 * p->L[a];
+      if (d[a] > hl) d[a] -= p->L[a];
+      else if (d[a] < -hl) d[a] += p->L[a];
+    }
+  }
+  dist = norm3(d);
+  for (a = 0; a < 3; ++a) nrm[a] = dist > 0.0 ? d[a] / dist : 0.0;
+  dn = r[i1] + r[i2] - dist; /* normal overlap, Sec. 2 */
+  h = find_history(nc_in, lo_in, hi_in, i1, i2);
+  if (h >= 0) for (a = 0; a < 3; ++a) dto[a] = dt_in[3 * h + a];
+  m1 = mass_of(p, r[i1]);
+  m2 = mass_of(p, r[i2]);
+  contact_force(p, alpha, nrm, dn, r[i1], r[i2], m1, m2, &v[3 * i1], &v[3 * i2], &w[3 * i1],
+                &w[3 * i2], dto, dtn, ci);
+}
+
 /* ------------------------------------------------------------------------ */
 /* One step.  The paper leaves the integrator unstated; it is read as       */
 /* symplectic Euler.  Order: wrap, contact set, forces (Algorithm 1          */
@@ -593,6 +667,9 @@ int orc_step(const orc_params* p, int64_t n, double* x, double* v, double* w,
   pair32* pr = (pair32*)malloc(sizeof(pair32) * (size_t)(cap > 0 ? cap : 1));
   if (!Fp || !Tp || !pr) { free(Fp); free(Tp); free(pr); return 1; }
 
+#ifdef ORC_OPENMP
+#pragma omp parallel for schedule(static) private(a)
+#endif
   for (i = 0; i < n; ++i)
     for (a = 0; a < 3; ++a)
       if (p->periodic[a]) x[3 * i + a] = wrap(x[3 * i + a], p->L[a]);
@@ -600,29 +677,67 @@ int orc_step(const orc_params* p, int64_t n, double* x, double* v, double* w,
   nc = find_pairs(p, n, x, r, cap, pr);
   if (nc < 0) { free(Fp); free(Tp); free(pr); return 4; }
 
-  for (k = 0; k < nc; ++k) {
-    int32_t i1 = pr[k].lo, i2 = pr[k].hi;
-    double d[3], nrm[3], dist, dn, m1, m2, dto[3] = {0.0, 0.0, 0.0}, dtn[3];
-    int64_t h;
-    orc_contact_info ci;
-    for (a = 0; a < 3; ++a) {
-      d[a] = x[3 * i2 + a] - x[3 * i1 + a];
-      if (p->periodic[a]) {
-        double hl = 0.5 * p->L[a];
-        if (d[a] > hl) d[a] -= p->L[a];
-        else if (d[a] < -hl) d[a] += p->L[a];
+#ifdef ORC_OPENMP
+  {
+    /* every pair's force on its own, then each particle's contributions in
+     * ascending pair index: the serial loop's order of additions */
+    orc_contact_info* cis = (orc_contact_info*)malloc(sizeof(orc_contact_info) *
+                                                      (size_t)(nc > 0 ? nc : 1));
+    int64_t* roff = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t* rlist = (int64_t*)malloc(sizeof(int64_t) * (size_t)(2 * nc > 0 ? 2 * nc : 1));
+    if (!cis || !roff || !rlist) {
+      free(cis); free(roff); free(rlist); free(Fp); free(Tp); free(pr);
+      return 1;
+    }
+#pragma omp parallel for schedule(static)
+    for (k = 0; k < nc; ++k) {
+      int32_t i1 = pr[k].lo, i2 = pr[k].hi;
+      pair_force(p, alpha, x, v, w, r, nc_in, lo_in, hi_in, dt_in, i1, i2, &dt_out[3 * k],
+                 &cis[k]);
+      lo_out[k] = i1;
+      hi_out[k] = i2;
+      if (info) info[k] = cis[k];
+    }
+    for (k = 0; k < nc; ++k) {
+      roff[pr[k].lo + 1]++;
+      roff[pr[k].hi + 1]++;
+    }
+    for (i = 0; i < n; ++i) roff[i + 1] += roff[i];
+    {
+      int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+      if (!fill) {
+        free(cis); free(roff); free(rlist); free(Fp); free(Tp); free(pr);
+        return 1;
+      }
+      memcpy(fill, roff, sizeof(int64_t) * (size_t)n);
+      for (k = 0; k < nc; ++k) {
+        rlist[fill[pr[k].lo]++] = k;
+        rlist[fill[pr[k].hi]++] = k;
+      }
+      free(fill);
+    }
+#pragma omp parallel for schedule(static) private(a)
+    for (i = 0; i < n; ++i) {
+      int64_t e;
+      for (e = roff[i]; e < roff[i + 1]; ++e) {
+        const int64_t q = rlist[e];
+        const int lo = pr[q].lo == i;
+        for (a = 0; a < 3; ++a) {
+          if (lo) Fp[3 * i + a] += cis[q].F[a];
+          else Fp[3 * i + a] -= cis[q].F[a];
+          Tp[3 * i + a] += r[i] * cis[q].nF[a];
+        }
       }
     }
-    dist = norm3(d);
-    for (a = 0; a < 3; ++a) nrm[a] = dist > 0.0 ? d[a] / dist : 0.0;
-    dn = r[i1] + r[i2] - dist; /* normal overlap, Sec. 2 */
-    /* history of this pair, zero for a new contact (Sec. 4.2) */
-    h = find_history(nc_in, lo_in, hi_in, i1, i2);
-    if (h >= 0) for (a = 0; a < 3; ++a) dto[a] = dt_in[3 * h + a];
-    m1 = mass_of(p, r[i1]);
-    m2 = mass_of(p, r[i2]);
-    contact_force(p, alpha, nrm, dn, r[i1], r[i2], m1, m2, &v[3 * i1],
-                  &v[3 * i2], &w[3 * i1], &w[3 * i2], dto, dtn, &ci);
+    free(cis);
+    free(roff);
+    free(rlist);
+  }
+#else
+  for (k = 0; k < nc; ++k) {
+    int32_t i1 = pr[k].lo, i2 = pr[k].hi;
+    orc_contact_info ci;
+    pair_force(p, alpha, x, v, w, r, nc_in, lo_in, hi_in, dt_in, i1, i2, &dt_out[3 * k], &ci);
     for (a = 0; a < 3; ++a) {
       Fp[3 * i1 + a] += ci.F[a];
       Fp[3 * i2 + a] -= ci.F[a];
@@ -632,9 +747,9 @@ int orc_step(const orc_params* p, int64_t n, double* x, double* v, double* w,
     }
     lo_out[k] = i1;
     hi_out[k] = i2;
-    for (a = 0; a < 3; ++a) dt_out[3 * k + a] = dtn[a];
     if (info) info[k] = ci;
   }
+#endif
   *nc_out = nc;
 
   /* walls: the floor z = 0, then rectangles and lines, each a particle of
@@ -647,6 +762,9 @@ int orc_step(const orc_params* p, int64_t n, double* x, double* v, double* w,
     for (wi = 0; wi < nw; ++wi) {
       const int floor = p->floor_wall && wi == 0;
       const orc_wall* wl = floor ? NULL : &p->walls[wi - (p->floor_wall ? 1 : 0)];
+#ifdef ORC_OPENMP
+#pragma omp parallel for schedule(static) private(a)
+#endif
       for (i = 0; i < n; ++i) {
         double nwall[3], dn;
         double* hist = wall_dt ? &wall_dt[3 * (i * nw + wi)] : NULL;
@@ -677,6 +795,9 @@ int orc_step(const orc_params* p, int64_t n, double* x, double* v, double* w,
   }
 
   /* gravity, Sec. 4.2 "ForceGravity" */
+#ifdef ORC_OPENMP
+#pragma omp parallel for schedule(static) private(a)
+#endif
   for (i = 0; i < n; ++i) {
     double m = mass_of(p, r[i]);
     for (a = 0; a < 3; ++a) Fp[3 * i + a] += m * p->g[a];
@@ -686,6 +807,9 @@ int orc_step(const orc_params* p, int64_t n, double* x, double* v, double* w,
   if (T) memcpy(T, Tp, sizeof(double) * 3 * (size_t)n);
 
   /* symplectic Euler, Sec. 4.2 "Integrate" */
+#ifdef ORC_OPENMP
+#pragma omp parallel for schedule(static) private(a)
+#endif
   for (i = 0; i < n; ++i) {
     double m = mass_of(p, r[i]);
     double I = 0.4 * m * r[i] * r[i];

@@ -30,7 +30,7 @@ def test_failing_leg_is_recorded(monkeypatch):
     monkeypatch.setattr(bench, "_fig4_leg", ok("fig4"))
     monkeypatch.setattr(bench, "_batched_leg", ok("batched"))
     args = types.SimpleNamespace(steps=10, no_batched=False, w3=False, w5=False, sweep=False)
-    out = bench._side_legs(args, None, None, None, None, None)
+    out = bench._side_legs(args, None, None, None, None, None, 0.0)
     assert out["collide_fused_vs_compact"]["error"].startswith("RuntimeError: no such workload")
     assert out["fp64_gpu"] == {"leg": "throughput"} and out["batched"] == {"leg": "batched"}
     assert "fig4" in calls and "size_binned" in calls  # the legs after the failure still ran
