@@ -618,6 +618,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   d.Cmax = ctx->Cmax;
   d.M_lin = ctx->M_lin;
   d.M_rank = ctx->M_rank;
+  d.nbox = (int)ctx->hbox.size();
   bool ok = true;
   auto A = [&](size_t bytes) {
     void* p = dalloc(ctx, bytes);
@@ -1696,6 +1697,7 @@ extern "C" dem_status dem_contacts_static(int64_t n, const double* x,
   B.rsplit_f = INFINITY;  // one size class
 
   Dev d{};
+  d.nbox = 1;
   d.boxes = (const BoxDev*)(base + lay.box);
   d.slot_box = (const int*)(base + lay.slot_box);
   d.N = N;

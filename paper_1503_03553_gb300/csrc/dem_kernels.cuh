@@ -119,6 +119,7 @@ struct Dev {
   int Cmax;      // contact list capacity
   int M_lin;     // cells over all boxes
   int M_rank;    // cells + one free-slot cell per box
+  int nbox;      // boxes (1: every slot is in box 0, no lookup needed)
   const int* rank_of_lin;  // box-local Morton rank of each linear cell
   const int* lin_of_rank;  // global linear cell of each rank cell, -1 = free
   int* ccount;   // per rank cell: particles in it (kept up to date by movers)
@@ -1657,11 +1658,14 @@ __device__ __forceinline__ bool pair_shift(const BoxDev& B, int a, int ci, int c
     else if (dc + n >= -w && dc + n <= w) image = 1;
     else return false;
   }
-  if (M == kMIXED) {
+  if (M != kMIXED) {
+    sh = 0.0f;  // the absolute-position rule needs no shift
+  } else if (w == 1) {
+    // the search's table: -H, 0, +H, wrap below, wrap above
+    sh = B.shift[a][image == 0 ? dc + 1 : (image < 0 ? 3 : 4)];
+  } else {
     const long long S = (long long)dc * B.Hq[a] + (long long)image * B.Lq[a];
     sh = __fmul_rn(i64_to_f32_rn(S), kQ);
-  } else {
-    sh = 0.0f;  // the absolute-position rule needs no shift
   }
   return true;
 }
@@ -1724,7 +1728,7 @@ k_pairs(Dev d, PState b, VList vl) {
       const int c = t0 + u * 32 + lane;
       bool hit = false;
       if (pr[u].x >= 0) {
-        const BoxDev& B = d.boxes[d.slot_box[pr[u].x]];
+        const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[pr[u].x]];
         hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
         if (!hit && vl.flag[c]) {
           ((DT*)vl.dx)[c] = DT{};
@@ -1742,7 +1746,7 @@ k_pairs(Dev d, PState b, VList vl) {
       if (k + lane < qn) {
         const int c = q[k + lane];
         const int2 p = vl.pair[c];
-        const int box = d.slot_box[p.x];
+        const int box = d.nbox == 1 ? 0 : d.slot_box[p.x];
         const BoxDev& B = d.boxes[box];
         PairOut<M> o;
         pair_law<M>(b, B, p.x, p.y, ((const DT*)vl.dx)[c], ((const DT*)vl.dy)[c],
