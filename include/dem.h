@@ -318,6 +318,39 @@ dem_status dem_set_timing(dem_ctx* ctx, int32_t on);
 dem_status dem_autotune(dem_ctx* ctx, int64_t steps, double* best_ms,
                         int32_t* block, int32_t* graph_steps);
 
+/* Layout tuner (orchestration).  Searches, on the live particles, the
+ * candidate-list skin (per box a multiple of r_max: 0, 0.5 %, 1.5 % or 4 %),
+ * the cell grid (the finest legal cells, 8 % and 18 % wider; Sec. 3.3: the
+ * cell size trades the length of each particle's candidate loop against the
+ * divergence of a warp and the cells it visits), the size split r_split (0,
+ * or the box's 90 % or 97 % radius quantile), then the block size
+ * {128, 256, 512} and the CUDA-graph length {8, 16, 32}, one parameter
+ * after the other, keeping the best of each.  The re-sort interval follows
+ * from the skin (a re-sort comes when a particle has moved about half of
+ * it).  Each candidate runs `steps` steps (at least 4) from the state the
+ * call started with, the first step's re-sort included; that state
+ * (positions, velocities, spins, pair history) is put back after every
+ * trial and at the end, so the call does not advance the simulation; wall
+ * histories restart from zero.  The context keeps the fastest
+ * configuration (dem_get_layout reads it per box).  The per-particle Collide
+ * forms search only the block size and graph length.  out (may be NULL)
+ * receives the choice. */
+typedef struct {
+  double ms_per_step;       /* device time per step of the chosen one      */
+  double skin_over_rmax;    /* skin / r_max                                */
+  double cell_scale;        /* cell edge / finest legal cell edge          */
+  double rsplit_quantile;   /* 0 = one size class                          */
+  int32_t block;
+  int32_t graph_steps;
+  int32_t trials;           /* configurations timed                        */
+  int32_t pad;
+} dem_tuning;
+dem_status dem_autotune_layout(dem_ctx* ctx, int64_t steps, dem_tuning* out);
+
+/* The layout of one box now in use: cells per axis, skin [m], r_split [m]. */
+dem_status dem_get_layout(dem_ctx* ctx, int32_t box, int32_t ncell[3], double* skin,
+                          double* r_split);
+
 /* Kernel launches issued by a step that does not re-sort in a CUDA graph
  * (DEM_COLLIDE_COMPACT) or by any step (the per-particle forms re-sort
  * every step). */

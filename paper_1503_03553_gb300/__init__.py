@@ -60,6 +60,13 @@ class dem_box(C.Structure):
                 ("r_split", C.c_double), ("skin", C.c_double)]
 
 
+class dem_tuning(C.Structure):
+    _fields_ = [("ms_per_step", C.c_double), ("skin_over_rmax", C.c_double),
+                ("cell_scale", C.c_double), ("rsplit_quantile", C.c_double),
+                ("block", C.c_int32), ("graph_steps", C.c_int32), ("trials", C.c_int32),
+                ("pad", C.c_int32)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -106,6 +113,8 @@ def lib() -> C.CDLL:
         "dem_set_timing": (C.c_int, [vp, C.c_int32]),
         "dem_launches_per_step": (C.c_int32, [vp]),
         "dem_get_resort_stats": (C.c_int, [vp, i64p]),
+        "dem_autotune_layout": (C.c_int, [vp, C.c_int64, C.POINTER(dem_tuning)]),
+        "dem_get_layout": (C.c_int, [vp, C.c_int32, ip, dp, dp]),
         "dem_autotune": (C.c_int, [vp, C.c_int64, dp, ip, ip]),
         "dem_sync": (C.c_int, [vp]),
         "dem_last_error": (C.c_char_p, [vp]),
@@ -337,6 +346,22 @@ def dem_autotune(ctx, steps: int = 32):
     return ms.value, blk.value, gs.value
 
 
+def dem_autotune_layout(ctx, steps: int = 32) -> dict:
+    """Search skin, cell grid, size split, block size and graph length on
+    the live particles (the state is put back); returns the choice."""
+    t = dem_tuning()
+    _check(ctx, lib().dem_autotune_layout(ctx, int(steps), C.byref(t)))
+    return {f: getattr(t, f) for f, _ in dem_tuning._fields_ if f != "pad"}
+
+
+def dem_get_layout(ctx, box: int = 0) -> dict:
+    nc = (C.c_int32 * 3)()
+    skin = C.c_double()
+    rs = C.c_double()
+    _check(ctx, lib().dem_get_layout(ctx, box, nc, C.byref(skin), C.byref(rs)))
+    return {"ncell": tuple(nc), "skin": skin.value, "r_split": rs.value}
+
+
 def dem_launches_per_step(ctx) -> int:
     return lib().dem_launches_per_step(ctx)
 
@@ -512,6 +537,12 @@ class Context:
 
     def resort_stats(self):
         return dem_get_resort_stats(self.ctx)
+
+    def autotune_layout(self, steps=32):
+        return dem_autotune_layout(self.ctx, steps)
+
+    def layout(self, box=0):
+        return dem_get_layout(self.ctx, box)
 
     def autotune(self, steps=32):
         return dem_autotune(self.ctx, steps)

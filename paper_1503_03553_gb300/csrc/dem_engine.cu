@@ -79,6 +79,7 @@ struct dem_ctx {
   int parity = 0;
   int nwh = 0;                   // wall histories per slot (largest box)
   std::vector<WallDev> hwalls;   // all boxes' rectangle and line walls
+  std::vector<std::vector<dem_wall>> wall_src;  // the caller's walls, copied
   bool have_particles = false;
   bool have_ft = false;
   unsigned* h_status = nullptr;  // pinned
@@ -360,71 +361,43 @@ int32_t dem_launches_per_step(const dem_ctx* ctx) {
   return ctx ? launches_per_step(ctx) : 0;
 }
 
-dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
-  dem_ctx* ctx = nullptr;
-  if (!out) return fail(nullptr, DEM_ERR_ARG, "out is null");
-  *out = nullptr;
-  if (!cfg || cfg->nboxes <= 0 || !cfg->boxes || cfg->nmaterials <= 0 ||
-      !cfg->materials)
-    return fail(nullptr, DEM_ERR_ARG, "config needs boxes and materials");
-  if (cfg->precision < 0 || cfg->precision > 2)
-    return fail(nullptr, DEM_ERR_ARG, "bad precision");
-  if (cfg->collide != DEM_COLLIDE_COMPACT && cfg->collide != DEM_COLLIDE_FUSED &&
-      cfg->collide != DEM_COLLIDE_TWOLOOP)
-    return fail(nullptr, DEM_ERR_ARG,
-                "collide must be DEM_COLLIDE_COMPACT, DEM_COLLIDE_FUSED or DEM_COLLIDE_TWOLOOP");
-  if (!!cfg->alloc != !!cfg->free)
-    return fail(nullptr, DEM_ERR_ARG, "alloc and free hooks go together");
-  ctx = new dem_ctx();
-  ctx->cfg = *cfg;
-  ctx->boxes.assign(cfg->boxes, cfg->boxes + cfg->nboxes);
-  ctx->mats.assign(cfg->materials, cfg->materials + cfg->nmaterials);
-  ctx->cfg.boxes = nullptr;
-  ctx->cfg.materials = nullptr;
-  ctx->mode = cfg->precision == DEM_FP64 ? kFP64
-              : cfg->precision == DEM_MIXED ? kMIXED : kFP32;
-  ctx->K = cfg->row_capacity > 0 ? cfg->row_capacity : 32;
-  ctx->fused = cfg->collide == DEM_COLLIDE_FUSED || cfg->collide == DEM_COLLIDE_TWOLOOP;
-  ctx->twoloop = cfg->collide == DEM_COLLIDE_TWOLOOP;
-  ctx->block = cfg->block > 0 ? cfg->block : 256;
-  ctx->graph_steps = cfg->graph_steps == 0 ? 16 : cfg->graph_steps;
-  if (ctx->graph_steps > 0 && (ctx->graph_steps & 1)) ctx->graph_steps += 1;
+// Device state for ctx->boxes from scratch: per-box geometry, cell grids and
+// material constants, every device array, their initial contents.  Used by
+// dem_create and by the layout tuner (which re-creates it for other grids,
+// skins and size splits).  On failure *msg says why and nothing stays
+// allocated.
+static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   auto bail = [&](dem_status s, const std::string& m) {
-    g_create_error = m;
-    if (ctx) {
-      free_all(ctx);
-      if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
-      if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-      if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
-      for (cudaEvent_t& e : ctx->xfer_ev)
-        if (e) cudaEventDestroy(e);
-      if (ctx->h_status) cudaFreeHost(ctx->h_status);
-      if (ctx->h_count) cudaFreeHost(ctx->h_count);
-      delete ctx;
-    }
+    *msg = m;
+    free_all(ctx);
     return s;
   };
-  if (ctx->K < 2 || ctx->K > 1024) return bail(DEM_ERR_ARG, "row_capacity out of range");
-  ctx->K = (ctx->K + 3) & ~3;  // rows are read four entries at a time
-  if (ctx->block < 32 || ctx->block > 1024 || (ctx->block & 31))
-    return bail(DEM_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
-  if (cudaGetDevice(&ctx->device) != cudaSuccess)
-    return bail(DEM_ERR_CUDA, "no CUDA device");
-  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-  if (cfg->stream) {
-    ctx->stream = (cudaStream_t)cfg->stream;
-  } else {
-    if (cudaStreamCreate(&ctx->stream) != cudaSuccess)
-      return bail(DEM_ERR_CUDA, "stream creation failed");
-    ctx->own_stream = true;
+  // derived state of a previous set-up
+  for (auto& g : ctx->gexec)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  free_all(ctx);
+  ctx->hbox.clear();
+  ctx->hwalls.clear();
+  ctx->nwh = 0;
+  ctx->split = false;
+  ctx->always_resort = false;
+  ctx->dev = Dev{};
+  for (int p = 0; p < 2; ++p) {
+    ctx->ps[p] = PState{};
+    ctx->cl[p] = CList{};
+    ctx->vl[p] = VList{};
   }
-  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess)
-    return bail(DEM_ERR_CUDA, "stream creation failed");
-  for (cudaEvent_t& e : ctx->xfer_ev)
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-      return bail(DEM_ERR_CUDA, "event creation failed");
-
+  ctx->cs_cur = ctx->cs_new = nullptr;
+  ctx->collect = ctx->chg = nullptr;
+  ctx->staging = nullptr;
+  ctx->staging_i = nullptr;
+  ctx->parity = 0;
+  ctx->sticky = 0;
+  ctx->have_particles = false;
+  ctx->have_ft = false;
   // ---- boxes: geometry, cell grids, material constants --------------------
   long long N = 0, Mlin = 0, Mrank = 0;
   int max_cap = 0;
@@ -432,7 +405,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   for (size_t b = 0; b < ctx->boxes.size(); ++b) {
     const dem_box& bx = ctx->boxes[b];
     BoxDev B{};
-    if (bx.material < 0 || bx.material >= cfg->nmaterials)
+    if (bx.material < 0 || bx.material >= (int)ctx->mats.size())
       return bail(DEM_ERR_ARG, "box material index out of range");
     const dem_material& mt = ctx->mats[bx.material];
     if (!(mt.E > 0) || !(mt.poisson > -1 && mt.poisson < 0.5) || !(mt.density > 0) ||
@@ -567,7 +540,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
       B.g_f[a] = (float)bx.g[a];
     }
     double s = mt.poisson;
-    double cn = cfg->kn_literal ? (2.0 - s * s) : (1.0 - s * s);
+    double cn = ctx->cfg.kn_literal ? (2.0 - s * s) : (1.0 - s * s);
     double G = mt.E / (2.0 * (1.0 + s));
     B.kn_c = 4.0 / 3.0 / (cn / mt.E + cn / mt.E);
     B.kt_c = 8.0 / ((2.0 - s) / G + (2.0 - s) / G);
@@ -714,9 +687,6 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   ctx->staging = (double*)A(sizeof(double) * 16 * (size_t)std::max(1, max_cap));
   ctx->staging_i = (int*)A(sizeof(int) * 2 * (size_t)std::max(1, max_cap));
   if (!ok) return bail(DEM_ERR_ALLOC, "device allocation failed");
-  if (cudaMallocHost(&ctx->h_status, sizeof(unsigned)) != cudaSuccess ||
-      cudaMallocHost(&ctx->h_count, sizeof(int)) != cudaSuccess)
-    return bail(DEM_ERR_ALLOC, "pinned host allocation failed");
 
   // ---- initial contents --------------------------------------------------------
   std::vector<int> slot_box(n, 0), rol(std::max(1, ctx->M_lin)),
@@ -763,6 +733,89 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   if (!e && !ctx->fused) e = cudaMemsetAsync(d.fcnt, 0, sizeof(int) * n, s);
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return bail(DEM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  return DEM_OK;
+}
+
+dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
+  dem_ctx* ctx = nullptr;
+  if (!out) return fail(nullptr, DEM_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!cfg || cfg->nboxes <= 0 || !cfg->boxes || cfg->nmaterials <= 0 ||
+      !cfg->materials)
+    return fail(nullptr, DEM_ERR_ARG, "config needs boxes and materials");
+  if (cfg->precision < 0 || cfg->precision > 2)
+    return fail(nullptr, DEM_ERR_ARG, "bad precision");
+  if (cfg->collide != DEM_COLLIDE_COMPACT && cfg->collide != DEM_COLLIDE_FUSED &&
+      cfg->collide != DEM_COLLIDE_TWOLOOP)
+    return fail(nullptr, DEM_ERR_ARG,
+                "collide must be DEM_COLLIDE_COMPACT, DEM_COLLIDE_FUSED or DEM_COLLIDE_TWOLOOP");
+  if (!!cfg->alloc != !!cfg->free)
+    return fail(nullptr, DEM_ERR_ARG, "alloc and free hooks go together");
+  ctx = new dem_ctx();
+  ctx->cfg = *cfg;
+  ctx->boxes.assign(cfg->boxes, cfg->boxes + cfg->nboxes);
+  ctx->mats.assign(cfg->materials, cfg->materials + cfg->nmaterials);
+  ctx->cfg.boxes = nullptr;
+  ctx->cfg.materials = nullptr;
+  ctx->mode = cfg->precision == DEM_FP64 ? kFP64
+              : cfg->precision == DEM_MIXED ? kMIXED : kFP32;
+  ctx->K = cfg->row_capacity > 0 ? cfg->row_capacity : 32;
+  ctx->fused = cfg->collide == DEM_COLLIDE_FUSED || cfg->collide == DEM_COLLIDE_TWOLOOP;
+  ctx->twoloop = cfg->collide == DEM_COLLIDE_TWOLOOP;
+  ctx->block = cfg->block > 0 ? cfg->block : 256;
+  ctx->graph_steps = cfg->graph_steps == 0 ? 16 : cfg->graph_steps;
+  if (ctx->graph_steps > 0 && (ctx->graph_steps & 1)) ctx->graph_steps += 1;
+  auto bail = [&](dem_status s, const std::string& m) {
+    g_create_error = m;
+    if (ctx) {
+      free_all(ctx);
+      if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+      if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+      if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
+      for (cudaEvent_t& e : ctx->xfer_ev)
+        if (e) cudaEventDestroy(e);
+      if (ctx->h_status) cudaFreeHost(ctx->h_status);
+      if (ctx->h_count) cudaFreeHost(ctx->h_count);
+      delete ctx;
+    }
+    return s;
+  };
+  if (ctx->K < 2 || ctx->K > 1024) return bail(DEM_ERR_ARG, "row_capacity out of range");
+  ctx->K = (ctx->K + 3) & ~3;  // rows are read four entries at a time
+  if (ctx->block < 32 || ctx->block > 1024 || (ctx->block & 31))
+    return bail(DEM_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
+  if (cudaGetDevice(&ctx->device) != cudaSuccess)
+    return bail(DEM_ERR_CUDA, "no CUDA device");
+  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+  if (cfg->stream) {
+    ctx->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreate(&ctx->stream) != cudaSuccess)
+      return bail(DEM_ERR_CUDA, "stream creation failed");
+    ctx->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(DEM_ERR_CUDA, "stream creation failed");
+  for (cudaEvent_t& e : ctx->xfer_ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return bail(DEM_ERR_CUDA, "event creation failed");
+
+  // the walls are read during the call: keep copies for later set-ups
+  ctx->wall_src.resize(ctx->boxes.size());
+  for (size_t b = 0; b < ctx->boxes.size(); ++b) {
+    dem_box& bx = ctx->boxes[b];
+    if (bx.nwalls > 0 && bx.walls && bx.nwalls <= 15)
+      ctx->wall_src[b].assign(bx.walls, bx.walls + bx.nwalls);
+    bx.walls = ctx->wall_src[b].empty() ? nullptr : ctx->wall_src[b].data();
+    if (bx.nwalls > 0 && ctx->wall_src[b].empty()) bx.walls = nullptr;
+  }
+  if (cudaMallocHost(&ctx->h_status, sizeof(unsigned)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_count, sizeof(int)) != cudaSuccess)
+    return bail(DEM_ERR_ALLOC, "pinned host allocation failed");
+  std::string msg;
+  const dem_status st = setup_device(ctx, &msg);
+  if (st) return bail(st, msg);
   *out = ctx;
   return DEM_OK;
 }
@@ -1081,6 +1134,247 @@ dem_status dem_autotune(dem_ctx* ctx, int64_t steps, double* best_ms,
   if (graph_steps) *graph_steps = bg;
   return read_status(ctx);
 }
+
+}  // extern "C"
+
+// ---- layout tuner ------------------------------------------------------------
+namespace {
+
+// the particles and pair history of every box, in id order (host)
+struct Snapshot {
+  std::vector<std::vector<double>> x, v, w, r, dt;
+  std::vector<std::vector<int32_t>> lo, hi;
+};
+
+dem_status take_snapshot(dem_ctx* ctx, Snapshot& sn) {
+  const size_t nb = ctx->boxes.size();
+  sn = Snapshot{};
+  sn.x.resize(nb); sn.v.resize(nb); sn.w.resize(nb); sn.r.resize(nb);
+  sn.lo.resize(nb); sn.hi.resize(nb); sn.dt.resize(nb);
+  for (size_t b = 0; b < nb; ++b) {
+    const int n = ctx->hbox[b].nlive;
+    sn.x[b].resize(3 * (size_t)n); sn.v[b].resize(3 * (size_t)n); sn.w[b].resize(3 * (size_t)n);
+    sn.r[b].resize((size_t)n);
+    if (n == 0) continue;
+    dem_status st = dem_get_state(ctx, (int32_t)b, sn.x[b].data(), sn.v[b].data(),
+                                  sn.w[b].data(), nullptr, nullptr, DEM_HOST);
+    if (st) return st;
+    double* dr = ctx->staging;
+    const int p = ctx->parity;
+    switch (ctx->mode) {
+      case kFP64: k_get_radius<kFP64><<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ctx->dev, ctx->ps[p], (int)b, dr); break;
+      case kMIXED: k_get_radius<kMIXED><<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ctx->dev, ctx->ps[p], (int)b, dr); break;
+      default: k_get_radius<kFP32><<<blocks_for(n, 256), 256, 0, ctx->stream>>>(ctx->dev, ctx->ps[p], (int)b, dr); break;
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(sn.r[b].data(), dr, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int64_t nc = 0;
+    st = dem_get_contacts(ctx, (int32_t)b, 0, &nc, nullptr, nullptr, nullptr);
+    if (st && st != DEM_ERR_CAPACITY) return st;
+    sn.lo[b].resize((size_t)nc); sn.hi[b].resize((size_t)nc); sn.dt[b].resize(3 * (size_t)nc);
+    st = dem_get_contacts(ctx, (int32_t)b, nc, &nc, sn.lo[b].data(), sn.hi[b].data(), sn.dt[b].data());
+    if (st) return st;
+  }
+  return DEM_OK;
+}
+
+dem_status restore_snapshot(dem_ctx* ctx, const Snapshot& sn) {
+  for (size_t b = 0; b < ctx->boxes.size(); ++b) {
+    const int64_t n = (int64_t)sn.r[b].size();
+    dem_status st = dem_set_particles(ctx, (int32_t)b, n, sn.x[b].data(), sn.v[b].data(),
+                                      sn.w[b].data(), sn.r[b].data(), DEM_HOST);
+    if (st) return st;
+    if (!sn.lo[b].empty()) {
+      st = dem_set_contacts(ctx, (int32_t)b, (int64_t)sn.lo[b].size(), sn.lo[b].data(),
+                            sn.hi[b].data(), sn.dt[b].data());
+      if (st) return st;
+    }
+  }
+  return DEM_OK;
+}
+
+// the finest legal cell count per axis of a box for a skin and size split
+int finest_cells(const dem_box& bx, int a, double skin, double rsplit) {
+  const bool split = rsplit > 0;
+  const double hmin = (split ? std::max(2.0 * rsplit + skin, bx.r_max + 0.5 * skin)
+                             : 2.0 * bx.r_max + skin) * (1.0 + 1e-5);
+  return std::max(1, (int)std::floor(bx.L[a] / hmin));
+}
+
+struct Layout {
+  double skin_rel = 0.0, scale = 1.0, rq = 0.0;
+};
+
+// the boxes of a layout (per box: skin = skin_rel r_max, cells scale times
+// the finest legal edge, r_split the rq quantile of its radii)
+std::vector<dem_box> layout_boxes(const std::vector<dem_box>& base, const Snapshot& sn,
+                                  const Layout& lay) {
+  std::vector<dem_box> out = base;
+  for (size_t b = 0; b < out.size(); ++b) {
+    dem_box& bx = out[b];
+    bx.skin = lay.skin_rel * bx.r_max;
+    bx.r_split = 0.0;
+    if (lay.rq > 0 && !sn.r[b].empty()) {
+      std::vector<double> r = sn.r[b];
+      const size_t k = std::min(r.size() - 1, (size_t)(lay.rq * (double)(r.size() - 1)));
+      std::nth_element(r.begin(), r.begin() + (ptrdiff_t)k, r.end());
+      if (r[k] > 0 && r[k] < bx.r_max) bx.r_split = r[k];
+    }
+    for (int a = 0; a < 3; ++a)
+      bx.ncell[a] = std::max(1, (int)std::floor(finest_cells(bx, a, bx.skin, bx.r_split) / lay.scale));
+  }
+  return out;
+}
+
+// device ms per step of `steps` steps from the snapshot (graphs built by an
+// untimed run first); a negative value when the configuration is refused
+dem_status time_trial(dem_ctx* ctx, const Snapshot& sn, int64_t steps, cudaEvent_t e0,
+                      cudaEvent_t e1, double* ms) {
+  *ms = -1.0;
+  dem_status st = restore_snapshot(ctx, sn);
+  if (st) return st;
+  st = dem_step(ctx, std::max<int64_t>(ctx->graph_steps, 1));
+  if (st) return st;
+  st = restore_snapshot(ctx, sn);
+  if (st) return st;
+  CK(cudaEventRecord(e0, ctx->stream));
+  st = dem_step(ctx, steps);
+  CK(cudaEventRecord(e1, ctx->stream));
+  CK(cudaEventSynchronize(e1));
+  if (st) return st;
+  float t = 0.f;
+  CK(cudaEventElapsedTime(&t, e0, e1));
+  *ms = t / (double)steps;
+  return DEM_OK;
+}
+
+}  // namespace
+
+extern "C" dem_status dem_autotune_layout(dem_ctx* ctx, int64_t steps, dem_tuning* out) {
+  if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");
+  if (!ctx->have_particles) return fail(ctx, DEM_ERR_STATE, "no particles set");
+  if (ctx->sticky) return read_status(ctx);
+  if (steps < 4) steps = 4;
+  Snapshot sn;
+  dem_status st = take_snapshot(ctx, sn);
+  if (st) return st;
+  const bool was_timing = ctx->tm.on;
+  ctx->tm.on = false;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const std::vector<dem_box> base = ctx->boxes;
+  Layout best_lay;
+  for (const dem_box& bx : base) {  // the layout the context starts with
+    best_lay.skin_rel = std::max(best_lay.skin_rel, bx.skin / bx.r_max);
+  }
+  int trials = 0;
+  double best = 1e300;
+  int best_block = ctx->block, best_graph = ctx->graph_steps;
+  auto apply = [&](const Layout& lay, std::string* msg) -> dem_status {
+    if (ctx->fused) return DEM_OK;
+    ctx->boxes = layout_boxes(base, sn, lay);
+    return setup_device(ctx, msg);
+  };
+  auto trial = [&](const Layout& lay, int block, int graph, double* ms) -> dem_status {
+    *ms = -1.0;
+    ctx->block = block;
+    ctx->graph_steps = graph;
+    std::string msg;
+    dem_status s2 = apply(lay, &msg);
+    if (s2 == DEM_ERR_ARG) return DEM_OK;  // not a legal layout for these boxes
+    if (s2) return fail(ctx, s2, msg);
+    s2 = time_trial(ctx, sn, steps, e0, e1, ms);
+    if (s2 == DEM_ERR_CAPACITY) {  // rows too short for this skin: not a candidate
+      *ms = -1.0;
+      return DEM_OK;
+    }
+    ++trials;
+    return s2;
+  };
+  auto consider = [&](const Layout& lay, int block, int graph) -> dem_status {
+    double ms;
+    dem_status s2 = trial(lay, block, graph, &ms);
+    if (s2) return s2;
+    if (ms > 0 && ms < best) {
+      best = ms;
+      best_lay = lay;
+      best_block = block;
+      best_graph = graph;
+    }
+    return DEM_OK;
+  };
+  st = consider(best_lay, best_block, best_graph);  // the starting point
+  if (!st && !ctx->fused) {
+    for (double sk : {0.0, 0.005, 0.015, 0.04}) {
+      Layout l = best_lay;
+      l.skin_rel = sk;
+      l.scale = 1.0;
+      l.rq = 0.0;
+      if ((st = consider(l, best_block, best_graph))) break;
+    }
+    for (double sc : {1.08, 1.18}) {
+      if (st) break;
+      Layout l = best_lay;
+      l.scale = sc;
+      st = consider(l, best_block, best_graph);
+    }
+    for (double q : {0.90, 0.97}) {
+      if (st) break;
+      Layout l = best_lay;
+      l.rq = q;
+      st = consider(l, best_block, best_graph);
+    }
+  }
+  for (int bl : {128, 256, 512}) {
+    if (st) break;
+    if (bl != best_block) st = consider(best_lay, bl, best_graph);
+  }
+  for (int gs : {8, 16, 32}) {
+    if (st) break;
+    if (gs != best_graph) st = consider(best_lay, best_block, gs);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // keep the best and put the starting state back
+  dem_status st2 = DEM_OK;
+  {
+    ctx->block = best_block;
+    ctx->graph_steps = best_graph;
+    std::string msg;
+    st2 = apply(best_lay, &msg);
+    if (st2) st2 = fail(ctx, st2, msg);
+    if (!st2) st2 = restore_snapshot(ctx, sn);
+  }
+  ctx->tm.on = was_timing;
+  if (st) return st;
+  if (st2) return st2;
+  if (out) {
+    out->ms_per_step = best;
+    out->skin_over_rmax = best_lay.skin_rel;
+    out->cell_scale = best_lay.scale;
+    out->rsplit_quantile = best_lay.rq;
+    out->block = best_block;
+    out->graph_steps = best_graph;
+    out->trials = trials;
+    out->pad = 0;
+  }
+  return read_status(ctx);
+}
+
+extern "C" dem_status dem_get_layout(dem_ctx* ctx, int32_t box, int32_t ncell[3], double* skin,
+                                     double* r_split) {
+  dem_status st = check_box(ctx, box);
+  if (st) return st;
+  if (ncell)
+    for (int a = 0; a < 3; ++a) ncell[a] = ctx->hbox[box].n[a];
+  if (skin) *skin = ctx->boxes[box].skin;
+  if (r_split) *r_split = ctx->boxes[box].r_split;
+  return DEM_OK;
+}
+
+extern "C" {
 
 dem_status dem_set_timing(dem_ctx* ctx, int32_t on) {
   if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");

@@ -1701,7 +1701,7 @@ constexpr int kPairTile = 32 * kPairU;
 constexpr int kPairWarps = 8;
 
 template <int M>
-__global__ void __launch_bounds__(32 * kPairWarps)
+__global__ void __launch_bounds__(32 * kPairWarps, 4)
 k_pairs(Dev d, PState b, VList vl) {
   using T = Tr<M>;
   using V4 = typename T::V4;
@@ -2204,8 +2204,8 @@ __global__ void k_walls(Dev d, PState b) {
 // then binning for the next step
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag,
-                                   int store_ft) {
+__global__ void __launch_bounds__(256, 4)
+k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, int store_ft) {
   using T = Tr<M>;
   using P = typename T::P;
   using R = typename T::R;
@@ -2219,10 +2219,11 @@ __global__ void k_gather_integrate(Dev d, PState b, const unsigned char* __restr
   const V4* nFc = (const V4*)d.nFc;
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
   if (!d.Ffused) {
-    // the slot's candidate pairs in increasing partner id, four at a time
-    // (their flags and forces loaded together); Fc is the force on the
-    // pair's lower-id member: added when this slot is that member,
-    // subtracted otherwise; n x F enters with the same sign for both
+    // the slot's candidate pairs in increasing partner id, four at a time:
+    // their contact flags first, then the forces of the pairs in contact;
+    // Fc is the force on the pair's lower-id member: added when this slot is
+    // that member, subtracted otherwise; n x F enters with the same sign for
+    // both
     const int nrow = min(d.fcnt[i], d.K);
     const int* row = d.frow + (size_t)i * d.K;
     for (int k = 0; k < nrow; k += 4) {
@@ -2231,13 +2232,12 @@ __global__ void k_gather_integrate(Dev d, PState b, const unsigned char* __restr
       unsigned char f[4];
       V4 fv[4], qv[4];
 #pragma unroll
+      for (int u = 0; u < 4; ++u) f[u] = k + u < nrow ? vl_flag[e[u] >> 1] : 0;
+#pragma unroll
       for (int u = 0; u < 4; ++u) {
-        f[u] = 0;
-        if (k + u < nrow) {
-          const int c = e[u] >> 1;
-          f[u] = vl_flag[c];
-          fv[u] = ld4(Fc + c);
-          qv[u] = ld4(nFc + c);
+        if (f[u]) {
+          fv[u] = ld4(Fc + (e[u] >> 1));
+          qv[u] = ld4(nFc + (e[u] >> 1));
         }
       }
 #pragma unroll
@@ -2468,6 +2468,17 @@ __global__ void k_get_state(Dev d, PState b, int box, double* x, double* v,
     Tq[3 * k + 1] = q.y;
     Tq[3 * k + 2] = q.z;
   }
+}
+
+// radii in id order (the layout tuner's snapshot)
+template <int M>
+__global__ void k_get_radius(Dev d, PState b, int box, double* r) {
+  using V4 = typename Tr<M>::V4;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const BoxDev& B = d.boxes[box];
+  if (t >= B.nlive) return;
+  const int slot = B.pbase + t;
+  r[b.id[slot] - B.pbase] = (double)((const V4*)b.omg)[slot].w;
 }
 
 __global__ void k_get_order(Dev d, PState b, int box, int* id_by_slot,
