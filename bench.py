@@ -63,8 +63,8 @@ def _args():
     ap.add_argument("--w5", action="store_true",
                     help="add the W5 precision-stress leg (4 M spheres at packing 0.60, "
                          "10,000 steps of each form, oracle snapshots every 1,000 steps)")
-    ap.add_argument("--sweep", action="store_true",
-                    help="add a particle-count sweep of the W2 workload (0.1 to 8 M)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the particle-count sweep of the W2 workload (0.1 to 8 M)")
     ap.add_argument("--w5-n", type=int, default=4_000_000)
     ap.add_argument("--w5-steps", type=int, default=10_000)
     ap.add_argument("--w5-every", type=int, default=1_000)
@@ -582,8 +582,8 @@ def _side_legs(args, D, torch, box, ncell, stream, skin):
         leg("w3_floor_8M", lambda: _w3_leg(args, D, torch, stream))
     if args.w5:
         leg("w5_precision", lambda: _w5_leg(args, D, torch, stream))
-    if args.sweep:
-        leg("n_sweep", lambda: _sweep_leg(args, D, torch, stream))
+    if not args.no_sweep:
+        leg("n_sweep", lambda: _sweep_leg(args, D, torch, stream, skin))
     return out
 
 
@@ -609,17 +609,19 @@ def _error_leg(out, box, ncell):
     return errs
 
 
-def _sweep_leg(args, D, torch, stream):
+def _sweep_leg(args, D, torch, stream, skin):
     """Particle-steps/s of the MIXED form against the particle count, W2
-    radius law and packing (tiles of 8,000 relaxed spheres)."""
+    radius law and packing (tiles of 8,000 relaxed spheres), the headline's
+    skin, steps 1..200 from the initial state at every size (Sec. 5.2: the
+    paper's speed-up is comparable for all sizes above 0.1 M)."""
     from paper_1503_03553_gb300 import synth
     from paper_1503_03553_gb300.synth import grid_for, prepared
     rows = []
     for n in (100_000, 300_000, 1_000_000, 3_000_000, 8_000_000):
         box = prepared(synth.w2_polydisperse(n=n, seed=2), "mixed")
-        nc = grid_for(box)
-        steps = 200  # the same steps 1..200 from the initial state at every size
-        r = _throughput(D, torch, stream, [box], "mixed", [nc], steps, warmup=5)
+        nc = grid_for(box, skin=skin)
+        steps = 200
+        r = _throughput(D, torch, stream, [box], "mixed", [nc], steps, warmup=5, skins=[skin])
         r.update({"particles": box.n, "ncell": nc})
         rows.append(r)
     return rows

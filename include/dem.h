@@ -347,6 +347,15 @@ typedef struct {
 } dem_tuning;
 dem_status dem_autotune_layout(dem_ctx* ctx, int64_t steps, dem_tuning* out);
 
+/* Measured arithmetic peaks of the current GPU (a measurement utility with
+ * no counterpart in the paper): the FP32 and FP64 fused multiply-add rates,
+ * 2 flops each, of a kernel that keeps eight independent FMA chains per
+ * thread on eight 256-thread blocks per SM, timed with CUDA events on
+ * `stream` after a warm-up launch.  They are the denominators of the
+ * rooflines of arithmetic-bound kernels (the FP64 force path in
+ * particular).  Synchronises the stream; allocates nothing. */
+dem_status dem_measure_fma_rates(double* fp32_tflops, double* fp64_tflops, void* stream);
+
 /* The layout of one box now in use: cells per axis, skin [m], r_split [m]. */
 dem_status dem_get_layout(dem_ctx* ctx, int32_t box, int32_t ncell[3], double* skin,
                           double* r_split);

@@ -115,6 +115,7 @@ def lib() -> C.CDLL:
         "dem_get_resort_stats": (C.c_int, [vp, i64p]),
         "dem_autotune_layout": (C.c_int, [vp, C.c_int64, C.POINTER(dem_tuning)]),
         "dem_get_layout": (C.c_int, [vp, C.c_int32, ip, dp, dp]),
+        "dem_measure_fma_rates": (C.c_int, [dp, dp, vp]),
         "dem_autotune": (C.c_int, [vp, C.c_int64, dp, ip, ip]),
         "dem_sync": (C.c_int, [vp]),
         "dem_last_error": (C.c_char_p, [vp]),
@@ -352,6 +353,15 @@ def dem_autotune_layout(ctx, steps: int = 32) -> dict:
     t = dem_tuning()
     _check(ctx, lib().dem_autotune_layout(ctx, int(steps), C.byref(t)))
     return {f: getattr(t, f) for f, _ in dem_tuning._fields_ if f != "pad"}
+
+
+def dem_measure_fma_rates(stream=None) -> dict:
+    """Measured FP32 and FP64 FMA peaks of the current GPU [TFLOP/s]."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    a, b = C.c_double(), C.c_double()
+    _check(None, lib().dem_measure_fma_rates(C.byref(a), C.byref(b), C.c_void_p(s.cuda_stream)))
+    return {"fp32_tflops": a.value, "fp64_tflops": b.value}
 
 
 def dem_get_layout(ctx, box: int = 0) -> dict:

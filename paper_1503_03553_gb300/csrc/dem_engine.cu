@@ -207,9 +207,10 @@ void enqueue_fused(dem_ctx* ctx, int p, bool store_ft) {
     cudaEventRecord(ev[3], s);
     cudaEventRecord(ev[4], s);
   }
+  const int bsg = bs < 256 ? bs : 256;  // compiled for at most 256 threads
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
-  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q], nullptr,
-                                                          store_ft ? 1 : 0);
+  k_gather_integrate<M><<<blocks_for(d.N, bsg), bsg, 0, s>>>(d, ctx->ps[q], nullptr,
+                                                            store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -258,7 +259,8 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
   d.gate = nullptr;
   d.collect = ctx->collect;
   cudaStream_t s = ctx->stream;
-  const int bs = ctx->block;
+  // the sum + integrate kernel is compiled for at most 256 threads per block
+  const int bs = ctx->block < 256 ? ctx->block : 256;
   if (tm) cudaEventRecord(ev[3], s);
   k_pairs<M><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0]);
   if (tm) cudaEventRecord(ev[4], s);
@@ -965,6 +967,7 @@ static dem_status build_graph(dem_ctx* ctx, int p) {
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   int q = p;
   cudaError_t e = cudaSuccess;
+  const char* where = "";
   for (int k = 0; k < ctx->graph_steps && e == cudaSuccess; ++k) {
     const bool last = k == ctx->graph_steps - 1;
     if (ctx->fused) {
@@ -976,9 +979,13 @@ static dem_status build_graph(dem_ctx* ctx, int p) {
     const cudaGraphNode_t* deps = nullptr;
     const cudaGraphEdgeData* edges = nullptr;
     size_t ndeps = 0;
+    where = "capture info";
     e = cudaStreamGetCaptureInfo(ctx->stream, &cst, nullptr, &cg, &deps, &edges, &ndeps);
     cudaGraphConditionalHandle h{};
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, cg, 0, 0);
+    if (e == cudaSuccess) {
+      where = "conditional handle";
+      e = cudaGraphConditionalHandleCreate(&h, cg, 0, 0);
+    }
     if (e != cudaSuccess) break;
     k_decide<<<1, 32, 0, ctx->stream>>>(ctx->dev.vctl, ctx->always_resort ? 1 : 0, h, 1);
     e = cudaStreamGetCaptureInfo(ctx->stream, &cst, nullptr, &cg, &deps, &edges, &ndeps);
@@ -989,11 +996,13 @@ static dem_status build_graph(dem_ctx* ctx, int p) {
     cp.conditional.type = cudaGraphCondTypeIf;
     cp.conditional.size = 1;
     cudaGraphNode_t node = nullptr;
+    where = "conditional node";
     e = cudaGraphAddNode(&node, cg, deps, edges, ndeps, &cp);
     if (e == cudaSuccess)
       e = cudaStreamUpdateCaptureDependencies(ctx->stream, &node, nullptr, 1,
                                               cudaStreamSetCaptureDependencies);
     if (e != cudaSuccess) break;
+    where = "re-sort body";
     e = cudaStreamBeginCaptureToGraph(ctx->body_stream, cp.conditional.phGraph_out[0], nullptr,
                                       nullptr, 0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) break;
@@ -1001,6 +1010,7 @@ static dem_status build_graph(dem_ctx* ctx, int p) {
     cudaGraph_t body = nullptr;
     e = cudaStreamEndCapture(ctx->body_stream, &body);
     if (e != cudaSuccess) break;
+    where = "step kernels";
     enqueue_tail_any(ctx, last);
   }
   cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
@@ -1008,7 +1018,8 @@ static dem_status build_graph(dem_ctx* ctx, int p) {
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     cudaGetLastError();
-    return fail(ctx, DEM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    return fail(ctx, DEM_ERR_CUDA, std::string("graph capture (") + where + "): " +
+                                       cudaGetErrorString(e));
   }
   e = cudaGraphInstantiate(&ctx->gexec[p], g, 0);
   cudaGraphDestroy(g);
@@ -1250,6 +1261,65 @@ dem_status time_trial(dem_ctx* ctx, const Snapshot& sn, int64_t steps, cudaEvent
 }
 
 }  // namespace
+
+// ---- arithmetic peak probe -----------------------------------------------------
+namespace {
+
+// Eight independent fused multiply-add chains per thread (enough in flight
+// to keep the pipe busy); the result is stored, to a file-scope sink, only
+// under a condition the compiler cannot rule out (the chains stay in [0, 1]
+// and their sum is never negative), so the chains are not removed.
+__device__ double g_fma_sink;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_rate(int iters, T a, T b) {
+  T x[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) x[u] = (T)(threadIdx.x + u) * (T)1e-3;
+  for (int k = 0; k < iters; ++k) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = fma(x[u], a, b);
+  }
+  T sum = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) sum += x[u];
+  if (sum < (T)0) g_fma_sink = (double)sum;
+}
+
+template <typename T>
+dem_status fma_rate(cudaStream_t s, int nsm, int iters, double* tflops) {
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) || cudaEventCreate(&e1)) return DEM_ERR_CUDA;
+  const int blocks = nsm * 8;
+  k_fma_rate<T><<<blocks, 256, 0, s>>>(iters / 8, (T)0.999999, (T)1e-6);  // warm-up
+  cudaEventRecord(e0, s);
+  k_fma_rate<T><<<blocks, 256, 0, s>>>(iters, (T)0.999999, (T)1e-6);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e || ms <= 0.f) return DEM_ERR_CUDA;
+  const double flops = 2.0 * 8.0 * (double)iters * 256.0 * (double)blocks;
+  *tflops = flops / (ms * 1e-3) / 1e12;
+  return DEM_OK;
+}
+
+}  // namespace
+
+extern "C" dem_status dem_measure_fma_rates(double* fp32_tflops, double* fp64_tflops,
+                                            void* stream) {
+  if (!fp32_tflops || !fp64_tflops) return fail(nullptr, DEM_ERR_ARG, "null output");
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))
+    return fail(nullptr, DEM_ERR_CUDA, "no CUDA device");
+  cudaStream_t s = (cudaStream_t)stream;
+  dem_status st = fma_rate<float>(s, nsm, 1 << 14, fp32_tflops);
+  if (!st) st = fma_rate<double>(s, nsm, 1 << 10, fp64_tflops);
+  if (st) return fail(nullptr, st, "dem_measure_fma_rates: kernel timing failed");
+  return DEM_OK;
+}
 
 extern "C" dem_status dem_autotune_layout(dem_ctx* ctx, int64_t steps, dem_tuning* out) {
   if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");

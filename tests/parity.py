@@ -89,9 +89,10 @@ def gpu_run(boxes, precision, ncells, steps=1, stencil=STENCIL, **kw):
         ctx.close()
 
 
-def oracle_run(box, precision, ncell, stencil=STENCIL, hist=None):
+def oracle_run(box, precision, ncell, stencil=STENCIL, hist=None, parallel=False):
     """One oracle step from box's state; hist = (id_lo, id_hi, delta_t) is
-    the contact history to start from (none: a fresh start)."""
+    the contact history to start from (none: a fresh start); parallel=True
+    runs the oracle's OpenMP build (the same results, bit for bit)."""
     p = oracle_params(box, precision, ncell, stencil=stencil)
     cell, order = O.order(p, box.x)
     s = O.State(box.x, box.v, box.w, box.r, floor_wall=bool(box.floor_wall),
@@ -99,7 +100,7 @@ def oracle_run(box, precision, ncell, stencil=STENCIL, hist=None):
     if hist is not None:
         s.lo, s.hi, s.dt = hist
     x0, v0, w0 = s.x.copy(), s.v.copy(), s.w.copy()
-    out = O.step(p, s)
+    out = O.step(p, s, parallel=parallel)
     out.update(order=order, cell=cell, x=s.x, v=s.v, w=s.w, x0=x0, v0=v0, w0=w0,
                params=p)
     if hist is not None:
