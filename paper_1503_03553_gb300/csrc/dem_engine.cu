@@ -69,7 +69,7 @@ struct dem_ctx {
   // the per-particle Collide forms sort every step from one to the other.
   PState ps[2]{};
   CList cl[2]{};               // contact lists of the per-particle forms
-  VList vl[2]{};               // candidate lists: [0] current, [1] a re-sort's
+  VList vs{};                  // the candidate list a re-sort's search writes
   int* cs_cur = nullptr;       // cell starts of the current order
   int* cs_new = nullptr;       // cell starts of the order being built
   unsigned char* collect = nullptr;  // cells changed since the last sort
@@ -153,8 +153,18 @@ int launches_per_step(const dem_ctx* ctx) {
   if (ctx->fused) return 7 + (ctx->hwalls.empty() ? 0 : 1);
   return 3 + (ctx->hwalls.empty() ? 0 : 1);
 }
-// kernels a re-sort adds (cell scan x3, scatter, reorder, search, rows, commit)
-int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 8 + (ctx->split ? 1 : 0); }
+// kernels a re-sort adds (cell scan x3, scatter, reorder, search, row scan
+// x3, rows, commit)
+int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 11 + (ctx->split ? 1 : 0); }
+
+// which of the two row lists is current (read from the device; the stream
+// is synchronised)
+int current_rows(dem_ctx* ctx, cudaError_t* err) {
+  int rp = 0;
+  *err = cudaMemcpyAsync(&rp, ctx->dev.rpar, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (*err == cudaSuccess) *err = cudaStreamSynchronize(ctx->stream);
+  return rp ? 1 : 0;
+}
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -209,8 +219,7 @@ void enqueue_fused(dem_ctx* ctx, int p, bool store_ft) {
   }
   const int bsg = bs < 256 ? bs : 256;  // compiled for at most 256 threads
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
-  k_gather_integrate<M><<<blocks_for(d.N, bsg), bsg, 0, s>>>(d, ctx->ps[q], nullptr,
-                                                            store_ft ? 1 : 0);
+  k_gather_integrate<M><<<blocks_for(d.N, bsg), bsg, 0, s>>>(d, ctx->ps[q], store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -236,21 +245,31 @@ void enqueue_resort(dem_ctx* ctx, cudaStream_t rs, bool tm, cudaEvent_t* ev) {
       d.ccount, d.M_rank, d.scan_bsum,
       CellEpi{d.cstart, d.crange, d.cellbox, d.lin_of_rank, d.collect, ctx->chg, d.ccur}, d.gate);
   k_scatter<<<blocks_for(d.N, bs), bs, 0, rs>>>(d, ctx->ps[0]);
-  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vl[1].count);
+  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vs.count);
   if (tm) cudaEventRecord(ev[1], rs);
   // the search kernel is compiled for at most 256 threads per block
   const int bs_search = bs < 256 ? bs : 256;
   if (ctx->split) {
-    k_candidates<M, true><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
+    k_candidates<M, true><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vs);
     // large particles of size-binned boxes: one warp each, persistent grid
-    k_candidates_large<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
+    k_candidates_large<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[1], ctx->vs);
   } else {
-    k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
+    k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vs);
   }
   if (tm) cudaEventRecord(ev[2], rs);
-  k_rows<M><<<blocks_for(d.N, 256), 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[0], ctx->vl[1]);
-  k_commit<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vl[0], ctx->vl[1],
-                                            ctx->cs_new, ctx->cs_cur);
+  // rows of the new candidate list: lengths, offsets (scan), entries ordered
+  // by partner id with their history, then the commit
+  const RowLenIn rin{ctx->vs.oc, d.icnt, d.K};
+  const RowEpi repi{{d.rl[0].rs, d.rl[1].rs}, {d.rl[0].cnt, d.rl[1].cnt},
+                    {d.rl[0].count, d.rl[1].count}, d.rpar, ctx->vs.oc, d.icnt, d.K, d.N, d.Emax,
+                    d.status};
+  const int nbr = blocks_for(d.N, kScanTile);
+  k_scanf_reduce<int, RowLenIn><<<nbr, kScanThreads, 0, rs>>>(rin, d.N, d.scan_bsum, d.gate);
+  k_scan_top<<<1, kScanTopThreads, 0, rs>>>(d.scan_bsum, nbr, nullptr, 0, d.status, 0u, d.gate);
+  k_scanf_apply<int, RowLenIn, RowEpi><<<nbr, kScanThreads, 0, rs>>>(rin, d.N, d.scan_bsum, repi,
+                                                                     d.gate);
+  k_rows<M><<<blocks_for(d.N, 256), 256, 0, rs>>>(d, ctx->ps[1], ctx->vs);
+  k_commit<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->cs_new, ctx->cs_cur);
 }
 
 template <int M>
@@ -262,11 +281,10 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
   // the sum + integrate kernel is compiled for at most 256 threads per block
   const int bs = ctx->block < 256 ? ctx->block : 256;
   if (tm) cudaEventRecord(ev[3], s);
-  k_pairs<M><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0]);
-  if (tm) cudaEventRecord(ev[4], s);
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
-  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0], ctx->vl[0].flag,
-                                                          store_ft ? 1 : 0);
+  if (tm) cudaEventRecord(ev[4], s);
+  k_step<M><<<blocks_for(d.N, 32 * kStepWarps), 32 * kStepWarps, 0, s>>>(d, ctx->ps[0],
+                                                                         store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -390,8 +408,8 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   for (int p = 0; p < 2; ++p) {
     ctx->ps[p] = PState{};
     ctx->cl[p] = CList{};
-    ctx->vl[p] = VList{};
   }
+  ctx->vs = VList{};
   ctx->cs_cur = ctx->cs_new = nullptr;
   ctx->collect = ctx->chg = nullptr;
   ctx->staging = nullptr;
@@ -582,6 +600,8 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   long long cmax = (long long)N * (ctx->fused ? std::max(4, ctx->K / 2) : std::max(4, ctx->K / 4));
   if (cmax > (1ll << 31) - 1) cmax = (1ll << 31) - 1;
   ctx->Cmax = (int)std::max(1ll, cmax);
+  // candidate rows: every pair in both of its members' rows
+  const long long emax = std::min<long long>(2 * (long long)ctx->Cmax, (1ll << 31) - 1);
   ctx->ko = (int)std::max(1ll, cmax / std::max(1ll, N));
 
   // ---- device allocations ----------------------------------------------------
@@ -591,6 +611,7 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   d.N = ctx->N;
   d.K = ctx->K;
   d.Cmax = ctx->Cmax;
+  d.Emax = (int)emax;
   d.M_lin = ctx->M_lin;
   d.M_rank = ctx->M_rank;
   d.nbox = (int)ctx->hbox.size();
@@ -623,15 +644,15 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   }
   d.icnt = (int*)A(sizeof(int) * n);
   d.prev = (int*)A(sizeof(int) * n);
-  d.Fc = A(v4_bytes(M) * ctx->Cmax);
-  d.nFc = A(v4_bytes(M) * ctx->Cmax);
+  if (ctx->fused) {
+    d.Fc = A(v4_bytes(M) * ctx->Cmax);
+    d.nFc = A(v4_bytes(M) * ctx->Cmax);
+  }
   if (ctx->fused) {
     d.Ffused = A(v4_bytes(M) * n);
     d.Tfused = A(v4_bytes(M) * n);
   } else {
     d.inrow = (int2*)A(sizeof(int2) * n * ctx->K);
-    d.frow = (int*)A(sizeof(int) * n * ctx->K);
-    d.fcnt = (int*)A(sizeof(int) * n);
     d.xb = A(pos_bytes(M) * n);
     d.yb = A(pos_bytes(M) * n);
     d.zb = A(pos_bytes(M) * n);
@@ -674,17 +695,27 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
       c.oc = (int*)A(sizeof(int) * n);
       c.count = (int*)A(sizeof(int));
     } else {
-      VList& c = ctx->vl[p];
-      c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
-      c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
-      c.dx = A(dt_bytes(M) * ctx->Cmax);
-      c.dy = A(dt_bytes(M) * ctx->Cmax);
-      c.dz = A(dt_bytes(M) * ctx->Cmax);
-      c.flag = (unsigned char*)A(ctx->Cmax);
-      c.hs = (int*)A(sizeof(int) * n);
-      c.oc = (int*)A(sizeof(int) * n);
-      c.count = (int*)A(sizeof(int));
+      RowList& r = d.rl[p];
+      r.rs = (int*)A(sizeof(int) * n);
+      r.cnt = (int*)A(sizeof(int) * n);
+      r.fp = (int*)A(sizeof(int) * (size_t)d.Emax);
+      r.flag = (unsigned char*)A((size_t)d.Emax);
+      r.dx = A(dt_bytes(M) * (size_t)d.Emax);
+      r.dy = A(dt_bytes(M) * (size_t)d.Emax);
+      r.dz = A(dt_bytes(M) * (size_t)d.Emax);
+      r.count = (int*)A(sizeof(int));
     }
+  }
+  if (!ctx->fused) {
+    VList& c = ctx->vs;
+    c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
+    c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
+    c.hs = (int*)A(sizeof(int) * n);
+    c.oc = (int*)A(sizeof(int) * n);
+    c.count = (int*)A(sizeof(int));
+    d.Fe = A(v4_bytes(M) * (size_t)d.Emax);
+    d.Ne = A(v4_bytes(M) * (size_t)d.Emax);
+    d.rpar = (int*)A(sizeof(int));
   }
   ctx->staging = (double*)A(sizeof(double) * 16 * (size_t)std::max(1, max_cap));
   ctx->staging_i = (int*)A(sizeof(int) * 2 * (size_t)std::max(1, max_cap));
@@ -725,14 +756,19 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   if (!e) e = cudaMemsetAsync(ctx->cs_new, 0, sizeof(int) * std::max(1, ctx->M_rank), s);
   if (!e) e = cudaMemsetAsync(d.vctl, 0, sizeof(unsigned) * kCtlWords, s);
   for (int p = 0; p < 2 && !e; ++p) {
-    int* oc = ctx->fused ? ctx->cl[p].oc : ctx->vl[p].oc;
-    int* hs = ctx->fused ? ctx->cl[p].hs : ctx->vl[p].hs;
-    int* cnt = ctx->fused ? ctx->cl[p].count : ctx->vl[p].count;
+    int* oc = ctx->fused ? ctx->cl[p].oc : d.rl[p].cnt;
+    int* hs = ctx->fused ? ctx->cl[p].hs : d.rl[p].rs;
+    int* cnt = ctx->fused ? ctx->cl[p].count : d.rl[p].count;
     e = cudaMemsetAsync(oc, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(hs, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(cnt, 0, sizeof(int), s);
   }
-  if (!e && !ctx->fused) e = cudaMemsetAsync(d.fcnt, 0, sizeof(int) * n, s);
+  if (!e && !ctx->fused) {
+    e = cudaMemsetAsync(ctx->vs.oc, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(ctx->vs.hs, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(ctx->vs.count, 0, sizeof(int), s);
+    if (!e) e = cudaMemsetAsync(d.rpar, 0, sizeof(int), s);
+  }
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return bail(DEM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
   return DEM_OK;
@@ -876,7 +912,7 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
   if (st) return st;
   // the box's history is empty: no slot of the box holds a stored contact
   for (int q = 0; q < 2; ++q)
-    CK(cudaMemsetAsync((ctx->fused ? ctx->cl[q].oc : ctx->vl[q].oc) + B.pbase, 0,
+    CK(cudaMemsetAsync((ctx->fused ? ctx->cl[q].oc : ctx->dev.rl[q].cnt) + B.pbase, 0,
                        sizeof(int) * B.cap, s));
   // the next sort starts from the order the particles were given in, and
   // the next step re-sorts
@@ -1471,12 +1507,15 @@ dem_status dem_get_resort_stats(dem_ctx* ctx, int64_t out[4]) {
   if (ctx->fused) return DEM_OK;
   unsigned ctl[kCtlWords] = {};
   int cnt = 0;
+  cudaError_t e;
+  const int rp = current_rows(ctx, &e);
+  CK(e);
   CK(cudaMemcpyAsync(ctl, ctx->dev.vctl, sizeof(ctl), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&cnt, ctx->vl[0].count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&cnt, ctx->dev.rl[rp].count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   out[0] = ctl[kCtlResorts];
   out[1] = launches_per_resort(ctx);
-  out[2] = std::min(cnt, ctx->Cmax);
+  out[2] = cnt / 2;  // every candidate pair is in two rows
   out[3] = ctx->steps_done;
   return DEM_OK;
 }
@@ -1558,6 +1597,90 @@ dem_status dem_get_order(dem_ctx* ctx, int32_t box, int32_t* id_by_slot,
   return DEM_OK;
 }
 
+// Entry values of a row list as doubles (delta_t components, V4 records).
+static double dt_value(int mode, const std::vector<unsigned char>& raw, long long k) {
+  double val;
+  if (mode == kMIXED) {
+    float hl[2];
+    std::memcpy(hl, raw.data() + 8 * k, 8);
+    val = (double)hl[0] + (double)hl[1];
+  } else if (mode == kFP64) {
+    std::memcpy(&val, raw.data() + 8 * k, 8);
+  } else {
+    float f;
+    std::memcpy(&f, raw.data() + 4 * k, 4);
+    val = f;
+  }
+  return val;
+}
+static double v4_value(int mode, const std::vector<unsigned char>& buf, long long k, int a) {
+  if (mode == kFP64) {
+    double v;
+    std::memcpy(&v, buf.data() + 32 * k + 8 * a, 8);
+    return v;
+  }
+  float v;
+  std::memcpy(&v, buf.data() + 16 * k + 4 * a, 4);
+  return (double)v;
+}
+
+// The contacts of the last step from the current candidate rows: each pair
+// in contact once, from its lower-id member's row (ids, delta_t, and the
+// recorded force and n x F).
+static dem_status download_rows(dem_ctx* ctx, std::vector<int2>& hid, std::vector<double>& dts,
+                                std::vector<double>* F, std::vector<double>* nF) {
+  cudaStream_t s = ctx->stream;
+  hid.clear();
+  dts.clear();
+  const int N = ctx->N;
+  if (N == 0) return DEM_OK;
+  cudaError_t e;
+  const int rp = current_rows(ctx, &e);
+  CK(e);
+  const RowList& rl = ctx->dev.rl[rp];
+  std::vector<int> rs(N), rc(N), ids(N);
+  int total = 0;
+  CK(cudaMemcpyAsync(rs.data(), rl.rs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rc.data(), rl.cnt, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(ids.data(), ctx->ps[0].id, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&total, rl.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const long long top = std::min<long long>(total, ctx->dev.Emax);
+  const size_t eb = dt_bytes(ctx->mode), vb = v4_bytes(ctx->mode);
+  std::vector<int> fp(std::max(1ll, top));
+  std::vector<unsigned char> fl(std::max(1ll, top)), raw[3], fr, nr;
+  for (int a = 0; a < 3; ++a) raw[a].resize(eb * std::max(1ll, top));
+  if (top > 0) {
+    CK(cudaMemcpyAsync(fp.data(), rl.fp, sizeof(int) * top, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(fl.data(), rl.flag, top, cudaMemcpyDeviceToHost, s));
+    void* const comps[3] = {rl.dx, rl.dy, rl.dz};
+    for (int a = 0; a < 3; ++a)
+      CK(cudaMemcpyAsync(raw[a].data(), comps[a], eb * top, cudaMemcpyDeviceToHost, s));
+    if (F) {
+      fr.resize(vb * top);
+      nr.resize(vb * top);
+      CK(cudaMemcpyAsync(fr.data(), ctx->dev.Fe, vb * top, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(nr.data(), ctx->dev.Ne, vb * top, cudaMemcpyDeviceToHost, s));
+    }
+    CK(cudaStreamSynchronize(s));
+  }
+  for (const BoxDev& B : ctx->hbox)
+    for (int g = B.pbase; g < B.pbase + B.nlive; ++g)
+      for (int k = 0; k < rc[g]; ++k) {
+        const long long q = (long long)rs[g] + k;
+        if (q >= top) break;
+        if (!(fp[q] & 1) || !fl[q]) continue;  // the lower-id member's entry of a contact
+        hid.push_back(make_int2(ids[g], ids[fp[q] >> 1]));
+        for (int a = 0; a < 3; ++a) dts.push_back(dt_value(ctx->mode, raw[a], q));
+        if (F)
+          for (int a = 0; a < 3; ++a) {
+            F->push_back(v4_value(ctx->mode, fr, q, a));
+            nF->push_back(v4_value(ctx->mode, nr, q, a));
+          }
+      }
+  return DEM_OK;
+}
+
 // Download the current contact list of all boxes as host vectors, walking
 // each particle's (start, count) index: works for the dense list, the fused
 // layout's per-slot blocks and a list restored by dem_set_contacts.
@@ -1566,16 +1689,15 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
                                 std::vector<double>& dts,
                                 std::vector<double>* F = nullptr,
                                 std::vector<double>* nF = nullptr) {
+  if (!ctx->fused) return download_rows(ctx, hid, dts, F, nF);
   cudaStream_t s = ctx->stream;
-  // the per-particle forms' list of the last step, or the candidate list
-  // (its pairs in contact in the last step carry flag 1)
-  const int* c_hs = ctx->fused ? ctx->cl[ctx->parity].hs : ctx->vl[0].hs;
-  const int* c_oc = ctx->fused ? ctx->cl[ctx->parity].oc : ctx->vl[0].oc;
-  const int2* c_hid = ctx->fused ? ctx->cl[ctx->parity].hid : ctx->vl[0].hid;
-  void* const comps[3] = {ctx->fused ? ctx->cl[ctx->parity].dx : ctx->vl[0].dx,
-                          ctx->fused ? ctx->cl[ctx->parity].dy : ctx->vl[0].dy,
-                          ctx->fused ? ctx->cl[ctx->parity].dz : ctx->vl[0].dz};
-  const unsigned char* c_flag = ctx->fused ? nullptr : ctx->vl[0].flag;
+  // the per-particle forms' list of the last step
+  const int* c_hs = ctx->cl[ctx->parity].hs;
+  const int* c_oc = ctx->cl[ctx->parity].oc;
+  const int2* c_hid = ctx->cl[ctx->parity].hid;
+  void* const comps[3] = {ctx->cl[ctx->parity].dx, ctx->cl[ctx->parity].dy,
+                          ctx->cl[ctx->parity].dz};
+  const unsigned char* c_flag = nullptr;
   const int N = ctx->N;
   std::vector<int> rs(N), rc(N);
   hid.clear();
@@ -1755,6 +1877,64 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
     if (slots[k].x < 0 || slots[k].y < 0)
       return fail(ctx, DEM_ERR_STATE, "contact of a particle that holds no slot");
   }
+  auto encode = [&](std::vector<unsigned char>& dst, size_t k, double val) {
+    if (ctx->mode == kMIXED) {
+      float hl[2];
+      hl[0] = (float)val;
+      hl[1] = (float)(val - (double)hl[0]);
+      std::memcpy(dst.data() + 8 * k, hl, 8);
+    } else if (ctx->mode == kFP64) {
+      std::memcpy(dst.data() + 8 * k, &val, 8);
+    } else {
+      float f = (float)val;
+      std::memcpy(dst.data() + 4 * k, &f, 4);
+    }
+  };
+  if (!ctx->fused) {
+    // the contact-list pipeline's rows: each pair in both members' rows, in
+    // increasing partner id; the re-sort of the next step carries them over
+    if (2ll * nc > ctx->dev.Emax) return fail(ctx, DEM_ERR_CAPACITY, "contact list capacity");
+    std::vector<std::vector<std::pair<int, int>>> rows(N);  // (partner id, contact)
+    for (int k = 0; k < nc; ++k) {
+      rows[slots[k].x].push_back({all[k].first.y, k});
+      rows[slots[k].y].push_back({all[k].first.x, k});
+    }
+    std::vector<int> rs(N, 0), rc(N, 0), fp(std::max(1, 2 * nc));
+    const size_t eb = dt_bytes(ctx->mode);
+    std::vector<unsigned char> comp[3];
+    for (int a = 0; a < 3; ++a) comp[a].resize(eb * std::max(1, 2 * nc));
+    int at = 0;
+    for (int g = 0; g < N; ++g) {
+      std::sort(rows[g].begin(), rows[g].end());
+      rs[g] = at;
+      rc[g] = (int)rows[g].size();
+      for (const auto& pr : rows[g]) {
+        const int k = pr.second;
+        const bool low = slots[k].x == g;
+        fp[at] = ((low ? slots[k].y : slots[k].x) << 1) | (low ? 1 : 0);
+        for (int a = 0; a < 3; ++a) encode(comp[a], (size_t)at, all[k].second[a]);
+        ++at;
+      }
+    }
+    cudaError_t e;
+    const int rp = current_rows(ctx, &e);
+    CK(e);
+    const RowList& rl = ctx->dev.rl[rp];
+    if (at > 0) {
+      CK(cudaMemcpyAsync(rl.fp, fp.data(), sizeof(int) * at, cudaMemcpyHostToDevice, s));
+      void* const dst[3] = {rl.dx, rl.dy, rl.dz};
+      for (int a = 0; a < 3; ++a)
+        CK(cudaMemcpyAsync(dst[a], comp[a].data(), eb * at, cudaMemcpyHostToDevice, s));
+      CK(cudaMemsetAsync(rl.flag, 1, at, s));
+    }
+    CK(cudaMemcpyAsync(rl.rs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(rl.cnt, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+    *ctx->h_count = at;
+    CK(cudaMemcpyAsync(rl.count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->dev.vctl + kCtlRequest, 1, sizeof(unsigned), s));
+    CK(cudaStreamSynchronize(s));
+    return DEM_OK;
+  }
   std::vector<int> order(nc);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
@@ -1771,44 +1951,21 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
     const int lo = p2[k].x;
     if (rc[lo] == 0) rs[lo] = k;
     rc[lo]++;
-    for (int a = 0; a < 3; ++a) {
-      double val = all[src].second[a];
-      if (ctx->mode == kMIXED) {
-        float hl[2];
-        hl[0] = (float)val;
-        hl[1] = (float)(val - (double)hl[0]);
-        std::memcpy(comp[a].data() + 8 * k, hl, 8);
-      } else if (ctx->mode == kFP64) {
-        std::memcpy(comp[a].data() + 8 * k, &val, 8);
-      } else {
-        float f = (float)val;
-        std::memcpy(comp[a].data() + 4 * k, &f, 4);
-      }
-    }
+    for (int a = 0; a < 3; ++a) encode(comp[a], (size_t)k, all[src].second[a]);
   }
-  // the per-particle forms read it as the previous step's list; the
-  // contact-list pipeline as its current candidate list (every pair in
-  // contact), carried into the list of the re-sort the next step makes
-  int2* c_hid = ctx->fused ? ctx->cl[ctx->parity].hid : ctx->vl[0].hid;
-  int2* c_pair = ctx->fused ? ctx->cl[ctx->parity].pair : ctx->vl[0].pair;
-  void* const c_d[3] = {ctx->fused ? ctx->cl[ctx->parity].dx : ctx->vl[0].dx,
-                        ctx->fused ? ctx->cl[ctx->parity].dy : ctx->vl[0].dy,
-                        ctx->fused ? ctx->cl[ctx->parity].dz : ctx->vl[0].dz};
-  int* c_hs = ctx->fused ? ctx->cl[ctx->parity].hs : ctx->vl[0].hs;
-  int* c_oc = ctx->fused ? ctx->cl[ctx->parity].oc : ctx->vl[0].oc;
-  int* c_count = ctx->fused ? ctx->cl[ctx->parity].count : ctx->vl[0].count;
+  // the per-particle forms read it as the previous step's list
+  const CList& c = ctx->cl[ctx->parity];
   if (nc > 0) {
-    CK(cudaMemcpyAsync(c_hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c_pair, p2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c.pair, p2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    void* const c_d[3] = {c.dx, c.dy, c.dz};
     for (int a = 0; a < 3; ++a)
       CK(cudaMemcpyAsync(c_d[a], comp[a].data(), eb * nc, cudaMemcpyHostToDevice, s));
-    if (!ctx->fused) CK(cudaMemsetAsync(ctx->vl[0].flag, 1, nc, s));
   }
-  CK(cudaMemcpyAsync(c_hs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(c_oc, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c.hs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c.oc, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
   *ctx->h_count = nc;
-  CK(cudaMemcpyAsync(c_count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
-  if (!ctx->fused) CK(cudaMemsetAsync(ctx->dev.vctl + kCtlRequest, 1, sizeof(unsigned), s));
+  CK(cudaMemcpyAsync(c.count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaStreamSynchronize(s));
   return DEM_OK;
 }
@@ -1822,13 +1979,13 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
   double* part = ctx->staging + 8;
   const int nparts = std::max(1, std::min(512, blocks_for(ctx->hbox[box].nlive, 256)));
   const int p = ctx->parity;
-  const int* hs = ctx->fused ? ctx->cl[p].hs : ctx->vl[0].hs;
-  const int* oc = ctx->fused ? ctx->cl[p].oc : ctx->vl[0].oc;
-  const unsigned char* fl = ctx->fused ? nullptr : ctx->vl[0].flag;
+  const int* hs = ctx->fused ? ctx->cl[p].hs : nullptr;
+  const int* oc = ctx->fused ? ctx->cl[p].oc : nullptr;
+  const int rows = ctx->fused ? 0 : 1;
   switch (ctx->mode) {
-    case kFP64: k_stats<kFP64><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
-    case kMIXED: k_stats<kMIXED><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
-    default: k_stats<kFP32><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
+    case kFP64: k_stats<kFP64><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, nullptr, rows, box, part); break;
+    case kMIXED: k_stats<kMIXED><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, nullptr, rows, box, part); break;
+    default: k_stats<kFP32><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, nullptr, rows, box, part); break;
   }
   k_stats_final<<<1, 32, 0, s>>>(part, nparts, dout);
   CK(cudaGetLastError());

@@ -96,6 +96,26 @@ struct VList {
   int* count;   // entries (device scalar)
 };
 
+// The candidate rows of the contact-list pipeline, built at a re-sort from
+// the candidate list: for every slot, all its candidate pairs (both members
+// hold the pair), in increasing partner id, stored contiguously (CSR over
+// slots).  Each entry keeps that pair's tangential history and whether the
+// pair was in contact in the last step; both copies of a pair's history are
+// computed by the same arithmetic in the same orientation (lower id first),
+// so they stay equal.  Two of them, current and the one a re-sort builds;
+// a device word says which is current.
+struct RowList {
+  int* rs;      // by slot: first entry of its row (a scan over all slots)
+  int* cnt;     // by slot: entries in its row
+  int* fp;      // by entry: partner slot << 1 | 1 if the row's slot is the
+                // pair's lower-id member
+  unsigned char* flag;  // by entry: 1 if the pair was in contact in the last step
+  void* dx;     // by entry: delta_t after the last step (DT), zero unless
+  void* dy;     // in contact then
+  void* dz;
+  int* count;   // entries (device scalar)
+};
+
 // One parity of the contact list of the per-particle Collide forms: the
 // pairs of one step.
 struct CList {
@@ -154,9 +174,12 @@ struct Dev {
   void* Fout;    // V4 per slot: total force of the last step
   void* Tout;    // V4 per slot: total torque of the last step
   // contact-list pipeline
-  int* frow;     // N x K: every candidate pair of a slot (entry << 1 | 1 if
-                 // the slot is the lower-id member), in increasing partner id
-  int* fcnt;     // their number per slot
+  RowList rl[2];         // candidate rows; *rpar says which one is current
+  int* rpar;             // device word: index of the current rows
+  void* Fe;      // V4 by entry: force of the pair on the row's slot's pair
+  void* Ne;      // V4 by entry: n x F (recorded on the lower-id member's
+                 // entry of each pair in contact, for the contact output)
+  int Emax;      // entry capacity of a row list
   void* xb;      // P per slot: position at the last re-sort (skin test);
   void* yb;      // null for the per-particle Collide forms
   void* zb;
@@ -1691,175 +1714,232 @@ __device__ __forceinline__ bool pair_in_contact(const BoxDev& B, const PState& b
   return pred_abs(pi, pj, B);
 }
 
-// One warp takes kPairTile candidates: each lane tests kPairU of them (their
-// loads in flight together), the pairs in contact are compacted by ballot into
-// a warp-local queue in shared memory, and the warp then computes their
-// forces 32 at a time with every lane busy.  A pair that left contact loses
-// its history.  Every output is written at the pair's own list entry.
-constexpr int kPairU = 4;
-constexpr int kPairTile = 32 * kPairU;
-constexpr int kPairWarps = 8;
+// ---------------------------------------------------------------------------
+// contact-list pipeline, at a re-sort (after the search wrote the candidate
+// list vs in the new slot order of b): each slot's row holds every
+// candidate pair of the slot, the pairs it found (its block of vs) and the
+// pairs its partners found (its incoming row), ordered by partner id; the
+// rows are stored one after another (CSR), at offsets from a scan of their
+// lengths, and each entry takes the pair's history from the current rows
+// (old slots, reached through the reorder's previous-slot map).
+// ---------------------------------------------------------------------------
 
-template <int M>
-__global__ void __launch_bounds__(32 * kPairWarps, 4)
-k_pairs(Dev d, PState b, VList vl) {
-  using T = Tr<M>;
-  using V4 = typename T::V4;
-  using DT = typename T::DT;
-  __shared__ int qbuf[kPairWarps][kPairTile];
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  int* q = qbuf[wi];
-  const int nc = min(*vl.count, d.Cmax);
-  const int nw = gridDim.x * kPairWarps;
-  int mbox = -1;
-  float m_ov = 0.0f, m_ratio = 0.0f;
-  for (int t0 = (blockIdx.x * kPairWarps + wi) * kPairTile; t0 < nc; t0 += nw * kPairTile) {
-    int2 pr[kPairU];
-#pragma unroll
-    for (int u = 0; u < kPairU; ++u) {
-      const int c = t0 + u * 32 + lane;
-      pr[u] = c < nc ? vl.pair[c] : make_int2(-1, -1);
-    }
-    int qn = 0;
-#pragma unroll
-    for (int u = 0; u < kPairU; ++u) {
-      const int c = t0 + u * 32 + lane;
-      bool hit = false;
-      if (pr[u].x >= 0) {
-        const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[pr[u].x]];
-        hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
-        if (!hit && vl.flag[c]) {
-          ((DT*)vl.dx)[c] = DT{};
-          ((DT*)vl.dy)[c] = DT{};
-          ((DT*)vl.dz)[c] = DT{};
-          vl.flag[c] = 0;
-        }
-      }
-      const unsigned bal = __ballot_sync(full, hit);
-      if (hit) q[qn + __popc(bal & lt)] = c;
-      qn += __popc(bal);
-    }
-    __syncwarp();
-    for (int k = 0; k < qn; k += 32) {
-      if (k + lane < qn) {
-        const int c = q[k + lane];
-        const int2 p = vl.pair[c];
-        const int box = d.nbox == 1 ? 0 : d.slot_box[p.x];
-        const BoxDev& B = d.boxes[box];
-        PairOut<M> o;
-        pair_law<M>(b, B, p.x, p.y, ((const DT*)vl.dx)[c], ((const DT*)vl.dy)[c],
-                    ((const DT*)vl.dz)[c], o);
-        ((DT*)vl.dx)[c] = o.nx;
-        ((DT*)vl.dy)[c] = o.ny;
-        ((DT*)vl.dz)[c] = o.nz;
-        vl.flag[c] = 1;
-        st4((V4*)d.Fc + c, o.F4);
-        st4((V4*)d.nFc + c, o.N4);
-        if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
-      }
-    }
-    __syncwarp();
+// row length of a slot: its own pairs plus the incoming ones, at most K
+struct RowLenIn {
+  const int* oc;
+  const int* icnt;
+  int K;
+  __device__ int operator()(int i) const { return min(oc[i] + icnt[i], K); }
+};
+
+// block scan of a functor's values (the row lengths) with the same
+// three-pass structure as the cell scan
+template <typename T, class In>
+__global__ void __launch_bounds__(kScanThreads)
+k_scanf_reduce(In in, int n, T* __restrict__ bsum, const unsigned* gate) {
+  if (gated_off(gate)) return;
+  const int base = blockIdx.x * kScanTile;
+  T s = 0;
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    const int idx = base + k;
+    if (idx < n) s += in(idx);
   }
-  flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ T ws[kScanThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T t = 0;
+    for (int q = 0; q < kScanThreads / 32; ++q) t += ws[q];
+    bsum[blockIdx.x] = t;
+  }
 }
 
-// ---------------------------------------------------------------------------
-// contact-list pipeline, at a re-sort (after the search wrote the new
-// candidate list vn in the new slot order of b): each slot's row of all its
-// candidate pairs, ordered by partner id (the order of the force sum, which
-// then does not depend on slots, re-sorts or timing), and the history of the
-// pairs it found carried over from the current list vo (old slots, reached
-// through the reorder's previous-slot map).  d.row, free after the search,
-// holds the partner ids while a row is ordered.
-// ---------------------------------------------------------------------------
+template <typename T, class In, class Epi>
+__global__ void __launch_bounds__(kScanThreads)
+k_scanf_apply(In in, int n, const T* __restrict__ bsum, Epi epi, const unsigned* gate) {
+  if (gated_off(gate)) return;
+  __shared__ T buf[kScanTile];
+  __shared__ T tot;
+  const int base = blockIdx.x * kScanTile;
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    const int idx = base + k;
+    buf[k] = idx < n ? in(idx) : T(0);
+  }
+  __syncthreads();
+  T v[kScanItems];
+  T sum = 0;
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    v[q] = buf[threadIdx.x * kScanItems + q];
+    sum += v[q];
+  }
+  T pre = block_excl_scan<kScanThreads, T>(sum, &tot) + bsum[blockIdx.x];
+#pragma unroll
+  for (int q = 0; q < kScanItems; ++q) {
+    buf[threadIdx.x * kScanItems + q] = pre;
+    pre += v[q];
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
+    const int idx = base + k;
+    if (idx < n) epi(idx, in(idx), buf[k]);
+  }
+}
+
+// row starts and lengths of the new rows (the row list that is not current,
+// 1 - *rpar) and their total; a slot with more candidates than a row holds
+// sets the row-overflow bit, more entries than a row list holds the
+// list-overflow bit
+struct RowEpi {
+  int* rs[2];
+  int* cnt[2];
+  int* count[2];
+  const int* rpar;
+  const int* oc;
+  const int* icnt;
+  int K, N, Emax;
+  unsigned* status;
+  __device__ void operator()(int i, int len, int pre) const {
+    const int w = 1 - *rpar;
+    rs[w][i] = pre;
+    cnt[w][i] = len;
+    if (oc[i] + icnt[i] > K) atomicOr(status, kStRowOverflow);
+    if (i == N - 1) {
+      const long long tot = (long long)pre + len;
+      if (tot > Emax) atomicOr(status, kStListOverflow);
+      *count[w] = (int)min(tot, (long long)Emax);
+    }
+  }
+};
+
+constexpr int kRowSort = 16;  // rows up to this length are ordered in registers
+
 template <int M>
 __global__ void __launch_bounds__(256)
-k_rows(Dev d, PState b, VList vo, VList vn) {
+k_rows(Dev d, PState b, VList vs) {
   if (gated_off(d.gate)) return;
   using DT = typename Tr<M>::DT;
+  const int rp = *d.rpar;
+  const RowList ro = rp ? d.rl[1] : d.rl[0];  // current rows (old slots)
+  const RowList rn = rp ? d.rl[0] : d.rl[1];  // the rows being built
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
-  const BoxDev& B = d.boxes[d.slot_box[i]];
-  if (i - B.pbase >= B.nlive) {
-    d.fcnt[i] = 0;
-    return;
-  }
   const int K = d.K;
-  const int own = vn.oc[i], hs = vn.hs[i];
-  const int inc = d.icnt[i];
-  if (own + inc > K) flag(d.status, kStRowOverflow);
+  const int base = rn.rs[i];
+  // after an overflow (flagged by the scan) only the part below the
+  // capacity is written, and read
+  const int n = min(rn.cnt[i], d.Emax - base);
+  if (n <= 0) return;
+  const int own = vs.oc[i], hs = vs.hs[i];
+  const int* __restrict__ ids = b.id;
+  // (partner id, partner slot << 1 | low) of the row's entries, then ordered
+  // by partner id: in registers for short rows, in place in the row (with
+  // d.row, free after the search, holding the keys) otherwise
+  int key[kRowSort], val[kRowSort];
   int* kr = d.row + (size_t)i * K;
-  int* vr = d.frow + (size_t)i * K;
-  int n = 0;
-  auto insert = [&](int key, int val) {
-    if (n >= K) return;
-    int pos = n;
-    while (pos > 0 && kr[pos - 1] > key) {
-      kr[pos] = kr[pos - 1];
-      vr[pos] = vr[pos - 1];
-      --pos;
+  int* vr = rn.fp + base;
+  const bool small = n <= kRowSort;
+  int m = 0;
+  auto put = [&](int k2, int v2) {
+    if (m >= n) return;
+    if (small) {
+#pragma unroll
+      for (int q = 0; q < kRowSort; ++q)
+        if (q == m) {
+          key[q] = k2;
+          val[q] = v2;
+        }
+    } else {
+      kr[m] = k2;
+      vr[m] = v2;
     }
-    kr[pos] = key;
-    vr[pos] = val;
-    ++n;
+    ++m;
   };
   for (int k = 0; k < own; ++k) {
-    const int c = hs + k;
-    const int2 pr = vn.pair[c];
+    const int2 pr = vs.pair[hs + k];
     const bool low = pr.x == i;
-    insert(b.id[low ? pr.y : pr.x], (c << 1) | (low ? 1 : 0));
-    // history: the pair in the current list, in the block of whichever of
-    // its particles found it then
-    const int si = d.prev[pr.x], sj = d.prev[pr.y];
-    int found = -1;
-    for (int u = 0; u < 2 && found < 0; ++u) {
-      const int s0 = u == 0 ? si : sj;
-      const int os = vo.hs[s0], on = vo.oc[s0];
-      for (int e = 0; e < on; ++e) {
-        const int2 h = vo.pair[os + e];
-        if (h.x == si && h.y == sj) {
-          found = os + e;
-          break;
+    const int j = low ? pr.y : pr.x;
+    put(ids[j], (j << 1) | (low ? 1 : 0));
+  }
+  const int inc = min(d.icnt[i], K);
+  for (int k = 0; k < inc; ++k) {
+    const int2 e = d.inrow[(size_t)i * K + k];
+    const int j = e.y >> 1;
+    put(ids[j], (j << 1) | (e.y & 1));
+  }
+  if (small) {
+    // insertion sort with compile-time indices (registers)
+#pragma unroll
+    for (int a = 1; a < kRowSort; ++a) {
+#pragma unroll
+      for (int q = a; q > 0; --q) {
+        if (q < m && key[q - 1] > key[q]) {
+          const int tk = key[q], tv = val[q];
+          key[q] = key[q - 1];
+          val[q] = val[q - 1];
+          key[q - 1] = tk;
+          val[q - 1] = tv;
         }
       }
     }
-    if (found >= 0) {
-      ((DT*)vn.dx)[c] = ((const DT*)vo.dx)[found];
-      ((DT*)vn.dy)[c] = ((const DT*)vo.dy)[found];
-      ((DT*)vn.dz)[c] = ((const DT*)vo.dz)[found];
-      vn.flag[c] = vo.flag[found];
-    } else {
-      ((DT*)vn.dx)[c] = DT{};
-      ((DT*)vn.dy)[c] = DT{};
-      ((DT*)vn.dz)[c] = DT{};
-      vn.flag[c] = 0;
+#pragma unroll
+    for (int q = 0; q < kRowSort; ++q)
+      if (q < m) vr[q] = val[q];
+  } else {
+    for (int a = 1; a < m; ++a) {
+      const int tk = kr[a], tv = vr[a];
+      int q = a;
+      while (q > 0 && kr[q - 1] > tk) {
+        kr[q] = kr[q - 1];
+        vr[q] = vr[q - 1];
+        --q;
+      }
+      kr[q] = tk;
+      vr[q] = tv;
     }
   }
-  const int ni = min(inc, K);
-  for (int k = 0; k < ni; ++k) {
-    const int2 e = d.inrow[(size_t)i * K + k];
-    insert(b.id[e.y >> 1], (e.x << 1) | (e.y & 1));
+  // history of each entry: the entry of the same partner in the slot's old
+  // row (old slots through the previous-slot map)
+  const int si = d.prev[i];
+  const int os = ro.rs[si], on = min(ro.cnt[si], d.Emax - os);
+  for (int k = 0; k < m; ++k) {
+    const int e = base + k;
+    const int sj = d.prev[vr[k] >> 1];
+    int found = -1;
+    for (int q = 0; q < on; ++q)
+      if ((ro.fp[os + q] >> 1) == sj) {
+        found = os + q;
+        break;
+      }
+    if (found >= 0) {
+      ((DT*)rn.dx)[e] = ((const DT*)ro.dx)[found];
+      ((DT*)rn.dy)[e] = ((const DT*)ro.dy)[found];
+      ((DT*)rn.dz)[e] = ((const DT*)ro.dz)[found];
+      rn.flag[e] = ro.flag[found];
+    } else {
+      ((DT*)rn.dx)[e] = DT{};
+      ((DT*)rn.dy)[e] = DT{};
+      ((DT*)rn.dz)[e] = DT{};
+      rn.flag[e] = 0;
+    }
   }
-  d.fcnt[i] = n;
 }
 
-// The re-sorted state b and list vn become the current a and vo (the state
-// stays in one place between re-sorts, where the integrator updates it); the
-// positions of this sort are kept for the skin test, and the new cell starts
-// become the current order's.
+// The re-sorted state b becomes the current a (the state stays in one place
+// between re-sorts, where the integrator updates it); the positions of this
+// sort are kept for the skin test, the new cell starts become the current
+// order's, and the new rows become current (the row word flips).
 template <int M>
-__global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const int* cs_new,
-                         int* cs_cur) {
+__global__ void k_commit(Dev d, PState a, PState b, const int* cs_new, int* cs_cur) {
   if (gated_off(d.gate)) return;
   using T = Tr<M>;
   using P = typename T::P;
   using V4 = typename T::V4;
   using PR = typename T::PR;
   using DT = typename T::DT;
-  const int nc = min(*vn.count, d.Cmax);
-  const int top = max(max(d.N, nc), d.M_rank);
+  const int top = max(d.N, d.M_rank);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < top; k += gridDim.x * blockDim.x) {
     if (k < d.N) {
       const BoxDev& B = d.boxes[d.slot_box[k]];
@@ -1887,20 +1967,146 @@ __global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const in
           }
         }
       }
-      vo.hs[k] = vn.hs[k];
-      vo.oc[k] = vn.oc[k];
-    }
-    if (k < nc) {
-      vo.pair[k] = vn.pair[k];
-      vo.hid[k] = vn.hid[k];
-      ((DT*)vo.dx)[k] = ((const DT*)vn.dx)[k];
-      ((DT*)vo.dy)[k] = ((const DT*)vn.dy)[k];
-      ((DT*)vo.dz)[k] = ((const DT*)vn.dz)[k];
-      vo.flag[k] = vn.flag[k];
     }
     if (k < d.M_rank) cs_cur[k] = cs_new[k];
-    if (k == 0) *vo.count = nc;
+    if (k == 0) *d.rpar = 1 - *d.rpar;
   }
+}
+
+// ---------------------------------------------------------------------------
+// contact-list pipeline, every step: one warp per 32 consecutive slots walks
+// their rows (contiguous) 32 entries at a time.  Each lane applies the
+// contact rule to one entry; the entries in contact are compacted by ballot
+// and their forces computed with every queued lane busy (each pair is
+// evaluated by both of its rows, in the same orientation, lower id first,
+// with the same history, so both get the same bits); then each slot adds its
+// entries of the tile in row order (partner id) and, after the last tile,
+// integrates.  A pair that left contact loses its history.
+// ---------------------------------------------------------------------------
+constexpr int kStepWarps = 8;
+
+template <int M>
+__device__ __forceinline__ void integrate_slot(const Dev& d, const PState& b, const BoxDev& B,
+                                               int i, v3<typename Tr<M>::R> F,
+                                               v3<typename Tr<M>::R> Tq,
+                                               typename Tr<M>::V4 vm, typename Tr<M>::V4 wr,
+                                               int store_ft);
+
+template <int M>
+__global__ void __launch_bounds__(32 * kStepWarps, M == kFP64 ? 2 : 4)
+k_step(Dev d, PState b, int store_ft) {
+  using T = Tr<M>;
+  using R = typename T::R;
+  using V4 = typename T::V4;
+  using DT = typename T::DT;
+  __shared__ typename vec4_of<R>::type cF[kStepWarps][32], cN[kStepWarps][32];
+  __shared__ int qk[kStepWarps][32];
+  __shared__ unsigned char own[kStepWarps][32];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const RowList rl = *d.rpar ? d.rl[1] : d.rl[0];
+  const int wbase = (blockIdx.x * kStepWarps + wi) * 32;
+  const int i = wbase + lane;
+  const int K = d.K;
+  bool live = false;
+  int box = 0;
+  int rs_i = 0, n_i = 0;
+  if (i < d.N) {
+    box = d.nbox == 1 ? 0 : d.slot_box[i];
+    live = i - d.boxes[box].pbase < d.boxes[box].nlive;
+    rs_i = rl.rs[i];  // dead slots: an empty row at the running offset
+    n_i = live ? max(0, min(min(rl.cnt[i], K), d.Emax - rs_i)) : 0;
+  } else {
+    rs_i = 0x7fffffff;
+  }
+  // the warp's entries (rows of consecutive slots are consecutive)
+  int e0 = live ? rs_i : 0x7fffffff, e1 = live ? rs_i + n_i : 0;
+  e0 = __reduce_min_sync(full, e0);
+  e1 = __reduce_max_sync(full, e1);
+  int mbox = -1;
+  float m_ov = 0.0f, m_ratio = 0.0f;
+  v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
+  for (int t0 = e0; t0 < e1; t0 += 32) {
+    const int e = t0 + lane;
+    // the lane whose row holds entry e: the last lane with rs <= e
+    int lo = 0, hi = 31;
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const int mid = (lo + hi + 1) >> 1;
+      const int v = __shfl_sync(full, rs_i, mid);
+      if (v <= e) lo = mid;
+      else hi = mid - 1;
+    }
+    const int ol = lo;
+    const int olive = __shfl_sync(full, live ? 1 : 0, ol);
+    const int orow = __shfl_sync(full, rs_i + n_i, ol);
+    const bool ok = e < e1 && olive && e < orow;
+    const int io = wbase + ol;
+    const int obox = __shfl_sync(full, box, ol);
+    const BoxDev& Bo = d.boxes[obox];
+    int fpe = 0;
+    bool hit = false;
+    if (ok) {
+      fpe = rl.fp[e];
+      hit = pair_in_contact<M>(Bo, b, io, fpe >> 1);
+      if (!hit && rl.flag[e]) {
+        ((DT*)rl.dx)[e] = DT{};
+        ((DT*)rl.dy)[e] = DT{};
+        ((DT*)rl.dz)[e] = DT{};
+        rl.flag[e] = 0;
+      }
+    }
+    cF[wi][lane] = typename vec4_of<R>::type{};
+    cN[wi][lane] = typename vec4_of<R>::type{};
+    own[wi][lane] = (unsigned char)ol;
+    const unsigned bal = __ballot_sync(full, hit);
+    if (hit) qk[wi][__popc(bal & lt)] = lane;
+    __syncwarp();
+    if (lane < __popc(bal)) {
+      const int k = qk[wi][lane];
+      const int e2 = t0 + k;
+      const int i2 = wbase + own[wi][k];
+      const int f2 = rl.fp[e2];
+      const int j2 = f2 >> 1;
+      const bool low = f2 & 1;
+      const int ob2 = d.nbox == 1 ? 0 : d.slot_box[i2];
+      const BoxDev& B2 = d.boxes[ob2];
+      PairOut<M> o;
+      pair_law<M>(b, B2, low ? i2 : j2, low ? j2 : i2, ((const DT*)rl.dx)[e2],
+                  ((const DT*)rl.dy)[e2], ((const DT*)rl.dz)[e2], o);
+      ((DT*)rl.dx)[e2] = o.nx;
+      ((DT*)rl.dy)[e2] = o.ny;
+      ((DT*)rl.dz)[e2] = o.nz;
+      rl.flag[e2] = 1;
+      if (low) {
+        // the pair's force as recorded for the contact output (once per pair)
+        st4((V4*)d.Fe + e2, o.F4);
+        st4((V4*)d.Ne + e2, o.N4);
+        cF[wi][k] = o.F4;
+      } else {
+        cF[wi][k] = mk4<R>(-o.F4.x, -o.F4.y, -o.F4.z, R(0));
+      }
+      cN[wi][k] = o.N4;
+      if (o.ov > 0.0f) track_diag(d, ob2, o.ov, o.ratio, mbox, m_ov, m_ratio);
+    }
+    __syncwarp();
+    // this slot's entries of the tile, in row order
+    if (live) {
+      const int ka = max(rs_i, t0) - t0, kb = min(rs_i + n_i, t0 + 32) - t0;
+      for (int k = ka; k < kb; ++k) {
+        F = F + xyz(cF[wi][k]);
+        Ns = Ns + xyz(cN[wi][k]);
+      }
+    }
+    __syncwarp();
+  }
+  flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
+  if (!live) return;
+  const V4 vm = ((const V4*)b.vel)[i];
+  const V4 wr = ((const V4*)b.omg)[i];
+  const R r = wr.w;
+  integrate_slot<M>(d, b, d.boxes[box], i, F, r * Ns, vm, wr, store_ft);
 }
 
 // Whether this step re-sorts: when a particle moved far enough since the
@@ -2200,63 +2406,22 @@ __global__ void k_walls(Dev d, PState b) {
 }
 
 // ---------------------------------------------------------------------------
-// per-particle sum (fixed order), floor wall, gravity, symplectic Euler,
-// then binning for the next step
+// one particle after its contact sums: floor wall (rectangles and lines come
+// from k_walls), gravity, symplectic Euler, then binning for the next step,
+// the contact rule's record and the skin test.  F is the contact force, Tq
+// the contact torque (r times the sum of n x F).
 // ---------------------------------------------------------------------------
 template <int M>
-__global__ void __launch_bounds__(256, 4)
-k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, int store_ft) {
+__device__ __forceinline__ void integrate_slot(const Dev& d, const PState& b, const BoxDev& B,
+                                               int i, v3<typename Tr<M>::R> F,
+                                               v3<typename Tr<M>::R> Tq,
+                                               typename Tr<M>::V4 vm, typename Tr<M>::V4 wr,
+                                               int store_ft) {
   using T = Tr<M>;
   using P = typename T::P;
   using R = typename T::R;
   using V4 = typename T::V4;
-  using DT = typename T::DT;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.N) return;
-  const BoxDev& B = d.boxes[d.slot_box[i]];
-  if (i - B.pbase >= B.nlive) return;
-  const V4* Fc = (const V4*)d.Fc;
-  const V4* nFc = (const V4*)d.nFc;
-  v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
-  if (!d.Ffused) {
-    // the slot's candidate pairs in increasing partner id, four at a time:
-    // their contact flags first, then the forces of the pairs in contact;
-    // Fc is the force on the pair's lower-id member: added when this slot is
-    // that member, subtracted otherwise; n x F enters with the same sign for
-    // both
-    const int nrow = min(d.fcnt[i], d.K);
-    const int* row = d.frow + (size_t)i * d.K;
-    for (int k = 0; k < nrow; k += 4) {
-      const int4 e4 = *(const int4*)(row + k);
-      const int e[4] = {e4.x, e4.y, e4.z, e4.w};
-      unsigned char f[4];
-      V4 fv[4], qv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) f[u] = k + u < nrow ? vl_flag[e[u] >> 1] : 0;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (f[u]) {
-          fv[u] = ld4(Fc + (e[u] >> 1));
-          qv[u] = ld4(nFc + (e[u] >> 1));
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (!f[u]) continue;
-        if (e[u] & 1) F = F + xyz(fv[u]);
-        else F = F - xyz(fv[u]);
-        Ns = Ns + xyz(qv[u]);
-      }
-    }
-  }
-  V4 vm = ((const V4*)b.vel)[i];
-  V4 wr = ((const V4*)b.omg)[i];
   R m = vm.w, r = wr.w;
-  v3<R> Tq = r * Ns;  // T = r (n x F), same sign for both members of a pair
-  if (d.Ffused) {
-    F = xyz(ld4((const V4*)d.Ffused + i));
-    Tq = xyz(ld4((const V4*)d.Tfused + i));
-  }
   P x = ((P*)b.px)[i], y = ((P*)b.py)[i], z = ((P*)b.pz)[i];
   // Walls (Sec. 3.3 item 5): the floor z = 0 here; rectangles and lines
   // were summed by k_walls into Fwall / Twall.  Each is a body of infinite
@@ -2422,6 +2587,25 @@ k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, i
 }
 
 // ---------------------------------------------------------------------------
+// the per-particle Collide forms' sum: their per-slot totals, then
+// integrate_slot
+// ---------------------------------------------------------------------------
+template <int M>
+__global__ void __launch_bounds__(256, M == kFP64 ? 2 : 4)
+k_gather_integrate(Dev d, PState b, int store_ft) {
+  using T = Tr<M>;
+  using V4 = typename T::V4;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[i]];
+  if (i - B.pbase >= B.nlive) return;
+  const V4 vm = ((const V4*)b.vel)[i];
+  const V4 wr = ((const V4*)b.omg)[i];
+  integrate_slot<M>(d, b, B, i, xyz(ld4((const V4*)d.Ffused + i)),
+                    xyz(ld4((const V4*)d.Tfused + i)), vm, wr, store_ft);
+}
+
+// ---------------------------------------------------------------------------
 // state out (id order, FP64)
 // ---------------------------------------------------------------------------
 template <int M>
@@ -2501,7 +2685,7 @@ __global__ void k_get_order(Dev d, PState b, int box, int* id_by_slot,
 // (a fixed order: the result does not depend on timing).
 template <int M>
 __global__ void k_stats(Dev d, PState b, const int* hs, const int* oc,
-                        const unsigned char* flag, int box, double* part) {
+                        const unsigned char* flag, int rows, int box, double* part) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   const BoxDev& B = d.boxes[box];
@@ -2519,7 +2703,16 @@ __global__ void k_stats(Dev d, PState b, const int* hs, const int* oc,
     acc[2] += m * vx;
     acc[3] += m * vy;
     acc[4] += m * vz;
-    if (flag) {  // candidate list: the pairs in contact in the last step
+    if (rows) {  // candidate rows: each pair in contact once, on its lower-id member's row
+      const RowList& rl = *d.rpar ? d.rl[1] : d.rl[0];
+      int nin = 0;
+      const int cnt = min(rl.cnt[s], d.Emax - rl.rs[s]);
+      for (int k = 0; k < cnt; ++k) {
+        const int e = rl.rs[s] + k;
+        nin += ((rl.fp[e] & 1) && rl.flag[e]) ? 1 : 0;
+      }
+      acc[5] += (double)nin;
+    } else if (flag) {
       int nin = 0;
       for (int k = 0; k < oc[s]; ++k) nin += flag[hs[s] + k] ? 1 : 0;
       acc[5] += (double)nin;
