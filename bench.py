@@ -133,71 +133,39 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # algorithmic traffic model (bytes per particle-step, DEM_MIXED layout)
 # ---------------------------------------------------------------------------
-def phase_bytes(n, c_half, ncells):
-    """Unique bytes each phase must move per step: every array element read
-    or written once (neighbour re-reads served by caches are not counted).
-    n particles, c_half contacts per particle (half list), ncells cells.
-    The contact list is written by the search kernel, so the compaction
-    phase moves nothing of its own."""
-    C = c_half * n
-    state = 24 + 16 + 16 + 4 + 4        # position, velocity, spin, id, cell
-    sort = (ncells * (4 + 4 + 8)                     # cell scan
-            + n * (4 + 4 + 4 + 4)                    # scatter
-            + n * (4 + 4 + 8 + 2 * state + 16 + 4)   # reorder, predicate record
-            + n * 16 + ncells * 32)                  # cell bounding boxes
-    search = (n * (16 + 4 + 4 + 4 + 4 + 8) + ncells * (8 + 4)
-              + C * (4 + 4 + 8 + 8 + 4 + 4))         # rows, list, incoming rows
-    compact = 0
-    force = C * (8 + 8 + 8 + 8 + 24 + 24 + 16 + 16) + n * (24 + 16 + 16)
-    integrate = n * (4 + 4 + 4 + 2 * (24 + 16 + 16) + 4 + 4 + 4) + C * (2 * 32 + 2 * 8 + 4)
-    return {"sort": sort, "search": search, "compact": compact, "force": force,
-            "integrate": integrate}
+def phase_bytes(n, c_half, cand_half, ncells, resorts_per_step):
+    """Unique bytes each phase must move, per step (DEM_MIXED layout): every
+    array element read or written once; re-reads of neighbours' data served
+    by the caches are not counted.  n particles, c_half contacts and
+    cand_half candidate pairs per particle (each pair counted once), ncells
+    cells.  The re-sort phases (sort, search, rows) run only in the steps
+    that re-sort: their bytes are scaled by resorts_per_step."""
+    C = c_half * n            # pairs in contact
+    Cc = cand_half * n        # candidate pairs
+    E = 2 * Cc                # row entries (each pair in both members' rows)
+    Ec = 2 * C                # row entries in contact
+    state = 24 + 16 + 16 + 16 + 4 + 4 + 4 + 4   # x, v, w, predicate record, id, cells
+    sort = (ncells * (4 + 4 + 8 + 1 + 1 + 32)        # cell scan, ranges, flags, box reset
+            + n * (4 + 4 + 4 + 1)                    # scatter
+            + n * (4 + 4 + 2 * state + 4)            # reorder (state, previous slot)
+            + ncells * 32)                           # cell bounding boxes
+    search = (n * (16 + 4 + 4 + 4 + 4) + ncells * (8 + 32)
+              + Cc * (4 + 8 + 8 + 8 + 4))            # rows, list pairs and ids, incoming rows
+    rows = (n * (4 + 4 + 4 + 4 + 4 + 4)              # lengths, scan, starts, previous slots
+            + E * (4 + 4 + 4 + 1 + 24)               # entries, ids, old rows, flags, history
+            + n * (2 * state + 24))                  # commit: state copy, positions of the sort
+    walls = 0
+    step = (n * (4 + 4 + 16 + 4 + 24 + 16 + 16 + 24)  # rows, record, cell, x, v, w, skin test
+            + n * (24 + 16 + 16 + 16 + 4)             # x, v, w, record, cell written
+            + E * (4 + 1)                              # row entries and flags
+            + Ec * (24 + 24 + 1)                       # history of contacts in and out
+            + C * 32)                                  # recorded pair force
+    f = resorts_per_step
+    return {"sort": sort * f, "search": search * f, "rows": rows * f, "walls": walls,
+            "step": step}
 
 
-def search_tests(box, ncell):
-    """Candidate tests the contact search performs: every pair is tested once,
-    by the particle whose half of the neighbourhood holds the other (its own
-    cell's later slots and the 13 cells after it in (dz, dy, dx) order); of
-    those 13 cells only the ones that survive the reach test count (the
-    bounding box of the cell's member centres within 1.001 (r_i + largest
-    radius in it)).  Computed from the same positions and grid as the run."""
-    L = np.asarray(box.L)
-    n = np.asarray(ncell)
-    h = L / n
-    c = np.minimum((box.x // h).astype(np.int64), n - 1)
-    o = box.x - c * h
-    lin = (c[:, 2] * n[1] + c[:, 1]) * n[0] + c[:, 0]
-    M = int(np.prod(n))
-    cnt = np.bincount(lin, minlength=M)
-    rmax = np.full(M, -1.0)
-    np.maximum.at(rmax, lin, box.r)
-    lo = np.full((M, 3), np.inf)
-    hi = np.full((M, 3), -np.inf)
-    for a in range(3):
-        np.minimum.at(lo[:, a], lin, o[:, a])
-        np.maximum.at(hi[:, a], lin, o[:, a])
-    tests = int((cnt * (cnt - 1) // 2).sum())  # own cell, later slots
-    for dz in (-1, 0, 1):
-        for dy in (-1, 0, 1):
-            for dx in (-1, 0, 1):
-                if (dz, dy, dx) <= (0, 0, 0):
-                    continue
-                cn = (c + np.array([dx, dy, dz])) % n
-                l2 = (cn[:, 2] * n[1] + cn[:, 1]) * n[0] + cn[:, 0]
-                g = np.zeros(box.n)
-                for a, dd in enumerate((dx, dy, dz)):
-                    blo = lo[l2, a] + dd * h[a]
-                    bhi = hi[l2, a] + dd * h[a]
-                    g += np.maximum(np.maximum(blo - o[:, a], o[:, a] - bhi), 0) ** 2
-                reach = 1.001 * (box.r + rmax[l2])
-                keep = (rmax[l2] >= 0) & (g <= reach ** 2)
-                tests += int(cnt[l2][keep].sum())
-    return tests
-
-
-SEARCH_OPS_PER_TEST = 14  # FP32 instructions of the contact predicate
-PHASES = ["sort", "search", "compact", "force", "integrate"]
-PHASE_KERNELS = {"sort": 6, "search": 1, "compact": 0, "force": 1, "integrate": 1}
+PHASES = ["sort", "search", "rows", "walls", "step"]
 
 
 def _torch_setup(args):
@@ -398,17 +366,19 @@ def main():
     resorts_timed = rs1["resorts"] - rs0["resorts"]
     secs = _max_over_ranks(secs, world, torch)
     value = job_throughput(n, world, args.steps, secs)
-    # ---- the same K steps again, untimed: contacts along the trajectory ---
-    # (the packing relaxes: the contact count falls during the run)
+    # ---- the same K steps again, untimed: contacts and candidate pairs ---
+    # along the trajectory (the packing relaxes: contacts fall during the run)
     _reset(ctx, [box])
     counts, chunk, done = [], max(1, args.steps // 20), 0
     while done < args.steps:
         k = min(chunk, args.steps - done)
         ctx.step(k)
         done += k
-        counts.append((k, ctx.stats(0)[5]))
-    contacts_total = sum(k * c for k, c in counts)  # each chunk at its end count
+        counts.append((k, ctx.stats(0)[5], ctx.resort_stats()["candidates"]))
+    contacts_total = sum(k * c for k, c, _ in counts)  # each chunk at its end count
+    cands_total = sum(k * c for k, _, c in counts)
     c_half = contacts_total / args.steps / n
+    cand_half = cands_total / args.steps / n
     # half contacts evaluated per second over the timed steps
     contact_evals = contacts_total * world / secs
     # ---- per-phase device time: the same K steps, direct launches ---------
@@ -418,32 +388,23 @@ def main():
     ph = ctx.phase_times()
     ctx.set_timing(False)
     ncells = int(np.prod(ncell))
-    pb = phase_bytes(n, c_half, ncells)
+    pb = phase_bytes(n, c_half, cand_half, ncells, resorts_timed / args.steps)
     ph_ms = dict(zip(PHASES, ph.tolist()))
-    dom = max(ph_ms, key=ph_ms.get)
     peaks, src = _peaks()
     total_bytes = sum(pb.values())
-    clk_mhz = clk.summary().get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    if dom == "search":
-        # ALU-bound: FP32 instruction issue, 152 SMs x 128 lanes per clock
-        tests = search_tests(box, ncell)
-        ops = tests * SEARCH_OPS_PER_TEST
-        peak = 152 * 128 * clk_mhz * 1e6 / 1e12
-        achieved = ops / (ph_ms[dom] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "k_candidates", "kernel_phase": dom,
-                "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s (FP32 instructions, each counted once)",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz (median SM clock)",
-                "algorithmic_ops_per_launch": ops, "candidate_tests_per_launch": tests}
-    else:
-        achieved = pb[dom] / (ph_ms[dom] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel_phase": dom, "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)",
-                "algorithmic_bytes_per_launch": pb[dom]}
+    # the dominant kernel: the fused step kernel, every step (the re-sort
+    # kernels run in the steps that re-sort only)
+    dom = "step"
+    achieved = pb[dom] / (ph_ms[dom] * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_step", "kernel_phase": dom, "achieved": achieved,
+            "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs; copy test, burst)",
+            "algorithmic_bytes_per_launch": pb[dom],
+            "kernel_ms": ph_ms[dom]}
     roof.update({"phase_ms": ph_ms, "phase_bytes": pb,
+                 "candidates_per_particle": cand_half,
+                 "resorts_per_step": resorts_timed / args.steps,
                  "step_algorithmic_bytes": total_bytes,
                  "step_frac_of_hbm": total_bytes / (secs / args.steps) / 1e9 / peaks["hbm_gbs"]})
     tr_path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -456,7 +417,7 @@ def main():
             for f in ("dem_kernels.cuh", "dem_common.cuh"):
                 with open(os.path.join(ROOT, "paper_1503_03553_gb300", "csrc", f), "rb") as fh:
                     h.update(fh.read())
-            if (tr.get("phase") == dom and tr.get("precision") == args.precision
+            if (tr.get("kernel") == "k_step" and tr.get("precision") == args.precision
                     and tr.get("kernel_sha256") == h.hexdigest()):
                 roof["traffic"] = tr["bytes_per_launch"] * n / tr["n"]
                 roof["traffic_source"] = tr.get("source")
@@ -746,6 +707,17 @@ def _phase_ms(D, torch, stream, boxes, precision, ncells, steps, **kw):
         ctx.close()
 
 
+def _contact_phase_ms(ph, fused):
+    """The contact part of a step (the paper's Collide): the per-particle
+    forms' one kernel (timed as the search phase); for the contact-list
+    pipeline the search and rows of its re-sorts (averaged over the steps)
+    and the fused step kernel, whose integration of each particle is a few
+    per cent of it and is counted in."""
+    if fused:
+        return ph["search"]
+    return ph["search"] + ph["rows"] + ph["step"]
+
+
 def _fused_leg(args, D, torch, stream, box):
     """The paper's comparison on this workload.  Its two per-particle Collide
     forms: Algorithm 1 as printed (search and force fused, each force as soon
@@ -763,9 +735,9 @@ def _fused_leg(args, D, torch, stream, box):
         out[f"{name}_step"] = _throughput(D, torch, stream, [box], "mixed", [ncell], steps,
                                           collide=form)
         pf = _phase_ms(D, torch, stream, [box], "mixed", [ncell], steps, collide=form)
-        coll[name] = pf["search"] + pf["compact"] + pf["force"]
+        coll[name] = _contact_phase_ms(pf, fused=True)
     pc = _phase_ms(D, torch, stream, [box], "mixed", [ncell], steps)
-    coll["compact"] = pc["search"] + pc["compact"] + pc["force"]
+    coll["compact"] = _contact_phase_ms(pc, fused=False)
     out.update({"collide_ms_fused": coll["fused"], "collide_ms_twoloop": coll["twoloop"],
                 "collide_ms_compact": coll["compact"],
                 "twoloop_speedup_over_fused": coll["fused"] / coll["twoloop"],
@@ -839,7 +811,7 @@ def _fig4_leg(args, D, torch, stream):
                                 ("twoloop_paper", D.DEM_COLLIDE_TWOLOOP),
                                 ("contact_list", D.DEM_COLLIDE_COMPACT)):
             ph = _phase_ms(D, torch, stream, [b], "mixed", [nc], 200, collide=form)
-            ph["collide"] = ph["search"] + ph["compact"] + ph["force"]
+            ph["collide"] = _contact_phase_ms(ph, fused=form != D.DEM_COLLIDE_COMPACT)
             rows[form_name] = {k: round(v, 5) for k, v in ph.items()}
         rows["twoloop_speedup_over_fused_collide"] = (rows["fused_previous"]["collide"] /
                                                       rows["twoloop_paper"]["collide"])

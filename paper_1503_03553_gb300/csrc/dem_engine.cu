@@ -148,7 +148,7 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 }
 
 // kernels of a step that does not re-sort (DEM_COLLIDE_COMPACT: decide,
-// pairs, sum + integrate; the per-particle forms sort every step)
+// contacts + sums, integrate; the per-particle forms sort every step)
 int launches_per_step(const dem_ctx* ctx) {
   if (ctx->fused) return 7 + (ctx->hwalls.empty() ? 0 : 1);
   return 3 + (ctx->hwalls.empty() ? 0 : 1);
@@ -157,13 +157,11 @@ int launches_per_step(const dem_ctx* ctx) {
 // x3, rows, commit)
 int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 11 + (ctx->split ? 1 : 0); }
 
-// which of the two row lists is current (read from the device; the stream
-// is synchronised)
+// the current row list (a re-sort builds the other one and commits it)
 int current_rows(dem_ctx* ctx, cudaError_t* err) {
-  int rp = 0;
-  *err = cudaMemcpyAsync(&rp, ctx->dev.rpar, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-  if (*err == cudaSuccess) *err = cudaStreamSynchronize(ctx->stream);
-  return rp ? 1 : 0;
+  *err = cudaSuccess;
+  (void)ctx;
+  return 0;
 }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
@@ -260,8 +258,7 @@ void enqueue_resort(dem_ctx* ctx, cudaStream_t rs, bool tm, cudaEvent_t* ev) {
   // rows of the new candidate list: lengths, offsets (scan), entries ordered
   // by partner id with their history, then the commit
   const RowLenIn rin{ctx->vs.oc, d.icnt, d.K};
-  const RowEpi repi{{d.rl[0].rs, d.rl[1].rs}, {d.rl[0].cnt, d.rl[1].cnt},
-                    {d.rl[0].count, d.rl[1].count}, d.rpar, ctx->vs.oc, d.icnt, d.K, d.N, d.Emax,
+  const RowEpi repi{d.rl[1].rs, d.rl[1].cnt, d.rl[1].count, ctx->vs.oc, d.icnt, d.K, d.N, d.Emax,
                     d.status};
   const int nbr = blocks_for(d.N, kScanTile);
   k_scanf_reduce<int, RowLenIn><<<nbr, kScanThreads, 0, rs>>>(rin, d.N, d.scan_bsum, d.gate);
@@ -283,8 +280,8 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
   if (tm) cudaEventRecord(ev[3], s);
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
   if (tm) cudaEventRecord(ev[4], s);
-  k_step<M><<<blocks_for(d.N, 32 * kStepWarps), 32 * kStepWarps, 0, s>>>(d, ctx->ps[0],
-                                                                         store_ft ? 1 : 0);
+  k_step<M><<<blocks_for(d.N, 32 * kStepWarps), 32 * kStepWarps, 0, s>>>(d, ctx->ps[0]);
+  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0], store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -648,10 +645,10 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
     d.Fc = A(v4_bytes(M) * ctx->Cmax);
     d.nFc = A(v4_bytes(M) * ctx->Cmax);
   }
-  if (ctx->fused) {
-    d.Ffused = A(v4_bytes(M) * n);
-    d.Tfused = A(v4_bytes(M) * n);
-  } else {
+  // per-slot contact totals, from the per-particle kernels or the step kernel
+  d.Ffused = A(v4_bytes(M) * n);
+  d.Tfused = A(v4_bytes(M) * n);
+  if (!ctx->fused) {
     d.inrow = (int2*)A(sizeof(int2) * n * ctx->K);
     d.xb = A(pos_bytes(M) * n);
     d.yb = A(pos_bytes(M) * n);
@@ -715,7 +712,6 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
     c.count = (int*)A(sizeof(int));
     d.Fe = A(v4_bytes(M) * (size_t)d.Emax);
     d.Ne = A(v4_bytes(M) * (size_t)d.Emax);
-    d.rpar = (int*)A(sizeof(int));
   }
   ctx->staging = (double*)A(sizeof(double) * 16 * (size_t)std::max(1, max_cap));
   ctx->staging_i = (int*)A(sizeof(int) * 2 * (size_t)std::max(1, max_cap));
@@ -767,7 +763,6 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
     e = cudaMemsetAsync(ctx->vs.oc, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(ctx->vs.hs, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(ctx->vs.count, 0, sizeof(int), s);
-    if (!e) e = cudaMemsetAsync(d.rpar, 0, sizeof(int), s);
   }
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return bail(DEM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));

@@ -102,8 +102,8 @@ struct VList {
 // slots).  Each entry keeps that pair's tangential history and whether the
 // pair was in contact in the last step; both copies of a pair's history are
 // computed by the same arithmetic in the same orientation (lower id first),
-// so they stay equal.  Two of them, current and the one a re-sort builds;
-// a device word says which is current.
+// so they stay equal.  Two of them: the current rows ([0]) and the ones a
+// re-sort builds ([1]) and then commits into [0].
 struct RowList {
   int* rs;      // by slot: first entry of its row (a scan over all slots)
   int* cnt;     // by slot: entries in its row
@@ -174,8 +174,7 @@ struct Dev {
   void* Fout;    // V4 per slot: total force of the last step
   void* Tout;    // V4 per slot: total torque of the last step
   // contact-list pipeline
-  RowList rl[2];         // candidate rows; *rpar says which one is current
-  int* rpar;             // device word: index of the current rows
+  RowList rl[2];         // candidate rows: [0] current, [1] a re-sort's
   void* Fe;      // V4 by entry: force of the pair on the row's slot's pair
   void* Ne;      // V4 by entry: n x F (recorded on the lower-id member's
                  // entry of each pair in contact, for the contact output)
@@ -1788,28 +1787,25 @@ k_scanf_apply(In in, int n, const T* __restrict__ bsum, Epi epi, const unsigned*
   }
 }
 
-// row starts and lengths of the new rows (the row list that is not current,
-// 1 - *rpar) and their total; a slot with more candidates than a row holds
-// sets the row-overflow bit, more entries than a row list holds the
-// list-overflow bit
+// row starts and lengths of the new rows and their total; a slot with more
+// candidates than a row holds sets the row-overflow bit, more entries than a
+// row list holds the list-overflow bit
 struct RowEpi {
-  int* rs[2];
-  int* cnt[2];
-  int* count[2];
-  const int* rpar;
+  int* rs;
+  int* cnt;
+  int* count;
   const int* oc;
   const int* icnt;
   int K, N, Emax;
   unsigned* status;
   __device__ void operator()(int i, int len, int pre) const {
-    const int w = 1 - *rpar;
-    rs[w][i] = pre;
-    cnt[w][i] = len;
+    rs[i] = pre;
+    cnt[i] = len;
     if (oc[i] + icnt[i] > K) atomicOr(status, kStRowOverflow);
     if (i == N - 1) {
       const long long tot = (long long)pre + len;
       if (tot > Emax) atomicOr(status, kStListOverflow);
-      *count[w] = (int)min(tot, (long long)Emax);
+      *count = (int)min(tot, (long long)Emax);
     }
   }
 };
@@ -1821,9 +1817,8 @@ __global__ void __launch_bounds__(256)
 k_rows(Dev d, PState b, VList vs) {
   if (gated_off(d.gate)) return;
   using DT = typename Tr<M>::DT;
-  const int rp = *d.rpar;
-  const RowList ro = rp ? d.rl[1] : d.rl[0];  // current rows (old slots)
-  const RowList rn = rp ? d.rl[0] : d.rl[1];  // the rows being built
+  const RowList& ro = d.rl[0];  // current rows (old slots)
+  const RowList& rn = d.rl[1];  // the rows being built
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
   const int K = d.K;
@@ -1930,7 +1925,7 @@ k_rows(Dev d, PState b, VList vs) {
 // The re-sorted state b becomes the current a (the state stays in one place
 // between re-sorts, where the integrator updates it); the positions of this
 // sort are kept for the skin test, the new cell starts become the current
-// order's, and the new rows become current (the row word flips).
+// order's, and the new rows the current rows.
 template <int M>
 __global__ void k_commit(Dev d, PState a, PState b, const int* cs_new, int* cs_cur) {
   if (gated_off(d.gate)) return;
@@ -1939,7 +1934,10 @@ __global__ void k_commit(Dev d, PState a, PState b, const int* cs_new, int* cs_c
   using V4 = typename T::V4;
   using PR = typename T::PR;
   using DT = typename T::DT;
-  const int top = max(d.N, d.M_rank);
+  const RowList& ro = d.rl[0];
+  const RowList& rn = d.rl[1];
+  const int ne = min(*rn.count, d.Emax);
+  const int top = max(max(d.N, d.M_rank), ne);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < top; k += gridDim.x * blockDim.x) {
     if (k < d.N) {
       const BoxDev& B = d.boxes[d.slot_box[k]];
@@ -1968,8 +1966,19 @@ __global__ void k_commit(Dev d, PState a, PState b, const int* cs_new, int* cs_c
         }
       }
     }
+    if (k < d.N) {
+      ro.rs[k] = rn.rs[k];
+      ro.cnt[k] = rn.cnt[k];
+    }
+    if (k < ne) {
+      ro.fp[k] = rn.fp[k];
+      ro.flag[k] = rn.flag[k];
+      ((DT*)ro.dx)[k] = ((const DT*)rn.dx)[k];
+      ((DT*)ro.dy)[k] = ((const DT*)rn.dy)[k];
+      ((DT*)ro.dz)[k] = ((const DT*)rn.dz)[k];
+    }
     if (k < d.M_rank) cs_cur[k] = cs_new[k];
-    if (k == 0) *d.rpar = 1 - *d.rpar;
+    if (k == 0) *ro.count = ne;
   }
 }
 
@@ -1980,8 +1989,10 @@ __global__ void k_commit(Dev d, PState a, PState b, const int* cs_new, int* cs_c
 // and their forces computed with every queued lane busy (each pair is
 // evaluated by both of its rows, in the same orientation, lower id first,
 // with the same history, so both get the same bits); then each slot adds its
-// entries of the tile in row order (partner id) and, after the last tile,
-// integrates.  A pair that left contact loses its history.
+// entries of the tile in row order (partner id).  The totals go to Ffused /
+// Tfused for k_gather_integrate: the state is read, never written, here, so
+// every force of the step sees the state at its start.  A pair that left
+// contact loses its history.
 // ---------------------------------------------------------------------------
 constexpr int kStepWarps = 8;
 
@@ -1993,8 +2004,8 @@ __device__ __forceinline__ void integrate_slot(const Dev& d, const PState& b, co
                                                int store_ft);
 
 template <int M>
-__global__ void __launch_bounds__(32 * kStepWarps, M == kFP64 ? 2 : 4)
-k_step(Dev d, PState b, int store_ft) {
+__global__ void __launch_bounds__(32 * kStepWarps, M == kFP64 ? 2 : 3)
+k_step(Dev d, PState b) {
   using T = Tr<M>;
   using R = typename T::R;
   using V4 = typename T::V4;
@@ -2005,7 +2016,7 @@ k_step(Dev d, PState b, int store_ft) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  const RowList rl = *d.rpar ? d.rl[1] : d.rl[0];
+  const RowList& rl = d.rl[0];
   const int wbase = (blockIdx.x * kStepWarps + wi) * 32;
   const int i = wbase + lane;
   const int K = d.K;
@@ -2103,10 +2114,9 @@ k_step(Dev d, PState b, int store_ft) {
   }
   flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
   if (!live) return;
-  const V4 vm = ((const V4*)b.vel)[i];
-  const V4 wr = ((const V4*)b.omg)[i];
-  const R r = wr.w;
-  integrate_slot<M>(d, b, d.boxes[box], i, F, r * Ns, vm, wr, store_ft);
+  const R r = ((const V4*)b.omg)[i].w;
+  st4((V4*)d.Ffused + i, mk4<R>(F.x, F.y, F.z, R(0)));
+  st4((V4*)d.Tfused + i, mk4<R>(r * Ns.x, r * Ns.y, r * Ns.z, R(0)));
 }
 
 // Whether this step re-sorts: when a particle moved far enough since the
@@ -2704,7 +2714,7 @@ __global__ void k_stats(Dev d, PState b, const int* hs, const int* oc,
     acc[3] += m * vy;
     acc[4] += m * vz;
     if (rows) {  // candidate rows: each pair in contact once, on its lower-id member's row
-      const RowList& rl = *d.rpar ? d.rl[1] : d.rl[0];
+      const RowList& rl = d.rl[0];
       int nin = 0;
       const int cnt = min(rl.cnt[s], d.Emax - rl.rs[s]);
       for (int k = 0; k < cnt; ++k) {
