@@ -69,7 +69,7 @@ struct dem_ctx {
   // the per-particle Collide forms sort every step from one to the other.
   PState ps[2]{};
   CList cl[2]{};               // contact lists of the per-particle forms
-  VList vs{};                  // the candidate list a re-sort's search writes
+  VList vl[2]{};               // candidate lists: [0] current, [1] a re-sort's
   int* cs_cur = nullptr;       // cell starts of the current order
   int* cs_new = nullptr;       // cell starts of the order being built
   unsigned char* collect = nullptr;  // cells changed since the last sort
@@ -157,12 +157,7 @@ int launches_per_step(const dem_ctx* ctx) {
 // x3, rows, commit)
 int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 11 + (ctx->split ? 1 : 0); }
 
-// the current row list (a re-sort builds the other one and commits it)
-int current_rows(dem_ctx* ctx, cudaError_t* err) {
-  *err = cudaSuccess;
-  (void)ctx;
-  return 0;
-}
+
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -243,30 +238,31 @@ void enqueue_resort(dem_ctx* ctx, cudaStream_t rs, bool tm, cudaEvent_t* ev) {
       d.ccount, d.M_rank, d.scan_bsum,
       CellEpi{d.cstart, d.crange, d.cellbox, d.lin_of_rank, d.collect, ctx->chg, d.ccur}, d.gate);
   k_scatter<<<blocks_for(d.N, bs), bs, 0, rs>>>(d, ctx->ps[0]);
-  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vs.count);
+  k_reorder<M><<<blocks_for(d.N, bs), bs, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vl[1].count);
   if (tm) cudaEventRecord(ev[1], rs);
   // the search kernel is compiled for at most 256 threads per block
   const int bs_search = bs < 256 ? bs : 256;
   if (ctx->split) {
-    k_candidates<M, true><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vs);
+    k_candidates<M, true><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
     // large particles of size-binned boxes: one warp each, persistent grid
-    k_candidates_large<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[1], ctx->vs);
+    k_candidates_large<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
   } else {
-    k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vs);
+    k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
   }
   if (tm) cudaEventRecord(ev[2], rs);
   // rows of the new candidate list: lengths, offsets (scan), entries ordered
-  // by partner id with their history, then the commit
-  const RowLenIn rin{ctx->vs.oc, d.icnt, d.K};
-  const RowEpi repi{d.rl[1].rs, d.rl[1].cnt, d.rl[1].count, ctx->vs.oc, d.icnt, d.K, d.N, d.Emax,
+  // by partner id, the history carried over, then the commit
+  const RowLenIn rin{ctx->vl[1].oc, d.icnt, d.K};
+  const RowEpi repi{d.rows.rs, d.rows.cnt, d.rows.count, ctx->vl[1].oc, d.icnt, d.K, d.N, d.Emax,
                     d.status};
   const int nbr = blocks_for(d.N, kScanTile);
   k_scanf_reduce<int, RowLenIn><<<nbr, kScanThreads, 0, rs>>>(rin, d.N, d.scan_bsum, d.gate);
   k_scan_top<<<1, kScanTopThreads, 0, rs>>>(d.scan_bsum, nbr, nullptr, 0, d.status, 0u, d.gate);
   k_scanf_apply<int, RowLenIn, RowEpi><<<nbr, kScanThreads, 0, rs>>>(rin, d.N, d.scan_bsum, repi,
                                                                      d.gate);
-  k_rows<M><<<blocks_for(d.N, 256), 256, 0, rs>>>(d, ctx->ps[1], ctx->vs);
-  k_commit<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->cs_new, ctx->cs_cur);
+  k_rows<M><<<blocks_for(d.N, 256), 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[0], ctx->vl[1]);
+  k_commit<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vl[0], ctx->vl[1],
+                                            ctx->cs_new, ctx->cs_cur);
 }
 
 template <int M>
@@ -280,8 +276,8 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
   if (tm) cudaEventRecord(ev[3], s);
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
   if (tm) cudaEventRecord(ev[4], s);
-  k_step<M><<<blocks_for(d.N, 32 * kStepWarps), 32 * kStepWarps, 0, s>>>(d, ctx->ps[0]);
-  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0], store_ft ? 1 : 0);
+  k_pairs<M><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0]);
+  k_rowsum_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0], store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -406,7 +402,7 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
     ctx->ps[p] = PState{};
     ctx->cl[p] = CList{};
   }
-  ctx->vs = VList{};
+  for (int p = 0; p < 2; ++p) ctx->vl[p] = VList{};
   ctx->cs_cur = ctx->cs_new = nullptr;
   ctx->collect = ctx->chg = nullptr;
   ctx->staging = nullptr;
@@ -692,26 +688,26 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
       c.oc = (int*)A(sizeof(int) * n);
       c.count = (int*)A(sizeof(int));
     } else {
-      RowList& r = d.rl[p];
-      r.rs = (int*)A(sizeof(int) * n);
-      r.cnt = (int*)A(sizeof(int) * n);
-      r.fp = (int*)A(sizeof(int) * (size_t)d.Emax);
-      r.flag = (unsigned char*)A((size_t)d.Emax);
-      r.dx = A(dt_bytes(M) * (size_t)d.Emax);
-      r.dy = A(dt_bytes(M) * (size_t)d.Emax);
-      r.dz = A(dt_bytes(M) * (size_t)d.Emax);
-      r.count = (int*)A(sizeof(int));
+      VList& c = ctx->vl[p];
+      c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
+      c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
+      c.dx = A(dt_bytes(M) * ctx->Cmax);
+      c.dy = A(dt_bytes(M) * ctx->Cmax);
+      c.dz = A(dt_bytes(M) * ctx->Cmax);
+      c.flag = (unsigned char*)A(ctx->Cmax);
+      c.epos = (int2*)A(sizeof(int2) * ctx->Cmax);
+      c.hs = (int*)A(sizeof(int) * n);
+      c.oc = (int*)A(sizeof(int) * n);
+      c.count = (int*)A(sizeof(int));
     }
   }
   if (!ctx->fused) {
-    VList& c = ctx->vs;
-    c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
-    c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
-    c.hs = (int*)A(sizeof(int) * n);
-    c.oc = (int*)A(sizeof(int) * n);
-    c.count = (int*)A(sizeof(int));
-    d.Fe = A(v4_bytes(M) * (size_t)d.Emax);
-    d.Ne = A(v4_bytes(M) * (size_t)d.Emax);
+    d.rows.rs = (int*)A(sizeof(int) * n);
+    d.rows.cnt = (int*)A(sizeof(int) * n);
+    d.rows.F = A(v4_bytes(M) * (size_t)d.Emax);
+    d.rows.N = A(v4_bytes(M) * (size_t)d.Emax);
+    d.rows.count = (int*)A(sizeof(int));
+    d.rowval = (int*)A(sizeof(int) * n * ctx->K);
   }
   ctx->staging = (double*)A(sizeof(double) * 16 * (size_t)std::max(1, max_cap));
   ctx->staging_i = (int*)A(sizeof(int) * 2 * (size_t)std::max(1, max_cap));
@@ -752,17 +748,17 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   if (!e) e = cudaMemsetAsync(ctx->cs_new, 0, sizeof(int) * std::max(1, ctx->M_rank), s);
   if (!e) e = cudaMemsetAsync(d.vctl, 0, sizeof(unsigned) * kCtlWords, s);
   for (int p = 0; p < 2 && !e; ++p) {
-    int* oc = ctx->fused ? ctx->cl[p].oc : d.rl[p].cnt;
-    int* hs = ctx->fused ? ctx->cl[p].hs : d.rl[p].rs;
-    int* cnt = ctx->fused ? ctx->cl[p].count : d.rl[p].count;
+    int* oc = ctx->fused ? ctx->cl[p].oc : ctx->vl[p].oc;
+    int* hs = ctx->fused ? ctx->cl[p].hs : ctx->vl[p].hs;
+    int* cnt = ctx->fused ? ctx->cl[p].count : ctx->vl[p].count;
     e = cudaMemsetAsync(oc, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(hs, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(cnt, 0, sizeof(int), s);
   }
   if (!e && !ctx->fused) {
-    e = cudaMemsetAsync(ctx->vs.oc, 0, sizeof(int) * n, s);
-    if (!e) e = cudaMemsetAsync(ctx->vs.hs, 0, sizeof(int) * n, s);
-    if (!e) e = cudaMemsetAsync(ctx->vs.count, 0, sizeof(int), s);
+    e = cudaMemsetAsync(d.rows.rs, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(d.rows.cnt, 0, sizeof(int) * n, s);
+    if (!e) e = cudaMemsetAsync(d.rows.count, 0, sizeof(int), s);
   }
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return bail(DEM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
@@ -907,7 +903,7 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
   if (st) return st;
   // the box's history is empty: no slot of the box holds a stored contact
   for (int q = 0; q < 2; ++q)
-    CK(cudaMemsetAsync((ctx->fused ? ctx->cl[q].oc : ctx->dev.rl[q].cnt) + B.pbase, 0,
+    CK(cudaMemsetAsync((ctx->fused ? ctx->cl[q].oc : ctx->vl[q].oc) + B.pbase, 0,
                        sizeof(int) * B.cap, s));
   // the next sort starts from the order the particles were given in, and
   // the next step re-sorts
@@ -1502,15 +1498,12 @@ dem_status dem_get_resort_stats(dem_ctx* ctx, int64_t out[4]) {
   if (ctx->fused) return DEM_OK;
   unsigned ctl[kCtlWords] = {};
   int cnt = 0;
-  cudaError_t e;
-  const int rp = current_rows(ctx, &e);
-  CK(e);
   CK(cudaMemcpyAsync(ctl, ctx->dev.vctl, sizeof(ctl), cudaMemcpyDeviceToHost, ctx->stream));
-  CK(cudaMemcpyAsync(&cnt, ctx->dev.rl[rp].count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(&cnt, ctx->vl[0].count, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   out[0] = ctl[kCtlResorts];
   out[1] = launches_per_resort(ctx);
-  out[2] = cnt / 2;  // every candidate pair is in two rows
+  out[2] = std::min(cnt, ctx->Cmax);
   out[3] = ctx->steps_done;
   return DEM_OK;
 }
@@ -1619,9 +1612,9 @@ static double v4_value(int mode, const std::vector<unsigned char>& buf, long lon
   return (double)v;
 }
 
-// The contacts of the last step from the current candidate rows: each pair
-// in contact once, from its lower-id member's row (ids, delta_t, and the
-// recorded force and n x F).
+// The contacts of the last step from the current candidate list (its pairs
+// with flag 1): ids, delta_t, and the force on the lower-id member and
+// n x F as the pair kernel wrote them into that member's row.
 static dem_status download_rows(dem_ctx* ctx, std::vector<int2>& hid, std::vector<double>& dts,
                                 std::vector<double>* F, std::vector<double>* nF) {
   cudaStream_t s = ctx->stream;
@@ -1629,33 +1622,39 @@ static dem_status download_rows(dem_ctx* ctx, std::vector<int2>& hid, std::vecto
   dts.clear();
   const int N = ctx->N;
   if (N == 0) return DEM_OK;
-  cudaError_t e;
-  const int rp = current_rows(ctx, &e);
-  CK(e);
-  const RowList& rl = ctx->dev.rl[rp];
-  std::vector<int> rs(N), rc(N), ids(N);
-  int total = 0;
-  CK(cudaMemcpyAsync(rs.data(), rl.rs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(rc.data(), rl.cnt, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(ids.data(), ctx->ps[0].id, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&total, rl.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+  const VList& c = ctx->vl[0];
+  std::vector<int> rs(N), rc(N);
+  CK(cudaMemcpyAsync(rs.data(), c.hs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(rc.data(), c.oc, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  const long long top = std::min<long long>(total, ctx->dev.Emax);
+  long long top = 0;
+  for (const BoxDev& B : ctx->hbox)
+    for (int g = B.pbase; g < B.pbase + B.nlive; ++g)
+      if (rc[g] > 0) top = std::max(top, (long long)rs[g] + rc[g]);
+  top = std::min<long long>(top, ctx->Cmax);
   const size_t eb = dt_bytes(ctx->mode), vb = v4_bytes(ctx->mode);
-  std::vector<int> fp(std::max(1ll, top));
+  std::vector<int2> h(std::max(1ll, top)), ep(std::max(1ll, top));
   std::vector<unsigned char> fl(std::max(1ll, top)), raw[3], fr, nr;
   for (int a = 0; a < 3; ++a) raw[a].resize(eb * std::max(1ll, top));
+  long long ne = 0;
   if (top > 0) {
-    CK(cudaMemcpyAsync(fp.data(), rl.fp, sizeof(int) * top, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(fl.data(), rl.flag, top, cudaMemcpyDeviceToHost, s));
-    void* const comps[3] = {rl.dx, rl.dy, rl.dz};
+    CK(cudaMemcpyAsync(h.data(), c.hid, sizeof(int2) * top, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(fl.data(), c.flag, top, cudaMemcpyDeviceToHost, s));
+    void* const comps[3] = {c.dx, c.dy, c.dz};
     for (int a = 0; a < 3; ++a)
       CK(cudaMemcpyAsync(raw[a].data(), comps[a], eb * top, cudaMemcpyDeviceToHost, s));
     if (F) {
-      fr.resize(vb * top);
-      nr.resize(vb * top);
-      CK(cudaMemcpyAsync(fr.data(), ctx->dev.Fe, vb * top, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(nr.data(), ctx->dev.Ne, vb * top, cudaMemcpyDeviceToHost, s));
+      int rcount = 0;
+      CK(cudaMemcpyAsync(ep.data(), c.epos, sizeof(int2) * top, cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(&rcount, ctx->dev.rows.count, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      ne = std::min<long long>(rcount, ctx->dev.Emax);
+      fr.resize(vb * std::max(1ll, ne));
+      nr.resize(vb * std::max(1ll, ne));
+      if (ne > 0) {
+        CK(cudaMemcpyAsync(fr.data(), ctx->dev.rows.F, vb * ne, cudaMemcpyDeviceToHost, s));
+        CK(cudaMemcpyAsync(nr.data(), ctx->dev.rows.N, vb * ne, cudaMemcpyDeviceToHost, s));
+      }
     }
     CK(cudaStreamSynchronize(s));
   }
@@ -1664,14 +1663,16 @@ static dem_status download_rows(dem_ctx* ctx, std::vector<int2>& hid, std::vecto
       for (int k = 0; k < rc[g]; ++k) {
         const long long q = (long long)rs[g] + k;
         if (q >= top) break;
-        if (!(fp[q] & 1) || !fl[q]) continue;  // the lower-id member's entry of a contact
-        hid.push_back(make_int2(ids[g], ids[fp[q] >> 1]));
+        if (!fl[q]) continue;  // a candidate pair not in contact
+        hid.push_back(h[q]);
         for (int a = 0; a < 3; ++a) dts.push_back(dt_value(ctx->mode, raw[a], q));
-        if (F)
+        if (F) {
+          const long long e = ep[q].x;
           for (int a = 0; a < 3; ++a) {
-            F->push_back(v4_value(ctx->mode, fr, q, a));
-            nF->push_back(v4_value(ctx->mode, nr, q, a));
+            F->push_back(e >= 0 && e < ne ? v4_value(ctx->mode, fr, e, a) : 0.0);
+            nF->push_back(e >= 0 && e < ne ? v4_value(ctx->mode, nr, e, a) : 0.0);
           }
+        }
       }
   return DEM_OK;
 }
@@ -1885,51 +1886,6 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
       std::memcpy(dst.data() + 4 * k, &f, 4);
     }
   };
-  if (!ctx->fused) {
-    // the contact-list pipeline's rows: each pair in both members' rows, in
-    // increasing partner id; the re-sort of the next step carries them over
-    if (2ll * nc > ctx->dev.Emax) return fail(ctx, DEM_ERR_CAPACITY, "contact list capacity");
-    std::vector<std::vector<std::pair<int, int>>> rows(N);  // (partner id, contact)
-    for (int k = 0; k < nc; ++k) {
-      rows[slots[k].x].push_back({all[k].first.y, k});
-      rows[slots[k].y].push_back({all[k].first.x, k});
-    }
-    std::vector<int> rs(N, 0), rc(N, 0), fp(std::max(1, 2 * nc));
-    const size_t eb = dt_bytes(ctx->mode);
-    std::vector<unsigned char> comp[3];
-    for (int a = 0; a < 3; ++a) comp[a].resize(eb * std::max(1, 2 * nc));
-    int at = 0;
-    for (int g = 0; g < N; ++g) {
-      std::sort(rows[g].begin(), rows[g].end());
-      rs[g] = at;
-      rc[g] = (int)rows[g].size();
-      for (const auto& pr : rows[g]) {
-        const int k = pr.second;
-        const bool low = slots[k].x == g;
-        fp[at] = ((low ? slots[k].y : slots[k].x) << 1) | (low ? 1 : 0);
-        for (int a = 0; a < 3; ++a) encode(comp[a], (size_t)at, all[k].second[a]);
-        ++at;
-      }
-    }
-    cudaError_t e;
-    const int rp = current_rows(ctx, &e);
-    CK(e);
-    const RowList& rl = ctx->dev.rl[rp];
-    if (at > 0) {
-      CK(cudaMemcpyAsync(rl.fp, fp.data(), sizeof(int) * at, cudaMemcpyHostToDevice, s));
-      void* const dst[3] = {rl.dx, rl.dy, rl.dz};
-      for (int a = 0; a < 3; ++a)
-        CK(cudaMemcpyAsync(dst[a], comp[a].data(), eb * at, cudaMemcpyHostToDevice, s));
-      CK(cudaMemsetAsync(rl.flag, 1, at, s));
-    }
-    CK(cudaMemcpyAsync(rl.rs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(rl.cnt, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
-    *ctx->h_count = at;
-    CK(cudaMemcpyAsync(rl.count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(ctx->dev.vctl + kCtlRequest, 1, sizeof(unsigned), s));
-    CK(cudaStreamSynchronize(s));
-    return DEM_OK;
-  }
   std::vector<int> order(nc);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
@@ -1948,19 +1904,29 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
     rc[lo]++;
     for (int a = 0; a < 3; ++a) encode(comp[a], (size_t)k, all[src].second[a]);
   }
-  // the per-particle forms read it as the previous step's list
-  const CList& c = ctx->cl[ctx->parity];
+  // the per-particle forms read it as the previous step's list; the
+  // contact-list pipeline as its current candidate list (every pair in
+  // contact), carried into the list of the re-sort the next step makes
+  int2* c_hid = ctx->fused ? ctx->cl[ctx->parity].hid : ctx->vl[0].hid;
+  int2* c_pair = ctx->fused ? ctx->cl[ctx->parity].pair : ctx->vl[0].pair;
+  void* const c_d[3] = {ctx->fused ? ctx->cl[ctx->parity].dx : ctx->vl[0].dx,
+                        ctx->fused ? ctx->cl[ctx->parity].dy : ctx->vl[0].dy,
+                        ctx->fused ? ctx->cl[ctx->parity].dz : ctx->vl[0].dz};
+  int* c_hs = ctx->fused ? ctx->cl[ctx->parity].hs : ctx->vl[0].hs;
+  int* c_oc = ctx->fused ? ctx->cl[ctx->parity].oc : ctx->vl[0].oc;
+  int* c_count = ctx->fused ? ctx->cl[ctx->parity].count : ctx->vl[0].count;
   if (nc > 0) {
-    CK(cudaMemcpyAsync(c.hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(c.pair, p2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
-    void* const c_d[3] = {c.dx, c.dy, c.dz};
+    CK(cudaMemcpyAsync(c_hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(c_pair, p2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
     for (int a = 0; a < 3; ++a)
       CK(cudaMemcpyAsync(c_d[a], comp[a].data(), eb * nc, cudaMemcpyHostToDevice, s));
+    if (!ctx->fused) CK(cudaMemsetAsync(ctx->vl[0].flag, 1, nc, s));
   }
-  CK(cudaMemcpyAsync(c.hs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(c.oc, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c_hs, rs.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c_oc, rc.data(), sizeof(int) * N, cudaMemcpyHostToDevice, s));
   *ctx->h_count = nc;
-  CK(cudaMemcpyAsync(c.count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c_count, ctx->h_count, sizeof(int), cudaMemcpyHostToDevice, s));
+  if (!ctx->fused) CK(cudaMemsetAsync(ctx->dev.vctl + kCtlRequest, 1, sizeof(unsigned), s));
   CK(cudaStreamSynchronize(s));
   return DEM_OK;
 }
@@ -1974,13 +1940,13 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]) {
   double* part = ctx->staging + 8;
   const int nparts = std::max(1, std::min(512, blocks_for(ctx->hbox[box].nlive, 256)));
   const int p = ctx->parity;
-  const int* hs = ctx->fused ? ctx->cl[p].hs : nullptr;
-  const int* oc = ctx->fused ? ctx->cl[p].oc : nullptr;
-  const int rows = ctx->fused ? 0 : 1;
+  const int* hs = ctx->fused ? ctx->cl[p].hs : ctx->vl[0].hs;
+  const int* oc = ctx->fused ? ctx->cl[p].oc : ctx->vl[0].oc;
+  const unsigned char* fl = ctx->fused ? nullptr : ctx->vl[0].flag;
   switch (ctx->mode) {
-    case kFP64: k_stats<kFP64><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, nullptr, rows, box, part); break;
-    case kMIXED: k_stats<kMIXED><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, nullptr, rows, box, part); break;
-    default: k_stats<kFP32><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, nullptr, rows, box, part); break;
+    case kFP64: k_stats<kFP64><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
+    case kMIXED: k_stats<kMIXED><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
+    default: k_stats<kFP32><<<nparts, 256, 0, s>>>(ctx->dev, ctx->ps[p], hs, oc, fl, box, part); break;
   }
   k_stats_final<<<1, 32, 0, s>>>(part, nparts, dout);
   CK(cudaGetLastError());

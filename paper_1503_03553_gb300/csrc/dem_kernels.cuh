@@ -91,28 +91,24 @@ struct VList {
   void* dy;     // unless the pair was in contact in that step
   void* dz;
   unsigned char* flag;  // 1: in contact in the last step
+  int2* epos;   // the pair's entries in the rows of its lower-id and of its
+                // higher-id member (RowList)
   int* hs;      // by slot: first entry of the pairs the slot found ...
   int* oc;      // ... and how many (the slot's block of the list)
   int* count;   // entries (device scalar)
 };
 
-// The candidate rows of the contact-list pipeline, built at a re-sort from
-// the candidate list: for every slot, all its candidate pairs (both members
-// hold the pair), in increasing partner id, stored contiguously (CSR over
-// slots).  Each entry keeps that pair's tangential history and whether the
-// pair was in contact in the last step; both copies of a pair's history are
-// computed by the same arithmetic in the same orientation (lower id first),
-// so they stay equal.  Two of them: the current rows ([0]) and the ones a
-// re-sort builds ([1]) and then commits into [0].
+// The candidate rows of the contact-list pipeline, built at a re-sort: for
+// every slot, one entry per candidate pair of the slot (both members of a
+// pair have one), in increasing partner id, the rows stored one after
+// another (CSR over slots).  Every step the pair kernel writes each pair's
+// force on a member into that member's entry (zero when not in contact), so
+// a slot's force is the sum of its row, in partner-id order.
 struct RowList {
   int* rs;      // by slot: first entry of its row (a scan over all slots)
   int* cnt;     // by slot: entries in its row
-  int* fp;      // by entry: partner slot << 1 | 1 if the row's slot is the
-                // pair's lower-id member
-  unsigned char* flag;  // by entry: 1 if the pair was in contact in the last step
-  void* dx;     // by entry: delta_t after the last step (DT), zero unless
-  void* dy;     // in contact then
-  void* dz;
+  void* F;      // V4 by entry: force of the pair on the row's slot
+  void* N;      // V4 by entry: n x F of the pair
   int* count;   // entries (device scalar)
 };
 
@@ -157,6 +153,7 @@ struct Dev {
   int* perm;     // scatter position -> old slot (cell order, not yet by id)
   int* pcell;    // scatter position -> linear cell
   int* row;      // N x K: partner slots a slot found
+  int* rowval;   // N x K: scratch of the row build (long rows)
   int* large;    // slots of the large particles of size-binned boxes (the
                  // search appends them; null when no box is size-binned)
   int* nlarge;   // their number (device scalar, reset by the reorder)
@@ -174,11 +171,8 @@ struct Dev {
   void* Fout;    // V4 per slot: total force of the last step
   void* Tout;    // V4 per slot: total torque of the last step
   // contact-list pipeline
-  RowList rl[2];         // candidate rows: [0] current, [1] a re-sort's
-  void* Fe;      // V4 by entry: force of the pair on the row's slot's pair
-  void* Ne;      // V4 by entry: n x F (recorded on the lower-id member's
-                 // entry of each pair in contact, for the contact output)
-  int Emax;      // entry capacity of a row list
+  RowList rows;  // candidate rows (force of each pair on each member)
+  int Emax;      // entry capacity of the rows
   void* xb;      // P per slot: position at the last re-sort (skin test);
   void* yb;      // null for the per-particle Collide forms
   void* zb;
@@ -1812,112 +1806,132 @@ struct RowEpi {
 
 constexpr int kRowSort = 16;  // rows up to this length are ordered in registers
 
+// Each slot's row: its own pairs (its block of vn) and the pairs its partners
+// found (its incoming row), ordered by partner id; each pair learns its two
+// entries (epos) and the entries start at zero force.  The history of the
+// pairs the slot found comes from the current list vo (old slots, reached
+// through the reorder's previous-slot map; the pair is in the block of
+// whichever of its particles found it then).  A row longer than kRowSort is
+// ordered in scratch (d.row, free after the search, and d.rowval).
 template <int M>
 __global__ void __launch_bounds__(256)
-k_rows(Dev d, PState b, VList vs) {
+k_rows(Dev d, PState b, VList vo, VList vn) {
   if (gated_off(d.gate)) return;
-  using DT = typename Tr<M>::DT;
-  const RowList& ro = d.rl[0];  // current rows (old slots)
-  const RowList& rn = d.rl[1];  // the rows being built
+  using T = Tr<M>;
+  using V4 = typename T::V4;
+  using DT = typename T::DT;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
   const int K = d.K;
-  const int base = rn.rs[i];
+  const RowList& rows = d.rows;
+  const int base = rows.rs[i];
   // after an overflow (flagged by the scan) only the part below the
   // capacity is written, and read
-  const int n = min(rn.cnt[i], d.Emax - base);
-  if (n <= 0) return;
-  const int own = vs.oc[i], hs = vs.hs[i];
+  const int n = min(rows.cnt[i], d.Emax - base);
+  const int own = vn.oc[i], hs = vn.hs[i];
   const int* __restrict__ ids = b.id;
-  // (partner id, partner slot << 1 | low) of the row's entries, then ordered
-  // by partner id: in registers for short rows, in place in the row (with
-  // d.row, free after the search, holding the keys) otherwise
-  int key[kRowSort], val[kRowSort];
-  int* kr = d.row + (size_t)i * K;
-  int* vr = rn.fp + base;
-  const bool small = n <= kRowSort;
-  int m = 0;
-  auto put = [&](int k2, int v2) {
-    if (m >= n) return;
+  if (n > 0) {
+    int key[kRowSort], val[kRowSort];
+    int* kr = d.row + (size_t)i * K;     // long rows: partner ids ...
+    int* vr = d.rowval + (size_t)i * K;  // ... and values, in scratch
+    const bool small = n <= kRowSort;
+    int m = 0;
+    auto put = [&](int k2, int v2) {
+      if (m >= n) return;
+      if (small) {
+#pragma unroll
+        for (int q = 0; q < kRowSort; ++q)
+          if (q == m) {
+            key[q] = k2;
+            val[q] = v2;
+          }
+      } else {
+        kr[m] = k2;
+        vr[m] = v2;
+      }
+      ++m;
+    };
+    for (int k = 0; k < own; ++k) {
+      const int c = hs + k;
+      const int2 pr = vn.pair[c];
+      const bool low = pr.x == i;
+      put(ids[low ? pr.y : pr.x], (c << 1) | (low ? 1 : 0));
+    }
+    const int inc = min(d.icnt[i], K);
+    for (int k = 0; k < inc; ++k) {
+      const int2 e = d.inrow[(size_t)i * K + k];
+      put(ids[e.y >> 1], (e.x << 1) | (e.y & 1));
+    }
     if (small) {
+      // insertion sort with compile-time indices (registers)
+#pragma unroll
+      for (int a = 1; a < kRowSort; ++a) {
+#pragma unroll
+        for (int q = a; q > 0; --q) {
+          if (q < m && key[q - 1] > key[q]) {
+            const int tk = key[q], tv = val[q];
+            key[q] = key[q - 1];
+            val[q] = val[q - 1];
+            key[q - 1] = tk;
+            val[q - 1] = tv;
+          }
+        }
+      }
 #pragma unroll
       for (int q = 0; q < kRowSort; ++q)
-        if (q == m) {
-          key[q] = k2;
-          val[q] = v2;
+        if (q < m) {
+          const int c = val[q] >> 1;
+          ((int*)(vn.epos + c))[(val[q] & 1) ? 0 : 1] = base + q;
+          st4((V4*)rows.F + base + q, V4{});
+          st4((V4*)rows.N + base + q, V4{});
         }
     } else {
-      kr[m] = k2;
-      vr[m] = v2;
+      for (int a = 1; a < m; ++a) {
+        const int tk = kr[a], tv = vr[a];
+        int q = a;
+        while (q > 0 && kr[q - 1] > tk) {
+          kr[q] = kr[q - 1];
+          vr[q] = vr[q - 1];
+          --q;
+        }
+        kr[q] = tk;
+        vr[q] = tv;
+      }
+      for (int q = 0; q < m; ++q) {
+        const int c = vr[q] >> 1;
+        ((int*)(vn.epos + c))[(vr[q] & 1) ? 0 : 1] = base + q;
+        st4((V4*)rows.F + base + q, V4{});
+        st4((V4*)rows.N + base + q, V4{});
+      }
     }
-    ++m;
-  };
+  }
+  // history of the pairs this slot found
   for (int k = 0; k < own; ++k) {
-    const int2 pr = vs.pair[hs + k];
-    const bool low = pr.x == i;
-    const int j = low ? pr.y : pr.x;
-    put(ids[j], (j << 1) | (low ? 1 : 0));
-  }
-  const int inc = min(d.icnt[i], K);
-  for (int k = 0; k < inc; ++k) {
-    const int2 e = d.inrow[(size_t)i * K + k];
-    const int j = e.y >> 1;
-    put(ids[j], (j << 1) | (e.y & 1));
-  }
-  if (small) {
-    // insertion sort with compile-time indices (registers)
-#pragma unroll
-    for (int a = 1; a < kRowSort; ++a) {
-#pragma unroll
-      for (int q = a; q > 0; --q) {
-        if (q < m && key[q - 1] > key[q]) {
-          const int tk = key[q], tv = val[q];
-          key[q] = key[q - 1];
-          val[q] = val[q - 1];
-          key[q - 1] = tk;
-          val[q - 1] = tv;
+    const int c = hs + k;
+    const int2 pr = vn.pair[c];
+    const int si = d.prev[pr.x], sj = d.prev[pr.y];
+    int found = -1;
+    for (int u = 0; u < 2 && found < 0; ++u) {
+      const int s0 = u == 0 ? si : sj;
+      const int os = vo.hs[s0], on = vo.oc[s0];
+      for (int e = 0; e < on; ++e) {
+        const int2 h = vo.pair[os + e];
+        if (h.x == si && h.y == sj) {
+          found = os + e;
+          break;
         }
       }
     }
-#pragma unroll
-    for (int q = 0; q < kRowSort; ++q)
-      if (q < m) vr[q] = val[q];
-  } else {
-    for (int a = 1; a < m; ++a) {
-      const int tk = kr[a], tv = vr[a];
-      int q = a;
-      while (q > 0 && kr[q - 1] > tk) {
-        kr[q] = kr[q - 1];
-        vr[q] = vr[q - 1];
-        --q;
-      }
-      kr[q] = tk;
-      vr[q] = tv;
-    }
-  }
-  // history of each entry: the entry of the same partner in the slot's old
-  // row (old slots through the previous-slot map)
-  const int si = d.prev[i];
-  const int os = ro.rs[si], on = min(ro.cnt[si], d.Emax - os);
-  for (int k = 0; k < m; ++k) {
-    const int e = base + k;
-    const int sj = d.prev[vr[k] >> 1];
-    int found = -1;
-    for (int q = 0; q < on; ++q)
-      if ((ro.fp[os + q] >> 1) == sj) {
-        found = os + q;
-        break;
-      }
     if (found >= 0) {
-      ((DT*)rn.dx)[e] = ((const DT*)ro.dx)[found];
-      ((DT*)rn.dy)[e] = ((const DT*)ro.dy)[found];
-      ((DT*)rn.dz)[e] = ((const DT*)ro.dz)[found];
-      rn.flag[e] = ro.flag[found];
+      ((DT*)vn.dx)[c] = ((const DT*)vo.dx)[found];
+      ((DT*)vn.dy)[c] = ((const DT*)vo.dy)[found];
+      ((DT*)vn.dz)[c] = ((const DT*)vo.dz)[found];
+      vn.flag[c] = vo.flag[found];
     } else {
-      ((DT*)rn.dx)[e] = DT{};
-      ((DT*)rn.dy)[e] = DT{};
-      ((DT*)rn.dz)[e] = DT{};
-      rn.flag[e] = 0;
+      ((DT*)vn.dx)[c] = DT{};
+      ((DT*)vn.dy)[c] = DT{};
+      ((DT*)vn.dz)[c] = DT{};
+      vn.flag[c] = 0;
     }
   }
 }
@@ -1925,19 +1939,18 @@ k_rows(Dev d, PState b, VList vs) {
 // The re-sorted state b becomes the current a (the state stays in one place
 // between re-sorts, where the integrator updates it); the positions of this
 // sort are kept for the skin test, the new cell starts become the current
-// order's, and the new rows the current rows.
+// order's, and the new candidate list vn the current vo.
 template <int M>
-__global__ void k_commit(Dev d, PState a, PState b, const int* cs_new, int* cs_cur) {
+__global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const int* cs_new,
+                         int* cs_cur) {
   if (gated_off(d.gate)) return;
   using T = Tr<M>;
   using P = typename T::P;
   using V4 = typename T::V4;
   using PR = typename T::PR;
   using DT = typename T::DT;
-  const RowList& ro = d.rl[0];
-  const RowList& rn = d.rl[1];
-  const int ne = min(*rn.count, d.Emax);
-  const int top = max(max(d.N, d.M_rank), ne);
+  const int nc = min(*vn.count, d.Cmax);
+  const int top = max(max(d.N, d.M_rank), nc);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < top; k += gridDim.x * blockDim.x) {
     if (k < d.N) {
       const BoxDev& B = d.boxes[d.slot_box[k]];
@@ -1965,37 +1978,114 @@ __global__ void k_commit(Dev d, PState a, PState b, const int* cs_new, int* cs_c
           }
         }
       }
+      vo.hs[k] = vn.hs[k];
+      vo.oc[k] = vn.oc[k];
     }
-    if (k < d.N) {
-      ro.rs[k] = rn.rs[k];
-      ro.cnt[k] = rn.cnt[k];
-    }
-    if (k < ne) {
-      ro.fp[k] = rn.fp[k];
-      ro.flag[k] = rn.flag[k];
-      ((DT*)ro.dx)[k] = ((const DT*)rn.dx)[k];
-      ((DT*)ro.dy)[k] = ((const DT*)rn.dy)[k];
-      ((DT*)ro.dz)[k] = ((const DT*)rn.dz)[k];
+    if (k < nc) {
+      vo.pair[k] = vn.pair[k];
+      vo.hid[k] = vn.hid[k];
+      vo.epos[k] = vn.epos[k];
+      ((DT*)vo.dx)[k] = ((const DT*)vn.dx)[k];
+      ((DT*)vo.dy)[k] = ((const DT*)vn.dy)[k];
+      ((DT*)vo.dz)[k] = ((const DT*)vn.dz)[k];
+      vo.flag[k] = vn.flag[k];
     }
     if (k < d.M_rank) cs_cur[k] = cs_new[k];
-    if (k == 0) *ro.count = ne;
+    if (k == 0) *vo.count = nc;
   }
 }
 
-// ---------------------------------------------------------------------------
-// contact-list pipeline, every step: one warp per 32 consecutive slots walks
-// their rows (contiguous) 32 entries at a time.  Each lane applies the
-// contact rule to one entry; the entries in contact are compacted by ballot
-// and their forces computed with every queued lane busy (each pair is
-// evaluated by both of its rows, in the same orientation, lower id first,
-// with the same history, so both get the same bits); then each slot adds its
-// entries of the tile in row order (partner id).  The totals go to Ffused /
-// Tfused for k_gather_integrate: the state is read, never written, here, so
-// every force of the step sees the state at its start.  A pair that left
-// contact loses its history.
-// ---------------------------------------------------------------------------
-constexpr int kStepWarps = 8;
+// One warp takes kPairTile candidate pairs: each lane tests kPairU of them
+// (their loads in flight together), the pairs in contact are compacted by
+// ballot into a warp-local queue in shared memory, and the warp then computes
+// their forces 32 at a time with every lane busy: each pair once, its force
+// on the lower-id member written into that member's row entry and the
+// opposite force into the other member's, n x F into both.  A pair that left
+// contact loses its history and its row entries return to zero.
+constexpr int kPairU = 4;
+constexpr int kPairTile = 32 * kPairU;
+constexpr int kPairWarps = 8;
 
+template <int M>
+__global__ void __launch_bounds__(32 * kPairWarps, M == kFP64 ? 2 : 4)
+k_pairs(Dev d, PState b, VList vl) {
+  using T = Tr<M>;
+  using R = typename T::R;
+  using V4 = typename T::V4;
+  using DT = typename T::DT;
+  __shared__ int qbuf[kPairWarps][kPairTile];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int* q = qbuf[wi];
+  const int nc = min(*vl.count, d.Cmax);
+  const int nw = gridDim.x * kPairWarps;
+  V4* __restrict__ rowF = (V4*)d.rows.F;
+  V4* __restrict__ rowN = (V4*)d.rows.N;
+  int mbox = -1;
+  float m_ov = 0.0f, m_ratio = 0.0f;
+  for (int t0 = (blockIdx.x * kPairWarps + wi) * kPairTile; t0 < nc; t0 += nw * kPairTile) {
+    int2 pr[kPairU];
+#pragma unroll
+    for (int u = 0; u < kPairU; ++u) {
+      const int c = t0 + u * 32 + lane;
+      pr[u] = c < nc ? vl.pair[c] : make_int2(-1, -1);
+    }
+    int qn = 0;
+#pragma unroll
+    for (int u = 0; u < kPairU; ++u) {
+      const int c = t0 + u * 32 + lane;
+      bool hit = false;
+      if (pr[u].x >= 0) {
+        const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[pr[u].x]];
+        hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
+        if (!hit && vl.flag[c]) {
+          ((DT*)vl.dx)[c] = DT{};
+          ((DT*)vl.dy)[c] = DT{};
+          ((DT*)vl.dz)[c] = DT{};
+          vl.flag[c] = 0;
+          const int2 ep = vl.epos[c];
+          st4(rowF + ep.x, V4{});
+          st4(rowF + ep.y, V4{});
+          st4(rowN + ep.x, V4{});
+          st4(rowN + ep.y, V4{});
+        }
+      }
+      const unsigned bal = __ballot_sync(full, hit);
+      if (hit) q[qn + __popc(bal & lt)] = c;
+      qn += __popc(bal);
+    }
+    __syncwarp();
+    for (int k = 0; k < qn; k += 32) {
+      if (k + lane < qn) {
+        const int c = q[k + lane];
+        const int2 p = vl.pair[c];
+        const int box = d.nbox == 1 ? 0 : d.slot_box[p.x];
+        const BoxDev& B = d.boxes[box];
+        PairOut<M> o;
+        pair_law<M>(b, B, p.x, p.y, ((const DT*)vl.dx)[c], ((const DT*)vl.dy)[c],
+                    ((const DT*)vl.dz)[c], o);
+        ((DT*)vl.dx)[c] = o.nx;
+        ((DT*)vl.dy)[c] = o.ny;
+        ((DT*)vl.dz)[c] = o.nz;
+        vl.flag[c] = 1;
+        const int2 ep = vl.epos[c];
+        st4(rowF + ep.x, o.F4);
+        st4(rowF + ep.y, mk4<R>(-o.F4.x, -o.F4.y, -o.F4.z, R(0)));
+        st4(rowN + ep.x, o.N4);
+        st4(rowN + ep.y, o.N4);
+        if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
+      }
+    }
+    __syncwarp();
+  }
+  flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
+}
+
+// ---------------------------------------------------------------------------
+// contact-list pipeline, every step: each slot adds its row (the forces the
+// pair kernel wrote, in partner-id order), then integrate_slot
+// ---------------------------------------------------------------------------
 template <int M>
 __device__ __forceinline__ void integrate_slot(const Dev& d, const PState& b, const BoxDev& B,
                                                int i, v3<typename Tr<M>::R> F,
@@ -2004,119 +2094,29 @@ __device__ __forceinline__ void integrate_slot(const Dev& d, const PState& b, co
                                                int store_ft);
 
 template <int M>
-__global__ void __launch_bounds__(32 * kStepWarps, M == kFP64 ? 2 : 3)
-k_step(Dev d, PState b) {
+__global__ void __launch_bounds__(256, M == kFP64 ? 2 : 4)
+k_rowsum_integrate(Dev d, PState b, int store_ft) {
   using T = Tr<M>;
   using R = typename T::R;
   using V4 = typename T::V4;
-  using DT = typename T::DT;
-  __shared__ typename vec4_of<R>::type cF[kStepWarps][32], cN[kStepWarps][32];
-  __shared__ int qk[kStepWarps][32];
-  __shared__ unsigned char own[kStepWarps][32];
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  const RowList& rl = d.rl[0];
-  const int wbase = (blockIdx.x * kStepWarps + wi) * 32;
-  const int i = wbase + lane;
-  const int K = d.K;
-  bool live = false;
-  int box = 0;
-  int rs_i = 0, n_i = 0;
-  if (i < d.N) {
-    box = d.nbox == 1 ? 0 : d.slot_box[i];
-    live = i - d.boxes[box].pbase < d.boxes[box].nlive;
-    rs_i = rl.rs[i];  // dead slots: an empty row at the running offset
-    n_i = live ? max(0, min(min(rl.cnt[i], K), d.Emax - rs_i)) : 0;
-  } else {
-    rs_i = 0x7fffffff;
-  }
-  // the warp's entries (rows of consecutive slots are consecutive)
-  int e0 = live ? rs_i : 0x7fffffff, e1 = live ? rs_i + n_i : 0;
-  e0 = __reduce_min_sync(full, e0);
-  e1 = __reduce_max_sync(full, e1);
-  int mbox = -1;
-  float m_ov = 0.0f, m_ratio = 0.0f;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[i]];
+  if (i - B.pbase >= B.nlive) return;
+  const int base = d.rows.rs[i];
+  const int n = max(0, min(d.rows.cnt[i], d.Emax - base));
+  const V4* __restrict__ rowF = (const V4*)d.rows.F + base;
+  const V4* __restrict__ rowN = (const V4*)d.rows.N + base;
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
-  for (int t0 = e0; t0 < e1; t0 += 32) {
-    const int e = t0 + lane;
-    // the lane whose row holds entry e: the last lane with rs <= e
-    int lo = 0, hi = 31;
-#pragma unroll
-    for (int it = 0; it < 5; ++it) {
-      const int mid = (lo + hi + 1) >> 1;
-      const int v = __shfl_sync(full, rs_i, mid);
-      if (v <= e) lo = mid;
-      else hi = mid - 1;
-    }
-    const int ol = lo;
-    const int olive = __shfl_sync(full, live ? 1 : 0, ol);
-    const int orow = __shfl_sync(full, rs_i + n_i, ol);
-    const bool ok = e < e1 && olive && e < orow;
-    const int io = wbase + ol;
-    const int obox = __shfl_sync(full, box, ol);
-    const BoxDev& Bo = d.boxes[obox];
-    int fpe = 0;
-    bool hit = false;
-    if (ok) {
-      fpe = rl.fp[e];
-      hit = pair_in_contact<M>(Bo, b, io, fpe >> 1);
-      if (!hit && rl.flag[e]) {
-        ((DT*)rl.dx)[e] = DT{};
-        ((DT*)rl.dy)[e] = DT{};
-        ((DT*)rl.dz)[e] = DT{};
-        rl.flag[e] = 0;
-      }
-    }
-    cF[wi][lane] = typename vec4_of<R>::type{};
-    cN[wi][lane] = typename vec4_of<R>::type{};
-    own[wi][lane] = (unsigned char)ol;
-    const unsigned bal = __ballot_sync(full, hit);
-    if (hit) qk[wi][__popc(bal & lt)] = lane;
-    __syncwarp();
-    if (lane < __popc(bal)) {
-      const int k = qk[wi][lane];
-      const int e2 = t0 + k;
-      const int i2 = wbase + own[wi][k];
-      const int f2 = rl.fp[e2];
-      const int j2 = f2 >> 1;
-      const bool low = f2 & 1;
-      const int ob2 = d.nbox == 1 ? 0 : d.slot_box[i2];
-      const BoxDev& B2 = d.boxes[ob2];
-      PairOut<M> o;
-      pair_law<M>(b, B2, low ? i2 : j2, low ? j2 : i2, ((const DT*)rl.dx)[e2],
-                  ((const DT*)rl.dy)[e2], ((const DT*)rl.dz)[e2], o);
-      ((DT*)rl.dx)[e2] = o.nx;
-      ((DT*)rl.dy)[e2] = o.ny;
-      ((DT*)rl.dz)[e2] = o.nz;
-      rl.flag[e2] = 1;
-      if (low) {
-        // the pair's force as recorded for the contact output (once per pair)
-        st4((V4*)d.Fe + e2, o.F4);
-        st4((V4*)d.Ne + e2, o.N4);
-        cF[wi][k] = o.F4;
-      } else {
-        cF[wi][k] = mk4<R>(-o.F4.x, -o.F4.y, -o.F4.z, R(0));
-      }
-      cN[wi][k] = o.N4;
-      if (o.ov > 0.0f) track_diag(d, ob2, o.ov, o.ratio, mbox, m_ov, m_ratio);
-    }
-    __syncwarp();
-    // this slot's entries of the tile, in row order
-    if (live) {
-      const int ka = max(rs_i, t0) - t0, kb = min(rs_i + n_i, t0 + 32) - t0;
-      for (int k = ka; k < kb; ++k) {
-        F = F + xyz(cF[wi][k]);
-        Ns = Ns + xyz(cN[wi][k]);
-      }
-    }
-    __syncwarp();
+#pragma unroll 1
+  for (int k = 0; k < n; ++k) {
+    F = F + xyz(ld4(rowF + k));
+    Ns = Ns + xyz(ld4(rowN + k));
   }
-  flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
-  if (!live) return;
-  const R r = ((const V4*)b.omg)[i].w;
-  st4((V4*)d.Ffused + i, mk4<R>(F.x, F.y, F.z, R(0)));
-  st4((V4*)d.Tfused + i, mk4<R>(r * Ns.x, r * Ns.y, r * Ns.z, R(0)));
+  const V4 vm = ((const V4*)b.vel)[i];
+  const V4 wr = ((const V4*)b.omg)[i];
+  const R r = wr.w;
+  integrate_slot<M>(d, b, B, i, F, r * Ns, vm, wr, store_ft);
 }
 
 // Whether this step re-sorts: when a particle moved far enough since the
@@ -2695,7 +2695,7 @@ __global__ void k_get_order(Dev d, PState b, int box, int* id_by_slot,
 // (a fixed order: the result does not depend on timing).
 template <int M>
 __global__ void k_stats(Dev d, PState b, const int* hs, const int* oc,
-                        const unsigned char* flag, int rows, int box, double* part) {
+                        const unsigned char* flag, int box, double* part) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   const BoxDev& B = d.boxes[box];
@@ -2713,16 +2713,7 @@ __global__ void k_stats(Dev d, PState b, const int* hs, const int* oc,
     acc[2] += m * vx;
     acc[3] += m * vy;
     acc[4] += m * vz;
-    if (rows) {  // candidate rows: each pair in contact once, on its lower-id member's row
-      const RowList& rl = d.rl[0];
-      int nin = 0;
-      const int cnt = min(rl.cnt[s], d.Emax - rl.rs[s]);
-      for (int k = 0; k < cnt; ++k) {
-        const int e = rl.rs[s] + k;
-        nin += ((rl.fp[e] & 1) && rl.flag[e]) ? 1 : 0;
-      }
-      acc[5] += (double)nin;
-    } else if (flag) {
+    if (flag) {  // candidate list: the pairs in contact in the last step
       int nin = 0;
       for (int k = 0; k < oc[s]; ++k) nin += flag[hs[s] + k] ? 1 : 0;
       acc[5] += (double)nin;
