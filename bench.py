@@ -142,8 +142,6 @@ def phase_bytes(n, c_half, cand_half, ncells, resorts_per_step):
     that re-sort: their bytes are scaled by resorts_per_step."""
     C = c_half * n            # pairs in contact
     Cc = cand_half * n        # candidate pairs
-    E = 2 * Cc                # row entries (each pair in both members' rows)
-    Ec = 2 * C                # row entries in contact
     state = 24 + 16 + 16 + 16 + 4 + 4 + 4 + 4   # x, v, w, predicate record, id, cells
     sort = (ncells * (4 + 4 + 8 + 1 + 1 + 32)        # cell scan, ranges, flags, box reset
             + n * (4 + 4 + 4 + 1)                    # scatter
@@ -151,21 +149,26 @@ def phase_bytes(n, c_half, cand_half, ncells, resorts_per_step):
             + ncells * 32)                           # cell bounding boxes
     search = (n * (16 + 4 + 4 + 4 + 4) + ncells * (8 + 32)
               + Cc * (4 + 8 + 8 + 8 + 4))            # rows, list pairs and ids, incoming rows
-    rows = (n * (4 + 4 + 4 + 4 + 4 + 4)              # lengths, scan, starts, previous slots
-            + E * (4 + 4 + 4 + 1 + 24)               # entries, ids, old rows, flags, history
-            + n * (2 * state + 24))                  # commit: state copy, positions of the sort
-    walls = 0
-    step = (n * (4 + 4 + 16 + 4 + 24 + 16 + 16 + 24)  # rows, record, cell, x, v, w, skin test
-            + n * (24 + 16 + 16 + 16 + 4)             # x, v, w, record, cell written
-            + E * (4 + 1)                              # row entries and flags
-            + Ec * (24 + 24 + 1)                       # history of contacts in and out
-            + C * 32)                                  # recorded pair force
+    rows = (n * (4 + 4 + 4 + 4)                      # blocks, incoming counts, previous slots
+            + Cc * (8 + 8 + 2 * 4 + 8 + 8)           # pairs, incoming rows, row entries, old lists
+            + C * (24 + 1)                           # history carried over
+            + Cc * 2 * (8 + 8 + 24 + 1)              # commit of the list
+            + n * (2 * state + 24))                  # commit of the state, positions of the sort
+    pairs = (Cc * (8 + 1)                                 # list pairs and contact flags
+             + n * (16 + 4 + 24 + 16 + 16)                # record, cell, x, v, w of the particles
+             + C * (24 + 24 + 1 + 16 + 16))               # history in and out, flag, F, n x F
+    sum_ = (n * (4 + 4 * 2 * cand_half)                   # row lengths and entries
+            + 2 * Cc * 1                                  # contact flags of the row entries
+            + C * (16 + 16)                               # F and n x F of each contact
+            + n * (24 + 16 + 16 + 4 + 24 + 4)             # x, v, w, cell, skin test, rank cell
+            + n * (24 + 16 + 16 + 16 + 4))                # x, v, w, record, cell written
     f = resorts_per_step
-    return {"sort": sort * f, "search": search * f, "rows": rows * f, "walls": walls,
-            "step": step}
+    return {"sort": sort * f, "search": search * f, "rows": rows * f, "pairs": pairs,
+            "sum": sum_}
 
 
-PHASES = ["sort", "search", "rows", "walls", "step"]
+PHASES = ["sort", "search", "rows", "pairs", "sum"]
+PHASE_KERNEL = {"pairs": "k_pairs", "sum": "k_gather_integrate"}
 
 
 def _torch_setup(args):
@@ -392,11 +395,12 @@ def main():
     ph_ms = dict(zip(PHASES, ph.tolist()))
     peaks, src = _peaks()
     total_bytes = sum(pb.values())
-    # the dominant kernel: the fused step kernel, every step (the re-sort
-    # kernels run in the steps that re-sort only)
-    dom = "step"
+    # the dominant kernel: of the two that run every step (the re-sort
+    # kernels run in the steps that re-sort only), the slower
+    dom = max(("pairs", "sum"), key=lambda k: ph_ms[k])
     achieved = pb[dom] / (ph_ms[dom] * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_step", "kernel_phase": dom, "achieved": achieved,
+    roof = {"bound": "hbm", "kernel": PHASE_KERNEL[dom], "kernel_phase": dom,
+            "achieved": achieved,
             "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": None,
             "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs; copy test, burst)",
@@ -417,7 +421,7 @@ def main():
             for f in ("dem_kernels.cuh", "dem_common.cuh"):
                 with open(os.path.join(ROOT, "paper_1503_03553_gb300", "csrc", f), "rb") as fh:
                     h.update(fh.read())
-            if (tr.get("kernel") == "k_step" and tr.get("precision") == args.precision
+            if (tr.get("kernel") == PHASE_KERNEL[dom] and tr.get("precision") == args.precision
                     and tr.get("kernel_sha256") == h.hexdigest()):
                 roof["traffic"] = tr["bytes_per_launch"] * n / tr["n"]
                 roof["traffic_source"] = tr.get("source")
@@ -711,11 +715,10 @@ def _contact_phase_ms(ph, fused):
     """The contact part of a step (the paper's Collide): the per-particle
     forms' one kernel (timed as the search phase); for the contact-list
     pipeline the search and rows of its re-sorts (averaged over the steps)
-    and the fused step kernel, whose integration of each particle is a few
-    per cent of it and is counted in."""
+    and the pair kernel."""
     if fused:
         return ph["search"]
-    return ph["search"] + ph["rows"] + ph["step"]
+    return ph["search"] + ph["rows"] + ph["pairs"]
 
 
 def _fused_leg(args, D, torch, stream, box):

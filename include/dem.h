@@ -78,12 +78,11 @@ typedef enum { DEM_HOST = 0, DEM_DEVICE = 1 } dem_where;
 /* Contact-force kernel layout.
  *   DEM_COLLIDE_COMPACT : the contact search writes a candidate list (the
  *                         contacts plus, with a skin, the pairs within the
- *                         skin of contact), kept as one row per particle;
- *                         every step one kernel applies the contact rule to
- *                         each row entry, compacts the contacts by warp
- *                         ballots, computes their forces with every lane
- *                         busy, sums each particle's row in partner-id order
- *                         (no float atomics) and integrates.
+ *                         skin of contact); every step the contact rule is
+ *                         applied to each candidate, the contacts are
+ *                         compacted by warp ballots and one thread per
+ *                         contact computes the force; a per-particle pass
+ *                         sums it in partner-id order (no float atomics).
  *   DEM_COLLIDE_FUSED   : Algorithm 1 of the paper: one thread per particle
  *                         searches and computes the force of each contact as
  *                         it is found (each pair evaluated from both sides).
@@ -304,9 +303,8 @@ dem_status dem_get_stats(dem_ctx* ctx, int32_t box, double out[DEM_NSTATS]);
  * then launched one by one and a step that does not re-sort still launches
  * the re-sort kernels, which return at once).  Phases:
  * [0] sort (scan, scatter, cell order, reorder)  [1] contact search
- * [2] candidate rows and history carry-over  [3] rectangle and line walls
- * [4] contact rule, force, sum, integration and binning (one kernel with
- * DEM_COLLIDE_COMPACT; the per-particle forms' kernel is timed in [1]).
+ * [2] candidate rows and history carry-over  [3] contact rule and force
+ * [4] sum + integrate + bin (+ rectangle and line walls).
  * Returns the number of phases written (<= cap). */
 int32_t dem_get_phase_times(dem_ctx* ctx, double* ms, int32_t cap);
 dem_status dem_set_timing(dem_ctx* ctx, int32_t on);

@@ -148,16 +148,13 @@ uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
 }
 
 // kernels of a step that does not re-sort (DEM_COLLIDE_COMPACT: decide,
-// contacts + sums, integrate; the per-particle forms sort every step)
+// pairs, sum + integrate; the per-particle forms sort every step)
 int launches_per_step(const dem_ctx* ctx) {
   if (ctx->fused) return 7 + (ctx->hwalls.empty() ? 0 : 1);
   return 3 + (ctx->hwalls.empty() ? 0 : 1);
 }
-// kernels a re-sort adds (cell scan x3, scatter, reorder, search, row scan
-// x3, rows, commit)
-int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 11 + (ctx->split ? 1 : 0); }
-
-
+// kernels a re-sort adds (cell scan x3, scatter, reorder, search, rows, commit)
+int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 8 + (ctx->split ? 1 : 0); }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }
@@ -212,7 +209,8 @@ void enqueue_fused(dem_ctx* ctx, int p, bool store_ft) {
   }
   const int bsg = bs < 256 ? bs : 256;  // compiled for at most 256 threads
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
-  k_gather_integrate<M><<<blocks_for(d.N, bsg), bsg, 0, s>>>(d, ctx->ps[q], store_ft ? 1 : 0);
+  k_gather_integrate<M><<<blocks_for(d.N, bsg), bsg, 0, s>>>(d, ctx->ps[q], nullptr,
+                                                            store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -250,16 +248,6 @@ void enqueue_resort(dem_ctx* ctx, cudaStream_t rs, bool tm, cudaEvent_t* ev) {
     k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
   }
   if (tm) cudaEventRecord(ev[2], rs);
-  // rows of the new candidate list: lengths, offsets (scan), entries ordered
-  // by partner id, the history carried over, then the commit
-  const RowLenIn rin{ctx->vl[1].oc, d.icnt, d.K};
-  const RowEpi repi{d.rows.rs, d.rows.cnt, d.rows.count, ctx->vl[1].oc, d.icnt, d.K, d.N, d.Emax,
-                    d.status};
-  const int nbr = blocks_for(d.N, kScanTile);
-  k_scanf_reduce<int, RowLenIn><<<nbr, kScanThreads, 0, rs>>>(rin, d.N, d.scan_bsum, d.gate);
-  k_scan_top<<<1, kScanTopThreads, 0, rs>>>(d.scan_bsum, nbr, nullptr, 0, d.status, 0u, d.gate);
-  k_scanf_apply<int, RowLenIn, RowEpi><<<nbr, kScanThreads, 0, rs>>>(rin, d.N, d.scan_bsum, repi,
-                                                                     d.gate);
   k_rows<M><<<blocks_for(d.N, 256), 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[0], ctx->vl[1]);
   k_commit<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vl[0], ctx->vl[1],
                                             ctx->cs_new, ctx->cs_cur);
@@ -274,10 +262,11 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
   // the sum + integrate kernel is compiled for at most 256 threads per block
   const int bs = ctx->block < 256 ? ctx->block : 256;
   if (tm) cudaEventRecord(ev[3], s);
-  if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
-  if (tm) cudaEventRecord(ev[4], s);
   k_pairs<M><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0]);
-  k_rowsum_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0], store_ft ? 1 : 0);
+  if (tm) cudaEventRecord(ev[4], s);
+  if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
+  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0], ctx->vl[0].flag,
+                                                          store_ft ? 1 : 0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -401,8 +390,8 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   for (int p = 0; p < 2; ++p) {
     ctx->ps[p] = PState{};
     ctx->cl[p] = CList{};
+    ctx->vl[p] = VList{};
   }
-  for (int p = 0; p < 2; ++p) ctx->vl[p] = VList{};
   ctx->cs_cur = ctx->cs_new = nullptr;
   ctx->collect = ctx->chg = nullptr;
   ctx->staging = nullptr;
@@ -593,8 +582,6 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   long long cmax = (long long)N * (ctx->fused ? std::max(4, ctx->K / 2) : std::max(4, ctx->K / 4));
   if (cmax > (1ll << 31) - 1) cmax = (1ll << 31) - 1;
   ctx->Cmax = (int)std::max(1ll, cmax);
-  // candidate rows: every pair in both of its members' rows
-  const long long emax = std::min<long long>(2 * (long long)ctx->Cmax, (1ll << 31) - 1);
   ctx->ko = (int)std::max(1ll, cmax / std::max(1ll, N));
 
   // ---- device allocations ----------------------------------------------------
@@ -604,7 +591,6 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   d.N = ctx->N;
   d.K = ctx->K;
   d.Cmax = ctx->Cmax;
-  d.Emax = (int)emax;
   d.M_lin = ctx->M_lin;
   d.M_rank = ctx->M_rank;
   d.nbox = (int)ctx->hbox.size();
@@ -637,15 +623,15 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   }
   d.icnt = (int*)A(sizeof(int) * n);
   d.prev = (int*)A(sizeof(int) * n);
+  d.Fc = A(v4_bytes(M) * ctx->Cmax);
+  d.nFc = A(v4_bytes(M) * ctx->Cmax);
   if (ctx->fused) {
-    d.Fc = A(v4_bytes(M) * ctx->Cmax);
-    d.nFc = A(v4_bytes(M) * ctx->Cmax);
-  }
-  // per-slot contact totals, from the per-particle kernels or the step kernel
-  d.Ffused = A(v4_bytes(M) * n);
-  d.Tfused = A(v4_bytes(M) * n);
-  if (!ctx->fused) {
+    d.Ffused = A(v4_bytes(M) * n);
+    d.Tfused = A(v4_bytes(M) * n);
+  } else {
     d.inrow = (int2*)A(sizeof(int2) * n * ctx->K);
+    d.frow = (int*)A(sizeof(int) * n * ctx->K);
+    d.fcnt = (int*)A(sizeof(int) * n);
     d.xb = A(pos_bytes(M) * n);
     d.yb = A(pos_bytes(M) * n);
     d.zb = A(pos_bytes(M) * n);
@@ -695,19 +681,10 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
       c.dy = A(dt_bytes(M) * ctx->Cmax);
       c.dz = A(dt_bytes(M) * ctx->Cmax);
       c.flag = (unsigned char*)A(ctx->Cmax);
-      c.epos = (int2*)A(sizeof(int2) * ctx->Cmax);
       c.hs = (int*)A(sizeof(int) * n);
       c.oc = (int*)A(sizeof(int) * n);
       c.count = (int*)A(sizeof(int));
     }
-  }
-  if (!ctx->fused) {
-    d.rows.rs = (int*)A(sizeof(int) * n);
-    d.rows.cnt = (int*)A(sizeof(int) * n);
-    d.rows.F = A(v4_bytes(M) * (size_t)d.Emax);
-    d.rows.N = A(v4_bytes(M) * (size_t)d.Emax);
-    d.rows.count = (int*)A(sizeof(int));
-    d.rowval = (int*)A(sizeof(int) * n * ctx->K);
   }
   ctx->staging = (double*)A(sizeof(double) * 16 * (size_t)std::max(1, max_cap));
   ctx->staging_i = (int*)A(sizeof(int) * 2 * (size_t)std::max(1, max_cap));
@@ -755,11 +732,7 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
     if (!e) e = cudaMemsetAsync(hs, 0, sizeof(int) * n, s);
     if (!e) e = cudaMemsetAsync(cnt, 0, sizeof(int), s);
   }
-  if (!e && !ctx->fused) {
-    e = cudaMemsetAsync(d.rows.rs, 0, sizeof(int) * n, s);
-    if (!e) e = cudaMemsetAsync(d.rows.cnt, 0, sizeof(int) * n, s);
-    if (!e) e = cudaMemsetAsync(d.rows.count, 0, sizeof(int), s);
-  }
+  if (!e && !ctx->fused) e = cudaMemsetAsync(d.fcnt, 0, sizeof(int) * n, s);
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return bail(DEM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
   return DEM_OK;
@@ -1585,98 +1558,6 @@ dem_status dem_get_order(dem_ctx* ctx, int32_t box, int32_t* id_by_slot,
   return DEM_OK;
 }
 
-// Entry values of a row list as doubles (delta_t components, V4 records).
-static double dt_value(int mode, const std::vector<unsigned char>& raw, long long k) {
-  double val;
-  if (mode == kMIXED) {
-    float hl[2];
-    std::memcpy(hl, raw.data() + 8 * k, 8);
-    val = (double)hl[0] + (double)hl[1];
-  } else if (mode == kFP64) {
-    std::memcpy(&val, raw.data() + 8 * k, 8);
-  } else {
-    float f;
-    std::memcpy(&f, raw.data() + 4 * k, 4);
-    val = f;
-  }
-  return val;
-}
-static double v4_value(int mode, const std::vector<unsigned char>& buf, long long k, int a) {
-  if (mode == kFP64) {
-    double v;
-    std::memcpy(&v, buf.data() + 32 * k + 8 * a, 8);
-    return v;
-  }
-  float v;
-  std::memcpy(&v, buf.data() + 16 * k + 4 * a, 4);
-  return (double)v;
-}
-
-// The contacts of the last step from the current candidate list (its pairs
-// with flag 1): ids, delta_t, and the force on the lower-id member and
-// n x F as the pair kernel wrote them into that member's row.
-static dem_status download_rows(dem_ctx* ctx, std::vector<int2>& hid, std::vector<double>& dts,
-                                std::vector<double>* F, std::vector<double>* nF) {
-  cudaStream_t s = ctx->stream;
-  hid.clear();
-  dts.clear();
-  const int N = ctx->N;
-  if (N == 0) return DEM_OK;
-  const VList& c = ctx->vl[0];
-  std::vector<int> rs(N), rc(N);
-  CK(cudaMemcpyAsync(rs.data(), c.hs, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(rc.data(), c.oc, sizeof(int) * N, cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
-  long long top = 0;
-  for (const BoxDev& B : ctx->hbox)
-    for (int g = B.pbase; g < B.pbase + B.nlive; ++g)
-      if (rc[g] > 0) top = std::max(top, (long long)rs[g] + rc[g]);
-  top = std::min<long long>(top, ctx->Cmax);
-  const size_t eb = dt_bytes(ctx->mode), vb = v4_bytes(ctx->mode);
-  std::vector<int2> h(std::max(1ll, top)), ep(std::max(1ll, top));
-  std::vector<unsigned char> fl(std::max(1ll, top)), raw[3], fr, nr;
-  for (int a = 0; a < 3; ++a) raw[a].resize(eb * std::max(1ll, top));
-  long long ne = 0;
-  if (top > 0) {
-    CK(cudaMemcpyAsync(h.data(), c.hid, sizeof(int2) * top, cudaMemcpyDeviceToHost, s));
-    CK(cudaMemcpyAsync(fl.data(), c.flag, top, cudaMemcpyDeviceToHost, s));
-    void* const comps[3] = {c.dx, c.dy, c.dz};
-    for (int a = 0; a < 3; ++a)
-      CK(cudaMemcpyAsync(raw[a].data(), comps[a], eb * top, cudaMemcpyDeviceToHost, s));
-    if (F) {
-      int rcount = 0;
-      CK(cudaMemcpyAsync(ep.data(), c.epos, sizeof(int2) * top, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(&rcount, ctx->dev.rows.count, sizeof(int), cudaMemcpyDeviceToHost, s));
-      CK(cudaStreamSynchronize(s));
-      ne = std::min<long long>(rcount, ctx->dev.Emax);
-      fr.resize(vb * std::max(1ll, ne));
-      nr.resize(vb * std::max(1ll, ne));
-      if (ne > 0) {
-        CK(cudaMemcpyAsync(fr.data(), ctx->dev.rows.F, vb * ne, cudaMemcpyDeviceToHost, s));
-        CK(cudaMemcpyAsync(nr.data(), ctx->dev.rows.N, vb * ne, cudaMemcpyDeviceToHost, s));
-      }
-    }
-    CK(cudaStreamSynchronize(s));
-  }
-  for (const BoxDev& B : ctx->hbox)
-    for (int g = B.pbase; g < B.pbase + B.nlive; ++g)
-      for (int k = 0; k < rc[g]; ++k) {
-        const long long q = (long long)rs[g] + k;
-        if (q >= top) break;
-        if (!fl[q]) continue;  // a candidate pair not in contact
-        hid.push_back(h[q]);
-        for (int a = 0; a < 3; ++a) dts.push_back(dt_value(ctx->mode, raw[a], q));
-        if (F) {
-          const long long e = ep[q].x;
-          for (int a = 0; a < 3; ++a) {
-            F->push_back(e >= 0 && e < ne ? v4_value(ctx->mode, fr, e, a) : 0.0);
-            nF->push_back(e >= 0 && e < ne ? v4_value(ctx->mode, nr, e, a) : 0.0);
-          }
-        }
-      }
-  return DEM_OK;
-}
-
 // Download the current contact list of all boxes as host vectors, walking
 // each particle's (start, count) index: works for the dense list, the fused
 // layout's per-slot blocks and a list restored by dem_set_contacts.
@@ -1685,15 +1566,16 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
                                 std::vector<double>& dts,
                                 std::vector<double>* F = nullptr,
                                 std::vector<double>* nF = nullptr) {
-  if (!ctx->fused) return download_rows(ctx, hid, dts, F, nF);
   cudaStream_t s = ctx->stream;
-  // the per-particle forms' list of the last step
-  const int* c_hs = ctx->cl[ctx->parity].hs;
-  const int* c_oc = ctx->cl[ctx->parity].oc;
-  const int2* c_hid = ctx->cl[ctx->parity].hid;
-  void* const comps[3] = {ctx->cl[ctx->parity].dx, ctx->cl[ctx->parity].dy,
-                          ctx->cl[ctx->parity].dz};
-  const unsigned char* c_flag = nullptr;
+  // the per-particle forms' list of the last step, or the candidate list
+  // (its pairs in contact in the last step carry flag 1)
+  const int* c_hs = ctx->fused ? ctx->cl[ctx->parity].hs : ctx->vl[0].hs;
+  const int* c_oc = ctx->fused ? ctx->cl[ctx->parity].oc : ctx->vl[0].oc;
+  const int2* c_hid = ctx->fused ? ctx->cl[ctx->parity].hid : ctx->vl[0].hid;
+  void* const comps[3] = {ctx->fused ? ctx->cl[ctx->parity].dx : ctx->vl[0].dx,
+                          ctx->fused ? ctx->cl[ctx->parity].dy : ctx->vl[0].dy,
+                          ctx->fused ? ctx->cl[ctx->parity].dz : ctx->vl[0].dz};
+  const unsigned char* c_flag = ctx->fused ? nullptr : ctx->vl[0].flag;
   const int N = ctx->N;
   std::vector<int> rs(N), rc(N);
   hid.clear();
@@ -1873,19 +1755,6 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
     if (slots[k].x < 0 || slots[k].y < 0)
       return fail(ctx, DEM_ERR_STATE, "contact of a particle that holds no slot");
   }
-  auto encode = [&](std::vector<unsigned char>& dst, size_t k, double val) {
-    if (ctx->mode == kMIXED) {
-      float hl[2];
-      hl[0] = (float)val;
-      hl[1] = (float)(val - (double)hl[0]);
-      std::memcpy(dst.data() + 8 * k, hl, 8);
-    } else if (ctx->mode == kFP64) {
-      std::memcpy(dst.data() + 8 * k, &val, 8);
-    } else {
-      float f = (float)val;
-      std::memcpy(dst.data() + 4 * k, &f, 4);
-    }
-  };
   std::vector<int> order(nc);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(),
@@ -1902,7 +1771,20 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
     const int lo = p2[k].x;
     if (rc[lo] == 0) rs[lo] = k;
     rc[lo]++;
-    for (int a = 0; a < 3; ++a) encode(comp[a], (size_t)k, all[src].second[a]);
+    for (int a = 0; a < 3; ++a) {
+      double val = all[src].second[a];
+      if (ctx->mode == kMIXED) {
+        float hl[2];
+        hl[0] = (float)val;
+        hl[1] = (float)(val - (double)hl[0]);
+        std::memcpy(comp[a].data() + 8 * k, hl, 8);
+      } else if (ctx->mode == kFP64) {
+        std::memcpy(comp[a].data() + 8 * k, &val, 8);
+      } else {
+        float f = (float)val;
+        std::memcpy(comp[a].data() + 4 * k, &f, 4);
+      }
+    }
   }
   // the per-particle forms read it as the previous step's list; the
   // contact-list pipeline as its current candidate list (every pair in

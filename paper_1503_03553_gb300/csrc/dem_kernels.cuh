@@ -91,24 +91,8 @@ struct VList {
   void* dy;     // unless the pair was in contact in that step
   void* dz;
   unsigned char* flag;  // 1: in contact in the last step
-  int2* epos;   // the pair's entries in the rows of its lower-id and of its
-                // higher-id member (RowList)
   int* hs;      // by slot: first entry of the pairs the slot found ...
   int* oc;      // ... and how many (the slot's block of the list)
-  int* count;   // entries (device scalar)
-};
-
-// The candidate rows of the contact-list pipeline, built at a re-sort: for
-// every slot, one entry per candidate pair of the slot (both members of a
-// pair have one), in increasing partner id, the rows stored one after
-// another (CSR over slots).  Every step the pair kernel writes each pair's
-// force on a member into that member's entry (zero when not in contact), so
-// a slot's force is the sum of its row, in partner-id order.
-struct RowList {
-  int* rs;      // by slot: first entry of its row (a scan over all slots)
-  int* cnt;     // by slot: entries in its row
-  void* F;      // V4 by entry: force of the pair on the row's slot
-  void* N;      // V4 by entry: n x F of the pair
   int* count;   // entries (device scalar)
 };
 
@@ -153,7 +137,6 @@ struct Dev {
   int* perm;     // scatter position -> old slot (cell order, not yet by id)
   int* pcell;    // scatter position -> linear cell
   int* row;      // N x K: partner slots a slot found
-  int* rowval;   // N x K: scratch of the row build (long rows)
   int* large;    // slots of the large particles of size-binned boxes (the
                  // search appends them; null when no box is size-binned)
   int* nlarge;   // their number (device scalar, reset by the reorder)
@@ -171,8 +154,9 @@ struct Dev {
   void* Fout;    // V4 per slot: total force of the last step
   void* Tout;    // V4 per slot: total torque of the last step
   // contact-list pipeline
-  RowList rows;  // candidate rows (force of each pair on each member)
-  int Emax;      // entry capacity of the rows
+  int* frow;     // N x K: every candidate pair of a slot (entry << 1 | 1 if
+                 // the slot is the lower-id member), in increasing partner id
+  int* fcnt;     // their number per slot
   void* xb;      // P per slot: position at the last re-sort (skin test);
   void* yb;      // null for the per-particle Collide forms
   void* zb;
@@ -1707,208 +1691,127 @@ __device__ __forceinline__ bool pair_in_contact(const BoxDev& B, const PState& b
   return pred_abs(pi, pj, B);
 }
 
-// ---------------------------------------------------------------------------
-// contact-list pipeline, at a re-sort (after the search wrote the candidate
-// list vs in the new slot order of b): each slot's row holds every
-// candidate pair of the slot, the pairs it found (its block of vs) and the
-// pairs its partners found (its incoming row), ordered by partner id; the
-// rows are stored one after another (CSR), at offsets from a scan of their
-// lengths, and each entry takes the pair's history from the current rows
-// (old slots, reached through the reorder's previous-slot map).
-// ---------------------------------------------------------------------------
+// One warp takes kPairTile candidates: each lane tests kPairU of them (their
+// loads in flight together), the pairs in contact are compacted by ballot into
+// a warp-local queue in shared memory, and the warp then computes their
+// forces 32 at a time with every lane busy.  A pair that left contact loses
+// its history.  Every output is written at the pair's own list entry.
+constexpr int kPairU = 4;
+constexpr int kPairTile = 32 * kPairU;
+constexpr int kPairWarps = 8;
 
-// row length of a slot: its own pairs plus the incoming ones, at most K
-struct RowLenIn {
-  const int* oc;
-  const int* icnt;
-  int K;
-  __device__ int operator()(int i) const { return min(oc[i] + icnt[i], K); }
-};
-
-// block scan of a functor's values (the row lengths) with the same
-// three-pass structure as the cell scan
-template <typename T, class In>
-__global__ void __launch_bounds__(kScanThreads)
-k_scanf_reduce(In in, int n, T* __restrict__ bsum, const unsigned* gate) {
-  if (gated_off(gate)) return;
-  const int base = blockIdx.x * kScanTile;
-  T s = 0;
-  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
-    const int idx = base + k;
-    if (idx < n) s += in(idx);
-  }
+template <int M>
+__global__ void __launch_bounds__(32 * kPairWarps, M == kFP64 ? 2 : 4)
+k_pairs(Dev d, PState b, VList vl) {
+  using T = Tr<M>;
+  using V4 = typename T::V4;
+  using DT = typename T::DT;
+  __shared__ int qbuf[kPairWarps][kPairTile];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  int* q = qbuf[wi];
+  const int nc = min(*vl.count, d.Cmax);
+  const int nw = gridDim.x * kPairWarps;
+  int mbox = -1;
+  float m_ov = 0.0f, m_ratio = 0.0f;
+  for (int t0 = (blockIdx.x * kPairWarps + wi) * kPairTile; t0 < nc; t0 += nw * kPairTile) {
+    int2 pr[kPairU];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  __shared__ T ws[kScanThreads / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    T t = 0;
-    for (int q = 0; q < kScanThreads / 32; ++q) t += ws[q];
-    bsum[blockIdx.x] = t;
-  }
-}
-
-template <typename T, class In, class Epi>
-__global__ void __launch_bounds__(kScanThreads)
-k_scanf_apply(In in, int n, const T* __restrict__ bsum, Epi epi, const unsigned* gate) {
-  if (gated_off(gate)) return;
-  __shared__ T buf[kScanTile];
-  __shared__ T tot;
-  const int base = blockIdx.x * kScanTile;
-  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
-    const int idx = base + k;
-    buf[k] = idx < n ? in(idx) : T(0);
-  }
-  __syncthreads();
-  T v[kScanItems];
-  T sum = 0;
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    v[q] = buf[threadIdx.x * kScanItems + q];
-    sum += v[q];
-  }
-  T pre = block_excl_scan<kScanThreads, T>(sum, &tot) + bsum[blockIdx.x];
-#pragma unroll
-  for (int q = 0; q < kScanItems; ++q) {
-    buf[threadIdx.x * kScanItems + q] = pre;
-    pre += v[q];
-  }
-  __syncthreads();
-  for (int k = threadIdx.x; k < kScanTile; k += kScanThreads) {
-    const int idx = base + k;
-    if (idx < n) epi(idx, in(idx), buf[k]);
-  }
-}
-
-// row starts and lengths of the new rows and their total; a slot with more
-// candidates than a row holds sets the row-overflow bit, more entries than a
-// row list holds the list-overflow bit
-struct RowEpi {
-  int* rs;
-  int* cnt;
-  int* count;
-  const int* oc;
-  const int* icnt;
-  int K, N, Emax;
-  unsigned* status;
-  __device__ void operator()(int i, int len, int pre) const {
-    rs[i] = pre;
-    cnt[i] = len;
-    if (oc[i] + icnt[i] > K) atomicOr(status, kStRowOverflow);
-    if (i == N - 1) {
-      const long long tot = (long long)pre + len;
-      if (tot > Emax) atomicOr(status, kStListOverflow);
-      *count = (int)min(tot, (long long)Emax);
+    for (int u = 0; u < kPairU; ++u) {
+      const int c = t0 + u * 32 + lane;
+      pr[u] = c < nc ? vl.pair[c] : make_int2(-1, -1);
     }
+    int qn = 0;
+#pragma unroll
+    for (int u = 0; u < kPairU; ++u) {
+      const int c = t0 + u * 32 + lane;
+      bool hit = false;
+      if (pr[u].x >= 0) {
+        const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[pr[u].x]];
+        hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
+        if (!hit && vl.flag[c]) {
+          ((DT*)vl.dx)[c] = DT{};
+          ((DT*)vl.dy)[c] = DT{};
+          ((DT*)vl.dz)[c] = DT{};
+          vl.flag[c] = 0;
+        }
+      }
+      const unsigned bal = __ballot_sync(full, hit);
+      if (hit) q[qn + __popc(bal & lt)] = c;
+      qn += __popc(bal);
+    }
+    __syncwarp();
+    for (int k = 0; k < qn; k += 32) {
+      if (k + lane < qn) {
+        const int c = q[k + lane];
+        const int2 p = vl.pair[c];
+        const int box = d.nbox == 1 ? 0 : d.slot_box[p.x];
+        const BoxDev& B = d.boxes[box];
+        PairOut<M> o;
+        pair_law<M>(b, B, p.x, p.y, ((const DT*)vl.dx)[c], ((const DT*)vl.dy)[c],
+                    ((const DT*)vl.dz)[c], o);
+        ((DT*)vl.dx)[c] = o.nx;
+        ((DT*)vl.dy)[c] = o.ny;
+        ((DT*)vl.dz)[c] = o.nz;
+        vl.flag[c] = 1;
+        st4((V4*)d.Fc + c, o.F4);
+        st4((V4*)d.nFc + c, o.N4);
+        if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
+      }
+    }
+    __syncwarp();
   }
-};
+  flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
+}
 
-constexpr int kRowSort = 16;  // rows up to this length are ordered in registers
-
-// Each slot's row: its own pairs (its block of vn) and the pairs its partners
-// found (its incoming row), ordered by partner id; each pair learns its two
-// entries (epos) and the entries start at zero force.  The history of the
-// pairs the slot found comes from the current list vo (old slots, reached
-// through the reorder's previous-slot map; the pair is in the block of
-// whichever of its particles found it then).  A row longer than kRowSort is
-// ordered in scratch (d.row, free after the search, and d.rowval).
+// ---------------------------------------------------------------------------
+// contact-list pipeline, at a re-sort (after the search wrote the new
+// candidate list vn in the new slot order of b): each slot's row of all its
+// candidate pairs, ordered by partner id (the order of the force sum, which
+// then does not depend on slots, re-sorts or timing), and the history of the
+// pairs it found carried over from the current list vo (old slots, reached
+// through the reorder's previous-slot map).  d.row, free after the search,
+// holds the partner ids while a row is ordered.
+// ---------------------------------------------------------------------------
 template <int M>
 __global__ void __launch_bounds__(256)
 k_rows(Dev d, PState b, VList vo, VList vn) {
   if (gated_off(d.gate)) return;
-  using T = Tr<M>;
-  using V4 = typename T::V4;
-  using DT = typename T::DT;
+  using DT = typename Tr<M>::DT;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
-  const int K = d.K;
-  const RowList& rows = d.rows;
-  const int base = rows.rs[i];
-  // after an overflow (flagged by the scan) only the part below the
-  // capacity is written, and read
-  const int n = min(rows.cnt[i], d.Emax - base);
-  const int own = vn.oc[i], hs = vn.hs[i];
-  const int* __restrict__ ids = b.id;
-  if (n > 0) {
-    int key[kRowSort], val[kRowSort];
-    int* kr = d.row + (size_t)i * K;     // long rows: partner ids ...
-    int* vr = d.rowval + (size_t)i * K;  // ... and values, in scratch
-    const bool small = n <= kRowSort;
-    int m = 0;
-    auto put = [&](int k2, int v2) {
-      if (m >= n) return;
-      if (small) {
-#pragma unroll
-        for (int q = 0; q < kRowSort; ++q)
-          if (q == m) {
-            key[q] = k2;
-            val[q] = v2;
-          }
-      } else {
-        kr[m] = k2;
-        vr[m] = v2;
-      }
-      ++m;
-    };
-    for (int k = 0; k < own; ++k) {
-      const int c = hs + k;
-      const int2 pr = vn.pair[c];
-      const bool low = pr.x == i;
-      put(ids[low ? pr.y : pr.x], (c << 1) | (low ? 1 : 0));
-    }
-    const int inc = min(d.icnt[i], K);
-    for (int k = 0; k < inc; ++k) {
-      const int2 e = d.inrow[(size_t)i * K + k];
-      put(ids[e.y >> 1], (e.x << 1) | (e.y & 1));
-    }
-    if (small) {
-      // insertion sort with compile-time indices (registers)
-#pragma unroll
-      for (int a = 1; a < kRowSort; ++a) {
-#pragma unroll
-        for (int q = a; q > 0; --q) {
-          if (q < m && key[q - 1] > key[q]) {
-            const int tk = key[q], tv = val[q];
-            key[q] = key[q - 1];
-            val[q] = val[q - 1];
-            key[q - 1] = tk;
-            val[q - 1] = tv;
-          }
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < kRowSort; ++q)
-        if (q < m) {
-          const int c = val[q] >> 1;
-          ((int*)(vn.epos + c))[(val[q] & 1) ? 0 : 1] = base + q;
-          st4((V4*)rows.F + base + q, V4{});
-          st4((V4*)rows.N + base + q, V4{});
-        }
-    } else {
-      for (int a = 1; a < m; ++a) {
-        const int tk = kr[a], tv = vr[a];
-        int q = a;
-        while (q > 0 && kr[q - 1] > tk) {
-          kr[q] = kr[q - 1];
-          vr[q] = vr[q - 1];
-          --q;
-        }
-        kr[q] = tk;
-        vr[q] = tv;
-      }
-      for (int q = 0; q < m; ++q) {
-        const int c = vr[q] >> 1;
-        ((int*)(vn.epos + c))[(vr[q] & 1) ? 0 : 1] = base + q;
-        st4((V4*)rows.F + base + q, V4{});
-        st4((V4*)rows.N + base + q, V4{});
-      }
-    }
+  const BoxDev& B = d.boxes[d.slot_box[i]];
+  if (i - B.pbase >= B.nlive) {
+    d.fcnt[i] = 0;
+    return;
   }
-  // history of the pairs this slot found
+  const int K = d.K;
+  const int own = vn.oc[i], hs = vn.hs[i];
+  const int inc = d.icnt[i];
+  if (own + inc > K) flag(d.status, kStRowOverflow);
+  int* kr = d.row + (size_t)i * K;
+  int* vr = d.frow + (size_t)i * K;
+  int n = 0;
+  auto insert = [&](int key, int val) {
+    if (n >= K) return;
+    int pos = n;
+    while (pos > 0 && kr[pos - 1] > key) {
+      kr[pos] = kr[pos - 1];
+      vr[pos] = vr[pos - 1];
+      --pos;
+    }
+    kr[pos] = key;
+    vr[pos] = val;
+    ++n;
+  };
   for (int k = 0; k < own; ++k) {
     const int c = hs + k;
     const int2 pr = vn.pair[c];
+    const bool low = pr.x == i;
+    insert(b.id[low ? pr.y : pr.x], (c << 1) | (low ? 1 : 0));
+    // history: the pair in the current list, in the block of whichever of
+    // its particles found it then
     const int si = d.prev[pr.x], sj = d.prev[pr.y];
     int found = -1;
     for (int u = 0; u < 2 && found < 0; ++u) {
@@ -1934,12 +1837,18 @@ k_rows(Dev d, PState b, VList vo, VList vn) {
       vn.flag[c] = 0;
     }
   }
+  const int ni = min(inc, K);
+  for (int k = 0; k < ni; ++k) {
+    const int2 e = d.inrow[(size_t)i * K + k];
+    insert(b.id[e.y >> 1], (e.x << 1) | (e.y & 1));
+  }
+  d.fcnt[i] = n;
 }
 
-// The re-sorted state b becomes the current a (the state stays in one place
-// between re-sorts, where the integrator updates it); the positions of this
-// sort are kept for the skin test, the new cell starts become the current
-// order's, and the new candidate list vn the current vo.
+// The re-sorted state b and list vn become the current a and vo (the state
+// stays in one place between re-sorts, where the integrator updates it); the
+// positions of this sort are kept for the skin test, and the new cell starts
+// become the current order's.
 template <int M>
 __global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const int* cs_new,
                          int* cs_cur) {
@@ -1950,7 +1859,7 @@ __global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const in
   using PR = typename T::PR;
   using DT = typename T::DT;
   const int nc = min(*vn.count, d.Cmax);
-  const int top = max(max(d.N, d.M_rank), nc);
+  const int top = max(max(d.N, nc), d.M_rank);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < top; k += gridDim.x * blockDim.x) {
     if (k < d.N) {
       const BoxDev& B = d.boxes[d.slot_box[k]];
@@ -1984,7 +1893,6 @@ __global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const in
     if (k < nc) {
       vo.pair[k] = vn.pair[k];
       vo.hid[k] = vn.hid[k];
-      vo.epos[k] = vn.epos[k];
       ((DT*)vo.dx)[k] = ((const DT*)vn.dx)[k];
       ((DT*)vo.dy)[k] = ((const DT*)vn.dy)[k];
       ((DT*)vo.dz)[k] = ((const DT*)vn.dz)[k];
@@ -1993,130 +1901,6 @@ __global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const in
     if (k < d.M_rank) cs_cur[k] = cs_new[k];
     if (k == 0) *vo.count = nc;
   }
-}
-
-// One warp takes kPairTile candidate pairs: each lane tests kPairU of them
-// (their loads in flight together), the pairs in contact are compacted by
-// ballot into a warp-local queue in shared memory, and the warp then computes
-// their forces 32 at a time with every lane busy: each pair once, its force
-// on the lower-id member written into that member's row entry and the
-// opposite force into the other member's, n x F into both.  A pair that left
-// contact loses its history and its row entries return to zero.
-constexpr int kPairU = 4;
-constexpr int kPairTile = 32 * kPairU;
-constexpr int kPairWarps = 8;
-
-template <int M>
-__global__ void __launch_bounds__(32 * kPairWarps, M == kFP64 ? 2 : 4)
-k_pairs(Dev d, PState b, VList vl) {
-  using T = Tr<M>;
-  using R = typename T::R;
-  using V4 = typename T::V4;
-  using DT = typename T::DT;
-  __shared__ int qbuf[kPairWarps][kPairTile];
-  const unsigned full = 0xffffffffu;
-  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  int* q = qbuf[wi];
-  const int nc = min(*vl.count, d.Cmax);
-  const int nw = gridDim.x * kPairWarps;
-  V4* __restrict__ rowF = (V4*)d.rows.F;
-  V4* __restrict__ rowN = (V4*)d.rows.N;
-  int mbox = -1;
-  float m_ov = 0.0f, m_ratio = 0.0f;
-  for (int t0 = (blockIdx.x * kPairWarps + wi) * kPairTile; t0 < nc; t0 += nw * kPairTile) {
-    int2 pr[kPairU];
-#pragma unroll
-    for (int u = 0; u < kPairU; ++u) {
-      const int c = t0 + u * 32 + lane;
-      pr[u] = c < nc ? vl.pair[c] : make_int2(-1, -1);
-    }
-    int qn = 0;
-#pragma unroll
-    for (int u = 0; u < kPairU; ++u) {
-      const int c = t0 + u * 32 + lane;
-      bool hit = false;
-      if (pr[u].x >= 0) {
-        const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[pr[u].x]];
-        hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
-        if (!hit && vl.flag[c]) {
-          ((DT*)vl.dx)[c] = DT{};
-          ((DT*)vl.dy)[c] = DT{};
-          ((DT*)vl.dz)[c] = DT{};
-          vl.flag[c] = 0;
-          const int2 ep = vl.epos[c];
-          st4(rowF + ep.x, V4{});
-          st4(rowF + ep.y, V4{});
-          st4(rowN + ep.x, V4{});
-          st4(rowN + ep.y, V4{});
-        }
-      }
-      const unsigned bal = __ballot_sync(full, hit);
-      if (hit) q[qn + __popc(bal & lt)] = c;
-      qn += __popc(bal);
-    }
-    __syncwarp();
-    for (int k = 0; k < qn; k += 32) {
-      if (k + lane < qn) {
-        const int c = q[k + lane];
-        const int2 p = vl.pair[c];
-        const int box = d.nbox == 1 ? 0 : d.slot_box[p.x];
-        const BoxDev& B = d.boxes[box];
-        PairOut<M> o;
-        pair_law<M>(b, B, p.x, p.y, ((const DT*)vl.dx)[c], ((const DT*)vl.dy)[c],
-                    ((const DT*)vl.dz)[c], o);
-        ((DT*)vl.dx)[c] = o.nx;
-        ((DT*)vl.dy)[c] = o.ny;
-        ((DT*)vl.dz)[c] = o.nz;
-        vl.flag[c] = 1;
-        const int2 ep = vl.epos[c];
-        st4(rowF + ep.x, o.F4);
-        st4(rowF + ep.y, mk4<R>(-o.F4.x, -o.F4.y, -o.F4.z, R(0)));
-        st4(rowN + ep.x, o.N4);
-        st4(rowN + ep.y, o.N4);
-        if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
-      }
-    }
-    __syncwarp();
-  }
-  flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
-}
-
-// ---------------------------------------------------------------------------
-// contact-list pipeline, every step: each slot adds its row (the forces the
-// pair kernel wrote, in partner-id order), then integrate_slot
-// ---------------------------------------------------------------------------
-template <int M>
-__device__ __forceinline__ void integrate_slot(const Dev& d, const PState& b, const BoxDev& B,
-                                               int i, v3<typename Tr<M>::R> F,
-                                               v3<typename Tr<M>::R> Tq,
-                                               typename Tr<M>::V4 vm, typename Tr<M>::V4 wr,
-                                               int store_ft);
-
-template <int M>
-__global__ void __launch_bounds__(256, M == kFP64 ? 2 : 4)
-k_rowsum_integrate(Dev d, PState b, int store_ft) {
-  using T = Tr<M>;
-  using R = typename T::R;
-  using V4 = typename T::V4;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.N) return;
-  const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[i]];
-  if (i - B.pbase >= B.nlive) return;
-  const int base = d.rows.rs[i];
-  const int n = max(0, min(d.rows.cnt[i], d.Emax - base));
-  const V4* __restrict__ rowF = (const V4*)d.rows.F + base;
-  const V4* __restrict__ rowN = (const V4*)d.rows.N + base;
-  v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
-#pragma unroll 1
-  for (int k = 0; k < n; ++k) {
-    F = F + xyz(ld4(rowF + k));
-    Ns = Ns + xyz(ld4(rowN + k));
-  }
-  const V4 vm = ((const V4*)b.vel)[i];
-  const V4 wr = ((const V4*)b.omg)[i];
-  const R r = wr.w;
-  integrate_slot<M>(d, b, B, i, F, r * Ns, vm, wr, store_ft);
 }
 
 // Whether this step re-sorts: when a particle moved far enough since the
@@ -2416,22 +2200,63 @@ __global__ void k_walls(Dev d, PState b) {
 }
 
 // ---------------------------------------------------------------------------
-// one particle after its contact sums: floor wall (rectangles and lines come
-// from k_walls), gravity, symplectic Euler, then binning for the next step,
-// the contact rule's record and the skin test.  F is the contact force, Tq
-// the contact torque (r times the sum of n x F).
+// per-particle sum (fixed order), floor wall, gravity, symplectic Euler,
+// then binning for the next step
 // ---------------------------------------------------------------------------
 template <int M>
-__device__ __forceinline__ void integrate_slot(const Dev& d, const PState& b, const BoxDev& B,
-                                               int i, v3<typename Tr<M>::R> F,
-                                               v3<typename Tr<M>::R> Tq,
-                                               typename Tr<M>::V4 vm, typename Tr<M>::V4 wr,
-                                               int store_ft) {
+__global__ void __launch_bounds__(256, M == kFP64 ? 2 : 4)
+k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, int store_ft) {
   using T = Tr<M>;
   using P = typename T::P;
   using R = typename T::R;
   using V4 = typename T::V4;
+  using DT = typename T::DT;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.N) return;
+  const BoxDev& B = d.boxes[d.slot_box[i]];
+  if (i - B.pbase >= B.nlive) return;
+  const V4* Fc = (const V4*)d.Fc;
+  const V4* nFc = (const V4*)d.nFc;
+  v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
+  if (!d.Ffused) {
+    // the slot's candidate pairs in increasing partner id, four at a time:
+    // their contact flags first, then the forces of the pairs in contact;
+    // Fc is the force on the pair's lower-id member: added when this slot is
+    // that member, subtracted otherwise; n x F enters with the same sign for
+    // both
+    const int nrow = min(d.fcnt[i], d.K);
+    const int* row = d.frow + (size_t)i * d.K;
+    for (int k = 0; k < nrow; k += 4) {
+      const int4 e4 = *(const int4*)(row + k);
+      const int e[4] = {e4.x, e4.y, e4.z, e4.w};
+      unsigned char f[4];
+      V4 fv[4], qv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) f[u] = k + u < nrow ? vl_flag[e[u] >> 1] : 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (f[u]) {
+          fv[u] = ld4(Fc + (e[u] >> 1));
+          qv[u] = ld4(nFc + (e[u] >> 1));
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!f[u]) continue;
+        if (e[u] & 1) F = F + xyz(fv[u]);
+        else F = F - xyz(fv[u]);
+        Ns = Ns + xyz(qv[u]);
+      }
+    }
+  }
+  V4 vm = ((const V4*)b.vel)[i];
+  V4 wr = ((const V4*)b.omg)[i];
   R m = vm.w, r = wr.w;
+  v3<R> Tq = r * Ns;  // T = r (n x F), same sign for both members of a pair
+  if (d.Ffused) {
+    F = xyz(ld4((const V4*)d.Ffused + i));
+    Tq = xyz(ld4((const V4*)d.Tfused + i));
+  }
   P x = ((P*)b.px)[i], y = ((P*)b.py)[i], z = ((P*)b.pz)[i];
   // Walls (Sec. 3.3 item 5): the floor z = 0 here; rectangles and lines
   // were summed by k_walls into Fwall / Twall.  Each is a body of infinite
@@ -2594,25 +2419,6 @@ __device__ __forceinline__ void integrate_slot(const Dev& d, const PState& b, co
     d.collect[g0] = 1;
     d.collect[g] = 1;
   }
-}
-
-// ---------------------------------------------------------------------------
-// the per-particle Collide forms' sum: their per-slot totals, then
-// integrate_slot
-// ---------------------------------------------------------------------------
-template <int M>
-__global__ void __launch_bounds__(256, M == kFP64 ? 2 : 4)
-k_gather_integrate(Dev d, PState b, int store_ft) {
-  using T = Tr<M>;
-  using V4 = typename T::V4;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.N) return;
-  const BoxDev& B = d.boxes[d.slot_box[i]];
-  if (i - B.pbase >= B.nlive) return;
-  const V4 vm = ((const V4*)b.vel)[i];
-  const V4 wr = ((const V4*)b.omg)[i];
-  integrate_slot<M>(d, b, B, i, xyz(ld4((const V4*)d.Ffused + i)),
-                    xyz(ld4((const V4*)d.Tfused + i)), vm, wr, store_ft);
 }
 
 // ---------------------------------------------------------------------------
