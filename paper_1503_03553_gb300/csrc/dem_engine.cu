@@ -676,7 +676,7 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
     } else {
       VList& c = ctx->vl[p];
       c.pair = (int2*)A(sizeof(int2) * ctx->Cmax);
-      c.hid = (int2*)A(sizeof(int2) * ctx->Cmax);
+      c.hid = nullptr;  // ids come from the slots' ids when they are read
       c.dx = A(dt_bytes(M) * ctx->Cmax);
       c.dy = A(dt_bytes(M) * ctx->Cmax);
       c.dz = A(dt_bytes(M) * ctx->Cmax);
@@ -1571,7 +1571,9 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
   // (its pairs in contact in the last step carry flag 1)
   const int* c_hs = ctx->fused ? ctx->cl[ctx->parity].hs : ctx->vl[0].hs;
   const int* c_oc = ctx->fused ? ctx->cl[ctx->parity].oc : ctx->vl[0].oc;
-  const int2* c_hid = ctx->fused ? ctx->cl[ctx->parity].hid : ctx->vl[0].hid;
+  // ids: the per-particle forms store them; the candidate list stores slots
+  // (lower id first), whose ids are read here
+  const int2* c_hid = ctx->fused ? ctx->cl[ctx->parity].hid : ctx->vl[0].pair;
   void* const comps[3] = {ctx->fused ? ctx->cl[ctx->parity].dx : ctx->vl[0].dx,
                           ctx->fused ? ctx->cl[ctx->parity].dy : ctx->vl[0].dy,
                           ctx->fused ? ctx->cl[ctx->parity].dz : ctx->vl[0].dz};
@@ -1590,6 +1592,12 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
       if (rc[g] > 0) top = std::max(top, (long long)rs[g] + rc[g]);
   top = std::min<long long>(top, ctx->Cmax);
   std::vector<int2> h(top);
+  std::vector<int> slot_id;
+  if (!ctx->fused) {
+    slot_id.resize(N);
+    CK(cudaMemcpyAsync(slot_id.data(), ctx->ps[ctx->parity].id, sizeof(int) * N,
+                       cudaMemcpyDeviceToHost, s));
+  }
   const size_t eb = dt_bytes(ctx->mode), vb = v4_bytes(ctx->mode);
   std::vector<unsigned char> raw[3], fr, nr, fl(std::max(1ll, top), 1);
   for (int a = 0; a < 3; ++a) raw[a].resize(eb * std::max(1ll, top));
@@ -1637,7 +1645,7 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
         long long e = (long long)rs[g] + k;
         if (e >= top) break;
         if (!fl[e]) continue;  // a candidate pair not in contact
-        hid.push_back(h[e]);
+        hid.push_back(ctx->fused ? h[e] : make_int2(slot_id[h[e].x], slot_id[h[e].y]));
         for (int a = 0; a < 3; ++a) dts.push_back(dtval(a, e));
         if (F)
           for (int a = 0; a < 3; ++a) {
@@ -1798,7 +1806,7 @@ dem_status dem_set_contacts(dem_ctx* ctx, int32_t box, int64_t n,
   int* c_oc = ctx->fused ? ctx->cl[ctx->parity].oc : ctx->vl[0].oc;
   int* c_count = ctx->fused ? ctx->cl[ctx->parity].count : ctx->vl[0].count;
   if (nc > 0) {
-    CK(cudaMemcpyAsync(c_hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
+    if (c_hid) CK(cudaMemcpyAsync(c_hid, h2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(c_pair, p2.data(), sizeof(int2) * nc, cudaMemcpyHostToDevice, s));
     for (int a = 0; a < 3; ++a)
       CK(cudaMemcpyAsync(c_d[a], comp[a].data(), eb * nc, cudaMemcpyHostToDevice, s));

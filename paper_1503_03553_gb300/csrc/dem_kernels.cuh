@@ -86,11 +86,12 @@ struct PState {
 // the one a re-sort builds.
 struct VList {
   int2* pair;   // storage slots (lower-id member, higher-id member)
-  int2* hid;    // ids (lo, hi), lo < hi
-  void* dx;     // delta_t after the last step, per component (DT); zero
-  void* dy;     // unless the pair was in contact in that step
+  int2* hid;    // ids (lo, hi), lo < hi; written only when not null
+  void* dx;     // delta_t after the last step, per component (DT), of a
+  void* dy;     // pair in contact in that step
   void* dz;
-  unsigned char* flag;  // 1: in contact in the last step
+  unsigned char* flag;  // 1: in contact in the last step (the history dx,
+                        // dy, dz of a pair without it is not read)
   int* hs;      // by slot: first entry of the pairs the slot found ...
   int* oc;      // ... and how many (the slot's block of the list)
   int* count;   // entries (device scalar)
@@ -1717,10 +1718,12 @@ k_pairs(Dev d, PState b, VList vl) {
   float m_ov = 0.0f, m_ratio = 0.0f;
   for (int t0 = (blockIdx.x * kPairWarps + wi) * kPairTile; t0 < nc; t0 += nw * kPairTile) {
     int2 pr[kPairU];
+    unsigned char fl[kPairU];
 #pragma unroll
     for (int u = 0; u < kPairU; ++u) {
       const int c = t0 + u * 32 + lane;
       pr[u] = c < nc ? vl.pair[c] : make_int2(-1, -1);
+      fl[u] = c < nc ? vl.flag[c] : 0;
     }
     int qn = 0;
 #pragma unroll
@@ -1730,27 +1733,30 @@ k_pairs(Dev d, PState b, VList vl) {
       if (pr[u].x >= 0) {
         const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[pr[u].x]];
         hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
-        if (!hit && vl.flag[c]) {
-          ((DT*)vl.dx)[c] = DT{};
-          ((DT*)vl.dy)[c] = DT{};
-          ((DT*)vl.dz)[c] = DT{};
-          vl.flag[c] = 0;
-        }
+        if (!hit && fl[u]) vl.flag[c] = 0;  // left contact: no history any more
       }
       const unsigned bal = __ballot_sync(full, hit);
-      if (hit) q[qn + __popc(bal & lt)] = c;
+      if (hit) q[qn + __popc(bal & lt)] = (c << 1) | (fl[u] ? 1 : 0);
       qn += __popc(bal);
     }
     __syncwarp();
     for (int k = 0; k < qn; k += 32) {
       if (k + lane < qn) {
-        const int c = q[k + lane];
+        const int qc = q[k + lane];
+        const int c = qc >> 1;
         const int2 p = vl.pair[c];
         const int box = d.nbox == 1 ? 0 : d.slot_box[p.x];
         const BoxDev& B = d.boxes[box];
+        // a pair in contact in the last step has a history; a new one starts
+        // from zero (the stored values of a pair without the flag mean nothing)
+        DT ox = {}, oy = {}, oz = {};
+        if (qc & 1) {
+          ox = ((const DT*)vl.dx)[c];
+          oy = ((const DT*)vl.dy)[c];
+          oz = ((const DT*)vl.dz)[c];
+        }
         PairOut<M> o;
-        pair_law<M>(b, B, p.x, p.y, ((const DT*)vl.dx)[c], ((const DT*)vl.dy)[c],
-                    ((const DT*)vl.dz)[c], o);
+        pair_law<M>(b, B, p.x, p.y, ox, oy, oz, o);
         ((DT*)vl.dx)[c] = o.nx;
         ((DT*)vl.dy)[c] = o.ny;
         ((DT*)vl.dz)[c] = o.nz;
@@ -1825,16 +1831,13 @@ k_rows(Dev d, PState b, VList vo, VList vn) {
         }
       }
     }
-    if (found >= 0) {
+    if (found >= 0 && vo.flag[found]) {
       ((DT*)vn.dx)[c] = ((const DT*)vo.dx)[found];
       ((DT*)vn.dy)[c] = ((const DT*)vo.dy)[found];
       ((DT*)vn.dz)[c] = ((const DT*)vo.dz)[found];
-      vn.flag[c] = vo.flag[found];
+      vn.flag[c] = 1;
     } else {
-      ((DT*)vn.dx)[c] = DT{};
-      ((DT*)vn.dy)[c] = DT{};
-      ((DT*)vn.dz)[c] = DT{};
-      vn.flag[c] = 0;
+      vn.flag[c] = 0;  // no history: the stored values are not read
     }
   }
   const int ni = min(inc, K);
@@ -1892,11 +1895,13 @@ __global__ void k_commit(Dev d, PState a, PState b, VList vo, VList vn, const in
     }
     if (k < nc) {
       vo.pair[k] = vn.pair[k];
-      vo.hid[k] = vn.hid[k];
-      ((DT*)vo.dx)[k] = ((const DT*)vn.dx)[k];
-      ((DT*)vo.dy)[k] = ((const DT*)vn.dy)[k];
-      ((DT*)vo.dz)[k] = ((const DT*)vn.dz)[k];
-      vo.flag[k] = vn.flag[k];
+      const unsigned char f = vn.flag[k];
+      vo.flag[k] = f;
+      if (f) {  // only a pair with the flag has a history
+        ((DT*)vo.dx)[k] = ((const DT*)vn.dx)[k];
+        ((DT*)vo.dy)[k] = ((const DT*)vn.dy)[k];
+        ((DT*)vo.dz)[k] = ((const DT*)vn.dz)[k];
+      }
     }
     if (k < d.M_rank) cs_cur[k] = cs_new[k];
     if (k == 0) *vo.count = nc;
