@@ -177,9 +177,14 @@ typedef struct {
   int32_t collide;            /* dem_collide                                */
   int32_t kn_literal;         /* 1 = k_n with the printed (2 - sigma^2)/E    */
                               /* term of Sec. 2 instead of Hertz 1 - sigma^2 */
-  int32_t row_capacity;       /* max contacts of one particle; 0 = 32       */
+  int32_t row_capacity;       /* max contacts of one particle; 0 = 32;      */
+                              /* rounded up to a multiple of 4, at least 8 */
   int32_t graph_steps;        /* steps per captured CUDA graph; 0 = 16,     */
-                              /* -1 = launch kernels directly              */
+                              /* -1 = launch kernels directly.  With       */
+                              /* DEM_COLLIDE_COMPACT the steps of a call   */
+                              /* beyond a multiple of it run as one-step   */
+                              /* graphs; the other forms launch them       */
+                              /* directly                                  */
   int32_t block;              /* threads per block of per-particle kernels; */
                               /* 0 = 256                                   */
   void* stream;               /* cudaStream_t; NULL = legacy default stream */

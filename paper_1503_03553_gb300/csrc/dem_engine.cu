@@ -6,6 +6,7 @@
 // replays G steps at a time from a captured CUDA graph.
 #include <algorithm>
 #include <array>
+#include <climits>
 #include <mutex>
 #include <cmath>
 #include <cstdio>
@@ -88,7 +89,10 @@ struct dem_ctx {
   int* staging_i = nullptr;      // device, max_cap x 2 ints
   std::string err;
   unsigned sticky = 0;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  // graphs of graph_steps steps by starting parity ([0], [1]); for the
+  // contact-list pipeline also one step without ([2]) and with ([3]) the
+  // force output, which take the steps left over
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
   Timing tm;
   double phase_ms[kPhases] = {};
   int64_t steps_done = 0;
@@ -165,6 +169,16 @@ int blocks_for(long long n, int b) { return (int)((n + b - 1) / b); }
 // --------------------------------------------------------------------------
 // one step, enqueued on ctx->stream
 // --------------------------------------------------------------------------
+// Box 0's constants as a kernel parameter for the one-box kernels (read
+// through the constant cache, and fixed in a captured graph).  Its particle
+// count changes with dem_set_particles, so the copy carries an impossible
+// value there and the kernels read the count from the device array.
+BoxDev box0_param(const dem_ctx* ctx) {
+  BoxDev B = ctx->hbox[0];
+  B.nlive = INT_MIN;
+  return B;
+}
+
 // The per-particle Collide forms (Algorithm 1 and its two-loop form): sort
 // every step from state p into state q, then the per-particle kernel.
 template <int M>
@@ -209,8 +223,13 @@ void enqueue_fused(dem_ctx* ctx, int p, bool store_ft) {
   }
   const int bsg = bs < 256 ? bs : 256;  // compiled for at most 256 threads
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[q]);
-  k_gather_integrate<M><<<blocks_for(d.N, bsg), bsg, 0, s>>>(d, ctx->ps[q], nullptr,
-                                                            store_ft ? 1 : 0);
+  const BoxDev B0 = box0_param(ctx);
+  if (ctx->hbox.size() == 1)
+    k_gather_integrate<M, true><<<blocks_for(d.N, bsg), bsg, 0, s>>>(
+        d, ctx->ps[q], nullptr, store_ft ? 1 : 0, B0);
+  else
+    k_gather_integrate<M, false><<<blocks_for(d.N, bsg), bsg, 0, s>>>(
+        d, ctx->ps[q], nullptr, store_ft ? 1 : 0, B0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -248,7 +267,8 @@ void enqueue_resort(dem_ctx* ctx, cudaStream_t rs, bool tm, cudaEvent_t* ev) {
     k_candidates<M, false><<<blocks_for(d.N, bs_search), bs_search, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
   }
   if (tm) cudaEventRecord(ev[2], rs);
-  k_rows<M><<<blocks_for(d.N, 256), 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[0], ctx->vl[1]);
+  k_rows<M><<<blocks_for(d.N, 256), 256, 0, rs>>>(d, ctx->ps[1], ctx->vl[1]);
+  k_carry<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[0], ctx->vl[0], ctx->vl[1]);
   k_commit<M><<<ctx->nsm * 8, 256, 0, rs>>>(d, ctx->ps[0], ctx->ps[1], ctx->vl[0], ctx->vl[1],
                                             ctx->cs_new, ctx->cs_cur);
 }
@@ -262,11 +282,20 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
   // the sum + integrate kernel is compiled for at most 256 threads per block
   const int bs = ctx->block < 256 ? ctx->block : 256;
   if (tm) cudaEventRecord(ev[3], s);
-  k_pairs<M><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0]);
+  const BoxDev B0 = box0_param(ctx);
+  const bool one = ctx->hbox.size() == 1;
+  if (one)
+    k_pairs<M, true><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0], B0);
+  else
+    k_pairs<M, false><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0], B0);
   if (tm) cudaEventRecord(ev[4], s);
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
-  k_gather_integrate<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0], ctx->vl[0].flag,
-                                                          store_ft ? 1 : 0);
+  if (one)
+    k_gather_integrate<M, true><<<blocks_for(d.N, bs), bs, 0, s>>>(
+        d, ctx->ps[0], ctx->vl[0].flag, store_ft ? 1 : 0, B0);
+  else
+    k_gather_integrate<M, false><<<blocks_for(d.N, bs), bs, 0, s>>>(
+        d, ctx->ps[0], ctx->vl[0].flag, store_ft ? 1 : 0, B0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 
@@ -623,8 +652,7 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   }
   d.icnt = (int*)A(sizeof(int) * n);
   d.prev = (int*)A(sizeof(int) * n);
-  d.Fc = A(v4_bytes(M) * ctx->Cmax);
-  d.nFc = A(v4_bytes(M) * ctx->Cmax);
+  d.Fc = A(2 * v4_bytes(M) * ctx->Cmax);
   if (ctx->fused) {
     d.Ffused = A(v4_bytes(M) * n);
     d.Tfused = A(v4_bytes(M) * n);
@@ -632,6 +660,7 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
     d.inrow = (int2*)A(sizeof(int2) * n * ctx->K);
     d.frow = (int*)A(sizeof(int) * n * ctx->K);
     d.fcnt = (int*)A(sizeof(int) * n);
+    d.next = (int*)A(sizeof(int) * n);
     d.xb = A(pos_bytes(M) * n);
     d.yb = A(pos_bytes(M) * n);
     d.zb = A(pos_bytes(M) * n);
@@ -783,7 +812,8 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
     return s;
   };
   if (ctx->K < 2 || ctx->K > 1024) return bail(DEM_ERR_ARG, "row_capacity out of range");
-  ctx->K = (ctx->K + 3) & ~3;  // rows are read four entries at a time
+  // rows are read four entries at a time, the first eight at once
+  ctx->K = std::max(8, (ctx->K + 3) & ~3);
   if (ctx->block < 32 || ctx->block > 1024 || (ctx->block & 31))
     return bail(DEM_ERR_ARG, "block must be a multiple of 32 in [32, 1024]");
   if (cudaGetDevice(&ctx->device) != cudaSuccess)
@@ -875,6 +905,8 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
   st = upload_box(ctx, box);
   if (st) return st;
   // the box's history is empty: no slot of the box holds a stored contact
+  if (!ctx->fused && B.cap > 0)
+    k_clear_flags<<<blocks_for(B.cap, 256), 256, 0, s>>>(ctx->vl[0], B.pbase, B.cap);
   for (int q = 0; q < 2; ++q)
     CK(cudaMemsetAsync((ctx->fused ? ctx->cl[q].oc : ctx->vl[q].oc) + B.pbase, 0,
                        sizeof(int) * B.cap, s));
@@ -962,14 +994,15 @@ dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
 // keeps its state in place: each step is a decision kernel, a conditional
 // node whose body holds the re-sort kernels (run only when the decision says
 // so), and the pair and integration kernels.
-static dem_status build_graph(dem_ctx* ctx, int p) {
+static dem_status build_graph(dem_ctx* ctx, int p, int nsteps, bool store_last,
+                              cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   int q = p;
   cudaError_t e = cudaSuccess;
   const char* where = "";
-  for (int k = 0; k < ctx->graph_steps && e == cudaSuccess; ++k) {
-    const bool last = k == ctx->graph_steps - 1;
+  for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
+    const bool last = k == nsteps - 1 && store_last;
     if (ctx->fused) {
       q = enqueue(ctx, q, last);
       continue;
@@ -1021,7 +1054,7 @@ static dem_status build_graph(dem_ctx* ctx, int p) {
     return fail(ctx, DEM_ERR_CUDA, std::string("graph capture (") + where + "): " +
                                        cudaGetErrorString(e));
   }
-  e = cudaGraphInstantiate(&ctx->gexec[p], g, 0);
+  e = cudaGraphInstantiate(out, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(ctx, DEM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   return DEM_OK;
@@ -1045,11 +1078,23 @@ dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
     while (left >= ctx->graph_steps) {
       int p = ctx->parity;
       if (!ctx->gexec[p]) {
-        dem_status st = build_graph(ctx, p);
+        dem_status st = build_graph(ctx, p, ctx->graph_steps, true, &ctx->gexec[p]);
         if (st) return st;
       }
       CK(cudaGraphLaunch(ctx->gexec[p], s));
       left -= ctx->graph_steps;  // an even number of steps: parity unchanged
+    }
+    // the contact-list pipeline keeps its state in place: the steps left over
+    // go through one-step graphs (the re-sort kernels skipped, not launched,
+    // in a step that does not re-sort)
+    while (!ctx->fused && left > 0) {
+      const int k = left == 1 ? 3 : 2;
+      if (!ctx->gexec[k]) {
+        dem_status st = build_graph(ctx, ctx->parity, 1, k == 3, &ctx->gexec[k]);
+        if (st) return st;
+      }
+      CK(cudaGraphLaunch(ctx->gexec[k], s));
+      --left;
     }
   }
   auto drain = [&]() -> dem_status {
@@ -1599,7 +1644,7 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
                        cudaMemcpyDeviceToHost, s));
   }
   const size_t eb = dt_bytes(ctx->mode), vb = v4_bytes(ctx->mode);
-  std::vector<unsigned char> raw[3], fr, nr, fl(std::max(1ll, top), 1);
+  std::vector<unsigned char> raw[3], fr, fl(std::max(1ll, top), 1);
   for (int a = 0; a < 3; ++a) raw[a].resize(eb * std::max(1ll, top));
   if (top > 0) {
     CK(cudaMemcpyAsync(h.data(), c_hid, sizeof(int2) * top, cudaMemcpyDeviceToHost, s));
@@ -1607,10 +1652,8 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
       CK(cudaMemcpyAsync(raw[a].data(), comps[a], eb * top, cudaMemcpyDeviceToHost, s));
     if (c_flag) CK(cudaMemcpyAsync(fl.data(), c_flag, top, cudaMemcpyDeviceToHost, s));
     if (F) {
-      fr.resize(vb * top);
-      nr.resize(vb * top);
-      CK(cudaMemcpyAsync(fr.data(), ctx->dev.Fc, vb * top, cudaMemcpyDeviceToHost, s));
-      CK(cudaMemcpyAsync(nr.data(), ctx->dev.nFc, vb * top, cudaMemcpyDeviceToHost, s));
+      fr.resize(2 * vb * top);  // per contact: F, then n x F
+      CK(cudaMemcpyAsync(fr.data(), ctx->dev.Fc, 2 * vb * top, cudaMemcpyDeviceToHost, s));
     }
     CK(cudaStreamSynchronize(s));
   }
@@ -1639,6 +1682,7 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
     std::memcpy(&v, buf.data() + 16 * k + 4 * a, 4);
     return (double)v;
   };
+  // the two vectors of a contact's record
   for (const BoxDev& B : ctx->hbox)
     for (int g = B.pbase; g < B.pbase + B.nlive; ++g)
       for (int k = 0; k < rc[g]; ++k) {
@@ -1649,8 +1693,8 @@ static dem_status download_list(dem_ctx* ctx, std::vector<int2>& hid,
         for (int a = 0; a < 3; ++a) dts.push_back(dtval(a, e));
         if (F)
           for (int a = 0; a < 3; ++a) {
-            F->push_back(v4val(fr, e, a));
-            nF->push_back(v4val(nr, e, a));
+            F->push_back(v4val(fr, 2 * e, a));
+            nF->push_back(v4val(fr, 2 * e + 1, a));
           }
       }
   return DEM_OK;

@@ -27,6 +27,8 @@
 //                                 (Integrate), next binning, skin test
 #pragma once
 
+#include <climits>
+
 #include <type_traits>
 
 #include "dem_common.cuh"
@@ -137,17 +139,21 @@ struct Dev {
                     // as offsets from the cell origin; radius -1 if empty
   int* perm;     // scatter position -> old slot (cell order, not yet by id)
   int* pcell;    // scatter position -> linear cell
-  int* row;      // N x K: partner slots a slot found
+  int* row;      // N x K: partner slots a slot found (the search); the
+                 // partner ids of its candidate row (contact-list pipeline,
+                 // after the search)
   int* large;    // slots of the large particles of size-binned boxes (the
                  // search appends them; null when no box is size-binned)
   int* nlarge;   // their number (device scalar, reset by the reorder)
   int* icnt;     // contacts in which a slot was found by its partner
   int* prev;     // slot of each particle before this step's reorder
+  int* next;     // the inverse: new slot of each slot before the reorder
+                 // (contact-list pipeline; null otherwise)
   int2* inrow;   // N x K: the contacts in which a slot was found by its
                  // partner (any order): (list entry, partner slot << 1 |
                  // 1 if this slot is the lower-id member)
-  void* Fc;      // V4 per contact: force on the lower-id particle
-  void* nFc;     // V4 per contact: n x F
+  void* Fc;      // 2 V4 per contact (one record: 32 bytes in FP32, 64 in
+                 // FP64): the force on the lower-id particle, then n x F
   void* Ffused;  // V4 per slot: contact force sum of the fused layout
   void* Tfused;  // V4 per slot: contact torque sum of the fused layout
   void* Fwall;   // V4 per slot: rectangle and line walls' force (k_walls)
@@ -638,6 +644,7 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
         t = rg.x + rank;
       }
       if (d.prev) d.prev[t] = s;
+      if (d.next) d.next[s] = t;
       P x = ((const P*)a.px)[s], y = ((const P*)a.py)[s], z = ((const P*)a.pz)[s];
       ((P*)b.px)[t] = x;
       ((P*)b.py)[t] = y;
@@ -1694,24 +1701,34 @@ __device__ __forceinline__ bool pair_in_contact(const BoxDev& B, const PState& b
 
 // One warp takes kPairTile candidates: each lane tests kPairU of them (their
 // loads in flight together), the pairs in contact are compacted by ballot into
-// a warp-local queue in shared memory, and the warp then computes their
-// forces 32 at a time with every lane busy.  A pair that left contact loses
-// its history.  Every output is written at the pair's own list entry.
+// a warp-local queue in shared memory (entry, history bit and both slots), and
+// the warp then computes their forces 32 at a time with every lane busy.  A
+// pair that left contact loses its history.  Every output is written at the
+// pair's own list entry.  kOne: the context holds one box, whose constants
+// come in B0 (a kernel parameter, read through the constant cache; its
+// particle count is not valid there and is not read).
 constexpr int kPairU = 4;
 constexpr int kPairTile = 32 * kPairU;
 constexpr int kPairWarps = 8;
 
-template <int M>
+template <bool kOne>
+__device__ __forceinline__ const BoxDev& box_of(const Dev& d, const BoxDev& B0, int slot) {
+  return kOne ? B0 : d.boxes[d.nbox == 1 ? 0 : d.slot_box[slot]];
+}
+
+template <int M, bool kOne>
 __global__ void __launch_bounds__(32 * kPairWarps, M == kFP64 ? 2 : 4)
-k_pairs(Dev d, PState b, VList vl) {
+k_pairs(Dev d, PState b, VList vl, const __grid_constant__ BoxDev B0) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   using DT = typename T::DT;
-  __shared__ int qbuf[kPairWarps][kPairTile];
+  __shared__ int qcb[kPairWarps][kPairTile];
+  __shared__ int2 qpb[kPairWarps][kPairTile];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  int* q = qbuf[wi];
+  int* qc_ = qcb[wi];
+  int2* qp = qpb[wi];
   const int nc = min(*vl.count, d.Cmax);
   const int nw = gridDim.x * kPairWarps;
   int mbox = -1;
@@ -1731,22 +1748,26 @@ k_pairs(Dev d, PState b, VList vl) {
       const int c = t0 + u * 32 + lane;
       bool hit = false;
       if (pr[u].x >= 0) {
-        const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[pr[u].x]];
+        const BoxDev& B = box_of<kOne>(d, B0, pr[u].x);
         hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
         if (!hit && fl[u]) vl.flag[c] = 0;  // left contact: no history any more
       }
       const unsigned bal = __ballot_sync(full, hit);
-      if (hit) q[qn + __popc(bal & lt)] = (c << 1) | (fl[u] ? 1 : 0);
+      if (hit) {
+        const int at = qn + __popc(bal & lt);
+        qc_[at] = (c << 1) | (fl[u] ? 1 : 0);
+        qp[at] = pr[u];
+      }
       qn += __popc(bal);
     }
     __syncwarp();
     for (int k = 0; k < qn; k += 32) {
       if (k + lane < qn) {
-        const int qc = q[k + lane];
+        const int qc = qc_[k + lane];
         const int c = qc >> 1;
-        const int2 p = vl.pair[c];
-        const int box = d.nbox == 1 ? 0 : d.slot_box[p.x];
-        const BoxDev& B = d.boxes[box];
+        const int2 p = qp[k + lane];
+        const int box = kOne ? 0 : (d.nbox == 1 ? 0 : d.slot_box[p.x]);
+        const BoxDev& B = box_of<kOne>(d, B0, p.x);
         // a pair in contact in the last step has a history; a new one starts
         // from zero (the stored values of a pair without the flag mean nothing)
         DT ox = {}, oy = {}, oz = {};
@@ -1761,8 +1782,8 @@ k_pairs(Dev d, PState b, VList vl) {
         ((DT*)vl.dy)[c] = o.ny;
         ((DT*)vl.dz)[c] = o.nz;
         vl.flag[c] = 1;
-        st4((V4*)d.Fc + c, o.F4);
-        st4((V4*)d.nFc + c, o.N4);
+        st4((V4*)d.Fc + 2 * (size_t)c, o.F4);
+        st4((V4*)d.Fc + 2 * (size_t)c + 1, o.N4);
         if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
       }
     }
@@ -1775,77 +1796,183 @@ k_pairs(Dev d, PState b, VList vl) {
 // contact-list pipeline, at a re-sort (after the search wrote the new
 // candidate list vn in the new slot order of b): each slot's row of all its
 // candidate pairs, ordered by partner id (the order of the force sum, which
-// then does not depend on slots, re-sorts or timing), and the history of the
-// pairs it found carried over from the current list vo (old slots, reached
-// through the reorder's previous-slot map).  d.row, free after the search,
-// holds the partner ids while a row is ordered.
+// then does not depend on slots, re-sorts or timing).  The row's entries go
+// to d.frow and the partner ids beside them to d.row (free after the search),
+// where k_carry looks pairs up.  A row of up to 16 entries is loaded into
+// registers and ordered there by a bitonic sorting network (Batcher, 1968):
+// 8 wide when every row of the warp fits, else 16 wide, unused places
+// holding the largest key; a longer row is ordered by insertion in place.
+// The new entries start without history (k_carry brings it).
 // ---------------------------------------------------------------------------
+template <int W>
+__device__ __forceinline__ void bitonic_sort(int (&key)[16], int (&val)[16]) {
+#pragma unroll
+  for (int k = 2; k <= W; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const int v = u ^ j;
+        if (v > u) {
+          const bool up = (u & k) == 0;  // this pair's run ascends
+          const bool sw = up ? key[u] > key[v] : key[u] < key[v];
+          const int ku = key[u], kv = key[v], vu = val[u], vv = val[v];
+          key[u] = sw ? kv : ku;
+          key[v] = sw ? ku : kv;
+          val[u] = sw ? vv : vu;
+          val[v] = sw ? vu : vv;
+        }
+      }
+    }
+  }
+}
+
 template <int M>
 __global__ void __launch_bounds__(256)
-k_rows(Dev d, PState b, VList vo, VList vn) {
+k_rows(Dev d, PState b, VList vn) {
   if (gated_off(d.gate)) return;
-  using DT = typename Tr<M>::DT;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
-  const BoxDev& B = d.boxes[d.slot_box[i]];
+  const BoxDev& B = d.boxes[d.nbox == 1 ? 0 : d.slot_box[i]];
   if (i - B.pbase >= B.nlive) {
     d.fcnt[i] = 0;
     return;
   }
   const int K = d.K;
   const int own = vn.oc[i], hs = vn.hs[i];
-  const int inc = d.icnt[i];
+  const int inc = min(d.icnt[i], K);
   if (own + inc > K) flag(d.status, kStRowOverflow);
+  const int n = min(own + inc, K);
   int* kr = d.row + (size_t)i * K;
   int* vr = d.frow + (size_t)i * K;
-  int n = 0;
-  auto insert = [&](int key, int val) {
-    if (n >= K) return;
-    int pos = n;
-    while (pos > 0 && kr[pos - 1] > key) {
-      kr[pos] = kr[pos - 1];
-      vr[pos] = vr[pos - 1];
-      --pos;
+  const int2* in = d.inrow + (size_t)i * K;
+  for (int k = 0; k < own; ++k) vn.flag[hs + k] = 0;
+  if (n <= 16) {
+    int key[16], val[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      int partner = -1, v = 0;
+      if (k < own) {
+        const int c = hs + k;
+        const int2 pr = vn.pair[c];
+        const bool low = pr.x == i;
+        partner = low ? pr.y : pr.x;
+        v = (c << 1) | (low ? 1 : 0);
+      } else if (k < n) {
+        const int2 e = in[k - own];
+        partner = e.y >> 1;
+        v = (e.x << 1) | (e.y & 1);
+      }
+      key[k] = partner;
+      val[k] = v;
     }
-    kr[pos] = key;
-    vr[pos] = val;
-    ++n;
-  };
-  for (int k = 0; k < own; ++k) {
-    const int c = hs + k;
-    const int2 pr = vn.pair[c];
-    const bool low = pr.x == i;
-    insert(b.id[low ? pr.y : pr.x], (c << 1) | (low ? 1 : 0));
-    // history: the pair in the current list, in the block of whichever of
-    // its particles found it then
-    const int si = d.prev[pr.x], sj = d.prev[pr.y];
-    int found = -1;
-    for (int u = 0; u < 2 && found < 0; ++u) {
-      const int s0 = u == 0 ? si : sj;
-      const int os = vo.hs[s0], on = vo.oc[s0];
-      for (int e = 0; e < on; ++e) {
-        const int2 h = vo.pair[os + e];
-        if (h.x == si && h.y == sj) {
-          found = os + e;
-          break;
-        }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) key[k] = key[k] >= 0 ? b.id[key[k]] : INT_MAX;
+    if (__all_sync(__activemask(), n <= 8)) bitonic_sort<8>(key, val);
+    else bitonic_sort<16>(key, val);
+#pragma unroll
+    for (int k = 0; k < 16; k += 4) {
+      if (k < n) {
+        *(int4*)(kr + k) = make_int4(key[k], key[k + 1], key[k + 2], key[k + 3]);
+        *(int4*)(vr + k) = make_int4(val[k], val[k + 1], val[k + 2], val[k + 3]);
       }
     }
-    if (found >= 0 && vo.flag[found]) {
-      ((DT*)vn.dx)[c] = ((const DT*)vo.dx)[found];
-      ((DT*)vn.dy)[c] = ((const DT*)vo.dy)[found];
-      ((DT*)vn.dz)[c] = ((const DT*)vo.dz)[found];
-      vn.flag[c] = 1;
-    } else {
-      vn.flag[c] = 0;  // no history: the stored values are not read
+  } else {
+    int m = 0;
+    auto insert = [&](int key, int val) {
+      int pos = m;
+      while (pos > 0 && kr[pos - 1] > key) {
+        kr[pos] = kr[pos - 1];
+        vr[pos] = vr[pos - 1];
+        --pos;
+      }
+      kr[pos] = key;
+      vr[pos] = val;
+      ++m;
+    };
+    for (int k = 0; k < n; ++k) {
+      if (k < own) {
+        const int c = hs + k;
+        const int2 pr = vn.pair[c];
+        const bool low = pr.x == i;
+        insert(b.id[low ? pr.y : pr.x], (c << 1) | (low ? 1 : 0));
+      } else {
+        const int2 e = in[k - own];
+        insert(b.id[e.y >> 1], (e.x << 1) | (e.y & 1));
+      }
     }
   }
-  const int ni = min(inc, K);
-  for (int k = 0; k < ni; ++k) {
-    const int2 e = d.inrow[(size_t)i * K + k];
-    insert(b.id[e.y >> 1], (e.x << 1) | (e.y & 1));
-  }
   d.fcnt[i] = n;
+}
+
+// History carried over at a re-sort: each pair of the current list vo that
+// was in contact in the last step (its flag) is looked up in the new row of
+// its lower-id member (new slot from the reorder's map d.next; the partner
+// found by id among the row's keys), and its delta_t goes to the new entry
+// there, which gets the flag.  A pair that is no longer a candidate loses
+// its history.  Four entries per thread, their loads in flight together.
+constexpr int kCarryU = 4;
+
+template <int M>
+__global__ void __launch_bounds__(256)
+k_carry(Dev d, PState a, VList vo, VList vn) {
+  if (gated_off(d.gate)) return;
+  using DT = typename Tr<M>::DT;
+  const int nc = min(*vo.count, d.Cmax);
+  const int K = d.K;
+  const int stride = gridDim.x * blockDim.x;
+  for (int c0 = blockIdx.x * blockDim.x + threadIdx.x; c0 < nc; c0 += kCarryU * stride) {
+    int c[kCarryU], ni[kCarryU], idj[kCarryU], e[kCarryU];
+    bool f[kCarryU];
+#pragma unroll
+    for (int u = 0; u < kCarryU; ++u) {
+      c[u] = c0 + u * stride;
+      // every listed pair holds two valid slots: the map and id loads need
+      // not wait for the flag
+      int2 p = make_int2(0, 0);
+      unsigned char fl = 0;
+      if (c[u] < nc) {
+        fl = vo.flag[c[u]];
+        p = vo.pair[c[u]];
+      }
+      ni[u] = d.next[p.x];
+      idj[u] = a.id[p.y];
+      f[u] = fl != 0;
+    }
+#pragma unroll
+    for (int u = 0; u < kCarryU; ++u) {
+      e[u] = -1;
+      if (!f[u]) continue;
+      const int* kr = d.row + (size_t)ni[u] * K;
+      const int n = min(d.fcnt[ni[u]], K);
+      const int4 q0 = *(const int4*)kr, q1 = *(const int4*)(kr + 4);
+      const int q[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      int at = -1;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (k < n && q[k] == idj[u]) at = k;
+      for (int k = 8; at < 0 && k < n; ++k)
+        if (kr[k] == idj[u]) at = k;
+      if (at >= 0) e[u] = d.frow[(size_t)ni[u] * K + at] >> 1;
+    }
+#pragma unroll
+    for (int u = 0; u < kCarryU; ++u) {
+      if (e[u] < 0) continue;
+      ((DT*)vn.dx)[e[u]] = ((const DT*)vo.dx)[c[u]];
+      ((DT*)vn.dy)[e[u]] = ((const DT*)vo.dy)[c[u]];
+      ((DT*)vn.dz)[e[u]] = ((const DT*)vo.dz)[c[u]];
+      vn.flag[e[u]] = 1;
+    }
+  }
+}
+
+// A box given new particles keeps no history: the contact flags of the
+// entries in its slots' blocks of the current list are cleared.
+__global__ void k_clear_flags(VList vo, int pbase, int cap) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= cap) return;
+  const int hs = vo.hs[pbase + s], oc = vo.oc[pbase + s];
+  for (int k = 0; k < oc; ++k) vo.flag[hs + k] = 0;
 }
 
 // The re-sorted state b and list vn become the current a and vo (the state
@@ -1984,8 +2111,8 @@ k_collide_per_particle(Dev d, PState b, CList co, CList cn, int ko) {
           ((DT*)cn.dx)[cc] = o.nx;
           ((DT*)cn.dy)[cc] = o.ny;
           ((DT*)cn.dz)[cc] = o.nz;
-          st4((V4*)d.Fc + cc, o.F4);
-          st4((V4*)d.nFc + cc, o.N4);
+          st4((V4*)d.Fc + 2 * (size_t)cc, o.F4);
+          st4((V4*)d.Fc + 2 * (size_t)cc + 1, o.N4);
           ++own;
         } else {
           over = true;
@@ -2207,10 +2334,13 @@ __global__ void k_walls(Dev d, PState b) {
 // ---------------------------------------------------------------------------
 // per-particle sum (fixed order), floor wall, gravity, symplectic Euler,
 // then binning for the next step
+// (kOne: one box, its constants in B0 as in k_pairs; the particle count is
+// read from the box array)
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, bool kOne>
 __global__ void __launch_bounds__(256, M == kFP64 ? 2 : 4)
-k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, int store_ft) {
+k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, int store_ft,
+                   const __grid_constant__ BoxDev B0) {
   using T = Tr<M>;
   using P = typename T::P;
   using R = typename T::R;
@@ -2218,10 +2348,10 @@ k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, i
   using DT = typename T::DT;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.N) return;
-  const BoxDev& B = d.boxes[d.slot_box[i]];
-  if (i - B.pbase >= B.nlive) return;
+  const int bi = kOne ? 0 : d.slot_box[i];
+  const BoxDev& B = kOne ? B0 : d.boxes[bi];
+  if (i - B.pbase >= d.boxes[bi].nlive) return;
   const V4* Fc = (const V4*)d.Fc;
-  const V4* nFc = (const V4*)d.nFc;
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
   if (!d.Ffused) {
     // the slot's candidate pairs in increasing partner id, four at a time:
@@ -2241,8 +2371,8 @@ k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, i
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (f[u]) {
-          fv[u] = ld4(Fc + (e[u] >> 1));
-          qv[u] = ld4(nFc + (e[u] >> 1));
+          fv[u] = ld4(Fc + 2 * (size_t)(e[u] >> 1));
+          qv[u] = ld4(Fc + 2 * (size_t)(e[u] >> 1) + 1);
         }
       }
 #pragma unroll
