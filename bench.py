@@ -541,8 +541,10 @@ def _side_legs(args, D, torch, box, ncell, stream, skin):
     leg("collide_fused_vs_compact", lambda: _fused_leg(args, D, torch, stream, box))
     leg("size_binned_search", lambda: _size_binned_leg(args, D, torch, stream, box, ncell))
     leg("fig4_kernel_times_131k", lambda: _fig4_leg(args, D, torch, stream))
+    skin_frac = skin / box.r_max  # the W2 skin as a fraction of the largest radius
+    leg("layout_tuner", lambda: _tuner_leg(args, D, torch, stream, box, skin_frac))
     if not args.no_batched:
-        leg("batched", lambda: _batched_leg(args, D, torch, stream))
+        leg("batched", lambda: _batched_leg(args, D, torch, stream, skin_frac))
     if args.w3:
         leg("w3_floor_8M", lambda: _w3_leg(args, D, torch, stream))
     if args.w5:
@@ -822,22 +824,40 @@ def _fig4_leg(args, D, torch, stream):
     return out
 
 
-def _batched_leg(args, D, torch, stream):
+def _w4_boxes(args):
+    from paper_1503_03553_gb300 import synth
+    from paper_1503_03553_gb300.synth import prepared
+    procs = max(1, min(16, os.cpu_count() or 1))
+    return [prepared(b, "mixed") for b in synth.w4_batched(nboxes=args.nboxes, processes=procs)]
+
+
+_W4 = {}
+
+
+def _w4_cached(args):
+    """W4's boxes, generated once per run (the tuner and batched legs)."""
+    if "b" not in _W4:
+        _W4["b"] = _w4_boxes(args)
+    return _W4["b"]
+
+
+def _batched_leg(args, D, torch, stream, skin_frac):
     """W4: many independent periodic boxes in one context (one launch per
     kernel for all boxes, CUDA graphs) against the same boxes stepped one
-    context at a time."""
-    from paper_1503_03553_gb300 import synth
-    from paper_1503_03553_gb300.synth import grid_for, prepared
-    procs = max(1, min(16, os.cpu_count() or 1))
-    boxes = [prepared(b, "mixed") for b in synth.w4_batched(nboxes=args.nboxes, processes=procs)]
-    ncells = [grid_for(b) for b in boxes]
+    context at a time; every box keeps a skin of the same fraction of its
+    largest radius as the W2 line."""
+    from paper_1503_03553_gb300.synth import grid_for
+    boxes = _w4_cached(args)
+    skins = [skin_frac * b.r_max for b in boxes]
+    ncells = [grid_for(b, skin=sk) for b, sk in zip(boxes, skins)]
     steps = args.batched_steps
-    res = {"boxes": len(boxes), "particles": int(sum(b.n for b in boxes)), "steps": steps}
-    res["batched"] = _throughput(D, torch, stream, boxes, "mixed", ncells, steps)
+    res = {"boxes": len(boxes), "particles": int(sum(b.n for b in boxes)), "steps": steps,
+           "skin_over_rmax": skin_frac}
+    res["batched"] = _throughput(D, torch, stream, boxes, "mixed", ncells, steps, skins=skins)
     total = 0.0
-    for b, nc in zip(boxes, ncells):
+    for b, nc, sk in zip(boxes, ncells, skins):
         with torch.cuda.stream(stream):
-            ctx = D.Context([b], precision="mixed", ncell=[nc])
+            ctx = D.Context([b], precision="mixed", ncell=[nc], skins=[sk])
         try:
             _reset(ctx, [b])
             ctx.step(3)
@@ -849,6 +869,44 @@ def _batched_leg(args, D, torch, stream):
                          "ms_per_step": total / steps * 1e3}
     res["speedup"] = res["batched"]["value"] / res["box_by_box"]["value"]
     return res
+
+
+def _tuner_leg(args, D, torch, stream, box, skin_frac):
+    """The layout tuner (dem_autotune_layout: skin, cell grid, size split,
+    block size, graph length) on W2, on a W3-law box of 1,000,000
+    particles (floor and gravity) and on W4's boxes: its choice, and steps
+    1..K from the initial state with the bench's default layout and with the
+    tuned one (a new context with the chosen skin and grid per box)."""
+    import dataclasses
+    from paper_1503_03553_gb300 import synth
+    from paper_1503_03553_gb300.synth import grid_for, prepared
+    steps = args.steps
+    cases = [("w2", [box])]
+    cases.append(("w3_1M", [prepared(synth.w3_bidisperse_floor(n=1_000_000), "mixed")]))
+    if not args.no_batched:
+        cases.append(("w4", _w4_cached(args)))
+    out = {}
+    for name, boxes in cases:
+        skins = [skin_frac * b.r_max for b in boxes]
+        ncells = [grid_for(b, skin=sk) for b, sk in zip(boxes, skins)]
+        res = {"particles": int(sum(b.n for b in boxes)), "boxes": len(boxes)}
+        res["default"] = _throughput(D, torch, stream, boxes, "mixed", ncells, steps, skins=skins)
+        with torch.cuda.stream(stream):
+            ctx = D.Context(boxes, precision="mixed", ncell=ncells, skins=skins)
+        try:
+            _reset(ctx, boxes)
+            res["choice"] = ctx.autotune_layout(steps=16)
+            lay = [ctx.layout(k) for k in range(len(boxes))]
+        finally:
+            ctx.close()
+        tb = [dataclasses.replace(b, r_split=lay[k]["r_split"]) for k, b in enumerate(boxes)]
+        res["tuned"] = _throughput(D, torch, stream, tb, "mixed", [l["ncell"] for l in lay], steps,
+                                   skins=[l["skin"] for l in lay],
+                                   block=res["choice"]["block"],
+                                   graph_steps=res["choice"]["graph_steps"])
+        res["tuned_layout_box0"] = lay[0]
+        out[name] = res
+    return out
 
 
 if __name__ == "__main__":

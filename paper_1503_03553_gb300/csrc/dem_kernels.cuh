@@ -590,8 +590,9 @@ __global__ void k_scatter(Dev d, PState a) {
   if (!d.chg[g]) {
     pos = d.cstart[g] + (s - d.cstart_old[g]);
   } else {
+    const int cnt = d.ccount[g];  // loaded beside the atomic, not after it
     const int k = atomicAdd(&d.ccur[g], 1);
-    if (k >= d.ccount[g]) {  // counts out of step: report
+    if (k >= cnt) {  // counts out of step: report
       flag(d.status, kStInconsistent);
       return;
     }
@@ -638,9 +639,18 @@ __global__ void k_reorder(Dev d, PState a, PState b, int* cursor) {
       const int key = a.id[s];
       int t = q;  // final slot
       if (changed) {
+        // the cell-mates' ids, eight at a time: their scatter entries, then
+        // their ids, each batch of loads in flight together
         const int2 rg = d.crange[lin];
+        const int end = rg.x + rg.y;
         int rank = 0;
-        for (int u = rg.x; u < rg.x + rg.y; ++u) rank += a.id[d.perm[u]] < key ? 1 : 0;
+        for (int u0 = rg.x; u0 < end; u0 += 8) {
+          int pu[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) pu[k] = u0 + k < end ? d.perm[u0 + k] : -1;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) rank += (pu[k] >= 0 && a.id[pu[k]] < key) ? 1 : 0;
+        }
         t = rg.x + rank;
       }
       if (d.prev) d.prev[t] = s;
@@ -1383,15 +1393,15 @@ __device__ __forceinline__ void geom_fixed(const BoxDev& B, long long X1,
                  f32_to_i64_rn(__fmul_rn(r2, kInvQ), &bad);
   u128 R2 = {0ull, 0ull};
   u128_add_sq(R2, (unsigned long long)Rq);
-  float distq = sqrtf(u128_to_f32(S));
+  float distq = fsqrt(u128_to_f32(S));
   if (u128_less(S, R2)) {
     float num = u128_to_f32(u128_sub(R2, S));
-    dn = __fmul_rn(num / (i64_to_f32_rn(Rq) + distq), kQ);
+    dn = __fmul_rn(fdiv(num, i64_to_f32_rn(Rq) + distq), kQ);
   } else {
     dn = 0.0f;
   }
   if (distq > 0.0f) {
-    float inv = 1.0f / distq;
+    float inv = frcp(distq);
     n = {i64_to_f32_rn(D[0]) * inv, i64_to_f32_rn(D[1]) * inv,
          i64_to_f32_rn(D[2]) * inv};
   } else {
@@ -1438,23 +1448,23 @@ __device__ __forceinline__ void contact_law(
   R dd = dot(dt_old, n);
   dt_delta = (dtstep * vt) - (dd * n);                     // Eq. (dt) increment
   v3<R> dtn = dt_old + dt_delta;
-  R Rs = wall ? r1 : r1 * r2 / (r1 + r2);
-  R ms = wall ? m1 : m1 * m2 / (m1 + m2);
-  R sdn = sqrt(dn);
-  R kn = kn_c * sqrt(Rs);
-  R kt = kt_c * sqrt(Rs * dn);
-  R eta = alpha * sqrt(ms * kn * sdn);                     // eta_n = eta_t
+  R Rs = wall ? r1 : fdiv(r1 * r2, r1 + r2);
+  R ms = wall ? m1 : fdiv(m1 * m2, m1 + m2);
+  R sdn = fsqrt(dn);
+  R kn = kn_c * fsqrt(Rs);
+  R kt = kt_c * fsqrt(Rs * dn);
+  R eta = alpha * fsqrt(ms * kn * sdn);                     // eta_n = eta_t
   R fel = kn * dn * sdn;
   v3<R> Fn = (-fel) * n - eta * vn;                        // Eq. (1), normal
   v3<R> Ft = (-kt) * dtn - eta * vt;                       // Eq. (1), tangential
-  R aFn = norm(Fn), aFt = norm(Ft);
+  R aFn = fsqrt(dot(Fn, Fn)), aFt = fsqrt(dot(Ft, Ft));
   R lim = mu * aFn;
-  o.ratio = lim > R(0) ? aFt / lim : (aFt > R(0) ? R(1e30) : R(0));
+  o.ratio = lim > R(0) ? fdiv(aFt, lim) : (aFt > R(0) ? R(1e30) : R(0));
   o.capped = aFt > lim;
   if (o.capped) {                                          // Eq. (sliding friction)
-    R s = lim / aFt;
+    R s = fdiv(lim, aFt);
     Ft = s * Ft;
-    dtn = (R(-1) / kt) * Ft;                               // F_t,new = -k_t delta_t
+    dtn = (-frcp(kt)) * Ft;                                // F_t,new = -k_t delta_t
   }
   o.dt = dtn;
   o.F = Fn + Ft;
@@ -1563,7 +1573,7 @@ __device__ __forceinline__ void pair_law(const PState& b, const BoxDev& B, int i
   out.F4 = mk4<R>(o.F.x, o.F.y, o.F.z, R(0));
   out.N4 = mk4<R>(o.nF.x, o.nF.y, o.nF.z, R(0));
   R rmin = r1 < r2 ? r1 : r2;
-  out.ov = (float)(dn / rmin);
+  out.ov = (float)fdiv(dn, rmin);
   out.ratio = (float)o.ratio;
 }
 

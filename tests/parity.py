@@ -135,6 +135,32 @@ def _explain(box, g, o, idx):
     return "\n".join(lines)
 
 
+def _wall_bounds(box, o, mass, rtol):
+    """Per particle: rtol |F_wall| + 1e-9 k_n r^1.5 (k_n with R* = r), where
+    F_wall is the oracle's total force less its pair contacts' forces and
+    gravity (zero for a particle touching no wall, up to round-off)."""
+    info = o["info"]
+    Fp = np.zeros((box.n, 3))
+    if len(o["lo"]):
+        np.add.at(Fp, o["lo"], info["F"])
+        np.add.at(Fp, o["hi"], -info["F"])
+    Fw = o["F"] - Fp - mass[:, None] * np.asarray(box.g, float)[None, :]
+    kn_c = O.kn(o["params"], 1.0, 1.0) / math.sqrt(0.5)
+    return rtol * np.linalg.norm(Fw, axis=1) + 1e-9 * kn_c * box.r ** 2
+
+
+def _explain_particles(box, g, o, idx, eP, bP):
+    """Human-readable detail of selected particles (for failure messages)."""
+    lines = []
+    for i in idx:
+        i = int(i)
+        nc = int(np.sum(o["lo"] == i) + np.sum(o["hi"] == i))
+        lines.append(f"  particle {i}: err {eP[i]:.4g} bound {bP[i]:.4g} contacts {nc} "
+                     f"F_ora={o['F'][i]} F_gpu={g['state']['F'][i]} r={box.r[i]:.4g} "
+                     f"x={o['x0'][i]}")
+    return "\n".join(lines)
+
+
 def check_one_step(box, g, o, precision, allow_dont_care=True, check_order=True):
     """Compare one step; returns a metrics dict, raises AssertionError.
     check_order=False skips the sort order and cells (a step of the
@@ -214,14 +240,19 @@ def check_one_step(box, g, o, precision, allow_dont_care=True, check_order=True)
     mass = box.density * 4.0 / 3.0 * math.pi * box.r ** 3
     gmag = float(np.linalg.norm(box.g))
     bP += 1e-6 * mass * gmag + 1e-300
-    if box.floor_wall or len(getattr(box, "walls", ())):
-        # wall contacts: k_n r^1.5 dn^1.5 scale, bounded via the force itself
-        bP += 1e-5 * np.linalg.norm(o["F"], axis=1) + 1e-5 * mass * gmag
+    walled = bool(box.floor_wall or len(getattr(box, "walls", ())))
+    if walled:
+        # the wall contacts of a particle, bounded like a particle contact:
+        # rtol times their force plus the floor 1e-9 k_n R*^1.5 (R* = r);
+        # their force is the oracle's total less its pair contacts and m g
+        bW = _wall_bounds(box, o, mass, rtol)
+        bP += bW + 1e-5 * np.linalg.norm(o["F"], axis=1) + 1e-5 * mass * gmag
     if dont.any():
         np.add.at(bP, o["lo"][dont], np.inf)
         np.add.at(bP, o["hi"][dont], np.inf)
     eP = np.linalg.norm(g["state"]["F"] - o["F"], axis=1)
-    assert np.all(eP <= bP), f"{int((eP > bP).sum())} particle forces outside tolerance"
+    assert np.all(eP <= bP), (f"{int((eP > bP).sum())} particle forces outside tolerance\n"
+                              + _explain_particles(box, g, o, np.where(eP > bP)[0][:4], eP, bP))
     if nc:
         # force-relative per particle: rtol times the sum of its contacts'
         # |F| plus their floors, for particles whose contacts are all
@@ -231,8 +262,8 @@ def check_one_step(box, g, o, precision, allow_dont_care=True, check_order=True)
         np.add.at(sF, o["lo"], rtol * normF + floor)
         np.add.at(sF, o["hi"], rtol * normF + floor)
         sF += 1e-6 * mass * gmag + 1e-300
-        if box.floor_wall or len(getattr(box, "walls", ())):
-            sF += 1e-5 * np.linalg.norm(o["F"], axis=1) + 1e-5 * mass * gmag
+        if walled:
+            sF += bW + 1e-5 * np.linalg.norm(o["F"], axis=1) + 1e-5 * mass * gmag
         cold = np.zeros(n, bool)
         notwell = ok & (kappa > KAPPA_MAX)
         cold[o["lo"][notwell]] = True
