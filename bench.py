@@ -39,6 +39,7 @@ METRIC = "particle-steps/s"  # the unit
 METRIC_NAME = ("particle-steps/s @1M: FP32 vs FP64 GPU at force rel err\u22641e-5; "
                "batched vs 1-by-1")
 L2_BYTES = 126.5 * 2 ** 20
+W2_R_MAX = 8e-6  # the largest radius of W2's law (clipped at 8 um)
 
 
 def _args():
@@ -541,7 +542,7 @@ def _side_legs(args, D, torch, box, ncell, stream, skin):
     leg("collide_fused_vs_compact", lambda: _fused_leg(args, D, torch, stream, box))
     leg("size_binned_search", lambda: _size_binned_leg(args, D, torch, stream, box, ncell))
     leg("fig4_kernel_times_131k", lambda: _fig4_leg(args, D, torch, stream))
-    skin_frac = skin / box.r_max  # the W2 skin as a fraction of the largest radius
+    skin_frac = skin / W2_R_MAX  # the W2 skin as a fraction of the largest radius
     leg("layout_tuner", lambda: _tuner_leg(args, D, torch, stream, box, skin_frac))
     if not args.no_batched:
         leg("batched", lambda: _batched_leg(args, D, torch, stream, skin_frac))
@@ -895,7 +896,7 @@ def _tuner_leg(args, D, torch, stream, box, skin_frac):
             ctx = D.Context(boxes, precision="mixed", ncell=ncells, skins=skins)
         try:
             _reset(ctx, boxes)
-            res["choice"] = ctx.autotune_layout(steps=16)
+            res["choice"] = ctx.autotune_layout(steps=max(steps, 32))
             lay = [ctx.layout(k) for k in range(len(boxes))]
         finally:
             ctx.close()
