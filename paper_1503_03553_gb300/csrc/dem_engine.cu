@@ -767,6 +767,8 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   return DEM_OK;
 }
 
+static dem_status prepare_graphs(dem_ctx* ctx);
+
 dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   dem_ctx* ctx = nullptr;
   if (!out) return fail(nullptr, DEM_ERR_ARG, "out is null");
@@ -849,7 +851,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   const dem_status st = setup_device(ctx, &msg);
   if (st) return bail(st, msg);
   *out = ctx;
-  return DEM_OK;
+  return prepare_graphs(ctx);
 }
 
 dem_status dem_destroy(dem_ctx* ctx) {
@@ -1060,6 +1062,34 @@ static dem_status build_graph(dem_ctx* ctx, int p, int nsteps, bool store_last,
   return DEM_OK;
 }
 
+// The graphs dem_step launches, instantiated ahead of the first step (at
+// creation and after a tuner changed the launch configuration), so that a
+// step never pays for a capture: G steps from the current parity (both
+// parities for the per-particle forms) and, for the contact-list pipeline,
+// the one-step graphs of the steps left over.
+static dem_status prepare_graphs(dem_ctx* ctx) {
+  if (ctx->graph_steps <= 0) return DEM_OK;
+  if (ctx->fused) {
+    for (int p = 0; p < 2; ++p)
+      if (!ctx->gexec[p]) {
+        dem_status st = build_graph(ctx, p, ctx->graph_steps, true, &ctx->gexec[p]);
+        if (st) return st;
+      }
+    return DEM_OK;
+  }
+  const int p = ctx->parity;
+  if (!ctx->gexec[p]) {
+    dem_status st = build_graph(ctx, p, ctx->graph_steps, true, &ctx->gexec[p]);
+    if (st) return st;
+  }
+  for (int k = 2; k < 4; ++k)
+    if (!ctx->gexec[k]) {
+      dem_status st = build_graph(ctx, p, 1, k == 3, &ctx->gexec[k]);
+      if (st) return st;
+    }
+  return DEM_OK;
+}
+
 dem_status dem_step(dem_ctx* ctx, int64_t nsteps) {
   if (!ctx) return fail(ctx, DEM_ERR_ARG, "null context");
   if (nsteps < 0) return fail(ctx, DEM_ERR_ARG, "nsteps < 0");
@@ -1188,6 +1218,8 @@ dem_status dem_autotune(dem_ctx* ctx, int64_t steps, double* best_ms,
   if (best_ms) *best_ms = best;
   if (block) *block = bb;
   if (graph_steps) *graph_steps = bg;
+  dem_status st = prepare_graphs(ctx);
+  if (st) return st;
   return read_status(ctx);
 }
 
@@ -1475,6 +1507,8 @@ extern "C" dem_status dem_autotune_layout(dem_ctx* ctx, int64_t steps, dem_tunin
     out->trials = trials;
     out->pad = 0;
   }
+  st = prepare_graphs(ctx);
+  if (st) return st;
   return read_status(ctx);
 }
 
