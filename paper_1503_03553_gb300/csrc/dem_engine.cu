@@ -284,10 +284,19 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
   if (tm) cudaEventRecord(ev[3], s);
   const BoxDev B0 = box0_param(ctx);
   const bool one = ctx->hbox.size() == 1;
+  // the pair kernel runs as one wave: as many blocks as the GPU holds at
+  // once (its warps stride over the candidate tiles), which measured faster
+  // than more, shorter-lived blocks
+  int per_sm = 0;
   if (one)
-    k_pairs<M, true><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0], B0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<M, true>, 32 * kPairWarps, 0);
   else
-    k_pairs<M, false><<<ctx->nsm * 8, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0], B0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<M, false>, 32 * kPairWarps, 0);
+  const int pgrid = ctx->nsm * std::max(1, per_sm);
+  if (one)
+    k_pairs<M, true><<<pgrid, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0], B0);
+  else
+    k_pairs<M, false><<<pgrid, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0], B0);
   if (tm) cudaEventRecord(ev[4], s);
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
   if (one)

@@ -150,7 +150,7 @@ struct Dev {
   int* next;     // the inverse: new slot of each slot before the reorder
                  // (contact-list pipeline; null otherwise)
   int2* inrow;   // N x K: the contacts in which a slot was found by its
-                 // partner (any order): (list entry, partner slot << 1 |
+                 // partner (any order): (list entry, partner id << 1 |
                  // 1 if this slot is the lower-id member)
   void* Fc;      // 2 V4 per contact (one record: 32 bytes in FP32, 64 in
                  // FP64): the force on the lower-id particle, then n x F
@@ -1047,7 +1047,7 @@ __device__ __forceinline__ void write_list(const Dev& d, const PState& b, const 
   cn.oc[i] = n;
   const int idi = b.id[i];
   const int K = d.K;
-  const int* rowp = d.row + (size_t)i * K;
+  int* rowp = d.row + (size_t)i * K;
   for (int k = 0; k < n; k += 4) {
     int jj[4], pos[4];
 #pragma unroll
@@ -1062,7 +1062,8 @@ __device__ __forceinline__ void write_list(const Dev& d, const PState& b, const 
       const int idj = b.id[j];
       cn.pair[c] = idi < idj ? make_int2(i, j) : make_int2(j, i);
       if (cn.hid) cn.hid[c] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
-      if (pos[u] < K) d.inrow[(size_t)j * K + pos[u]] = make_int2(c, (i << 1) | (idj < idi ? 1 : 0));
+      if (pos[u] < K) d.inrow[(size_t)j * K + pos[u]] = make_int2(c, (idi << 1) | (idj < idi ? 1 : 0));
+      rowp[k + u] = idj;  // the row now holds the partners' ids (the keys of k_rows)
     }
   }
 }
@@ -1324,7 +1325,8 @@ k_candidates_large(Dev d, PState b, VList cn) {
         const int idj = b.id[j2];
         cn.pair[c2] = idi < idj ? make_int2(i, j2) : make_int2(j2, i);
         if (cn.hid) cn.hid[c2] = idi < idj ? make_int2(idi, idj) : make_int2(idj, idi);
-        if (pos < K) d.inrow[(size_t)j2 * K + pos] = make_int2(c2, (i << 1) | (idj < idi ? 1 : 0));
+        if (pos < K) d.inrow[(size_t)j2 * K + pos] = make_int2(c2, (idi << 1) | (idj < idi ? 1 : 0));
+        rowp[k] = idj;  // the row now holds the partners' ids (the keys of k_rows)
       }
     }
   }
@@ -1807,8 +1809,9 @@ k_pairs(Dev d, PState b, VList vl, const __grid_constant__ BoxDev B0) {
 // candidate list vn in the new slot order of b): each slot's row of all its
 // candidate pairs, ordered by partner id (the order of the force sum, which
 // then does not depend on slots, re-sorts or timing).  The row's entries go
-// to d.frow and the partner ids beside them to d.row (free after the search),
-// where k_carry looks pairs up.  A row of up to 16 entries is loaded into
+// to d.frow and the partner ids beside them to d.row (where the search left
+// the ids of the slot's own partners), where k_carry looks pairs up.  Every
+// input is the slot's own: no partner's record is read.  A row of up to 16 entries is loaded into
 // registers and ordered there by a bitonic sorting network (Batcher, 1968):
 // 8 wide when every row of the warp fits, else 16 wide, unused places
 // holding the largest key; a longer row is ordered by insertion in place.
@@ -1853,6 +1856,10 @@ k_rows(Dev d, PState b, VList vn) {
   const int inc = min(d.icnt[i], K);
   if (own + inc > K) flag(d.status, kStRowOverflow);
   const int n = min(own + inc, K);
+  const int idi = b.id[i];
+  // the search left the partners' ids of the slot's own pairs in its row
+  // (the entry of the k-th is hs + k) and the incoming pairs as (entry,
+  // partner id << 1 | lower-id bit)
   int* kr = d.row + (size_t)i * K;
   int* vr = d.frow + (size_t)i * K;
   const int2* in = d.inrow + (size_t)i * K;
@@ -1861,23 +1868,18 @@ k_rows(Dev d, PState b, VList vn) {
     int key[16], val[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) {
-      int partner = -1, v = 0;
+      int id = INT_MAX, v = 0;
       if (k < own) {
-        const int c = hs + k;
-        const int2 pr = vn.pair[c];
-        const bool low = pr.x == i;
-        partner = low ? pr.y : pr.x;
-        v = (c << 1) | (low ? 1 : 0);
+        id = kr[k];
+        v = ((hs + k) << 1) | (idi < id ? 1 : 0);
       } else if (k < n) {
         const int2 e = in[k - own];
-        partner = e.y >> 1;
+        id = e.y >> 1;
         v = (e.x << 1) | (e.y & 1);
       }
-      key[k] = partner;
+      key[k] = id;
       val[k] = v;
     }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) key[k] = key[k] >= 0 ? b.id[key[k]] : INT_MAX;
     if (__all_sync(__activemask(), n <= 8)) bitonic_sort<8>(key, val);
     else bitonic_sort<16>(key, val);
 #pragma unroll
@@ -1888,8 +1890,9 @@ k_rows(Dev d, PState b, VList vn) {
       }
     }
   } else {
-    int m = 0;
-    auto insert = [&](int key, int val) {
+    // the own entries in place first, then the incoming ones inserted
+    for (int k = 0; k < own; ++k) vr[k] = ((hs + k) << 1) | (idi < kr[k] ? 1 : 0);
+    auto insert = [&](int m, int key, int val) {
       int pos = m;
       while (pos > 0 && kr[pos - 1] > key) {
         kr[pos] = kr[pos - 1];
@@ -1898,18 +1901,11 @@ k_rows(Dev d, PState b, VList vn) {
       }
       kr[pos] = key;
       vr[pos] = val;
-      ++m;
     };
-    for (int k = 0; k < n; ++k) {
-      if (k < own) {
-        const int c = hs + k;
-        const int2 pr = vn.pair[c];
-        const bool low = pr.x == i;
-        insert(b.id[low ? pr.y : pr.x], (c << 1) | (low ? 1 : 0));
-      } else {
-        const int2 e = in[k - own];
-        insert(b.id[e.y >> 1], (e.x << 1) | (e.y & 1));
-      }
+    for (int m = 1; m < own; ++m) insert(m, kr[m], vr[m]);
+    for (int m = own; m < n; ++m) {
+      const int2 e = in[m - own];
+      insert(m, e.y >> 1, (e.x << 1) | (e.y & 1));
     }
   }
   d.fcnt[i] = n;
