@@ -532,8 +532,7 @@ def _side_legs(args, D, torch, box, ncell, stream, skin):
         except Exception as e:  # recorded, not hidden: the line says which leg failed
             out[name] = {"error": f"{type(e).__name__}: {str(e)[:300]}"}
 
-    leg("fp64_gpu", lambda: _throughput(D, torch, stream, [box], "fp64", [ncell], args.steps,
-                                        skins=[skin]))
+    leg("fp64_gpu", lambda: _fp64_leg(args, D, torch, stream, box, ncell, skin))
     leg("fp32_gpu", lambda: _throughput(D, torch, stream, [box], "fp32", [ncell], args.steps,
                                         skins=[skin]))
     leg("mixed_gpu_search_every_step", lambda: _throughput(D, torch, stream, [box], "mixed",
@@ -553,6 +552,46 @@ def _side_legs(args, D, torch, box, ncell, stream, skin):
     if not args.no_sweep:
         leg("n_sweep", lambda: _sweep_leg(args, D, torch, stream, skin))
     return out
+
+
+# FP64 operations (an FMA counts two) per pair in contact of the FP64 pair
+# kernel, the contact rule on every candidate included: ncu thread-level
+# DFMA/DADD/DMUL counts of one launch on the 512,000-particle W2 box
+# (profiles/fp64_pairs_w2_512k.md)
+FP64_FLOPS_PER_CONTACT = 320.0
+
+
+def _fp64_leg(args, D, torch, stream, box, ncell, skin):
+    """The plain FP64 form on the same workload and skin: throughput, and the
+    roofline of its dominant kernel, the pair kernel, against the FP64 FMA
+    rate measured on this GPU in this run (the form is bound by the FP64
+    pipe, not by HBM)."""
+    from paper_1503_03553_gb300.synth import prepared
+    b = prepared(box, "fp64")
+    res = _throughput(D, torch, stream, [b], "fp64", [ncell], args.steps, skins=[skin])
+    ph = _phase_ms(D, torch, stream, [b], "fp64", [ncell], args.steps, skins=[skin])
+    with torch.cuda.stream(stream):
+        ctx = D.Context([b], precision="fp64", ncell=[ncell], skins=[skin])
+    try:
+        _reset(ctx, [b])
+        contacts = 0.0
+        for _ in range(args.steps):
+            ctx.step(1)
+            contacts += ctx.stats(0)[5]
+    finally:
+        ctx.close()
+    peaks = D.dem_measure_fma_rates(stream)
+    per_launch = FP64_FLOPS_PER_CONTACT * contacts / args.steps
+    achieved = per_launch / (ph["pairs"] * 1e-3) / 1e12
+    res["roofline"] = {"bound": "alu", "kernel": "k_pairs (FP64)", "achieved": achieved,
+                       "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+                       "frac": achieved / peaks["fp64_tflops"],
+                       "peak_source": "measured in this run (dem_measure_fma_rates: FP64 FMA)",
+                       "flops_per_contact": FP64_FLOPS_PER_CONTACT,
+                       "flops_source": "profiles/fp64_pairs_w2_512k.md (ncu DFMA/DADD/DMUL counts)",
+                       "kernel_ms": ph["pairs"], "phase_ms": ph}
+    res["alu_peaks_tflops"] = peaks
+    return res
 
 
 def _error_leg(out, box, ncell):
@@ -602,18 +641,25 @@ def _w3_leg(args, D, torch, stream):
     from paper_1503_03553_gb300 import synth
     from paper_1503_03553_gb300.synth import grid_for, prepared
     box = prepared(synth.w3_bidisperse_floor(n=8_000_000, seed=3), "mixed")
-    nc = grid_for(box)
-    res = {"particles": box.n, "ncell": nc}
+    skin = W5_SKIN_OVER_RMAX * box.r_max  # the W2 line's skin fraction
+    nc = grid_for(box)  # the per-particle forms and the search every step
+    ncs = grid_for(box, skin=skin)
+    res = {"particles": box.n, "ncell": nc, "ncell_with_skin": ncs, "skin_m": skin}
     k = 500  # the workload's steps, 1..500 from the initial state, every form
     res["steps"] = k
-    res["mixed_compact"] = _throughput(D, torch, stream, [box], "mixed", [nc], k)
-    res["mixed_compact"]["phase_ms"] = _phase_ms(D, torch, stream, [box], "mixed", [nc], k)
+    res["mixed_compact"] = _throughput(D, torch, stream, [box], "mixed", [ncs], k, skins=[skin])
+    res["mixed_compact"]["phase_ms"] = _phase_ms(D, torch, stream, [box], "mixed", [ncs], k,
+                                                 skins=[skin])
+    res["mixed_compact_search_every_step"] = _throughput(D, torch, stream, [box], "mixed",
+                                                         [nc], k)
     res["mixed_fused"] = _throughput(D, torch, stream, [box], "mixed", [nc], k,
                                      collide=D.DEM_COLLIDE_FUSED)
     res["mixed_twoloop"] = _throughput(D, torch, stream, [box], "mixed", [nc], k,
                                        collide=D.DEM_COLLIDE_TWOLOOP)
-    res["fp32_compact"] = _throughput(D, torch, stream, [box], "fp32", [nc], k)
-    res["fp64_compact"] = _throughput(D, torch, stream, [box], "fp64", [nc], k)
+    res["fp32_compact"] = _throughput(D, torch, stream, [prepared(box, "fp32")], "fp32", [ncs],
+                                      k, skins=[skin])
+    res["fp64_compact"] = _throughput(D, torch, stream, [prepared(box, "fp64")], "fp64", [ncs],
+                                      k, skins=[skin])
     return res
 
 
@@ -634,6 +680,9 @@ def _w5_oracle(path):
     out = O.step(p, s)
     out["params"] = p
     return force_errors(b2, g, out, prec, detail=5)
+
+
+W5_SKIN_OVER_RMAX = 0.025  # the candidate-list skin of the W5 leg, as W2's
 
 
 def _w5_leg(args, D, torch, stream):
@@ -657,9 +706,10 @@ def _w5_leg(args, D, torch, stream):
     with mp.get_context("spawn").Pool(workers) as pool:
         for prec in args.w5_forms.split(","):
             b = prepared(raw, prec)
-            nc = grid_for(b)
+            skin = W5_SKIN_OVER_RMAX * b.r_max
+            nc = grid_for(b, skin=skin)
             with torch.cuda.stream(stream):
-                ctx = D.Context([b], precision=prec, ncell=[nc])
+                ctx = D.Context([b], precision=prec, ncell=[nc], skins=[skin])
             try:
                 ctx.set_particles(0, b.x, b.v, b.w, b.r)
                 gpu_s = 0.0
@@ -695,6 +745,11 @@ def _w5_leg(args, D, torch, stream):
             x.get("max_err_over_scale_cared", float("inf")) for x in sn)
         res[prec]["min_frac_within_1e-5_cared"] = min(x.get("frac_within_1e-5_cared", 0.0) for x in sn)
         res[prec]["contact_sets_equal"] = all(x["contact_sets_equal"] for x in sn)
+        # the force-relative criterion, 1e-5 |F_ora| + 1e-9 k_n R*^1.5
+        res[prec]["max_F_rel_bound_exceeded"] = max(x.get("F_rel_bound_exceeded", 0) for x in sn)
+        res[prec]["worst_F_rel_bound_max"] = max(x.get("F_rel_bound_max", 0.0) for x in sn)
+        res[prec]["max_F_rel_bound_exceeded_kappa_le_10"] = max(
+            x.get("F_rel_bound_exceeded_kappa_le_10", 0) for x in sn)
     return res
 
 

@@ -30,9 +30,11 @@ def test_failing_leg_is_recorded(monkeypatch):
     monkeypatch.setattr(bench, "_fig4_leg", ok("fig4"))
     monkeypatch.setattr(bench, "_batched_leg", ok("batched"))
     monkeypatch.setattr(bench, "_tuner_leg", ok("tuner"))
+    monkeypatch.setattr(bench, "_fp64_leg", ok("fp64"))
     args = types.SimpleNamespace(steps=10, no_batched=False, w3=False, w5=False, no_sweep=True)
     out = bench._side_legs(args, None, None, None, None, None, 0.0)
     assert out["collide_fused_vs_compact"]["error"].startswith("RuntimeError: no such workload")
-    assert out["fp64_gpu"] == {"leg": "throughput"} and out["batched"] == {"leg": "batched"}
+    assert out["fp64_gpu"] == {"leg": "fp64"} and out["batched"] == {"leg": "batched"}
+    assert out["fp32_gpu"] == {"leg": "throughput"}
     assert "fig4" in calls and "size_binned" in calls  # the legs after the failure still ran
     assert out["layout_tuner"] == {"leg": "tuner"}
