@@ -223,7 +223,10 @@ dem_status dem_set_particles(dem_ctx* ctx, int32_t box, int64_t n,
  * may be NULL to keep it) of the particles already in a box, keeping radii
  * and the contact history.  Host arrays are read by the time the call
  * returns.  A non-finite value is reported by the next dem_step
- * (DEM_ERR_NONFINITE). */
+ * (DEM_ERR_NONFINITE).  With DEM_COLLIDE_COMPACT new positions are taken
+ * like those of a step: the next step re-sorts only if a particle moved
+ * beyond its box's skin limit since the last re-sort (the results do not
+ * depend on when re-sorts happen). */
 dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
                          const double* v, const double* omega, int32_t where);
 

@@ -983,15 +983,21 @@ dem_status dem_set_state(dem_ctx* ctx, int32_t box, const double* x,
     const double* a0 = k == 0 ? dk : nullptr;
     const double* a1 = k == 1 ? dk : nullptr;
     const double* a2 = k == 2 ? dk : nullptr;
+    // the contact-list pipeline tracks new positions like a step's (cells,
+    // records, skin test); the per-particle forms sort every step anyway
+    Dev dd = ctx->dev;
+    dd.collect = ctx->collect;
+    const int track = ctx->fused ? 0 : 1;
     switch (ctx->mode) {
-      case kFP64: k_set_state<kFP64><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, a0, a1, a2); break;
-      case kMIXED: k_set_state<kMIXED><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, a0, a1, a2); break;
-      default: k_set_state<kFP32><<<nb, 256, 0, s>>>(ctx->dev, ctx->ps[p], box, n, a0, a1, a2); break;
+      case kFP64: k_set_state<kFP64><<<nb, 256, 0, s>>>(dd, ctx->ps[p], box, n, a0, a1, a2, track); break;
+      case kMIXED: k_set_state<kMIXED><<<nb, 256, 0, s>>>(dd, ctx->ps[p], box, n, a0, a1, a2, track); break;
+      default: k_set_state<kFP32><<<nb, 256, 0, s>>>(dd, ctx->ps[p], box, n, a0, a1, a2, track); break;
     }
     CK(cudaGetLastError());
   }
-  // new positions may have changed cells: the next step re-sorts from scratch
-  if (x) {
+  // the per-particle forms: new positions may have changed cells, the next
+  // sort starts from every cell
+  if (x && ctx->fused) {
     CK(cudaMemsetAsync(ctx->collect, 1, std::max(1, ctx->M_rank), s));
     CK(cudaMemsetAsync(ctx->dev.vctl + kCtlRequest, 1, sizeof(unsigned), s));
   }

@@ -347,12 +347,81 @@ __global__ void k_set_particles(Dev d, PState s, int box, int n,
   }
 }
 
+// The contact rule's record of a particle at position p in cell c: its
+// offset from the cell's origin (DEM_MIXED, rounded as the sort rounds it) or
+// its position, and its radius r.
+template <int M>
+__device__ __forceinline__ typename Tr<M>::PR pos_record(const BoxDev& B,
+                                                         const typename Tr<M>::P* p,
+                                                         const int* c, typename Tr<M>::R r) {
+  typename Tr<M>::PR pr;
+  if (M == kMIXED) {
+    pr.x = __fmul_rn(i64_to_f32_rn((long long)p[0] - (long long)c[0] * B.Hq[0]), kQ);
+    pr.y = __fmul_rn(i64_to_f32_rn((long long)p[1] - (long long)c[1] * B.Hq[1]), kQ);
+    pr.z = __fmul_rn(i64_to_f32_rn((long long)p[2] - (long long)c[2] * B.Hq[2]), kQ);
+  } else {
+    pr.x = p[0];
+    pr.y = p[1];
+    pr.z = p[2];
+  }
+  pr.w = r;
+  return pr;
+}
+
+// Skin test: whether the particle of slot i, now at p, moved farther than
+// the box's limit since the last re-sort (the squared displacement rounded
+// up); false where the box keeps no skin (it re-sorts every step).
+template <int M>
+__device__ __forceinline__ bool skin_exceeded(const Dev& d, const BoxDev& B,
+                                              const typename Tr<M>::P* p, int i) {
+  using P = typename Tr<M>::P;
+  if (!d.xb || B.disp2_lim < 0.0f) return false;
+  float d2;
+  if (M == kMIXED) {
+    const long long* xb3[3] = {(const long long*)d.xb, (const long long*)d.yb,
+                               (const long long*)d.zb};
+    float acc = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      long long D = (long long)p[a] - xb3[a][i];
+      if (B.periodic[a]) {
+        const long long L = B.Lq[a], h = L >> 1;
+        if (D > h) D -= L;
+        else if (D < -h) D += L;
+      }
+      const float f = __fmul_rn(i64_to_f32_rn(D), kQ);
+      acc = __fmaf_ru(f, f, acc);
+    }
+    d2 = __fmul_ru(acc, 1.000001f);
+  } else {
+    const P* xb3[3] = {(const P*)d.xb, (const P*)d.yb, (const P*)d.zb};
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double D = (double)p[a] - (double)xb3[a][i];
+      if (B.periodic[a]) {
+        if (D > B.half_L[a]) D -= B.L[a];
+        else if (D < -B.half_L[a]) D += B.L[a];
+      }
+      acc += D * D;
+    }
+    d2 = __fmul_ru(__double2float_ru(acc), 1.000001f);
+  }
+  return d2 > B.disp2_lim;
+}
+
 // Overwrite x / v / w of live particles (id order), keep everything else.
+// New positions (track = 1, the contact-list pipeline) are handled as the
+// integrator handles a step's: the contact rule's record and the current
+// cell follow them, a particle that changed cell updates the counts and
+// flags both cells for the next sort, and one that moved beyond the skin
+// limit asks for a re-sort; otherwise (the per-particle forms, which sort
+// every step) the next sort starts from every cell.
 template <int M>
 __global__ void k_set_state(Dev d, PState s, int box, int n,
                             const double* __restrict__ x,
                             const double* __restrict__ v,
-                            const double* __restrict__ w) {
+                            const double* __restrict__ w, int track) {
   using T = Tr<M>;
   using P = typename T::P;
   using R = typename T::R;
@@ -386,10 +455,20 @@ __global__ void k_set_state(Dev d, PState s, int box, int n,
     if (g != old) {
       atomicSub(&d.ccount[old], 1);
       atomicAdd(&d.ccount[g], 1);
+      if (track) {
+        d.collect[old] = 1;
+        d.collect[g] = 1;
+      }
     }
     s.cellg[slot] = g;
     s.cellc[slot] = pack_cell(c[0], c[1], c[2]);
-    s.cellx[slot] = pack_cell(c[0], c[1], c[2]);
+    if (track) {
+      using PR = typename T::PR;
+      st4((PR*)s.posr + slot, pos_record<M>(B, p, c, (R)((const V4*)s.omg)[slot].w));
+      if (skin_exceeded<M>(d, B, p, slot)) d.vctl[kCtlRequest] = 1u;
+    } else {
+      s.cellx[slot] = pack_cell(c[0], c[1], c[2]);
+    }
   }
   if (v) {
     V4 q = ((V4*)s.vel)[slot];
@@ -2497,59 +2576,9 @@ k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, i
   ((P*)b.pz)[i] = p[2];
   const int cnew = pack_cell(c[0], c[1], c[2]);
   b.cellc[i] = cnew;
-  // the contact rule's record for the next step: offset from the new cell's
-  // origin (DEM_MIXED, rounded as the sort rounds it) or the position, and r
-  {
-    using PR = typename T::PR;
-    PR pr;
-    if (M == kMIXED) {
-      pr.x = __fmul_rn(i64_to_f32_rn((long long)p[0] - (long long)c[0] * B.Hq[0]), kQ);
-      pr.y = __fmul_rn(i64_to_f32_rn((long long)p[1] - (long long)c[1] * B.Hq[1]), kQ);
-      pr.z = __fmul_rn(i64_to_f32_rn((long long)p[2] - (long long)c[2] * B.Hq[2]), kQ);
-    } else {
-      pr.x = p[0];
-      pr.y = p[1];
-      pr.z = p[2];
-    }
-    pr.w = wr.w;
-    st4((PR*)b.posr + i, pr);
-  }
-  // skin test: a particle displaced more than the box's limit since the last
-  // re-sort asks for the next one (the squared displacement rounded up)
-  if (d.xb && B.disp2_lim >= 0.0f) {
-    float d2;
-    if (M == kMIXED) {
-      const long long* xb3[3] = {(const long long*)d.xb, (const long long*)d.yb,
-                                 (const long long*)d.zb};
-      float acc = 0.0f;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        long long D = (long long)p[a] - xb3[a][i];
-        if (B.periodic[a]) {
-          const long long L = B.Lq[a], h = L >> 1;
-          if (D > h) D -= L;
-          else if (D < -h) D += L;
-        }
-        const float f = __fmul_rn(i64_to_f32_rn(D), kQ);
-        acc = __fmaf_ru(f, f, acc);
-      }
-      d2 = __fmul_ru(acc, 1.000001f);
-    } else {
-      const P* xb3[3] = {(const P*)d.xb, (const P*)d.yb, (const P*)d.zb};
-      double acc = 0.0;
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        double D = (double)p[a] - (double)xb3[a][i];
-        if (B.periodic[a]) {
-          if (D > B.half_L[a]) D -= B.L[a];
-          else if (D < -B.half_L[a]) D += B.L[a];
-        }
-        acc += D * D;
-      }
-      d2 = __fmul_ru(__double2float_ru(acc), 1.000001f);
-    }
-    if (d2 > B.disp2_lim) d.vctl[kCtlRequest] = 1u;
-  }
+  // the contact rule's record for the next step, then the skin test
+  st4((typename T::PR*)b.posr + i, pos_record<M>(B, p, c, wr.w));
+  if (skin_exceeded<M>(d, B, p, i)) d.vctl[kCtlRequest] = 1u;
   if (cnew != cc) {
     // moved to another cell: counts and the changed-cell flags of both
     const int g0 = b.cellg[i];

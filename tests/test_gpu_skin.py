@@ -191,3 +191,47 @@ def test_skin_rejected_configurations(dense3k):
     with pytest.raises(D.DemError) as e:
         D.Context([b], precision="mixed", ncell=[grid_for(b)], skins=[2e-6])
     assert e.value.status == D.DEM_ERR_ARG
+
+
+def _run_with_set_state(b, skin, ncell, shift):
+    """Ten steps, then the positions read back, moved by `shift` metres
+    along x and set again (dem_set_state), then twenty steps."""
+    import paper_1503_03553_gb300 as D
+    ctx = D.Context([b], precision="mixed", ncell=[ncell], skins=[skin])
+    try:
+        ctx.set_particles(0, b.x, b.v, b.w, b.r)
+        ctx.step(10)
+        st = ctx.get_state(0)
+        x = st["x"].copy()
+        x[:, 0] += shift
+        before = ctx.resort_stats()["resorts"]
+        ctx.set_state(0, x, st["v"], st["w"])
+        ctx.step(1)
+        resorted = ctx.resort_stats()["resorts"] > before
+        ctx.step(19)
+        out = dict(state=ctx.get_state(0))
+        out["lo"], out["hi"], out["dt"] = ctx.contacts(0)
+        out["flo"], out["fhi"], out["Fc"], out["nFc"] = ctx.contact_forces(0)
+    finally:
+        ctx.close()
+    return out, resorted
+
+
+@pytest.mark.parametrize("shift_over_skin", [0.0, 0.1, 3.0])
+def test_set_state_positions_tracked_like_a_step(dense3k, shift_over_skin):
+    """New positions from the host keep the candidate list when every
+    particle stayed within the skin limit and re-sort otherwise; either way
+    the run is bit for bit the run that re-sorts every step."""
+    b = prepared(dense3k, "mixed")
+    ncell = grid_for(b, skin=SKIN_LARGE)
+    shift = shift_over_skin * SKIN_LARGE
+    ref, _ = _run_with_set_state(b, 0.0, ncell, shift)
+    g, resorted = _run_with_set_state(b, SKIN_LARGE, ncell, shift)
+    if shift_over_skin >= 1.0:
+        assert resorted
+    elif shift_over_skin == 0.0:
+        assert not resorted
+    for k in ("x", "v", "w", "F", "T"):
+        assert np.array_equal(g["state"][k], ref["state"][k]), k
+    assert np.array_equal(g["lo"], ref["lo"]) and np.array_equal(g["dt"], ref["dt"])
+    assert np.array_equal(g["Fc"], ref["Fc"])
