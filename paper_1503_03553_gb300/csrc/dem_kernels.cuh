@@ -368,22 +368,18 @@ __device__ __forceinline__ typename Tr<M>::PR pos_record(const BoxDev& B,
   return pr;
 }
 
-// Skin test: whether the particle of slot i, now at p, moved farther than
-// the box's limit since the last re-sort (the squared displacement rounded
-// up); false where the box keeps no skin (it re-sorts every step).
+// Skin test: whether a particle now at p moved farther than the box's limit
+// since the last re-sort, where it was at q (the squared displacement
+// rounded up); the caller checks that the box keeps a skin.
 template <int M>
-__device__ __forceinline__ bool skin_exceeded(const Dev& d, const BoxDev& B,
-                                              const typename Tr<M>::P* p, int i) {
-  using P = typename Tr<M>::P;
-  if (!d.xb || B.disp2_lim < 0.0f) return false;
+__device__ __forceinline__ bool skin_exceeded(const BoxDev& B, const typename Tr<M>::P* p,
+                                              const typename Tr<M>::P* q) {
   float d2;
   if (M == kMIXED) {
-    const long long* xb3[3] = {(const long long*)d.xb, (const long long*)d.yb,
-                               (const long long*)d.zb};
     float acc = 0.0f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      long long D = (long long)p[a] - xb3[a][i];
+      long long D = (long long)p[a] - (long long)q[a];
       if (B.periodic[a]) {
         const long long L = B.Lq[a], h = L >> 1;
         if (D > h) D -= L;
@@ -394,11 +390,10 @@ __device__ __forceinline__ bool skin_exceeded(const Dev& d, const BoxDev& B,
     }
     d2 = __fmul_ru(acc, 1.000001f);
   } else {
-    const P* xb3[3] = {(const P*)d.xb, (const P*)d.yb, (const P*)d.zb};
     double acc = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double D = (double)p[a] - (double)xb3[a][i];
+      double D = (double)p[a] - (double)q[a];
       if (B.periodic[a]) {
         if (D > B.half_L[a]) D -= B.L[a];
         else if (D < -B.half_L[a]) D += B.L[a];
@@ -408,6 +403,11 @@ __device__ __forceinline__ bool skin_exceeded(const Dev& d, const BoxDev& B,
     d2 = __fmul_ru(__double2float_ru(acc), 1.000001f);
   }
   return d2 > B.disp2_lim;
+}
+
+// whether slot i's box runs the skin test (a candidate list with a skin)
+__device__ __forceinline__ bool has_skin_test(const Dev& d, const BoxDev& B) {
+  return d.xb && B.disp2_lim >= 0.0f;
 }
 
 // Overwrite x / v / w of live particles (id order), keep everything else.
@@ -465,7 +465,10 @@ __global__ void k_set_state(Dev d, PState s, int box, int n,
     if (track) {
       using PR = typename T::PR;
       st4((PR*)s.posr + slot, pos_record<M>(B, p, c, (R)((const V4*)s.omg)[slot].w));
-      if (skin_exceeded<M>(d, B, p, slot)) d.vctl[kCtlRequest] = 1u;
+      if (has_skin_test(d, B)) {
+        const P q[3] = {((const P*)d.xb)[slot], ((const P*)d.yb)[slot], ((const P*)d.zb)[slot]};
+        if (skin_exceeded<M>(B, p, q)) d.vctl[kCtlRequest] = 1u;
+      }
     } else {
       s.cellx[slot] = pack_cell(c[0], c[1], c[2]);
     }
@@ -2471,6 +2474,15 @@ k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, i
   }
   V4 vm = ((const V4*)b.vel)[i];
   V4 wr = ((const V4*)b.omg)[i];
+  // the position of the last re-sort, for the skin test at the end (loaded
+  // here, before the stores, so that its latency overlaps the integration)
+  const bool skin_test = has_skin_test(d, B);
+  P q[3] = {P(0), P(0), P(0)};
+  if (skin_test) {
+    q[0] = ((const P*)d.xb)[i];
+    q[1] = ((const P*)d.yb)[i];
+    q[2] = ((const P*)d.zb)[i];
+  }
   R m = vm.w, r = wr.w;
   v3<R> Tq = r * Ns;  // T = r (n x F), same sign for both members of a pair
   if (d.Ffused) {
@@ -2578,7 +2590,7 @@ k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, i
   b.cellc[i] = cnew;
   // the contact rule's record for the next step, then the skin test
   st4((typename T::PR*)b.posr + i, pos_record<M>(B, p, c, wr.w));
-  if (skin_exceeded<M>(d, B, p, i)) d.vctl[kCtlRequest] = 1u;
+  if (skin_test && skin_exceeded<M>(B, p, q)) d.vctl[kCtlRequest] = 1u;
   if (cnew != cc) {
     // moved to another cell: counts and the changed-cell flags of both
     const int g0 = b.cellg[i];
