@@ -2442,14 +2442,42 @@ k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, i
   const V4* Fc = (const V4*)d.Fc;
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
   if (!d.Ffused) {
-    // the slot's candidate pairs in increasing partner id, four at a time:
-    // their contact flags first, then the forces of the pairs in contact;
-    // Fc is the force on the pair's lower-id member: added when this slot is
-    // that member, subtracted otherwise; n x F enters with the same sign for
-    // both
+    // the slot's candidate pairs in increasing partner id (the first eight,
+    // then four at a time): their contact flags first, then the forces of
+    // the pairs in contact; Fc is the force on the pair's lower-id member:
+    // added when this slot is that member, subtracted otherwise; n x F
+    // enters with the same sign for both
     const int nrow = min(d.fcnt[i], d.K);
     const int* row = d.frow + (size_t)i * d.K;
-    for (int k = 0; k < nrow; k += 4) {
+    {
+      // the first eight entries (a row holds at least eight): their flags in
+      // one batch, then the records of those in contact
+      const int4 ea = *(const int4*)row, eb = *(const int4*)(row + 4);
+      const int e[8] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
+      unsigned mask = 0u;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (u < nrow && vl_flag[e[u] >> 1]) mask |= 1u << u;
+#pragma unroll
+      for (int g = 0; g < 8; g += 4) {
+        V4 fv[4], qv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (mask & (1u << (g + u))) {
+            fv[u] = ld4(Fc + 2 * (size_t)(e[g + u] >> 1));
+            qv[u] = ld4(Fc + 2 * (size_t)(e[g + u] >> 1) + 1);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (!(mask & (1u << (g + u)))) continue;
+          if (e[g + u] & 1) F = F + xyz(fv[u]);
+          else F = F - xyz(fv[u]);
+          Ns = Ns + xyz(qv[u]);
+        }
+      }
+    }
+    for (int k = 8; k < nrow; k += 4) {
       const int4 e4 = *(const int4*)(row + k);
       const int e[4] = {e4.x, e4.y, e4.z, e4.w};
       unsigned char f[4];
