@@ -157,8 +157,9 @@ int launches_per_step(const dem_ctx* ctx) {
   if (ctx->fused) return 7 + (ctx->hwalls.empty() ? 0 : 1);
   return 3 + (ctx->hwalls.empty() ? 0 : 1);
 }
-// kernels a re-sort adds (cell scan x3, scatter, reorder, search, rows, commit)
-int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 8 + (ctx->split ? 1 : 0); }
+// kernels a re-sort adds (cell scan x3, scatter, reorder, search, rows,
+// history, commit)
+int launches_per_resort(const dem_ctx* ctx) { return ctx->fused ? 0 : 9 + (ctx->split ? 1 : 0); }
 
 size_t pos_bytes(int mode) { return mode == kMIXED ? 8 : (mode == kFP64 ? 8 : 4); }
 size_t v4_bytes(int mode) { return mode == kFP64 ? 32 : 16; }

@@ -3,7 +3,7 @@
 // Per step (Nakahara & Washizawa, arXiv 1503.03553, Sec. 4.2 kernel list,
 // re-laid out for one GB300):
 //   scan of cell counts        -> cell starts          (CalcHash/BitonicSort)
-//   k_scatter + k_cellsort     -> permutation by (Morton cell, id)
+//   k_scatter                  -> permutation by (Morton cell, id)
 //   k_reorder                  -> state in sorted order (FindCellBoundsAndReorder)
 //   k_candidates               -> search over half the neighbour cells (the
 //                                 loops of Algorithm 1; the paper's first loop,
@@ -11,11 +11,12 @@
 //                                 skin: the candidate list (Sec. 3.4 split,
 //                                 global)
 //   k_rows                     -> each particle's candidates in partner-id
-//                                 order; delta_t history carried to the new
-//                                 list (InitializeContactIDs)
+//                                 order
+//   k_carry                    -> delta_t history carried to the new list
+//                                 (InitializeContactIDs)
 //   k_commit                   -> the sorted state and list become current
-//   (the five kernels above run only in a step that re-sorts: the first one,
-//    and then whenever a particle has moved far enough for a pair outside the
+//   (the kernels above run only in a step that re-sorts: the first one, and
+//    then whenever a particle has moved far enough for a pair outside the
 //    list to reach contact; k_decide makes that call on the device)
 //   k_pairs                    -> the contact rule on every candidate, ballot
 //                                 compaction of the contacts, one lane per
