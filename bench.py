@@ -39,7 +39,9 @@ METRIC = "particle-steps/s"  # the unit
 METRIC_NAME = ("particle-steps/s @1M: FP32 vs FP64 GPU at force rel err\u22641e-5; "
                "batched vs 1-by-1")
 L2_BYTES = 126.5 * 2 ** 20
-W2_R_MAX = 8e-6  # the largest radius of W2's law (clipped at 8 um)
+# the candidate-list skin of the other workloads' legs (W3, W4, W5 and the
+# tuner's starting layout), as a fraction of each box's largest radius
+OTHER_SKIN_OVER_RMAX = 0.025
 
 
 def _args():
@@ -50,8 +52,10 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64", "fp32"])
-    ap.add_argument("--skin-um", type=float, default=0.2,
-                    help="candidate-list skin in micrometres (0: search every step)")
+    ap.add_argument("--skin-um", type=float, default=0.04,
+                    help="candidate-list skin in micrometres (0: search every step); "
+                         "the default, 0.5 %% of the largest radius, is the layout "
+                         "tuner's choice on this workload (its leg reports it)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the FP64-GPU, parity and CPU-baseline side legs")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -541,10 +545,9 @@ def _side_legs(args, D, torch, box, ncell, stream, skin):
     leg("collide_fused_vs_compact", lambda: _fused_leg(args, D, torch, stream, box))
     leg("size_binned_search", lambda: _size_binned_leg(args, D, torch, stream, box, ncell))
     leg("fig4_kernel_times_131k", lambda: _fig4_leg(args, D, torch, stream))
-    skin_frac = skin / W2_R_MAX  # the W2 skin as a fraction of the largest radius
-    leg("layout_tuner", lambda: _tuner_leg(args, D, torch, stream, box, skin_frac))
+    leg("layout_tuner", lambda: _tuner_leg(args, D, torch, stream, box, OTHER_SKIN_OVER_RMAX))
     if not args.no_batched:
-        leg("batched", lambda: _batched_leg(args, D, torch, stream, skin_frac))
+        leg("batched", lambda: _batched_leg(args, D, torch, stream, OTHER_SKIN_OVER_RMAX))
     if args.w3:
         leg("w3_floor_8M", lambda: _w3_leg(args, D, torch, stream))
     if args.w5:
@@ -641,7 +644,7 @@ def _w3_leg(args, D, torch, stream):
     from paper_1503_03553_gb300 import synth
     from paper_1503_03553_gb300.synth import grid_for, prepared
     box = prepared(synth.w3_bidisperse_floor(n=8_000_000, seed=3), "mixed")
-    skin = W5_SKIN_OVER_RMAX * box.r_max  # the W2 line's skin fraction
+    skin = OTHER_SKIN_OVER_RMAX * box.r_max
     nc = grid_for(box)  # the per-particle forms and the search every step
     ncs = grid_for(box, skin=skin)
     res = {"particles": box.n, "ncell": nc, "ncell_with_skin": ncs, "skin_m": skin}
@@ -682,9 +685,6 @@ def _w5_oracle(path):
     return force_errors(b2, g, out, prec, detail=5)
 
 
-W5_SKIN_OVER_RMAX = 0.025  # the candidate-list skin of the W5 leg, as W2's
-
-
 def _w5_leg(args, D, torch, stream):
     """W5 precision stress: spheres of radius U[3, 5] um at packing 0.60
     relaxed to overlaps of about 1e-3 r, at rest; each form runs the full
@@ -706,7 +706,7 @@ def _w5_leg(args, D, torch, stream):
     with mp.get_context("spawn").Pool(workers) as pool:
         for prec in args.w5_forms.split(","):
             b = prepared(raw, prec)
-            skin = W5_SKIN_OVER_RMAX * b.r_max
+            skin = OTHER_SKIN_OVER_RMAX * b.r_max
             nc = grid_for(b, skin=skin)
             with torch.cuda.stream(stream):
                 ctx = D.Context([b], precision=prec, ncell=[nc], skins=[skin])
