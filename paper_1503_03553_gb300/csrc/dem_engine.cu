@@ -54,6 +54,7 @@ struct dem_ctx {
   cudaEvent_t xfer_ev[6] = {};
   int device = 0;
   int nsm = 152;
+  int pairs_grid = 0;  // blocks of the pair kernel: one wave (set at set-up)
   int N = 0, K = 32, Cmax = 0, M_lin = 0, M_rank = 0;
   int block = 256;
   int graph_steps = 16;
@@ -285,15 +286,10 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
   if (tm) cudaEventRecord(ev[3], s);
   const BoxDev B0 = box0_param(ctx);
   const bool one = ctx->hbox.size() == 1;
-  // the pair kernel runs as one wave: as many blocks as the GPU holds at
-  // once (its warps stride over the candidate tiles), which measured faster
-  // than more, shorter-lived blocks
-  int per_sm = 0;
-  if (one)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<M, true>, 32 * kPairWarps, 0);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pairs<M, false>, 32 * kPairWarps, 0);
-  const int pgrid = ctx->nsm * std::max(1, per_sm);
+  // the pair kernel runs as one wave of resident blocks (its warps stride
+  // over the candidate tiles), which measured faster than more,
+  // shorter-lived blocks
+  const int pgrid = ctx->pairs_grid;
   if (one)
     k_pairs<M, true><<<pgrid, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0], B0);
   else
@@ -407,6 +403,23 @@ int32_t dem_launches_per_step(const dem_ctx* ctx) {
 // dem_create and by the layout tuner (which re-creates it for other grids,
 // skins and size splits).  On failure *msg says why and nothing stays
 // allocated.
+// resident blocks per SM of the context's pair kernel
+static cudaError_t pairs_per_sm(const dem_ctx* ctx, int* per_sm) {
+  const bool one = ctx->hbox.size() == 1;
+  const int nt = 32 * kPairWarps;
+  switch (ctx->mode) {
+    case kFP64:
+      return one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pairs<kFP64, true>, nt, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pairs<kFP64, false>, nt, 0);
+    case kMIXED:
+      return one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pairs<kMIXED, true>, nt, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pairs<kMIXED, false>, nt, 0);
+    default:
+      return one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pairs<kFP32, true>, nt, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_pairs<kFP32, false>, nt, 0);
+  }
+}
+
 static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   auto bail = [&](dem_status s, const std::string& m) {
     *msg = m;
@@ -774,6 +787,13 @@ static dem_status setup_device(dem_ctx* ctx, std::string* msg) {
   if (!e && !ctx->fused) e = cudaMemsetAsync(d.fcnt, 0, sizeof(int) * n, s);
   if (!e) e = cudaStreamSynchronize(s);
   if (e) return bail(DEM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+  // the pair kernel runs as one wave: as many blocks as the GPU holds at
+  // once (queried here, outside any stream capture)
+  int per_sm = 0;
+  e = pairs_per_sm(ctx, &per_sm);
+  if (e || per_sm < 1)
+    return bail(DEM_ERR_CUDA, std::string("pair kernel occupancy: ") + cudaGetErrorString(e));
+  ctx->pairs_grid = ctx->nsm * per_sm;
   return DEM_OK;
 }
 
