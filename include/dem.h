@@ -186,7 +186,7 @@ typedef struct {
                               /* graphs; the other forms launch them       */
                               /* directly                                  */
   int32_t block;              /* threads per block of per-particle kernels; */
-                              /* 0 = 256                                   */
+                              /* 0 = 128                                   */
   void* stream;               /* cudaStream_t; NULL = legacy default stream */
   void* (*alloc)(size_t bytes, void* ctx);  /* device allocator or NULL     */
   void (*free)(void* ptr, void* ctx);

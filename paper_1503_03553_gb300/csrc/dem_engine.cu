@@ -825,7 +825,7 @@ dem_status dem_create(const dem_config* cfg, dem_ctx** out) {
   ctx->K = cfg->row_capacity > 0 ? cfg->row_capacity : 32;
   ctx->fused = cfg->collide == DEM_COLLIDE_FUSED || cfg->collide == DEM_COLLIDE_TWOLOOP;
   ctx->twoloop = cfg->collide == DEM_COLLIDE_TWOLOOP;
-  ctx->block = cfg->block > 0 ? cfg->block : 256;
+  ctx->block = cfg->block > 0 ? cfg->block : 128;  // the tuners' usual pick
   ctx->graph_steps = cfg->graph_steps == 0 ? 16 : cfg->graph_steps;
   if (ctx->graph_steps > 0 && (ctx->graph_steps & 1)) ctx->graph_steps += 1;
   auto bail = [&](dem_status s, const std::string& m) {
