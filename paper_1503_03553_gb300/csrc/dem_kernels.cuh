@@ -1817,8 +1817,8 @@ k_pairs(Dev d, PState b, VList vl, const __grid_constant__ BoxDev B0) {
   using T = Tr<M>;
   using V4 = typename T::V4;
   using DT = typename T::DT;
-  __shared__ int qcb[kPairWarps][kPairTile];
-  __shared__ int2 qpb[kPairWarps][kPairTile];
+  __shared__ int qcb[kPairWarps][kPairTile + 32];
+  __shared__ int2 qpb[kPairWarps][kPairTile + 32];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
@@ -1828,36 +1828,46 @@ k_pairs(Dev d, PState b, VList vl, const __grid_constant__ BoxDev B0) {
   const int nw = gridDim.x * kPairWarps;
   int mbox = -1;
   float m_ov = 0.0f, m_ratio = 0.0f;
-  for (int t0 = (blockIdx.x * kPairWarps + wi) * kPairTile; t0 < nc; t0 += nw * kPairTile) {
-    int2 pr[kPairU];
-    unsigned char fl[kPairU];
+  // qn pairs wait in the queue.  After each tile the whole groups of 32 are
+  // computed and the rest (fewer than 32) waits for the next tile's, so that
+  // every lane computes a force but in the warp's last group; one pass past
+  // the warp's last tile computes what is left.  (The force is computed at
+  // one place in the code, so that a pair's result does not depend on which
+  // group it falls in.)
+  int qn = 0;
+  for (int t0 = (blockIdx.x * kPairWarps + wi) * kPairTile;; t0 += nw * kPairTile) {
+    const bool more = t0 < nc;
+    if (more) {
+      int2 pr[kPairU];
+      unsigned char fl[kPairU];
 #pragma unroll
-    for (int u = 0; u < kPairU; ++u) {
-      const int c = t0 + u * 32 + lane;
-      pr[u] = c < nc ? vl.pair[c] : make_int2(-1, -1);
-      fl[u] = c < nc ? vl.flag[c] : 0;
-    }
-    int qn = 0;
+      for (int u = 0; u < kPairU; ++u) {
+        const int c = t0 + u * 32 + lane;
+        pr[u] = c < nc ? vl.pair[c] : make_int2(-1, -1);
+        fl[u] = c < nc ? vl.flag[c] : 0;
+      }
 #pragma unroll
-    for (int u = 0; u < kPairU; ++u) {
-      const int c = t0 + u * 32 + lane;
-      bool hit = false;
-      if (pr[u].x >= 0) {
-        const BoxDev& B = box_of<kOne>(d, B0, pr[u].x);
-        hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
-        if (!hit && fl[u]) vl.flag[c] = 0;  // left contact: no history any more
+      for (int u = 0; u < kPairU; ++u) {
+        const int c = t0 + u * 32 + lane;
+        bool hit = false;
+        if (pr[u].x >= 0) {
+          const BoxDev& B = box_of<kOne>(d, B0, pr[u].x);
+          hit = pair_in_contact<M>(B, b, pr[u].x, pr[u].y);
+          if (!hit && fl[u]) vl.flag[c] = 0;  // left contact: no history any more
+        }
+        const unsigned bal = __ballot_sync(full, hit);
+        if (hit) {
+          const int at = qn + __popc(bal & lt);
+          qc_[at] = (c << 1) | (fl[u] ? 1 : 0);
+          qp[at] = pr[u];
+        }
+        qn += __popc(bal);
       }
-      const unsigned bal = __ballot_sync(full, hit);
-      if (hit) {
-        const int at = qn + __popc(bal & lt);
-        qc_[at] = (c << 1) | (fl[u] ? 1 : 0);
-        qp[at] = pr[u];
-      }
-      qn += __popc(bal);
     }
     __syncwarp();
-    for (int k = 0; k < qn; k += 32) {
-      if (k + lane < qn) {
+    const int upto = more ? (qn & ~31) : qn;
+    for (int k = 0; k < upto; k += 32) {
+      if (k + lane < upto) {
         const int qc = qc_[k + lane];
         const int c = qc >> 1;
         const int2 p = qp[k + lane];
@@ -1882,6 +1892,14 @@ k_pairs(Dev d, PState b, VList vl, const __grid_constant__ BoxDev B0) {
         if (o.ov > 0.0f) track_diag(d, box, o.ov, o.ratio, mbox, m_ov, m_ratio);
       }
     }
+    if (!more) break;
+    __syncwarp();
+    // the rest moves to the front of the queue
+    if (lane < qn - upto) {
+      qc_[lane] = qc_[upto + lane];
+      qp[lane] = qp[upto + lane];
+    }
+    qn -= upto;
     __syncwarp();
   }
   flush_diag(d, mbox, m_ov, m_ratio);  // every lane of the warp gets here
