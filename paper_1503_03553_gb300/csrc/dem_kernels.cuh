@@ -1802,7 +1802,7 @@ __device__ __forceinline__ bool pair_in_contact(const BoxDev& B, const PState& b
 // pair's own list entry.  kOne: the context holds one box, whose constants
 // come in B0 (a kernel parameter, read through the constant cache; its
 // particle count is not valid there and is not read).
-constexpr int kPairU = 4;
+constexpr int kPairU = 2;
 constexpr int kPairTile = 32 * kPairU;
 constexpr int kPairWarps = 8;
 
