@@ -59,7 +59,7 @@ typedef enum {
   DEM_ERR_CUDA = 3,       /* a CUDA runtime call failed                     */
   DEM_ERR_CAPACITY = 4,   /* a contact row or the contact list overflowed   */
   DEM_ERR_NONFINITE = 5,  /* a position, velocity or force became NaN/Inf   */
-  DEM_ERR_TIMEOUT = 6,    /* reserved: no kernel of this build waits on     */
+  DEM_ERR_TIMEOUT = 6,    /* reserved: no kernel of this library waits on   */
                           /* another, so no wait can time out               */
   DEM_ERR_STATE = 7       /* call out of order (e.g. step before particles) */
 } dem_status;
