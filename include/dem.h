@@ -187,6 +187,17 @@ typedef struct {
                               /* directly                                  */
   int32_t block;              /* threads per block of per-particle kernels; */
                               /* 0 = 128                                   */
+  int32_t l2_fetch;           /* L2 fetch granularity in bytes set on the   */
+                              /* CUDA context at creation (the runtime's    */
+                              /* cudaLimitMaxL2FetchGranularity, a hint):   */
+                              /* 0 = 64, or 32, 64, 128; -1 = leave the     */
+                              /* context's limit alone.  The limit holds for */
+                              /* every kernel of the context (other         */
+                              /* libraries' too) until it is set again.  64 */
+                              /* keeps the per-particle sum's scattered     */
+                              /* 32-byte reads from fetching more; the pair */
+                              /* kernel asks for 128-byte fetches on its    */
+                              /* own loads of partner state                 */
   void* stream;               /* cudaStream_t; NULL = legacy default stream */
   void* (*alloc)(size_t bytes, void* ctx);  /* device allocator or NULL     */
   void (*free)(void* ptr, void* ctx);

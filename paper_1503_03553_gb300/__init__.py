@@ -77,7 +77,7 @@ class dem_config(C.Structure):
                 ("precision", C.c_int32), ("collide", C.c_int32),
                 ("kn_literal", C.c_int32), ("row_capacity", C.c_int32),
                 ("graph_steps", C.c_int32), ("block", C.c_int32),
-                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("l2_fetch", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_ctx", C.c_void_p)]
 
 
@@ -406,7 +406,7 @@ class Context:
 
     def __init__(self, boxes: Sequence, precision="mixed", collide=DEM_COLLIDE_COMPACT,
                  kn_literal=0, row_capacity=0, graph_steps=0, block=0,
-                 capacities: Optional[Sequence[int]] = None,
+                 l2_fetch=0, capacities: Optional[Sequence[int]] = None,
                  r_max: Optional[Sequence[float]] = None,
                  ncell: Optional[Sequence] = None, torch_alloc: bool = True,
                  skins: Optional[Sequence[float]] = None):
@@ -460,6 +460,7 @@ class Context:
         cfg.row_capacity = int(row_capacity)
         cfg.graph_steps = int(graph_steps)
         cfg.block = int(block)
+        cfg.l2_fetch = int(l2_fetch)
         self.stream = torch.cuda.current_stream()
         cfg.stream = C.c_void_p(self.stream.cuda_stream)
         self._device = torch.cuda.current_device()

@@ -218,6 +218,44 @@ __device__ __forceinline__ d4 ld4(const d4* p) {
   double2 a = __ldg(q), b = __ldg(q + 1);
   return {a.x, a.y, b.x, b.y};
 }
+// Read-only loads with a 128-byte L2 fetch hint (PTX ld.global.nc with
+// .L2::128B), for gathers whose neighbouring slots the same warp reads soon
+// after (the pair kernel's loads of both members' state: a warp's pairs lie in
+// a few neighbouring cells), whatever fetch granularity the context sets for
+// the other loads.
+__device__ __forceinline__ float4 ld4_fetch128(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L2::128B.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ d4 ld4_fetch128(const d4* p) {
+  d4 v;
+  asm("ld.global.nc.L2::128B.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  asm("ld.global.nc.L2::128B.v2.f64 {%0, %1}, [%2];"
+      : "=d"(v.z), "=d"(v.w) : "l"(reinterpret_cast<const double*>(p) + 2));
+  return v;
+}
+__device__ __forceinline__ long long ld_fetch128(const long long* p) {
+  long long v;
+  asm("ld.global.nc.L2::128B.s64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ double ld_fetch128(const double* p) {
+  double v;
+  asm("ld.global.nc.L2::128B.f64 %0, [%1];" : "=d"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_fetch128(const float* p) {
+  float v;
+  asm("ld.global.nc.L2::128B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ int ld_fetch128(const int* p) {
+  int v;
+  asm("ld.global.nc.L2::128B.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
 __device__ __forceinline__ void st4(float4* p, float4 v) { *p = v; }
 __device__ __forceinline__ void st4(d4* p, d4 v) {
   double2* q = reinterpret_cast<double2*>(p);

@@ -1592,22 +1592,24 @@ __device__ __forceinline__ void pair_law(const PState& b, const BoxDev& B, int i
   const P* __restrict__ pz = (const P*)b.pz;
   const V4* __restrict__ vel = (const V4*)b.vel;
   const V4* __restrict__ omg = (const V4*)b.omg;
-  V4 v1 = ld4(vel + i), v2 = ld4(vel + j);
-  V4 w1 = ld4(omg + i), w2 = ld4(omg + j);
+  V4 v1 = ld4_fetch128(vel + i), v2 = ld4_fetch128(vel + j);
+  V4 w1 = ld4_fetch128(omg + i), w2 = ld4_fetch128(omg + j);
   R r1 = w1.w, r2 = w2.w;
   v3<R> n;
   R dn;
   if (M == kMIXED) {
     float fn_dn;
     v3<float> fn_n;
-    geom_fixed(B, (long long)px[i], (long long)py[i], (long long)pz[i],
-               (long long)px[j], (long long)py[j], (long long)pz[j],
+    geom_fixed(B, (long long)ld_fetch128(px + i), (long long)ld_fetch128(py + i),
+               (long long)ld_fetch128(pz + i), (long long)ld_fetch128(px + j),
+               (long long)ld_fetch128(py + j), (long long)ld_fetch128(pz + j),
                (float)r1, (float)r2, fn_n, fn_dn);
     n = {(R)fn_n.x, (R)fn_n.y, (R)fn_n.z};
     dn = (R)fn_dn;
   } else {
-    geom_abs<R>(B, (R)px[i], (R)py[i], (R)pz[i], (R)px[j], (R)py[j],
-                (R)pz[j], r1, r2, n, dn);
+    geom_abs<R>(B, (R)ld_fetch128(px + i), (R)ld_fetch128(py + i), (R)ld_fetch128(pz + i),
+                (R)ld_fetch128(px + j), (R)ld_fetch128(py + j), (R)ld_fetch128(pz + j), r1, r2,
+                n, dn);
   }
   out.F4 = V4{};
   out.N4 = V4{};
@@ -1783,13 +1785,13 @@ __device__ __forceinline__ bool pair_in_contact(const BoxDev& B, const PState& b
   using PR = typename Tr<M>::PR;
   const int w = B.rsplit_f < INFINITY ? 2 : 1;  // size-binned boxes: +-2 cells
   int ci[3], cj[3];
-  unpack_cell(b.cellc[i], ci[0], ci[1], ci[2]);
-  unpack_cell(b.cellc[j], cj[0], cj[1], cj[2]);
+  unpack_cell(ld_fetch128(b.cellc + i), ci[0], ci[1], ci[2]);
+  unpack_cell(ld_fetch128(b.cellc + j), cj[0], cj[1], cj[2]);
   float sh[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     if (!pair_shift<M>(B, a, ci[a], cj[a], w, sh[a])) return false;
-  const PR pi = ld4((const PR*)b.posr + i), pj = ld4((const PR*)b.posr + j);
+  const PR pi = ld4_fetch128((const PR*)b.posr + i), pj = ld4_fetch128((const PR*)b.posr + j);
   if (M == kMIXED) return pred_fixed(*(const float4*)&pi, *(const float4*)&pj, sh[0], sh[1], sh[2]);
   return pred_abs(pi, pj, B);
 }
