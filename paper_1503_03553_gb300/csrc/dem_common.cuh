@@ -256,6 +256,17 @@ __device__ __forceinline__ int ld_fetch128(const int* p) {
   asm("ld.global.nc.L2::128B.s32 %0, [%1];" : "=r"(v) : "l"(p));
   return v;
 }
+// Programmatic dependent launch (PTX griddepcontrol): a kernel launched with
+// the programmatic stream serialization attribute may start while the kernel
+// before it in the stream is still running, once that kernel's blocks have
+// all signalled (or exited); it must wait (pdl_wait: until that kernel has
+// completed and its writes are visible) before it reads what that kernel
+// writes or writes what it reads.  Both are no-ops for a kernel launched
+// without the attribute.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void st4(float4* p, float4 v) { *p = v; }
 __device__ __forceinline__ void st4(d4* p, d4 v) {
   double2* q = reinterpret_cast<double2*>(p);

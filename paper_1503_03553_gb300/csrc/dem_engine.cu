@@ -296,12 +296,25 @@ void enqueue_tail(dem_ctx* ctx, bool store_ft, bool tm, cudaEvent_t* ev) {
     k_pairs<M, false><<<pgrid, 32 * kPairWarps, 0, s>>>(d, ctx->ps[0], ctx->vl[0], B0);
   if (tm) cudaEventRecord(ev[4], s);
   if (d.Fwall) k_walls<M><<<blocks_for(d.N, bs), bs, 0, s>>>(d, ctx->ps[0]);
+  // the sum kernel as a programmatic dependent of the kernel before it: its
+  // blocks start on the SMs the pair kernel's blocks leave, read their rows
+  // and wait there for the pair kernel's results
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3(blocks_for(d.N, bs));
+  lc.blockDim = dim3(bs);
+  lc.dynamicSmemBytes = 0;
+  lc.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  lc.attrs = at;
+  lc.numAttrs = 1;
+  const int sft = store_ft ? 1 : 0;
+  const unsigned char* flag = ctx->vl[0].flag;
   if (one)
-    k_gather_integrate<M, true><<<blocks_for(d.N, bs), bs, 0, s>>>(
-        d, ctx->ps[0], ctx->vl[0].flag, store_ft ? 1 : 0, B0);
+    cudaLaunchKernelEx(&lc, k_gather_integrate<M, true>, d, ctx->ps[0], flag, sft, B0);
   else
-    k_gather_integrate<M, false><<<blocks_for(d.N, bs), bs, 0, s>>>(
-        d, ctx->ps[0], ctx->vl[0].flag, store_ft ? 1 : 0, B0);
+    cudaLaunchKernelEx(&lc, k_gather_integrate<M, false>, d, ctx->ps[0], flag, sft, B0);
   if (tm) cudaEventRecord(ev[5], s);
 }
 

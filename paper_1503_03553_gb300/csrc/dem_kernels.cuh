@@ -1826,6 +1826,9 @@ k_pairs(Dev d, PState b, VList vl, const __grid_constant__ BoxDev B0) {
   const unsigned lt = (1u << lane) - 1u;
   int* qc_ = qcb[wi];
   int2* qp = qpb[wi];
+  // the sum kernel after this one may start on the SMs this kernel's blocks
+  // leave (it waits for this kernel's results before it reads them)
+  pdl_launch_dependents();
   const int nc = min(*vl.count, d.Cmax);
   const int nw = gridDim.x * kPairWarps;
   int mbox = -1;
@@ -2462,18 +2465,28 @@ k_gather_integrate(Dev d, PState b, const unsigned char* __restrict__ vl_flag, i
   if (i - B.pbase >= d.boxes[bi].nlive) return;
   const V4* Fc = (const V4*)d.Fc;
   v3<R> F = {R(0), R(0), R(0)}, Ns = {R(0), R(0), R(0)};
+  // Launched as a dependent of the pair kernel, this kernel may start while
+  // that kernel finishes: before waiting for it, it reads only what the pair
+  // kernel does not write (the row, written at the last re-sort) and writes
+  // nothing.  (Asking L2 for the slot's own state there as well measured
+  // slower.)
+  const int* row = d.Ffused ? nullptr : d.frow + (size_t)i * d.K;
+  const int nrow = d.Ffused ? 0 : min(d.fcnt[i], d.K);
+  int4 ea = make_int4(0, 0, 0, 0), eb = ea;
+  if (!d.Ffused) {
+    ea = *(const int4*)row;
+    eb = *(const int4*)(row + 4);
+  }
+  pdl_wait();
   if (!d.Ffused) {
     // the slot's candidate pairs in increasing partner id (the first eight,
     // then four at a time): their contact flags first, then the forces of
     // the pairs in contact; Fc is the force on the pair's lower-id member:
     // added when this slot is that member, subtracted otherwise; n x F
     // enters with the same sign for both
-    const int nrow = min(d.fcnt[i], d.K);
-    const int* row = d.frow + (size_t)i * d.K;
     {
       // the first eight entries (a row holds at least eight): their flags in
       // one batch, then the records of those in contact
-      const int4 ea = *(const int4*)row, eb = *(const int4*)(row + 4);
       const int e[8] = {ea.x, ea.y, ea.z, ea.w, eb.x, eb.y, eb.z, eb.w};
       unsigned mask = 0u;
 #pragma unroll
