@@ -1972,21 +1972,47 @@ k_rows(Dev d, PState b, VList vn) {
   for (int k = 0; k < own; ++k) vn.flag[hs + k] = 0;
   if (n <= 16) {
     int key[16], val[16];
+    // the row's inputs in 16-byte loads; the own entries fill the first
+    // places, the incoming ones the last (entry m at place W - 1 - m), the
+    // places between hold the largest key: every register index is fixed
+    const int ninc = n - own;
+    int4 ko[4], ic[8];
 #pragma unroll
-    for (int k = 0; k < 16; ++k) {
+    for (int q = 0; q < 4; ++q)
+      ko[q] = 4 * q < own ? *(const int4*)(kr + 4 * q) : make_int4(0, 0, 0, 0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      ic[q] = 2 * q < ninc ? *(const int4*)(in + 2 * q) : make_int4(0, 0, 0, 0);
+    const bool w8 = __all_sync(__activemask(), n <= 8);  // W = 8, else 16
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      const int4 o4 = ko[s >> 2];
+      const int oid = (s & 3) == 0 ? o4.x : (s & 3) == 1 ? o4.y : (s & 3) == 2 ? o4.z : o4.w;
       int id = INT_MAX, v = 0;
-      if (k < own) {
-        id = kr[k];
-        v = ((hs + k) << 1) | (idi < id ? 1 : 0);
-      } else if (k < n) {
-        const int2 e = in[k - own];
-        id = e.y >> 1;
-        v = (e.x << 1) | (e.y & 1);
+      if (s < own) {
+        id = oid;
+        v = ((hs + s) << 1) | (idi < id ? 1 : 0);
       }
-      key[k] = id;
-      val[k] = v;
+      key[s] = id;
+      val[s] = v;
     }
-    if (__all_sync(__activemask(), n <= 8)) bitonic_sort<8>(key, val);
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+      const int4 c4 = ic[m >> 1];
+      const int ex = (m & 1) ? c4.z : c4.x, ey = (m & 1) ? c4.w : c4.y;
+      if (m < ninc) {
+        if (w8) {
+          if (m < 8) {
+            key[7 - m] = ey >> 1;
+            val[7 - m] = (ex << 1) | (ey & 1);
+          }
+        } else {
+          key[15 - m] = ey >> 1;
+          val[15 - m] = (ex << 1) | (ey & 1);
+        }
+      }
+    }
+    if (w8) bitonic_sort<8>(key, val);
     else bitonic_sort<16>(key, val);
 #pragma unroll
     for (int k = 0; k < 16; k += 4) {
