@@ -50,7 +50,7 @@
 extern "C" {
 #endif
 
-#define DEM_ABI_VERSION 4
+#define DEM_ABI_VERSION 5
 
 typedef enum {
   DEM_OK = 0,

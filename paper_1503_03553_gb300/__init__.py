@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdem_gb300.so")
 
-ABI_VERSION = 4  # the include/dem.h this binding marshals for
+ABI_VERSION = 5  # the include/dem.h this binding marshals for
 DEM_OK, DEM_ERR_ARG, DEM_ERR_ALLOC, DEM_ERR_CUDA, DEM_ERR_CAPACITY = 0, 1, 2, 3, 4
 DEM_ERR_NONFINITE, DEM_ERR_TIMEOUT, DEM_ERR_STATE = 5, 6, 7
 DEM_FP64, DEM_MIXED, DEM_FP32 = 0, 1, 2
