@@ -65,6 +65,31 @@ def test_create_rejects_bad_config_without_gpu(lib):
     assert e.value.status == D.DEM_ERR_ARG
 
 
+@pytest.mark.parametrize("field, value, words", [
+    ("l2_fetch", 7, "l2_fetch"), ("l2_fetch", 256, "l2_fetch"), ("block", 48, "block"),
+    ("row_capacity", 2000, "row_capacity"), ("precision", 3, "precision")])
+def test_create_rejects_bad_launch_settings_without_gpu(lib, field, value, words):
+    """A config that is complete but for one bad setting is refused before
+    any device call, with the setting named."""
+    import ctypes as C
+    import paper_1503_03553_gb300 as D
+    mat = (D.dem_material * 1)()
+    mat[0].E, mat[0].poisson, mat[0].density = 5e9, 0.3, 1000.0
+    mat[0].restitution, mat[0].mu_d = 0.5, 0.5
+    box = (D.dem_box * 1)()
+    for a in range(3):
+        box[0].L[a], box[0].periodic[a] = 1e-4, 1
+    box[0].dt, box[0].max_particles, box[0].r_max = 1e-9, 16, 5e-6
+    cfg = D.dem_config()
+    cfg.nboxes, cfg.boxes = 1, C.cast(box, C.POINTER(D.dem_box))
+    cfg.nmaterials, cfg.materials = 1, C.cast(mat, C.POINTER(D.dem_material))
+    setattr(cfg, field, value)
+    with pytest.raises(D.DemError) as e:
+        D.dem_create(cfg)
+    assert e.value.status == D.DEM_ERR_ARG
+    assert words in str(e.value), str(e.value)
+
+
 def test_header_compiles_as_c_and_matches_the_binding(tmp_path):
     """include/dem.h compiles as C99, and the sizes and member offsets of its
     structs are those of the ctypes structures of the binding."""
