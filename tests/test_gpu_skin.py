@@ -100,6 +100,18 @@ def _stepwise(b, precision, ncell, skin, nmax):
     return found
 
 
+@pytest.mark.parametrize("l2_fetch", [-1, 32, 128])
+def test_l2_fetch_setting_leaves_results_unchanged(dense3k, l2_fetch):
+    """The context's L2 fetch granularity (dem_config.l2_fetch; the library
+    sets 64 bytes unless told otherwise) is a hint to the memory system:
+    every result is the same, bit for bit, whatever it is set to."""
+    b = prepared(dense3k, "mixed")
+    ncell = grid_for(b, skin=SKIN_SMALL)
+    ref = gpu_run([b], "mixed", [ncell], steps=40, skins=[SKIN_SMALL])[0]
+    g = gpu_run([b], "mixed", [ncell], steps=40, skins=[SKIN_SMALL], l2_fetch=l2_fetch)[0]
+    _same(ref, g)
+
+
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_steps_between_and_at_resorts_match_oracle(dense3k, precision):
     b = prepared(dense3k, precision)
