@@ -259,6 +259,17 @@ def _cpu_model():
     return None
 
 
+def _w2_construction(n):
+    """How the W2 box of n particles is built (synth.w2_polydisperse)."""
+    from paper_1503_03553_gb300 import synth
+    k, n0 = synth.tiling(n)
+    law = "radii log-normal (median 4 um, log-sd 0.25, clipped to 2-8 um)"
+    if k == 1:
+        return f"one relaxed tile of {n0} spheres, {law}"
+    return (f"{k}^3 copies of one relaxed tile of {n0} spheres, {law}; "
+            "particle ids in random order")
+
+
 def _oracle_threads():
     return int(os.environ.get("OMP_NUM_THREADS") or os.cpu_count() or 1)
 
@@ -479,6 +490,7 @@ def main():
         "config": {"workload": f"W2 polydisperse periodic box, {n} particles per GPU, "
                    "packing 0.55, dense contact network; steps 1..K from the initial "
                    "state (the packing relaxes: contacts fall during the run)",
+                   "construction": _w2_construction(n),
                    "steps_from_initial_state": args.steps,
                    "n_per_gpu": n, "precision": args.precision,
                    "precision_detail": {"mixed": "FP32 force arithmetic; positions in 64-bit "

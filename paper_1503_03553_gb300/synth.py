@@ -245,6 +245,15 @@ def _tile(rng, x, r, L, k):
     return X[perm], R[perm], tuple(k * l for l in L)
 
 
+def tiling(n: int, tile_n: int = 8000) -> tuple:
+    """(k, n0): a box of n > tile_n particles is k^3 copies of one relaxed
+    tile of n0 particles (n rounded to k^3 n0); (1, n) otherwise."""
+    if n <= tile_n:
+        return 1, n
+    k = max(1, int(round((n / tile_n) ** (1.0 / 3.0))))
+    return k, int(round(n / k ** 3))
+
+
 def w2_polydisperse(n: int = 1_000_000, seed: int = 2, tile_n: int = 8000,
                     phi: float = 0.55) -> Box:
     """W2: dense polydisperse periodic box (the throughput workload).  For
@@ -255,8 +264,7 @@ def w2_polydisperse(n: int = 1_000_000, seed: int = 2, tile_n: int = 8000,
     if n <= tile_n:
         x, r, L = _dense_tile(rng, n, phi, radii, 0.01)
     else:
-        k = max(1, int(round((n / tile_n) ** (1.0 / 3.0))))
-        n0 = int(round(n / k ** 3))
+        k, n0 = tiling(n, tile_n)
         x0, r0, L0 = _dense_tile(rng, n0, phi, radii, 0.01)
         x, r, L = _tile(rng, x0, r0, L0, k)
     m = len(r)

@@ -38,7 +38,7 @@ def _rank_main(rank, world, port, out):
 
 def test_two_gloo_ranks_combine_like_the_bench():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork: earlier tests may have started threads
     out = mgr.dict()
     mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
     assert out[0] == out[1]
