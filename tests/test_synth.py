@@ -73,3 +73,22 @@ def test_lattice_gas_has_no_contacts():
     t = cKDTree(np.mod(b.x, L), boxsize=L)
     d, _ = t.query(np.mod(b.x, L), k=2)
     assert np.all(d[:, 1] > 2 * b.r.max())
+
+
+def test_w2_tiling_of_large_boxes():
+    """A W2 box above one tile is k^3 shifted copies of one relaxed tile,
+    its ids in random order (the bench's 1 M box: 5^3 tiles of 8,000)."""
+    assert synth.tiling(1_000_000) == (5, 8000)
+    assert synth.tiling(512_000) == (4, 8000)
+    assert synth.tiling(3000) == (1, 3000)
+    tile = synth.w2_polydisperse(n=1000, seed=7, tile_n=1000)
+    big = synth.w2_polydisperse(n=8000, seed=7, tile_n=1000)
+    assert big.n == 8000 and np.allclose(big.L, 2 * np.asarray(tile.L))
+    assert np.array_equal(np.sort(big.r), np.sort(np.tile(tile.r, 8)))
+    # every particle sits at a tile particle's position shifted by whole tiles
+    L0 = np.asarray(tile.L)
+    frac = np.mod(big.x, L0)
+    key = lambda x: np.round(np.mod(x, L0) / L0 * 2 ** 20).astype(np.int64)
+    a = {tuple(k) for k in key(tile.x)}
+    assert all(tuple(k) in a for k in key(frac))
+    assert not np.array_equal(big.r[:1000], tile.r)  # ids are not in tile order
