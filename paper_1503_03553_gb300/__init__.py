@@ -144,22 +144,28 @@ def _check(ctx, status: int):
 # ---------------------------------------------------------------------------
 # array marshalling
 # ---------------------------------------------------------------------------
-def _ptr(a, where: int, dtype=np.float64, shape=None):
+def _ptr(a, where: int, dtype=np.float64, elems=None, name="array"):
     """Return (pointer, keepalive) for a numpy array (host) or a torch tensor
-    (device)."""
+    (device, on the current CUDA device).  elems: the number of elements the
+    C call reads or writes there; an array of another size is refused before
+    the call (a short one would be read or written past its end)."""
     if a is None:
         return None, None
     if where == DEM_DEVICE:
         import torch
         if not (isinstance(a, torch.Tensor) and a.is_cuda):
-            raise TypeError("device arrays must be CUDA tensors")
+            raise TypeError(f"{name}: device arrays must be CUDA tensors")
         want = torch.float64 if dtype == np.float64 else torch.int32
         if a.dtype != want or not a.is_contiguous():
-            raise TypeError(f"device array must be contiguous {want}")
+            raise TypeError(f"{name}: device array must be contiguous {want}")
+        if a.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device")
+        if elems is not None and a.numel() != elems:
+            raise ValueError(f"{name} must hold {elems} elements, not {a.numel()}")
         return C.c_void_p(a.data_ptr()), a
     arr = np.ascontiguousarray(a, dtype=dtype)
-    if shape is not None and arr.shape != shape:
-        arr = arr.reshape(shape)
+    if elems is not None and arr.size != elems:
+        raise ValueError(f"{name} must hold {elems} elements, not {arr.size}")
     return C.c_void_p(arr.ctypes.data), arr
 
 
@@ -221,18 +227,21 @@ def dem_destroy(ctx) -> None:
 
 
 def dem_set_particles(ctx, box: int, x, v, omega, radius, where: int = DEM_HOST):
+    """x, v, omega: (n, 3); radius: (n,); n is x's first dimension."""
     n = int(x.shape[0])
-    px, kx = _ptr(x, where)
-    pv, kv = _ptr(v, where)
-    pw, kw = _ptr(omega, where)
-    pr, kr = _ptr(radius, where)
+    px, kx = _ptr(x, where, elems=3 * n, name="x")
+    pv, kv = _ptr(v, where, elems=3 * n, name="v")
+    pw, kw = _ptr(omega, where, elems=3 * n, name="omega")
+    pr, kr = _ptr(radius, where, elems=n, name="radius")
     _check(ctx, lib().dem_set_particles(ctx, box, n, px, pv, pw, pr, where))
 
 
 def dem_set_state(ctx, box: int, x=None, v=None, omega=None, where: int = DEM_HOST):
-    px, kx = _ptr(x, where)
-    pv, kv = _ptr(v, where)
-    pw, kw = _ptr(omega, where)
+    """Each given array: (n, 3) with n the box's particle count."""
+    n = dem_get_count(ctx, box)
+    px, kx = _ptr(x, where, elems=3 * n, name="x")
+    pv, kv = _ptr(v, where, elems=3 * n, name="v")
+    pw, kw = _ptr(omega, where, elems=3 * n, name="omega")
     _check(ctx, lib().dem_set_state(ctx, box, px, pv, pw, where))
 
 
@@ -250,11 +259,14 @@ def dem_get_state(ctx, box: int, x=None, v=None, omega=None, force=None,
                   torque=None, where: int = DEM_HOST):
     """Fill the given arrays (n x 3 float64, numpy for DEM_HOST, CUDA
     tensors for DEM_DEVICE)."""
-    ptrs = [(_ptr(a, where)[0] if a is not None else None) for a in (x, v, omega, force, torque)]
-    for a in (x, v, omega, force, torque):
+    n = dem_get_count(ctx, box)
+    names = ("x", "v", "omega", "force", "torque")
+    for a, name in zip((x, v, omega, force, torque), names):
         if a is not None and where == DEM_HOST:
             if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
-                raise TypeError("host outputs must be C-contiguous float64 numpy arrays")
+                raise TypeError(f"{name}: host outputs must be C-contiguous float64 numpy arrays")
+    ptrs = [_ptr(a, where, elems=3 * n, name=name)[0]
+            for a, name in zip((x, v, omega, force, torque), names)]
     _check(ctx, lib().dem_get_state(ctx, box, *ptrs, where))
 
 

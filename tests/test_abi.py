@@ -119,3 +119,19 @@ def test_header_compiles_as_c_and_matches_the_binding(tmp_path):
         assert seen[(name, "size")] == C.sizeof(cls), name
         for fname, _ in cls._fields_:
             assert seen[(name, fname)] == getattr(cls, fname).offset, (name, fname)
+
+
+def test_host_arrays_of_the_wrong_size_are_refused_before_the_call(lib):
+    """The binding checks the element count of every array a C call reads or
+    writes (a short array would be read or written past its end)."""
+    import numpy as np
+    import paper_1503_03553_gb300 as D
+    p, keep = D._ptr(np.zeros((4, 3)), D.DEM_HOST, elems=12, name="x")
+    assert p.value == keep.ctypes.data
+    with pytest.raises(ValueError, match="x must hold 12 elements, not 9"):
+        D._ptr(np.zeros((3, 3)), D.DEM_HOST, elems=12, name="x")
+    with pytest.raises(ValueError, match="radius must hold 4 elements, not 5"):
+        D._ptr(np.zeros(5), D.DEM_HOST, elems=4, name="radius")
+    assert D._ptr(None, D.DEM_HOST, elems=12) == (None, None)
+    with pytest.raises(TypeError, match="CUDA tensors"):
+        D._ptr(np.zeros((4, 3)), D.DEM_DEVICE, elems=12, name="x")
